@@ -1,0 +1,29 @@
+"""FP64 CPU oracle for the two-beam FFT beam-propagation z-march.
+
+TEST INFRASTRUCTURE ONLY.  This package is a plain, slow, deliberately
+unoptimised restatement of the method of Krzywinski & Halavanau,
+"Simulation package for solving dynamic diffraction problems in deformed
+crystals using beam propagation method" (arXiv 2601.06340), written in
+numpy float64 / complex128 so that a reader can check it against the paper's
+equations by eye.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it.
+The product path (``paper_2601_06340_gb300``) never imports, links or runs
+anything here, and this package imports nothing from the product path.
+
+Modules
+-------
+``bpm``       plan scalars (Eqs. fov3-fov12), Bessel series, the first-order
+              two-beam march (Eq. fov10), powers and records.
+``geometry``  crystal-shape masks (slab of any asymmetry angle, polygon) and
+              displacement fields (cylindrical bend, Eq. fov110; edge
+              dislocation, Eq. fov120 with the Burgers vector normal to the
+              line), and the strain phase h*u_x of Eq. (Authier).
+``timeaxis``  the energy -> time transform of a batch of exit fields
+              (Section "Time-Dependent Simulation of Reflection").
+
+Every function is pinned by a ``-m "not gpu"`` test in
+``tests/test_oracle_pins.py`` against closed forms, invariants, brute force
+or a library routine.  The one function without such a pin is
+``timeaxis.omega_to_t`` beyond its DFT definition: its physical time axis
+reading is stated in its docstring.
+"""

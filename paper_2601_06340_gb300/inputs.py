@@ -1,0 +1,289 @@
+"""Seeded synthetic inputs for the two-beam FFT-BPM z-march.
+
+This module is shared by the tests, the benchmark and users who want the
+standard workloads.  It builds *inputs only* -- grids, photon energies,
+incident envelopes, crystal-shape descriptors, displacement descriptors --
+and holds none of the march's arithmetic (no propagators, no coupling, no
+FFTs).  Every random draw comes from ``numpy.random.default_rng`` with a
+fixed seed (base seed 20260106, workload i uses base + i).
+
+The five workloads are the problem classes the paper simulates (Laue and
+Bragg slabs, bent crystals, dislocations in arbitrarily shaped crystals,
+time-dependent pulses as batches of photon energies) with the sizes of the
+project's benchmark table:
+
+1. ``laue_perfect``      symmetric Laue, perfect, 8 keV, 100 um, Nx=1024, Nz=2000
+2. ``bragg_bent``        symmetric Bragg, bent R = 1 m, 200 um, Nx=4096, Nz=8000
+3. ``asym_dislocation``  asymmetric Bragg (10 deg) slab cut by a seeded star
+                         polygon, edge dislocation, Nx=8192, Nz=12000
+4. ``pulse_batched``     256 energies over 9 keV +- 5 eV, Laue, bent R = 2 m,
+                         Nx=4096, Nz=6000, SASE-like random spectral phases
+5. ``serving_stream``    Poisson request stream of mixed solves (see
+                         ``serving_requests``)
+
+Each builder takes optional smaller ``nx`` / ``nz`` so that the same
+geometry can be run at sizes the FP64 oracle finishes in seconds.
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+BASE_SEED = 20260106
+HC_EV_ANGSTROM = 12398.419843320026
+
+# Kind codes (same values as include/bpm.h).
+CRYSTAL_VACUUM, CRYSTAL_BULK, CRYSTAL_SLAB, CRYSTAL_MASK = 0, 1, 2, 3
+CRYSTAL_SLAB_AND_MASK, CRYSTAL_SLAB_AND_POLYGON = 4, 5
+STRAIN_NONE, STRAIN_ARRAY, STRAIN_BENT, STRAIN_EDGE_DISLOCATION = 0, 1, 2, 3
+
+# Si(220)-like reflection at 8 keV as configured (Bragg angle 23.65 deg).
+E_REF_EV = 8000.0
+THETA_B_REF = math.radians(23.65)
+CHI0 = complex(-1.51e-5, 3.5e-7)
+CHIH = complex(-9.1e-6, 3.4e-7)
+
+
+@dataclass
+class Workload:
+    name: str
+    nx: int
+    nz: int
+    dx_um: float
+    dz_um: float
+    x0_um: float
+    energies_ev: np.ndarray
+    e_ref_ev: float
+    theta_b_ref_rad: float
+    chi0: complex
+    chih: complex
+    record_every: int
+    crystal: dict
+    strain: dict
+    psi0: np.ndarray                      # [B][2][N] complex128
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def batch(self) -> int:
+        return len(self.energies_ev)
+
+    @property
+    def cell_updates(self) -> int:
+        return self.batch * self.nx * self.nz
+
+
+def gaussian_envelope(nx: int, x0_um: float, dx_um: float, centre_um: float,
+                      fwhm_um: float, cos_theta: float,
+                      tilt_per_um: float = 0.0) -> np.ndarray:
+    """Incident psi_+(x, z=0): intensity FWHM ``fwhm_um`` measured normal to
+    the beam, so the trace on the z = 0 plane has FWHM fwhm / cos(theta);
+    ``tilt_per_um`` adds a linear envelope phase (rad / um) about the centre.
+    """
+    x = x0_um + np.arange(nx, dtype=np.float64) * dx_um
+    wx = fwhm_um / cos_theta
+    amp = np.exp(-2.0 * math.log(2.0) * ((x - centre_um) / wx) ** 2)
+    return amp * np.exp(1j * tilt_per_um * (x - centre_um))
+
+
+def _two_band(psi_plus: np.ndarray) -> np.ndarray:
+    out = np.zeros((1, 2, psi_plus.shape[-1]), dtype=np.complex128)
+    out[0, 0] = psi_plus
+    return out
+
+
+def laue_perfect(nx: int = 1024, nz: int = 2000, dx_um: float = 0.4,
+                 dz_um: float = 0.05, record_every: int = 100) -> Workload:
+    """Symmetric Laue slab of 100 um (Pi = 1 on every step of the march)."""
+    x0 = -0.5 * nx * dx_um
+    c = math.cos(THETA_B_REF)
+    psi0 = _two_band(gaussian_envelope(nx, x0, dx_um, 0.0, 20.0, c))
+    return Workload(
+        "laue_perfect", nx, nz, dx_um, dz_um, x0, np.array([E_REF_EV]),
+        E_REF_EV, THETA_B_REF, CHI0, CHIH, record_every,
+        crystal=dict(kind=CRYSTAL_SLAB, asym_angle_rad=math.pi / 2,
+                     thickness_um=100.0, surf_x_um=0.0, surf_z_um=0.0),
+        strain=dict(kind=STRAIN_NONE), psi0=psi0)
+
+
+def bragg_bent(nx: int = 4096, nz: int = 8000, dx_um: float = 0.2,
+               dz_um: float = 0.1, record_every: int = 100,
+               radius_um: float = 1.0e6, nu: float = 0.28) -> Workload:
+    """Symmetric Bragg slab x in [0, 200] um, bent (u = (x^2 + nu z'^2)/2R).
+
+    The beam (50 um FWHM) starts at z = 0 and hits the surface x = 0 at
+    z_hit = (march length) * 5/16 (250 um for the full 800 um march).
+    """
+    x0 = -0.5 * nx * dx_um
+    tan_t = math.tan(THETA_B_REF)
+    z_hit = nz * dz_um * 5.0 / 16.0
+    xc = -tan_t * z_hit
+    psi0 = _two_band(gaussian_envelope(nx, x0, dx_um, xc, 50.0,
+                                       math.cos(THETA_B_REF)))
+    return Workload(
+        "bragg_bent", nx, nz, dx_um, dz_um, x0, np.array([E_REF_EV]),
+        E_REF_EV, THETA_B_REF, CHI0, CHIH, record_every,
+        crystal=dict(kind=CRYSTAL_SLAB, asym_angle_rad=0.0,
+                     thickness_um=200.0, surf_x_um=0.0, surf_z_um=0.0),
+        strain=dict(kind=STRAIN_BENT, params=[radius_um, nu, 0.0, z_hit]),
+        psi0=psi0, meta=dict(z_hit_um=z_hit))
+
+
+def star_polygon(rng: np.random.Generator, centre: tuple[float, float],
+                 extent_um: float, nv: int) -> np.ndarray:
+    """Seeded star-shaped polygon: sorted angles, radii U[0.5, 1] * D/2."""
+    ang = np.sort(rng.uniform(0.0, 2.0 * math.pi, nv))
+    rad = rng.uniform(0.5, 1.0, nv) * extent_um / 2.0
+    return np.stack([centre[0] + rad * np.cos(ang),
+                     centre[1] + rad * np.sin(ang)], axis=1)
+
+
+def asym_dislocation(nx: int = 8192, nz: int = 12000, dx_um: float = 0.1,
+                     dz_um: float = 0.05, record_every: int = 200,
+                     asym_deg: float = 10.0, seed: int = BASE_SEED + 3,
+                     burgers_um: float = 3.84e-4, nu: float = 0.28,
+                     core_depth_um: float = 20.0) -> Workload:
+    """Asymmetric Bragg slab (300 um) cut by a seeded star polygon, with an
+    edge dislocation 20 um below the entrance surface at the beam hit point.
+    """
+    rng = np.random.default_rng(seed)
+    nv = int(rng.integers(5, 9))
+    extent = float(rng.uniform(50.0, 300.0))
+    x0 = -0.5 * nx * dx_um
+    a = math.radians(asym_deg)
+    nrm = (math.cos(a), math.sin(a))
+    z_hit = nz * dz_um / 2.0
+    tan_t = math.tan(THETA_B_REF)
+    xb = -tan_t * z_hit                        # beam centre at z = 0
+    surf = (0.0, z_hit)                        # hit point on the surface
+    centre = (surf[0] + nrm[0] * extent / 2.0, surf[1] + nrm[1] * extent / 2.0)
+    poly = star_polygon(rng, centre, extent, nv)
+    core = (surf[0] + nrm[0] * core_depth_um, surf[1] + nrm[1] * core_depth_um)
+    psi0 = _two_band(gaussian_envelope(nx, x0, dx_um, xb, 50.0,
+                                       math.cos(THETA_B_REF)))
+    return Workload(
+        "asym_dislocation", nx, nz, dx_um, dz_um, x0, np.array([E_REF_EV]),
+        E_REF_EV, THETA_B_REF, CHI0, CHIH, record_every,
+        crystal=dict(kind=CRYSTAL_SLAB_AND_POLYGON, asym_angle_rad=a,
+                     thickness_um=300.0, surf_x_um=surf[0], surf_z_um=surf[1],
+                     polygon=poly),
+        strain=dict(kind=STRAIN_EDGE_DISLOCATION,
+                    params=[burgers_um, nu, core[0], core[1]]),
+        psi0=psi0, meta=dict(nv=nv, extent_um=extent))
+
+
+def pulse_energies(n_energy: int = 256, centre_ev: float = 9000.0,
+                   span_ev: float = 10.0) -> np.ndarray:
+    """E_j = centre - span/2 + span * j / B, ascending."""
+    return centre_ev - span_ev / 2.0 + span_ev * np.arange(n_energy) / n_energy
+
+
+def pulse_batched(nx: int = 4096, nz: int = 6000, n_energy: int = 256,
+                  dx_um: float = 0.1, dz_um: float = 0.05,
+                  record_every: int = 0, sigma_ev: float = 1.5,
+                  radius_um: float = 2.0e6, nu: float = 0.28,
+                  seed: int = BASE_SEED + 4) -> Workload:
+    """Batch of photon energies through one bent Laue slab (300 um).
+
+    The crystal is set at the Bragg angle of the centre energy, so row j's
+    incident envelope carries the tilt (sin theta_0 - s_j) k_j: its carrier
+    is the fixed incident direction while the band centre s_j = lambda_j/2d
+    moves with energy.  Spectral amplitudes: Gaussian envelope (intensity
+    RMS sigma) times seeded uniform random phases (SASE-like).
+    """
+    rng = np.random.default_rng(seed)
+    energies = pulse_energies(n_energy)
+    phases = rng.uniform(0.0, 2.0 * math.pi, n_energy)
+    centre_ev = 9000.0
+    s_ref = math.sin(THETA_B_REF)
+    s0 = s_ref * E_REF_EV / centre_ev
+    c0 = math.sqrt(1.0 - s0 * s0)
+    x0 = -0.5 * nx * dx_um
+    thickness = 300.0
+    xb = -0.5 * thickness * s0 / c0             # centre the Borrmann fan
+    psi0 = np.zeros((n_energy, 2, nx), dtype=np.complex128)
+    for j, e in enumerate(energies):
+        k = 2.0 * math.pi / (HC_EV_ANGSTROM / e * 1e-4)
+        sj = s_ref * E_REF_EV / e
+        amp = math.exp(-((e - centre_ev) ** 2) / (4.0 * sigma_ev ** 2))
+        env = gaussian_envelope(nx, x0, dx_um, xb, 50.0, c0,
+                                tilt_per_um=(s0 - sj) * k)
+        psi0[j, 0] = amp * complex(math.cos(phases[j]), math.sin(phases[j])) * env
+    return Workload(
+        "pulse_batched", nx, nz, dx_um, dz_um, x0, energies, E_REF_EV,
+        THETA_B_REF, CHI0, CHIH, record_every,
+        crystal=dict(kind=CRYSTAL_SLAB, asym_angle_rad=math.pi / 2,
+                     thickness_um=thickness, surf_x_um=0.0, surf_z_um=0.0),
+        strain=dict(kind=STRAIN_BENT, params=[radius_um, nu, 0.0, 0.0]),
+        psi0=psi0, meta=dict(centre_ev=centre_ev, sigma_ev=sigma_ev))
+
+
+@dataclass
+class Request:
+    arrival_s: float
+    workload: Workload
+
+
+def serving_request(rng: np.random.Generator, nx: int, nz: int,
+                    dx_um: float = 0.1, dz_um: float = 0.05) -> Workload:
+    """One mixed solve: Bragg / Laue / asymmetric, bent or dislocated."""
+    geom = int(rng.integers(0, 3))
+    x0 = -0.5 * nx * dx_um
+    tan_t = math.tan(THETA_B_REF)
+    c = math.cos(THETA_B_REF)
+    length = nz * dz_um
+    if geom == 0:                                  # symmetric Bragg
+        a, surf = 0.0, (0.0, length * 0.25)
+        xb = -tan_t * surf[1]
+    elif geom == 1:                                # symmetric Laue
+        a, surf = math.pi / 2, (0.0, 0.0)
+        xb = -0.5 * length * tan_t
+    else:                                          # asymmetric Bragg
+        a = math.radians(float(rng.uniform(5.0, 30.0)))
+        surf = (0.0, length * 0.25)
+        xb = -tan_t * surf[1]
+    xb = max(xb, x0 + 0.25 * nx * dx_um)
+    nrm = (math.cos(a), math.sin(a))
+    if rng.uniform() < 0.5:
+        strain = dict(kind=STRAIN_BENT,
+                      params=[float(rng.uniform(0.5e6, 5.0e6)), 0.28,
+                              surf[0], surf[1]])
+    else:
+        depth = 20.0
+        strain = dict(kind=STRAIN_EDGE_DISLOCATION,
+                      params=[3.84e-4, 0.28, surf[0] + nrm[0] * depth,
+                              surf[1] + nrm[1] * depth])
+    fwhm = min(50.0, 0.1 * nx * dx_um)
+    psi0 = _two_band(gaussian_envelope(nx, x0, dx_um, xb, fwhm, c))
+    return Workload(
+        "serving_request", nx, nz, dx_um, dz_um, x0, np.array([E_REF_EV]),
+        E_REF_EV, THETA_B_REF, CHI0, CHIH, 0,
+        crystal=dict(kind=CRYSTAL_SLAB, asym_angle_rad=a, thickness_um=300.0,
+                     surf_x_um=surf[0], surf_z_um=surf[1]),
+        strain=strain, psi0=psi0, meta=dict(geometry=geom))
+
+
+def serving_requests(n: int, rate_per_s: float = 200.0,
+                     nx_choices=(512, 1024, 2048, 4096, 8192, 16384),
+                     nz_range=(500, 20000), seed: int = BASE_SEED + 5
+                     ) -> list[Request]:
+    """Poisson arrivals (mean ``rate_per_s``) of mixed solves."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for _ in range(n):
+        t += float(rng.exponential(1.0 / rate_per_s))
+        nx = int(rng.choice(nx_choices))
+        nz = int(rng.integers(nz_range[0], nz_range[1] + 1))
+        out.append(Request(t, serving_request(rng, nx, nz)))
+    return out
+
+
+WORKLOADS = {
+    "laue_perfect": laue_perfect,
+    "bragg_bent": bragg_bent,
+    "asym_dislocation": asym_dislocation,
+    "pulse_batched": pulse_batched,
+}

@@ -1,0 +1,419 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test fixes part of ``oracle/`` with a closed form, a textbook law, an
+invariant of the equations, brute force, or an independent library routine,
+chosen so that a plausible slip (a dropped factor, a wrong sign or index, a
+swapped band) fails at least one of them.  None of them needs a GPU.
+"""
+
+import math
+
+import numpy as np
+import pytest
+import scipy.special
+
+from oracle import bpm, geometry, timeaxis
+
+E = 8000.0
+THETA = math.radians(23.65)
+CHI0 = complex(-1.51e-5, 3.5e-7)
+CHIH = complex(-9.1e-6, 3.4e-7)
+
+
+def _plan(nx, dx, dz, chi0=CHI0, chih=CHIH, energy=E):
+    return bpm.energy_plan(energy, E, THETA, chi0, chih, nx, dx, dz)
+
+
+def _crystal(nx, x0, dx, dz, kind):
+    cr = geometry.Crystal(nx, x0, dx, dz, bpm.d_spacing_um(E, THETA))
+    return cr.set_crystal(kind)
+
+
+# ---------------------------------------------------------------- P1 -------
+def test_p1_fft_convention_and_q_grid():
+    """The oracle's q_m is the wave number of DFT bin m (numpy convention):
+    a sampled plane wave exp(i q_m x^) transforms to a single spike at m, and
+    numpy's FFT equals the brute-force DFT sum with the e^{-2 pi i m j/N}
+    kernel."""
+    rng = np.random.default_rng(1)
+    for n in (8, 16, 64, 256):
+        x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        jj = np.arange(n)
+        brute = np.array([np.sum(x * np.exp(-2j * np.pi * m * jj / n))
+                          for m in range(n)])
+        assert np.max(np.abs(np.fft.fft(x) - brute)) <= 1e-12 * np.max(np.abs(brute))
+    nx, dx = 64, 0.3
+    p = _plan(nx, dx, 0.05)
+    xh = p.k_um * (-7.0 + np.arange(nx) * dx)
+    for m in (0, 1, 5, nx // 2 - 1, nx // 2, nx // 2 + 3, nx - 1):
+        spec = np.fft.fft(np.exp(1j * p.q[m] * xh))
+        others = np.delete(np.abs(spec), m)
+        assert abs(abs(spec[m]) - nx) < 1e-9 and np.max(others) < 1e-9
+
+
+# ---------------------------------------------------------------- P2 -------
+def _angular_spectrum_closed_form(xh_eval, sigma_h, xh_c, s, dzh_total):
+    """(1/2pi) int A(q) exp(i q x^) exp(i Z^ sqrt(1 - (q + s)^2)) dq for the
+    Gaussian psi(x^) = exp(-(x^ - x^_c)^2 / (2 sigma^2)), by a fine
+    trapezoid rule in q, with the exponent taken in 40-digit arithmetic."""
+    import mpmath
+    mpmath.mp.dps = 40
+    nq = 6001
+    qmax = 14.0 / sigma_h
+    q = np.linspace(-qmax, qmax, nq)
+    hq = q[1] - q[0]
+    amp = sigma_h * math.sqrt(2.0 * math.pi) * np.exp(-0.5 * (q * sigma_h) ** 2)
+    prop = np.empty(nq, dtype=np.complex128)
+    s_mp = mpmath.mpf(s)
+    z_mp = mpmath.mpf(dzh_total)
+    for i, qi in enumerate(q):
+        ph = z_mp * mpmath.sqrt(1 - (mpmath.mpf(qi) + s_mp) ** 2)
+        ph = ph - 2 * mpmath.pi * mpmath.floor(ph / (2 * mpmath.pi))
+        prop[i] = complex(mpmath.cos(ph), mpmath.sin(ph))
+    out = []
+    for xh in xh_eval:
+        integrand = amp * np.exp(1j * q * (xh - xh_c)) * prop
+        out.append(hq * np.sum(integrand) / (2.0 * math.pi))
+    return np.array(out)
+
+
+def test_p2_free_space_gaussian_matches_angular_spectrum_integral():
+    """Pi = 0: the march is pure angular-spectrum propagation of psi_+.
+    Compare with the continuum integral (exact square root, no delta split,
+    no global-phase split).  Fixes the propagator's sign and centring on
+    +s, dz^ = k dz, the q grid and the per-step common phase g."""
+    nx, dx, dz, nsteps = 1024, 0.4, 0.05, 400
+    x0 = -0.5 * nx * dx
+    sigma = 10.0
+    p = _plan(nx, dx, dz)
+    x = x0 + np.arange(nx) * dx
+    psi0 = np.zeros((1, 2, nx), dtype=complex)
+    psi0[0, 0] = np.exp(-0.5 * ((x + 3.0) / sigma) ** 2)
+    cr = _crystal(nx, x0, dx, dz, geometry.CRYSTAL_VACUUM)
+    res = bpm.march([p], psi0, cr, 0, nsteps, 0, dx)
+    drift = nsteps * dz * math.tan(THETA)
+    idx = np.searchsorted(x, np.linspace(-3.0 + drift - 20, -3.0 + drift + 20, 16))
+    ref = _angular_spectrum_closed_form(p.k_um * x[idx], p.k_um * sigma,
+                                        p.k_um * (-3.0), p.s, nsteps * p.dzh)
+    got = res.psi[0, 0, idx]
+    # g is rounded once per step (|error| <= ulp(dz^ c)/2 = 1.2e-13 rad).
+    assert np.max(np.abs(got - ref)) < 1e-10 * np.max(np.abs(ref))
+    assert np.max(np.abs(res.psi[0, 1])) == 0.0
+
+
+def test_p2_free_space_drift_is_along_plus_x_at_tan_theta():
+    """The + envelope is the beam travelling at +theta_B to z: its intensity
+    centroid moves by z tan(theta_B) (ray optics), the - envelope's by
+    -z tan(theta_B)."""
+    nx, dx, dz, nsteps = 512, 0.4, 0.05, 1000
+    x0 = -0.5 * nx * dx
+    p = _plan(nx, dx, dz)
+    x = x0 + np.arange(nx) * dx
+    g = np.exp(-0.5 * (x / 8.0) ** 2)
+    psi0 = np.stack([g, g])[None].astype(complex)
+    cr = _crystal(nx, x0, dx, dz, geometry.CRYSTAL_VACUUM)
+    res = bpm.march([p], psi0, cr, 0, nsteps, 0, dx)
+    for band, sign in ((0, 1.0), (1, -1.0)):
+        inten = np.abs(res.psi[0, band]) ** 2
+        cen = np.sum(x * inten) / np.sum(inten)
+        assert abs(cen - sign * nsteps * dz * math.tan(THETA)) < 1e-6
+
+
+def test_p2b_free_space_power_is_conserved():
+    """Parseval with |P+-| = 1: vacuum conserves each band's power."""
+    nx, dx, dz = 256, 0.4, 0.05
+    rng = np.random.default_rng(2)
+    psi0 = (rng.standard_normal((1, 2, nx)) + 1j * rng.standard_normal((1, 2, nx)))
+    cr = _crystal(nx, -50.0, dx, dz, geometry.CRYSTAL_VACUUM)
+    res = bpm.march([_plan(nx, dx, dz)], psi0, cr, 0, 300, 100, dx)
+    p0 = bpm.band_power(psi0[0], dx)
+    for rec in range(4):
+        assert np.allclose(res.powers[0, rec], p0, rtol=300 * 1e-13, atol=0)
+
+
+# ---------------------------------------------------------------- P3 -------
+def test_p3_single_mode_is_a_2x2_matrix_power():
+    """One grid mode q_m in both bands, Pi = 1, no strain: the step is the
+    2x2 map v -> [[a, b], [b, a]] diag(g P+(m), g P-(m)) v.  Compare the
+    march (FFTs, masks, records) with the matrix power."""
+    nx, dx, dz, nsteps = 32, 0.5, 0.05, 250
+    x0 = -8.0
+    p = _plan(nx, dx, dz)
+    xh = p.k_um * (x0 + np.arange(nx) * dx)
+    for m in (0, 3, nx - 2, nx // 2):
+        mode = np.exp(1j * p.q[m] * xh)
+        v0 = np.array([0.7 - 0.2j, 0.1 + 0.4j])
+        psi0 = np.stack([v0[0] * mode, v0[1] * mode])[None]
+        cr = _crystal(nx, x0, dx, dz, geometry.CRYSTAL_BULK)
+        res = bpm.march([p], psi0, cr, 0, nsteps, 0, dx)
+        mat = np.array([[p.a, p.b], [p.b, p.a]]) @ np.diag(
+            [p.g * p.prop_plus[m], p.g * p.prop_minus[m]])
+        v = np.linalg.matrix_power(mat, nsteps) @ v0
+        got = res.psi[0] / mode
+        assert np.max(np.abs(got - v[:, None])) < 1e-12
+
+
+# ---------------------------------------------------------------- P4 -------
+def test_p4_pendelloesung_period_symmetric_laue():
+    """Plane wave at the exact Bragg angle in a perfect symmetric Laue
+    crystal (no absorption): the reflected fraction follows the textbook
+    Pendelloesung law sin^2(pi z / Lambda0), Lambda0 = lambda cos(theta_B)
+    / |chi_h| (15.6 um here).  The truncated expansion (Eqs. fov11-12)
+    deviates by O(w^3) per step, < 1e-3 over two periods at dz = 0.05 um."""
+    nx, dx, dz, nsteps = 16, 1.0, 0.05, 700
+    chi0, chih = complex(-1.51e-5, 0.0), complex(-9.1e-6, 0.0)
+    p = _plan(nx, dx, dz, chi0, chih)
+    psi0 = np.zeros((1, 2, nx), dtype=complex)
+    psi0[0, 0] = 1.0
+    cr = _crystal(nx, 0.0, dx, dz, geometry.CRYSTAL_BULK)
+    res = bpm.march([p], psi0, cr, 0, nsteps, 1, dx)
+    pw = res.powers[0, :nsteps]
+    frac = pw[:, 1] / (pw[:, 0] + pw[:, 1])
+    lam = bpm.HC_EV_ANGSTROM / E * 1e-4
+    lam0 = lam * math.cos(THETA) / abs(chih)
+    assert abs(lam0 - 15.60) < 0.01
+    z = dz * np.arange(1, nsteps + 1)
+    assert np.max(np.abs(frac - np.sin(np.pi * z / lam0) ** 2)) < 1e-3
+
+
+def test_p4b_beer_lambert_and_refraction_phase():
+    """chi_h = 0, uniform field in bulk: the wave only refracts and is
+    absorbed.  Intensity falls as exp(-mu z / cos(theta_B)) with
+    mu = 4 pi beta / lambda, beta = Im(chi_0)/2, and the phase (after the
+    vacuum phase g^n) advances by k (Re chi_0 / 2) z / cos(theta_B)."""
+    nx, dx, dz, nsteps = 8, 1.0, 0.05, 2000
+    chi0 = complex(-1.51e-5, 3.5e-7)
+    p = _plan(nx, dx, dz, chi0, 0j)
+    psi0 = np.zeros((1, 2, nx), dtype=complex)
+    psi0[0, 0] = 1.0
+    cr = _crystal(nx, 0.0, dx, dz, geometry.CRYSTAL_BULK)
+    res = bpm.march([p], psi0, cr, 0, nsteps, 0, dx)
+    lam = bpm.HC_EV_ANGSTROM / E * 1e-4
+    z = nsteps * dz
+    mu = 4.0 * math.pi * (chi0.imag / 2.0) / lam
+    assert abs(abs(res.psi[0, 0, 0]) ** 2 / math.exp(-mu * z / math.cos(THETA)) - 1) < 1e-12
+    phase = np.angle(res.psi[0, 0, 0] / p.g ** nsteps)
+    expect = math.remainder(2 * math.pi / lam * chi0.real / 2 * z / math.cos(THETA),
+                            2 * math.pi)
+    assert abs(phase - expect) < 1e-10
+
+
+# ---------------------------------------------------------------- P6 -------
+def test_p6_zero_absorption_power_law():
+    """Real chi_0, chi_h, Pi = 1 everywhere, arbitrary beam and strain: the
+    coupling matrix M satisfies M^H M = (J0(w)^2 + J1(w)^2) I for any strain
+    phase, so the total power after n steps is sigma^n P_0 exactly (sigma
+    from scipy's Bessel functions, independent of the oracle's series)."""
+    nx, dx, dz, nsteps = 128, 0.4, 0.05, 300
+    chi0, chih = complex(-1.51e-5, 0.0), complex(-9.1e-6, 0.0)
+    p = _plan(nx, dx, dz, chi0, chih)
+    rng = np.random.default_rng(3)
+    psi0 = rng.standard_normal((1, 2, nx)) + 1j * rng.standard_normal((1, 2, nx))
+    cr = _crystal(nx, -25.0, dx, dz, geometry.CRYSTAL_BULK)
+    ux = rng.uniform(-1e-3, 1e-3, (nsteps, nx))
+    cr.set_strain(geometry.STRAIN_ARRAY, ux=ux)
+    res = bpm.march([p], psi0, cr, 0, nsteps, 100, dx)
+    w = p.dzh * chih.real / p.c
+    sigma = scipy.special.jv(0, w) ** 2 + scipy.special.jv(1, w) ** 2
+    p0 = np.sum(bpm.band_power(psi0[0], dx))
+    for rec, n in enumerate((100, 200, 300)):
+        assert abs(np.sum(res.powers[0, rec]) / (sigma ** n * p0) - 1) < 1e-12
+
+
+# ---------------------------------------------------------------- P7 -------
+def test_p7_strain_gauge_identity():
+    """A commensurate linear strain phase theta = G x^ (G k dx = 2 pi m0/N)
+    is a gauge: (psi_+, e^{i theta} psi_-) follows the unstrained march with
+    psi_-'s propagator shifted by m0 bins.  Fixes which band gets e^{+i
+    theta} and that the strain phase multiplies Delta_eps_{+-1} only."""
+    nx, dx, dz, nsteps, m0 = 64, 0.4, 0.05, 120, 3
+    x0 = -12.0
+    p = _plan(nx, dx, dz)
+    x = x0 + np.arange(nx) * dx
+    gk = 2 * np.pi * m0 / (nx * dx)                   # theta = gk * x
+    rng = np.random.default_rng(4)
+    psi0 = (rng.standard_normal((1, 2, nx)) + 1j * rng.standard_normal((1, 2, nx)))
+    inside = rng.uniform(size=(nsteps, nx)) < 0.7
+    h = 2 * np.pi / bpm.d_spacing_um(E, THETA)
+
+    cr_s = geometry.Crystal(nx, x0, dx, dz, bpm.d_spacing_um(E, THETA))
+    cr_s.set_crystal(geometry.CRYSTAL_MASK, mask=inside)
+    cr_s.set_strain(geometry.STRAIN_ARRAY, ux=np.tile(gk * x / h, (nsteps, 1)))
+    strained = bpm.march([p], psi0, cr_s, 0, nsteps, 0, dx)
+
+    cr_u = geometry.Crystal(nx, x0, dx, dz, bpm.d_spacing_um(E, THETA))
+    cr_u.set_crystal(geometry.CRYSTAL_MASK, mask=inside)
+    gauge = np.exp(1j * gk * x)
+    psi0_g = psi0.copy()
+    psi0_g[0, 1] *= gauge
+    plain = bpm.march([p], psi0_g, cr_u, 0, nsteps, 0, dx,
+                      prop_override=(p.prop_plus, np.roll(p.prop_minus, m0)))
+    assert np.max(np.abs(strained.psi[0, 0] - plain.psi[0, 0])) < 1e-12
+    assert np.max(np.abs(strained.psi[0, 1] * gauge - plain.psi[0, 1])) < 1e-12
+
+
+# ---------------------------------------------------------------- P8 -------
+def test_p8_one_lattice_spacing_is_invisible():
+    """u_x -> u_x + d changes h u_x by exactly 2 pi."""
+    nx, dx, dz, nsteps = 64, 0.4, 0.05, 50
+    p = _plan(nx, dx, dz)
+    d = bpm.d_spacing_um(E, THETA)
+    rng = np.random.default_rng(5)
+    psi0 = rng.standard_normal((1, 2, nx)) + 0j
+    ux = rng.uniform(-0.01, 0.01, (nsteps, nx))
+    runs = []
+    for shift in (0.0, d, -3 * d):
+        cr = geometry.Crystal(nx, -10.0, dx, dz, d).set_crystal(geometry.CRYSTAL_BULK)
+        cr.set_strain(geometry.STRAIN_ARRAY, ux=ux + shift)
+        runs.append(bpm.march([p], psi0, cr, 0, nsteps, 0, dx).psi)
+    assert np.max(np.abs(runs[1] - runs[0])) < 1e-12
+    assert np.max(np.abs(runs[2] - runs[0])) < 1e-12
+
+
+# ---------------------------------------------------------------- P9 -------
+@pytest.mark.parametrize("w", [0.0201 - 0.00075j, -0.02014 + 0.00075j, 0.3 + 0.2j,
+                               1e-9 + 0j, 0j, 1.7 - 0.4j])
+def test_p9_bessel_series_matches_scipy(w):
+    for nu in (0, 1):
+        ref = scipy.special.jv(nu, w)
+        got = bpm.bessel_series(nu, w)
+        assert abs(got - ref) <= 2e-15 * max(1.0, abs(ref))
+    # J0 - 1 without cancellation, against 40-digit mpmath.
+    import mpmath
+    mpmath.mp.dps = 40
+    ref_m1 = complex(mpmath.besselj(0, mpmath.mpc(w.real, w.imag)) - 1)
+    got_m1 = bpm.bessel_series(0, w, skip_first=True)
+    assert abs(got_m1 - ref_m1) <= 1e-15 * abs(ref_m1) + 1e-300
+
+
+# ---------------------------------------------------------------- P10 ------
+def test_p10_linearity_and_batch_independence():
+    nx, dx, dz, nsteps = 64, 0.4, 0.05, 60
+    rng = np.random.default_rng(6)
+    psi_a = rng.standard_normal((1, 2, nx)) + 1j * rng.standard_normal((1, 2, nx))
+    psi_b = rng.standard_normal((1, 2, nx)) + 1j * rng.standard_normal((1, 2, nx))
+    cr = _crystal(nx, -12.0, dx, dz, geometry.CRYSTAL_BULK)
+    cr.set_strain(geometry.STRAIN_BENT, params=[1e5, 0.28, 0.0, 0.0])
+    pa, pb = _plan(nx, dx, dz), _plan(nx, dx, dz, energy=8003.0)
+    alpha = 0.3 - 1.7j
+    ra = bpm.march([pa], psi_a, cr, 0, nsteps, 0, dx).psi
+    r_scaled = bpm.march([pa], alpha * psi_a, cr, 0, nsteps, 0, dx).psi
+    assert np.max(np.abs(r_scaled - alpha * ra)) < 1e-13 * np.max(np.abs(r_scaled))
+    rb = bpm.march([pb], psi_b, cr, 0, nsteps, 0, dx).psi
+    both = bpm.march([pa, pb], np.concatenate([psi_a, psi_b]), cr, 0, nsteps, 0, dx).psi
+    assert np.array_equal(both[0], ra[0]) or np.max(np.abs(both[0] - ra[0])) < 1e-14
+    assert np.max(np.abs(both[1] - rb[0])) < 1e-14
+
+
+def test_resume_equals_unsplit_march():
+    """The state after n steps is (psi_+, psi_-): a march split at n equals
+    the unsplit march, records included."""
+    nx, dx, dz = 64, 0.4, 0.05
+    rng = np.random.default_rng(9)
+    psi0 = rng.standard_normal((1, 2, nx)) + 1j * rng.standard_normal((1, 2, nx))
+    cr = _crystal(nx, -12.0, dx, dz, geometry.CRYSTAL_BULK)
+    p = _plan(nx, dx, dz)
+    full = bpm.march([p], psi0, cr, 0, 100, 10, dx)
+    first = bpm.march([p], psi0, cr, 0, 40, 10, dx)
+    second = bpm.march([p], first.psi, cr, 40, 100, 10, dx)
+    assert np.array_equal(second.psi, full.psi)
+    assert np.array_equal(second.records[:, 4:], full.records[:, 4:])
+
+
+# ---------------------------------------------------------------- P11 ------
+def test_p11_chi_h_sign_only_flips_psi_minus():
+    """chi_h -> -chi_h sends b -> -b, which is the same as psi_- -> -psi_-:
+    intensities of both bands are unchanged."""
+    nx, dx, dz, nsteps = 64, 0.4, 0.05, 200
+    rng = np.random.default_rng(7)
+    psi0 = np.zeros((1, 2, nx), dtype=complex)
+    psi0[0, 0] = rng.standard_normal(nx) + 1j * rng.standard_normal(nx)
+    cr = _crystal(nx, -12.0, dx, dz, geometry.CRYSTAL_BULK)
+    r1 = bpm.march([_plan(nx, dx, dz, chih=CHIH)], psi0, cr, 0, nsteps, 0, dx).psi
+    r2 = bpm.march([_plan(nx, dx, dz, chih=-CHIH)], psi0, cr, 0, nsteps, 0, dx).psi
+    assert np.max(np.abs(r1[0, 0] - r2[0, 0])) < 1e-13
+    assert np.max(np.abs(r1[0, 1] + r2[0, 1])) < 1e-13
+
+
+# ---------------------------------------------------- geometry pins ---------
+def test_slab_bragg_laue_and_rotated_frame():
+    nx, dx, dz = 200, 0.5, 0.25
+    x0 = -50.0
+    x = x0 + np.arange(nx) * dx
+    # a = 0: Bragg slab x in [xs, xs + T] on every row.
+    for n in (0, 7, 100):
+        row = geometry.slab_row(x, n * dz, 0.0, 20.0, 3.0, 0.0)
+        assert np.array_equal(row, (x >= 3.0) & (x <= 23.0))
+    # a = 90 deg: Laue slab z in [zs, zs + T], whole rows.
+    for n in range(0, 200, 13):
+        row = geometry.slab_row(x, n * dz, math.pi / 2, 10.0, 0.0, 5.0)
+        z = n * dz
+        assert row.all() == (5.0 <= z <= 15.0) and (row.any() == row.all())
+    # Any angle: same set as the distance to the surface line measured with
+    # the cross product against the surface direction (independent form).
+    a, t, xs, zs = math.radians(10.0), 30.0, 2.0, 20.0
+    tdir = np.array([-math.sin(a), math.cos(a)])
+    for n in range(0, 200, 7):
+        z = n * dz
+        row = geometry.slab_row(x, z, a, t, xs, zs)
+        depth = (x - xs) * tdir[1] - (z - zs) * tdir[0]       # cross(t, r - rs)
+        away = (np.abs(depth) > 1e-9) & (np.abs(depth - t) > 1e-9)
+        assert np.array_equal(row[away], ((depth >= 0) & (depth <= t))[away])
+
+
+def test_polygon_even_odd_matches_winding_number():
+    rng = np.random.default_rng(8)
+    from paper_2601_06340_gb300 import inputs
+    poly = inputs.star_polygon(rng, (1.0, 2.0), 40.0, 7)
+    x = -25.0 + 0.37 * np.arange(150)
+    for z in np.linspace(-25.0, 25.0, 41):
+        row = geometry.polygon_row(x, z, poly[:, 0], poly[:, 1])
+        vx = poly[:, 0][None, :] - x[:, None]
+        vz = poly[:, 1][None, :] - z
+        ang = np.arctan2(vz, vx)
+        dang = np.diff(np.concatenate([ang, ang[:, :1]], axis=1), axis=1)
+        dang = (dang + np.pi) % (2 * np.pi) - np.pi
+        winding = np.rint(np.sum(dang, axis=1) / (2 * np.pi)) != 0
+        assert np.array_equal(row, winding)
+
+
+def test_bent_displacement_curvatures():
+    """Second derivatives of the bend field: d2u/dx2 = 1/R, d2u/dz2 = nu/R,
+    and u = 0 at the reference point."""
+    r, nu, xr, zr = 2.0e6, 0.28, 5.0, 40.0
+    x = np.array([xr - 1.0, xr, xr + 1.0])
+    u0 = geometry.bent_ux(x, zr, r, nu, xr, zr)
+    assert u0[1] == 0.0
+    assert abs((u0[0] - 2 * u0[1] + u0[2]) - 1.0 / r) < 1e-18
+    uz = [geometry.bent_ux(np.array([xr]), zr + dzz, r, nu, xr, zr)[0]
+          for dzz in (-1.0, 0.0, 1.0)]
+    assert abs((uz[0] - 2 * uz[1] + uz[2]) - nu / r) < 1e-18
+
+
+def test_edge_dislocation_burgers_circuit():
+    """A closed circuit around the core gains exactly one Burgers vector in
+    u_x; the elastic term vanishes on the axes through the core."""
+    b, nu, xc, zc = 3.84e-4, 0.28, 1.0, -2.0
+    ang = np.linspace(-np.pi + 1e-3, np.pi - 1e-3, 4001)
+    rad = 5.0
+    xs, zs = xc + rad * np.cos(ang), zc + rad * np.sin(ang)
+    u = np.array([geometry.edge_dislocation_ux(np.array([xs[i]]), zs[i], b, nu, xc, zc)[0]
+                  for i in range(len(ang))])
+    jumps = np.diff(u)
+    # continuous along the circuit except across the cut on -x'
+    assert np.max(np.abs(jumps)) < 1e-3 * b
+    # ... and the whole circuit's closure failure sits in the jump across
+    # the cut, which is exactly one Burgers vector.
+    eta = 1e-9
+    up = geometry.edge_dislocation_ux(np.array([xc - rad]), zc + eta, b, nu, xc, zc)[0]
+    dn = geometry.edge_dislocation_ux(np.array([xc - rad]), zc - eta, b, nu, xc, zc)[0]
+    assert abs((up - dn) - b) < 1e-9 * b
+    on_axis = geometry.edge_dislocation_ux(np.array([xc + 3.0, xc - 0.0]), zc, b, nu, xc, zc)
+    assert on_axis[0] == 0.0 and on_axis[1] == 0.0
+
+
+# ---------------------------------------------------- time axis -------------
+def test_omega_to_t_matches_direct_sum():
+    rng = np.random.default_rng(10)
+    f = rng.standard_normal((12, 2, 5)) + 1j * rng.standard_normal((12, 2, 5))
+    assert np.max(np.abs(timeaxis.omega_to_t(f) - timeaxis.omega_to_t_direct(f))) < 1e-14
