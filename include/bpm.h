@@ -1,0 +1,214 @@
+/*
+ * bpm.h -- C ABI of the GB300 (sm_103a) two-beam FFT beam-propagation march.
+ *
+ * Method: Krzywinski & Halavanau, arXiv 2601.06340, Section 2.  Two slowly
+ * varying envelopes psi_+ (transmitted) and psi_- (reflected) (Eqs. fov6-7)
+ * are advanced in z by the first-order split step of Eq. fov10: each band is
+ * propagated through its own angular-spectrum operator exp(i dz^ sqrt(1 -
+ * kx^2)) centred on its carrier (forward FFT, multiply, inverse FFT), then
+ * the two are coupled in real space through chi_0, chi_h (Eqs. fov8,
+ * fov11-12), the strain phase h*u_x (Eq. Authier) and the crystal mask Pi.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Units: lengths in micrometres, angles in radians, energies in eV.
+ * Grid: x_j = x0 + j*dx (j < nx), z_n = n*dz; the mask and strain of step n
+ *   are sampled at z_n (start of the step).
+ * Complex numbers are interleaved (re, im).  "c128" = 2 doubles, "c64" = 2
+ *   floats.
+ * Field layout: [B][2][nx], B = number of photon energies (batch rows), band
+ *   0 = psi_+, band 1 = psi_-.  Records: [B][n_rec][2][nx] with
+ *   n_rec = nz / record_every (0 when record_every = 0); record i is the
+ *   state after step (i+1)*record_every.  Powers: [B][n_rec+1][2] doubles,
+ *   P = dx * sum_j |psi_j|^2 per band, at each record and (last entry) for
+ *   the returned state.
+ * Precision: BPM_FP64_PLAIN marches complex128 with one kernel launch per
+ *   FFT pass and per pointwise step; BPM_FP32_FUSED marches complex64 in a
+ *   persistent kernel that keeps each row on chip for many steps, with every
+ *   phase argument (propagator, strain phase, common phase) formed in FP64
+ *   and rounded once.  FP32 plans return c64 records; FP64 plans c128.
+ * Errors: every call returns a bpm_status; negative values are errors and
+ *   bpm_last_error() (thread-local) describes the last one.  Nothing aborts
+ *   the process.  Arguments are validated on the host before any device
+ *   work, so an invalid call leaves the plan unchanged.
+ * Ownership: the caller owns every pointer it passes.  bpm_plan and
+ *   bpm_set_* copy what they need before returning.  The plan owns all
+ *   device memory it allocates and frees it in bpm_destroy.
+ * Threading: calls on one plan are serialised by the plan's lock; distinct
+ *   plans may be used from different threads.
+ */
+#ifndef BPM_H
+#define BPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bpm_plan_s* bpm_plan_t;
+typedef uint64_t bpm_ticket_t;
+
+enum bpm_status {
+  BPM_OK = 0,
+  BPM_NOT_READY = 1,     /* bpm_poll: ticket still running (not an error) */
+  BPM_ERR_INVALID = -1,  /* bad argument; nothing was changed              */
+  BPM_ERR_OOM = -2,      /* device allocation failed or over the budget   */
+  BPM_ERR_CUDA = -3,     /* a CUDA call failed (message in last_error)    */
+  BPM_ERR_BUSY = -4,     /* plan has pending tickets, or queue is full    */
+  BPM_ERR_TIMEOUT = -5,  /* a bounded device wait gave up                 */
+  BPM_ERR_NUMERIC = -6   /* a non-finite power appeared in the result     */
+};
+
+enum bpm_precision { BPM_FP64_PLAIN = 0, BPM_FP32_FUSED = 1 };
+
+/* Crystal shape Pi(x, z) (Eqs. fov11-12: 1 inside, 0 outside; Section 3
+ * for the slab and its asymmetry angle, Section 6 for arbitrary shapes). */
+enum bpm_crystal_kind {
+  BPM_CRYSTAL_VACUUM = 0,          /* Pi = 0 everywhere (free space)        */
+  BPM_CRYSTAL_BULK = 1,            /* Pi = 1 everywhere                     */
+  BPM_CRYSTAL_SLAB = 2,            /* slab of thickness T, see set_crystal  */
+  BPM_CRYSTAL_MASK = 3,            /* user map [nz][nx], nonzero = inside   */
+  BPM_CRYSTAL_SLAB_AND_MASK = 4,   /* slab AND user map                     */
+  BPM_CRYSTAL_SLAB_AND_POLYGON = 5 /* slab AND polygon (even-odd rule)      */
+};
+
+/* Displacement u_x(x, z) entering as exp(+-i h u_x) (Eq. Authier). */
+enum bpm_strain_kind {
+  BPM_STRAIN_NONE = 0,
+  BPM_STRAIN_ARRAY = 1,            /* u_x[nz][nx] in um                       */
+  BPM_STRAIN_BENT = 2,             /* Eq. fov110, configured form, see below  */
+  BPM_STRAIN_EDGE_DISLOCATION = 3  /* Eq. fov120 with b along x, see below    */
+};
+
+typedef struct {
+  int32_t nx;              /* transverse points: power of two in [8, 8192]     */
+  int32_t nz;              /* z steps in the plan's march: >= 1                */
+  double dx_um;            /* > 0                                              */
+  double dz_um;            /* > 0                                              */
+  double x0_um;            /* x of the first cell                              */
+  int32_t n_energy;        /* B >= 1 batch rows (photon energies)              */
+  const double* energy_ev; /* [B] photon energies (copied)                     */
+  double e_ref_ev;         /* energy at which theta_b_ref_rad is the Bragg     */
+  double theta_b_ref_rad;  /*   angle; fixes d = lambda(E_ref) / (2 sin theta) */
+  double chi0_re, chi0_im; /* chi_0 (Eq. fov8)                                 */
+  double chih_re, chih_im; /* chi_h (Eq. fov8), used as given (no sign fix-up) */
+  int32_t record_every;    /* zsep: record every k steps; 0 = no records       */
+  int32_t precision;       /* enum bpm_precision                               */
+} bpm_problem;
+
+/* Create a plan: per-energy constants of Eqs. fov4-fov12 in FP64 (wave
+ * number, s = sin theta_B(E) = lambda/2d, cos(alpha) = sqrt(1 - s^2), dz^,
+ * the Jacobi-Anger coefficients J0(w)e^{i phi0}, i J1(w)e^{i phi0} with
+ * w = dz^ chi_h / cos(alpha), phi0 = dz^ chi_0 / (2 cos(alpha)), each band's
+ * propagator table) and the device buffers.  The crystal starts as VACUUM
+ * and the strain as NONE.  Returns BPM_ERR_INVALID for a bad problem
+ * (including an evanescent band, 1 - (|q| + s)^2 <= 0), BPM_ERR_OOM if
+ * device memory runs out, BPM_ERR_CUDA without a usable device. */
+int bpm_plan(const bpm_problem* problem, bpm_plan_t* out);
+
+/* Set the crystal shape.  Slab: unit normal n = (cos a, sin a) in (x, z)
+ * (a = asym_angle_rad: 0 = Bragg, pi/2 = Laue, between = asymmetric;
+ * components below 1e-12 in magnitude are set to 0), surface point
+ * r_s = (surf_x_um, surf_z_um), inside = {0 <= n.(r - r_s) <= thickness}.
+ * mask: uint8 [nz][nx] (row n = z_n), nonzero = inside, for MASK and
+ * SLAB_AND_MASK, else ignored (may be NULL).  poly_xz_um: nv vertices
+ * (x, z) in order, nv >= 3, for SLAB_AND_POLYGON, else ignored.  A cell is
+ * inside when its centre is (even-odd rule; an edge is crossed when exactly
+ * one end lies above z and x is left of its crossing point).  The decision
+ * is taken in FP64 with the operations in the documented order and no
+ * fused multiply-add. */
+int bpm_set_crystal(bpm_plan_t plan, int32_t kind, double asym_angle_rad,
+                    double thickness_um, double surf_x_um, double surf_z_um,
+                    const uint8_t* mask, const double* poly_xz_um, int32_t nv);
+
+/* Set the displacement.  ux_um: [nz][nx] doubles for ARRAY, else ignored.
+ * params (n_params values) for the parametric kinds:
+ *   BENT:  {R_um, nu, x_ref_um, z_ref_um}:
+ *          u_x = ((x - x_ref)^2 + nu (z - z_ref)^2) / (2 R)
+ *   EDGE_DISLOCATION: {b_um, nu, x_core_um, z_core_um}: with x' = x - x_core,
+ *          z' = z - z_core, u_x = b/(2 pi) [atan2(z', x')
+ *                              + x' z' / (2 (1 - nu) (x'^2 + z'^2))],
+ *          u_x = 0 at the core itself.
+ * The strain phase h u_x (h = 2 pi / d, d from bpm_problem) is formed in
+ * FP64, reduced modulo 2 pi, and turned into exp(i h u_x) once, on the
+ * device; the march streams that phasor (c64 or c128 per cell). */
+int bpm_set_strain(bpm_plan_t plan, int32_t kind, const double* ux_um,
+                   const double* params, int32_t n_params);
+
+/* March rows [0, B) from the state after n_begin steps to the state after
+ * n_end steps (0 <= n_begin < n_end <= nz) and copy results to the host.
+ * psi_in / psi_out: host c128 [B][2][nx] (may alias).  records: host buffer
+ * laid out [B][n_rec][2][nx] (c64 for FP32 plans, c128 for FP64 plans) or
+ * NULL; only records with index in [n_begin/k, n_end/k) are written.
+ * powers: host double [B][n_rec+1][2] or NULL (same slots as records; the
+ * last slot is the returned state).  Synchronous.  BPM_ERR_NUMERIC if a
+ * power is not finite (outputs are still written). */
+int bpm_propagate(bpm_plan_t plan, const double* psi_in, double* psi_out,
+                  void* records, double* powers, int32_t n_begin,
+                  int32_t n_end);
+
+/* Same march on device buffers, asynchronous on `stream` (a cudaStream_t;
+ * NULL = legacy default stream).  d_psi_in / d_psi_out: [B][2][nx], c64 for
+ * FP32 plans and c128 for FP64 plans (may alias).  d_records: device
+ * buffer as in bpm_propagate or NULL.  d_powers: device double
+ * [B][n_rec+1][2] or NULL.  The call returns after enqueueing; the caller
+ * synchronises the stream before reading outputs or freeing inputs. */
+int bpm_propagate_device(bpm_plan_t plan, const void* d_psi_in,
+                         void* d_psi_out, void* d_records, void* d_powers,
+                         int32_t n_begin, int32_t n_end, void* stream);
+
+/* Energy -> time synthesis of a batch of exit fields (Section
+ * "Time-Dependent Simulation"): out[b][x][m] = (1/B) sum_j in[j][b][x]
+ * exp(+2 pi i j m / B) over the B rows (energies ascending), B a power of
+ * two in [2, 4096].  Device buffers, c64 if precision == BPM_FP32_FUSED
+ * else c128; in: [B][2][nx], out: [2][nx][B].  Asynchronous on stream. */
+int bpm_omega_to_t_device(const void* d_in, void* d_out, int32_t n_energy,
+                          int32_t nx, int32_t precision, void* stream);
+
+/* Continuous-batching server.  bpm_submit enqueues a full march (steps
+ * [0, nz)) of the plan's B rows with input psi_in (host c128 [B][2][nx],
+ * copied before return); outputs as in bpm_propagate and must stay valid
+ * until bpm_poll returns BPM_OK or an error.  Requests are admitted as
+ * device memory (within the configured budget) and launch slots free up;
+ * admitted requests advance together in epochs of fused launches, grouped by
+ * transverse size.  BPM_ERR_BUSY if the queue is full.  bpm_poll waits up
+ * to timeout_ms (0 = just test, <0 = wait forever) and returns BPM_OK once
+ * (outputs written), BPM_NOT_READY, or the request's error. */
+int bpm_submit(bpm_plan_t plan, const double* psi_in, double* psi_out,
+               void* records, double* powers, bpm_ticket_t* out);
+int bpm_poll(bpm_ticket_t ticket, int32_t timeout_ms);
+
+/* Server settings (call before the first submit or when idle):
+ * mem_fraction of the device's free memory usable for admitted requests
+ * (0 < f <= 0.9), max_active admitted requests, epoch_steps z steps per
+ * epoch launch, max_queue pending requests.  Values <= 0 keep defaults
+ * (0.6, 256, 256, 100000). */
+int bpm_server_configure(double mem_fraction, int32_t max_active,
+                         int32_t epoch_steps, int32_t max_queue);
+
+/* Timestamps (seconds, steady clock) of a finished or running ticket:
+ * submit, admission to the device, completion (0 while not reached). */
+int bpm_ticket_times(bpm_ticket_t ticket, double* t_submit, double* t_admit,
+                     double* t_done);
+
+/* Copy the plan's prepared slices to the host: mask uint8 [nz][nx] (1 =
+ * inside) and/or the strain phasor exp(i h u_x) as c128 [nz][nx] (0 outside
+ * the crystal).  Either pointer may be NULL.  For inspection and tests. */
+int bpm_fetch_slices(bpm_plan_t plan, uint8_t* mask, double* phasor);
+
+/* Release the plan and its device memory.  BPM_ERR_BUSY while tickets of
+ * the plan are pending. */
+int bpm_destroy(bpm_plan_t plan);
+
+/* Message for the calling thread's last error ("" if none). */
+const char* bpm_last_error(void);
+
+/* Library version string. */
+const char* bpm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BPM_H */

@@ -1,0 +1,260 @@
+"""ctypes binding of the C ABI declared in include/bpm.h.
+
+The module-level functions carry the C names (``bpm_plan``,
+``bpm_set_crystal``, ...) and only marshal arguments: numpy arrays become
+pointers, torch tensors pass ``data_ptr()`` and their stream handle.  Every
+step of the march runs in the CUDA library; if the library is missing this
+module raises instead of falling back to anything else.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libbpm.so")
+
+BPM_OK, BPM_NOT_READY = 0, 1
+BPM_ERR_INVALID, BPM_ERR_OOM, BPM_ERR_CUDA = -1, -2, -3
+BPM_ERR_BUSY, BPM_ERR_TIMEOUT, BPM_ERR_NUMERIC = -4, -5, -6
+BPM_FP64_PLAIN, BPM_FP32_FUSED = 0, 1
+
+_STATUS_NAMES = {0: "OK", 1: "NOT_READY", -1: "ERR_INVALID", -2: "ERR_OOM",
+                 -3: "ERR_CUDA", -4: "ERR_BUSY", -5: "ERR_TIMEOUT", -6: "ERR_NUMERIC"}
+
+
+class BpmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class bpm_problem(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("dx_um", ctypes.c_double), ("dz_um", ctypes.c_double), ("x0_um", ctypes.c_double),
+        ("n_energy", ctypes.c_int32), ("energy_ev", ctypes.POINTER(ctypes.c_double)),
+        ("e_ref_ev", ctypes.c_double), ("theta_b_ref_rad", ctypes.c_double),
+        ("chi0_re", ctypes.c_double), ("chi0_im", ctypes.c_double),
+        ("chih_re", ctypes.c_double), ("chih_im", ctypes.c_double),
+        ("record_every", ctypes.c_int32), ("precision", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int32
+_D = ctypes.c_double
+_SIGS = {
+    "bpm_plan": ([ctypes.POINTER(bpm_problem), ctypes.POINTER(_P)], ctypes.c_int),
+    "bpm_set_crystal": ([_P, _I, _D, _D, _D, _D, _P, _P, _I], ctypes.c_int),
+    "bpm_set_strain": ([_P, _I, _P, _P, _I], ctypes.c_int),
+    "bpm_propagate": ([_P, _P, _P, _P, _P, _I, _I], ctypes.c_int),
+    "bpm_propagate_device": ([_P, _P, _P, _P, _P, _I, _I, _P], ctypes.c_int),
+    "bpm_omega_to_t_device": ([_P, _P, _I, _I, _I, _P], ctypes.c_int),
+    "bpm_submit": ([_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "bpm_poll": ([ctypes.c_uint64, _I], ctypes.c_int),
+    "bpm_server_configure": ([_D, _I, _I, _I], ctypes.c_int),
+    "bpm_ticket_times": ([ctypes.c_uint64, ctypes.POINTER(_D), ctypes.POINTER(_D),
+                          ctypes.POINTER(_D)], ctypes.c_int),
+    "bpm_fetch_slices": ([_P, _P, _P], ctypes.c_int),
+    "bpm_destroy": ([_P], ctypes.c_int),
+    "bpm_last_error": ([], ctypes.c_char_p),
+    "bpm_version": ([], ctypes.c_char_p),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(code: int) -> int:
+    if code < 0:
+        raise BpmError(code, load().bpm_last_error().decode())
+    return code
+
+
+def _ptr(a) -> int | None:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"], "arrays must be C-contiguous"
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return int(a)
+
+
+# ---- C names, marshalling only -------------------------------------------
+
+def bpm_plan(problem: bpm_problem) -> int:
+    h = ctypes.c_void_p()
+    _check(load().bpm_plan(ctypes.byref(problem), ctypes.byref(h)))
+    return h.value
+
+
+def bpm_set_crystal(plan, kind, asym_angle_rad=0.0, thickness_um=0.0, surf_x_um=0.0,
+                    surf_z_um=0.0, mask=None, poly_xz_um=None):
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    p = None if poly_xz_um is None else np.ascontiguousarray(poly_xz_um, dtype=np.float64)
+    nv = 0 if p is None else p.size // 2
+    return _check(load().bpm_set_crystal(plan, int(kind), float(asym_angle_rad),
+                                         float(thickness_um), float(surf_x_um),
+                                         float(surf_z_um), _ptr(m), _ptr(p), nv))
+
+
+def bpm_set_strain(plan, kind, ux_um=None, params=None):
+    u = None if ux_um is None else np.ascontiguousarray(ux_um, dtype=np.float64)
+    p = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
+    return _check(load().bpm_set_strain(plan, int(kind), _ptr(u), _ptr(p),
+                                        0 if p is None else p.size))
+
+
+def bpm_propagate(plan, psi_in, psi_out, records, powers, n_begin, n_end):
+    return _check(load().bpm_propagate(plan, _ptr(psi_in), _ptr(psi_out), _ptr(records),
+                                       _ptr(powers), int(n_begin), int(n_end)))
+
+
+def bpm_propagate_device(plan, d_psi_in, d_psi_out, d_records, d_powers, n_begin, n_end,
+                         stream=None):
+    return _check(load().bpm_propagate_device(plan, _ptr(d_psi_in), _ptr(d_psi_out),
+                                              _ptr(d_records), _ptr(d_powers), int(n_begin),
+                                              int(n_end), stream))
+
+
+def bpm_omega_to_t_device(d_in, d_out, n_energy, nx, precision, stream=None):
+    return _check(load().bpm_omega_to_t_device(_ptr(d_in), _ptr(d_out), int(n_energy),
+                                               int(nx), int(precision), stream))
+
+
+def bpm_submit(plan, psi_in, psi_out, records=None, powers=None) -> int:
+    t = ctypes.c_uint64()
+    _check(load().bpm_submit(plan, _ptr(psi_in), _ptr(psi_out), _ptr(records), _ptr(powers),
+                             ctypes.byref(t)))
+    return t.value
+
+
+def bpm_poll(ticket, timeout_ms=0) -> int:
+    return _check(load().bpm_poll(ctypes.c_uint64(ticket), int(timeout_ms)))
+
+
+def bpm_server_configure(mem_fraction=0.0, max_active=0, epoch_steps=0, max_queue=0):
+    return _check(load().bpm_server_configure(float(mem_fraction), int(max_active),
+                                              int(epoch_steps), int(max_queue)))
+
+
+def bpm_ticket_times(ticket):
+    a, b, c = _D(), _D(), _D()
+    _check(load().bpm_ticket_times(ctypes.c_uint64(ticket), ctypes.byref(a), ctypes.byref(b),
+                                   ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def bpm_fetch_slices(plan, mask=None, phasor=None):
+    return _check(load().bpm_fetch_slices(plan, _ptr(mask), _ptr(phasor)))
+
+
+def bpm_destroy(plan):
+    return _check(load().bpm_destroy(plan))
+
+
+def bpm_last_error() -> str:
+    return load().bpm_last_error().decode()
+
+
+def bpm_version() -> str:
+    return load().bpm_version().decode()
+
+
+# ---- convenience wrapper over the same calls -------------------------------
+
+@dataclass
+class MarchOutput:
+    psi: np.ndarray        # [B][2][N] complex128
+    records: np.ndarray    # [B][n_rec][2][N] complex64 (FP32) / complex128 (FP64)
+    powers: np.ndarray     # [B][n_rec+1][2]
+
+
+class Plan:
+    """Owns one bpm plan built from a workload (see ``inputs.Workload``)."""
+
+    def __init__(self, wl, precision: int = BPM_FP32_FUSED, record_every: int | None = None):
+        self.wl = wl
+        self.precision = precision
+        self.record_every = wl.record_every if record_every is None else record_every
+        self._energies = np.ascontiguousarray(wl.energies_ev, dtype=np.float64)
+        prob = bpm_problem(
+            nx=wl.nx, nz=wl.nz, dx_um=wl.dx_um, dz_um=wl.dz_um, x0_um=wl.x0_um,
+            n_energy=len(self._energies),
+            energy_ev=self._energies.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            e_ref_ev=wl.e_ref_ev, theta_b_ref_rad=wl.theta_b_ref_rad,
+            chi0_re=wl.chi0.real, chi0_im=wl.chi0.imag, chih_re=wl.chih.real,
+            chih_im=wl.chih.imag, record_every=self.record_every, precision=precision)
+        self.handle = bpm_plan(prob)
+        c = dict(wl.crystal)
+        kind = c.pop("kind")
+        bpm_set_crystal(self.handle, kind, c.get("asym_angle_rad", 0.0),
+                        c.get("thickness_um", 0.0), c.get("surf_x_um", 0.0),
+                        c.get("surf_z_um", 0.0), c.get("mask"), c.get("polygon"))
+        st = dict(wl.strain)
+        bpm_set_strain(self.handle, st.pop("kind"), st.get("ux"), st.get("params"))
+        self.n_rec = (wl.nz // self.record_every) if self.record_every > 0 else 0
+
+    @property
+    def rec_dtype(self):
+        return np.complex64 if self.precision == BPM_FP32_FUSED else np.complex128
+
+    def propagate(self, psi_in=None, n_begin=0, n_end=None, records=True, powers=True,
+                  out: MarchOutput | None = None) -> MarchOutput:
+        wl = self.wl
+        psi_in = np.ascontiguousarray(wl.psi0 if psi_in is None else psi_in,
+                                      dtype=np.complex128)
+        n_end = wl.nz if n_end is None else n_end
+        if out is None:
+            out = MarchOutput(np.empty_like(psi_in),
+                              np.zeros((wl.batch, self.n_rec, 2, wl.nx), self.rec_dtype),
+                              np.zeros((wl.batch, self.n_rec + 1, 2)))
+        bpm_propagate(self.handle, psi_in, out.psi, out.records if records else None,
+                      out.powers if powers else None, n_begin, n_end)
+        return out
+
+    def slices(self):
+        mask = np.zeros((self.wl.nz, self.wl.nx), np.uint8)
+        ph = np.zeros((self.wl.nz, self.wl.nx), np.complex128)
+        bpm_fetch_slices(self.handle, mask, ph)
+        return mask, ph
+
+    def close(self):
+        if self.handle:
+            bpm_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

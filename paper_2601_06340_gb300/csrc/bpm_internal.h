@@ -1,0 +1,128 @@
+// Internal types shared by the host runtime and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <complex>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/bpm.h"
+
+namespace bpm {
+
+constexpr int kMinLogN = 3;
+constexpr int kMaxLogN = 13;          // nx <= 8192 in one CTA
+constexpr double kTwoPi = 6.283185307179586;
+constexpr double kHcEvAngstrom = 12398.419843320026;
+
+// Device status word bits (per launch).
+enum : int { kStatusWaitTimeout = 1 };
+
+// One batch row of a fused FP32 launch.  Everything the kernel needs for a
+// row is here, so rows of different plans (different energies, strain
+// streams, step ranges) can share one launch.
+struct RowDescF32 {
+  float2* state;            // [2][N] raw envelopes (common phase removed)
+  const float2* prop;       // [2][N] (P(q)-1)/N in the FFT's output order
+  const float2* phasor;     // [nz][N] exp(i h u_x), (0,0) outside the crystal
+  float2* records;          // [n_rec][2][N] or null
+  double* powers;           // [n_rec+1][2] or null
+  float2 am1;               // Delta_eps_0 - 1 inside the crystal
+  float2 b;                 // Delta_eps_{+-1} inside the crystal
+  double gphase;            // common per-step phase (dz^ cos alpha) mod 2 pi
+  double dx_um;
+  int32_t n_begin;          // first step of this launch (absolute)
+  int32_t n_end;            // one past the last step this row may take
+  int32_t n_phase0;         // absolute step at which `state` carries phase 0
+  int32_t record_every;     // 0 = no records
+};
+
+// One batch row of the FP64 plain path (all rows of a plan share N).
+struct RowDescF64 {
+  const double2* prop;      // [2][N] P(q)/N in natural FFT order
+  double2 a;                // Delta_eps_0
+  double2 b;                // Delta_eps_{+-1}
+  double gphase;
+};
+
+// FP64 constants of one photon energy (Eqs. fov4-fov12).
+struct EnergyConsts {
+  double e_ev, k_um, s, c, dzh, dxh;
+  std::complex<double> w, phi0, a, b, am1;
+  double gphase;            // fmod(dzh * c, 2 pi)
+};
+
+}  // namespace bpm
+
+struct bpm_plan_s {
+  std::mutex mu;
+  // problem
+  int32_t nx = 0, nz = 0, logn = 0, nb = 0, record_every = 0, precision = 0;
+  double dx_um = 0, dz_um = 0, x0_um = 0, e_ref_ev = 0, theta_b_ref = 0;
+  std::complex<double> chi0, chih;
+  std::vector<double> energies;
+  std::vector<bpm::EnergyConsts> ec;
+  int32_t n_rec = 0;
+  double d_um = 0, h_per_um = 0;
+  // crystal and strain descriptions (host copies)
+  int32_t crystal_kind = BPM_CRYSTAL_VACUUM;
+  double asym = 0, thick = 0, surf_x = 0, surf_z = 0;
+  std::vector<uint8_t> mask;
+  std::vector<double> poly;
+  int32_t strain_kind = BPM_STRAIN_NONE;
+  std::vector<double> ux;
+  double sparams[4] = {0, 0, 0, 0};
+  bool slices_dirty = true;
+  // device
+  int device = 0;
+  void* d_phasor = nullptr;       // [nz][nx] c64 (FP32) or c128 (FP64)
+  void* d_prop = nullptr;         // [B][2][nx] c64 (delta form) or c128
+  void* d_tw = nullptr;           // FP32: float4 [nx] hi/lo; FP64: double2 [nx]
+  void* d_state = nullptr;        // [B][2][nx] c64 / c128
+  void* d_state2 = nullptr;       // FP64 ping-pong buffer
+  void* d_rows = nullptr;         // RowDescF32[B] or RowDescF64[B]
+  void* d_io = nullptr;           // [B][2][nx] c128 host-transfer staging
+  int* d_status = nullptr;        // device status word
+  size_t device_bytes = 0;
+  int pending = 0;                // tickets not yet finished
+};
+
+namespace bpm {
+
+// Thread-local error reporting (capi.cpp).
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+// Plan math (plan.cpp).
+int validate_problem(const bpm_problem* p, std::string* why);
+void compute_energy_consts(bpm_plan_s* plan);
+void fused_prop_table(const bpm_plan_s* plan, int row, std::vector<float2>* out);
+void plain_prop_table(const bpm_plan_s* plan, int row, std::vector<double2>* out);
+void twiddle_table_f32(int n, std::vector<float4>* out);
+void twiddle_table_f64(int n, std::vector<double2>* out);
+std::vector<int> fft_output_order(int logn);   // position -> frequency index
+
+// Kernels (launchers in *.cu).
+int prepare_slices(bpm_plan_s* plan, cudaStream_t st);
+int launch_fused(int logn, const RowDescF32* d_rows, int n_rows, int steps,
+                 const float4* d_tw, int* d_status, cudaStream_t st);
+int plain_march(bpm_plan_s* plan, int n_begin, int n_end, int n_phase0, void* d_records,
+                double* d_powers, cudaStream_t st);
+int launch_convert_in(const double2* src, float2* dst, size_t n, cudaStream_t st);
+int launch_finish_f32(const float2* state, double2* out_c128, float2* out_c64,
+                      const double* gphase, int n_rows, int nx, int steps,
+                      double dx, double* final_powers, int power_stride,
+                      cudaStream_t st);
+int launch_finish_f64(const double2* state, double2* out, const double* gphase,
+                      int n_rows, int nx, int steps, double dx,
+                      double* final_powers, int power_stride, cudaStream_t st);
+int launch_omega_to_t(const void* d_in, void* d_out, int nb, int nx,
+                      int precision, cudaStream_t st);
+int fused_smem_bytes(int logn);
+int fused_rows_per_cta(int logn);
+int fused_threads(int logn);
+
+}  // namespace bpm

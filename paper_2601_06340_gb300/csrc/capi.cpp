@@ -1,0 +1,523 @@
+// C ABI: plan lifetime, crystal/strain description, synchronous and
+// stream-ordered marches.  See include/bpm.h for the contract.
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "bpm_internal.h"
+
+namespace bpm {
+
+static thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();  // clear a sticky-free error so later calls start clean
+  return e == cudaErrorMemoryAllocation ? BPM_ERR_OOM : BPM_ERR_CUDA;
+}
+
+namespace {
+
+struct DevAlloc {
+  std::vector<void**> owned;
+};
+
+int dev_alloc(bpm_plan_s* plan, void** p, size_t bytes, const char* what) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? BPM_ERR_OOM : BPM_ERR_CUDA,
+                std::string("cudaMalloc(") + what + ", " + std::to_string(bytes) +
+                    " bytes): " + cudaGetErrorString(e));
+  }
+  plan->device_bytes += bytes;
+  return BPM_OK;
+}
+
+void free_plan_memory(bpm_plan_s* plan) {
+  void** ptrs[] = {&plan->d_phasor, &plan->d_prop, &plan->d_tw, &plan->d_state,
+                   &plan->d_state2, &plan->d_rows, &plan->d_io};
+  for (void** p : ptrs) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+  if (plan->d_status) cudaFree(plan->d_status);
+  plan->d_status = nullptr;
+}
+
+size_t csize(const bpm_plan_s* plan) { return plan->precision == BPM_FP32_FUSED ? 8 : 16; }
+
+}  // namespace
+
+// Per-plan auxiliaries that are not part of the public struct layout.
+struct PlanAux {
+  cudaStream_t stream = nullptr;
+  void* d_rec = nullptr;      // host-API record buffer
+  size_t rec_bytes = 0;
+  double* d_pow = nullptr;    // host-API powers buffer
+  size_t pow_bytes = 0;
+  double2* d_g = nullptr;     // [B] common phase factors
+};
+
+static PlanAux* aux_of(bpm_plan_s* plan);
+
+}  // namespace bpm
+
+using namespace bpm;
+
+// Aux storage lives in a side table keyed by plan pointer (keeps the plan
+// struct plain).
+#include <unordered_map>
+static std::mutex g_aux_mu;
+static std::unordered_map<bpm_plan_s*, std::unique_ptr<PlanAux>> g_aux;
+
+namespace bpm {
+static PlanAux* aux_of(bpm_plan_s* plan) {
+  std::lock_guard<std::mutex> lk(g_aux_mu);
+  auto& slot = g_aux[plan];
+  if (!slot) slot = std::make_unique<PlanAux>();
+  return slot.get();
+}
+
+// Build the fused row descriptors for rows [0, B) of `plan`.
+void fused_rows(bpm_plan_s* plan, float2* state, float2* rec, double* pw, int n_begin,
+                int n_end, std::vector<RowDescF32>* out) {
+  out->resize(plan->nb);
+  const size_t n = plan->nx;
+  for (int r = 0; r < plan->nb; ++r) {
+    RowDescF32& d = (*out)[r];
+    d.state = state + size_t(r) * 2 * n;
+    d.prop = static_cast<const float2*>(plan->d_prop) + size_t(r) * 2 * n;
+    d.phasor = static_cast<const float2*>(plan->d_phasor);
+    d.records = rec ? rec + size_t(r) * plan->n_rec * 2 * n : nullptr;
+    d.powers = pw ? pw + size_t(r) * (plan->n_rec + 1) * 2 : nullptr;
+    const EnergyConsts& c = plan->ec[r];
+    d.am1 = make_float2(float(c.am1.real()), float(c.am1.imag()));
+    d.b = make_float2(float(c.b.real()), float(c.b.imag()));
+    d.gphase = c.gphase;
+    d.dx_um = plan->dx_um;
+    d.n_begin = n_begin;
+    d.n_end = n_end;
+    d.n_phase0 = n_begin;
+    d.record_every = (rec || pw) ? plan->record_every : 0;
+  }
+}
+
+// Common phase g^(steps) per row in FP64.
+void phase_factors(const bpm_plan_s* plan, int steps, std::vector<double2>* out) {
+  out->resize(plan->nb);
+  for (int r = 0; r < plan->nb; ++r) {
+    double ang = std::fmod(double(steps) * plan->ec[r].gphase, kTwoPi);
+    (*out)[r] = make_double2(std::cos(ang), std::sin(ang));
+  }
+}
+
+// Enqueue the march of all rows on `st`.  state: the buffer holding the
+// state at n_begin (c64 for FP32, the plan's d_state for FP64); outputs as
+// documented for bpm_propagate_device.
+static int enqueue_march(bpm_plan_s* plan, PlanAux* aux, void* state, void* d_rec, double* d_pw,
+                         int n_begin, int n_end, void* out, bool out_c128, cudaStream_t st) {
+  const int steps = n_end - n_begin;
+  std::vector<double2> g;
+  phase_factors(plan, steps, &g);
+  cudaError_t e = cudaMemcpyAsync(aux->d_g, g.data(), sizeof(double2) * plan->nb,
+                                  cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "upload phase factors");
+  double* final_pw = d_pw ? d_pw + 2 * plan->n_rec : nullptr;
+  const int pw_stride = 2 * (plan->n_rec + 1);
+  if (plan->precision == BPM_FP32_FUSED) {
+    std::vector<RowDescF32> rows;
+    fused_rows(plan, static_cast<float2*>(state), static_cast<float2*>(d_rec), d_pw, n_begin,
+               n_end, &rows);
+    e = cudaMemcpyAsync(plan->d_rows, rows.data(), sizeof(RowDescF32) * rows.size(),
+                        cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "upload row descriptors");
+    int rc = launch_fused(plan->logn, static_cast<const RowDescF32*>(plan->d_rows), plan->nb,
+                          steps, static_cast<const float4*>(plan->d_tw), plan->d_status, st);
+    if (rc != BPM_OK) return rc;
+    return launch_finish_f32(static_cast<const float2*>(state),
+                             out_c128 ? static_cast<double2*>(out) : nullptr,
+                             out_c128 ? nullptr : static_cast<float2*>(out),
+                             reinterpret_cast<const double*>(aux->d_g), plan->nb, plan->nx, steps,
+                             plan->dx_um, final_pw, pw_stride, st);
+  }
+  int rc = plain_march(plan, n_begin, n_end, n_begin, d_rec, d_pw, st);
+  if (rc != BPM_OK) return rc;
+  return launch_finish_f64(static_cast<const double2*>(plan->d_state), static_cast<double2*>(out),
+                           reinterpret_cast<const double*>(aux->d_g), plan->nb, plan->nx, steps,
+                           plan->dx_um, final_pw, pw_stride, st);
+}
+
+}  // namespace bpm
+
+extern "C" {
+
+const char* bpm_last_error(void) { return g_last_error.c_str(); }
+
+const char* bpm_version(void) { return "bpm-gb300 0.1 (sm_103a)"; }
+
+int bpm_plan(const bpm_problem* p, bpm_plan_t* out) {
+  if (!out) return fail(BPM_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  std::string why;
+  if (validate_problem(p, &why) != BPM_OK) return fail(BPM_ERR_INVALID, why);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "no usable CUDA device");
+
+  auto plan = std::make_unique<bpm_plan_s>();
+  plan->device = dev;
+  plan->nx = p->nx;
+  plan->nz = p->nz;
+  plan->logn = 0;
+  while ((1 << plan->logn) < p->nx) ++plan->logn;
+  plan->nb = p->n_energy;
+  plan->record_every = p->record_every;
+  plan->precision = p->precision;
+  plan->dx_um = p->dx_um;
+  plan->dz_um = p->dz_um;
+  plan->x0_um = p->x0_um;
+  plan->e_ref_ev = p->e_ref_ev;
+  plan->theta_b_ref = p->theta_b_ref_rad;
+  plan->chi0 = std::complex<double>(p->chi0_re, p->chi0_im);
+  plan->chih = std::complex<double>(p->chih_re, p->chih_im);
+  plan->energies.assign(p->energy_ev, p->energy_ev + p->n_energy);
+  plan->n_rec = p->record_every > 0 ? p->nz / p->record_every : 0;
+  double lam_ref_um = kHcEvAngstrom / p->e_ref_ev * 1e-4;
+  plan->d_um = lam_ref_um / (2.0 * std::sin(p->theta_b_ref_rad));
+  plan->h_per_um = kTwoPi / plan->d_um;
+  compute_energy_consts(plan.get());
+
+  bpm_plan_s* pl = plan.get();
+  const size_t n = pl->nx, nb = pl->nb, cs = csize(pl);
+  int rc = BPM_OK;
+  auto A = [&](void** ptr, size_t bytes, const char* what) {
+    if (rc == BPM_OK) rc = dev_alloc(pl, ptr, bytes, what);
+  };
+  A(&pl->d_prop, nb * 2 * n * cs, "propagator tables");
+  A(&pl->d_tw, n * 16, "twiddles");
+  A(&pl->d_state, nb * 2 * n * cs, "state");
+  if (pl->precision == BPM_FP64_PLAIN) A(&pl->d_state2, nb * 2 * n * cs, "state scratch");
+  A(&pl->d_rows, nb * std::max(sizeof(RowDescF32), sizeof(RowDescF64)), "row descriptors");
+  A(&pl->d_io, nb * 2 * n * 16, "host staging");
+  A(reinterpret_cast<void**>(&pl->d_status), sizeof(int), "status");
+  PlanAux* aux = aux_of(pl);
+  A(reinterpret_cast<void**>(&aux->d_g), nb * sizeof(double2), "phase factors");
+  if (rc == BPM_OK) {
+    e = cudaStreamCreateWithFlags(&aux->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) rc = cuda_fail(e, "stream");
+  }
+  if (rc == BPM_OK) {
+    cudaStream_t st = aux->stream;
+    if (pl->precision == BPM_FP32_FUSED) {
+      std::vector<float4> tw;
+      twiddle_table_f32(pl->nx, &tw);
+      e = cudaMemcpyAsync(pl->d_tw, tw.data(), n * 16, cudaMemcpyHostToDevice, st);
+      for (int r = 0; r < pl->nb && e == cudaSuccess; ++r) {
+        std::vector<float2> t;
+        fused_prop_table(pl, r, &t);
+        e = cudaMemcpyAsync(static_cast<float2*>(pl->d_prop) + size_t(r) * 2 * n, t.data(),
+                            t.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
+      }
+    } else {
+      std::vector<double2> tw;
+      twiddle_table_f64(pl->nx, &tw);
+      e = cudaMemcpyAsync(pl->d_tw, tw.data(), n * 16, cudaMemcpyHostToDevice, st);
+      std::vector<RowDescF64> rows(pl->nb);
+      for (int r = 0; r < pl->nb && e == cudaSuccess; ++r) {
+        std::vector<double2> t;
+        plain_prop_table(pl, r, &t);
+        e = cudaMemcpyAsync(static_cast<double2*>(pl->d_prop) + size_t(r) * 2 * n, t.data(),
+                            t.size() * sizeof(double2), cudaMemcpyHostToDevice, st);
+        rows[r].prop = static_cast<const double2*>(pl->d_prop) + size_t(r) * 2 * n;
+        rows[r].a = make_double2(pl->ec[r].a.real(), pl->ec[r].a.imag());
+        rows[r].b = make_double2(pl->ec[r].b.real(), pl->ec[r].b.imag());
+        rows[r].gphase = pl->ec[r].gphase;
+      }
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(pl->d_rows, rows.data(), rows.size() * sizeof(RowDescF64),
+                            cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(pl->d_status, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "plan upload");
+  }
+  if (rc != BPM_OK) {
+    if (aux->stream) cudaStreamDestroy(aux->stream);
+    if (aux->d_g) cudaFree(aux->d_g);
+    free_plan_memory(pl);
+    std::lock_guard<std::mutex> lk(g_aux_mu);
+    g_aux.erase(pl);
+    return rc;
+  }
+  *out = plan.release();
+  return BPM_OK;
+}
+
+int bpm_set_crystal(bpm_plan_t plan, int32_t kind, double asym_angle_rad, double thickness_um,
+                    double surf_x_um, double surf_z_um, const uint8_t* mask,
+                    const double* poly_xz_um, int32_t nv) {
+  if (!plan) return fail(BPM_ERR_INVALID, "plan is NULL");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  if (plan->pending) return fail(BPM_ERR_BUSY, "plan has pending tickets");
+  if (kind < BPM_CRYSTAL_VACUUM || kind > BPM_CRYSTAL_SLAB_AND_POLYGON)
+    return fail(BPM_ERR_INVALID, "unknown crystal kind");
+  const bool slab = kind == BPM_CRYSTAL_SLAB || kind == BPM_CRYSTAL_SLAB_AND_MASK ||
+                    kind == BPM_CRYSTAL_SLAB_AND_POLYGON;
+  if (slab && (!std::isfinite(asym_angle_rad) || !(thickness_um >= 0) ||
+               !std::isfinite(thickness_um) || !std::isfinite(surf_x_um) ||
+               !std::isfinite(surf_z_um)))
+    return fail(BPM_ERR_INVALID, "slab parameters must be finite, thickness >= 0");
+  const bool needs_mask = kind == BPM_CRYSTAL_MASK || kind == BPM_CRYSTAL_SLAB_AND_MASK;
+  if (needs_mask && !mask) return fail(BPM_ERR_INVALID, "mask is NULL");
+  if (kind == BPM_CRYSTAL_SLAB_AND_POLYGON) {
+    if (!poly_xz_um || nv < 3) return fail(BPM_ERR_INVALID, "polygon needs nv >= 3 vertices");
+    for (int i = 0; i < 2 * nv; ++i)
+      if (!std::isfinite(poly_xz_um[i])) return fail(BPM_ERR_INVALID, "polygon not finite");
+  }
+  plan->crystal_kind = kind;
+  plan->asym = asym_angle_rad;
+  plan->thick = thickness_um;
+  plan->surf_x = surf_x_um;
+  plan->surf_z = surf_z_um;
+  if (needs_mask) plan->mask.assign(mask, mask + size_t(plan->nx) * plan->nz);
+  else plan->mask.clear();
+  if (kind == BPM_CRYSTAL_SLAB_AND_POLYGON) plan->poly.assign(poly_xz_um, poly_xz_um + 2 * nv);
+  else plan->poly.clear();
+  plan->slices_dirty = true;
+  return BPM_OK;
+}
+
+int bpm_set_strain(bpm_plan_t plan, int32_t kind, const double* ux_um, const double* params,
+                   int32_t n_params) {
+  if (!plan) return fail(BPM_ERR_INVALID, "plan is NULL");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  if (plan->pending) return fail(BPM_ERR_BUSY, "plan has pending tickets");
+  if (kind < BPM_STRAIN_NONE || kind > BPM_STRAIN_EDGE_DISLOCATION)
+    return fail(BPM_ERR_INVALID, "unknown strain kind");
+  const size_t cells = size_t(plan->nx) * plan->nz;
+  if (kind == BPM_STRAIN_ARRAY) {
+    if (!ux_um) return fail(BPM_ERR_INVALID, "ux_um is NULL");
+    for (size_t i = 0; i < cells; ++i)
+      if (!std::isfinite(ux_um[i])) return fail(BPM_ERR_INVALID, "ux_um not finite");
+  }
+  if (kind == BPM_STRAIN_BENT || kind == BPM_STRAIN_EDGE_DISLOCATION) {
+    if (!params || n_params < 4) return fail(BPM_ERR_INVALID, "need 4 strain parameters");
+    for (int i = 0; i < 4; ++i)
+      if (!std::isfinite(params[i])) return fail(BPM_ERR_INVALID, "strain parameters not finite");
+    if (kind == BPM_STRAIN_BENT && params[0] == 0.0)
+      return fail(BPM_ERR_INVALID, "bend radius must be nonzero");
+    if (kind == BPM_STRAIN_EDGE_DISLOCATION && params[1] == 1.0)
+      return fail(BPM_ERR_INVALID, "Poisson ratio must differ from 1");
+  }
+  plan->strain_kind = kind;
+  if (kind == BPM_STRAIN_ARRAY) plan->ux.assign(ux_um, ux_um + cells);
+  else plan->ux.clear();
+  for (int i = 0; i < 4; ++i)
+    plan->sparams[i] = (params && i < n_params) ? params[i] : 0.0;
+  plan->slices_dirty = true;
+  return BPM_OK;
+}
+
+static int check_range(bpm_plan_s* plan, int32_t n_begin, int32_t n_end) {
+  if (n_begin < 0 || n_end > plan->nz || n_begin >= n_end)
+    return fail(BPM_ERR_INVALID, "need 0 <= n_begin < n_end <= nz");
+  return BPM_OK;
+}
+
+static int finish_status(bpm_plan_s* plan, cudaStream_t st) {
+  int status = 0;
+  cudaError_t e = cudaMemcpyAsync(&status, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "march");
+  if (status & kStatusWaitTimeout) {
+    cudaMemsetAsync(plan->d_status, 0, sizeof(int), st);
+    cudaStreamSynchronize(st);
+    return fail(BPM_ERR_TIMEOUT, "a bounded wait for a strain slice expired on the device");
+  }
+  return BPM_OK;
+}
+
+int bpm_propagate(bpm_plan_t plan, const double* psi_in, double* psi_out, void* records,
+                  double* powers, int32_t n_begin, int32_t n_end) {
+  if (!plan) return fail(BPM_ERR_INVALID, "plan is NULL");
+  if (!psi_in || !psi_out) return fail(BPM_ERR_INVALID, "psi_in / psi_out is NULL");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  if (plan->pending) return fail(BPM_ERR_BUSY, "plan has pending tickets");
+  int rc = check_range(plan, n_begin, n_end);
+  if (rc != BPM_OK) return rc;
+  PlanAux* aux = aux_of(plan);
+  cudaStream_t st = aux->stream;
+  if (plan->slices_dirty && (rc = prepare_slices(plan, st)) != BPM_OK) return rc;
+
+  const size_t n = plan->nx, nb = plan->nb, cs = csize(plan);
+  const int nrec = plan->n_rec;
+  const bool want_rec = records && nrec > 0;
+  const bool want_pw = powers != nullptr;
+  size_t rec_bytes = nb * size_t(nrec) * 2 * n * cs;
+  size_t pow_bytes = nb * size_t(nrec + 1) * 2 * sizeof(double);
+  if (want_rec && aux->rec_bytes < rec_bytes) {
+    if (aux->d_rec) cudaFree(aux->d_rec);
+    aux->d_rec = nullptr;
+    aux->rec_bytes = 0;
+    if ((rc = dev_alloc(plan, &aux->d_rec, rec_bytes, "records")) != BPM_OK) return rc;
+    aux->rec_bytes = rec_bytes;
+  }
+  if (want_pw && aux->pow_bytes < pow_bytes) {
+    if (aux->d_pow) cudaFree(aux->d_pow);
+    aux->d_pow = nullptr;
+    aux->pow_bytes = 0;
+    if ((rc = dev_alloc(plan, reinterpret_cast<void**>(&aux->d_pow), pow_bytes, "powers")) != BPM_OK)
+      return rc;
+    aux->pow_bytes = pow_bytes;
+  }
+  const size_t io_bytes = nb * 2 * n * 16;
+  cudaError_t e = cudaMemcpyAsync(plan->d_io, psi_in, io_bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "copy psi_in");
+  void* state = plan->d_state;
+  if (plan->precision == BPM_FP32_FUSED) {
+    rc = launch_convert_in(static_cast<const double2*>(plan->d_io), static_cast<float2*>(state),
+                           nb * 2 * n, st);
+  } else {
+    e = cudaMemcpyAsync(state, plan->d_io, io_bytes, cudaMemcpyDeviceToDevice, st);
+    rc = e == cudaSuccess ? BPM_OK : cuda_fail(e, "stage psi_in");
+  }
+  if (rc != BPM_OK) return rc;
+  rc = enqueue_march(plan, aux, state, want_rec ? aux->d_rec : nullptr,
+                     want_pw ? aux->d_pow : nullptr, n_begin, n_end, plan->d_io, true, st);
+  if (rc != BPM_OK) return rc;
+  e = cudaMemcpyAsync(psi_out, plan->d_io, io_bytes, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(e, "copy psi_out");
+  if (want_rec || want_pw) {
+    const int k = plan->record_every;
+    const int s0 = k > 0 ? n_begin / k : 0, s1 = k > 0 ? n_end / k : 0;
+    for (size_t r = 0; r < nb && e == cudaSuccess; ++r) {
+      if (want_rec && s1 > s0) {
+        const size_t off = (r * nrec + s0) * 2 * n * cs;
+        e = cudaMemcpyAsync(static_cast<char*>(records) + off, static_cast<char*>(aux->d_rec) + off,
+                            size_t(s1 - s0) * 2 * n * cs, cudaMemcpyDeviceToHost, st);
+      }
+      if (want_pw && e == cudaSuccess) {
+        if (s1 > s0) {
+          const size_t off = (r * (nrec + 1) + s0) * 2;
+          e = cudaMemcpyAsync(powers + off, aux->d_pow + off, size_t(s1 - s0) * 2 * sizeof(double),
+                              cudaMemcpyDeviceToHost, st);
+        }
+        const size_t fin = (r * (nrec + 1) + nrec) * 2;
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(powers + fin, aux->d_pow + fin, 2 * sizeof(double),
+                              cudaMemcpyDeviceToHost, st);
+      }
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "copy records / powers");
+  }
+  rc = finish_status(plan, st);
+  if (rc != BPM_OK) return rc;
+  if (want_pw) {
+    for (size_t r = 0; r < nb; ++r)
+      for (int i = 0; i < 2 * (nrec + 1); ++i) {
+        double v = powers[r * 2 * (nrec + 1) + i];
+        if (!std::isfinite(v)) return fail(BPM_ERR_NUMERIC, "non-finite band power");
+      }
+  }
+  return BPM_OK;
+}
+
+int bpm_propagate_device(bpm_plan_t plan, const void* d_psi_in, void* d_psi_out, void* d_records,
+                         void* d_powers, int32_t n_begin, int32_t n_end, void* stream) {
+  if (!plan) return fail(BPM_ERR_INVALID, "plan is NULL");
+  if (!d_psi_in || !d_psi_out) return fail(BPM_ERR_INVALID, "d_psi_in / d_psi_out is NULL");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  if (plan->pending) return fail(BPM_ERR_BUSY, "plan has pending tickets");
+  int rc = check_range(plan, n_begin, n_end);
+  if (rc != BPM_OK) return rc;
+  PlanAux* aux = aux_of(plan);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (plan->slices_dirty && (rc = prepare_slices(plan, aux->stream)) != BPM_OK) return rc;
+  const size_t bytes = size_t(plan->nb) * 2 * plan->nx * csize(plan);
+  void* rec = plan->n_rec > 0 ? d_records : nullptr;
+  if (plan->precision == BPM_FP32_FUSED) {
+    if (d_psi_out != d_psi_in) {
+      cudaError_t e = cudaMemcpyAsync(d_psi_out, d_psi_in, bytes, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return cuda_fail(e, "copy input");
+    }
+    return enqueue_march(plan, aux, d_psi_out, rec, static_cast<double*>(d_powers), n_begin, n_end,
+                         d_psi_out, false, st);
+  }
+  cudaError_t e = cudaMemcpyAsync(plan->d_state, d_psi_in, bytes, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "copy input");
+  return enqueue_march(plan, aux, plan->d_state, rec, static_cast<double*>(d_powers), n_begin,
+                       n_end, d_psi_out, true, st);
+}
+
+int bpm_omega_to_t_device(const void* d_in, void* d_out, int32_t n_energy, int32_t nx,
+                          int32_t precision, void* stream) {
+  if (!d_in || !d_out) return fail(BPM_ERR_INVALID, "buffer is NULL");
+  if (n_energy < 2 || n_energy > 4096 || (n_energy & (n_energy - 1)))
+    return fail(BPM_ERR_INVALID, "n_energy must be a power of two in [2, 4096]");
+  if (nx < 1) return fail(BPM_ERR_INVALID, "nx must be >= 1");
+  if (precision != BPM_FP32_FUSED && precision != BPM_FP64_PLAIN)
+    return fail(BPM_ERR_INVALID, "bad precision");
+  return launch_omega_to_t(d_in, d_out, n_energy, nx, precision, static_cast<cudaStream_t>(stream));
+}
+
+int bpm_fetch_slices(bpm_plan_t plan, uint8_t* mask, double* phasor) {
+  if (!plan) return fail(BPM_ERR_INVALID, "plan is NULL");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  PlanAux* aux = aux_of(plan);
+  int rc = BPM_OK;
+  if (plan->slices_dirty && (rc = prepare_slices(plan, aux->stream)) != BPM_OK) return rc;
+  const size_t cells = size_t(plan->nx) * plan->nz;
+  std::vector<double> buf;
+  if (plan->precision == BPM_FP32_FUSED) {
+    std::vector<float> f(2 * cells);
+    cudaError_t e = cudaMemcpy(f.data(), plan->d_phasor, cells * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "fetch slices");
+    buf.assign(f.begin(), f.end());
+  } else {
+    buf.resize(2 * cells);
+    cudaError_t e = cudaMemcpy(buf.data(), plan->d_phasor, cells * 16, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "fetch slices");
+  }
+  for (size_t c = 0; c < cells; ++c) {
+    if (mask) mask[c] = (buf[2 * c] != 0.0 || buf[2 * c + 1] != 0.0) ? 1 : 0;
+    if (phasor) {
+      phasor[2 * c] = buf[2 * c];
+      phasor[2 * c + 1] = buf[2 * c + 1];
+    }
+  }
+  return BPM_OK;
+}
+
+int bpm_destroy(bpm_plan_t plan) {
+  if (!plan) return fail(BPM_ERR_INVALID, "plan is NULL");
+  {
+    std::lock_guard<std::mutex> lk(plan->mu);
+    if (plan->pending) return fail(BPM_ERR_BUSY, "plan has pending tickets");
+  }
+  PlanAux* aux = aux_of(plan);
+  if (aux->stream) {
+    cudaStreamSynchronize(aux->stream);
+    cudaStreamDestroy(aux->stream);
+  }
+  if (aux->d_rec) cudaFree(aux->d_rec);
+  if (aux->d_pow) cudaFree(aux->d_pow);
+  if (aux->d_g) cudaFree(aux->d_g);
+  free_plan_memory(plan);
+  {
+    std::lock_guard<std::mutex> lk(g_aux_mu);
+    g_aux.erase(plan);
+  }
+  delete plan;
+  return BPM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,425 @@
+// Persistent fused FP32 march (one CTA advances one or more batch rows for
+// `steps` z-steps without returning the fields to global memory).
+//
+// One step of Eq. fov10 (arXiv 2601.06340):
+//   psi_p+- = F^-1[ F[psi_+-] exp(i dz^ delta_+-(q)) ]          (bands apart)
+//   psi_+   <- psi_p+ + (a-1) psi_p+ + b e^{+i h u} psi_p-       inside Pi
+//   psi_-   <- psi_p- + (a-1) psi_p- + b e^{-i h u} psi_p+       inside Pi
+// with the common phase exp(i dz^ cos alpha) removed from the march and put
+// back (in FP64) when results leave the kernel.
+//
+// Layout.  N = 2^LOGN points per band.  Each row is handled by T = N/16
+// threads that own E = 16 points of each band in registers.  The FFT is a
+// mixed-radix decimation-in-frequency transform with passes of radix 16
+// (and one last pass of radix 2^(LOGN mod 4) when needed); the output stays
+// in digit-reversed order, the propagator table is stored in that order, and
+// the inverse is the matching decimation-in-time transform, which restores
+// natural order.  Between passes the fields go through shared memory
+// (padded by one slot per 16 to avoid bank conflicts).  Three passes are
+// fused without a shared-memory round trip:
+//   * inverse pass 0 + coupling + record + next step's forward pass 0,
+//   * forward last pass + propagator + inverse last pass,
+// so a step costs 2 (passes - 1) shared-memory transposes per band.
+//
+// The strain/mask slice exp(i h u_x[n][.]) (8 bytes per cell, (0,0) outside
+// the crystal) is fetched for each step by one bulk asynchronous copy (TMA)
+// into shared memory, completing on an mbarrier; the copy is issued early in
+// the step and consumed at the coupling, so it overlaps the FFT passes.
+// Every wait on that mbarrier is bounded; on expiry the kernel raises a bit
+// in the status word and carries on.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bpm_internal.h"
+#include "radix.cuh"
+
+namespace bpm {
+
+template <int LOGN>
+struct FusedCfg {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int E = N < 16 ? N : 16;          // points per band per thread
+  static constexpr int T = N / E;                    // threads per row
+  static constexpr int NP = (LOGN + 3) / 4;          // FFT passes
+  static constexpr int RL = 1 << (LOGN - 4 * (NP - 1));  // radix of the last pass
+  static constexpr int ROWS = T >= 64 ? 1 : 64 / T;  // rows per CTA
+  static constexpr int THREADS = T * ROWS;
+  static constexpr int PADN = N + (N >> 4);          // padded band length
+  static constexpr int WARPS_PER_ROW = T >= 32 ? T / 32 : 1;
+  // shared memory layout per CTA (bytes)
+  static constexpr int OFF_BUF = 0;                                  // [ROWS][2][PADN] float2
+  static constexpr int OFF_PH = OFF_BUF + ROWS * 2 * PADN * 8;       // [ROWS][N] float2
+  static constexpr int OFF_MBAR = OFF_PH + ROWS * N * 8;             // [ROWS] u64
+  static constexpr int OFF_RECPH = OFF_MBAR + ROWS * 8;              // [ROWS] float2
+  static constexpr int OFF_RED = OFF_RECPH + ROWS * 8;               // [ROWS][WARPS][2] double
+  static constexpr int SMEM = OFF_RED + ROWS * WARPS_PER_ROW * 2 * 8;
+
+  __host__ __device__ static constexpr int radix(int p) { return p < NP - 1 ? 16 : RL; }
+  __host__ __device__ static constexpr int len(int p) { return N >> (4 * p); }
+  __host__ __device__ static constexpr int stride(int p) { return len(p) / radix(p); }
+  __host__ __device__ static constexpr int groups(int p) { return E / radix(p); }
+};
+
+__device__ __forceinline__ int padi(int a) { return a + (a >> 4); }
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src,
+                                          uint32_t bytes, uint64_t* bar) {
+  uint32_t b = smem_u32(bar);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile(
+      "{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }" ::"r"(b),
+      "r"(bytes)
+      : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(b)
+      : "memory");
+}
+
+// Bounded wait for phase `parity` of the barrier; false on expiry.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t b = smem_u32(bar);
+  for (int i = 0; i < (1 << 22); ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(b), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// ---- per-pass helpers (thread owns groups gi = t + i*T) ------------------
+template <int LOGN, int P>
+__device__ __forceinline__ int pass_pos(int gi, int j) {
+  using C = FusedCfg<LOGN>;
+  constexpr int S = C::stride(P), L = C::len(P);
+  return (gi / S) * L + (gi % S) + j * S;
+}
+
+template <int LOGN, int P>
+__device__ __forceinline__ void store_pass(float2* buf, const float2* v, int t) {
+  using C = FusedCfg<LOGN>;
+  constexpr int R = C::radix(P), G = C::groups(P);
+#pragma unroll
+  for (int i = 0; i < G; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+      buf[padi(pass_pos<LOGN, P>(t + i * C::T, j))] = v[i * R + j];
+}
+
+template <int LOGN, int P>
+__device__ __forceinline__ void load_pass(const float2* buf, float2* v, int t) {
+  using C = FusedCfg<LOGN>;
+  constexpr int R = C::radix(P), G = C::groups(P);
+#pragma unroll
+  for (int i = 0; i < G; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+      v[i * R + j] = buf[padi(pass_pos<LOGN, P>(t + i * C::T, j))];
+}
+
+// Twiddles after forward pass P (before inverse pass P): element j of group
+// gi gets W_{L_P}^{o j}, o = gi mod S_P, i.e. table entry (o j) * 16^P.
+template <int LOGN, int P, bool INV>
+__device__ __forceinline__ void twiddle_pass(float2* v0, float2* v1, int t,
+                                             const float4* __restrict__ tw) {
+  using C = FusedCfg<LOGN>;
+  constexpr int R = C::radix(P), G = C::groups(P), S = C::stride(P);
+#pragma unroll
+  for (int i = 0; i < G; ++i) {
+    const int o = (t + i * C::T) % S;
+#pragma unroll
+    for (int j = 1; j < R; ++j) {
+      const float4 w = __ldg(&tw[(o * j) << (4 * P)]);
+      v0[i * R + j] = mul_tw<INV>(v0[i * R + j], w);
+      v1[i * R + j] = mul_tw<INV>(v1[i * R + j], w);
+    }
+  }
+}
+
+template <int LOGN, int P, bool INV>
+__device__ __forceinline__ void dft_pass(float2* v0, float2* v1) {
+  using C = FusedCfg<LOGN>;
+  constexpr int R = C::radix(P), G = C::groups(P);
+#pragma unroll
+  for (int i = 0; i < G; ++i) {
+    dft<R, INV>(v0 + i * R);
+    dft<R, INV>(v1 + i * R);
+  }
+}
+
+// Forward middle pass P (1 <= P <= NP-2): load, DFT, twiddle, store.
+template <int LOGN, int P>
+__device__ __forceinline__ void fwd_mid(float2* b0, float2* b1, float2* v0,
+                                        float2* v1, int t, const float4* tw) {
+  load_pass<LOGN, P>(b0, v0, t);
+  load_pass<LOGN, P>(b1, v1, t);
+  dft_pass<LOGN, P, false>(v0, v1);
+  twiddle_pass<LOGN, P, false>(v0, v1, t, tw);
+  store_pass<LOGN, P>(b0, v0, t);
+  store_pass<LOGN, P>(b1, v1, t);
+  __syncthreads();
+}
+
+template <int LOGN, int P>
+__device__ __forceinline__ void inv_mid(float2* b0, float2* b1, float2* v0,
+                                        float2* v1, int t, const float4* tw) {
+  load_pass<LOGN, P>(b0, v0, t);
+  load_pass<LOGN, P>(b1, v1, t);
+  twiddle_pass<LOGN, P, true>(v0, v1, t, tw);
+  dft_pass<LOGN, P, true>(v0, v1);
+  store_pass<LOGN, P>(b0, v0, t);
+  store_pass<LOGN, P>(b1, v1, t);
+  __syncthreads();
+}
+
+// Last pass: forward DFT, propagator in delta form (x/N + x (P-1)/N), inverse.
+template <int LOGN>
+__device__ __forceinline__ void last_pass(float2* v0, float2* v1, int t,
+                                          const float2* __restrict__ prop) {
+  using C = FusedCfg<LOGN>;
+  constexpr int P = C::NP - 1, R = C::radix(P), G = C::groups(P);
+  constexpr float inv_n = 1.0f / float(C::N);
+  dft_pass<LOGN, P, false>(v0, v1);
+#pragma unroll
+  for (int i = 0; i < G; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int pos = pass_pos<LOGN, P>(t + i * C::T, j);
+      const float2 d0 = __ldg(&prop[pos]);
+      const float2 d1 = __ldg(&prop[C::N + pos]);
+      float2 x = v0[i * R + j];
+      v0[i * R + j] = make_float2(fmaf(x.x, inv_n, fmaf(x.x, d0.x, -(x.y * d0.y))),
+                                  fmaf(x.y, inv_n, fmaf(x.x, d0.y, x.y * d0.x)));
+      x = v1[i * R + j];
+      v1[i * R + j] = make_float2(fmaf(x.x, inv_n, fmaf(x.x, d1.x, -(x.y * d1.y))),
+                                  fmaf(x.y, inv_n, fmaf(x.x, d1.y, x.y * d1.x)));
+    }
+  dft_pass<LOGN, P, true>(v0, v1);
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(FusedCfg<LOGN>::THREADS)
+    fused_march_kernel(const RowDescF32* __restrict__ rows, int n_rows,
+                       int steps, const float4* __restrict__ tw,
+                       int* __restrict__ status) {
+  using C = FusedCfg<LOGN>;
+  constexpr int N = C::N, T = C::T, NP = C::NP, R0 = C::radix(0);
+  constexpr int G0 = C::groups(0), S0 = C::stride(0);
+  extern __shared__ __align__(128) unsigned char smem[];
+
+  const int rl = threadIdx.x / T;
+  const int t = threadIdx.x % T;
+  const int row = blockIdx.x * C::ROWS + rl;
+  const bool active = row < n_rows;
+  const RowDescF32 d = rows[active ? row : 0];
+
+  float2* b0 = reinterpret_cast<float2*>(smem + C::OFF_BUF) + rl * 2 * C::PADN;
+  float2* b1 = b0 + C::PADN;
+  float2* ph = reinterpret_cast<float2*>(smem + C::OFF_PH) + rl * N;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::OFF_MBAR) + rl;
+  float2* recph = reinterpret_cast<float2*>(smem + C::OFF_RECPH) + rl;
+  double* red = reinterpret_cast<double*>(smem + C::OFF_RED) + rl * C::WARPS_PER_ROW * 2;
+
+  if (t == 0) mbar_init(bar);
+  fence_mbar_init();
+
+  // Registers: pass-0 groups of both bands, natural positions gi + j*S0.
+  float2 v0[C::E], v1[C::E];
+#pragma unroll
+  for (int i = 0; i < G0; ++i)
+#pragma unroll
+    for (int j = 0; j < R0; ++j) {
+      const int pos = (t + i * T) + j * S0;
+      v0[i * R0 + j] = active ? d.state[pos] : make_float2(0.f, 0.f);
+      v1[i * R0 + j] = active ? d.state[N + pos] : make_float2(0.f, 0.f);
+    }
+  __syncthreads();
+
+  const uint32_t slice_bytes = uint32_t(N) * 8u;
+  int pending_slot = -1;            // record whose powers await reduction
+  bool timed_out = false;
+
+  for (int it = 0; it < steps; ++it) {
+    const int n = d.n_begin + it;
+    const bool rec = active && d.record_every > 0 &&
+                     ((n + 1) % d.record_every) == 0 &&
+                     (d.records != nullptr || d.powers != nullptr);
+    if (t == 0 && rec) {
+      // Common phase exp(i (n+1-n_phase0) dz^ cos(alpha)) in FP64, once per row.
+      double ang = fmod(double(n + 1 - d.n_phase0) * d.gphase, 6.283185307179586);
+      double sa, ca;
+      sincos(ang, &sa, &ca);
+      *recph = make_float2(float(ca), float(sa));
+    }
+
+    if constexpr (NP == 1) {
+      if (t == 0 && active) bulk_load(ph, d.phasor + size_t(n) * N, slice_bytes, bar);
+      last_pass<LOGN>(v0, v1, t, d.prop);
+    } else {
+      // forward pass 0: DFT + twiddle, to shared memory
+      dft_pass<LOGN, 0, false>(v0, v1);
+      twiddle_pass<LOGN, 0, false>(v0, v1, t, tw);
+      store_pass<LOGN, 0>(b0, v0, t);
+      store_pass<LOGN, 0>(b1, v1, t);
+      __syncthreads();
+      // every thread of the row has finished the previous step's coupling:
+      // the slice buffer is free for this step's copy.
+      if (t == 0 && active) bulk_load(ph, d.phasor + size_t(n) * N, slice_bytes, bar);
+      if (t == 0 && pending_slot >= 0) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int w = 0; w < C::WARPS_PER_ROW; ++w) {
+          s0 += red[2 * w];
+          s1 += red[2 * w + 1];
+        }
+        d.powers[2 * pending_slot] = s0 * d.dx_um;
+        d.powers[2 * pending_slot + 1] = s1 * d.dx_um;
+        pending_slot = -1;
+      }
+      if constexpr (NP >= 3) fwd_mid<LOGN, 1>(b0, b1, v0, v1, t, tw);
+      if constexpr (NP >= 4) fwd_mid<LOGN, 2>(b0, b1, v0, v1, t, tw);
+      load_pass<LOGN, NP - 1>(b0, v0, t);
+      load_pass<LOGN, NP - 1>(b1, v1, t);
+      last_pass<LOGN>(v0, v1, t, d.prop);
+      store_pass<LOGN, NP - 1>(b0, v0, t);
+      store_pass<LOGN, NP - 1>(b1, v1, t);
+      __syncthreads();
+      if constexpr (NP >= 4) inv_mid<LOGN, 2>(b0, b1, v0, v1, t, tw);
+      if constexpr (NP >= 3) inv_mid<LOGN, 1>(b0, b1, v0, v1, t, tw);
+      load_pass<LOGN, 0>(b0, v0, t);
+      load_pass<LOGN, 0>(b1, v1, t);
+      twiddle_pass<LOGN, 0, true>(v0, v1, t, tw);
+      dft_pass<LOGN, 0, true>(v0, v1);
+    }
+
+    // ---- coupling through chi_0, chi_h, the strain phase and the mask ----
+    if (active) {
+      if (!mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
+      const float2 am1 = d.am1, bb = d.b;
+#pragma unroll
+      for (int i = 0; i < G0; ++i)
+#pragma unroll
+        for (int j = 0; j < R0; ++j) {
+          const int pos = (t + i * T) + j * S0;
+          const float2 e = ph[pos];
+          const bool inside = (e.x != 0.f) | (e.y != 0.f);
+          const float ax = inside ? am1.x : 0.f, ay = inside ? am1.y : 0.f;
+          // b e and b conj(e)
+          const float2 bp = make_float2(fmaf(bb.x, e.x, -(bb.y * e.y)),
+                                        fmaf(bb.x, e.y, bb.y * e.x));
+          const float2 bm = make_float2(fmaf(bb.x, e.x, bb.y * e.y),
+                                        fmaf(bb.y, e.x, -(bb.x * e.y)));
+          const float2 p = v0[i * R0 + j], m = v1[i * R0 + j];
+          float px = fmaf(ax, p.x, p.x);
+          px = fmaf(-ay, p.y, px);
+          px = fmaf(bp.x, m.x, px);
+          px = fmaf(-bp.y, m.y, px);
+          float py = fmaf(ax, p.y, p.y);
+          py = fmaf(ay, p.x, py);
+          py = fmaf(bp.x, m.y, py);
+          py = fmaf(bp.y, m.x, py);
+          float mx = fmaf(ax, m.x, m.x);
+          mx = fmaf(-ay, m.y, mx);
+          mx = fmaf(bm.x, p.x, mx);
+          mx = fmaf(-bm.y, p.y, mx);
+          float my = fmaf(ax, m.y, m.y);
+          my = fmaf(ay, m.x, my);
+          my = fmaf(bm.x, p.y, my);
+          my = fmaf(bm.y, p.x, my);
+          v0[i * R0 + j] = make_float2(px, py);
+          v1[i * R0 + j] = make_float2(mx, my);
+        }
+    }
+
+    // ---- record: coalesced write of psi * g^k, band powers ----------------
+    const bool want_pw = rec && d.powers != nullptr;
+    const int slot = rec ? (n + 1) / d.record_every - 1 : 0;
+    float s0 = 0.f, s1 = 0.f;
+    if (rec) {
+      const float2 g = *recph;
+      float2* r0 = d.records ? d.records + size_t(slot) * 2 * N : nullptr;
+#pragma unroll
+      for (int i = 0; i < G0; ++i)
+#pragma unroll
+        for (int j = 0; j < R0; ++j) {
+          const int pos = (t + i * T) + j * S0;
+          const float2 p = v0[i * R0 + j], m = v1[i * R0 + j];
+          s0 = fmaf(p.x, p.x, fmaf(p.y, p.y, s0));
+          s1 = fmaf(m.x, m.x, fmaf(m.y, m.y, s1));
+          if (r0) {
+            r0[pos] = make_float2(fmaf(p.x, g.x, -(p.y * g.y)), fmaf(p.x, g.y, p.y * g.x));
+            r0[N + pos] = make_float2(fmaf(m.x, g.x, -(m.y * g.y)), fmaf(m.x, g.y, m.y * g.x));
+          }
+        }
+    }
+    if constexpr (NP == 1) {
+      if (want_pw) {
+        d.powers[2 * slot] = double(s0) * d.dx_um;
+        d.powers[2 * slot + 1] = double(s1) * d.dx_um;
+      }
+    } else {
+      // All lanes of the warp take part in the shuffles (rows that share a
+      // warp may record on different steps); offsets stay inside a row.
+      constexpr int LANES = T < 32 ? T : 32;
+      if (__any_sync(0xffffffffu, want_pw)) {
+        double ds0 = s0, ds1 = s1;
+#pragma unroll
+        for (int off = LANES / 2; off > 0; off >>= 1) {
+          ds0 += __shfl_xor_sync(0xffffffffu, ds0, off);
+          ds1 += __shfl_xor_sync(0xffffffffu, ds1, off);
+        }
+        if (want_pw) {
+          if ((t & (LANES - 1)) == 0) {
+            red[2 * (t / 32)] = ds0;
+            red[2 * (t / 32) + 1] = ds1;
+          }
+          if (t == 0) pending_slot = slot;
+        }
+      }
+    }
+  }
+
+  __syncthreads();
+  if (t == 0 && pending_slot >= 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int w = 0; w < C::WARPS_PER_ROW; ++w) {
+      s0 += red[2 * w];
+      s1 += red[2 * w + 1];
+    }
+    d.powers[2 * pending_slot] = s0 * d.dx_um;
+    d.powers[2 * pending_slot + 1] = s1 * d.dx_um;
+  }
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < G0; ++i)
+#pragma unroll
+      for (int j = 0; j < R0; ++j) {
+        const int pos = (t + i * T) + j * S0;
+        d.state[pos] = v0[i * R0 + j];
+        d.state[N + pos] = v1[i * R0 + j];
+      }
+  }
+  if (timed_out && t == 0) atomicOr(status, kStatusWaitTimeout);
+}
+
+}  // namespace bpm

@@ -1,0 +1,220 @@
+// Plain per-step FP64 march: the same step as the fused path (Eq. fov10 of
+// arXiv 2601.06340), written the straightforward way with complex128 fields
+// in global memory and one kernel launch per FFT pass and per pointwise
+// operation:
+//   forward Stockham passes (radix 4, plus one radix-2 pass for odd log2 N)
+//   -> propagator multiply P(q)/N (natural order) -> inverse passes
+//   -> real-space coupling with the strain phasor and mask -> [record].
+// It is the FP64 reference form on the GPU and the baseline the fused FP32
+// kernel is measured against.
+#include <vector>
+
+#include "bpm_internal.h"
+
+namespace bpm {
+
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) {
+  return make_double2(a.x + b.x, a.y + b.y);
+}
+__device__ __forceinline__ double2 csub(double2 a, double2 b) {
+  return make_double2(a.x - b.x, a.y - b.y);
+}
+
+// One Stockham autosort pass of radix R over `lines` independent transforms
+// of length n: sub-transforms of length ns are combined into length ns*R.
+template <int R, bool INV>
+__global__ void stockham_pass(const double2* __restrict__ in, double2* __restrict__ out,
+                              int n, int ns, int lines, const double2* __restrict__ tw) {
+  const int per_line = n / R;
+  const long total = long(lines) * per_line;
+  for (long g = blockIdx.x * long(blockDim.x) + threadIdx.x; g < total;
+       g += long(gridDim.x) * blockDim.x) {
+    const int line = int(g / per_line), j = int(g % per_line);
+    const double2* src = in + size_t(line) * n;
+    double2* dst = out + size_t(line) * n;
+    const int k = j % ns;
+    double2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[j + r * per_line];
+    // twiddle W_{ns R}^{r k} = table[r k n / (ns R)]
+    const int step = n / (ns * R);
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      double2 w = tw[r * k * step];
+      if (INV) w.y = -w.y;
+      v[r] = cmul(v[r], w);
+    }
+    if (R == 2) {
+      double2 a = v[0], b = v[1];
+      v[0] = cadd(a, b);
+      v[1] = csub(a, b);
+    } else {
+      double2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+      double2 t2 = cadd(v[1], v[3]), t3 = csub(v[1], v[3]);
+      t3 = INV ? make_double2(-t3.y, t3.x) : make_double2(t3.y, -t3.x);
+      v[0] = cadd(t0, t2);
+      v[2] = csub(t0, t2);
+      v[1] = cadd(t1, t3);
+      v[3] = csub(t1, t3);
+    }
+    const int base = (j / ns) * ns * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[base + r * ns] = v[r];
+  }
+}
+
+// x[row][band][m] *= P_band(q_m) / N
+__global__ void prop_kernel(double2* __restrict__ x, const RowDescF64* __restrict__ rows,
+                            int n, int nb) {
+  const long total = long(nb) * 2 * n;
+  for (long c = blockIdx.x * long(blockDim.x) + threadIdx.x; c < total;
+       c += long(gridDim.x) * blockDim.x) {
+    const int row = int(c / (2 * n));
+    const int rem = int(c % (2 * n));   // band * n + m
+    x[c] = cmul(x[c], rows[row].prop[rem]);
+  }
+}
+
+// Coupling of Eq. fov10 inside the crystal (phasor != 0).
+__global__ void couple_kernel(double2* __restrict__ x, const RowDescF64* __restrict__ rows,
+                              const double2* __restrict__ phasor_row, int n, int nb) {
+  const long total = long(nb) * n;
+  for (long c = blockIdx.x * long(blockDim.x) + threadIdx.x; c < total;
+       c += long(gridDim.x) * blockDim.x) {
+    const int row = int(c / n), j = int(c % n);
+    const double2 e = phasor_row[j];
+    if (e.x == 0.0 && e.y == 0.0) continue;
+    double2* xr = x + size_t(row) * 2 * n;
+    const double2 p = xr[j], m = xr[n + j];
+    const double2 a = rows[row].a, b = rows[row].b;
+    const double2 be = cmul(b, e), bc = cmul(b, make_double2(e.x, -e.y));
+    xr[j] = cadd(cmul(a, p), cmul(be, m));
+    xr[n + j] = cadd(cmul(a, m), cmul(bc, p));
+  }
+}
+
+// Block-wide FP64 sum of |x|^2 over one (row, band) line, fixed order.
+__device__ double line_power(const double2* x, int n) {
+  __shared__ double part[32];
+  double s = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) s += x[j].x * x[j].x + x[j].y * x[j].y;
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double tot = 0.0;
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) tot += part[w];
+  }
+  __syncthreads();
+  return tot;
+}
+
+// Record slot `slot`: records[row][slot][band][:] = x * g^k, powers.
+__global__ void record_kernel(const double2* __restrict__ x, double2* __restrict__ rec,
+                              double* __restrict__ pw, const double2* __restrict__ gk,
+                              int n, int n_rec, int slot, double dx) {
+  const int row = blockIdx.x >> 1, band = blockIdx.x & 1;
+  const double2* src = x + (size_t(row) * 2 + band) * n;
+  const double2 g = gk[row];
+  if (rec) {
+    double2* dst = rec + ((size_t(row) * n_rec + slot) * 2 + band) * n;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) dst[j] = cmul(src[j], g);
+  }
+  if (pw) {
+    double tot = line_power(src, n);
+    if (threadIdx.x == 0) pw[(size_t(row) * (n_rec + 1) + slot) * 2 + band] = tot * dx;
+  }
+}
+
+int grid_for(long work, int threads) {
+  long b = (work + threads - 1) / threads;
+  return int(b < 32768 ? (b > 0 ? b : 1) : 32768);
+}
+
+}  // namespace
+
+// x: current buffer (state), y: scratch; returns the buffer holding the result.
+static double2* fft_lines(double2* x, double2* y, int logn, int lines, const double2* tw,
+                          bool inv, cudaStream_t st) {
+  const int n = 1 << logn;
+  int ns = 1;
+  const int threads = 256;
+  if (logn & 1) {
+    const int g = grid_for(long(lines) * n / 2, threads);
+    if (inv) stockham_pass<2, true><<<g, threads, 0, st>>>(x, y, n, ns, lines, tw);
+    else stockham_pass<2, false><<<g, threads, 0, st>>>(x, y, n, ns, lines, tw);
+    std::swap(x, y);
+    ns *= 2;
+  }
+  while (ns < n) {
+    const int g = grid_for(long(lines) * n / 4, threads);
+    if (inv) stockham_pass<4, true><<<g, threads, 0, st>>>(x, y, n, ns, lines, tw);
+    else stockham_pass<4, false><<<g, threads, 0, st>>>(x, y, n, ns, lines, tw);
+    std::swap(x, y);
+    ns *= 4;
+  }
+  return x;
+}
+
+// March the plan's state (d_state, c128 [B][2][N]) from n_begin to n_end.
+// d_records: c128 [B][n_rec][2][N] or null; d_powers: [B][n_rec+1][2] or null.
+// Records carry the common phase g^k with k = steps since n_phase0 (the step
+// at which the state had phase 0);
+// the returned state in d_state is raw (caller applies g^(n_end-n_begin)).
+int plain_march(bpm_plan_s* plan, int n_begin, int n_end, int n_phase0, void* d_records,
+                double* d_powers, cudaStream_t st) {
+  const int n = plan->nx, nb = plan->nb, logn = plan->logn;
+  const int lines = 2 * nb;
+  const double2* tw = static_cast<const double2*>(plan->d_tw);
+  const RowDescF64* rows = static_cast<const RowDescF64*>(plan->d_rows);
+  double2* x = static_cast<double2*>(plan->d_state);
+  double2* y = static_cast<double2*>(plan->d_state2);
+  const double2* phasor = static_cast<const double2*>(plan->d_phasor);
+  const int threads = 256;
+
+  // Per-record common phases g^k (host FP64, uploaded once per record slot).
+  std::vector<double2> gk(nb);
+  double2* d_gk = nullptr;
+  const bool any_rec = plan->record_every > 0 && (d_records || d_powers);
+  if (any_rec) {
+    cudaError_t e = cudaMallocAsync(&d_gk, sizeof(double2) * nb * 2, st);
+    if (e != cudaSuccess) return cuda_fail(e, "plain march: phase buffer");
+  }
+  int slot_toggle = 0;
+  for (int s = n_begin; s < n_end; ++s) {
+    double2* r = fft_lines(x, y, logn, lines, tw, false, st);
+    if (r != x) std::swap(x, y);
+    prop_kernel<<<grid_for(long(lines) * n, threads), threads, 0, st>>>(x, rows, n, nb);
+    r = fft_lines(x, y, logn, lines, tw, true, st);
+    if (r != x) std::swap(x, y);
+    couple_kernel<<<grid_for(long(nb) * n, threads), threads, 0, st>>>(
+        x, rows, phasor + size_t(s) * n, n, nb);
+    if (any_rec && (s + 1) % plan->record_every == 0) {
+      const int slot = (s + 1) / plan->record_every - 1;
+      for (int row = 0; row < nb; ++row) {
+        double ang = std::fmod(double(s + 1 - n_phase0) * plan->ec[row].gphase, kTwoPi);
+        gk[row] = make_double2(std::cos(ang), std::sin(ang));
+      }
+      double2* dg = d_gk + slot_toggle * nb;   // two halves so the async copy never races a reader
+      slot_toggle ^= 1;
+      cudaMemcpyAsync(dg, gk.data(), sizeof(double2) * nb, cudaMemcpyHostToDevice, st);
+      record_kernel<<<2 * nb, 256, 0, st>>>(x, static_cast<double2*>(d_records), d_powers, dg,
+                                            n, plan->n_rec, slot, plan->dx_um);
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  if (d_gk) cudaFreeAsync(d_gk, st);
+  if (e != cudaSuccess) return cuda_fail(e, "plain march launch");
+  if (x != static_cast<double2*>(plan->d_state)) {
+    // the result ended in the scratch buffer: swap ownership
+    std::swap(plan->d_state, plan->d_state2);
+  }
+  return BPM_OK;
+}
+
+}  // namespace bpm

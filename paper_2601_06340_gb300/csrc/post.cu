@@ -1,0 +1,151 @@
+// Input conversion, output finishing (common phase, final powers) and the
+// energy -> time synthesis of a batch of exit fields.
+#include "bpm_internal.h"
+
+namespace bpm {
+
+namespace {
+
+__global__ void convert_in_kernel(const double2* __restrict__ src, float2* __restrict__ dst,
+                                  size_t n) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x)
+    dst[i] = make_float2(float(src[i].x), float(src[i].y));
+}
+
+// One block per (row, band): out = state * g_row (FP64 product), power of
+// the line in FP64 (fixed summation order).
+template <typename TIn>
+__global__ void finish_kernel(const TIn* __restrict__ state, double2* __restrict__ out128,
+                              float2* __restrict__ out64, const double2* __restrict__ g,
+                              int nx, double dx, double* __restrict__ pw, int pw_stride) {
+  __shared__ double part[32];
+  const int row = blockIdx.x >> 1, band = blockIdx.x & 1;
+  const size_t base = (size_t(row) * 2 + band) * nx;
+  const double2 gr = g[row];
+  double s = 0.0;
+  for (int j = threadIdx.x; j < nx; j += blockDim.x) {
+    const double vx = double(state[base + j].x), vy = double(state[base + j].y);
+    s += vx * vx + vy * vy;
+    const double ox = vx * gr.x - vy * gr.y, oy = vx * gr.y + vy * gr.x;
+    if (out128) out128[base + j] = make_double2(ox, oy);
+    if (out64) out64[base + j] = make_float2(float(ox), float(oy));
+  }
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0 && pw) {
+    double tot = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) tot += part[w];
+    pw[size_t(row) * pw_stride + band] = tot * dx;
+  }
+}
+
+// Energy -> time: for each (band, x) line, out[band][x][m] =
+// (1/B) sum_j in[j][band][x] exp(+2 pi i j m / B), by a radix-2 Stockham
+// transform in shared memory.  A block handles `tx` consecutive x of one band.
+template <typename C, typename R>
+__global__ void omega_to_t_kernel(const C* __restrict__ in, C* __restrict__ out, int nb,
+                                  int logb, int nx, int tx) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  C* a = reinterpret_cast<C*>(sm);
+  C* b = a + size_t(tx) * nb;
+  const int band = blockIdx.y;
+  const int x0 = blockIdx.x * tx;
+  // load [nb][tx] -> a[xi][j]
+  for (int c = threadIdx.x; c < nb * tx; c += blockDim.x) {
+    const int j = c / tx, xi = c % tx;
+    a[xi * nb + j] = in[(size_t(j) * 2 + band) * nx + x0 + xi];
+  }
+  __syncthreads();
+  const int half = nb >> 1;
+  for (int ns = 1; ns < nb; ns <<= 1) {
+    for (int c = threadIdx.x; c < half * tx; c += blockDim.x) {
+      const int xi = c / half, j = c % half;
+      const int k = j % ns;
+      const C u = a[xi * nb + j];
+      C v = a[xi * nb + j + half];
+      // w = exp(+i pi k / ns)
+      R sw, cw;
+      if constexpr (sizeof(R) == 8) sincospi(double(k) / double(ns), &sw, &cw);
+      else sincospif(float(k) / float(ns), &sw, &cw);
+      v = C{v.x * cw - v.y * sw, v.x * sw + v.y * cw};
+      const int base = (j / ns) * ns * 2 + k;
+      b[xi * nb + base] = C{u.x + v.x, u.y + v.y};
+      b[xi * nb + base + ns] = C{u.x - v.x, u.y - v.y};
+    }
+    __syncthreads();
+    C* t = a;
+    a = b;
+    b = t;
+  }
+  const R scale = R(1) / R(nb);
+  for (int c = threadIdx.x; c < nb * tx; c += blockDim.x) {
+    const int xi = c / nb, m = c % nb;
+    const C v = a[xi * nb + m];
+    out[(size_t(band) * nx + x0 + xi) * nb + m] = C{v.x * scale, v.y * scale};
+  }
+}
+
+}  // namespace
+
+int launch_convert_in(const double2* src, float2* dst, size_t n, cudaStream_t st) {
+  const int threads = 256;
+  size_t blocks = (n + threads - 1) / threads;
+  if (blocks > 65536) blocks = 65536;
+  convert_in_kernel<<<int(blocks), threads, 0, st>>>(src, dst, n);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? BPM_OK : cuda_fail(e, "convert input");
+}
+
+int launch_finish_f32(const float2* state, double2* out_c128, float2* out_c64,
+                      const double* g, int n_rows, int nx, int /*steps*/, double dx,
+                      double* final_powers, int power_stride, cudaStream_t st) {
+  finish_kernel<float2><<<2 * n_rows, 256, 0, st>>>(state, out_c128, out_c64,
+                                                    reinterpret_cast<const double2*>(g), nx, dx,
+                                                    final_powers, power_stride);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? BPM_OK : cuda_fail(e, "finish (fp32)");
+}
+
+int launch_finish_f64(const double2* state, double2* out, const double* g, int n_rows, int nx,
+                      int /*steps*/, double dx, double* final_powers, int power_stride,
+                      cudaStream_t st) {
+  finish_kernel<double2><<<2 * n_rows, 256, 0, st>>>(state, out, nullptr,
+                                                     reinterpret_cast<const double2*>(g), nx, dx,
+                                                     final_powers, power_stride);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? BPM_OK : cuda_fail(e, "finish (fp64)");
+}
+
+int launch_omega_to_t(const void* d_in, void* d_out, int nb, int nx, int precision,
+                      cudaStream_t st) {
+  int logb = 0;
+  while ((1 << logb) < nb) ++logb;
+  const size_t csize = precision == BPM_FP32_FUSED ? 8 : 16;
+  int tx = 1;
+  while (tx < 16 && size_t(tx) * 2 * nb * 2 * csize <= 96 * 1024 && (nx % (tx * 2)) == 0) tx *= 2;
+  const size_t smem = size_t(tx) * nb * 2 * csize;
+  dim3 grid(nx / tx, 2);
+  cudaError_t e;
+  if (precision == BPM_FP32_FUSED) {
+    auto k = omega_to_t_kernel<float2, float>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e == cudaSuccess) {
+      k<<<grid, 256, smem, st>>>(static_cast<const float2*>(d_in), static_cast<float2*>(d_out),
+                                 nb, logb, nx, tx);
+      e = cudaGetLastError();
+    }
+  } else {
+    auto k = omega_to_t_kernel<double2, double>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e == cudaSuccess) {
+      k<<<grid, 256, smem, st>>>(static_cast<const double2*>(d_in), static_cast<double2*>(d_out),
+                                 nb, logb, nx, tx);
+      e = cudaGetLastError();
+    }
+  }
+  return e == cudaSuccess ? BPM_OK : cuda_fail(e, "omega_to_t");
+}
+
+}  // namespace bpm

@@ -1,0 +1,456 @@
+// Continuous-batching request server (bpm_submit / bpm_poll).
+//
+// A worker thread owns the device side.  Each loop iteration it
+//   1. admits queued requests in arrival order while the number of active
+//      requests and their device footprint stay within the configured
+//      limits (footprint = the request's state, records, powers and, if the
+//      plan has none yet, its strain-phasor stream);
+//   2. advances every active request by up to `epoch_steps` z-steps: rows
+//      of all active FP32 requests with the same transform size and the
+//      same step count in this epoch share one fused launch (one stream per
+//      transform size, so sizes overlap on the device); FP64 requests run
+//      their plain per-step march;
+//   3. retires finished requests: common phase, conversion to c128, copies
+//      to the caller's buffers, wake-up of pollers.
+// Requests that arrive while others run join at the next epoch boundary.
+// A request's arithmetic does not depend on which other requests share its
+// launches (rows are independent and each row's work is the same code for
+// the same shape), so a result is the same alone and in the mix.
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "bpm_internal.h"
+
+namespace bpm {
+
+// from capi.cpp
+void fused_rows(bpm_plan_s* plan, float2* state, float2* rec, double* pw, int n_begin, int n_end,
+                std::vector<RowDescF32>* out);
+void phase_factors(const bpm_plan_s* plan, int steps, std::vector<double2>* out);
+
+namespace {
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+  bpm_ticket_t id = 0;
+  bpm_plan_s* plan = nullptr;
+  std::vector<double> psi_in;
+  double* psi_out = nullptr;
+  void* records = nullptr;
+  double* powers = nullptr;
+  int status = BPM_NOT_READY;
+  std::string error;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  // device side
+  size_t footprint = 0;
+  bool owns_phasor = false;
+  void* d_state = nullptr;     // c64 (FP32) or unused (FP64 uses the plan's state)
+  void* d_rec = nullptr;
+  double* d_pow = nullptr;
+  double2* d_g = nullptr;
+  double2* d_out = nullptr;    // c128 staging
+  int n_done = 0;
+};
+
+struct Server {
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<std::shared_ptr<Request>> queue;
+  std::vector<std::shared_ptr<Request>> active;
+  std::unordered_map<bpm_ticket_t, std::shared_ptr<Request>> tickets;
+  std::map<bpm_ticket_t, std::array<double, 3>> times;
+  bpm_ticket_t next_id = 1;
+  double mem_fraction = 0.6;
+  int max_active = 256, epoch_steps = 256, max_queue = 100000;
+  size_t budget = 0, used = 0;
+  bool started = false;
+  std::thread worker;
+  std::map<int, cudaStream_t> streams;   // per transform size
+  cudaStream_t io_stream = nullptr;
+  RowDescF32* d_rows = nullptr;
+  size_t d_rows_cap = 0;
+  int* d_status = nullptr;
+  float4* d_tw[kMaxLogN + 1] = {};
+
+  ~Server() {
+    // The worker is detached at process exit; nothing to join here.
+  }
+};
+
+Server& srv() {
+  static Server* s = new Server();   // never destroyed: the worker may outlive main()
+  return *s;
+}
+
+size_t csize_of(const bpm_plan_s* p) { return p->precision == BPM_FP32_FUSED ? 8 : 16; }
+
+size_t footprint_of(const bpm_plan_s* p, bool need_rec) {
+  const size_t n = p->nx, nb = p->nb, cs = csize_of(p);
+  size_t b = nb * 2 * n * cs                       // state
+             + nb * 2 * n * 16                     // c128 output staging
+             + nb * size_t(p->n_rec + 1) * 2 * 8   // powers
+             + nb * 16;                            // phase factors
+  if (need_rec) b += nb * size_t(p->n_rec) * 2 * n * cs;
+  if (!p->d_phasor) b += size_t(p->nz) * n * cs;
+  return b;
+}
+
+void release(Request& r) {
+  if (r.d_state) cudaFree(r.d_state);
+  if (r.d_rec) cudaFree(r.d_rec);
+  if (r.d_pow) cudaFree(r.d_pow);
+  if (r.d_g) cudaFree(r.d_g);
+  if (r.d_out) cudaFree(r.d_out);
+  r.d_state = r.d_rec = nullptr;
+  r.d_pow = nullptr;
+  r.d_g = r.d_out = nullptr;
+}
+
+// Allocate and stage a request; runs on the worker with srv().mu released.
+int admit_device(Server& s, Request& r) {
+  bpm_plan_s* p = r.plan;
+  const size_t n = p->nx, nb = p->nb, cs = csize_of(p);
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** ptr, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+  };
+  {
+    std::lock_guard<std::mutex> lk(p->mu);
+    if (!p->d_phasor) {
+      A(&p->d_phasor, size_t(p->nz) * n * cs);
+      r.owns_phasor = (e == cudaSuccess);
+      p->slices_dirty = true;
+    }
+    if (e == cudaSuccess && p->slices_dirty) {
+      int rc = prepare_slices(p, s.io_stream);
+      if (rc != BPM_OK) return rc;
+    }
+  }
+  if (p->precision == BPM_FP32_FUSED) A(&r.d_state, nb * 2 * n * cs);
+  if (r.records && p->n_rec > 0) A(&r.d_rec, nb * size_t(p->n_rec) * 2 * n * cs);
+  A(reinterpret_cast<void**>(&r.d_pow), nb * size_t(p->n_rec + 1) * 2 * 8);
+  A(reinterpret_cast<void**>(&r.d_g), nb * 16);
+  A(reinterpret_cast<void**>(&r.d_out), nb * 2 * n * 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? BPM_ERR_OOM : BPM_ERR_CUDA;
+  }
+  e = cudaMemcpyAsync(r.d_out, r.psi_in.data(), nb * 2 * n * 16, cudaMemcpyHostToDevice, s.io_stream);
+  if (e != cudaSuccess) return BPM_ERR_CUDA;
+  if (p->precision == BPM_FP32_FUSED) {
+    int rc = launch_convert_in(r.d_out, static_cast<float2*>(r.d_state), nb * 2 * n, s.io_stream);
+    if (rc != BPM_OK) return rc;
+  } else {
+    e = cudaMemcpyAsync(p->d_state, r.d_out, nb * 2 * n * 16, cudaMemcpyDeviceToDevice, s.io_stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s.io_stream);
+  return e == cudaSuccess ? BPM_OK : BPM_ERR_CUDA;
+}
+
+int retire_device(Server& s, Request& r) {
+  bpm_plan_s* p = r.plan;
+  const size_t n = p->nx, nb = p->nb, cs = csize_of(p);
+  std::vector<double2> g;
+  phase_factors(p, p->nz, &g);
+  cudaStream_t st = s.io_stream;
+  cudaError_t e = cudaMemcpyAsync(r.d_g, g.data(), nb * 16, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return BPM_ERR_CUDA;
+  const int pw_stride = 2 * (p->n_rec + 1);
+  int rc;
+  if (p->precision == BPM_FP32_FUSED)
+    rc = launch_finish_f32(static_cast<const float2*>(r.d_state), r.d_out, nullptr,
+                           reinterpret_cast<const double*>(r.d_g), p->nb, p->nx, p->nz, p->dx_um,
+                           r.d_pow + 2 * p->n_rec, pw_stride, st);
+  else
+    rc = launch_finish_f64(static_cast<const double2*>(p->d_state), r.d_out,
+                           reinterpret_cast<const double*>(r.d_g), p->nb, p->nx, p->nz, p->dx_um,
+                           r.d_pow + 2 * p->n_rec, pw_stride, st);
+  if (rc != BPM_OK) return rc;
+  e = cudaMemcpyAsync(r.psi_out, r.d_out, nb * 2 * n * 16, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && r.d_rec)
+    e = cudaMemcpyAsync(r.records, r.d_rec, nb * size_t(p->n_rec) * 2 * n * cs,
+                        cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && r.powers)
+    e = cudaMemcpyAsync(r.powers, r.d_pow, nb * size_t(p->n_rec + 1) * 2 * 8,
+                        cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return BPM_ERR_CUDA;
+  if (r.powers)
+    for (size_t i = 0; i < nb * size_t(p->n_rec + 1) * 2; ++i)
+      if (!std::isfinite(r.powers[i])) return BPM_ERR_NUMERIC;
+  return BPM_OK;
+}
+
+void finish_request(Server& s, std::shared_ptr<Request> r, int status, const std::string& msg) {
+  release(*r);
+  {
+    std::lock_guard<std::mutex> lk(r->plan->mu);
+    if (r->owns_phasor) {
+      cudaFree(r->plan->d_phasor);
+      r->plan->d_phasor = nullptr;
+      r->plan->slices_dirty = true;
+    }
+    r->plan->pending -= 1;
+  }
+  std::lock_guard<std::mutex> lk(s.mu);
+  s.used -= r->footprint;
+  r->status = status;
+  r->error = msg;
+  r->t_done = now_s();
+  s.times[r->id] = {r->t_submit, r->t_admit, r->t_done};
+  s.cv_done.notify_all();
+}
+
+cudaStream_t stream_for(Server& s, int logn) {
+  auto it = s.streams.find(logn);
+  if (it != s.streams.end()) return it->second;
+  cudaStream_t st;
+  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  s.streams[logn] = st;
+  return st;
+}
+
+void worker_loop() {
+  Server& s = srv();
+  std::vector<RowDescF32> rows;
+  for (;;) {
+    std::vector<std::shared_ptr<Request>> admitted;
+    {
+      std::unique_lock<std::mutex> lk(s.mu);
+      s.cv_work.wait(lk, [&] { return !s.queue.empty() || !s.active.empty(); });
+      while (!s.queue.empty() && int(s.active.size() + admitted.size()) < s.max_active) {
+        auto r = s.queue.front();
+        if (s.used + r->footprint > s.budget) break;   // arrival order: wait for memory
+        s.queue.pop_front();
+        s.used += r->footprint;
+        admitted.push_back(r);
+      }
+    }
+    for (auto& r : admitted) {
+      r->t_admit = now_s();
+      int rc = admit_device(s, *r);
+      if (rc != BPM_OK) {
+        finish_request(s, r, rc, "admission failed on the device");
+        continue;
+      }
+      std::lock_guard<std::mutex> lk(s.mu);
+      s.active.push_back(r);
+    }
+    std::vector<std::shared_ptr<Request>> act;
+    {
+      std::lock_guard<std::mutex> lk(s.mu);
+      act = s.active;
+    }
+    if (act.empty()) continue;
+
+    // ---- one epoch: group FP32 rows by (transform size, steps this epoch)
+    std::map<std::pair<int, int>, std::vector<RowDescF32>> groups;
+    std::vector<std::shared_ptr<Request>> plain;
+    for (auto& r : act) {
+      bpm_plan_s* p = r->plan;
+      const int steps = std::min(s.epoch_steps, p->nz - r->n_done);
+      if (p->precision != BPM_FP32_FUSED) {
+        plain.push_back(r);
+        continue;
+      }
+      fused_rows(p, static_cast<float2*>(r->d_state), static_cast<float2*>(r->d_rec), r->d_pow,
+                 r->n_done, r->n_done + steps, &rows);
+      for (auto& d : rows) d.n_phase0 = 0;
+      auto& g = groups[{p->logn, steps}];
+      g.insert(g.end(), rows.begin(), rows.end());
+    }
+    size_t total_rows = 0;
+    for (auto& kv : groups) total_rows += kv.second.size();
+    int err = BPM_OK;
+    if (total_rows > s.d_rows_cap) {
+      if (s.d_rows) cudaFree(s.d_rows);
+      s.d_rows_cap = std::max<size_t>(total_rows * 2, 1024);
+      if (cudaMalloc(&s.d_rows, s.d_rows_cap * sizeof(RowDescF32)) != cudaSuccess) {
+        s.d_rows = nullptr;
+        s.d_rows_cap = 0;
+        err = BPM_ERR_OOM;
+      }
+    }
+    size_t off = 0;
+    for (auto& kv : groups) {
+      if (err != BPM_OK) break;
+      const int logn = kv.first.first, steps = kv.first.second;
+      cudaStream_t st = stream_for(s, logn);
+      auto& v = kv.second;
+      if (!s.d_tw[logn]) {
+        std::vector<float4> tw;
+        twiddle_table_f32(1 << logn, &tw);
+        cudaMalloc(&s.d_tw[logn], tw.size() * sizeof(float4));
+        cudaMemcpy(s.d_tw[logn], tw.data(), tw.size() * sizeof(float4), cudaMemcpyHostToDevice);
+      }
+      cudaMemcpyAsync(s.d_rows + off, v.data(), v.size() * sizeof(RowDescF32),
+                      cudaMemcpyHostToDevice, st);
+      err = launch_fused(logn, s.d_rows + off, int(v.size()), steps, s.d_tw[logn], s.d_status, st);
+      off += v.size();
+    }
+    for (auto& r : plain) {
+      if (err != BPM_OK) break;
+      bpm_plan_s* p = r->plan;
+      const int steps = std::min(s.epoch_steps, p->nz - r->n_done);
+      std::lock_guard<std::mutex> lk(p->mu);
+      err = plain_march(p, r->n_done, r->n_done + steps, 0, r->d_rec, r->d_pow, s.io_stream);
+    }
+    for (auto& kv : s.streams) cudaStreamSynchronize(kv.second);
+    cudaStreamSynchronize(s.io_stream);
+    int status = 0;
+    cudaMemcpy(&status, s.d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (status) {
+      cudaMemset(s.d_status, 0, sizeof(int));
+      err = BPM_ERR_TIMEOUT;
+    }
+    cudaError_t ce = cudaGetLastError();
+    if (err == BPM_OK && ce != cudaSuccess) err = BPM_ERR_CUDA;
+
+    // ---- advance and retire
+    std::vector<std::shared_ptr<Request>> done;
+    for (auto& r : act) {
+      r->n_done += std::min(s.epoch_steps, r->plan->nz - r->n_done);
+      if (err != BPM_OK || r->n_done >= r->plan->nz) done.push_back(r);
+    }
+    {
+      std::lock_guard<std::mutex> lk(s.mu);
+      for (auto& r : done)
+        s.active.erase(std::remove(s.active.begin(), s.active.end(), r), s.active.end());
+    }
+    for (auto& r : done) {
+      int rc = err != BPM_OK ? err : retire_device(s, *r);
+      finish_request(s, r, rc, rc == BPM_OK ? "" : "request failed on the device");
+    }
+  }
+}
+
+void ensure_started(Server& s) {
+  if (s.started) return;
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  s.budget = size_t(double(free_b) * s.mem_fraction);
+  cudaStreamCreateWithFlags(&s.io_stream, cudaStreamNonBlocking);
+  cudaMalloc(&s.d_status, sizeof(int));
+  cudaMemset(s.d_status, 0, sizeof(int));
+  s.started = true;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  s.worker = std::thread([dev] {
+    cudaSetDevice(dev);
+    worker_loop();
+  });
+  s.worker.detach();
+}
+
+}  // namespace
+}  // namespace bpm
+
+using namespace bpm;
+
+extern "C" {
+
+int bpm_server_configure(double mem_fraction, int32_t max_active, int32_t epoch_steps,
+                         int32_t max_queue) {
+  Server& s = srv();
+  std::lock_guard<std::mutex> lk(s.mu);
+  if (!s.queue.empty() || !s.active.empty())
+    return fail(BPM_ERR_BUSY, "server has requests in flight");
+  if (mem_fraction > 0.9) return fail(BPM_ERR_INVALID, "mem_fraction must be <= 0.9");
+  s.mem_fraction = mem_fraction > 0 ? mem_fraction : 0.6;
+  s.max_active = max_active > 0 ? max_active : 256;
+  s.epoch_steps = epoch_steps > 0 ? epoch_steps : 256;
+  s.max_queue = max_queue > 0 ? max_queue : 100000;
+  if (s.started) {
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    s.budget = size_t(double(free_b) * s.mem_fraction);
+  }
+  return BPM_OK;
+}
+
+int bpm_submit(bpm_plan_t plan, const double* psi_in, double* psi_out, void* records,
+               double* powers, bpm_ticket_t* out) {
+  if (!plan || !psi_in || !psi_out || !out)
+    return fail(BPM_ERR_INVALID, "plan, psi_in, psi_out and out must be non-NULL");
+  *out = 0;
+  Server& s = srv();
+  auto r = std::make_shared<Request>();
+  r->plan = plan;
+  const size_t count = size_t(plan->nb) * 2 * plan->nx * 2;
+  r->psi_in.assign(psi_in, psi_in + count);
+  r->psi_out = psi_out;
+  r->records = records;
+  r->powers = powers;
+  {
+    std::lock_guard<std::mutex> lk(plan->mu);
+    r->footprint = footprint_of(plan, records != nullptr && plan->n_rec > 0);
+  }
+  std::lock_guard<std::mutex> lk(s.mu);
+  ensure_started(s);
+  if (r->footprint > s.budget)
+    return fail(BPM_ERR_OOM, "request needs more device memory than the server budget");
+  if (int(s.queue.size()) >= s.max_queue) return fail(BPM_ERR_BUSY, "server queue is full");
+  {
+    std::lock_guard<std::mutex> pk(plan->mu);
+    plan->pending += 1;
+  }
+  r->id = s.next_id++;
+  r->t_submit = now_s();
+  s.tickets[r->id] = r;
+  s.queue.push_back(r);
+  s.cv_work.notify_one();
+  *out = r->id;
+  return BPM_OK;
+}
+
+int bpm_poll(bpm_ticket_t ticket, int32_t timeout_ms) {
+  Server& s = srv();
+  std::unique_lock<std::mutex> lk(s.mu);
+  auto it = s.tickets.find(ticket);
+  if (it == s.tickets.end()) return fail(BPM_ERR_INVALID, "unknown or already collected ticket");
+  auto r = it->second;
+  auto ready = [&] { return r->status != BPM_NOT_READY; };
+  if (timeout_ms < 0) s.cv_done.wait(lk, ready);
+  else if (timeout_ms > 0) s.cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
+  if (!ready()) return BPM_NOT_READY;
+  s.tickets.erase(it);
+  if (r->status != BPM_OK) return fail(r->status, r->error);
+  return BPM_OK;
+}
+
+int bpm_ticket_times(bpm_ticket_t ticket, double* t_submit, double* t_admit, double* t_done) {
+  Server& s = srv();
+  std::lock_guard<std::mutex> lk(s.mu);
+  auto it = s.tickets.find(ticket);
+  double a = 0, b = 0, c = 0;
+  if (it != s.tickets.end()) {
+    a = it->second->t_submit;
+    b = it->second->t_admit;
+    c = it->second->t_done;
+  } else {
+    auto jt = s.times.find(ticket);
+    if (jt == s.times.end()) return fail(BPM_ERR_INVALID, "unknown ticket");
+    a = jt->second[0];
+    b = jt->second[1];
+    c = jt->second[2];
+  }
+  if (t_submit) *t_submit = a;
+  if (t_admit) *t_admit = b;
+  if (t_done) *t_done = c;
+  return BPM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,231 @@
+"""GPU parity: the CUDA paths (through the C ABI) against the FP64 oracle.
+
+FP64 plain path: relative L2 per band <= 1e-10; fused FP32 path: <= 2e-4,
+over the final fields and every record (see ``parity_util.band_errors``).
+Masks are compared bit for bit (the decision is taken in FP64 with the same
+operation order on both sides).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import bpm as obpm
+from oracle import run as orun
+from oracle import timeaxis
+from paper_2601_06340_gb300 import binding, inputs
+
+from parity_util import TOL_FP32, TOL_FP64, band_errors, run_gpu, run_ref
+
+pytestmark = pytest.mark.gpu
+
+FP64, FP32 = binding.BPM_FP64_PLAIN, binding.BPM_FP32_FUSED
+
+
+def _reduced(name):
+    if name == "laue_perfect":
+        return inputs.laue_perfect(nx=512, nz=1000, record_every=90)
+    if name == "bragg_bent":
+        return inputs.bragg_bent(nx=1024, nz=2000, record_every=150)
+    if name == "asym_dislocation":
+        return inputs.asym_dislocation(nx=1024, nz=3000, record_every=250)
+    if name == "pulse_batched":
+        return inputs.pulse_batched(nx=512, nz=600, n_energy=8, record_every=70)
+    raise KeyError(name)
+
+
+CONFIGS = ["laue_perfect", "bragg_bent", "asym_dislocation", "pulse_batched"]
+
+
+@pytest.fixture(scope="module")
+def refs():
+    return {name: (_reduced(name), run_ref(_reduced(name))) for name in CONFIGS}
+
+
+@pytest.mark.parametrize("name", CONFIGS)
+def test_fp64_plain_matches_oracle(bpm_lib, refs, name):
+    wl, ref = refs[name]
+    out = run_gpu(wl, FP64)
+    errs = band_errors(out.psi, ref.psi, out.records, ref.records)
+    assert max(errs) <= TOL_FP64, errs
+    assert np.allclose(out.powers, ref.powers, rtol=1e-10, atol=0)
+
+
+@pytest.mark.parametrize("name", CONFIGS)
+def test_fp32_fused_matches_oracle(bpm_lib, refs, name):
+    wl, ref = refs[name]
+    out = run_gpu(wl, FP32)
+    errs = band_errors(out.psi, ref.psi, out.records, ref.records)
+    assert max(errs) <= TOL_FP32, errs
+    assert np.allclose(out.powers, ref.powers, rtol=4e-4, atol=1e-12 * np.max(ref.powers))
+
+
+@pytest.mark.parametrize("nx", [8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 8192])
+def test_every_transform_size(bpm_lib, nx):
+    """Random two-band input, masked strained bulk, 37 steps with a ragged
+    record tail (37 = 3 * 12 + 1): exercises every radix decomposition."""
+    rng = np.random.default_rng(nx)
+    nz = 37
+    wl = inputs.laue_perfect(nx=nx, nz=nz, dx_um=0.4, record_every=12)
+    wl.psi0 = (rng.standard_normal((1, 2, nx)) + 1j * rng.standard_normal((1, 2, nx)))
+    wl.crystal = dict(kind=inputs.CRYSTAL_MASK, mask=(rng.uniform(size=(nz, nx)) < 0.8))
+    wl.strain = dict(kind=inputs.STRAIN_ARRAY, ux=rng.uniform(-1e-3, 1e-3, (nz, nx)))
+    ref = run_ref(wl)
+    out64 = run_gpu(wl, FP64)
+    e64 = band_errors(out64.psi, ref.psi, out64.records, ref.records)
+    assert max(e64) <= TOL_FP64, e64
+    out32 = run_gpu(wl, FP32)
+    e32 = band_errors(out32.psi, ref.psi, out32.records, ref.records)
+    assert max(e32) <= 2e-6, e32
+
+
+@pytest.mark.parametrize("name", ["laue_perfect", "bragg_bent", "asym_dislocation"])
+def test_mask_is_bit_exact(bpm_lib, name):
+    wl = _reduced(name)
+    for prec in (FP32, FP64):
+        with binding.Plan(wl, prec) as plan:
+            mask, ph = plan.slices()
+        ref = orun.mask_of(wl)
+        assert np.array_equal(mask.astype(bool), ref)
+
+
+def test_strain_phasor_fp64(bpm_lib):
+    wl = _reduced("asym_dislocation")
+    with binding.Plan(wl, FP64) as plan:
+        mask, ph = plan.slices()
+    cr = orun.crystal_for(wl)
+    for n in range(0, wl.nz, 97):
+        inside, theta = cr(n)
+        ref = np.where(inside, np.exp(1j * theta), 0)
+        assert np.max(np.abs(ph[n] - ref)) < 1e-12
+
+
+def test_full_size_laue_perfect(bpm_lib):
+    wl = inputs.laue_perfect()
+    ref = run_ref(wl)
+    for prec, tol in ((FP64, TOL_FP64), (FP32, TOL_FP32)):
+        out = run_gpu(wl, prec)
+        errs = band_errors(out.psi, ref.psi, out.records, ref.records)
+        assert max(errs) <= tol, (prec, errs)
+
+
+def test_full_size_bragg_bent(bpm_lib):
+    wl = inputs.bragg_bent()
+    ref = run_ref(wl)
+    for prec, tol in ((FP64, TOL_FP64), (FP32, TOL_FP32)):
+        out = run_gpu(wl, prec)
+        errs = band_errors(out.psi, ref.psi, out.records, ref.records)
+        assert max(errs) <= tol, (prec, errs)
+
+
+def test_full_size_asym_dislocation_fp32(bpm_lib):
+    wl = inputs.asym_dislocation()
+    with binding.Plan(wl, FP32) as plan:
+        mask, _ = plan.slices()
+        out = plan.propagate()
+    assert np.array_equal(mask.astype(bool), orun.mask_of(wl))
+    ref = run_ref(wl)
+    errs = band_errors(out.psi, ref.psi, out.records, ref.records)
+    assert max(errs) <= TOL_FP32, errs
+
+
+def test_full_size_pulse_batched_sampled_rows(bpm_lib):
+    """All 256 energies on the GPU in one launch; the oracle checks rows 0,
+    131 and 255 one by one."""
+    wl = inputs.pulse_batched()
+    out = run_gpu(wl, FP32)
+    rows = [0, 131, 255]
+    ref = run_ref(wl, rows=rows)
+    errs = band_errors(out.psi[rows], ref.psi)
+    assert max(errs) <= TOL_FP32, errs
+
+
+def test_resume_split_equals_unsplit(bpm_lib):
+    wl = _reduced("bragg_bent")
+    for prec, tol in ((FP64, 1e-12), (FP32, 1e-5)):
+        with binding.Plan(wl, prec) as plan:
+            full = plan.propagate()
+            first = plan.propagate(n_end=700)
+            rec = first.records.copy()
+            pw = first.powers.copy()
+            second = plan.propagate(first.psi, n_begin=700,
+                                    out=binding.MarchOutput(np.empty_like(first.psi), rec, pw))
+        e = band_errors(second.psi, full.psi, second.records, full.records)
+        assert max(e) <= tol, (prec, e)
+
+
+def test_repeat_runs_are_bitwise_equal(bpm_lib):
+    wl = _reduced("asym_dislocation")
+    for prec in (FP32, FP64):
+        with binding.Plan(wl, prec) as plan:
+            a = plan.propagate()
+            b = plan.propagate()
+        assert np.array_equal(a.psi, b.psi) and np.array_equal(a.records, b.records)
+        assert np.array_equal(a.powers, b.powers)
+
+
+def test_batch_rows_are_independent(bpm_lib):
+    """A row's result does not depend on the rows launched beside it."""
+    wl = inputs.pulse_batched(nx=256, nz=300, n_energy=12)
+    full = run_gpu(wl, FP32)
+    for r in (0, 5, 11):
+        one = inputs.pulse_batched(nx=256, nz=300, n_energy=12)
+        one.energies_ev = one.energies_ev[r:r + 1]
+        one.psi0 = one.psi0[r:r + 1]
+        single = run_gpu(one, FP32)
+        assert np.array_equal(single.psi[0], full.psi[r])
+
+
+def test_edge_cases(bpm_lib):
+    # one step, records coarser than the march, smallest grid
+    wl = inputs.laue_perfect(nx=8, nz=1, dx_um=0.4, record_every=5)
+    ref = run_ref(wl)
+    for prec in (FP32, FP64):
+        out = run_gpu(wl, prec)
+        assert out.records.shape[1] == 0
+        assert max(band_errors(out.psi, ref.psi)) <= 1e-6
+    # record on every step
+    wl = inputs.bragg_bent(nx=256, nz=50, record_every=1)
+    ref = run_ref(wl)
+    out = run_gpu(wl, FP32)
+    assert max(band_errors(out.psi, ref.psi, out.records, ref.records)) <= 1e-5
+    # vacuum: fields only propagate; zero input stays zero
+    wl = inputs.laue_perfect(nx=128, nz=20)
+    wl.crystal = dict(kind=inputs.CRYSTAL_VACUUM)
+    wl.psi0 = np.zeros_like(wl.psi0)
+    out = run_gpu(wl, FP32)
+    assert np.all(out.psi == 0)
+
+
+def test_device_api_with_torch_tensors(bpm_lib):
+    torch = pytest.importorskip("torch")
+    wl = _reduced("bragg_bent")
+    ref = run_gpu(wl, FP32)
+    dev = torch.device("cuda:0")
+    x = torch.from_numpy(wl.psi0.astype(np.complex64)).to(dev)
+    y = torch.empty_like(x)
+    with binding.Plan(wl, FP32) as plan:
+        rec = torch.zeros((1, plan.n_rec, 2, wl.nx), dtype=torch.complex64, device=dev)
+        pw = torch.zeros((1, plan.n_rec + 1, 2), dtype=torch.float64, device=dev)
+        st = torch.cuda.current_stream()
+        binding.bpm_propagate_device(plan.handle, x, y, rec, pw, 0, wl.nz, st.cuda_stream)
+        st.synchronize()
+    assert np.array_equal(y.cpu().numpy().astype(np.complex128), ref.psi.astype(np.complex64))
+    assert np.array_equal(rec.cpu().numpy(), ref.records)
+
+
+def test_omega_to_t_matches_oracle(bpm_lib):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(11)
+    nb, nx = 64, 48
+    f = rng.standard_normal((nb, 2, nx)) + 1j * rng.standard_normal((nb, 2, nx))
+    ref = timeaxis.omega_to_t(f)
+    dev = torch.device("cuda:0")
+    for prec, dt, tol in ((FP64, torch.complex128, 1e-13), (FP32, torch.complex64, 3e-6)):
+        x = torch.from_numpy(f.astype(np.complex128)).to(dtype=dt, device=dev).contiguous()
+        y = torch.empty((2, nx, nb), dtype=dt, device=dev)
+        binding.bpm_omega_to_t_device(x, y, nb, nx, prec, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        got = y.cpu().numpy()
+        assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref))
