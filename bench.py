@@ -1,0 +1,379 @@
+"""Benchmark of the two-beam FFT-BPM z-march on GB300.
+
+Default workload (the one the headline metric is quoted on): symmetric
+Bragg, cylindrically bent crystal (R = 1 m), Nx = 4096, Nz = 8000, one
+photon energy.  One benchmark "step" is one whole march of that solve
+(8000 z-steps of forward FFT, propagator, inverse FFT and coupling for both
+envelopes).  ``value`` is cell-updates/s of the fused FP32 path with inputs
+resident in device memory; ``e2e`` is the same metric through the host
+C-ABI call (pinned host buffers, copies inside the timed region).  The line
+also carries the plain FP64 GPU path, both paths' relative L2 errors
+against the FP64 oracle, single-solve latency percentiles, the batched
+256-energy workload, the roofline of the dominant kernel and the oracle's
+own throughput on the host cores.
+
+``--impl reference`` times the FP64 oracle instead (bounded samples of the
+same march on the host cores).  Multi-GPU runs (torchrun) are independent
+replicas: every rank marches its own copy, there is no collective on the
+data path.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BPM cell-updates/s, fused FP32 vs plain FP64 GPU at stated err; p50/p99 latency"
+UNIT = "cell-updates/s"
+WORKLOAD = ("bragg_bent: 2D symmetric Bragg, bent crystal R=1 m nu=0.28, 8 keV, "
+            "theta_B=23.65 deg, 200 um slab, Nx=4096, Nz=8000, dx=0.2 um, dz=0.1 um, "
+            "one energy, Gaussian 50 um FWHM")
+FLOPS_PER_CELL = lambda n: 4 * 5 * math.log2(n)      # 4 FFTs x 5 N log2 N / N
+KERNEL_SOURCES = ["paper_2601_06340_gb300/csrc/fused_kernel.cuh",
+                  "paper_2601_06340_gb300/csrc/radix.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name: str):
+    """dram bytes per launch from a committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_hash = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
+    m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_bytes or m_hash.group(1) != kernel_hash():
+        return None
+    return float(m_bytes.group(1))
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            self.proc.wait(timeout=10)
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def rel_l2_bands(got, ref):
+    out = []
+    for b in range(2):
+        den = np.linalg.norm(ref[:, b])
+        out.append(float(np.linalg.norm(got[:, b] - ref[:, b]) / den) if den > 0 else 0.0)
+    return out
+
+
+# --------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    """FP64 oracle on the host cores: each step is a bounded sample (the
+    first `sample_steps` z-steps of the march)."""
+    if rank != 0:
+        return
+    from oracle import run as orun
+    from paper_2601_06340_gb300 import inputs
+    wl = inputs.bragg_bent()
+    sample_steps = args.ref_sample_steps
+    for _ in range(args.warmup):
+        orun.run_workload(wl, 0, sample_steps, record_every=0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        orun.run_workload(wl, 0, sample_steps, record_every=0)
+    dt = (time.perf_counter() - t0) / args.steps
+    cells = wl.nx * sample_steps
+    value = cells / dt
+    sample = (f"first {sample_steps} of the {wl.nz} z-steps of the bragg_bent march "
+              f"(Nx={wl.nx}, one energy) per step, numpy float64, single thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_gpu(args, rank, world):
+    import torch
+    import torch.distributed as dist
+    from paper_2601_06340_gb300 import binding, inputs
+    import __graft_entry__
+    __graft_entry__.build()
+    binding.load()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    FP32, FP64 = binding.BPM_FP32_FUSED, binding.BPM_FP64_PLAIN
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    wl = inputs.bragg_bent()
+    cells = wl.cell_updates
+    plan32 = binding.Plan(wl, FP32)
+    n_rec = plan32.n_rec
+    x = torch.from_numpy(wl.psi0.astype(np.complex64)).to(dev)
+    y = torch.empty_like(x)
+    rec = torch.zeros((1, n_rec, 2, wl.nx), dtype=torch.complex64, device=dev)
+    pw = torch.zeros((1, n_rec + 1, 2), dtype=torch.float64, device=dev)
+
+    def march32():
+        binding.bpm_propagate_device(plan32.handle, x, y, rec, pw, 0, wl.nz, stream.cuda_stream)
+
+    # ---- fused FP32, device-resident (the headline value) -----------------
+    for _ in range(args.warmup):
+        march32()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with ClockSampler(dev.index) as clk:
+        barrier()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_stop = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            march32()
+            ev[i][1].record(stream)
+        t_stop.record(stream)
+        barrier()
+    total_ms = max_over_ranks(t_start.elapsed_time(t_stop))
+    per_ms = [a.elapsed_time(b) for a, b in ev]
+    value = world * args.steps * cells / (total_ms * 1e-3)
+    clocks = clk.summary()
+
+    if args.only == "fused":
+        if rank == 0:
+            print(json.dumps({"only": "fused", "value": value, "unit": UNIT,
+                              "ms_per_step": total_ms / args.steps}), flush=True)
+        plan32.close()
+        return
+
+    # ---- parity on the timed workload (oracle on the host) ----------------
+    fused_psi = y.cpu().numpy().astype(np.complex128)
+    ref = None
+    cpu_baseline = None
+    if rank == 0 and not args.skip_oracle:
+        from oracle import run as orun
+        t0 = time.perf_counter()
+        ref = orun.run_workload(wl, record_every=0)
+        cpu_s = time.perf_counter() - t0
+        cpu_baseline = {"value": cells / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+                        "sample": "the whole bragg_bent march (Nx=4096, Nz=8000) once, "
+                                  "numpy float64, single thread"}
+    err32 = rel_l2_bands(fused_psi, ref.psi) if ref is not None else None
+
+    # ---- end to end through the host C-ABI (pinned host buffers) ----------
+    pin_in = torch.from_numpy(wl.psi0.astype(np.complex128)).pin_memory()
+    pin_out = torch.empty_like(pin_in).pin_memory()
+    pin_rec = torch.empty((1, n_rec, 2, wl.nx), dtype=torch.complex64).pin_memory()
+    pin_pw = torch.empty((1, n_rec + 1, 2), dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, args.steps // 2)
+    binding.bpm_propagate(plan32.handle, pin_in, pin_out, pin_rec, pin_pw, 0, wl.nz)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        binding.bpm_propagate(plan32.handle, pin_in, pin_out, pin_rec, pin_pw, 0, wl.nz)
+        _ = float(pin_pw[0, -1, 1])          # read the step's result on the host
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_value = world * e2e_steps * cells / e2e_s
+    h2d = pin_in.numel() * 16
+    d2h = pin_out.numel() * 16 + pin_rec.numel() * 8 + pin_pw.numel() * 8
+    plan32.close()
+
+    # ---- plain FP64 per-step GPU path (same workload) ----------------------
+    plan64 = binding.Plan(wl, FP64)
+    x64 = torch.from_numpy(wl.psi0).to(dev)
+    y64 = torch.empty_like(x64)
+    binding.bpm_propagate_device(plan64.handle, x64, y64, None, None, 0, wl.nz,
+                                 stream.cuda_stream)
+    barrier()
+    s64 = max(1, args.steps // 5)
+    a64, b64 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a64.record(stream)
+    for _ in range(s64):
+        binding.bpm_propagate_device(plan64.handle, x64, y64, None, None, 0, wl.nz,
+                                     stream.cuda_stream)
+    b64.record(stream)
+    barrier()
+    ms64 = max_over_ranks(a64.elapsed_time(b64)) / s64
+    value64 = world * cells / (ms64 * 1e-3)
+    err64 = rel_l2_bands(y64.cpu().numpy(), ref.psi) if ref is not None else None
+    plan64.close()
+
+    # ---- batched: 256 photon energies (pulse), one launch + energy->time --
+    batched = None
+    if not args.skip_batched:
+        wb = inputs.pulse_batched()
+        planb = binding.Plan(wb, FP32)
+        xb = torch.from_numpy(wb.psi0.astype(np.complex64)).to(dev)
+        yb = torch.empty_like(xb)
+        tb = torch.empty((2, wb.nx, wb.batch), dtype=torch.complex64, device=dev)
+
+        def march_b():
+            binding.bpm_propagate_device(planb.handle, xb, yb, None, None, 0, wb.nz,
+                                         stream.cuda_stream)
+            binding.bpm_omega_to_t_device(yb, tb, wb.batch, wb.nx, FP32, stream.cuda_stream)
+        march_b()
+        barrier()
+        kb = 3
+        ab, bb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ab.record(stream)
+        for _ in range(kb):
+            march_b()
+        bb.record(stream)
+        barrier()
+        msb = max_over_ranks(ab.elapsed_time(bb)) / kb
+        cells_b = wb.cell_updates
+        batched = {"workload": "pulse_batched: 256 energies 9 keV +- 5 eV, Laue 300 um, "
+                               "bent R=2 m, Nx=4096, Nz=6000, + energy->time IDFT",
+                   "value": world * cells_b / (msb * 1e-3), "unit": UNIT,
+                   "ms_per_march": msb}
+        planb.close()
+
+    # ---- roofline of the dominant kernel (fused march) ---------------------
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak_tflops = sms * 128 * 2 * max_mhz * 1e6 / 1e12
+    avg_launch_s = float(np.mean(per_ms)) * 1e-3
+    achieved = cells * FLOPS_PER_CELL(wl.nx) / avg_launch_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops,
+                "traffic": profiled_traffic("fused_march_bragg_bent.md"),
+                "kernel": "fused_march_kernel<12> (one CTA per solve)",
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
+                "sm_frac": achieved / (peak_tflops / sms),
+                "flops_per_cell_update": FLOPS_PER_CELL(wl.nx)}
+    if batched is not None:
+        ach_b = batched["value"] / world * FLOPS_PER_CELL(4096) / 1e12
+        batched["roofline"] = {"bound": "alu", "achieved": ach_b, "peak": peak_tflops,
+                               "unit": "TFLOP/s", "frac": ach_b / peak_tflops}
+
+    if rank == 0:
+        lat = np.array(per_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (262 MB strain-phasor stream per march)"},
+            "rel_l2_err": err32,
+            "tolerance": 2e-4,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                           "p99": float(np.percentile(lat, 99))},
+            "fp64_plain": {"value": value64, "unit": UNIT, "ms_per_step": ms64,
+                           "rel_l2_err": err64, "tolerance": 1e-10,
+                           "fused_speedup": value / value64},
+            "batched": batched,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": 2 * args.steps,
+            "roofline": roofline,
+            "cpu_baseline": cpu_baseline,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--ref-sample-steps", type=int, default=1000)
+    ap.add_argument("--skip-oracle", action="store_true")
+    ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--only", default="all", choices=["all", "fused"],
+                    help="fused: time only the fused march (used for profiling runs)")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "gpu":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world)
+    if world > 1 and args.impl == "gpu":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

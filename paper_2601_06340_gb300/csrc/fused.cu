@@ -1,15 +1,19 @@
 // Dispatch of the fused FP32 march by transform size.
 #include "fused_kernel.cuh"
+#include "fused2_kernel.cuh"
 
 namespace bpm {
 
 #define BPM_DECLARE_FUSED(L)                                                     \
   int fused_launch_##L(const RowDescF32*, int, int, const float4*, int*,         \
                        cudaStream_t);
+#define BPM_DECLARE_FUSED2(L)                                                    \
+  int fused2_launch_##L(const RowDescF32*, int, int, const float4*, int*,        \
+                        cudaStream_t);
 BPM_DECLARE_FUSED(3) BPM_DECLARE_FUSED(4) BPM_DECLARE_FUSED(5)
-BPM_DECLARE_FUSED(6) BPM_DECLARE_FUSED(7) BPM_DECLARE_FUSED(8)
-BPM_DECLARE_FUSED(9) BPM_DECLARE_FUSED(10) BPM_DECLARE_FUSED(11)
-BPM_DECLARE_FUSED(12) BPM_DECLARE_FUSED(13)
+BPM_DECLARE_FUSED(6) BPM_DECLARE_FUSED(7) BPM_DECLARE_FUSED2(8)
+BPM_DECLARE_FUSED2(9) BPM_DECLARE_FUSED2(10) BPM_DECLARE_FUSED2(11)
+BPM_DECLARE_FUSED2(12) BPM_DECLARE_FUSED(13)
 
 int launch_fused(int logn, const RowDescF32* d_rows, int n_rows, int steps,
                  const float4* d_tw, int* d_status, cudaStream_t st) {
@@ -20,11 +24,11 @@ int launch_fused(int logn, const RowDescF32* d_rows, int n_rows, int steps,
     case 5: return fused_launch_5(d_rows, n_rows, steps, d_tw, d_status, st);
     case 6: return fused_launch_6(d_rows, n_rows, steps, d_tw, d_status, st);
     case 7: return fused_launch_7(d_rows, n_rows, steps, d_tw, d_status, st);
-    case 8: return fused_launch_8(d_rows, n_rows, steps, d_tw, d_status, st);
-    case 9: return fused_launch_9(d_rows, n_rows, steps, d_tw, d_status, st);
-    case 10: return fused_launch_10(d_rows, n_rows, steps, d_tw, d_status, st);
-    case 11: return fused_launch_11(d_rows, n_rows, steps, d_tw, d_status, st);
-    case 12: return fused_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
+    case 8: return fused2_launch_8(d_rows, n_rows, steps, d_tw, d_status, st);
+    case 9: return fused2_launch_9(d_rows, n_rows, steps, d_tw, d_status, st);
+    case 10: return fused2_launch_10(d_rows, n_rows, steps, d_tw, d_status, st);
+    case 11: return fused2_launch_11(d_rows, n_rows, steps, d_tw, d_status, st);
+    case 12: return fused2_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
     case 13: return fused_launch_13(d_rows, n_rows, steps, d_tw, d_status, st);
     default: return fail(BPM_ERR_INVALID, "unsupported transform size");
   }
@@ -37,6 +41,13 @@ static void cfg_of(int* smem, int* rows, int* threads) {
   *threads = FusedCfg<L>::THREADS;
 }
 
+template <int L>
+static void cfg2_of(int* smem, int* rows, int* threads) {
+  *smem = F2Cfg<L>::SMEM;
+  *rows = F2Cfg<L>::ROWS;
+  *threads = F2Cfg<L>::THREADS;
+}
+
 static void fused_cfg(int logn, int* smem, int* rows, int* threads) {
   switch (logn) {
     case 3: cfg_of<3>(smem, rows, threads); break;
@@ -44,11 +55,11 @@ static void fused_cfg(int logn, int* smem, int* rows, int* threads) {
     case 5: cfg_of<5>(smem, rows, threads); break;
     case 6: cfg_of<6>(smem, rows, threads); break;
     case 7: cfg_of<7>(smem, rows, threads); break;
-    case 8: cfg_of<8>(smem, rows, threads); break;
-    case 9: cfg_of<9>(smem, rows, threads); break;
-    case 10: cfg_of<10>(smem, rows, threads); break;
-    case 11: cfg_of<11>(smem, rows, threads); break;
-    case 12: cfg_of<12>(smem, rows, threads); break;
+    case 8: cfg2_of<8>(smem, rows, threads); break;
+    case 9: cfg2_of<9>(smem, rows, threads); break;
+    case 10: cfg2_of<10>(smem, rows, threads); break;
+    case 11: cfg2_of<11>(smem, rows, threads); break;
+    case 12: cfg2_of<12>(smem, rows, threads); break;
     default: cfg_of<13>(smem, rows, threads); break;
   }
 }

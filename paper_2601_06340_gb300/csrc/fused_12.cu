@@ -1,2 +1,2 @@
 #include "fused_launch.cuh"
-BPM_INSTANTIATE_FUSED(12)
+BPM_INSTANTIATE_FUSED2(12)

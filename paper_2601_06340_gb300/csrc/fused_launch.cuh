@@ -3,8 +3,12 @@
 #pragma once
 
 #include "fused_kernel.cuh"
+#include "fused2_kernel.cuh"
 
 namespace bpm {
+
+// Butterfly-constant policy of the band-per-thread kernel.
+constexpr bool kFusedExactConstants = true;
 
 template <int LOGN>
 int fused_launch_impl(const RowDescF32* d_rows, int n_rows, int steps,
@@ -26,7 +30,35 @@ int fused_launch_impl(const RowDescF32* d_rows, int n_rows, int steps,
   return BPM_OK;
 }
 
+// Band-per-thread kernel (256 <= N <= 4096); EX selects hi+lo butterfly constants.
+template <int LOGN, bool EX>
+int fused2_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const float4* d_tw,
+                       int* d_status, cudaStream_t st) {
+  using C = F2Cfg<LOGN>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(fused2_march_kernel<LOGN, EX>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused2)");
+    configured = true;
+  }
+  const int grid = (n_rows + C::ROWS - 1) / C::ROWS;
+  fused2_march_kernel<LOGN, EX><<<grid, C::THREADS, C::SMEM, st>>>(d_rows, n_rows, steps, d_tw,
+                                                                  d_status);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "fused2 march launch");
+  return BPM_OK;
+}
+
 }  // namespace bpm
+
+#define BPM_INSTANTIATE_FUSED2(L)                                                 \
+  namespace bpm {                                                                 \
+  int fused2_launch_##L(const RowDescF32* r, int n, int s, const float4* tw,     \
+                        int* status, cudaStream_t st) {                           \
+    return fused2_launch_impl<L, kFusedExactConstants>(r, n, s, tw, status, st);  \
+  }                                                                               \
+  }
 
 #define BPM_INSTANTIATE_FUSED(L)                                                  \
   namespace bpm {                                                                 \

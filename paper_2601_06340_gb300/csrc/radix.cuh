@@ -52,36 +52,53 @@ __device__ __forceinline__ float2 cmul_hl(float2 z, float ch, float sh,
   return make_float2(re, im);
 }
 
-// x * sqrt(1/2) with the double-float constant.
-__device__ __forceinline__ float mul_h(float x) { return fmaf(x, kHh, x * kHl); }
+// Constant policy: EXACT = true carries every internal constant as hi + lo;
+// EXACT = false uses the nearest float (cheaper; adequate when the FFT only
+// acts on the small per-step increment, see the fused kernel).
+template <bool EXACT>
+__device__ __forceinline__ float mul_h(float x) {
+  if constexpr (EXACT) return fmaf(x, kHh, x * kHl);
+  else return x * kHh;
+}
+
+// z * (c + i s) with a plain float constant.
+__device__ __forceinline__ float2 cmul_f(float2 z, float c, float s) {
+  return make_float2(fmaf(z.x, c, -(z.y * s)), fmaf(z.x, s, z.y * c));
+}
+
+template <bool EXACT>
+__device__ __forceinline__ float2 cmul_k(float2 z, float ch, float sh, float cl, float sl) {
+  if constexpr (EXACT) return cmul_hl(z, ch, sh, cl, sl);
+  else return cmul_f(z, ch, sh);
+}
 
 // z * W8^1 (forward: (1 - i)/sqrt2; inverse: (1 + i)/sqrt2).
-template <bool INV>
+template <bool INV, bool EXACT = true>
 __device__ __forceinline__ float2 mul_w8(float2 z) {
-  return INV ? make_float2(mul_h(z.x - z.y), mul_h(z.x + z.y))
-             : make_float2(mul_h(z.x + z.y), mul_h(z.y - z.x));
+  return INV ? make_float2(mul_h<EXACT>(z.x - z.y), mul_h<EXACT>(z.x + z.y))
+             : make_float2(mul_h<EXACT>(z.x + z.y), mul_h<EXACT>(z.y - z.x));
 }
 // z * W8^3 (forward: (-1 - i)/sqrt2; inverse: (-1 + i)/sqrt2).
-template <bool INV>
+template <bool INV, bool EXACT = true>
 __device__ __forceinline__ float2 mul_w8_3(float2 z) {
-  return INV ? make_float2(-mul_h(z.x + z.y), mul_h(z.x - z.y))
-             : make_float2(mul_h(z.y - z.x), -mul_h(z.x + z.y));
+  return INV ? make_float2(-mul_h<EXACT>(z.x + z.y), mul_h<EXACT>(z.x - z.y))
+             : make_float2(mul_h<EXACT>(z.y - z.x), -mul_h<EXACT>(z.x + z.y));
 }
 // z * W16^1, W16^3, W16^9 (forward exp(-2 pi i m/16); inverse conjugate).
-template <bool INV>
+template <bool INV, bool EXACT = true>
 __device__ __forceinline__ float2 mul_w16_1(float2 z) {
-  return INV ? cmul_hl(z, kC1h, kS1h, kC1l, kS1l)
-             : cmul_hl(z, kC1h, -kS1h, kC1l, -kS1l);
+  return INV ? cmul_k<EXACT>(z, kC1h, kS1h, kC1l, kS1l)
+             : cmul_k<EXACT>(z, kC1h, -kS1h, kC1l, -kS1l);
 }
-template <bool INV>
+template <bool INV, bool EXACT = true>
 __device__ __forceinline__ float2 mul_w16_3(float2 z) {
-  return INV ? cmul_hl(z, kS1h, kC1h, kS1l, kC1l)
-             : cmul_hl(z, kS1h, -kC1h, kS1l, -kC1l);
+  return INV ? cmul_k<EXACT>(z, kS1h, kC1h, kS1l, kC1l)
+             : cmul_k<EXACT>(z, kS1h, -kC1h, kS1l, -kC1l);
 }
-template <bool INV>
+template <bool INV, bool EXACT = true>
 __device__ __forceinline__ float2 mul_w16_9(float2 z) {
-  return INV ? cmul_hl(z, -kC1h, -kS1h, -kC1l, -kS1l)
-             : cmul_hl(z, -kC1h, kS1h, -kC1l, kS1l);
+  return INV ? cmul_k<EXACT>(z, -kC1h, -kS1h, -kC1l, -kS1l)
+             : cmul_k<EXACT>(z, -kC1h, kS1h, -kC1l, kS1l);
 }
 
 template <bool INV>
@@ -108,13 +125,13 @@ __device__ __forceinline__ void dft4(float2* v) {
 }
 
 // 8 = 4 x 2: n = 2 n1 + n2, k = k1 + 4 k2.
-template <bool INV>
+template <bool INV, bool EXACT = true>
 __device__ __forceinline__ void dft8(float2* v) {
   dft4_inplace<INV>(v[0], v[2], v[4], v[6]);   // n2 = 0 -> a[k1][0] at v[2 k1]
   dft4_inplace<INV>(v[1], v[3], v[5], v[7]);   // n2 = 1 -> a[k1][1] at v[2 k1 + 1]
-  v[3] = mul_w8<INV>(v[3]);
+  v[3] = mul_w8<INV, EXACT>(v[3]);
   v[5] = mul_w4<INV>(v[5]);
-  v[7] = mul_w8_3<INV>(v[7]);
+  v[7] = mul_w8_3<INV, EXACT>(v[7]);
   float2 o[8];
 #pragma unroll
   for (int k1 = 0; k1 < 4; ++k1) {
@@ -126,21 +143,21 @@ __device__ __forceinline__ void dft8(float2* v) {
 }
 
 // 16 = 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2, inner twiddles W16^(n2 k1).
-template <bool INV>
+template <bool INV, bool EXACT = true>
 __device__ __forceinline__ void dft16(float2* v) {
 #pragma unroll
   for (int n2 = 0; n2 < 4; ++n2)
     dft4_inplace<INV>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
   // a[k1][n2] now at v[4 k1 + n2]
-  v[5] = mul_w16_1<INV>(v[5]);      // k1=1,n2=1: W^1
-  v[6] = mul_w8<INV>(v[6]);         // k1=1,n2=2: W^2
-  v[7] = mul_w16_3<INV>(v[7]);      // k1=1,n2=3: W^3
-  v[9] = mul_w8<INV>(v[9]);         // k1=2,n2=1: W^2
-  v[10] = mul_w4<INV>(v[10]);       // k1=2,n2=2: W^4
-  v[11] = mul_w8_3<INV>(v[11]);     // k1=2,n2=3: W^6
-  v[13] = mul_w16_3<INV>(v[13]);    // k1=3,n2=1: W^3
-  v[14] = mul_w8_3<INV>(v[14]);     // k1=3,n2=2: W^6
-  v[15] = mul_w16_9<INV>(v[15]);    // k1=3,n2=3: W^9
+  v[5] = mul_w16_1<INV, EXACT>(v[5]);      // k1=1,n2=1: W^1
+  v[6] = mul_w8<INV, EXACT>(v[6]);         // k1=1,n2=2: W^2
+  v[7] = mul_w16_3<INV, EXACT>(v[7]);      // k1=1,n2=3: W^3
+  v[9] = mul_w8<INV, EXACT>(v[9]);         // k1=2,n2=1: W^2
+  v[10] = mul_w4<INV>(v[10]);              // k1=2,n2=2: W^4
+  v[11] = mul_w8_3<INV, EXACT>(v[11]);     // k1=2,n2=3: W^6
+  v[13] = mul_w16_3<INV, EXACT>(v[13]);    // k1=3,n2=1: W^3
+  v[14] = mul_w8_3<INV, EXACT>(v[14]);     // k1=3,n2=2: W^6
+  v[15] = mul_w16_9<INV, EXACT>(v[15]);    // k1=3,n2=3: W^9
 #pragma unroll
   for (int k1 = 0; k1 < 4; ++k1)
     dft4_inplace<INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
@@ -154,12 +171,12 @@ __device__ __forceinline__ void dft16(float2* v) {
   for (int k = 0; k < 16; ++k) v[k] = o[k];
 }
 
-template <int R, bool INV>
+template <int R, bool INV, bool EXACT = true>
 __device__ __forceinline__ void dft(float2* v) {
   if constexpr (R == 2) dft2<INV>(v);
   else if constexpr (R == 4) dft4<INV>(v);
-  else if constexpr (R == 8) dft8<INV>(v);
-  else if constexpr (R == 16) dft16<INV>(v);
+  else if constexpr (R == 8) dft8<INV, EXACT>(v);
+  else if constexpr (R == 16) dft16<INV, EXACT>(v);
 }
 
 // z * w for a table twiddle t = (ch, sh, cl, sl) holding W = exp(-i a);
