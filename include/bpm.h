@@ -197,6 +197,38 @@ int bpm_ticket_times(bpm_ticket_t ticket, double* t_submit, double* t_admit,
  * the crystal).  Either pointer may be NULL.  For inspection and tests. */
 int bpm_fetch_slices(bpm_plan_t plan, uint8_t* mask, double* phasor);
 
+/* Allocation-free FP64 march.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory -- code that
+ * runs where cudaMalloc is not allowed or not wanted (a host callback, a
+ * process whose device memory is owned by another allocator or budget, an
+ * embedding that must not grow its footprint after start-up).  It advances
+ * caller-owned device buffers with the plain FP64 step of bpm_propagate
+ * (one launch per Stockham pass, propagator and coupling) and calls no
+ * cudaMalloc, cudaFree or allocating library routine: its working memory
+ * (16 MiB ping-pong buffer, 8192-entry twiddle table, 1024 row descriptors)
+ * lives in static device arrays that every GPU loading this library holds
+ * until the process exits.
+ *   d_psi      [n_rows][2][nx] c128, in/out: the state after n_begin steps
+ *              becomes the state after n_end steps WITHOUT the common phase
+ *              exp(i dz^ cos(alpha)) per step (bpm_propagate_device includes
+ *              it: multiply by exp(i (n_end-n_begin) dz^ cos(alpha)) to
+ *              compare);
+ *   d_prop     [n_rows][2][nx] c128: exp(i dz^ delta_+-(q_m)) / nx per band,
+ *              natural FFT order, q_m = 2 pi fftfreq(nx, dx^) (band 0 uses
+ *              q + s, band 1 q - s);
+ *   d_coupling [n_rows][2] c128: (Delta_eps_0, Delta_eps_{+-1}) inside Pi;
+ *   d_phasor   [>= n_end][nx] c128: exp(i h u_x) per cell, (0,0) outside.
+ * Limits: nx a power of two in [8, 8192], 1 <= n_rows <= 1024 and
+ * n_rows * 2 * nx <= 2^20; other sizes return BPM_ERR_INVALID before any
+ * device work.  Asynchronous on `stream`.  The first call on a device looks
+ * up the arrays' device addresses (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the arrays, and each rewrites what it reads, so calls that overlap on the
+ * GPU race. */
+int bpm_march_f64_noalloc(void* d_psi, int32_t nx, int32_t n_rows, const void* d_prop,
+                          const void* d_coupling, const void* d_phasor, int32_t n_begin,
+                          int32_t n_end, void* stream);
+
 /* Release the plan and its device memory.  BPM_ERR_BUSY while tickets of
  * the plan are pending. */
 int bpm_destroy(bpm_plan_t plan);

@@ -63,6 +63,7 @@ _SIGS = {
     "bpm_ticket_times": ([ctypes.c_uint64, ctypes.POINTER(_D), ctypes.POINTER(_D),
                           ctypes.POINTER(_D)], ctypes.c_int),
     "bpm_fetch_slices": ([_P, _P, _P], ctypes.c_int),
+    "bpm_march_f64_noalloc": ([_P, _I, _I, _P, _P, _P, _I, _I, _P], ctypes.c_int),
     "bpm_destroy": ([_P], ctypes.c_int),
     "bpm_last_error": ([], ctypes.c_char_p),
     "bpm_version": ([], ctypes.c_char_p),
@@ -170,6 +171,13 @@ def bpm_ticket_times(ticket):
 
 def bpm_fetch_slices(plan, mask=None, phasor=None):
     return _check(load().bpm_fetch_slices(plan, _ptr(mask), _ptr(phasor)))
+
+
+def bpm_march_f64_noalloc(d_psi, nx, n_rows, d_prop, d_coupling, d_phasor, n_begin, n_end,
+                          stream=None):
+    return _check(load().bpm_march_f64_noalloc(_ptr(d_psi), int(nx), int(n_rows), _ptr(d_prop),
+                                                _ptr(d_coupling), _ptr(d_phasor), int(n_begin),
+                                                int(n_end), stream))
 
 
 def bpm_destroy(plan):

@@ -7,6 +7,8 @@
 //   -> real-space coupling with the strain phasor and mask -> [record].
 // It is the FP64 reference form on the GPU and the baseline the fused FP32
 // kernel is measured against.
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "bpm_internal.h"
@@ -218,3 +220,137 @@ int plain_march(bpm_plan_s* plan, int n_begin, int n_end, int n_phase0, void* d_
 }
 
 }  // namespace bpm
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the plain FP64 march.
+//
+// For callers that cannot allocate device memory (for example code that runs
+// where cudaMalloc is not allowed, such as inside a host callback, under an
+// allocator that must not grow, or in a process whose device memory is owned
+// by someone else): it marches caller-owned buffers and keeps its own working
+// memory -- the Stockham ping-pong buffer, the twiddle table and the row
+// descriptors -- in the file-scope device arrays below, which every GPU that
+// loads this library holds until the process exits.  Limits: at most
+// kNoAllocMaxRows rows and n_rows * 2 * nx <= kNoAllocMaxComplex complex
+// values (16 MiB of scratch).  All calls share these arrays, so calls that
+// overlap on the GPU (on different streams or from different threads) race;
+// each call rewrites the twiddles and descriptors it reads before using them,
+// and the ping-pong buffer needs no clearing because every pass overwrites
+// what it later reads.
+namespace bpm {
+namespace {
+
+constexpr size_t kNoAllocMaxComplex = size_t(1) << 20;
+constexpr int kNoAllocMaxRows = 1024;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocMaxComplex];
+static __device__ __align__(256) double2 g_noalloc_twiddles[1 << kMaxLogN];
+static __device__ __align__(256) RowDescF64 g_noalloc_rows[kNoAllocMaxRows];
+
+struct NoAllocSymbols {
+  bool ready = false;
+  double2* scratch = nullptr;
+  double2* twiddles = nullptr;
+  RowDescF64* rows = nullptr;
+};
+std::mutex g_noalloc_mu;
+NoAllocSymbols g_noalloc_sym[kNoAllocMaxDevices];
+
+// W_n^m = exp(-2 pi i m / n), exact on the axes.
+__global__ void noalloc_twiddle_kernel(double2* tw, int n) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi(2.0 * double(m) / double(n), &s, &c);
+    if ((4 * m) % n == 0) {
+      const int q = ((4 * m) / n) & 3;
+      c = (q == 0) ? 1.0 : (q == 2) ? -1.0 : 0.0;
+      s = (q == 1) ? 1.0 : (q == 3) ? -1.0 : 0.0;
+    }
+    tw[m] = make_double2(c, -s);
+  }
+}
+
+__global__ void noalloc_rows_kernel(RowDescF64* rows, const double2* prop, const double2* ab,
+                                    int nx, int n_rows) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_rows; r += gridDim.x * blockDim.x) {
+    rows[r].prop = prop + size_t(r) * 2 * nx;
+    rows[r].a = ab[2 * r];
+    rows[r].b = ab[2 * r + 1];
+    rows[r].gphase = 0.0;
+  }
+}
+
+}  // namespace
+
+}  // namespace bpm
+
+extern "C" int bpm_march_f64_noalloc(void* d_psi, int32_t nx, int32_t n_rows,
+                                     const void* d_prop, const void* d_coupling,
+                                     const void* d_phasor, int32_t n_begin, int32_t n_end,
+                                     void* stream) {
+  using namespace bpm;
+  if (!d_psi || !d_prop || !d_coupling || !d_phasor)
+    return fail(BPM_ERR_INVALID, "noalloc march: a buffer is NULL");
+  if (nx < 8 || nx > (1 << kMaxLogN) || (nx & (nx - 1)))
+    return fail(BPM_ERR_INVALID, "noalloc march: nx must be a power of two in [8, " +
+                                     std::to_string(1 << kMaxLogN) + "]");
+  if (n_rows < 1 || n_rows > kNoAllocMaxRows)
+    return fail(BPM_ERR_INVALID, "noalloc march: n_rows must be in [1, " +
+                                     std::to_string(kNoAllocMaxRows) + "]");
+  if (size_t(n_rows) * 2 * size_t(nx) > kNoAllocMaxComplex)
+    return fail(BPM_ERR_INVALID, "noalloc march: n_rows * 2 * nx exceeds the " +
+                                     std::to_string(kNoAllocMaxComplex) +
+                                     " complex values of static scratch");
+  if (n_begin < 0 || n_end <= n_begin)
+    return fail(BPM_ERR_INVALID, "noalloc march: need 0 <= n_begin < n_end");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "noalloc march: no device");
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return fail(BPM_ERR_INVALID, "noalloc march: device index out of range");
+  NoAllocSymbols sym;
+  {
+    // Once per device, with that device current: device addresses of the
+    // static arrays (their host-side names are not device addresses).
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    NoAllocSymbols& s = g_noalloc_sym[dev];
+    if (!s.ready) {
+      e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.scratch), g_noalloc_scratch);
+      if (e == cudaSuccess)
+        e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.twiddles), g_noalloc_twiddles);
+      if (e == cudaSuccess)
+        e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.rows), g_noalloc_rows);
+      if (e != cudaSuccess) return cuda_fail(e, "noalloc march: cudaGetSymbolAddress");
+      s.ready = true;
+    }
+    sym = s;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int logn = 0;
+  while ((1 << logn) < nx) ++logn;
+  const int lines = 2 * n_rows;
+  noalloc_twiddle_kernel<<<(nx + 255) / 256, 256, 0, st>>>(sym.twiddles, nx);
+  noalloc_rows_kernel<<<(n_rows + 127) / 128, 128, 0, st>>>(
+      sym.rows, static_cast<const double2*>(d_prop), static_cast<const double2*>(d_coupling), nx,
+      n_rows);
+  double2* user = static_cast<double2*>(d_psi);
+  double2* x = user;
+  double2* y = sym.scratch;
+  const double2* phasor = static_cast<const double2*>(d_phasor);
+  const int threads = 256;
+  for (int s = n_begin; s < n_end; ++s) {
+    double2* r = fft_lines(x, y, logn, lines, sym.twiddles, false, st);
+    if (r != x) std::swap(x, y);
+    prop_kernel<<<grid_for(long(lines) * nx, threads), threads, 0, st>>>(x, sym.rows, nx, n_rows);
+    r = fft_lines(x, y, logn, lines, sym.twiddles, true, st);
+    if (r != x) std::swap(x, y);
+    couple_kernel<<<grid_for(long(n_rows) * nx, threads), threads, 0, st>>>(
+        x, sym.rows, phasor + size_t(s) * nx, nx, n_rows);
+  }
+  if (x != user)
+    e = cudaMemcpyAsync(user, x, size_t(lines) * nx * sizeof(double2), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "noalloc march");
+  return BPM_OK;
+}
