@@ -1,4 +1,7 @@
 // Dispatch of the fused FP32 march by transform size.
+#include <cstdlib>
+#include <cstring>
+
 #include "fused_kernel.cuh"
 #include "fused2_kernel.cuh"
 
@@ -14,10 +17,42 @@ BPM_DECLARE_FUSED(3) BPM_DECLARE_FUSED(4) BPM_DECLARE_FUSED(5)
 BPM_DECLARE_FUSED(6) BPM_DECLARE_FUSED(7) BPM_DECLARE_FUSED2(8)
 BPM_DECLARE_FUSED2(9) BPM_DECLARE_FUSED2(10) BPM_DECLARE_FUSED2(11)
 BPM_DECLARE_FUSED2(12) BPM_DECLARE_FUSED(13)
+#define BPM_DECLARE_FUSED3(L)                                                    \
+  int fused3_launch_##L(const RowDescF32*, int, int, const float4*, int*,        \
+                        cudaStream_t);
+BPM_DECLARE_FUSED3(10) BPM_DECLARE_FUSED3(11) BPM_DECLARE_FUSED3(12)
+
+// Layout choice: a 2-CTA cluster per row (a whole SM per band) when every
+// row of the launch gets its own pair of SMs, else one CTA per row.  The
+// environment variable BPM_FUSED_LAYOUT=cta|cluster forces one of them.
+static bool use_cluster_layout(int logn, int n_rows) {
+  if (logn < 10 || logn > 12) return false;
+  static int forced = -2;
+  if (forced == -2) {
+    const char* v = std::getenv("BPM_FUSED_LAYOUT");
+    forced = !v ? -1 : (std::strcmp(v, "cluster") == 0 ? 1 : (std::strcmp(v, "cta") == 0 ? 0 : -1));
+  }
+  if (forced >= 0) return forced == 1;
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return 2 * n_rows <= sms;
+}
 
 int launch_fused(int logn, const RowDescF32* d_rows, int n_rows, int steps,
                  const float4* d_tw, int* d_status, cudaStream_t st) {
   if (n_rows <= 0 || steps <= 0) return BPM_OK;
+  if (use_cluster_layout(logn, n_rows)) {
+    switch (logn) {
+      case 10: return fused3_launch_10(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 11: return fused3_launch_11(d_rows, n_rows, steps, d_tw, d_status, st);
+      default: return fused3_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
+    }
+  }
   switch (logn) {
     case 3: return fused_launch_3(d_rows, n_rows, steps, d_tw, d_status, st);
     case 4: return fused_launch_4(d_rows, n_rows, steps, d_tw, d_status, st);

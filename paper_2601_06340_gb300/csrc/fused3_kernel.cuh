@@ -1,0 +1,220 @@
+// Fused FP32 march on a 2-CTA thread-block cluster: one row (one solve) per
+// cluster, CTA rank b advances band b (psi_+ or psi_-).  Used where a single
+// solve must finish fast: each band gets a whole SM.
+//
+// Same step as the band-per-thread kernel (real-space increment form of
+// Eq. fov10, see fused2_kernel.cuh), with a different placement:
+//   * T = N/16 threads per CTA, each owning 16 points of its band; with one
+//     CTA per SM a thread can keep in registers its 16 points, the step's
+//     original field, its table twiddles and its slice of the propagator
+//     table (loaded once per launch);
+//   * the coupling partner psi_p(other band) is read from the peer CTA's
+//     shared memory (distributed shared memory) after one cluster barrier
+//     per step; the exchange buffer alternates between two halves by step
+//     parity, so a step never overwrites what the peer may still be reading;
+//   * each CTA fetches the strain/mask slice of the step into its own shared
+//     memory with a bulk asynchronous copy on an mbarrier (bounded wait).
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "fused2_kernel.cuh"
+
+namespace bpm {
+
+template <int LOGN>
+struct F3Cfg {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int T = N / 16;
+  static constexpr int NP = (LOGN + 3) / 4;
+  static constexpr int RL = 1 << (LOGN - 4 * (NP - 1));
+  static constexpr int G_LAST = 16 / RL;
+  static constexpr int PADN = N + (N >> 4);
+  static constexpr int WARPS = T / 32;
+  static constexpr int OFF_BUF = 0;                       // [PADN]
+  static constexpr int OFF_X = OFF_BUF + PADN * 8;        // [2][N] exchange
+  static constexpr int OFF_PH = OFF_X + 2 * N * 8;        // [N]
+  static constexpr int OFF_MBAR = OFF_PH + N * 8;
+  static constexpr int OFF_RECPH = OFF_MBAR + 8;
+  static constexpr int OFF_RED = OFF_RECPH + 8;           // [WARPS] double
+  static constexpr int SMEM = OFF_RED + WARPS * 8;
+  static_assert(LOGN >= 9 && LOGN <= 12, "cluster kernel covers 512..4096");
+};
+
+template <int LOGN, bool EX>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
+    fused3_march_kernel(const RowDescF32* __restrict__ rows, int n_rows, int steps,
+                        const float4* __restrict__ tw, int* __restrict__ status) {
+  namespace cg = cooperative_groups;
+  using C = F3Cfg<LOGN>;
+  using F = F2Cfg<LOGN>;   // same pass geometry (E = 16 points per thread)
+  constexpr int N = C::N, T = C::T, NP = C::NP, RL = C::RL, GL = C::G_LAST;
+  extern __shared__ __align__(128) unsigned char smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+
+  const int band = int(cluster.block_rank());
+  const int row = blockIdx.x >> 1;
+  const int t = threadIdx.x;
+  const int lane = t & 31, warp = t >> 5;
+  const RowDescF32 d = rows[row < n_rows ? row : 0];
+  const bool lead = t == 0;
+
+  float2* buf = reinterpret_cast<float2*>(smem + C::OFF_BUF);
+  float2* xb = reinterpret_cast<float2*>(smem + C::OFF_X);
+  float2* ph = reinterpret_cast<float2*>(smem + C::OFF_PH);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::OFF_MBAR);
+  float2* recph = reinterpret_cast<float2*>(smem + C::OFF_RECPH);
+  double* red = reinterpret_cast<double*>(smem + C::OFF_RED);
+  const float2* xpeer = cluster.map_shared_rank(xb, band ^ 1);
+
+  if (lead) mbar_init(bar);
+  fence_mbar_init();
+
+  float2 w0[15], w1[15];
+#pragma unroll
+  for (int j = 1; j < 16; ++j) {
+    const float4 a = __ldg(&tw[t * j]);
+    w0[j - 1] = make_float2(a.x, a.y);
+    if constexpr (NP >= 3) {
+      const float4 b = __ldg(&tw[((t % F::stride(1)) * j) << 4]);
+      w1[j - 1] = make_float2(b.x, b.y);
+    } else {
+      w1[j - 1] = make_float2(0.f, 0.f);
+    }
+  }
+  // this thread's slice of (P - 1)/N in the last pass, for the whole launch
+  float2 pr[16];
+#pragma unroll
+  for (int i = 0; i < GL; ++i)
+#pragma unroll
+    for (int j = 0; j < RL; ++j)
+      pr[i * RL + j] = __ldg(&d.prop[band * N + f2_pos<LOGN, NP - 1>(t + i * T, j)]);
+
+  float2 v[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = d.state[band * N + t + j * T];
+  cluster.sync();   // peers initialised (mbarriers, shared memory) before any exchange
+
+  const uint32_t slice_bytes = uint32_t(N) * 8u;
+  int pending_slot = -1;
+  bool timed_out = false;
+  const float2 am1 = d.am1, bb = d.b;
+
+  for (int it = 0; it < steps; ++it) {
+    const int n = d.n_begin + it;
+    const bool rec = d.record_every > 0 && ((n + 1) % d.record_every) == 0 &&
+                     (d.records != nullptr || d.powers != nullptr);
+    if (lead && rec) {
+      double ang = fmod(double(n + 1 - d.n_phase0) * d.gphase, 6.283185307179586);
+      double sa, ca;
+      sincos(ang, &sa, &ca);
+      *recph = make_float2(float(ca), float(sa));
+    }
+    float2 org[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) org[j] = v[j];
+    dft<16, false, EX>(v);
+    f2_twiddle<false>(v, w0);
+    f2_store<LOGN, 0>(buf, v, t);
+    __syncthreads();
+    if (lead) bulk_load(ph, d.phasor + size_t(n) * N, slice_bytes, bar);
+    if (lead && pending_slot >= 0) {
+      double s = 0.0;
+      for (int w = 0; w < C::WARPS; ++w) s += red[w];
+      d.powers[2 * pending_slot + band] = s * d.dx_um;
+      pending_slot = -1;
+    }
+    if constexpr (NP >= 3) {
+      f2_load<LOGN, 1>(buf, v, t);
+      dft<16, false, EX>(v);
+      f2_twiddle<false>(v, w1);
+      f2_store<LOGN, 1>(buf, v, t);
+      __syncthreads();
+    }
+    {
+      constexpr int P = NP - 1;
+      f2_load<LOGN, P>(buf, v, t);
+      f2_dft<LOGN, P, false, EX>(v);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const float2 x = v[k], dd = pr[k];
+        v[k] = make_float2(fmaf(x.x, dd.x, -(x.y * dd.y)), fmaf(x.x, dd.y, x.y * dd.x));
+      }
+      f2_dft<LOGN, P, true, EX>(v);
+      f2_store<LOGN, P>(buf, v, t);
+      __syncthreads();
+    }
+    if constexpr (NP >= 3) {
+      f2_load<LOGN, 1>(buf, v, t);
+      f2_twiddle<true>(v, w1);
+      dft<16, true, EX>(v);
+      f2_store<LOGN, 1>(buf, v, t);
+      __syncthreads();
+    }
+    f2_load<LOGN, 0>(buf, v, t);
+    f2_twiddle<true>(v, w0);
+    dft<16, true, EX>(v);
+    float2* xo = xb + (it & 1) * N;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      v[j] = make_float2(org[j].x + v[j].x, org[j].y + v[j].y);
+      xo[t + j * T] = v[j];
+    }
+    cluster.sync();   // both bands' psi_p of this step are published
+
+    if (!mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
+    const float2* xi = xpeer + (it & 1) * N;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const float2 q = xi[t + j * T];
+      float2 e = ph[t + j * T];
+      const bool inside = (e.x != 0.f) | (e.y != 0.f);
+      if (band) e.y = -e.y;
+      const float ax = inside ? am1.x : 0.f, ay = inside ? am1.y : 0.f;
+      const float cx = fmaf(bb.x, e.x, -(bb.y * e.y)), cy = fmaf(bb.x, e.y, bb.y * e.x);
+      const float2 p = v[j];
+      float rx = fmaf(ax, p.x, p.x);
+      rx = fmaf(-ay, p.y, rx);
+      rx = fmaf(cx, q.x, rx);
+      rx = fmaf(-cy, q.y, rx);
+      float ry = fmaf(ax, p.y, p.y);
+      ry = fmaf(ay, p.x, ry);
+      ry = fmaf(cx, q.y, ry);
+      ry = fmaf(cy, q.x, ry);
+      v[j] = make_float2(rx, ry);
+    }
+
+    if (rec) {
+      const int slot = (n + 1) / d.record_every - 1;
+      const float2 g = *recph;
+      float s = 0.f;
+      float2* r0 = d.records ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float2 p = v[j];
+        s = fmaf(p.x, p.x, fmaf(p.y, p.y, s));
+        if (r0) r0[t + j * T] = make_float2(fmaf(p.x, g.x, -(p.y * g.y)), fmaf(p.x, g.y, p.y * g.x));
+      }
+      if (d.powers) {
+        double ds = s;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, off);
+        if (lane == 0) red[warp] = ds;
+        if (lead) pending_slot = slot;
+      }
+    }
+  }
+
+  __syncthreads();
+  if (lead && pending_slot >= 0) {
+    double s = 0.0;
+    for (int w = 0; w < C::WARPS; ++w) s += red[w];
+    d.powers[2 * pending_slot + band] = s * d.dx_um;
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j) d.state[band * N + t + j * T] = v[j];
+  if (timed_out && lead) atomicOr(status, kStatusWaitTimeout);
+  cluster.sync();   // the peer may still read our exchange buffer: stay resident
+}
+
+}  // namespace bpm

@@ -4,6 +4,7 @@
 
 #include "fused_kernel.cuh"
 #include "fused2_kernel.cuh"
+#include "fused3_kernel.cuh"
 
 namespace bpm {
 
@@ -50,7 +51,34 @@ int fused2_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
   return BPM_OK;
 }
 
+// 2-CTA cluster kernel (one row per cluster, one band per CTA).
+template <int LOGN, bool EX>
+int fused3_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const float4* d_tw,
+                       int* d_status, cudaStream_t st) {
+  using C = F3Cfg<LOGN>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(fused3_march_kernel<LOGN, EX>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused3)");
+    configured = true;
+  }
+  fused3_march_kernel<LOGN, EX><<<2 * n_rows, C::T, C::SMEM, st>>>(d_rows, n_rows, steps, d_tw,
+                                                                  d_status);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "fused3 march launch");
+  return BPM_OK;
+}
+
 }  // namespace bpm
+
+#define BPM_INSTANTIATE_FUSED3(L)                                                 \
+  namespace bpm {                                                                 \
+  int fused3_launch_##L(const RowDescF32* r, int n, int s, const float4* tw,     \
+                        int* status, cudaStream_t st) {                           \
+    return fused3_launch_impl<L, kFusedExactConstants>(r, n, s, tw, status, st);  \
+  }                                                                               \
+  }
 
 #define BPM_INSTANTIATE_FUSED2(L)                                                 \
   namespace bpm {                                                                 \
