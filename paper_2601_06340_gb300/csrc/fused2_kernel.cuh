@@ -44,7 +44,9 @@ struct F2Cfg {
   static constexpr int OFF_MBAR = OFF_PH + ROWS * N * 8;
   static constexpr int OFF_RECPH = OFF_MBAR + ROWS * 8;
   static constexpr int OFF_RED = OFF_RECPH + ROWS * 8;                // [ROWS][WPR][2] double
-  static constexpr int SMEM = OFF_RED + ROWS * WPR * 2 * 8;
+  static constexpr int S1 = NP >= 3 ? (N >> 8) : 1;                   // pass-1 group offsets
+  static constexpr int OFF_TW1 = OFF_RED + ROWS * WPR * 2 * 8;        // [S1][16] float2
+  static constexpr int SMEM = OFF_TW1 + S1 * 16 * 8;
   static_assert(LOGN >= 8 && LOGN <= 12, "band-per-thread kernel covers 256..4096");
   __host__ __device__ static constexpr int radix(int p) { return p < NP - 1 ? 16 : RL; }
   __host__ __device__ static constexpr int len(int p) { return N >> (4 * p); }
@@ -125,21 +127,32 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
   if (t == 0 && band == 0) mbar_init(bar);
   fence_mbar_init();
 
-  // Register twiddles: pass 0 (group o = t) and pass 1 (o = t mod S1).
-  float2 w0[15], w1[15];
+  // Twiddles: pass 0 (group o = t) in registers; pass 1 (o = t mod S1, only
+  // S1 distinct groups) from a small shared table W_{N/16}^{o j}.
+  float2 w0[15];
 #pragma unroll
   for (int j = 1; j < 16; ++j) {
     const float4 a = __ldg(&tw[t * j]);
     w0[j - 1] = make_float2(a.x, a.y);
-    if constexpr (NP >= 3) {
-      const float4 b = __ldg(&tw[((t % C::stride(1)) * j) << 4]);
-      w1[j - 1] = make_float2(b.x, b.y);
-    } else {
-      w1[j - 1] = make_float2(0.f, 0.f);
-    }
   }
+  float2* tw1 = reinterpret_cast<float2*>(smem + C::OFF_TW1);
+  for (int k = threadIdx.x; k < C::S1 * 16; k += blockDim.x) {
+    const float4 a = __ldg(&tw[((k >> 4) * (k & 15)) << 4]);
+    tw1[k] = make_float2(a.x, a.y);
+  }
+  const float2* w1 = tw1 + (t % C::S1) * 16 + 1;   // w1[j - 1] = W^{o j}, j >= 1
 
-  const float2* prop = d.prop + band * N;
+  // this thread's slice of (P - 1)/N in the last pass, for the whole launch
+  float2 pr[16];
+  {
+    constexpr int P = NP - 1;
+#pragma unroll
+    for (int i = 0; i < C::groups(P); ++i)
+#pragma unroll
+      for (int j = 0; j < RL; ++j)
+        pr[i * RL + j] = active ? __ldg(&d.prop[band * N + f2_pos<LOGN, P>(t + i * T, j)])
+                                : make_float2(0.f, 0.f);
+  }
   float2 v[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j)
@@ -188,17 +201,14 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
     }
     // last pass: forward DFT, (P - 1)/N, inverse DFT
     {
-      constexpr int P = NP - 1, G = C::groups(P);
+      constexpr int P = NP - 1;
       f2_load<LOGN, P>(buf, v, t);
       f2_dft<LOGN, P, false, EX>(v);
 #pragma unroll
-      for (int i = 0; i < G; ++i)
-#pragma unroll
-        for (int j = 0; j < RL; ++j) {
-          const float2 dd = __ldg(&prop[f2_pos<LOGN, P>(t + i * T, j)]);
-          const float2 x = v[i * RL + j];
-          v[i * RL + j] = make_float2(fmaf(x.x, dd.x, -(x.y * dd.y)), fmaf(x.x, dd.y, x.y * dd.x));
-        }
+      for (int k = 0; k < 16; ++k) {
+        const float2 dd = pr[k], x = v[k];
+        v[k] = make_float2(fmaf(x.x, dd.x, -(x.y * dd.y)), fmaf(x.x, dd.y, x.y * dd.x));
+      }
       f2_dft<LOGN, P, true, EX>(v);
       f2_store<LOGN, P>(buf, v, t);
       __syncthreads();

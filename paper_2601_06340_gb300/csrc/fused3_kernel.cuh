@@ -8,10 +8,11 @@
 //     CTA per SM a thread can keep in registers its 16 points, the step's
 //     original field, its table twiddles and its slice of the propagator
 //     table (loaded once per launch);
-//   * the coupling partner psi_p(other band) is read from the peer CTA's
-//     shared memory (distributed shared memory) after one cluster barrier
-//     per step; the exchange buffer alternates between two halves by step
-//     parity, so a step never overwrites what the peer may still be reading;
+//   * each CTA writes its psi_p straight into the peer CTA's shared memory
+//     (distributed shared memory) and reads the partner band from its own
+//     after one cluster barrier per step; the exchange buffer alternates
+//     between two halves by step parity, so a write never lands on values
+//     the peer may still be reading;
 //   * each CTA fetches the strain/mask slice of the step into its own shared
 //     memory with a bulk asynchronous copy on an mbarrier (bounded wait).
 #pragma once
@@ -65,7 +66,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::OFF_MBAR);
   float2* recph = reinterpret_cast<float2*>(smem + C::OFF_RECPH);
   double* red = reinterpret_cast<double*>(smem + C::OFF_RED);
-  const float2* xpeer = cluster.map_shared_rank(xb, band ^ 1);
+  float2* xpeer = cluster.map_shared_rank(xb, band ^ 1);
 
   if (lead) mbar_init(bar);
   fence_mbar_init();
@@ -154,7 +155,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
     f2_load<LOGN, 0>(buf, v, t);
     f2_twiddle<true>(v, w0);
     dft<16, true, EX>(v);
-    float2* xo = xb + (it & 1) * N;
+    // push psi_p into the peer's exchange buffer (remote stores do not
+    // stall the writer); after the barrier the partner band is local.
+    float2* xo = xpeer + (it & 1) * N;
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       v[j] = make_float2(org[j].x + v[j].x, org[j].y + v[j].y);
@@ -163,7 +166,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
     cluster.sync();   // both bands' psi_p of this step are published
 
     if (!mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
-    const float2* xi = xpeer + (it & 1) * N;
+    const float2* xi = xb + (it & 1) * N;
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       const float2 q = xi[t + j * T];

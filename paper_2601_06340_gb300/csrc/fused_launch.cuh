@@ -2,14 +2,23 @@
 // separate translation units so they compile in parallel).
 #pragma once
 
+#include <cstdlib>
+
 #include "fused_kernel.cuh"
 #include "fused2_kernel.cuh"
 #include "fused3_kernel.cuh"
 
 namespace bpm {
 
-// Butterfly-constant policy of the band-per-thread kernel.
-constexpr bool kFusedExactConstants = true;
+// Butterfly-constant policy: hi+lo constants (default) unless BPM_FUSED_EXACT=0.
+inline bool fused_exact_constants() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("BPM_FUSED_EXACT");
+    v = (e && e[0] == '0') ? 0 : 1;
+  }
+  return v == 1;
+}
 
 template <int LOGN>
 int fused_launch_impl(const RowDescF32* d_rows, int n_rows, int steps,
@@ -76,7 +85,9 @@ int fused3_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
   namespace bpm {                                                                 \
   int fused3_launch_##L(const RowDescF32* r, int n, int s, const float4* tw,     \
                         int* status, cudaStream_t st) {                           \
-    return fused3_launch_impl<L, kFusedExactConstants>(r, n, s, tw, status, st);  \
+    return fused_exact_constants()                                                \
+               ? fused3_launch_impl<L, true>(r, n, s, tw, status, st)             \
+               : fused3_launch_impl<L, false>(r, n, s, tw, status, st);           \
   }                                                                               \
   }
 
@@ -84,7 +95,9 @@ int fused3_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
   namespace bpm {                                                                 \
   int fused2_launch_##L(const RowDescF32* r, int n, int s, const float4* tw,     \
                         int* status, cudaStream_t st) {                           \
-    return fused2_launch_impl<L, kFusedExactConstants>(r, n, s, tw, status, st);  \
+    return fused_exact_constants()                                                \
+               ? fused2_launch_impl<L, true>(r, n, s, tw, status, st)             \
+               : fused2_launch_impl<L, false>(r, n, s, tw, status, st);           \
   }                                                                               \
   }
 
