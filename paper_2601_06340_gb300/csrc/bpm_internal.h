@@ -122,6 +122,7 @@ int launch_finish_f64(const double2* state, double2* out, const double* gphase,
 int launch_omega_to_t(const void* d_in, void* d_out, int nb, int nx,
                       int precision, cudaStream_t st);
 int fused_smem_bytes(int logn);
+int fused_rows_resident(int logn, int n_rows);
 int fused_rows_per_cta(int logn);
 int fused_threads(int logn);
 

@@ -1,5 +1,6 @@
 // C ABI: plan lifetime, crystal/strain description, synchronous and
 // stream-ordered marches.  See include/bpm.h for the contract.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -65,6 +66,8 @@ struct PlanAux {
   double* d_pow = nullptr;    // host-API powers buffer
   size_t pow_bytes = 0;
   double2* d_g = nullptr;     // [B] common phase factors
+  RowDescF32* d_sched = nullptr;  // rotated launch schedule
+  size_t sched_cap = 0;
 };
 
 static PlanAux* aux_of(bpm_plan_s* plan);
@@ -120,6 +123,57 @@ void phase_factors(const bpm_plan_s* plan, int steps, std::vector<double2>* out)
   }
 }
 
+// More rows than the GPU keeps resident: split the march into equal chunks
+// and issue launches of exactly `resident` (row, chunk) items taken in
+// round-robin order (item i = row i mod B, chunk i div B).  Every launch is
+// full, each row's chunks run in order (item i + B lands in a later launch),
+// no row appears twice in a launch, and rows sweeping the same z-range share
+// their strain slices in L2.  A remainder shorter than a chunk runs as a
+// second round of the same kind.
+static int launch_rotated(bpm_plan_s* plan, PlanAux* aux, const std::vector<RowDescF32>& rows,
+                          int n_begin, int steps, int resident, cudaStream_t st) {
+  const int nb = plan->nb;
+  const int chunk = std::max(std::min(steps, 64), steps / 24);
+  const int full = steps / chunk, rem = steps - full * chunk;
+  std::vector<RowDescF32> sched;
+  struct Launch { size_t off; int count; int steps; };
+  std::vector<Launch> launches;
+  auto round = [&](int c0, int c1, int len) {
+    const long items = long(nb) * (c1 - c0);
+    for (long i = 0; i < items; i += resident) {
+      const int cnt = int(std::min<long>(resident, items - i));
+      launches.push_back({sched.size(), cnt, len});
+      for (int k = 0; k < cnt; ++k) {
+        const long it = i + k;
+        RowDescF32 d = rows[it % nb];
+        d.n_begin = n_begin + int(c0 + it / nb) * chunk;
+        d.n_end = d.n_begin + len;
+        sched.push_back(d);
+      }
+    }
+  };
+  round(0, full, chunk);
+  if (rem > 0) round(full, full + 1, rem);
+  if (aux->sched_cap < sched.size()) {
+    if (aux->d_sched) cudaFree(aux->d_sched);
+    aux->d_sched = nullptr;
+    aux->sched_cap = 0;
+    int rc = dev_alloc(plan, reinterpret_cast<void**>(&aux->d_sched),
+                       sched.size() * sizeof(RowDescF32), "launch schedule");
+    if (rc != BPM_OK) return rc;
+    aux->sched_cap = sched.size();
+  }
+  cudaError_t e = cudaMemcpyAsync(aux->d_sched, sched.data(), sched.size() * sizeof(RowDescF32),
+                                  cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "upload launch schedule");
+  for (const Launch& l : launches) {
+    int rc = launch_fused(plan->logn, aux->d_sched + l.off, l.count, l.steps,
+                          static_cast<const float4*>(plan->d_tw), plan->d_status, st);
+    if (rc != BPM_OK) return rc;
+  }
+  return BPM_OK;
+}
+
 // Enqueue the march of all rows on `st`.  state: the buffer holding the
 // state at n_begin (c64 for FP32, the plan's d_state for FP64); outputs as
 // documented for bpm_propagate_device.
@@ -137,11 +191,17 @@ static int enqueue_march(bpm_plan_s* plan, PlanAux* aux, void* state, void* d_re
     std::vector<RowDescF32> rows;
     fused_rows(plan, static_cast<float2*>(state), static_cast<float2*>(d_rec), d_pw, n_begin,
                n_end, &rows);
-    e = cudaMemcpyAsync(plan->d_rows, rows.data(), sizeof(RowDescF32) * rows.size(),
-                        cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "upload row descriptors");
-    int rc = launch_fused(plan->logn, static_cast<const RowDescF32*>(plan->d_rows), plan->nb,
-                          steps, static_cast<const float4*>(plan->d_tw), plan->d_status, st);
+    const int resident = fused_rows_resident(plan->logn, plan->nb);
+    int rc = BPM_OK;
+    if (resident <= 0 || plan->nb <= resident) {
+      e = cudaMemcpyAsync(plan->d_rows, rows.data(), sizeof(RowDescF32) * rows.size(),
+                          cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) return cuda_fail(e, "upload row descriptors");
+      rc = launch_fused(plan->logn, static_cast<const RowDescF32*>(plan->d_rows), plan->nb,
+                        steps, static_cast<const float4*>(plan->d_tw), plan->d_status, st);
+    } else {
+      rc = launch_rotated(plan, aux, rows, n_begin, steps, resident, st);
+    }
     if (rc != BPM_OK) return rc;
     return launch_finish_f32(static_cast<const float2*>(state),
                              out_c128 ? static_cast<double2*>(out) : nullptr,
@@ -511,6 +571,7 @@ int bpm_destroy(bpm_plan_t plan) {
   if (aux->d_rec) cudaFree(aux->d_rec);
   if (aux->d_pow) cudaFree(aux->d_pow);
   if (aux->d_g) cudaFree(aux->d_g);
+  if (aux->d_sched) cudaFree(aux->d_sched);
   free_plan_memory(plan);
   {
     std::lock_guard<std::mutex> lk(g_aux_mu);

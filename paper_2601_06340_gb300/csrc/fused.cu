@@ -21,10 +21,16 @@ BPM_DECLARE_FUSED2(12) BPM_DECLARE_FUSED(13)
   int fused3_launch_##L(const RowDescF32*, int, int, const float4*, int*,        \
                         cudaStream_t);
 BPM_DECLARE_FUSED3(10) BPM_DECLARE_FUSED3(11) BPM_DECLARE_FUSED3(12)
+int fused_rows_resident_3(); int fused_rows_resident_4(); int fused_rows_resident_5();
+int fused_rows_resident_6(); int fused_rows_resident_7(); int fused2_rows_resident_8();
+int fused2_rows_resident_9(); int fused2_rows_resident_10(); int fused2_rows_resident_11();
+int fused2_rows_resident_12(); int fused_rows_resident_13();
 
 // Layout choice: a 2-CTA cluster per row (a whole SM per band) when every
 // row of the launch gets its own pair of SMs, else one CTA per row.  The
 // environment variable BPM_FUSED_LAYOUT=cta|cluster forces one of them.
+static int sm_count();
+
 static bool use_cluster_layout(int logn, int n_rows) {
   if (logn < 10 || logn > 12) return false;
   static int forced = -2;
@@ -33,14 +39,7 @@ static bool use_cluster_layout(int logn, int n_rows) {
     forced = !v ? -1 : (std::strcmp(v, "cluster") == 0 ? 1 : (std::strcmp(v, "cta") == 0 ? 0 : -1));
   }
   if (forced >= 0) return forced == 1;
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
-  return 2 * n_rows <= sms;
+  return 2 * n_rows <= sm_count();
 }
 
 int launch_fused(int logn, const RowDescF32* d_rows, int n_rows, int steps,
@@ -97,6 +96,43 @@ static void fused_cfg(int logn, int* smem, int* rows, int* threads) {
     case 12: cfg2_of<12>(smem, rows, threads); break;
     default: cfg_of<13>(smem, rows, threads); break;
   }
+}
+
+static int sm_count() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+// Rows of size 2^logn that one launch keeps resident on the whole GPU (one
+// CTA per row layout).  0 when a launch of n_rows would use the cluster
+// layout, where every row already has its own SMs.
+int fused_rows_resident(int logn, int n_rows) {
+  if (use_cluster_layout(logn, n_rows)) return 0;
+  static int cache[kMaxLogN + 1] = {};
+  if (cache[logn] == 0) {
+    int r = 1;
+    switch (logn) {
+      case 3: r = fused_rows_resident_3(); break;
+      case 4: r = fused_rows_resident_4(); break;
+      case 5: r = fused_rows_resident_5(); break;
+      case 6: r = fused_rows_resident_6(); break;
+      case 7: r = fused_rows_resident_7(); break;
+      case 8: r = fused2_rows_resident_8(); break;
+      case 9: r = fused2_rows_resident_9(); break;
+      case 10: r = fused2_rows_resident_10(); break;
+      case 11: r = fused2_rows_resident_11(); break;
+      case 12: r = fused2_rows_resident_12(); break;
+      default: r = fused_rows_resident_13(); break;
+    }
+    cache[logn] = r * sm_count();
+  }
+  return cache[logn];
 }
 
 int fused_smem_bytes(int logn) { int a, b, c; fused_cfg(logn, &a, &b, &c); return a; }

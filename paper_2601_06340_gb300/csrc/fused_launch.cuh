@@ -60,6 +60,18 @@ int fused2_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
   return BPM_OK;
 }
 
+// Resident CTAs per SM of a kernel with its launch shape.
+template <typename K>
+int blocks_per_sm(K kernel, int threads, int smem) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n > 0 ? n : 1;
+}
+
 // 2-CTA cluster kernel (one row per cluster, one band per CTA).
 template <int LOGN, bool EX>
 int fused3_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const float4* d_tw,
@@ -93,6 +105,11 @@ int fused3_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
 
 #define BPM_INSTANTIATE_FUSED2(L)                                                 \
   namespace bpm {                                                                 \
+  int fused2_rows_resident_##L() {                                                \
+    using C = F2Cfg<L>;                                                           \
+    return blocks_per_sm(fused2_march_kernel<L, true>, C::THREADS, C::SMEM) *     \
+           C::ROWS;                                                               \
+  }                                                                               \
   int fused2_launch_##L(const RowDescF32* r, int n, int s, const float4* tw,     \
                         int* status, cudaStream_t st) {                           \
     return fused_exact_constants()                                                \
@@ -103,6 +120,10 @@ int fused3_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
 
 #define BPM_INSTANTIATE_FUSED(L)                                                  \
   namespace bpm {                                                                 \
+  int fused_rows_resident_##L() {                                                 \
+    using C = FusedCfg<L>;                                                        \
+    return blocks_per_sm(fused_march_kernel<L>, C::THREADS, C::SMEM) * C::ROWS;   \
+  }                                                                               \
   int fused_launch_##L(const RowDescF32* r, int n, int s, const float4* tw,      \
                        int* status, cudaStream_t st) {                            \
     return fused_launch_impl<L>(r, n, s, tw, status, st);                         \

@@ -232,3 +232,20 @@ def test_omega_to_t_matches_oracle(bpm_lib):
         torch.cuda.synchronize()
         got = y.cpu().numpy()
         assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref))
+
+
+def test_rotated_schedule_matches_single_launch(bpm_lib):
+    """200 rows of N=4096 exceed what one launch keeps resident: the march is
+    split into (row, chunk) launches (64-step chunks plus a 36-step
+    remainder round).  Rows must come out bit-identical to a batch small
+    enough for one launch, and match the oracle."""
+    big = inputs.pulse_batched(nx=4096, nz=100, n_energy=200)
+    small = inputs.pulse_batched(nx=4096, nz=100, n_energy=200)
+    small.energies_ev = small.energies_ev[:100]
+    small.psi0 = small.psi0[:100]
+    out_big = run_gpu(big, FP32)
+    out_small = run_gpu(small, FP32)
+    assert np.array_equal(out_big.psi[:100], out_small.psi)
+    rows = [3, 150, 199]
+    ref = run_ref(big, rows=rows)
+    assert max(band_errors(out_big.psi[rows], ref.psi)) <= 2e-5
