@@ -172,7 +172,10 @@ int bpm_omega_to_t_device(const void* d_in, void* d_out, int32_t n_energy,
  * until bpm_poll returns BPM_OK or an error.  Requests are admitted as
  * device memory (within the configured budget) and launch slots free up;
  * admitted requests advance together in epochs of fused launches, grouped by
- * transverse size.  BPM_ERR_BUSY if the queue is full.  bpm_poll waits up
+ * transverse size.  A plan carries at most one request at a time.
+ * BPM_ERR_BUSY if the queue is full or the plan already has a request in
+ * flight; BPM_ERR_OOM if the request alone exceeds the memory budget.
+ * bpm_poll waits up
  * to timeout_ms (0 = just test, <0 = wait forever) and returns BPM_OK once
  * (outputs written), BPM_NOT_READY, or the request's error. */
 int bpm_submit(bpm_plan_t plan, const double* psi_in, double* psi_out,

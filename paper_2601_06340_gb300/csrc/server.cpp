@@ -396,6 +396,8 @@ int bpm_submit(bpm_plan_t plan, const double* psi_in, double* psi_out, void* rec
   r->powers = powers;
   {
     std::lock_guard<std::mutex> lk(plan->mu);
+    if (plan->pending > 0)
+      return fail(BPM_ERR_BUSY, "the plan already has a request in flight");
     r->footprint = footprint_of(plan, records != nullptr && plan->n_rec > 0);
   }
   std::lock_guard<std::mutex> lk(s.mu);
