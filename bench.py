@@ -123,6 +123,63 @@ def rel_l2_bands(got, ref):
 
 
 # --------------------------------------------------------------------------
+def serving_run(n_requests: int, rate: float, warm: int = 40, n_check: int = 8):
+    """Replay a seeded Poisson stream of mixed solves (Nx up to 8192) in real
+    time through bpm_submit / bpm_poll; latency = completion - submission as
+    stamped by the server.  The first `warm` requests are excluded from the
+    statistics.  `n_check` sampled requests are re-run alone for parity."""
+    import threading
+    from paper_2601_06340_gb300 import binding, inputs
+    FP32 = binding.BPM_FP32_FUSED
+    reqs = inputs.serving_requests(n_requests, rate_per_s=rate,
+                                   nx_choices=(512, 1024, 2048, 4096, 8192))
+    binding.bpm_server_configure(0.6, 256, 256, 100000)
+    tickets = [None] * len(reqs)
+    outs = [np.empty_like(r.workload.psi0) for r in reqs]
+    plans = [None] * len(reqs)
+    done = [None] * len(reqs)
+
+    def poller():
+        for i in range(len(reqs)):
+            while tickets[i] is None:
+                time.sleep(1e-4)
+            binding.bpm_poll(tickets[i], -1)
+            done[i] = binding.bpm_ticket_times(tickets[i])
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.perf_counter()
+    for i, r in enumerate(reqs):
+        wait = t0 + r.arrival_s - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        plans[i] = binding.Plan(r.workload, FP32)
+        tickets[i] = binding.bpm_submit(plans[i].handle, r.workload.psi0, outs[i])
+    th.join()
+    times = np.array(done[warm:])
+    lat_ms = (times[:, 2] - times[:, 0]) * 1e3
+    wait_ms = (times[:, 1] - times[:, 0]) * 1e3
+    span = times[:, 2].max() - times[:, 0].min()
+    cells = sum(r.workload.cell_updates for r in reqs[warm:])
+    rng = np.random.default_rng(7)
+    errs = []
+    for i in sorted(rng.choice(np.arange(warm, len(reqs)), n_check, replace=False)):
+        alone = plans[i].propagate(records=False, powers=False).psi
+        for b in range(2):
+            den = np.linalg.norm(alone[0, b])
+            if den > 0:
+                errs.append(float(np.linalg.norm(outs[i][0, b] - alone[0, b]) / den))
+    for p in plans:
+        p.close()
+    return {"requests": len(reqs) - warm, "warmup_requests": warm, "rate_per_s": rate,
+            "nx_choices": [512, 1024, 2048, 4096, 8192], "nz_range": [500, 20000],
+            "throughput": cells / span, "unit": UNIT,
+            "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
+                           "p99": float(np.percentile(lat_ms, 99)),
+                           "max": float(lat_ms.max())},
+            "queue_wait_ms_p99": float(np.percentile(wait_ms, 99)),
+            "alone_vs_mix_max_rel_l2": max(errs) if errs else None}
+
+
 def run_reference(args, rank, world):
     """FP64 oracle on the host cores: each step is a bounded sample (the
     first `sample_steps` z-steps of the march)."""
@@ -176,6 +233,13 @@ def run_gpu(args, rank, world):
         t = torch.tensor([x], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
+
+    if args.only == "serving":
+        if rank == 0:
+            print(json.dumps({"only": "serving",
+                              **serving_run(args.serving_requests, args.serving_rate)}),
+                  flush=True)
+        return
 
     if args.only == "batched":
         wb = inputs.pulse_batched()
@@ -324,6 +388,11 @@ def run_gpu(args, rank, world):
                    "ms_per_march": msb}
         planb.close()
 
+    # ---- serving: Poisson stream of mixed solves through submit/poll ------
+    serving = None
+    if not args.skip_serving and rank == 0:
+        serving = serving_run(args.serving_requests, args.serving_rate)
+
     # ---- roofline of the dominant kernel (fused march) ---------------------
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
@@ -360,6 +429,7 @@ def run_gpu(args, rank, world):
                            "rel_l2_err": err64, "tolerance": 1e-10,
                            "fused_speedup": value / value64},
             "batched": batched,
+            "serving": serving,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": 2 * args.steps,
@@ -379,7 +449,10 @@ def main():
     ap.add_argument("--ref-sample-steps", type=int, default=1000)
     ap.add_argument("--skip-oracle", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
-    ap.add_argument("--only", default="all", choices=["all", "fused", "batched"],
+    ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=440)
+    ap.add_argument("--serving-rate", type=float, default=200.0)
+    ap.add_argument("--only", default="all", choices=["all", "fused", "batched", "serving"],
                     help="time only the fused single-solve march, or only the 256-energy "
                          "batch (used for profiling runs)")
     args = ap.parse_args()

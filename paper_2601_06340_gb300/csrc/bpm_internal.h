@@ -14,7 +14,11 @@
 namespace bpm {
 
 constexpr int kMinLogN = 3;
-constexpr int kMaxLogN = 13;          // nx <= 8192 in one CTA
+constexpr int kMaxLogN = 14;          // nx <= 16384
+// N >= 2^kSplitLogN: each band is split over a cluster of N/4096 CTAs
+// (interleaved samples), and the strain stream / propagator tables of FP32
+// plans are stored per part (see fused4_kernel.cuh).
+constexpr int kSplitLogN = 13;
 constexpr double kTwoPi = 6.283185307179586;
 constexpr double kHcEvAngstrom = 12398.419843320026;
 
@@ -106,7 +110,9 @@ void twiddle_table_f64(int n, std::vector<double2>* out);
 std::vector<int> fft_output_order(int logn);   // position -> frequency index
 
 // Kernels (launchers in *.cu).
-int prepare_slices(bpm_plan_s* plan, cudaStream_t st);
+// Prepare mask + strain phasor on `st`; with sync = false the call returns
+// once the work is enqueued (temporaries, if any, still force a wait).
+int prepare_slices(bpm_plan_s* plan, cudaStream_t st, bool sync = true);
 int launch_fused(int logn, const RowDescF32* d_rows, int n_rows, int steps,
                  const float4* d_tw, int* d_status, cudaStream_t st);
 int plain_march(bpm_plan_s* plan, int n_begin, int n_end, int n_phase0, void* d_records,

@@ -547,11 +547,19 @@ int bpm_fetch_slices(bpm_plan_t plan, uint8_t* mask, double* phasor) {
     cudaError_t e = cudaMemcpy(buf.data(), plan->d_phasor, cells * 16, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "fetch slices");
   }
+  const int parts = (plan->precision == BPM_FP32_FUSED && plan->logn >= kSplitLogN)
+                        ? (plan->nx >> 12) : 1;
+  const size_t nx = plan->nx, m = nx / parts;
   for (size_t c = 0; c < cells; ++c) {
-    if (mask) mask[c] = (buf[2 * c] != 0.0 || buf[2 * c + 1] != 0.0) ? 1 : 0;
+    size_t src = c;
+    if (parts > 1) {
+      const size_t n = c / nx, j = c % nx;
+      src = n * nx + (j % parts) * m + j / parts;
+    }
+    if (mask) mask[c] = (buf[2 * src] != 0.0 || buf[2 * src + 1] != 0.0) ? 1 : 0;
     if (phasor) {
-      phasor[2 * c] = buf[2 * c];
-      phasor[2 * c + 1] = buf[2 * c + 1];
+      phasor[2 * c] = buf[2 * src];
+      phasor[2 * c + 1] = buf[2 * src + 1];
     }
   }
   return BPM_OK;

@@ -4,6 +4,7 @@
 
 #include "fused_kernel.cuh"
 #include "fused2_kernel.cuh"
+#include "fused4_kernel.cuh"
 
 namespace bpm {
 
@@ -16,7 +17,9 @@ namespace bpm {
 BPM_DECLARE_FUSED(3) BPM_DECLARE_FUSED(4) BPM_DECLARE_FUSED(5)
 BPM_DECLARE_FUSED(6) BPM_DECLARE_FUSED(7) BPM_DECLARE_FUSED2(8)
 BPM_DECLARE_FUSED2(9) BPM_DECLARE_FUSED2(10) BPM_DECLARE_FUSED2(11)
-BPM_DECLARE_FUSED2(12) BPM_DECLARE_FUSED(13)
+BPM_DECLARE_FUSED2(12)
+int fused4_launch_13(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
+int fused4_launch_14(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
 #define BPM_DECLARE_FUSED3(L)                                                    \
   int fused3_launch_##L(const RowDescF32*, int, int, const float4*, int*,        \
                         cudaStream_t);
@@ -24,7 +27,7 @@ BPM_DECLARE_FUSED3(10) BPM_DECLARE_FUSED3(11) BPM_DECLARE_FUSED3(12)
 int fused_rows_resident_3(); int fused_rows_resident_4(); int fused_rows_resident_5();
 int fused_rows_resident_6(); int fused_rows_resident_7(); int fused2_rows_resident_8();
 int fused2_rows_resident_9(); int fused2_rows_resident_10(); int fused2_rows_resident_11();
-int fused2_rows_resident_12(); int fused_rows_resident_13();
+int fused2_rows_resident_12();
 
 // Layout choice: a 2-CTA cluster per row (a whole SM per band) when every
 // row of the launch gets its own pair of SMs, else one CTA per row.  The
@@ -63,9 +66,17 @@ int launch_fused(int logn, const RowDescF32* d_rows, int n_rows, int steps,
     case 10: return fused2_launch_10(d_rows, n_rows, steps, d_tw, d_status, st);
     case 11: return fused2_launch_11(d_rows, n_rows, steps, d_tw, d_status, st);
     case 12: return fused2_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
-    case 13: return fused_launch_13(d_rows, n_rows, steps, d_tw, d_status, st);
+    case 13: return fused4_launch_13(d_rows, n_rows, steps, d_tw, d_status, st);
+    case 14: return fused4_launch_14(d_rows, n_rows, steps, d_tw, d_status, st);
     default: return fail(BPM_ERR_INVALID, "unsupported transform size");
   }
+}
+
+template <int P>
+static void cfg4_of(int* smem, int* rows, int* threads) {
+  *smem = F4Cfg<P>::SMEM;
+  *rows = 1;
+  *threads = F4Cfg<P>::T;
 }
 
 template <int L>
@@ -94,7 +105,8 @@ static void fused_cfg(int logn, int* smem, int* rows, int* threads) {
     case 10: cfg2_of<10>(smem, rows, threads); break;
     case 11: cfg2_of<11>(smem, rows, threads); break;
     case 12: cfg2_of<12>(smem, rows, threads); break;
-    default: cfg_of<13>(smem, rows, threads); break;
+    case 13: cfg4_of<2>(smem, rows, threads); break;
+    default: cfg4_of<4>(smem, rows, threads); break;
   }
 }
 
@@ -113,7 +125,7 @@ static int sm_count() {
 // CTA per row layout).  0 when a launch of n_rows would use the cluster
 // layout, where every row already has its own SMs.
 int fused_rows_resident(int logn, int n_rows) {
-  if (use_cluster_layout(logn, n_rows)) return 0;
+  if (logn >= kSplitLogN || use_cluster_layout(logn, n_rows)) return 0;
   static int cache[kMaxLogN + 1] = {};
   if (cache[logn] == 0) {
     int r = 1;
@@ -127,8 +139,7 @@ int fused_rows_resident(int logn, int n_rows) {
       case 9: r = fused2_rows_resident_9(); break;
       case 10: r = fused2_rows_resident_10(); break;
       case 11: r = fused2_rows_resident_11(); break;
-      case 12: r = fused2_rows_resident_12(); break;
-      default: r = fused_rows_resident_13(); break;
+      default: r = fused2_rows_resident_12(); break;
     }
     cache[logn] = r * sm_count();
   }

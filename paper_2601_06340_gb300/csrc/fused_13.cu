@@ -1,2 +1,2 @@
 #include "fused_launch.cuh"
-BPM_INSTANTIATE_FUSED(13)
+BPM_INSTANTIATE_FUSED4(2, 13)

@@ -7,6 +7,7 @@
 #include "fused_kernel.cuh"
 #include "fused2_kernel.cuh"
 #include "fused3_kernel.cuh"
+#include "fused4_kernel.cuh"
 
 namespace bpm {
 
@@ -91,7 +92,36 @@ int fused3_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
   return BPM_OK;
 }
 
+// Split-band cluster kernel for N = 4096 P (cluster of 2P CTAs per row).
+template <int P, bool EX>
+int fused4_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const float4* d_tw,
+                       int* d_status, cudaStream_t st) {
+  using C = F4Cfg<P>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(fused4_march_kernel<P, EX>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused4)");
+    configured = true;
+  }
+  fused4_march_kernel<P, EX><<<2 * P * n_rows, C::T, C::SMEM, st>>>(d_rows, n_rows, steps, d_tw,
+                                                                   d_status);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "fused4 march launch");
+  return BPM_OK;
+}
+
 }  // namespace bpm
+
+#define BPM_INSTANTIATE_FUSED4(P, L)                                              \
+  namespace bpm {                                                                 \
+  int fused4_launch_##L(const RowDescF32* r, int n, int s, const float4* tw,     \
+                        int* status, cudaStream_t st) {                           \
+    return fused_exact_constants()                                                \
+               ? fused4_launch_impl<P, true>(r, n, s, tw, status, st)             \
+               : fused4_launch_impl<P, false>(r, n, s, tw, status, st);           \
+  }                                                                               \
+  }
 
 #define BPM_INSTANTIATE_FUSED3(L)                                                 \
   namespace bpm {                                                                 \

@@ -245,7 +245,8 @@ constexpr int kNoAllocMaxRows = 1024;
 constexpr int kNoAllocMaxDevices = 64;
 
 static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocMaxComplex];
-static __device__ __align__(256) double2 g_noalloc_twiddles[1 << kMaxLogN];
+constexpr int kNoAllocMaxLogN = 13;
+static __device__ __align__(256) double2 g_noalloc_twiddles[1 << kNoAllocMaxLogN];
 static __device__ __align__(256) RowDescF64 g_noalloc_rows[kNoAllocMaxRows];
 
 struct NoAllocSymbols {
@@ -292,9 +293,9 @@ extern "C" int bpm_march_f64_noalloc(void* d_psi, int32_t nx, int32_t n_rows,
   using namespace bpm;
   if (!d_psi || !d_prop || !d_coupling || !d_phasor)
     return fail(BPM_ERR_INVALID, "noalloc march: a buffer is NULL");
-  if (nx < 8 || nx > (1 << kMaxLogN) || (nx & (nx - 1)))
+  if (nx < 8 || nx > (1 << kNoAllocMaxLogN) || (nx & (nx - 1)))
     return fail(BPM_ERR_INVALID, "noalloc march: nx must be a power of two in [8, " +
-                                     std::to_string(1 << kMaxLogN) + "]");
+                                     std::to_string(1 << kNoAllocMaxLogN) + "]");
   if (n_rows < 1 || n_rows > kNoAllocMaxRows)
     return fail(BPM_ERR_INVALID, "noalloc march: n_rows must be in [1, " +
                                      std::to_string(kNoAllocMaxRows) + "]");

@@ -158,6 +158,25 @@ std::vector<int> fft_output_order(int logn) {
 void fused_prop_table(const bpm_plan_s* plan, int row, std::vector<float2>* out) {
   const EnergyConsts& c = plan->ec[row];
   int n = plan->nx;
+  if (plan->logn >= kSplitLogN) {
+    // [band][part r][local position]: the local 4096-point transform's
+    // digit-reversed position pos holds spectral index k(pos) + 4096 r.
+    const int m = 1 << 12, parts = n / m;
+    std::vector<int> local = fft_output_order(12);
+    out->assign(2 * size_t(n), float2{0.f, 0.f});
+    for (int band = 0; band < 2; ++band) {
+      int sign = band == 0 ? +1 : -1;
+      for (int r = 0; r < parts; ++r)
+        for (int pos = 0; pos < m; ++pos) {
+          double q = fftfreq_q(local[pos] + m * r, n, c.dxh);
+          double ph = c.dzh * delta_q(q, c.s, c.c, sign);
+          cd dd = expm1_i(cd(ph, 0.0)) * (1.0 / double(n));
+          (*out)[size_t(band) * n + size_t(r) * m + pos] =
+              float2{float(dd.real()), float(dd.imag())};
+        }
+    }
+    return;
+  }
   std::vector<int> order = fft_output_order(plan->logn);
   out->assign(2 * size_t(n), float2{0.f, 0.f});
   double inv_n = 1.0 / double(n);

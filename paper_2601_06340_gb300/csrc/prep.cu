@@ -32,6 +32,7 @@ struct PrepParams {
   double h;
   float2* out32;
   double2* out64;
+  int parts;     // > 1: out32 row layout [parts][nx/parts], column j at (j % parts, j / parts)
 };
 
 __device__ bool inside_cell(const PrepParams& p, int n, int j, double x, double z) {
@@ -92,14 +93,21 @@ __global__ void prep_kernel(PrepParams p) {
       const double theta = p.h * strain_ux(p, n, j, x, z);
       sincos(fmod(theta, 6.283185307179586), &im, &re);
     }
-    if (p.out32) p.out32[c] = make_float2(float(re), float(im));
+    if (p.out32) {
+      size_t o = c;
+      if (p.parts > 1) {
+        const int m = p.nx / p.parts;
+        o = size_t(n) * p.nx + size_t(j % p.parts) * m + j / p.parts;
+      }
+      p.out32[o] = make_float2(float(re), float(im));
+    }
     if (p.out64) p.out64[c] = make_double2(re, im);
   }
 }
 
 }  // namespace
 
-int prepare_slices(bpm_plan_s* plan, cudaStream_t st) {
+int prepare_slices(bpm_plan_s* plan, cudaStream_t st, bool sync) {
   const size_t phasor_bytes = size_t(plan->nx) * plan->nz *
                               (plan->precision == BPM_FP32_FUSED ? 8 : 16);
   if (!plan->d_phasor) {
@@ -132,6 +140,8 @@ int prepare_slices(bpm_plan_s* plan, cudaStream_t st) {
   p.p2 = plan->sparams[2];
   p.p3 = plan->sparams[3];
   p.h = plan->h_per_um;
+  p.parts = 1;
+  if (plan->precision == BPM_FP32_FUSED && plan->logn >= kSplitLogN) p.parts = plan->nx >> 12;
   if (plan->precision == BPM_FP32_FUSED) p.out32 = static_cast<float2*>(plan->d_phasor);
   else p.out64 = static_cast<double2*>(plan->d_phasor);
 
@@ -167,12 +177,13 @@ int prepare_slices(bpm_plan_s* plan, cudaStream_t st) {
     prep_kernel<<<blocks, threads, 0, st>>>(p);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  const bool temporaries = d_mask || d_poly || d_ux;
+  if (e == cudaSuccess && (sync || temporaries)) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) rc = (e == cudaErrorMemoryAllocation) ? fail(BPM_ERR_OOM, "slice preparation: out of device memory")
                                                              : cuda_fail(e, "slice preparation");
-  cudaFree(d_mask);
-  cudaFree(d_poly);
-  cudaFree(d_ux);
+  if (d_mask) cudaFree(d_mask);
+  if (d_poly) cudaFree(d_poly);
+  if (d_ux) cudaFree(d_ux);
   if (rc == BPM_OK) plan->slices_dirty = false;
   return rc;
 }

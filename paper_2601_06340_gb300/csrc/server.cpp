@@ -1,21 +1,23 @@
 // Continuous-batching request server (bpm_submit / bpm_poll).
 //
-// A worker thread owns the device side.  Each loop iteration it
-//   1. admits queued requests in arrival order while the number of active
-//      requests and their device footprint stay within the configured
-//      limits (footprint = the request's state, records, powers and, if the
-//      plan has none yet, its strain-phasor stream);
-//   2. advances every active request by up to `epoch_steps` z-steps: rows
-//      of all active FP32 requests with the same transform size and the
-//      same step count in this epoch share one fused launch (one stream per
-//      transform size, so sizes overlap on the device); FP64 requests run
-//      their plain per-step march;
-//   3. retires finished requests: common phase, conversion to c128, copies
-//      to the caller's buffers, wake-up of pollers.
-// Requests that arrive while others run join at the next epoch boundary.
+// A worker thread owns the device side.  Requests wait in arrival order and
+// are admitted while the number of active requests and their device
+// footprint (state, staging, records, powers and, if the plan has none yet,
+// its strain-phasor stream) stay within the configured limits.  Active
+// requests are grouped into buckets by transform size (FP32) -- FP64
+// requests get a bucket each -- and every bucket runs its own pipeline on
+// its own stream: as soon as a bucket's previous epoch has finished (event
+// query, no device-wide wait), the worker retires the requests that are
+// done and launches the next epoch for the bucket's current members, so
+// requests that arrive while others run join at the next epoch of their
+// size, and sizes do not wait for each other.  All rows of one bucket with
+// the same remaining step count share one fused launch.  Device memory of
+// requests is allocated and released stream-ordered (cudaMallocAsync /
+// cudaFreeAsync), so retiring a request never stalls other buckets.
+//
 // A request's arithmetic does not depend on which other requests share its
-// launches (rows are independent and each row's work is the same code for
-// the same shape), so a result is the same alone and in the mix.
+// launches (rows are independent and each row runs the same code for the
+// same shape), so a result is the same alone and in the mix.
 #include <algorithm>
 #include <array>
 #include <chrono>
@@ -57,20 +59,33 @@ struct Request {
   // device side
   size_t footprint = 0;
   bool owns_phasor = false;
-  void* d_state = nullptr;     // c64 (FP32) or unused (FP64 uses the plan's state)
+  void* d_state = nullptr;     // c64 (FP32); FP64 requests march in their plan's state
   void* d_rec = nullptr;
   double* d_pow = nullptr;
   double2* d_g = nullptr;
   double2* d_out = nullptr;    // c128 staging
+  cudaEvent_t ready = nullptr; // staged and prepared on io_stream
   int n_done = 0;
+};
+using ReqPtr = std::shared_ptr<Request>;
+
+struct Bucket {
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr;
+  bool busy = false;
+  std::vector<ReqPtr> members;
+  std::vector<std::pair<ReqPtr, int>> launched;   // (request, steps) of the epoch in flight
+  RowDescF32* d_rows = nullptr;
+  size_t cap = 0;
+  int* d_status = nullptr;
 };
 
 struct Server {
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
-  std::deque<std::shared_ptr<Request>> queue;
-  std::vector<std::shared_ptr<Request>> active;
-  std::unordered_map<bpm_ticket_t, std::shared_ptr<Request>> tickets;
+  std::deque<ReqPtr> queue;
+  int n_active = 0;
+  std::unordered_map<bpm_ticket_t, ReqPtr> tickets;
   std::map<bpm_ticket_t, std::array<double, 3>> times;
   bpm_ticket_t next_id = 1;
   double mem_fraction = 0.6;
@@ -78,16 +93,11 @@ struct Server {
   size_t budget = 0, used = 0;
   bool started = false;
   std::thread worker;
-  std::map<int, cudaStream_t> streams;   // per transform size
-  cudaStream_t io_stream = nullptr;
-  RowDescF32* d_rows = nullptr;
-  size_t d_rows_cap = 0;
-  int* d_status = nullptr;
+  // worker-owned
+  std::map<long, Bucket> buckets;   // key: logn (FP32) or -(ticket id) (FP64)
+  cudaStream_t io_stream = nullptr;    // admission: staging and strain preparation
+  cudaStream_t out_stream = nullptr;   // retirement: finishing and copies out
   float4* d_tw[kMaxLogN + 1] = {};
-
-  ~Server() {
-    // The worker is detached at process exit; nothing to join here.
-  }
 };
 
 Server& srv() {
@@ -108,24 +118,27 @@ size_t footprint_of(const bpm_plan_s* p, bool need_rec) {
   return b;
 }
 
-void release(Request& r) {
-  if (r.d_state) cudaFree(r.d_state);
-  if (r.d_rec) cudaFree(r.d_rec);
-  if (r.d_pow) cudaFree(r.d_pow);
-  if (r.d_g) cudaFree(r.d_g);
-  if (r.d_out) cudaFree(r.d_out);
+void release(Server& s, Request& r) {
+  if (r.ready) {
+    cudaEventDestroy(r.ready);
+    r.ready = nullptr;
+  }
+  void* ptrs[] = {r.d_state, r.d_rec, r.d_pow, r.d_g, r.d_out};
+  for (void* p : ptrs)
+    if (p) cudaFreeAsync(p, s.io_stream);
   r.d_state = r.d_rec = nullptr;
   r.d_pow = nullptr;
   r.d_g = r.d_out = nullptr;
 }
 
-// Allocate and stage a request; runs on the worker with srv().mu released.
+// Allocate and stage a request (stream-ordered on io_stream).
 int admit_device(Server& s, Request& r) {
   bpm_plan_s* p = r.plan;
   const size_t n = p->nx, nb = p->nb, cs = csize_of(p);
+  cudaStream_t st = s.io_stream;
   cudaError_t e = cudaSuccess;
   auto A = [&](void** ptr, size_t bytes) {
-    if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+    if (e == cudaSuccess) e = cudaMallocAsync(ptr, bytes, st);
   };
   {
     std::lock_guard<std::mutex> lk(p->mu);
@@ -135,7 +148,7 @@ int admit_device(Server& s, Request& r) {
       p->slices_dirty = true;
     }
     if (e == cudaSuccess && p->slices_dirty) {
-      int rc = prepare_slices(p, s.io_stream);
+      int rc = prepare_slices(p, st, false);
       if (rc != BPM_OK) return rc;
     }
   }
@@ -148,15 +161,18 @@ int admit_device(Server& s, Request& r) {
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? BPM_ERR_OOM : BPM_ERR_CUDA;
   }
-  e = cudaMemcpyAsync(r.d_out, r.psi_in.data(), nb * 2 * n * 16, cudaMemcpyHostToDevice, s.io_stream);
+  e = cudaMemcpyAsync(r.d_out, r.psi_in.data(), nb * 2 * n * 16, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return BPM_ERR_CUDA;
   if (p->precision == BPM_FP32_FUSED) {
-    int rc = launch_convert_in(r.d_out, static_cast<float2*>(r.d_state), nb * 2 * n, s.io_stream);
+    int rc = launch_convert_in(r.d_out, static_cast<float2*>(r.d_state), nb * 2 * n, st);
     if (rc != BPM_OK) return rc;
   } else {
-    e = cudaMemcpyAsync(p->d_state, r.d_out, nb * 2 * n * 16, cudaMemcpyDeviceToDevice, s.io_stream);
+    e = cudaMemcpyAsync(p->d_state, r.d_out, nb * 2 * n * 16, cudaMemcpyDeviceToDevice, st);
   }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s.io_stream);
+  // No wait here: the request's first epoch waits on this event instead, so
+  // preparing a large strain stream never stalls the other buckets.
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.ready, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(r.ready, st);
   return e == cudaSuccess ? BPM_OK : BPM_ERR_CUDA;
 }
 
@@ -165,7 +181,7 @@ int retire_device(Server& s, Request& r) {
   const size_t n = p->nx, nb = p->nb, cs = csize_of(p);
   std::vector<double2> g;
   phase_factors(p, p->nz, &g);
-  cudaStream_t st = s.io_stream;
+  cudaStream_t st = s.out_stream;
   cudaError_t e = cudaMemcpyAsync(r.d_g, g.data(), nb * 16, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return BPM_ERR_CUDA;
   const int pw_stride = 2 * (p->n_rec + 1);
@@ -194,12 +210,12 @@ int retire_device(Server& s, Request& r) {
   return BPM_OK;
 }
 
-void finish_request(Server& s, std::shared_ptr<Request> r, int status, const std::string& msg) {
-  release(*r);
+void finish_request(Server& s, const ReqPtr& r, int status, const std::string& msg) {
+  release(s, *r);
   {
     std::lock_guard<std::mutex> lk(r->plan->mu);
     if (r->owns_phasor) {
-      cudaFree(r->plan->d_phasor);
+      cudaFreeAsync(r->plan->d_phasor, s.io_stream);
       r->plan->d_phasor = nullptr;
       r->plan->slices_dirty = true;
     }
@@ -207,6 +223,7 @@ void finish_request(Server& s, std::shared_ptr<Request> r, int status, const std
   }
   std::lock_guard<std::mutex> lk(s.mu);
   s.used -= r->footprint;
+  s.n_active -= 1;
   r->status = status;
   r->error = msg;
   r->t_done = now_s();
@@ -214,28 +231,94 @@ void finish_request(Server& s, std::shared_ptr<Request> r, int status, const std
   s.cv_done.notify_all();
 }
 
-cudaStream_t stream_for(Server& s, int logn) {
-  auto it = s.streams.find(logn);
-  if (it != s.streams.end()) return it->second;
-  cudaStream_t st;
-  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-  s.streams[logn] = st;
-  return st;
+Bucket& bucket_for(Server& s, long key) {
+  auto it = s.buckets.find(key);
+  if (it != s.buckets.end()) return it->second;
+  Bucket& b = s.buckets[key];
+  cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking);
+  cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming);
+  cudaMalloc(&b.d_status, sizeof(int));
+  cudaMemset(b.d_status, 0, sizeof(int));
+  return b;
+}
+
+// Launch the next epoch of a bucket.
+int launch_epoch(Server& s, long key, Bucket& b) {
+  b.launched.clear();
+  std::map<int, std::vector<RowDescF32>> groups;   // FP32 rows by step count
+  std::vector<RowDescF32> rows;
+  for (auto& r : b.members) {
+    bpm_plan_s* p = r->plan;
+    if (r->ready) {   // first epoch of this request: wait for its staging
+      cudaStreamWaitEvent(b.st, r->ready, 0);
+      cudaEventDestroy(r->ready);
+      r->ready = nullptr;
+    }
+    const int steps = std::min(s.epoch_steps, p->nz - r->n_done);
+    b.launched.push_back({r, steps});
+    if (p->precision != BPM_FP32_FUSED) {
+      int err = plain_march(p, r->n_done, r->n_done + steps, 0, r->d_rec, r->d_pow, b.st);
+      if (err != BPM_OK) return err;
+      continue;
+    }
+    fused_rows(p, static_cast<float2*>(r->d_state), static_cast<float2*>(r->d_rec), r->d_pow,
+               r->n_done, r->n_done + steps, &rows);
+    for (auto& d : rows) d.n_phase0 = 0;
+    auto& g = groups[steps];
+    g.insert(g.end(), rows.begin(), rows.end());
+  }
+  if (!groups.empty()) {
+    size_t total = 0;
+    for (auto& kv : groups) total += kv.second.size();
+    if (total > b.cap) {
+      if (b.d_rows) cudaFreeAsync(b.d_rows, b.st);
+      b.cap = std::max<size_t>(2 * total, 64);
+      if (cudaMallocAsync(&b.d_rows, b.cap * sizeof(RowDescF32), b.st) != cudaSuccess) {
+        b.d_rows = nullptr;
+        b.cap = 0;
+        cudaGetLastError();
+        return BPM_ERR_OOM;
+      }
+    }
+    const int logn = int(key);
+    if (!s.d_tw[logn]) {
+      std::vector<float4> tw;
+      twiddle_table_f32(1 << logn, &tw);
+      cudaMalloc(&s.d_tw[logn], tw.size() * sizeof(float4));
+      cudaMemcpy(s.d_tw[logn], tw.data(), tw.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    }
+    size_t off = 0;
+    for (auto& kv : groups) {
+      cudaMemcpyAsync(b.d_rows + off, kv.second.data(), kv.second.size() * sizeof(RowDescF32),
+                      cudaMemcpyHostToDevice, b.st);
+      int err = launch_fused(logn, b.d_rows + off, int(kv.second.size()), kv.first, s.d_tw[logn],
+                             b.d_status, b.st);
+      if (err != BPM_OK) return err;
+      off += kv.second.size();
+    }
+  }
+  cudaEventRecord(b.ev, b.st);
+  b.busy = true;
+  return BPM_OK;
 }
 
 void worker_loop() {
   Server& s = srv();
-  std::vector<RowDescF32> rows;
   for (;;) {
-    std::vector<std::shared_ptr<Request>> admitted;
+    // ---- admission (arrival order, memory budget, active cap)
+    std::vector<ReqPtr> admitted;
     {
       std::unique_lock<std::mutex> lk(s.mu);
-      s.cv_work.wait(lk, [&] { return !s.queue.empty() || !s.active.empty(); });
-      while (!s.queue.empty() && int(s.active.size() + admitted.size()) < s.max_active) {
+      bool any_work = false;
+      for (auto& kv : s.buckets) any_work = any_work || kv.second.busy || !kv.second.members.empty();
+      if (s.queue.empty() && !any_work)
+        s.cv_work.wait(lk, [&] { return !s.queue.empty(); });
+      while (!s.queue.empty() && s.n_active < s.max_active) {
         auto r = s.queue.front();
-        if (s.used + r->footprint > s.budget) break;   // arrival order: wait for memory
+        if (s.used + r->footprint > s.budget) break;
         s.queue.pop_front();
         s.used += r->footprint;
+        s.n_active += 1;
         admitted.push_back(r);
       }
     }
@@ -246,93 +329,66 @@ void worker_loop() {
         finish_request(s, r, rc, "admission failed on the device");
         continue;
       }
-      std::lock_guard<std::mutex> lk(s.mu);
-      s.active.push_back(r);
+      const long key = r->plan->precision == BPM_FP32_FUSED ? long(r->plan->logn) : -long(r->id);
+      bucket_for(s, key).members.push_back(r);
     }
-    std::vector<std::shared_ptr<Request>> act;
-    {
-      std::lock_guard<std::mutex> lk(s.mu);
-      act = s.active;
-    }
-    if (act.empty()) continue;
 
-    // ---- one epoch: group FP32 rows by (transform size, steps this epoch)
-    std::map<std::pair<int, int>, std::vector<RowDescF32>> groups;
-    std::vector<std::shared_ptr<Request>> plain;
-    for (auto& r : act) {
-      bpm_plan_s* p = r->plan;
-      const int steps = std::min(s.epoch_steps, p->nz - r->n_done);
-      if (p->precision != BPM_FP32_FUSED) {
-        plain.push_back(r);
+    // ---- progress every bucket independently
+    bool progressed = !admitted.empty();
+    for (auto it = s.buckets.begin(); it != s.buckets.end();) {
+      Bucket& b = it->second;
+      if (b.busy) {
+        cudaError_t q = cudaEventQuery(b.ev);
+        if (q == cudaErrorNotReady) {
+          ++it;
+          continue;
+        }
+        b.busy = false;
+        progressed = true;
+        int err = q == cudaSuccess ? BPM_OK : BPM_ERR_CUDA;
+        int status = 0;
+        cudaMemcpy(&status, b.d_status, sizeof(int), cudaMemcpyDeviceToHost);
+        if (status) {
+          cudaMemset(b.d_status, 0, sizeof(int));
+          err = BPM_ERR_TIMEOUT;
+        }
+        std::vector<ReqPtr> done;
+        for (auto& rs : b.launched) {
+          rs.first->n_done += rs.second;
+          if (err != BPM_OK || rs.first->n_done >= rs.first->plan->nz) done.push_back(rs.first);
+        }
+        b.launched.clear();
+        for (auto& r : done) {
+          b.members.erase(std::remove(b.members.begin(), b.members.end(), r), b.members.end());
+          const int rc = err != BPM_OK ? err : retire_device(s, *r);
+          finish_request(s, r, rc, rc == BPM_OK ? "" : "request failed on the device");
+        }
+      }
+      if (!b.busy && !b.members.empty()) {
+        const int err = launch_epoch(s, it->first, b);
+        progressed = true;
+        if (err != BPM_OK) {
+          auto members = b.members;
+          b.members.clear();
+          b.launched.clear();
+          b.busy = false;
+          for (auto& r : members) finish_request(s, r, err, "epoch launch failed");
+        }
+      }
+      if (!b.busy && b.members.empty() && it->first < 0) {
+        cudaStreamSynchronize(b.st);
+        cudaStreamDestroy(b.st);
+        cudaEventDestroy(b.ev);
+        if (b.d_rows) cudaFree(b.d_rows);
+        cudaFree(b.d_status);
+        it = s.buckets.erase(it);
         continue;
       }
-      fused_rows(p, static_cast<float2*>(r->d_state), static_cast<float2*>(r->d_rec), r->d_pow,
-                 r->n_done, r->n_done + steps, &rows);
-      for (auto& d : rows) d.n_phase0 = 0;
-      auto& g = groups[{p->logn, steps}];
-      g.insert(g.end(), rows.begin(), rows.end());
+      ++it;
     }
-    size_t total_rows = 0;
-    for (auto& kv : groups) total_rows += kv.second.size();
-    int err = BPM_OK;
-    if (total_rows > s.d_rows_cap) {
-      if (s.d_rows) cudaFree(s.d_rows);
-      s.d_rows_cap = std::max<size_t>(total_rows * 2, 1024);
-      if (cudaMalloc(&s.d_rows, s.d_rows_cap * sizeof(RowDescF32)) != cudaSuccess) {
-        s.d_rows = nullptr;
-        s.d_rows_cap = 0;
-        err = BPM_ERR_OOM;
-      }
-    }
-    size_t off = 0;
-    for (auto& kv : groups) {
-      if (err != BPM_OK) break;
-      const int logn = kv.first.first, steps = kv.first.second;
-      cudaStream_t st = stream_for(s, logn);
-      auto& v = kv.second;
-      if (!s.d_tw[logn]) {
-        std::vector<float4> tw;
-        twiddle_table_f32(1 << logn, &tw);
-        cudaMalloc(&s.d_tw[logn], tw.size() * sizeof(float4));
-        cudaMemcpy(s.d_tw[logn], tw.data(), tw.size() * sizeof(float4), cudaMemcpyHostToDevice);
-      }
-      cudaMemcpyAsync(s.d_rows + off, v.data(), v.size() * sizeof(RowDescF32),
-                      cudaMemcpyHostToDevice, st);
-      err = launch_fused(logn, s.d_rows + off, int(v.size()), steps, s.d_tw[logn], s.d_status, st);
-      off += v.size();
-    }
-    for (auto& r : plain) {
-      if (err != BPM_OK) break;
-      bpm_plan_s* p = r->plan;
-      const int steps = std::min(s.epoch_steps, p->nz - r->n_done);
-      std::lock_guard<std::mutex> lk(p->mu);
-      err = plain_march(p, r->n_done, r->n_done + steps, 0, r->d_rec, r->d_pow, s.io_stream);
-    }
-    for (auto& kv : s.streams) cudaStreamSynchronize(kv.second);
-    cudaStreamSynchronize(s.io_stream);
-    int status = 0;
-    cudaMemcpy(&status, s.d_status, sizeof(int), cudaMemcpyDeviceToHost);
-    if (status) {
-      cudaMemset(s.d_status, 0, sizeof(int));
-      err = BPM_ERR_TIMEOUT;
-    }
-    cudaError_t ce = cudaGetLastError();
-    if (err == BPM_OK && ce != cudaSuccess) err = BPM_ERR_CUDA;
-
-    // ---- advance and retire
-    std::vector<std::shared_ptr<Request>> done;
-    for (auto& r : act) {
-      r->n_done += std::min(s.epoch_steps, r->plan->nz - r->n_done);
-      if (err != BPM_OK || r->n_done >= r->plan->nz) done.push_back(r);
-    }
-    {
-      std::lock_guard<std::mutex> lk(s.mu);
-      for (auto& r : done)
-        s.active.erase(std::remove(s.active.begin(), s.active.end(), r), s.active.end());
-    }
-    for (auto& r : done) {
-      int rc = err != BPM_OK ? err : retire_device(s, *r);
-      finish_request(s, r, rc, rc == BPM_OK ? "" : "request failed on the device");
+    if (!progressed) {
+      std::unique_lock<std::mutex> lk(s.mu);
+      s.cv_work.wait_for(lk, std::chrono::microseconds(50));
     }
   }
 }
@@ -343,8 +399,7 @@ void ensure_started(Server& s) {
   cudaMemGetInfo(&free_b, &total_b);
   s.budget = size_t(double(free_b) * s.mem_fraction);
   cudaStreamCreateWithFlags(&s.io_stream, cudaStreamNonBlocking);
-  cudaMalloc(&s.d_status, sizeof(int));
-  cudaMemset(s.d_status, 0, sizeof(int));
+  cudaStreamCreateWithFlags(&s.out_stream, cudaStreamNonBlocking);
   s.started = true;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -366,7 +421,7 @@ int bpm_server_configure(double mem_fraction, int32_t max_active, int32_t epoch_
                          int32_t max_queue) {
   Server& s = srv();
   std::lock_guard<std::mutex> lk(s.mu);
-  if (!s.queue.empty() || !s.active.empty())
+  if (!s.queue.empty() || s.n_active > 0)
     return fail(BPM_ERR_BUSY, "server has requests in flight");
   if (mem_fraction > 0.9) return fail(BPM_ERR_INVALID, "mem_fraction must be <= 0.9");
   s.mem_fraction = mem_fraction > 0 ? mem_fraction : 0.6;
@@ -428,7 +483,7 @@ int bpm_poll(bpm_ticket_t ticket, int32_t timeout_ms) {
   if (timeout_ms < 0) s.cv_done.wait(lk, ready);
   else if (timeout_ms > 0) s.cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
   if (!ready()) return BPM_NOT_READY;
-  s.tickets.erase(it);
+  s.tickets.erase(ticket);
   if (r->status != BPM_OK) return fail(r->status, r->error);
   return BPM_OK;
 }

@@ -61,7 +61,7 @@ def test_fp32_fused_matches_oracle(bpm_lib, refs, name):
     assert np.allclose(out.powers, ref.powers, rtol=4e-4, atol=1e-12 * np.max(ref.powers))
 
 
-@pytest.mark.parametrize("nx", [8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 8192])
+@pytest.mark.parametrize("nx", [8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 8192, 16384])
 def test_every_transform_size(bpm_lib, nx):
     """Random two-band input, masked strained bulk, 37 steps with a ragged
     record tail (37 = 3 * 12 + 1): exercises every radix decomposition."""
@@ -249,3 +249,21 @@ def test_rotated_schedule_matches_single_launch(bpm_lib):
     rows = [3, 150, 199]
     ref = run_ref(big, rows=rows)
     assert max(band_errors(out_big.psi[rows], ref.psi)) <= 2e-5
+
+
+def test_split_band_sizes_against_oracle(bpm_lib):
+    """N = 8192 and 16384 run as bands split over 2 and 4 CTAs per band:
+    a few hundred steps of a dislocated asymmetric Bragg request against the
+    oracle, the strain stream fetched back in natural order."""
+    rng = np.random.default_rng(21)
+    for nx in (8192, 16384):
+        wl = inputs.serving_request(rng, nx, 300)
+        wl.record_every = 100
+        ref = run_ref(wl)
+        for prec, tol in ((FP32, 2e-5), (FP64, TOL_FP64)):
+            with binding.Plan(wl, prec) as plan:
+                mask, _ = plan.slices()
+                out = plan.propagate()
+            assert np.array_equal(mask.astype(bool), orun.mask_of(wl))
+            errs = band_errors(out.psi, ref.psi, out.records, ref.records)
+            assert max(errs) <= tol, (nx, prec, errs)
