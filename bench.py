@@ -124,15 +124,14 @@ def rel_l2_bands(got, ref):
 
 # --------------------------------------------------------------------------
 def serving_run(n_requests: int, rate: float, warm: int = 40, n_check: int = 8):
-    """Replay a seeded Poisson stream of mixed solves (Nx up to 8192) in real
+    """Replay a seeded Poisson stream of mixed solves (Nx 512..16384) in real
     time through bpm_submit / bpm_poll; latency = completion - submission as
     stamped by the server.  The first `warm` requests are excluded from the
     statistics.  `n_check` sampled requests are re-run alone for parity."""
     import threading
     from paper_2601_06340_gb300 import binding, inputs
     FP32 = binding.BPM_FP32_FUSED
-    reqs = inputs.serving_requests(n_requests, rate_per_s=rate,
-                                   nx_choices=(512, 1024, 2048, 4096, 8192))
+    reqs = inputs.serving_requests(n_requests, rate_per_s=rate)
     binding.bpm_server_configure(0.6, 256, 256, 100000)
     tickets = [None] * len(reqs)
     outs = [np.empty_like(r.workload.psi0) for r in reqs]
@@ -171,7 +170,7 @@ def serving_run(n_requests: int, rate: float, warm: int = 40, n_check: int = 8):
     for p in plans:
         p.close()
     return {"requests": len(reqs) - warm, "warmup_requests": warm, "rate_per_s": rate,
-            "nx_choices": [512, 1024, 2048, 4096, 8192], "nz_range": [500, 20000],
+            "nx_choices": [512, 1024, 2048, 4096, 8192, 16384], "nz_range": [500, 20000],
             "throughput": cells / span, "unit": UNIT,
             "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
                            "p99": float(np.percentile(lat_ms, 99)),

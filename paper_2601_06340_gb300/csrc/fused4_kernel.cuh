@@ -14,7 +14,9 @@
 // Every CTA uses the same thread -> k map, so each exchange is "thread t of
 // every CTA of the band swaps the values of its 16 frequencies": each CTA
 // pushes its values into every peer's exchange buffer (distributed shared
-// memory), and after a cluster barrier reads them locally.  The step is the
+// memory), and after a cluster barrier reads them locally.  The exchange
+// buffers are indexed by (value j, thread t) -- consecutive lanes hit
+// consecutive words -- rather than by spectral position.  The step is the
 // real-space increment form of Eq. fov10 (see fused2_kernel.cuh); the band
 // coupling swaps psi_p with the CTA of the other band that holds the same
 // samples.  Four cluster barriers per step: G published, G consumed, X'
@@ -109,11 +111,9 @@ __global__ void __cluster_dims__(2 * P, 1, 1) __launch_bounds__(F4Cfg<P>::T, 1)
   // Last-pass slice: local spectral index k_j of position pos_j, combine
   // twiddle W_N^{h k_j} and the propagator increment of X[k_j + 4096 h].
   float2 pr[16], cw[16];
-  int kpos[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
     const int pos = f2_pos<L, NP - 1>(t, j);
-    kpos[j] = pos;
     // digit reversal of the local 16 x 16 x 16 transform
     const int k = (pos >> 8) + ((pos >> 4) & 15) * 16 + (pos & 15) * 256;
     const float4 a = __ldg(&tw[h * k]);
@@ -161,7 +161,7 @@ __global__ void __cluster_dims__(2 * P, 1, 1) __launch_bounds__(F4Cfg<P>::T, 1)
     for (int j = 0; j < 16; ++j) {
       const float2 g = cmul_f(v[j], cw[j].x, cw[j].y);
 #pragma unroll
-      for (int r = 0; r < P; ++r) xpeer[r][h * M + kpos[j]] = g;
+      for (int r = 0; r < P; ++r) xpeer[r][h * M + j * T + t] = g;
     }
     cluster.sync();                              // G published
     if (lead && pending_slot >= 0) {
@@ -178,7 +178,7 @@ __global__ void __cluster_dims__(2 * P, 1, 1) __launch_bounds__(F4Cfg<P>::T, 1)
       float2 s = make_float2(0.f, 0.f);
 #pragma unroll
       for (int hh = 0; hh < P; ++hh) {
-        const float2 g = mul_root<P>(xb[hh * M + kpos[j]], hh * h, false);
+        const float2 g = mul_root<P>(xb[hh * M + j * T + t], hh * h, false);
         s = make_float2(s.x + g.x, s.y + g.y);
       }
       const float2 dd = pr[j];
@@ -188,14 +188,14 @@ __global__ void __cluster_dims__(2 * P, 1, 1) __launch_bounds__(F4Cfg<P>::T, 1)
 #pragma unroll
     for (int j = 0; j < 16; ++j)
 #pragma unroll
-      for (int r = 0; r < P; ++r) xpeer[r][h * M + kpos[j]] = v[j];
+      for (int r = 0; r < P; ++r) xpeer[r][h * M + j * T + t] = v[j];
     cluster.sync();                              // X' published
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       float2 s = make_float2(0.f, 0.f);
 #pragma unroll
       for (int rr = 0; rr < P; ++rr) {
-        const float2 g = mul_root<P>(xb[rr * M + kpos[j]], h * rr, true);
+        const float2 g = mul_root<P>(xb[rr * M + j * T + t], h * rr, true);
         s = make_float2(s.x + g.x, s.y + g.y);
       }
       v[j] = cmul_f(s, cw[j].x, -cw[j].y);
