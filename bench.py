@@ -169,7 +169,18 @@ def serving_run(n_requests: int, rate: float, warm: int = 40, n_check: int = 8):
                 errs.append(float(np.linalg.norm(outs[i][0, b] - alone[0, b]) / den))
     for p in plans:
         p.close()
+    per_nx = {}
+    svc_ms = (times[:, 2] - times[:, 1]) * 1e3
+    for nx in sorted({r.workload.nx for r in reqs[warm:]}):
+        sel = np.array([r.workload.nx == nx for r in reqs[warm:]])
+        nzs = np.array([r.workload.nz for r in reqs[warm:]])[sel]
+        per_nx[str(nx)] = {"count": int(sel.sum()),
+                           "latency_p50_ms": float(np.percentile(lat_ms[sel], 50)),
+                           "service_us_per_step_p50": float(np.percentile(
+                               svc_ms[sel] * 1e3 / nzs, 50))}
     return {"requests": len(reqs) - warm, "warmup_requests": warm, "rate_per_s": rate,
+            "per_nx": per_nx,
+            "mean_active": float(np.sum(times[:, 2] - times[:, 1]) / span),
             "nx_choices": [512, 1024, 2048, 4096, 8192, 16384], "nz_range": [500, 20000],
             "throughput": cells / span, "unit": UNIT,
             "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),

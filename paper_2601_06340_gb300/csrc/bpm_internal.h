@@ -115,6 +115,12 @@ std::vector<int> fft_output_order(int logn);   // position -> frequency index
 int prepare_slices(bpm_plan_s* plan, cudaStream_t st, bool sync = true);
 int launch_fused(int logn, const RowDescF32* d_rows, int n_rows, int steps,
                  const float4* d_tw, int* d_status, cudaStream_t st);
+// layout: -1 automatic, 0 one CTA per row, 1 two-CTA cluster per row (only
+// for 1024 <= N <= 4096; larger N always use the split-band cluster).
+int launch_fused_layout(int logn, const RowDescF32* d_rows, int n_rows, int steps,
+                        const float4* d_tw, int* d_status, cudaStream_t st, int layout);
+// SMs one row occupies in its cluster layout (0 if the size has none).
+int fused_cluster_sms(int logn);
 int plain_march(bpm_plan_s* plan, int n_begin, int n_end, int n_phase0, void* d_records,
                 double* d_powers, cudaStream_t st);
 int launch_convert_in(const double2* src, float2* dst, size_t n, cudaStream_t st);

@@ -47,8 +47,20 @@ static bool use_cluster_layout(int logn, int n_rows) {
 
 int launch_fused(int logn, const RowDescF32* d_rows, int n_rows, int steps,
                  const float4* d_tw, int* d_status, cudaStream_t st) {
+  return launch_fused_layout(logn, d_rows, n_rows, steps, d_tw, d_status, st, -1);
+}
+
+int fused_cluster_sms(int logn) {
+  if (logn >= kSplitLogN) return 2 << (logn - 12);
+  return (logn >= 10 && logn <= 12) ? 2 : 0;
+}
+
+int launch_fused_layout(int logn, const RowDescF32* d_rows, int n_rows, int steps,
+                        const float4* d_tw, int* d_status, cudaStream_t st, int layout) {
   if (n_rows <= 0 || steps <= 0) return BPM_OK;
-  if (use_cluster_layout(logn, n_rows)) {
+  const bool cluster = logn >= 10 && logn <= 12 &&
+                       (layout == 1 || (layout < 0 && use_cluster_layout(logn, n_rows)));
+  if (cluster) {
     switch (logn) {
       case 10: return fused3_launch_10(d_rows, n_rows, steps, d_tw, d_status, st);
       case 11: return fused3_launch_11(d_rows, n_rows, steps, d_tw, d_status, st);

@@ -1,7 +1,9 @@
 // Slice preparation: the crystal mask Pi(x_j, z_n) and the strain phasor
 // exp(i h u_x(x_j, z_n)) for every cell, computed once per set_crystal /
-// set_strain on the device in FP64 and stored as c64 (fused path) or c128
-// (plain path), with (0, 0) marking cells outside the crystal.
+// set_strain on the device -- the phase h u_x and its reduction modulo 2 pi
+// in FP64, the unit phasor in the precision it is stored in -- as c64
+// (fused path) or c128 (plain path), with (0, 0) marking cells outside the
+// crystal.
 //
 // Mask decisions (slab faces, polygon edges) use the IEEE operations
 // __dadd_rn / __dmul_rn / __ddiv_rn explicitly so that no multiply-add is
@@ -90,8 +92,19 @@ __global__ void prep_kernel(PrepParams p) {
     const double z = __dmul_rn(double(n), p.dz);
     double re = 0.0, im = 0.0;
     if (inside_cell(p, n, j, x, z)) {
+      // h u_x in FP64, reduced to [-pi, pi] in FP64; the unit phasor is
+      // evaluated in the precision it is stored in (FP64 plans: FP64,
+      // FP32 plans: FP32 of the reduced angle).
       const double theta = p.h * strain_ux(p, n, j, x, z);
-      sincos(fmod(theta, 6.283185307179586), &im, &re);
+      const double t = theta - 6.283185307179586 * rint(theta * 0.15915494309189535);
+      if (p.out64) {
+        sincos(t, &im, &re);
+      } else {
+        float sf, cf;
+        sincosf(float(t), &sf, &cf);
+        re = cf;
+        im = sf;
+      }
     }
     if (p.out32) {
       size_t o = c;

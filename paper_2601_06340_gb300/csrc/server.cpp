@@ -22,6 +22,7 @@
 #include <array>
 #include <chrono>
 #include <cmath>
+#include <cstring>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -65,6 +66,9 @@ struct Request {
   double2* d_g = nullptr;
   double2* d_out = nullptr;    // c128 staging
   cudaEvent_t ready = nullptr; // staged and prepared on io_stream
+  cudaEvent_t out_ev = nullptr;   // results copied to the pinned staging
+  void* h_stage = nullptr;        // pinned staging: psi c128, records, powers
+  size_t h_stage_bytes = 0;
   int n_done = 0;
 };
 using ReqPtr = std::shared_ptr<Request>;
@@ -72,6 +76,7 @@ using ReqPtr = std::shared_ptr<Request>;
 struct Bucket {
   cudaStream_t st = nullptr;
   cudaEvent_t ev = nullptr;
+  int* h_status = nullptr;      // pinned copy of the epoch's status word
   bool busy = false;
   std::vector<ReqPtr> members;
   std::vector<std::pair<ReqPtr, int>> launched;   // (request, steps) of the epoch in flight
@@ -95,8 +100,13 @@ struct Server {
   std::thread worker;
   // worker-owned
   std::map<long, Bucket> buckets;   // key: logn (FP32) or -(ticket id) (FP64)
+  std::vector<ReqPtr> retiring;     // results on their way to the caller
+  std::vector<Bucket> spare;        // recycled per-request buckets
+  std::map<size_t, std::vector<void*>> pinned_pool;   // pinned staging by size
   cudaStream_t io_stream = nullptr;    // admission: staging and strain preparation
   cudaStream_t out_stream = nullptr;   // retirement: finishing and copies out
+  int sm_count = 1;
+  bool per_request = false;  // true: one launch stream per request (else one per size)
   float4* d_tw[kMaxLogN + 1] = {};
 };
 
@@ -118,7 +128,39 @@ size_t footprint_of(const bpm_plan_s* p, bool need_rec) {
   return b;
 }
 
+void* pinned_get(Server& s, size_t bytes) {
+  auto& v = s.pinned_pool[bytes];
+  if (!v.empty()) {
+    void* p = v.back();
+    v.pop_back();
+    return p;
+  }
+  void* p = nullptr;
+  if (cudaHostAlloc(&p, bytes, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void pinned_put(Server& s, void* p, size_t bytes) {
+  if (p) s.pinned_pool[bytes].push_back(p);
+}
+
+// Pinned staging of a request: [psi c128][records][powers].
+size_t stage_bytes(const bpm_plan_s* p, bool rec) {
+  const size_t n = p->nx, nb = p->nb, cs = csize_of(p);
+  return nb * 2 * n * 16 + (rec ? nb * size_t(p->n_rec) * 2 * n * cs : 0) +
+         nb * size_t(p->n_rec + 1) * 2 * 8;
+}
+
 void release(Server& s, Request& r) {
+  if (r.out_ev) {
+    cudaEventDestroy(r.out_ev);
+    r.out_ev = nullptr;
+  }
+  pinned_put(s, r.h_stage, r.h_stage_bytes);
+  r.h_stage = nullptr;
   if (r.ready) {
     cudaEventDestroy(r.ready);
     r.ready = nullptr;
@@ -161,7 +203,11 @@ int admit_device(Server& s, Request& r) {
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? BPM_ERR_OOM : BPM_ERR_CUDA;
   }
-  e = cudaMemcpyAsync(r.d_out, r.psi_in.data(), nb * 2 * n * 16, cudaMemcpyHostToDevice, st);
+  r.h_stage_bytes = stage_bytes(p, r.d_rec != nullptr);
+  r.h_stage = pinned_get(s, r.h_stage_bytes);
+  if (!r.h_stage) return BPM_ERR_OOM;
+  std::memcpy(r.h_stage, r.psi_in.data(), nb * 2 * n * 16);
+  e = cudaMemcpyAsync(r.d_out, r.h_stage, nb * 2 * n * 16, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return BPM_ERR_CUDA;
   if (p->precision == BPM_FP32_FUSED) {
     int rc = launch_convert_in(r.d_out, static_cast<float2*>(r.d_state), nb * 2 * n, st);
@@ -176,13 +222,19 @@ int admit_device(Server& s, Request& r) {
   return e == cudaSuccess ? BPM_OK : BPM_ERR_CUDA;
 }
 
-int retire_device(Server& s, Request& r) {
+// Enqueue the end of a request on out_stream: common phase, conversion to
+// c128, final powers, copies into the pinned staging; completion is an event.
+int retire_enqueue(Server& s, Request& r) {
   bpm_plan_s* p = r.plan;
   const size_t n = p->nx, nb = p->nb, cs = csize_of(p);
   std::vector<double2> g;
   phase_factors(p, p->nz, &g);
   cudaStream_t st = s.out_stream;
-  cudaError_t e = cudaMemcpyAsync(r.d_g, g.data(), nb * 16, cudaMemcpyHostToDevice, st);
+  double2* hg = reinterpret_cast<double2*>(
+      static_cast<char*>(r.h_stage) + r.h_stage_bytes - nb * size_t(p->n_rec + 1) * 2 * 8);
+  // phase factors go through the (not yet used) powers area of the staging
+  std::memcpy(hg, g.data(), nb * 16);
+  cudaError_t e = cudaMemcpyAsync(r.d_g, hg, nb * 16, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return BPM_ERR_CUDA;
   const int pw_stride = 2 * (p->n_rec + 1);
   int rc;
@@ -195,18 +247,36 @@ int retire_device(Server& s, Request& r) {
                            reinterpret_cast<const double*>(r.d_g), p->nb, p->nx, p->nz, p->dx_um,
                            r.d_pow + 2 * p->n_rec, pw_stride, st);
   if (rc != BPM_OK) return rc;
-  e = cudaMemcpyAsync(r.psi_out, r.d_out, nb * 2 * n * 16, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && r.d_rec)
-    e = cudaMemcpyAsync(r.records, r.d_rec, nb * size_t(p->n_rec) * 2 * n * cs,
-                        cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && r.powers)
-    e = cudaMemcpyAsync(r.powers, r.d_pow, nb * size_t(p->n_rec + 1) * 2 * 8,
-                        cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return BPM_ERR_CUDA;
-  if (r.powers)
-    for (size_t i = 0; i < nb * size_t(p->n_rec + 1) * 2; ++i)
-      if (!std::isfinite(r.powers[i])) return BPM_ERR_NUMERIC;
+  char* h = static_cast<char*>(r.h_stage);
+  e = cudaMemcpyAsync(h, r.d_out, nb * 2 * n * 16, cudaMemcpyDeviceToHost, st);
+  h += nb * 2 * n * 16;
+  if (e == cudaSuccess && r.d_rec) {
+    e = cudaMemcpyAsync(h, r.d_rec, nb * size_t(p->n_rec) * 2 * n * cs, cudaMemcpyDeviceToHost, st);
+    h += nb * size_t(p->n_rec) * 2 * n * cs;
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h, r.d_pow, nb * size_t(p->n_rec + 1) * 2 * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.out_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(r.out_ev, st);
+  return e == cudaSuccess ? BPM_OK : BPM_ERR_CUDA;
+}
+
+// Copy a finished request's staged results to the caller's buffers.
+int retire_complete(Request& r) {
+  bpm_plan_s* p = r.plan;
+  const size_t n = p->nx, nb = p->nb, cs = csize_of(p);
+  const char* h = static_cast<const char*>(r.h_stage);
+  std::memcpy(r.psi_out, h, nb * 2 * n * 16);
+  h += nb * 2 * n * 16;
+  if (r.d_rec) {
+    std::memcpy(r.records, h, nb * size_t(p->n_rec) * 2 * n * cs);
+    h += nb * size_t(p->n_rec) * 2 * n * cs;
+  }
+  const double* pw = reinterpret_cast<const double*>(h);
+  const size_t npw = nb * size_t(p->n_rec + 1) * 2;
+  if (r.powers) std::memcpy(r.powers, pw, npw * 8);
+  for (size_t i = 0; i < npw; ++i)
+    if (!std::isfinite(pw[i])) return BPM_ERR_NUMERIC;
   return BPM_OK;
 }
 
@@ -234,15 +304,39 @@ void finish_request(Server& s, const ReqPtr& r, int status, const std::string& m
 Bucket& bucket_for(Server& s, long key) {
   auto it = s.buckets.find(key);
   if (it != s.buckets.end()) return it->second;
+  if (!s.spare.empty()) {
+    Bucket& b = s.buckets[key];
+    b = std::move(s.spare.back());
+    s.spare.pop_back();
+    b.busy = false;
+    b.members.clear();
+    b.launched.clear();
+    return b;
+  }
   Bucket& b = s.buckets[key];
   cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking);
   cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming);
   cudaMalloc(&b.d_status, sizeof(int));
   cudaMemset(b.d_status, 0, sizeof(int));
+  cudaHostAlloc(reinterpret_cast<void**>(&b.h_status), sizeof(int), cudaHostAllocDefault);
+  *b.h_status = 0;
   return b;
 }
 
-// Launch the next epoch of a bucket.
+// SMs the active FP32 rows would occupy in their cluster layouts.
+int cluster_demand(Server& s) {
+  int d = 0;
+  for (auto& kv : s.buckets)
+    for (auto& r : kv.second.members)
+      if (r->plan->precision == BPM_FP32_FUSED) d += fused_cluster_sms(r->plan->logn);
+  return d;
+}
+
+// Launch the next epoch of a bucket.  Layout by load: when every active row
+// can have the SMs of its cluster layout the launch is latency-first (a
+// 2-CTA cluster per row for N <= 4096); once that demand would exceed the
+// GPU, rows of N <= 4096 go one CTA per row (several rows per SM for small N),
+// which does more cell-updates per SM.
 int launch_epoch(Server& s, long key, Bucket& b) {
   b.launched.clear();
   std::map<int, std::vector<RowDescF32>> groups;   // FP32 rows by step count
@@ -280,23 +374,25 @@ int launch_epoch(Server& s, long key, Bucket& b) {
         return BPM_ERR_OOM;
       }
     }
-    const int logn = int(key);
+    const int logn = b.members.front()->plan->logn;   // one size per bucket
     if (!s.d_tw[logn]) {
       std::vector<float4> tw;
       twiddle_table_f32(1 << logn, &tw);
       cudaMalloc(&s.d_tw[logn], tw.size() * sizeof(float4));
       cudaMemcpy(s.d_tw[logn], tw.data(), tw.size() * sizeof(float4), cudaMemcpyHostToDevice);
     }
+    const int layout = cluster_demand(s) <= s.sm_count ? -1 : 0;
     size_t off = 0;
     for (auto& kv : groups) {
       cudaMemcpyAsync(b.d_rows + off, kv.second.data(), kv.second.size() * sizeof(RowDescF32),
                       cudaMemcpyHostToDevice, b.st);
-      int err = launch_fused(logn, b.d_rows + off, int(kv.second.size()), kv.first, s.d_tw[logn],
-                             b.d_status, b.st);
+      int err = launch_fused_layout(logn, b.d_rows + off, int(kv.second.size()), kv.first,
+                                    s.d_tw[logn], b.d_status, b.st, layout);
       if (err != BPM_OK) return err;
       off += kv.second.size();
     }
   }
+  cudaMemcpyAsync(b.h_status, b.d_status, sizeof(int), cudaMemcpyDeviceToHost, b.st);
   cudaEventRecord(b.ev, b.st);
   b.busy = true;
   return BPM_OK;
@@ -311,6 +407,7 @@ void worker_loop() {
       std::unique_lock<std::mutex> lk(s.mu);
       bool any_work = false;
       for (auto& kv : s.buckets) any_work = any_work || kv.second.busy || !kv.second.members.empty();
+      any_work = any_work || !s.retiring.empty();
       if (s.queue.empty() && !any_work)
         s.cv_work.wait(lk, [&] { return !s.queue.empty(); });
       while (!s.queue.empty() && s.n_active < s.max_active) {
@@ -329,12 +426,27 @@ void worker_loop() {
         finish_request(s, r, rc, "admission failed on the device");
         continue;
       }
-      const long key = r->plan->precision == BPM_FP32_FUSED ? long(r->plan->logn) : -long(r->id);
+      const long key = s.per_request ? -long(r->id)
+                       : (r->plan->precision == BPM_FP32_FUSED ? long(r->plan->logn) : -long(r->id));
       bucket_for(s, key).members.push_back(r);
     }
 
-    // ---- progress every bucket independently
+    // ---- hand finished results to their callers
     bool progressed = !admitted.empty();
+    for (size_t i = 0; i < s.retiring.size();) {
+      ReqPtr r = s.retiring[i];
+      cudaError_t q = cudaEventQuery(r->out_ev);
+      if (q == cudaErrorNotReady) {
+        ++i;
+        continue;
+      }
+      s.retiring.erase(s.retiring.begin() + long(i));
+      progressed = true;
+      const int rc = q == cudaSuccess ? retire_complete(*r) : BPM_ERR_CUDA;
+      finish_request(s, r, rc, rc == BPM_OK ? "" : "request failed on the device");
+    }
+
+    // ---- progress every bucket independently
     for (auto it = s.buckets.begin(); it != s.buckets.end();) {
       Bucket& b = it->second;
       if (b.busy) {
@@ -346,10 +458,9 @@ void worker_loop() {
         b.busy = false;
         progressed = true;
         int err = q == cudaSuccess ? BPM_OK : BPM_ERR_CUDA;
-        int status = 0;
-        cudaMemcpy(&status, b.d_status, sizeof(int), cudaMemcpyDeviceToHost);
-        if (status) {
-          cudaMemset(b.d_status, 0, sizeof(int));
+        if (*b.h_status) {
+          *b.h_status = 0;
+          cudaMemsetAsync(b.d_status, 0, sizeof(int), b.st);
           err = BPM_ERR_TIMEOUT;
         }
         std::vector<ReqPtr> done;
@@ -360,8 +471,9 @@ void worker_loop() {
         b.launched.clear();
         for (auto& r : done) {
           b.members.erase(std::remove(b.members.begin(), b.members.end(), r), b.members.end());
-          const int rc = err != BPM_OK ? err : retire_device(s, *r);
-          finish_request(s, r, rc, rc == BPM_OK ? "" : "request failed on the device");
+          const int rc = err != BPM_OK ? err : retire_enqueue(s, *r);
+          if (rc == BPM_OK) s.retiring.push_back(r);
+          else finish_request(s, r, rc, "request failed on the device");
         }
       }
       if (!b.busy && !b.members.empty()) {
@@ -376,11 +488,9 @@ void worker_loop() {
         }
       }
       if (!b.busy && b.members.empty() && it->first < 0) {
-        cudaStreamSynchronize(b.st);
-        cudaStreamDestroy(b.st);
-        cudaEventDestroy(b.ev);
-        if (b.d_rows) cudaFree(b.d_rows);
-        cudaFree(b.d_status);
+        // keep the stream, event and buffers for the next request (freeing
+        // them would synchronise the device)
+        s.spare.push_back(std::move(b));
         it = s.buckets.erase(it);
         continue;
       }
@@ -403,6 +513,8 @@ void ensure_started(Server& s) {
   s.started = true;
   int dev = 0;
   cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&s.sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (s.sm_count <= 0) s.sm_count = 1;
   s.worker = std::thread([dev] {
     cudaSetDevice(dev);
     worker_loop();
