@@ -42,8 +42,10 @@ WORKLOAD = ("bragg_bent: 2D symmetric Bragg, bent crystal R=1 m nu=0.28, 8 keV, 
             "theta_B=23.65 deg, 200 um slab, Nx=4096, Nz=8000, dx=0.2 um, dz=0.1 um, "
             "one energy, Gaussian 50 um FWHM")
 FLOPS_PER_CELL = lambda n: 4 * 5 * math.log2(n)      # 4 FFTs x 5 N log2 N / N
-KERNEL_SOURCES = ["paper_2601_06340_gb300/csrc/fused_kernel.cuh",
-                  "paper_2601_06340_gb300/csrc/radix.cuh"]
+KERNEL_SOURCES = ["paper_2601_06340_gb300/csrc/radix.cuh",
+                  "paper_2601_06340_gb300/csrc/fused_kernel.cuh",
+                  "paper_2601_06340_gb300/csrc/fused2_kernel.cuh",
+                  "paper_2601_06340_gb300/csrc/fused3_kernel.cuh"]
 
 
 def kernel_hash() -> str:

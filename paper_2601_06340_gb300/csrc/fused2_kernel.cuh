@@ -89,6 +89,16 @@ __device__ __forceinline__ void f2_dft(float2* v) {
   for (int i = 0; i < G; ++i) dft<R, INV, EX>(v + i * R);
 }
 
+// radix-16 twiddle pass with twiddles W^{o j} = w[j * STRIDE] (shared table)
+template <bool INV, int STRIDE>
+__device__ __forceinline__ void f2_twiddle_s(float2* v, const float2* w) {
+#pragma unroll
+  for (int j = 1; j < 16; ++j) {
+    const float2 t = w[j * STRIDE];
+    v[j] = INV ? cmul_f(v[j], t.x, -t.y) : cmul_f(v[j], t.x, t.y);
+  }
+}
+
 // radix-16 twiddle pass with register twiddles w[j-1] = W^{o j}
 template <bool INV>
 __device__ __forceinline__ void f2_twiddle(float2* v, const float2* w) {
@@ -135,12 +145,15 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
     const float4 a = __ldg(&tw[t * j]);
     w0[j - 1] = make_float2(a.x, a.y);
   }
+  // table layout [j][o] (o fastest): lanes with consecutive o read
+  // consecutive words
   float2* tw1 = reinterpret_cast<float2*>(smem + C::OFF_TW1);
   for (int k = threadIdx.x; k < C::S1 * 16; k += blockDim.x) {
-    const float4 a = __ldg(&tw[((k >> 4) * (k & 15)) << 4]);
+    const int j = k / C::S1, o = k % C::S1;
+    const float4 a = __ldg(&tw[(o * j) << 4]);
     tw1[k] = make_float2(a.x, a.y);
   }
-  const float2* w1 = tw1 + (t % C::S1) * 16 + 1;   // w1[j - 1] = W^{o j}, j >= 1
+  const float2* tw1o = tw1 + (t % C::S1);
 
   // this thread's slice of (P - 1)/N in the last pass, for the whole launch
   float2 pr[16];
@@ -195,7 +208,7 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
     if constexpr (NP >= 3) {
       f2_load<LOGN, 1>(buf, v, t);
       dft<16, false, EX>(v);
-      f2_twiddle<false>(v, w1);
+      f2_twiddle_s<false, C::S1>(v, tw1o);
       f2_store<LOGN, 1>(buf, v, t);
       __syncthreads();
     }
@@ -215,7 +228,7 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
     }
     if constexpr (NP >= 3) {
       f2_load<LOGN, 1>(buf, v, t);
-      f2_twiddle<true>(v, w1);
+      f2_twiddle_s<true, C::S1>(v, tw1o);
       dft<16, true, EX>(v);
       f2_store<LOGN, 1>(buf, v, t);
       __syncthreads();
