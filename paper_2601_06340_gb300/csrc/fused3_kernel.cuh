@@ -8,11 +8,13 @@
 //     CTA per SM a thread can keep in registers its 16 points, the step's
 //     original field, its table twiddles and its slice of the propagator
 //     table (loaded once per launch);
-//   * each CTA writes its psi_p straight into the peer CTA's shared memory
-//     (distributed shared memory) and reads the partner band from its own
-//     after one cluster barrier per step; the exchange buffer alternates
-//     between two halves by step parity, so a write never lands on values
-//     the peer may still be reading;
+//   * each CTA sends its psi_p straight into the peer CTA's shared memory
+//     with asynchronous remote stores that complete on the peer's mbarrier
+//     (armed with the expected byte count), and reads the partner band from
+//     its own buffer once its barrier completes -- no cluster-wide barrier
+//     per step.  The buffer alternates between two halves by step parity;
+//     a half is rewritten only after the sender has received the receiver's
+//     next-step values, which the receiver sends after consuming the half;
 //   * each CTA fetches the strain/mask slice of the step into its own shared
 //     memory with a bulk asynchronous copy on an mbarrier (bounded wait).
 #pragma once
@@ -35,12 +37,51 @@ struct F3Cfg {
   static constexpr int OFF_BUF = 0;                       // [PADN]
   static constexpr int OFF_X = OFF_BUF + PADN * 8;        // [2][N] exchange
   static constexpr int OFF_PH = OFF_X + 2 * N * 8;        // [N]
-  static constexpr int OFF_MBAR = OFF_PH + N * 8;
-  static constexpr int OFF_RECPH = OFF_MBAR + 8;
+  static constexpr int OFF_MBAR = OFF_PH + N * 8;          // strain slice barrier
+  static constexpr int OFF_XBAR = OFF_MBAR + 8;            // [2] exchange barriers
+  static constexpr int OFF_RECPH = OFF_XBAR + 16;
   static constexpr int OFF_RED = OFF_RECPH + 8;           // [WARPS] double
   static constexpr int SMEM = OFF_RED + WARPS * 8;
   static_assert(LOGN >= 9 && LOGN <= 12, "cluster kernel covers 512..4096");
 };
+
+__device__ __forceinline__ uint32_t mapa_u32(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void st_async_v2(uint32_t raddr, float2 v, uint32_t rbar) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(
+          raddr),
+      "f"(v.x), "f"(v.y), "r"(rbar)
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile(
+      "{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }" ::"r"(
+          smem_u32(bar)),
+      "r"(bytes)
+      : "memory");
+}
+
+// Bounded wait with cluster-scope acquire (data written by a peer CTA).
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t b = smem_u32(bar);
+  for (int i = 0; i < (1 << 22); ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(b), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
 
 template <int LOGN, bool EX>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
@@ -64,11 +105,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
   float2* xb = reinterpret_cast<float2*>(smem + C::OFF_X);
   float2* ph = reinterpret_cast<float2*>(smem + C::OFF_PH);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::OFF_MBAR);
+  uint64_t* xbar = reinterpret_cast<uint64_t*>(smem + C::OFF_XBAR);
   float2* recph = reinterpret_cast<float2*>(smem + C::OFF_RECPH);
   double* red = reinterpret_cast<double*>(smem + C::OFF_RED);
-  float2* xpeer = cluster.map_shared_rank(xb, band ^ 1);
+  const uint32_t peer = uint32_t(band ^ 1);
+  const uint32_t xpeer = mapa_u32(smem_u32(xb), peer);          // peer's exchange buffer
+  const uint32_t xbar_peer = mapa_u32(smem_u32(xbar), peer);    // peer's exchange barriers
 
-  if (lead) mbar_init(bar);
+  if (lead) {
+    mbar_init(bar);
+    mbar_init(&xbar[0]);
+    mbar_init(&xbar[1]);
+  }
   fence_mbar_init();
 
   float2 w0[15], w1[15];
@@ -155,18 +203,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
     f2_load<LOGN, 0>(buf, v, t);
     f2_twiddle<true>(v, w0);
     dft<16, true, EX>(v);
-    // push psi_p into the peer's exchange buffer (remote stores do not
-    // stall the writer); after the barrier the partner band is local.
-    float2* xo = xpeer + (it & 1) * N;
+    // send psi_p to the peer (asynchronous remote stores completing on the
+    // peer's barrier of this parity); arm our own barrier for the peer's.
+    const int half = it & 1;
+    if (lead) mbar_expect_tx(&xbar[half], uint32_t(N) * 8u);
+    const uint32_t xo = xpeer + uint32_t(half * N) * 8u;
+    const uint32_t xbo = xbar_peer + uint32_t(half) * 8u;
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       v[j] = make_float2(org[j].x + v[j].x, org[j].y + v[j].y);
-      xo[t + j * T] = v[j];
+      st_async_v2(xo + uint32_t(t + j * T) * 8u, v[j], xbo);
     }
-    cluster.sync();   // both bands' psi_p of this step are published
+    // (after one expired wait a thread stops waiting, so a fault costs one
+    // bounded wait, not one per step; the host reports BPM_ERR_TIMEOUT)
+    if (!timed_out && !mbar_wait_cluster(&xbar[half], uint32_t((it >> 1) & 1))) timed_out = true;
 
-    if (!mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
-    const float2* xi = xb + (it & 1) * N;
+    if (!timed_out && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
+    const float2* xi = xb + half * N;
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       const float2 q = xi[t + j * T];
