@@ -92,20 +92,24 @@ int fused3_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
   return BPM_OK;
 }
 
-// Split-band cluster kernel for N = 4096 P (cluster of 2P CTAs per row).
+// Split-band cluster kernels for N = 4096 P (cluster of 2P CTAs per row):
+// P = 2 runs the one-exchange form, P = 4 the two-round form.
 template <int P, bool EX>
 int fused4_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const float4* d_tw,
                        int* d_status, cudaStream_t st) {
-  using C = F4Cfg<P>;
+  auto kern = [] {
+    if constexpr (P == 2) return fused4e_march_kernel<EX>;
+    else return fused4_march_kernel<P, EX>;
+  }();
+  constexpr int smem = P == 2 ? F4ECfg::SMEM : F4Cfg<P>::SMEM;
+  constexpr int threads = P == 2 ? F4ECfg::T : F4Cfg<P>::T;
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(fused4_march_kernel<P, EX>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused4)");
     configured = true;
   }
-  fused4_march_kernel<P, EX><<<2 * P * n_rows, C::T, C::SMEM, st>>>(d_rows, n_rows, steps, d_tw,
-                                                                   d_status);
+  kern<<<2 * P * n_rows, threads, smem, st>>>(d_rows, n_rows, steps, d_tw, d_status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "fused4 march launch");
   return BPM_OK;
