@@ -101,6 +101,38 @@ def test_strain_phasor_fp64(bpm_lib):
         assert np.max(np.abs(ph[n] - ref)) < 1e-12
 
 
+@pytest.mark.parametrize("name", ["bragg_bent", "asym_dislocation"])
+def test_strain_phasor_fp32(bpm_lib, name):
+    """FP32 plans: the unit phasor of every inside cell to FP32 accuracy (the
+    bent phase reaches hundreds of radians, so this also checks its FP64
+    reduction), zero outside."""
+    wl = _reduced(name)
+    with binding.Plan(wl, FP32) as plan:
+        mask, ph = plan.slices()
+    cr = orun.crystal_for(wl)
+    for n in range(0, wl.nz, 61):
+        inside, theta = cr(n)
+        ref = np.where(inside, np.exp(1j * theta), 0)
+        assert np.max(np.abs(ph[n] - ref)) < 4e-6, n
+
+
+def test_split_band_slices_fp32(bpm_lib):
+    """Mask and phasor of FP32 plans at N = 8192 and 16384 (stored per part
+    on the device) against the oracle, in natural order."""
+    rng = np.random.default_rng(33)
+    for nx in (8192, 16384):
+        for _ in range(2):
+            wl = inputs.serving_request(rng, nx, 200)
+            with binding.Plan(wl, FP32) as plan:
+                mask, ph = plan.slices()
+            assert np.array_equal(mask.astype(bool), orun.mask_of(wl))
+            cr = orun.crystal_for(wl)
+            for n in range(0, wl.nz, 37):
+                inside, theta = cr(n)
+                ref = np.where(inside, np.exp(1j * theta), 0)
+                assert np.max(np.abs(ph[n] - ref)) < 4e-6, (nx, n)
+
+
 def _check_full(out, ref, tol):
     """Bound both readings: every record plus the final field, and the final
     field alone (the stricter one when a band has decayed)."""
