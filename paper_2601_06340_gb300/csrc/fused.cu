@@ -5,6 +5,7 @@
 #include "fused_kernel.cuh"
 #include "fused2_kernel.cuh"
 #include "fused4_kernel.cuh"
+#include "fused4t_kernel.cuh"
 
 namespace bpm {
 
@@ -84,11 +85,11 @@ int launch_fused_layout(int logn, const RowDescF32* d_rows, int n_rows, int step
   }
 }
 
-template <int P>
+template <typename Cfg>
 static void cfg4_of(int* smem, int* rows, int* threads) {
-  *smem = F4Cfg<P>::SMEM;
+  *smem = Cfg::SMEM;
   *rows = 1;
-  *threads = F4Cfg<P>::T;
+  *threads = Cfg::T;
 }
 
 template <int L>
@@ -117,8 +118,8 @@ static void fused_cfg(int logn, int* smem, int* rows, int* threads) {
     case 10: cfg2_of<10>(smem, rows, threads); break;
     case 11: cfg2_of<11>(smem, rows, threads); break;
     case 12: cfg2_of<12>(smem, rows, threads); break;
-    case 13: cfg4_of<2>(smem, rows, threads); break;
-    default: cfg4_of<4>(smem, rows, threads); break;
+    case 13: cfg4_of<F4ECfg>(smem, rows, threads); break;
+    default: cfg4_of<F4TCfg>(smem, rows, threads); break;
   }
 }
 

@@ -1,6 +1,7 @@
-// Fused FP32 march for N = 4096 P (P = 2 or 4): one row per cluster of 2P
-// CTAs, CTA rank c = b P + h advances band b on the samples x[P m + h]
-// (m < 4096), i.e. one of the P interleaved sub-sequences of its band.
+// Split-band fused FP32 marches for N = 4096 P (P = 2 here, P = 4 in
+// fused4t_kernel.cuh): one row per cluster of 2P CTAs, CTA rank c = b P + h
+// advances band b on the samples x[P m + h] (m < 4096), i.e. one of the P
+// interleaved sub-sequences of its band.
 //
 // The length-N transform is split as N = 4096 x P (decimation in time over
 // the P sub-sequences):
@@ -9,19 +10,13 @@
 // and back:
 //   H_h[k]        = W_N^{-h k} sum_r W_P^{-h r} X'[k + 4096 r]
 //   x'[P m + h]   = sum_k H_h[k] W_4096^{-m k}               (local)
-// CTA h produces X[k + 4096 h] (its quarter or half of the spectrum), so the
-// propagator increment (P(q) - 1)/N is applied where the spectrum is owned.
-// Every CTA uses the same thread -> k map, so each exchange is "thread t of
-// every CTA of the band swaps the values of its 16 frequencies": each CTA
-// pushes its values into every peer's exchange buffer (distributed shared
-// memory), and after a cluster barrier reads them locally.  The exchange
-// buffers are indexed by (value j, thread t) -- consecutive lanes hit
-// consecutive words -- rather than by spectral position.  The step is the
-// real-space increment form of Eq. fov10 (see fused2_kernel.cuh); the band
-// coupling swaps psi_p with the CTA of the other band that holds the same
-// samples.  Four cluster barriers per step: G published, G consumed, X'
-// published, psi_p published.  (The launcher uses this kernel for P = 4; P = 2
-// runs the one-exchange kernel at the end of this file.)
+// with X' = D X, D = (P(q) - 1)/N the propagator increment of the
+// real-space increment form of Eq. fov10 (see fused2_kernel.cuh).  Every CTA
+// uses the same thread -> k map, so a spectral exchange is "thread t of
+// every CTA of the band swaps the values of its 16 frequencies", indexed by
+// (value j, thread t) in the exchange buffers so that consecutive lanes hit
+// consecutive words.  The band coupling swaps psi_p with the CTA of the
+// other band that holds the same samples.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -30,263 +25,10 @@
 
 namespace bpm {
 
-template <int P>
-struct F4Cfg {
-  static constexpr int LOCAL = 12;                 // local transform 4096
-  static constexpr int M = 1 << LOCAL;
-  static constexpr int N = M * P;
-  static constexpr int T = M / 16;                 // 256 threads per CTA
-  static constexpr int PADM = M + (M >> 4);
-  static constexpr int WARPS = T / 32;
-  static constexpr int OFF_BUF = 0;                          // [PADM]
-  static constexpr int OFF_X = OFF_BUF + PADM * 8;           // [P][M] spectrum exchange
-  static constexpr int OFF_C = OFF_X + P * M * 8;            // [M] coupling exchange
-  static constexpr int OFF_PH = OFF_C + M * 8;               // [M] strain slice
-  static constexpr int OFF_MBAR = OFF_PH + M * 8;
-  static constexpr int OFF_RECPH = OFF_MBAR + 8;
-  static constexpr int OFF_RED = OFF_RECPH + 8;              // [WARPS] double
-  static constexpr int OFF_PART = OFF_RED + WARPS * 8;       // band power of this CTA
-  static constexpr int SMEM = OFF_PART + 8;
-  static_assert(P == 2 || P == 4, "N = 8192 or 16384");
-};
-
-// x * W_P^{e} for the exact P-th roots of unity (sign = -1 forward, +1 inverse).
-template <int P>
-__device__ __forceinline__ float2 mul_root(float2 x, int e, bool inv) {
-  if constexpr (P == 2) {
-    return (e & 1) ? make_float2(-x.x, -x.y) : x;
-  } else {
-    switch (e & 3) {
-      case 0: return x;
-      case 1: return inv ? make_float2(-x.y, x.x) : make_float2(x.y, -x.x);
-      case 2: return make_float2(-x.x, -x.y);
-      default: return inv ? make_float2(x.y, -x.x) : make_float2(-x.y, x.x);
-    }
-  }
-}
-
-template <int P, bool EX>
-__global__ void __cluster_dims__(2 * P, 1, 1) __launch_bounds__(F4Cfg<P>::T, 1)
-    fused4_march_kernel(const RowDescF32* __restrict__ rows, int n_rows, int steps,
-                        const float4* __restrict__ tw, int* __restrict__ status) {
-  namespace cg = cooperative_groups;
-  using C = F4Cfg<P>;
-  using F = F2Cfg<12>;
-  constexpr int L = C::LOCAL, M = C::M, N = C::N, T = C::T, NP = F::NP;
-  extern __shared__ __align__(128) unsigned char smem[];
-  cg::cluster_group cluster = cg::this_cluster();
-
-  const int c = int(cluster.block_rank());
-  const int band = c / P, h = c % P;
-  const int row = blockIdx.x / (2 * P);
-  const int t = threadIdx.x;
-  const int lane = t & 31, warp = t >> 5;
-  const RowDescF32 d = rows[row < n_rows ? row : 0];
-  const bool lead = t == 0;
-
-  float2* buf = reinterpret_cast<float2*>(smem + C::OFF_BUF);
-  float2* xb = reinterpret_cast<float2*>(smem + C::OFF_X);
-  float2* cb = reinterpret_cast<float2*>(smem + C::OFF_C);
-  float2* ph = reinterpret_cast<float2*>(smem + C::OFF_PH);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::OFF_MBAR);
-  float2* recph = reinterpret_cast<float2*>(smem + C::OFF_RECPH);
-  double* red = reinterpret_cast<double*>(smem + C::OFF_RED);
-  double* part = reinterpret_cast<double*>(smem + C::OFF_PART);
-  float2* xpeer[P];
-#pragma unroll
-  for (int r = 0; r < P; ++r) xpeer[r] = cluster.map_shared_rank(xb, band * P + r);
-  float2* cpartner = cluster.map_shared_rank(cb, (1 - band) * P + h);
-
-  if (lead) mbar_init(bar);
-  fence_mbar_init();
-
-  // Local twiddles W_4096^{o j} = W_N^{P o j} from the length-N table.
-  float2 w0[15], w1[15];
-#pragma unroll
-  for (int j = 1; j < 16; ++j) {
-    const float4 a = __ldg(&tw[P * (t * j)]);
-    w0[j - 1] = make_float2(a.x, a.y);
-    const float4 bq = __ldg(&tw[P * (((t % F::stride(1)) * j) << 4)]);
-    w1[j - 1] = make_float2(bq.x, bq.y);
-  }
-  // Last-pass slice: local spectral index k_j of position pos_j, combine
-  // twiddle W_N^{h k_j} and the propagator increment of X[k_j + 4096 h].
-  float2 pr[16], cw[16];
-#pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const int pos = f2_pos<L, NP - 1>(t, j);
-    // digit reversal of the local 16 x 16 x 16 transform
-    const int k = (pos >> 8) + ((pos >> 4) & 15) * 16 + (pos & 15) * 256;
-    const float4 a = __ldg(&tw[h * k]);
-    cw[j] = make_float2(a.x, a.y);
-    pr[j] = __ldg(&d.prop[(band * P + h) * M + pos]);
-  }
-
-  float2 v[16];
-#pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = d.state[band * N + P * (t + j * T) + h];
-  cluster.sync();
-
-  const uint32_t slice_bytes = uint32_t(M) * 8u;
-  int pending_slot = -1;
-  bool timed_out = false;
-  const float2 am1 = d.am1, bb = d.b;
-
-  for (int it = 0; it < steps; ++it) {
-    const int n = d.n_begin + it;
-    const bool rec = d.record_every > 0 && ((n + 1) % d.record_every) == 0 &&
-                     (d.records != nullptr || d.powers != nullptr);
-    if (lead && rec) {
-      double ang = fmod(double(n + 1 - d.n_phase0) * d.gphase, 6.283185307179586);
-      double sa, ca;
-      sincos(ang, &sa, &ca);
-      *recph = make_float2(float(ca), float(sa));
-    }
-    float2 org[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) org[j] = v[j];
-    dft<16, false, EX>(v);
-    f2_twiddle<false>(v, w0);
-    f2_store<L, 0>(buf, v, t);
-    __syncthreads();
-    if (lead) bulk_load(ph, d.phasor + size_t(n) * N + size_t(h) * M, slice_bytes, bar);
-    f2_load<L, 1>(buf, v, t);
-    dft<16, false, EX>(v);
-    f2_twiddle<false>(v, w1);
-    f2_store<L, 1>(buf, v, t);
-    __syncthreads();
-    f2_load<L, NP - 1>(buf, v, t);
-    dft<16, false, EX>(v);                       // v[j] = F_h[k_j]
-    // ---- forward combine across the band's CTAs
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const float2 g = cmul_f(v[j], cw[j].x, cw[j].y);
-#pragma unroll
-      for (int r = 0; r < P; ++r) xpeer[r][h * M + j * T + t] = g;
-    }
-    cluster.sync();                              // G published
-    if (lead && pending_slot >= 0) {
-      // band power of record `pending_slot`: the P parts of this band
-      if (h == 0) {
-        double s = 0.0;
-        for (int r = 0; r < P; ++r) s += *cluster.map_shared_rank(part, band * P + r);
-        d.powers[2 * pending_slot + band] = s * d.dx_um;
-      }
-      pending_slot = -1;
-    }
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      float2 s = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int hh = 0; hh < P; ++hh) {
-        const float2 g = mul_root<P>(xb[hh * M + j * T + t], hh * h, false);
-        s = make_float2(s.x + g.x, s.y + g.y);
-      }
-      const float2 dd = pr[j];
-      v[j] = make_float2(fmaf(s.x, dd.x, -(s.y * dd.y)), fmaf(s.x, dd.y, s.y * dd.x));
-    }
-    cluster.sync();                              // G consumed
-#pragma unroll
-    for (int j = 0; j < 16; ++j)
-#pragma unroll
-      for (int r = 0; r < P; ++r) xpeer[r][h * M + j * T + t] = v[j];
-    cluster.sync();                              // X' published
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      float2 s = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int rr = 0; rr < P; ++rr) {
-        const float2 g = mul_root<P>(xb[rr * M + j * T + t], h * rr, true);
-        s = make_float2(s.x + g.x, s.y + g.y);
-      }
-      v[j] = cmul_f(s, cw[j].x, -cw[j].y);
-    }
-    dft<16, true, EX>(v);
-    f2_store<L, NP - 1>(buf, v, t);
-    __syncthreads();
-    f2_load<L, 1>(buf, v, t);
-    f2_twiddle<true>(v, w1);
-    dft<16, true, EX>(v);
-    f2_store<L, 1>(buf, v, t);
-    __syncthreads();
-    f2_load<L, 0>(buf, v, t);
-    f2_twiddle<true>(v, w0);
-    dft<16, true, EX>(v);
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      v[j] = make_float2(org[j].x + v[j].x, org[j].y + v[j].y);
-      cpartner[t + j * T] = v[j];
-    }
-    cluster.sync();                              // psi_p published to the other band
-
-    if (!mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const float2 q = cb[t + j * T];
-      float2 e = ph[t + j * T];
-      const bool inside = (e.x != 0.f) | (e.y != 0.f);
-      if (band) e.y = -e.y;
-      const float ax = inside ? am1.x : 0.f, ay = inside ? am1.y : 0.f;
-      const float cx = fmaf(bb.x, e.x, -(bb.y * e.y)), cy = fmaf(bb.x, e.y, bb.y * e.x);
-      const float2 p = v[j];
-      float rx = fmaf(ax, p.x, p.x);
-      rx = fmaf(-ay, p.y, rx);
-      rx = fmaf(cx, q.x, rx);
-      rx = fmaf(-cy, q.y, rx);
-      float ry = fmaf(ax, p.y, p.y);
-      ry = fmaf(ay, p.x, ry);
-      ry = fmaf(cx, q.y, ry);
-      ry = fmaf(cy, q.x, ry);
-      v[j] = make_float2(rx, ry);
-    }
-
-    if (rec) {
-      const int slot = (n + 1) / d.record_every - 1;
-      const float2 g = *recph;
-      float s = 0.f;
-      float2* r0 = d.records ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const float2 p = v[j];
-        s = fmaf(p.x, p.x, fmaf(p.y, p.y, s));
-        if (r0)
-          r0[P * (t + j * T) + h] =
-              make_float2(fmaf(p.x, g.x, -(p.y * g.y)), fmaf(p.x, g.y, p.y * g.x));
-      }
-      if (d.powers) {
-        double ds = s;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, off);
-        if (lane == 0) red[warp] = ds;
-        __syncthreads();
-        if (lead) {
-          double tot = 0.0;
-          for (int w = 0; w < C::WARPS; ++w) tot += red[w];
-          *part = tot;
-          pending_slot = slot;
-        }
-      }
-    }
-  }
-
-  cluster.sync();
-  if (lead && pending_slot >= 0 && h == 0) {
-    double s = 0.0;
-    for (int r = 0; r < P; ++r) s += *cluster.map_shared_rank(part, band * P + r);
-    d.powers[2 * pending_slot + band] = s * d.dx_um;
-  }
-#pragma unroll
-  for (int j = 0; j < 16; ++j) d.state[band * N + P * (t + j * T) + h] = v[j];
-  if (timed_out && lead) atomicOr(status, kStatusWaitTimeout);
-  cluster.sync();   // peers may still read our shared memory
-}
-
-
-// ---------------------------------------------------------------------------
 // N = 8192 (P = 2) with one spectral exchange per step.
 //
-// For P = 2 the forward combine, the propagator increment D = (P(q) - 1)/N
-// and the inverse combine above collapse, per local frequency k, into a 2x2
+// For P = 2 the forward combine, the propagator increment and the inverse
+// combine above collapse, per local frequency k, into a 2x2
 // circulant over the band's two halves:
 //   H_h[k] = W_N^{-h k} (E_0[k] G_h[k] + E_1[k] G_{1-h}[k]),
 //   E_0[k] = D[k] + D[k + 4096],   E_1[k] = D[k] - D[k + 4096],

@@ -1,0 +1,389 @@
+// Fused FP32 march for N = 16384: one row per cluster of 8 CTAs, CTA rank
+// c = 4 band + h advances band b on the samples x[4 m + h] (m < 4096), with
+// one all-to-all spectral exchange per step.
+//
+// With the band split over P = 4 interleaved sub-sequences, the forward
+// recombination of the partial spectra G_h = W_N^{h k} F_h, the propagator
+// increment D = (P(q) - 1)/N and the inverse recombination collapse, per
+// local frequency k, into a circulant over the four parts:
+//   H_h[k] = W_N^{-h k} sum_{d=0..3} E_d[k] G_{(h+d) mod 4}[k],
+//   E_d[k] = sum_r W_4^{d r} D[k + 4096 r]
+// (tabulated in FP64, rounded once).  Each CTA sends its G to the three other
+// CTAs of its band and needs nothing else from them, so one exchange of
+// 3 x 32 KB per CTA replaces the two all-to-all rounds of the unfused form.
+//
+// Storage.  Shared memory holds the FFT scratch, the three received G, the
+// other band's psi_p (double-buffered by step parity) and the strain slice:
+// 226 KB.  The 64 complex E values of a thread (4 per owned frequency) live
+// in tensor memory: written once per launch with tcgen05.st, read back in
+// chunks of two frequencies with tcgen05.ld each step (256 columns of the SM's 512).
+//
+// Synchronisation, all point to point, no cluster-wide barrier in the march:
+//   * G arrives by st.async on the receiver's mbarrier (expected bytes);
+//   * a CTA that has read its three G slots arrives remotely on each sender's
+//     "free" barrier; a sender waits for all three before writing the next
+//     step's G (normally long satisfied: a whole inverse FFT lies between);
+//   * psi_p goes to the other band as in the 2-CTA kernel (fused3_kernel.cuh).
+// Band powers: the parts of CTAs h = 1..3 ride on the next step's G to h = 0,
+// which sums the four in a fixed order.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "fused4_kernel.cuh"
+
+namespace bpm {
+
+struct F4TCfg {
+  static constexpr int M = 4096;
+  static constexpr int N = 4 * M;
+  static constexpr int T = M / 16;
+  static constexpr int PADM = M + (M >> 4);
+  static constexpr int WARPS = T / 32;
+  static constexpr int TMEM_COLS = 256;                    // 2 x 128 columns per lane
+  static constexpr int OFF_BUF = 0;                        // [PADM]
+  static constexpr int OFF_G = OFF_BUF + PADM * 8;         // [3][M] G of parts h+1, h+2, h+3
+  static constexpr int OFF_C = OFF_G + 3 * M * 8;          // [2][M] other band's psi_p
+  static constexpr int OFF_PH = OFF_C + 2 * M * 8;         // [M] strain slice
+  static constexpr int OFF_MBAR = OFF_PH + M * 8;          // strain-slice barrier
+  static constexpr int OFF_GBAR = OFF_MBAR + 8;            // G arrival
+  static constexpr int OFF_FREE = OFF_GBAR + 8;            // peers have read our G
+  static constexpr int OFF_CBAR = OFF_FREE + 8;            // [2] psi_p arrival
+  static constexpr int OFF_PPEER = OFF_CBAR + 16;          // [3] band-power parts (h = 0)
+  static constexpr int OFF_RECPH = OFF_PPEER + 24;
+  static constexpr int OFF_RED = OFF_RECPH + 8;            // [WARPS] double
+  static constexpr int OFF_PART = OFF_RED + WARPS * 8;
+  static constexpr int OFF_TMEM = OFF_PART + 8;            // allocated TMEM address
+  static constexpr int SMEM = OFF_TMEM + 8;
+  static_assert(SMEM <= 232448, "fits one SM");
+};
+
+__device__ __forceinline__ void mbar_init_count(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+// Arrive (release, cluster scope) on a barrier in another CTA's shared memory.
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t raddr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(raddr)
+               : "memory");
+}
+
+// Tensor memory: allocation by one warp, per-thread loads/stores of
+// consecutive columns of the thread's own lane (32x32b shape).
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst_smem)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31, %32};" ::"r"(taddr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]),
+      "f"(v[8]), "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]),
+      "f"(v[15]), "f"(v[16]), "f"(v[17]), "f"(v[18]), "f"(v[19]), "f"(v[20]), "f"(v[21]),
+      "f"(v[22]), "f"(v[23]), "f"(v[24]), "f"(v[25]), "f"(v[26]), "f"(v[27]), "f"(v[28]),
+      "f"(v[29]), "f"(v[30]), "f"(v[31])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]),
+        "=f"(v[7]), "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]),
+        "=f"(v[14]), "=f"(v[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <bool EX>
+__global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
+    fused4t_march_kernel(const RowDescF32* __restrict__ rows, int n_rows, int steps,
+                         const float4* __restrict__ tw, int* __restrict__ status) {
+  namespace cg = cooperative_groups;
+  using C = F4TCfg;
+  using F = F2Cfg<12>;
+  constexpr int L = 12, M = C::M, N = C::N, T = C::T, NP = F::NP;
+  extern __shared__ __align__(128) unsigned char smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+
+  const int c = int(cluster.block_rank());
+  const int band = c >> 2, h = c & 3;
+  const int row = blockIdx.x >> 3;
+  const int t = threadIdx.x;
+  const int lane = t & 31, warp = t >> 5;
+  const RowDescF32 d = rows[row < n_rows ? row : 0];
+  const bool lead = t == 0;
+
+  float2* buf = reinterpret_cast<float2*>(smem + C::OFF_BUF);
+  float2* gx = reinterpret_cast<float2*>(smem + C::OFF_G);
+  float2* cb = reinterpret_cast<float2*>(smem + C::OFF_C);
+  float2* ph = reinterpret_cast<float2*>(smem + C::OFF_PH);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::OFF_MBAR);
+  uint64_t* gbar = reinterpret_cast<uint64_t*>(smem + C::OFF_GBAR);
+  uint64_t* gfree = reinterpret_cast<uint64_t*>(smem + C::OFF_FREE);
+  uint64_t* cbar = reinterpret_cast<uint64_t*>(smem + C::OFF_CBAR);
+  double* ppeer = reinterpret_cast<double*>(smem + C::OFF_PPEER);
+  float2* recph = reinterpret_cast<float2*>(smem + C::OFF_RECPH);
+  double* red = reinterpret_cast<double*>(smem + C::OFF_RED);
+  double* part = reinterpret_cast<double*>(smem + C::OFF_PART);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::OFF_TMEM);
+
+  // peer e (1..3) of the band is part (h + e) & 3; our G goes to its slot
+  // 3 - e (the receiver indexes slots by d - 1, d = sender - receiver mod 4)
+  uint32_t g_to[3], gbar_to[3], free_to[3];
+#pragma unroll
+  for (int e = 1; e <= 3; ++e) {
+    const uint32_t r = uint32_t(band * 4 + ((h + e) & 3));
+    g_to[e - 1] = mapa_u32(smem_u32(gx + (3 - e) * M), r);
+    gbar_to[e - 1] = mapa_u32(smem_u32(gbar), r);
+    free_to[e - 1] = mapa_u32(smem_u32(gfree), r);
+  }
+  const uint32_t pp_to = mapa_u32(smem_u32(ppeer + (h > 0 ? h - 1 : 0)), uint32_t(band * 4));
+  const uint32_t partner = uint32_t(c ^ 4);
+  const uint32_t c_part = mapa_u32(smem_u32(cb), partner);
+  const uint32_t cbar_part = mapa_u32(smem_u32(cbar), partner);
+
+  if (lead) {
+    mbar_init(bar);
+    mbar_init(gbar);
+    mbar_init_count(gfree, 3);
+    mbar_init(&cbar[0]);
+    mbar_init(&cbar[1]);
+  }
+  fence_mbar_init();
+  if (warp == 0) tmem_alloc(tmem_slot, C::TMEM_COLS);
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  // this thread's 128 columns: lanes 32 (warp mod 4) + lane, columns from 0
+  // (warps 0-3) or 128 (warps 4-7)
+  const uint32_t tbase = *tmem_slot + (uint32_t(32 * (warp & 3)) << 16) +
+                         uint32_t(warp >= 4 ? 128 : 0);
+
+  float2 w0[15], w1[15];
+#pragma unroll
+  for (int j = 1; j < 16; ++j) {
+    const float4 a = __ldg(&tw[4 * (t * j)]);
+    w0[j - 1] = make_float2(a.x, a.y);
+    const float4 bq = __ldg(&tw[4 * (((t % F::stride(1)) * j) << 4)]);
+    w1[j - 1] = make_float2(bq.x, bq.y);
+  }
+  // combine twiddles W_N^{h k_j}; E_d[k_j] into tensor memory, chunk q of
+  // 4 frequencies at columns 32 q: (j - 4q) * 8 + 2 d + {re, im}
+  float2 cw[16];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float ev[32];
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int j = 4 * q + jj;
+      const int pos = f2_pos<L, NP - 1>(t, j);
+      const int k = (pos >> 8) + ((pos >> 4) & 15) * 16 + (pos & 15) * 256;
+      const float4 a = __ldg(&tw[h * k]);
+      cw[j] = make_float2(a.x, a.y);
+#pragma unroll
+      for (int dl = 0; dl < 4; ++dl) {
+        const float2 e = __ldg(&d.prop[(band * 4 + dl) * M + pos]);
+        ev[jj * 8 + 2 * dl] = e.x;
+        ev[jj * 8 + 2 * dl + 1] = e.y;
+      }
+    }
+    tmem_st32(tbase + uint32_t(32 * q), ev);
+  }
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+
+  float2 v[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = d.state[band * N + 4 * (t + j * T) + h];
+  cluster.sync();   // every CTA's barriers initialised before any remote operation
+
+  const uint32_t slice_bytes = uint32_t(M) * 8u;
+  bool timed_out = false;
+  double my_part = 0.0;
+  const float2 am1 = d.am1, bb = d.b;
+  const bool pow_on = d.powers != nullptr && d.record_every > 0;
+
+  for (int it = 0; it < steps; ++it) {
+    const int n = d.n_begin + it;
+    const int half = it & 1;
+    const bool rec = d.record_every > 0 && ((n + 1) % d.record_every) == 0 &&
+                     (d.records != nullptr || d.powers != nullptr);
+    const bool part_due = pow_on && it > 0 && (n % d.record_every) == 0;
+    if (lead && rec) {
+      double ang = fmod(double(n + 1 - d.n_phase0) * d.gphase, 6.283185307179586);
+      double sa, ca;
+      sincos(ang, &sa, &ca);
+      *recph = make_float2(float(ca), float(sa));
+    }
+    float2 org[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) org[j] = v[j];
+    dft<16, false, EX>(v);
+    f2_twiddle<false>(v, w0);
+    f2_store<L, 0>(buf, v, t);
+    __syncthreads();
+    if (lead) {
+      bulk_load(ph, d.phasor + size_t(n) * N + size_t(h) * M, slice_bytes, bar);
+      mbar_expect_tx(gbar, 3u * uint32_t(M) * 8u + ((part_due && h == 0) ? 24u : 0u));
+      if (part_due) {
+        double s = 0.0;
+        for (int w = 0; w < C::WARPS; ++w) s += red[w];
+        my_part = s;
+      }
+    }
+    f2_load<L, 1>(buf, v, t);
+    dft<16, false, EX>(v);
+    f2_twiddle<false>(v, w1);
+    f2_store<L, 1>(buf, v, t);
+    __syncthreads();
+    f2_load<L, NP - 1>(buf, v, t);
+    dft<16, false, EX>(v);                       // v[j] = F_h[k_j]
+    // the peers have read our previous G before we overwrite their slots
+    if (it > 0 && !timed_out && !mbar_wait_cluster(gfree, uint32_t((it - 1) & 1))) timed_out = true;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      v[j] = cmul_f(v[j], cw[j].x, cw[j].y);     // G_h[k_j]
+#pragma unroll
+      for (int e = 0; e < 3; ++e) st_async_v2(g_to[e] + uint32_t(j * T + t) * 8u, v[j], gbar_to[e]);
+    }
+    if (lead && part_due && h > 0) st_async_f64(pp_to, my_part, gbar_to[3 - h]);
+    if (!timed_out && !mbar_wait_cluster(gbar, uint32_t(it & 1))) timed_out = true;
+    if (lead && part_due && h == 0)
+      d.powers[2 * (n / d.record_every - 1) + band] =
+          (((my_part + ppeer[0]) + ppeer[1]) + ppeer[2]) * d.dx_um;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      float ev[16];
+      tmem_ld16(tbase + uint32_t(16 * q), ev);
+#pragma unroll
+      for (int jj = 0; jj < 2; ++jj) {
+        const int j = 2 * q + jj;
+        const float2 g0 = v[j];
+        float sx = fmaf(ev[jj * 8], g0.x, -(ev[jj * 8 + 1] * g0.y));
+        float sy = fmaf(ev[jj * 8], g0.y, ev[jj * 8 + 1] * g0.x);
+#pragma unroll
+        for (int dl = 1; dl < 4; ++dl) {
+          const float2 g = gx[(dl - 1) * M + j * T + t];
+          const float ex = ev[jj * 8 + 2 * dl], ey = ev[jj * 8 + 2 * dl + 1];
+          sx = fmaf(ex, g.x, sx);
+          sx = fmaf(-ey, g.y, sx);
+          sy = fmaf(ex, g.y, sy);
+          sy = fmaf(ey, g.x, sy);
+        }
+        v[j] = cmul_f(make_float2(sx, sy), cw[j].x, -cw[j].y);
+      }
+    }
+    __syncthreads();                             // all of our G slots read
+    if (lead)
+#pragma unroll
+      for (int e = 0; e < 3; ++e) mbar_arrive_remote(free_to[e]);
+    dft<16, true, EX>(v);
+    f2_store<L, NP - 1>(buf, v, t);
+    __syncthreads();
+    f2_load<L, 1>(buf, v, t);
+    f2_twiddle<true>(v, w1);
+    dft<16, true, EX>(v);
+    f2_store<L, 1>(buf, v, t);
+    __syncthreads();
+    f2_load<L, 0>(buf, v, t);
+    f2_twiddle<true>(v, w0);
+    dft<16, true, EX>(v);
+    {
+      if (lead) mbar_expect_tx(&cbar[half], uint32_t(M) * 8u);
+      const uint32_t co = c_part + uint32_t(half * M) * 8u;
+      const uint32_t cbo = cbar_part + uint32_t(half) * 8u;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        v[j] = make_float2(org[j].x + v[j].x, org[j].y + v[j].y);
+        st_async_v2(co + uint32_t(t + j * T) * 8u, v[j], cbo);
+      }
+    }
+    if (!timed_out && !mbar_wait_cluster(&cbar[half], uint32_t((it >> 1) & 1))) timed_out = true;
+    if (!timed_out && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
+    const float2* ci = cb + half * M;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const float2 q = ci[t + j * T];
+      float2 e = ph[t + j * T];
+      const bool inside = (e.x != 0.f) | (e.y != 0.f);
+      if (band) e.y = -e.y;
+      const float ax = inside ? am1.x : 0.f, ay = inside ? am1.y : 0.f;
+      const float cx = fmaf(bb.x, e.x, -(bb.y * e.y)), cy = fmaf(bb.x, e.y, bb.y * e.x);
+      const float2 p = v[j];
+      float rx = fmaf(ax, p.x, p.x);
+      rx = fmaf(-ay, p.y, rx);
+      rx = fmaf(cx, q.x, rx);
+      rx = fmaf(-cy, q.y, rx);
+      float ry = fmaf(ax, p.y, p.y);
+      ry = fmaf(ay, p.x, ry);
+      ry = fmaf(cx, q.y, ry);
+      ry = fmaf(cy, q.x, ry);
+      v[j] = make_float2(rx, ry);
+    }
+
+    if (rec) {
+      const int slot = (n + 1) / d.record_every - 1;
+      const float2 g = *recph;
+      float s = 0.f;
+      float2* r0 = d.records ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float2 p = v[j];
+        s = fmaf(p.x, p.x, fmaf(p.y, p.y, s));
+        if (r0)
+          r0[4 * (t + j * T) + h] =
+              make_float2(fmaf(p.x, g.x, -(p.y * g.y)), fmaf(p.x, g.y, p.y * g.x));
+      }
+      if (d.powers) {
+        double ds = s;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, off);
+        if (lane == 0) red[warp] = ds;   // summed by the lead after the next barrier
+      }
+    }
+  }
+
+  __syncthreads();
+  const bool last_due = pow_on && steps > 0 && ((d.n_begin + steps) % d.record_every) == 0;
+  if (lead && last_due) {
+    double s = 0.0;
+    for (int w = 0; w < C::WARPS; ++w) s += red[w];
+    *part = s;
+  }
+  cluster.sync();
+  if (lead && last_due && h == 0) {
+    double s = *part;
+    for (int r = 1; r < 4; ++r) s += *cluster.map_shared_rank(part, band * 4 + r);
+    d.powers[2 * ((d.n_begin + steps) / d.record_every - 1) + band] = s * d.dx_um;
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j) d.state[band * N + 4 * (t + j * T) + h] = v[j];
+  if (timed_out && lead) atomicOr(status, kStatusWaitTimeout);
+  tmem_fence_before();
+  cluster.sync();   // peers may still read our shared memory
+  tmem_fence_after();
+  if (warp == 0) tmem_dealloc(*tmem_slot, C::TMEM_COLS);
+}
+
+}  // namespace bpm

@@ -8,6 +8,7 @@
 #include "fused2_kernel.cuh"
 #include "fused3_kernel.cuh"
 #include "fused4_kernel.cuh"
+#include "fused4t_kernel.cuh"
 
 namespace bpm {
 
@@ -93,16 +94,17 @@ int fused3_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
 }
 
 // Split-band cluster kernels for N = 4096 P (cluster of 2P CTAs per row):
-// P = 2 runs the one-exchange form, P = 4 the two-round form.
+// both run the one-exchange form (P = 4 with its tables in tensor memory).
 template <int P, bool EX>
 int fused4_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const float4* d_tw,
                        int* d_status, cudaStream_t st) {
+  static_assert(P == 2 || P == 4, "N = 8192 or 16384");
   auto kern = [] {
     if constexpr (P == 2) return fused4e_march_kernel<EX>;
-    else return fused4_march_kernel<P, EX>;
+    else return fused4t_march_kernel<EX>;
   }();
-  constexpr int smem = P == 2 ? F4ECfg::SMEM : F4Cfg<P>::SMEM;
-  constexpr int threads = P == 2 ? F4ECfg::T : F4Cfg<P>::T;
+  constexpr int smem = P == 2 ? F4ECfg::SMEM : F4TCfg::SMEM;
+  constexpr int threads = P == 2 ? F4ECfg::T : F4TCfg::T;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

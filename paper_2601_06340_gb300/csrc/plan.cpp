@@ -66,6 +66,8 @@ double delta_q(double q, double s, double c, int sign) {
 
 }  // namespace
 
+static void unit_root(int m, int n, double* cr, double* ci);
+
 int validate_problem(const bpm_problem* p, std::string* why) {
   auto bad = [&](const std::string& m) { *why = m; return BPM_ERR_INVALID; };
   if (!p) return bad("problem is NULL");
@@ -158,44 +160,33 @@ std::vector<int> fft_output_order(int logn) {
 void fused_prop_table(const bpm_plan_s* plan, int row, std::vector<float2>* out) {
   const EnergyConsts& c = plan->ec[row];
   int n = plan->nx;
-  if (plan->logn == kSplitLogN) {
-    // N = 8192, one-exchange form: [band][E_0 | E_1][local position] with
-    // E_0 = D[k] + D[k + 4096], E_1 = D[k] - D[k + 4096], D = (P - 1)/N at
-    // the local transform's digit-reversed position's spectral index k.
-    const int m = 1 << 12;
-    std::vector<int> local = fft_output_order(12);
-    out->assign(2 * size_t(n), float2{0.f, 0.f});
-    for (int band = 0; band < 2; ++band) {
-      int sign = band == 0 ? +1 : -1;
-      for (int pos = 0; pos < m; ++pos) {
-        cd dk[2];
-        for (int r = 0; r < 2; ++r) {
-          double q = fftfreq_q(local[pos] + m * r, n, c.dxh);
-          dk[r] = expm1_i(cd(c.dzh * delta_q(q, c.s, c.c, sign), 0.0)) * (1.0 / double(n));
-        }
-        const cd e0 = dk[0] + dk[1], e1 = dk[0] - dk[1];
-        (*out)[size_t(band) * n + pos] = float2{float(e0.real()), float(e0.imag())};
-        (*out)[size_t(band) * n + m + pos] = float2{float(e1.real()), float(e1.imag())};
-      }
-    }
-    return;
-  }
-  if (plan->logn > kSplitLogN) {
-    // [band][part r][local position]: the local 4096-point transform's
-    // digit-reversed position pos holds spectral index k(pos) + 4096 r.
+  if (plan->logn >= kSplitLogN) {
+    // Split bands (N = 4096 P, P = 2 or 4), one-exchange form:
+    // [band][delta][local position] with E_delta[k] = sum_r W_P^{delta r}
+    // D[k + 4096 r], W_P = exp(-2 pi i / P), D = (P(q) - 1)/N at the local
+    // 4096-point transform's digit-reversed position's spectral index k.
     const int m = 1 << 12, parts = n / m;
     std::vector<int> local = fft_output_order(12);
     out->assign(2 * size_t(n), float2{0.f, 0.f});
+    std::vector<cd> dk(parts), w(parts);
+    for (int r = 0; r < parts; ++r) {
+      double cr, ci;
+      unit_root(r, parts, &cr, &ci);
+      w[r] = cd(cr, ci);
+    }
     for (int band = 0; band < 2; ++band) {
       int sign = band == 0 ? +1 : -1;
-      for (int r = 0; r < parts; ++r)
-        for (int pos = 0; pos < m; ++pos) {
+      for (int pos = 0; pos < m; ++pos) {
+        for (int r = 0; r < parts; ++r) {
           double q = fftfreq_q(local[pos] + m * r, n, c.dxh);
-          double ph = c.dzh * delta_q(q, c.s, c.c, sign);
-          cd dd = expm1_i(cd(ph, 0.0)) * (1.0 / double(n));
-          (*out)[size_t(band) * n + size_t(r) * m + pos] =
-              float2{float(dd.real()), float(dd.imag())};
+          dk[r] = expm1_i(cd(c.dzh * delta_q(q, c.s, c.c, sign), 0.0)) * (1.0 / double(n));
         }
+        for (int dl = 0; dl < parts; ++dl) {
+          cd e(0.0, 0.0);
+          for (int r = 0; r < parts; ++r) e += w[(dl * r) % parts] * dk[r];
+          (*out)[size_t(band) * n + size_t(dl) * m + pos] = float2{float(e.real()), float(e.imag())};
+        }
+      }
     }
     return;
   }
