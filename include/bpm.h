@@ -82,7 +82,7 @@ enum bpm_strain_kind {
 };
 
 typedef struct {
-  int32_t nx;              /* transverse points: power of two in [8, 8192]     */
+  int32_t nx;              /* transverse points: power of two in [8, 16384]    */
   int32_t nz;              /* z steps in the plan's march: >= 1                */
   double dx_um;            /* > 0                                              */
   double dz_um;            /* > 0                                              */
