@@ -9,8 +9,8 @@ resident in device memory; ``e2e`` is the same metric through the host
 C-ABI call (pinned host buffers, copies inside the timed region).  The line
 also carries the plain FP64 GPU path, both paths' relative L2 errors
 against the FP64 oracle, single-solve latency percentiles, the batched
-256-energy workload, the roofline of the dominant kernel and the oracle's
-own throughput on the host cores.
+256-energy workload, the 256-angle rocking-curve scan, the serving run, the roofline of the
+dominant kernel and the oracle's own throughput on the host cores.
 
 ``--impl reference`` times the FP64 oracle instead (bounded samples of the
 same march on the host cores).  Multi-GPU runs (torchrun) are independent
@@ -192,6 +192,66 @@ def serving_run(n_requests: int, rate: float, warm: int = 40, n_check: int = 8):
             "alone_vs_mix_max_rel_l2": max(errs) if errs else None}
 
 
+def curve_fwhm(x: np.ndarray, y: np.ndarray) -> float:
+    """Full width at half maximum of a sampled curve (linear interpolation
+    at the outermost half-maximum crossings around the peak)."""
+    i = int(np.argmax(y))
+    half = 0.5 * y[i]
+    lo = i
+    while lo > 0 and y[lo - 1] >= half:
+        lo -= 1
+    hi = i
+    while hi < len(y) - 1 and y[hi + 1] >= half:
+        hi += 1
+    xl = x[lo] if lo == 0 else x[lo - 1] + (half - y[lo - 1]) * (x[lo] - x[lo - 1]) / (y[lo] - y[lo - 1])
+    xr = x[hi] if hi == len(y) - 1 else x[hi] + (y[hi] - half) * (x[hi + 1] - x[hi]) / (y[hi] - y[hi + 1])
+    return float(xr - xl)
+
+
+def rocking_run(dev, stream, barrier, max_over_ranks, world, rank, check, steps=3):
+    """256 incidence angles of a Laue slab as the rows of one batched march;
+    reflectivity per row from the FP64 band powers."""
+    import torch
+    from paper_2601_06340_gb300 import binding, inputs
+    FP32 = binding.BPM_FP32_FUSED
+    wr = inputs.rocking_scan()
+    plan = binding.Plan(wr, FP32)
+    x = torch.from_numpy(wr.psi0.astype(np.complex64)).to(dev)
+    y = torch.empty_like(x)
+    pw = torch.zeros((wr.batch, 1, 2), dtype=torch.float64, device=dev)
+
+    def march():
+        binding.bpm_propagate_device(plan.handle, x, y, None, pw, 0, wr.nz, stream.cuda_stream)
+    march()
+    barrier()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        march()
+    b.record(stream)
+    barrier()
+    ms = max_over_ranks(a.elapsed_time(b)) / steps
+    p_in = wr.dx_um * np.sum(np.abs(wr.psi0[:, 0]) ** 2, axis=-1)
+    refl = pw[:, -1, 1].cpu().numpy() / p_in
+    angles = wr.meta["angles_urad"]
+    out = {"workload": "rocking_scan: symmetric Laue slab 100 um, 8 keV, 256 incidence angles "
+                       "over +-50 urad, Nx=2048, Nz=2000, Gaussian 200 um FWHM, one batch",
+           "value": world * wr.cell_updates / (ms * 1e-3), "unit": UNIT, "ms_per_scan": ms,
+           "reflectivity": {"peak": float(refl.max()),
+                            "peak_angle_urad": float(angles[int(np.argmax(refl))]),
+                            "fwhm_urad": curve_fwhm(angles, refl)}}
+    if check:
+        from oracle import run as orun
+        rows = [128, 140]
+        ref = orun.run_workload(wr, rows=rows)
+        got = y.cpu().numpy().astype(np.complex128)[rows]
+        errs = [rel_l2_bands(got[i:i + 1], ref.psi[i:i + 1]) for i in range(len(rows))]
+        out["rel_l2_err_sampled_rows"] = [max(e[0] for e in errs), max(e[1] for e in errs)]
+        out["sampled_rows"] = rows
+    plan.close()
+    return out
+
+
 def run_reference(args, rank, world):
     """FP64 oracle on the host cores: each step is a bounded sample (the
     first `sample_steps` z-steps of the march)."""
@@ -251,6 +311,13 @@ def run_gpu(args, rank, world):
             print(json.dumps({"only": "serving",
                               **serving_run(args.serving_requests, args.serving_rate)}),
                   flush=True)
+        return
+
+    if args.only == "rocking":
+        r = rocking_run(dev, stream, barrier, max_over_ranks, world, rank, check=False,
+                        steps=args.steps)
+        if rank == 0:
+            print(json.dumps({"only": "rocking", **r}), flush=True)
         return
 
     if args.only == "batched":
@@ -400,6 +467,12 @@ def run_gpu(args, rank, world):
                    "ms_per_march": msb}
         planb.close()
 
+    # ---- rocking curve: incidence angles as the rows of one batch ----------
+    rocking = None
+    if not args.skip_rocking:
+        rocking = rocking_run(dev, stream, barrier, max_over_ranks, world, rank,
+                              check=rank == 0 and not args.skip_oracle)
+
     # ---- serving: Poisson stream of mixed solves through submit/poll ------
     serving = None
     if not args.skip_serving and rank == 0:
@@ -423,6 +496,10 @@ def run_gpu(args, rank, world):
         ach_b = batched["value"] / world * FLOPS_PER_CELL(4096) / 1e12
         batched["roofline"] = {"bound": "alu", "achieved": ach_b, "peak": peak_tflops,
                                "unit": "TFLOP/s", "frac": ach_b / peak_tflops}
+    if rocking is not None:
+        ach_r = rocking["value"] / world * FLOPS_PER_CELL(2048) / 1e12
+        rocking["roofline"] = {"bound": "alu", "achieved": ach_r, "peak": peak_tflops,
+                               "unit": "TFLOP/s", "frac": ach_r / peak_tflops}
 
     if rank == 0:
         lat = np.array(per_ms)
@@ -441,6 +518,7 @@ def run_gpu(args, rank, world):
                            "rel_l2_err": err64, "tolerance": 1e-10,
                            "fused_speedup": value / value64},
             "batched": batched,
+            "rocking": rocking,
             "serving": serving,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -462,11 +540,12 @@ def main():
     ap.add_argument("--skip-oracle", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--skip-rocking", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=440)
     ap.add_argument("--serving-rate", type=float, default=200.0)
-    ap.add_argument("--only", default="all", choices=["all", "fused", "batched", "serving"],
-                    help="time only the fused single-solve march, or only the 256-energy "
-                         "batch (used for profiling runs)")
+    ap.add_argument("--only", default="all", choices=["all", "fused", "batched", "rocking", "serving"],
+                    help="time only the fused single-solve march, the 256-energy batch, "
+                         "the 256-angle rocking scan or the serving run (profiling runs)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

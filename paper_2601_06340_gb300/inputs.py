@@ -20,6 +20,8 @@ project's benchmark table:
                          Nx=4096, Nz=6000, SASE-like random spectral phases
 5. ``serving_stream``    Poisson request stream of mixed solves (see
                          ``serving_requests``)
+6. ``rocking_scan``      256 incidence angles over +-50 urad through one Laue
+                         slab (100 um), Nx=2048, Nz=2000, one batched launch
 
 Each builder takes optional smaller ``nx`` / ``nz`` so that the same
 geometry can be run at sizes the FP64 oracle finishes in seconds.
@@ -218,6 +220,48 @@ def pulse_batched(nx: int = 4096, nz: int = 6000, n_energy: int = 256,
                      thickness_um=thickness, surf_x_um=0.0, surf_z_um=0.0),
         strain=dict(kind=STRAIN_BENT, params=[radius_um, nu, 0.0, 0.0]),
         psi0=psi0, meta=dict(centre_ev=centre_ev, sigma_ev=sigma_ev))
+
+
+def rocking_angles_urad(n_angles: int = 256, span_urad: float = 100.0) -> np.ndarray:
+    """Incidence offsets from the Bragg angle, evenly spaced over
+    [-span/2, span/2), ascending (urad)."""
+    return -0.5 * span_urad + span_urad * np.arange(n_angles) / n_angles
+
+
+def rocking_scan(nx: int = 2048, nz: int = 2000, n_angles: int = 256,
+                 span_urad: float = 100.0, dx_um: float = 0.4,
+                 dz_um: float = 0.05, fwhm_um: float = 200.0,
+                 radius_um: float | None = None, nu: float = 0.28) -> Workload:
+    """Rocking curve of a symmetric Laue slab (Sec. 3: rocking curves as
+    independent solves over the incidence angle; Sec. 4: the Laue-geometry
+    rocking curve): every row is the same photon energy (8 keV)
+    with the incident beam turned by dtheta_b from the Bragg angle, i.e. the
+    envelope of psi_+ carries the tilt k cos(theta_B) dtheta_b.  The slab is
+    as thick as the march (nz dz); the beam (``fwhm_um``, wide enough that
+    its divergence is far below the Darwin width) is centred on the Borrmann
+    fan.  Optional cylindrical bend (radius, Poisson ratio).  The
+    reflectivity of row b is its final P_- over its incident P_+.
+    """
+    angles = rocking_angles_urad(n_angles, span_urad)
+    x0 = -0.5 * nx * dx_um
+    s = math.sin(THETA_B_REF)
+    c = math.cos(THETA_B_REF)
+    thickness = nz * dz_um
+    k = 2.0 * math.pi / (HC_EV_ANGSTROM / E_REF_EV * 1e-4)
+    xb = -0.5 * thickness * s / c
+    psi0 = np.zeros((n_angles, 2, nx), dtype=np.complex128)
+    for b, a in enumerate(angles):
+        psi0[b, 0] = gaussian_envelope(nx, x0, dx_um, xb, fwhm_um, c,
+                                       tilt_per_um=k * c * a * 1e-6)
+    strain = dict(kind=STRAIN_NONE)
+    if radius_um is not None:
+        strain = dict(kind=STRAIN_BENT, params=[radius_um, nu, 0.0, 0.0])
+    return Workload(
+        "rocking_scan", nx, nz, dx_um, dz_um, x0,
+        np.full(n_angles, E_REF_EV), E_REF_EV, THETA_B_REF, CHI0, CHIH, 0,
+        crystal=dict(kind=CRYSTAL_SLAB, asym_angle_rad=math.pi / 2,
+                     thickness_um=thickness, surf_x_um=0.0, surf_z_um=0.0),
+        strain=strain, psi0=psi0, meta=dict(angles_urad=angles))
 
 
 @dataclass
