@@ -282,29 +282,21 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
-def run_gpu(args, rank, world):
+def run_gpu(args, rks):
     import torch
-    import torch.distributed as dist
     from paper_2601_06340_gb300 import binding, inputs
     import __graft_entry__
     __graft_entry__.build()
     binding.load()
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
-    torch.cuda.set_device(dev)
+    rank, world = rks.rank, rks.world
+    dev = rks.device
     stream = torch.cuda.current_stream()
     FP32, FP64 = binding.BPM_FP32_FUSED, binding.BPM_FP64_PLAIN
 
     def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
+        rks.barrier(torch.cuda.synchronize)
 
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    max_over_ranks = rks.max
 
     if args.only == "serving":
         if rank == 0:
@@ -549,18 +541,18 @@ def main():
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    if world > 1 and args.impl == "gpu":
-        import torch
-        import torch.distributed as dist
-        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        dist.init_process_group("nccl")
     if args.impl == "reference":
         run_reference(args, rank, world)
-    else:
-        run_gpu(args, rank, world)
-    if world > 1 and args.impl == "gpu":
-        import torch.distributed as dist
-        dist.destroy_process_group()
+        return
+    import torch
+    from paper_2601_06340_gb300 import replicas
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    rks = replicas.Ranks(backend="nccl", device=dev)   # replicas: no data-path collective
+    try:
+        run_gpu(args, rks)
+    finally:
+        rks.close()
 
 
 if __name__ == "__main__":
