@@ -161,6 +161,7 @@ def serving_run(n_requests: int, rate: float, warm: int = 40, n_check: int = 8):
     wait_ms = (times[:, 1] - times[:, 0]) * 1e3
     span = times[:, 2].max() - times[:, 0].min()
     cells = sum(r.workload.cell_updates for r in reqs[warm:])
+    flops = sum(r.workload.cell_updates * FLOPS_PER_CELL(r.workload.nx) for r in reqs[warm:])
     rng = np.random.default_rng(7)
     errs = []
     for i in sorted(rng.choice(np.arange(warm, len(reqs)), n_check, replace=False)):
@@ -185,6 +186,7 @@ def serving_run(n_requests: int, rate: float, warm: int = 40, n_check: int = 8):
             "mean_active": float(np.sum(times[:, 2] - times[:, 1]) / span),
             "nx_choices": [512, 1024, 2048, 4096, 8192, 16384], "nz_range": [500, 20000],
             "throughput": cells / span, "unit": UNIT,
+            "achieved_tflops": flops / span / 1e12,
             "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
                            "p99": float(np.percentile(lat_ms, 99)),
                            "max": float(lat_ms.max())},
@@ -469,6 +471,13 @@ def run_gpu(args, rks):
     serving = None
     if not args.skip_serving and rank == 0:
         serving = serving_run(args.serving_requests, args.serving_rate)
+        # the same mix arriving far faster than it can be served: the GPU
+        # stays saturated, so the throughput is the server's capacity
+        sat = serving_run(args.capacity_requests, args.capacity_rate, warm=0, n_check=0)
+        serving["capacity"] = {"requests": sat["requests"], "rate_per_s": sat["rate_per_s"],
+                               "throughput": sat["throughput"], "unit": UNIT,
+                               "achieved_tflops": sat["achieved_tflops"],
+                               "mean_active": sat["mean_active"]}
 
     # ---- roofline of the dominant kernel (fused march) ---------------------
     props = torch.cuda.get_device_properties(dev)
@@ -488,6 +497,12 @@ def run_gpu(args, rks):
         ach_b = batched["value"] / world * FLOPS_PER_CELL(4096) / 1e12
         batched["roofline"] = {"bound": "alu", "achieved": ach_b, "peak": peak_tflops,
                                "unit": "TFLOP/s", "frac": ach_b / peak_tflops}
+    if serving is not None:
+        for part in (serving, serving.get("capacity")):
+            if part is not None:
+                part["roofline"] = {"bound": "alu", "achieved": part["achieved_tflops"],
+                                    "peak": peak_tflops, "unit": "TFLOP/s",
+                                    "frac": part["achieved_tflops"] / peak_tflops}
     if rocking is not None:
         ach_r = rocking["value"] / world * FLOPS_PER_CELL(2048) / 1e12
         rocking["roofline"] = {"bound": "alu", "achieved": ach_r, "peak": peak_tflops,
@@ -535,6 +550,8 @@ def main():
     ap.add_argument("--skip-rocking", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=440)
     ap.add_argument("--serving-rate", type=float, default=200.0)
+    ap.add_argument("--capacity-requests", type=int, default=600)
+    ap.add_argument("--capacity-rate", type=float, default=3000.0)
     ap.add_argument("--only", default="all", choices=["all", "fused", "batched", "rocking", "serving"],
                     help="time only the fused single-solve march, the 256-energy batch, "
                          "the 256-angle rocking scan or the serving run (profiling runs)")
