@@ -9,7 +9,7 @@
 //     original field, its table twiddles and its slice of the propagator
 //     table (loaded once per launch);
 //   * each CTA sends its psi_p straight into the peer CTA's shared memory
-//     with asynchronous remote stores that complete on the peer's mbarrier
+//     with asynchronous 16-byte remote stores that complete on the peer's mbarrier
 //     (armed with the expected byte count), and reads the partner band from
 //     its own buffer once its barrier completes -- no cluster-wide barrier
 //     per step.  The buffer alternates between two halves by step parity;
@@ -51,12 +51,40 @@ __device__ __forceinline__ uint32_t mapa_u32(uint32_t addr, uint32_t rank) {
   return r;
 }
 
-__device__ __forceinline__ void st_async_v2(uint32_t raddr, float2 v, uint32_t rbar) {
+// Two values per asynchronous remote store.  Exchange buffers keep a
+// thread's values in pairs: pair p = (v[2p], v[2p+1]) of thread t sits at
+// float2 index p * 2T + 2t (xpair), so one 16-byte st.async carries two values,
+// the receiver reads them with one 16-byte load, and consecutive lanes touch
+// consecutive 16-byte words (no bank conflicts).
+__device__ __forceinline__ void st_async_v4(uint32_t raddr, float2 a, float2 b, uint32_t rbar) {
   asm volatile(
-      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(
-          raddr),
-      "f"(v.x), "f"(v.y), "r"(rbar)
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, "
+      "[%5];" ::"r"(raddr),
+      "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "r"(rbar)
       : "memory");
+}
+
+__host__ __device__ constexpr int xpair(int p, int t, int T) { return p * 2 * T + 2 * t; }
+
+// Coupling of one cell (Eq. fov10 with Eqs. fov11, fov12 and the strain
+// phase): p = this band's psi_p, q = the other band's, e = exp(i h u) of the
+// cell, (0, 0) outside the crystal; band 1 uses the conjugate phase.
+// Returns p + (a - 1) p + b e^{+-i h u} q inside, p outside.
+__device__ __forceinline__ float2 couple_cell(float2 p, float2 q, float2 e, int band,
+                                              float2 am1, float2 bb) {
+  const bool inside = (e.x != 0.f) | (e.y != 0.f);
+  if (band) e.y = -e.y;
+  const float ax = inside ? am1.x : 0.f, ay = inside ? am1.y : 0.f;
+  const float cx = fmaf(bb.x, e.x, -(bb.y * e.y)), cy = fmaf(bb.x, e.y, bb.y * e.x);
+  float rx = fmaf(ax, p.x, p.x);
+  rx = fmaf(-ay, p.y, rx);
+  rx = fmaf(cx, q.x, rx);
+  rx = fmaf(-cy, q.y, rx);
+  float ry = fmaf(ax, p.y, p.y);
+  ry = fmaf(ay, p.x, ry);
+  ry = fmaf(cx, q.y, ry);
+  ry = fmaf(cy, q.x, ry);
+  return make_float2(rx, ry);
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
@@ -210,10 +238,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
     const uint32_t xo = xpeer + uint32_t(half * N) * 8u;
     const uint32_t xbo = xbar_peer + uint32_t(half) * 8u;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      v[j] = make_float2(org[j].x + v[j].x, org[j].y + v[j].y);
-      st_async_v2(xo + uint32_t(t + j * T) * 8u, v[j], xbo);
-    }
+    for (int j = 0; j < 16; ++j) v[j] = make_float2(org[j].x + v[j].x, org[j].y + v[j].y);
+#pragma unroll
+    for (int pp = 0; pp < 8; ++pp)
+      st_async_v4(xo + uint32_t(xpair(pp, t, T)) * 8u, v[2 * pp], v[2 * pp + 1], xbo);
     // (after one expired wait a thread stops waiting, so a fault costs one
     // bounded wait, not one per step; the host reports BPM_ERR_TIMEOUT)
     if (!timed_out && !mbar_wait_cluster(&xbar[half], uint32_t((it >> 1) & 1))) timed_out = true;
@@ -221,23 +249,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
     if (!timed_out && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
     const float2* xi = xb + half * N;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const float2 q = xi[t + j * T];
-      float2 e = ph[t + j * T];
-      const bool inside = (e.x != 0.f) | (e.y != 0.f);
-      if (band) e.y = -e.y;
-      const float ax = inside ? am1.x : 0.f, ay = inside ? am1.y : 0.f;
-      const float cx = fmaf(bb.x, e.x, -(bb.y * e.y)), cy = fmaf(bb.x, e.y, bb.y * e.x);
-      const float2 p = v[j];
-      float rx = fmaf(ax, p.x, p.x);
-      rx = fmaf(-ay, p.y, rx);
-      rx = fmaf(cx, q.x, rx);
-      rx = fmaf(-cy, q.y, rx);
-      float ry = fmaf(ax, p.y, p.y);
-      ry = fmaf(ay, p.x, ry);
-      ry = fmaf(cx, q.y, ry);
-      ry = fmaf(cy, q.x, ry);
-      v[j] = make_float2(rx, ry);
+    for (int pp = 0; pp < 8; ++pp) {
+      const float4 q2 = *reinterpret_cast<const float4*>(xi + xpair(pp, t, T));
+      v[2 * pp] = couple_cell(v[2 * pp], make_float2(q2.x, q2.y), ph[t + 2 * pp * T], band, am1, bb);
+      v[2 * pp + 1] =
+          couple_cell(v[2 * pp + 1], make_float2(q2.z, q2.w), ph[t + (2 * pp + 1) * T], band, am1, bb);
     }
 
     if (rec) {

@@ -12,11 +12,11 @@
 //   x'[P m + h]   = sum_k H_h[k] W_4096^{-m k}               (local)
 // with X' = D X, D = (P(q) - 1)/N the propagator increment of the
 // real-space increment form of Eq. fov10 (see fused2_kernel.cuh).  Every CTA
-// uses the same thread -> k map, so a spectral exchange is "thread t of
-// every CTA of the band swaps the values of its 16 frequencies", indexed by
-// (value j, thread t) in the exchange buffers so that consecutive lanes hit
-// consecutive words.  The band coupling swaps psi_p with the CTA of the
-// other band that holds the same samples.
+// uses the same thread -> k map, so a spectral exchange is "thread t of every
+// CTA of the band swaps the values of its 16 frequencies", indexed by thread
+// and value pair in the exchange buffers (see fused3_kernel.cuh) so that
+// consecutive lanes hit consecutive 16-byte words.  The band coupling swaps
+// psi_p with the CTA of the other band that holds the same samples.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -190,10 +190,10 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg::T, 1)
       const uint32_t go = g_peer + uint32_t(half * M) * 8u;
       const uint32_t gbo = gbar_peer + uint32_t(half) * 8u;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        v[j] = cmul_f(v[j], cw[j].x, cw[j].y);   // G_h[k_j]
-        st_async_v2(go + uint32_t(j * T + t) * 8u, v[j], gbo);
-      }
+      for (int j = 0; j < 16; ++j) v[j] = cmul_f(v[j], cw[j].x, cw[j].y);   // G_h[k_j]
+#pragma unroll
+      for (int pp = 0; pp < 8; ++pp)
+        st_async_v4(go + uint32_t(xpair(pp, t, T)) * 8u, v[2 * pp], v[2 * pp + 1], gbo);
     }
     // (no barrier before the inverse pass rewrites buf: each thread's
     // last-pass positions are its own in both directions)
@@ -204,7 +204,9 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg::T, 1)
       const float2* gi = gx + half * M;
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        const float2 gp = gi[j * T + t], e1 = e1s[j * T + t], a = e0[j], g = v[j];
+        const float4 g2 = *reinterpret_cast<const float4*>(gi + xpair(j >> 1, t, T));
+        const float2 gp = (j & 1) ? make_float2(g2.z, g2.w) : make_float2(g2.x, g2.y);
+        const float2 e1 = e1s[j * T + t], a = e0[j], g = v[j];
         float sx = fmaf(a.x, g.x, -(a.y * g.y));
         float sy = fmaf(a.x, g.y, a.y * g.x);
         sx = fmaf(e1.x, gp.x, sx);
@@ -230,32 +232,20 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg::T, 1)
       const uint32_t co = c_part + uint32_t(half * M) * 8u;
       const uint32_t cbo = cbar_part + uint32_t(half) * 8u;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        v[j] = make_float2(org[j].x + v[j].x, org[j].y + v[j].y);
-        st_async_v2(co + uint32_t(t + j * T) * 8u, v[j], cbo);
-      }
+      for (int j = 0; j < 16; ++j) v[j] = make_float2(org[j].x + v[j].x, org[j].y + v[j].y);
+#pragma unroll
+      for (int pp = 0; pp < 8; ++pp)
+        st_async_v4(co + uint32_t(xpair(pp, t, T)) * 8u, v[2 * pp], v[2 * pp + 1], cbo);
     }
     if (!timed_out && !mbar_wait_cluster(&cbar[half], uint32_t((it >> 1) & 1))) timed_out = true;
     if (!timed_out && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
     const float2* ci = cb + half * M;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const float2 q = ci[t + j * T];
-      float2 e = ph[t + j * T];
-      const bool inside = (e.x != 0.f) | (e.y != 0.f);
-      if (band) e.y = -e.y;
-      const float ax = inside ? am1.x : 0.f, ay = inside ? am1.y : 0.f;
-      const float cx = fmaf(bb.x, e.x, -(bb.y * e.y)), cy = fmaf(bb.x, e.y, bb.y * e.x);
-      const float2 p = v[j];
-      float rx = fmaf(ax, p.x, p.x);
-      rx = fmaf(-ay, p.y, rx);
-      rx = fmaf(cx, q.x, rx);
-      rx = fmaf(-cy, q.y, rx);
-      float ry = fmaf(ax, p.y, p.y);
-      ry = fmaf(ay, p.x, ry);
-      ry = fmaf(cx, q.y, ry);
-      ry = fmaf(cy, q.x, ry);
-      v[j] = make_float2(rx, ry);
+    for (int pp = 0; pp < 8; ++pp) {
+      const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
+      v[2 * pp] = couple_cell(v[2 * pp], make_float2(q2.x, q2.y), ph[t + 2 * pp * T], band, am1, bb);
+      v[2 * pp + 1] =
+          couple_cell(v[2 * pp + 1], make_float2(q2.z, q2.w), ph[t + (2 * pp + 1) * T], band, am1, bb);
     }
 
     if (rec) {

@@ -104,6 +104,9 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
       : "memory");
 }
 
+// Issue a load of 16 columns; the registers are valid only after
+// tmem_wait16 on the same array (the wait names them as operands, so the
+// compiler cannot move their uses above it).
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
@@ -113,7 +116,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
         "=f"(v[14]), "=f"(v[15])
       : "r"(taddr)
       : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_wait16(float* v) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]),
+                 "+f"(v[6]), "+f"(v[7]), "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]),
+                 "+f"(v[12]), "+f"(v[13]), "+f"(v[14]), "+f"(v[15])
+               :
+               : "memory");
 }
 
 template <bool EX>
@@ -262,36 +273,51 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
     // the peers have read our previous G before we overwrite their slots
     if (it > 0 && !timed_out && !mbar_wait_cluster(gfree, uint32_t((it - 1) & 1))) timed_out = true;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      v[j] = cmul_f(v[j], cw[j].x, cw[j].y);     // G_h[k_j]
+    for (int j = 0; j < 16; ++j) v[j] = cmul_f(v[j], cw[j].x, cw[j].y);   // G_h[k_j]
 #pragma unroll
-      for (int e = 0; e < 3; ++e) st_async_v2(g_to[e] + uint32_t(j * T + t) * 8u, v[j], gbar_to[e]);
-    }
+    for (int pp = 0; pp < 8; ++pp)
+#pragma unroll
+      for (int e = 0; e < 3; ++e)
+        st_async_v4(g_to[e] + uint32_t(xpair(pp, t, T)) * 8u, v[2 * pp], v[2 * pp + 1],
+                    gbar_to[e]);
     if (lead && part_due && h > 0) st_async_f64(pp_to, my_part, gbar_to[3 - h]);
     if (!timed_out && !mbar_wait_cluster(gbar, uint32_t(it & 1))) timed_out = true;
     if (lead && part_due && h == 0)
       d.powers[2 * (n / d.record_every - 1) + band] =
           (((my_part + ppeer[0]) + ppeer[1]) + ppeer[2]) * d.dx_um;
+    {
+      // chunk q (frequencies 2q, 2q+1) of E from tensor memory, the next
+      // chunk's load in flight while this one is used
+      float ev[2][16];
+      tmem_ld16(tbase, ev[0]);
+      tmem_wait16(ev[0]);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      float ev[16];
-      tmem_ld16(tbase + uint32_t(16 * q), ev);
+      for (int q = 0; q < 8; ++q) {
+        if (q < 7) tmem_ld16(tbase + uint32_t(16 * (q + 1)), ev[(q + 1) & 1]);
+        const float* e = ev[q & 1];
+        float4 g2[3];
 #pragma unroll
-      for (int jj = 0; jj < 2; ++jj) {
-        const int j = 2 * q + jj;
-        const float2 g0 = v[j];
-        float sx = fmaf(ev[jj * 8], g0.x, -(ev[jj * 8 + 1] * g0.y));
-        float sy = fmaf(ev[jj * 8], g0.y, ev[jj * 8 + 1] * g0.x);
+        for (int dl = 1; dl < 4; ++dl)
+          g2[dl - 1] = *reinterpret_cast<const float4*>(gx + (dl - 1) * M + xpair(q, t, T));
 #pragma unroll
-        for (int dl = 1; dl < 4; ++dl) {
-          const float2 g = gx[(dl - 1) * M + j * T + t];
-          const float ex = ev[jj * 8 + 2 * dl], ey = ev[jj * 8 + 2 * dl + 1];
-          sx = fmaf(ex, g.x, sx);
-          sx = fmaf(-ey, g.y, sx);
-          sy = fmaf(ex, g.y, sy);
-          sy = fmaf(ey, g.x, sy);
+        for (int jj = 0; jj < 2; ++jj) {
+          const int j = 2 * q + jj;
+          const float2 g0 = v[j];
+          float sx = fmaf(e[jj * 8], g0.x, -(e[jj * 8 + 1] * g0.y));
+          float sy = fmaf(e[jj * 8], g0.y, e[jj * 8 + 1] * g0.x);
+#pragma unroll
+          for (int dl = 1; dl < 4; ++dl) {
+            const float4 gg = g2[dl - 1];
+            const float2 g = jj ? make_float2(gg.z, gg.w) : make_float2(gg.x, gg.y);
+            const float ex = e[jj * 8 + 2 * dl], ey = e[jj * 8 + 2 * dl + 1];
+            sx = fmaf(ex, g.x, sx);
+            sx = fmaf(-ey, g.y, sx);
+            sy = fmaf(ex, g.y, sy);
+            sy = fmaf(ey, g.x, sy);
+          }
+          v[j] = cmul_f(make_float2(sx, sy), cw[j].x, -cw[j].y);
         }
-        v[j] = cmul_f(make_float2(sx, sy), cw[j].x, -cw[j].y);
+        if (q < 7) tmem_wait16(ev[(q + 1) & 1]);
       }
     }
     __syncthreads();                             // all of our G slots read
@@ -314,32 +340,20 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
       const uint32_t co = c_part + uint32_t(half * M) * 8u;
       const uint32_t cbo = cbar_part + uint32_t(half) * 8u;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        v[j] = make_float2(org[j].x + v[j].x, org[j].y + v[j].y);
-        st_async_v2(co + uint32_t(t + j * T) * 8u, v[j], cbo);
-      }
+      for (int j = 0; j < 16; ++j) v[j] = make_float2(org[j].x + v[j].x, org[j].y + v[j].y);
+#pragma unroll
+      for (int pp = 0; pp < 8; ++pp)
+        st_async_v4(co + uint32_t(xpair(pp, t, T)) * 8u, v[2 * pp], v[2 * pp + 1], cbo);
     }
     if (!timed_out && !mbar_wait_cluster(&cbar[half], uint32_t((it >> 1) & 1))) timed_out = true;
     if (!timed_out && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
     const float2* ci = cb + half * M;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const float2 q = ci[t + j * T];
-      float2 e = ph[t + j * T];
-      const bool inside = (e.x != 0.f) | (e.y != 0.f);
-      if (band) e.y = -e.y;
-      const float ax = inside ? am1.x : 0.f, ay = inside ? am1.y : 0.f;
-      const float cx = fmaf(bb.x, e.x, -(bb.y * e.y)), cy = fmaf(bb.x, e.y, bb.y * e.x);
-      const float2 p = v[j];
-      float rx = fmaf(ax, p.x, p.x);
-      rx = fmaf(-ay, p.y, rx);
-      rx = fmaf(cx, q.x, rx);
-      rx = fmaf(-cy, q.y, rx);
-      float ry = fmaf(ax, p.y, p.y);
-      ry = fmaf(ay, p.x, ry);
-      ry = fmaf(cx, q.y, ry);
-      ry = fmaf(cy, q.x, ry);
-      v[j] = make_float2(rx, ry);
+    for (int pp = 0; pp < 8; ++pp) {
+      const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
+      v[2 * pp] = couple_cell(v[2 * pp], make_float2(q2.x, q2.y), ph[t + 2 * pp * T], band, am1, bb);
+      v[2 * pp + 1] =
+          couple_cell(v[2 * pp + 1], make_float2(q2.z, q2.w), ph[t + (2 * pp + 1) * T], band, am1, bb);
     }
 
     if (rec) {
