@@ -254,6 +254,45 @@ def rocking_run(dev, stream, barrier, max_over_ranks, world, rank, check, steps=
     return out
 
 
+def volume_run(dev, stream, barrier, max_over_ranks, world, rank, check, steps=3):
+    """The 3D stand-in workload (both transverse coordinates): one solve of
+    512 x 256 x 300 cells.  The paper's only timing (its 3D example, 300 x 200
+    x 300 cells, ~13 s on a Perlmutter node) is quoted as context."""
+    import torch
+    from paper_2601_06340_gb300 import binding, inputs
+    FP32 = binding.BPM_FP32_FUSED
+    wv = inputs.cube_dislocation_3d()
+    plan = binding.Plan(wv, FP32)
+    x = torch.from_numpy(wv.psi0.astype(np.complex64)).to(dev)
+    y = torch.empty_like(x)
+
+    def march():
+        binding.bpm_propagate_device(plan.handle, x, y, None, None, 0, wv.nz, stream.cuda_stream)
+    march()
+    barrier()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        march()
+    b.record(stream)
+    barrier()
+    ms = max_over_ranks(a.elapsed_time(b)) / steps
+    out = {"workload": "cube_dislocation_3d: Si(440)-like at 17.45 keV, 10 um box crystal, "
+                       "edge dislocation along y, Nx=512, Ny=256, Nz=300, dx=dy=dz=0.05 um",
+           "value": world * wv.cell_updates / (ms * 1e-3), "unit": UNIT, "ms_per_march": ms,
+           "launches_per_march": 2 * wv.nz + 2,
+           "paper_context": {"seconds": 13.0, "grid": "300 x 200 x 300",
+                             "hardware": "one Perlmutter node (CPU vs GPU not stated)"}}
+    if check:
+        from oracle import run as orun
+        t0 = time.perf_counter()
+        ref = orun.run_workload3d(wv, record_every=0)
+        out["oracle_seconds_1core"] = time.perf_counter() - t0
+        out["rel_l2_err"] = rel_l2_bands(y.cpu().numpy().astype(np.complex128), ref.psi)
+    plan.close()
+    return out
+
+
 def run_reference(args, rank, world):
     """FP64 oracle on the host cores: each step is a bounded sample (the
     first `sample_steps` z-steps of the march)."""
@@ -305,6 +344,13 @@ def run_gpu(args, rks):
             print(json.dumps({"only": "serving",
                               **serving_run(args.serving_requests, args.serving_rate)}),
                   flush=True)
+        return
+
+    if args.only == "volume":
+        r = volume_run(dev, stream, barrier, max_over_ranks, world, rank, check=False,
+                       steps=args.steps)
+        if rank == 0:
+            print(json.dumps({"only": "volume", **r}), flush=True)
         return
 
     if args.only == "rocking":
@@ -467,6 +513,12 @@ def run_gpu(args, rks):
         rocking = rocking_run(dev, stream, barrier, max_over_ranks, world, rank,
                               check=rank == 0 and not args.skip_oracle)
 
+    # ---- 3D: both transverse coordinates -----------------------------------
+    volume = None
+    if not args.skip_volume:
+        volume = volume_run(dev, stream, barrier, max_over_ranks, world, rank,
+                            check=rank == 0 and not args.skip_oracle)
+
     # ---- serving: Poisson stream of mixed solves through submit/poll ------
     serving = None
     if not args.skip_serving and rank == 0:
@@ -503,6 +555,11 @@ def run_gpu(args, rks):
                 part["roofline"] = {"bound": "alu", "achieved": part["achieved_tflops"],
                                     "peak": peak_tflops, "unit": "TFLOP/s",
                                     "frac": part["achieved_tflops"] / peak_tflops}
+    if volume is not None:
+        # two 2D FFTs per band and step: 4 x 5 log2(Nx Ny) flops per cell-update
+        ach_v = volume["value"] / world * FLOPS_PER_CELL(512 * 256) / 1e12
+        volume["roofline"] = {"bound": "alu", "achieved": ach_v, "peak": peak_tflops,
+                              "unit": "TFLOP/s", "frac": ach_v / peak_tflops}
     if rocking is not None:
         ach_r = rocking["value"] / world * FLOPS_PER_CELL(2048) / 1e12
         rocking["roofline"] = {"bound": "alu", "achieved": ach_r, "peak": peak_tflops,
@@ -526,6 +583,7 @@ def run_gpu(args, rks):
                            "fused_speedup": value / value64},
             "batched": batched,
             "rocking": rocking,
+            "volume": volume,
             "serving": serving,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -548,13 +606,15 @@ def main():
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--skip-rocking", action="store_true")
+    ap.add_argument("--skip-volume", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=440)
     ap.add_argument("--serving-rate", type=float, default=200.0)
     ap.add_argument("--capacity-requests", type=int, default=600)
     ap.add_argument("--capacity-rate", type=float, default=3000.0)
-    ap.add_argument("--only", default="all", choices=["all", "fused", "batched", "rocking", "serving"],
+    ap.add_argument("--only", default="all", choices=["all", "fused", "batched", "rocking", "volume", "serving"],
                     help="time only the fused single-solve march, the 256-energy batch, "
-                         "the 256-angle rocking scan or the serving run (profiling runs)")
+                         "the 256-angle rocking scan, the 3D solve or the serving run "
+                         "(profiling runs)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -70,7 +70,8 @@ enum bpm_crystal_kind {
   BPM_CRYSTAL_SLAB = 2,            /* slab of thickness T, see set_crystal  */
   BPM_CRYSTAL_MASK = 3,            /* user map [nz][nx], nonzero = inside   */
   BPM_CRYSTAL_SLAB_AND_MASK = 4,   /* slab AND user map                     */
-  BPM_CRYSTAL_SLAB_AND_POLYGON = 5 /* slab AND polygon (even-odd rule)      */
+  BPM_CRYSTAL_SLAB_AND_POLYGON = 5, /* slab AND polygon (even-odd rule)     */
+  BPM_CRYSTAL_BOX = 6              /* 3D plans: box, see set_crystal_box    */
 };
 
 /* Displacement u_x(x, z) entering as exp(+-i h u_x) (Eq. Authier). */
@@ -135,6 +136,26 @@ int bpm_set_crystal(bpm_plan_t plan, int32_t kind, double asym_angle_rad,
  * device; the march streams that phasor (c64 or c128 per cell). */
 int bpm_set_strain(bpm_plan_t plan, int32_t kind, const double* ux_um,
                    const double* params, int32_t n_params);
+
+/* 3D plans: the march of Eq. fov4 with both transverse coordinates (x, y)
+ * and the two-beam envelopes of Eqs. fov6-fov10 (the Bragg shift k_d/2 is
+ * along x only): each band goes through exp(i dz^ sqrt(1 - (qx +- s)^2 -
+ * qy^2)), qy = 2 pi fftfreq(ny, dy^), and the coupling is pointwise in (x, y)
+ * (Sec. 2; the paper's 3D cases, Sec. 6).  `problem` as for bpm_plan with
+ * precision BPM_FP32_FUSED and nx a power of two in [256, 4096]; ny a power
+ * of two in [256, 1024], dy_um > 0, y0_um the y of the first cell.  Every
+ * field of the other calls then carries [ny][nx] per band: psi [B][2][ny][nx],
+ * records [B][n_rec][2][ny][nx], mask and u_x arrays [nz][ny][nx]; band
+ * powers are dx dy sum |psi|^2.  The 2D crystal kinds and strain fields apply
+ * at every y.  bpm_submit does not take 3D plans (BPM_ERR_INVALID). */
+int bpm_plan3d(const bpm_problem* problem, int32_t ny, double dy_um, double y0_um,
+               bpm_plan_t* out);
+
+/* 3D plans: a box crystal, inside = {x0 <= x <= x1, y0 <= y <= y1,
+ * z0 <= z <= z1} at the cell centres (x_j, y_i, z_n), box_um = {x0, x1, y0,
+ * y1, z0, z1} (FP64 comparisons).  BPM_ERR_INVALID for a 2D plan or
+ * non-finite bounds. */
+int bpm_set_crystal_box(bpm_plan_t plan, const double* box_um);
 
 /* March rows [0, B) from the state after n_begin steps to the state after
  * n_end steps (0 <= n_begin < n_end <= nz) and copy results to the host.

@@ -20,9 +20,11 @@ Modules
               line), and the strain phase h*u_x of Eq. (Authier).
 ``timeaxis``  the energy -> time transform of a batch of exit fields
               (Section "Time-Dependent Simulation of Reflection").
+``bpm3d``     the same march with both transverse coordinates (x, y):
+              2D angular-spectrum propagators, box crystals, 3D arrays.
 
 Every function is pinned by a ``-m "not gpu"`` test in
-``tests/test_oracle_pins.py`` against closed forms, invariants, brute force
+``tests/test_oracle_pins.py`` (3D: ``tests/test_oracle3d_pins.py``) against closed forms, invariants, brute force
 or a library routine.  The one function without such a pin is
 ``timeaxis.omega_to_t`` beyond its DFT definition: its physical time axis
 reading is stated in its docstring.

@@ -47,3 +47,29 @@ def run_workload(wl, n_begin=0, n_end=None, rows=None, psi_in=None,
 def mask_of(wl) -> np.ndarray:
     cr = crystal_for(wl)
     return np.stack([cr.inside(n) for n in range(wl.nz)])
+
+
+def run_workload3d(wl, n_begin=0, n_end=None, psi_in=None, record_every=None):
+    """March a 3D workload (fields [B][2][Ny][Nx]) from n_begin to n_end."""
+    from . import bpm3d
+    n_end = wl.nz if n_end is None else n_end
+    plans = [bpm3d.energy_plan3d(float(e), wl.e_ref_ev, wl.theta_b_ref_rad, complex(wl.chi0),
+                                 complex(wl.chih), wl.nx, wl.ny, wl.dx_um, wl.dy_um, wl.dz_um)
+             for e in wl.energies_ev]
+    cr = bpm3d.Crystal3D(wl.nx, wl.ny, wl.x0_um, wl.y0_um, wl.dx_um, wl.dy_um, wl.dz_um,
+                         bpm.d_spacing_um(wl.e_ref_ev, wl.theta_b_ref_rad))
+    c = dict(wl.crystal)
+    kind = c.pop("kind")
+    if kind == bpm3d.CRYSTAL_BOX:
+        cr.set_crystal(kind, box=c["box_um"])
+    elif kind == geometry.CRYSTAL_MASK:
+        cr.set_crystal(kind, mask3=c["mask"])
+    else:
+        cr.set_crystal(kind, asym_angle_rad=c.get("asym_angle_rad", 0.0),
+                       thickness_um=c.get("thickness_um", 0.0), surf_x_um=c.get("surf_x_um", 0.0),
+                       surf_z_um=c.get("surf_z_um", 0.0), polygon=c.get("polygon"))
+    s = dict(wl.strain)
+    cr.set_strain(s.pop("kind"), ux3=s.get("ux"), params=s.get("params"))
+    psi = wl.psi0 if psi_in is None else psi_in
+    rec = wl.record_every if record_every is None else record_every
+    return bpm3d.march3d(plans, psi, cr, n_begin, n_end, rec, wl.dx_um, wl.dy_um)

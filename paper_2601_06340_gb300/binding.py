@@ -22,6 +22,7 @@ BPM_OK, BPM_NOT_READY = 0, 1
 BPM_ERR_INVALID, BPM_ERR_OOM, BPM_ERR_CUDA = -1, -2, -3
 BPM_ERR_BUSY, BPM_ERR_TIMEOUT, BPM_ERR_NUMERIC = -4, -5, -6
 BPM_FP64_PLAIN, BPM_FP32_FUSED = 0, 1
+BPM_CRYSTAL_BOX = 6
 
 _STATUS_NAMES = {0: "OK", 1: "NOT_READY", -1: "ERR_INVALID", -2: "ERR_OOM",
                  -3: "ERR_CUDA", -4: "ERR_BUSY", -5: "ERR_TIMEOUT", -6: "ERR_NUMERIC"}
@@ -52,6 +53,8 @@ _I = ctypes.c_int32
 _D = ctypes.c_double
 _SIGS = {
     "bpm_plan": ([ctypes.POINTER(bpm_problem), ctypes.POINTER(_P)], ctypes.c_int),
+    "bpm_plan3d": ([ctypes.POINTER(bpm_problem), _I, _D, _D, ctypes.POINTER(_P)], ctypes.c_int),
+    "bpm_set_crystal_box": ([_P, _P], ctypes.c_int),
     "bpm_set_crystal": ([_P, _I, _D, _D, _D, _D, _P, _P, _I], ctypes.c_int),
     "bpm_set_strain": ([_P, _I, _P, _P, _I], ctypes.c_int),
     "bpm_propagate": ([_P, _P, _P, _P, _P, _I, _I], ctypes.c_int),
@@ -110,6 +113,19 @@ def bpm_plan(problem: bpm_problem) -> int:
     h = ctypes.c_void_p()
     _check(load().bpm_plan(ctypes.byref(problem), ctypes.byref(h)))
     return h.value
+
+
+def bpm_plan3d(problem: bpm_problem, ny: int, dy_um: float, y0_um: float) -> int:
+    h = ctypes.c_void_p()
+    _check(load().bpm_plan3d(ctypes.byref(problem), int(ny), float(dy_um), float(y0_um),
+                             ctypes.byref(h)))
+    return h.value
+
+
+def bpm_set_crystal_box(plan, box_um):
+    b = np.ascontiguousarray(box_um, dtype=np.float64)
+    assert b.size == 6
+    return _check(load().bpm_set_crystal_box(plan, _ptr(b)))
 
 
 def bpm_set_crystal(plan, kind, asym_angle_rad=0.0, thickness_um=0.0, surf_x_um=0.0,
@@ -216,12 +232,19 @@ class Plan:
             e_ref_ev=wl.e_ref_ev, theta_b_ref_rad=wl.theta_b_ref_rad,
             chi0_re=wl.chi0.real, chi0_im=wl.chi0.imag, chih_re=wl.chih.real,
             chih_im=wl.chih.imag, record_every=self.record_every, precision=precision)
-        self.handle = bpm_plan(prob)
+        self.ny = int(getattr(wl, "ny", 1))
+        if self.ny > 1:
+            self.handle = bpm_plan3d(prob, self.ny, wl.dy_um, wl.y0_um)
+        else:
+            self.handle = bpm_plan(prob)
         c = dict(wl.crystal)
         kind = c.pop("kind")
-        bpm_set_crystal(self.handle, kind, c.get("asym_angle_rad", 0.0),
-                        c.get("thickness_um", 0.0), c.get("surf_x_um", 0.0),
-                        c.get("surf_z_um", 0.0), c.get("mask"), c.get("polygon"))
+        if kind == BPM_CRYSTAL_BOX:
+            bpm_set_crystal_box(self.handle, c["box_um"])
+        else:
+            bpm_set_crystal(self.handle, kind, c.get("asym_angle_rad", 0.0),
+                            c.get("thickness_um", 0.0), c.get("surf_x_um", 0.0),
+                            c.get("surf_z_um", 0.0), c.get("mask"), c.get("polygon"))
         st = dict(wl.strain)
         bpm_set_strain(self.handle, st.pop("kind"), st.get("ux"), st.get("params"))
         self.n_rec = (wl.nz // self.record_every) if self.record_every > 0 else 0
@@ -238,15 +261,16 @@ class Plan:
         n_end = wl.nz if n_end is None else n_end
         if out is None:
             out = MarchOutput(np.empty_like(psi_in),
-                              np.zeros((wl.batch, self.n_rec, 2, wl.nx), self.rec_dtype),
+                              np.zeros((wl.batch, self.n_rec) + psi_in.shape[1:], self.rec_dtype),
                               np.zeros((wl.batch, self.n_rec + 1, 2)))
         bpm_propagate(self.handle, psi_in, out.psi, out.records if records else None,
                       out.powers if powers else None, n_begin, n_end)
         return out
 
     def slices(self):
-        mask = np.zeros((self.wl.nz, self.wl.nx), np.uint8)
-        ph = np.zeros((self.wl.nz, self.wl.nx), np.complex128)
+        shape = (self.wl.nz, self.ny, self.wl.nx) if self.ny > 1 else (self.wl.nz, self.wl.nx)
+        mask = np.zeros(shape, np.uint8)
+        ph = np.zeros(shape, np.complex128)
         bpm_fetch_slices(self.handle, mask, ph)
         return mask, ph
 

@@ -66,6 +66,9 @@ struct bpm_plan_s {
   // problem
   int32_t nx = 0, nz = 0, logn = 0, nb = 0, record_every = 0, precision = 0;
   double dx_um = 0, dz_um = 0, x0_um = 0, e_ref_ev = 0, theta_b_ref = 0;
+  // second transverse coordinate (3D plans: ny > 1; fields are [ny][nx])
+  int32_t ny = 1, logny = 0;
+  double dy_um = 0, y0_um = 0;
   std::complex<double> chi0, chih;
   std::vector<double> energies;
   std::vector<bpm::EnergyConsts> ec;
@@ -74,6 +77,7 @@ struct bpm_plan_s {
   // crystal and strain descriptions (host copies)
   int32_t crystal_kind = BPM_CRYSTAL_VACUUM;
   double asym = 0, thick = 0, surf_x = 0, surf_z = 0;
+  double box[6] = {0, 0, 0, 0, 0, 0};   // BPM_CRYSTAL_BOX: x0, x1, y0, y1, z0, z1
   std::vector<uint8_t> mask;
   std::vector<double> poly;
   int32_t strain_kind = BPM_STRAIN_NONE;
@@ -90,11 +94,18 @@ struct bpm_plan_s {
   void* d_rows = nullptr;         // RowDescF32[B] or RowDescF64[B]
   void* d_io = nullptr;           // [B][2][nx] c128 host-transfer staging
   int* d_status = nullptr;        // device status word
+  void* d_spec = nullptr;         // 3D: [B][2][ny][nx] c64 x-spectra
+  void* d_twy = nullptr;          // 3D: float4 [ny] twiddles along y
+  double* d_pwpart = nullptr;     // 3D: [B][n_rec][2][ny] line power sums
+  size_t pwpart_bytes = 0;
   size_t device_bytes = 0;
   int pending = 0;                // tickets not yet finished
 };
 
 namespace bpm {
+
+// Points of one band's transverse field (nx, or nx * ny for 3D plans).
+inline size_t plane_of(const bpm_plan_s* p) { return size_t(p->nx) * size_t(p->ny); }
 
 // Thread-local error reporting (capi.cpp).
 int fail(int code, const std::string& msg);
@@ -104,6 +115,11 @@ int cuda_fail(cudaError_t e, const char* what);
 int validate_problem(const bpm_problem* p, std::string* why);
 void compute_energy_consts(bpm_plan_s* plan);
 void fused_prop_table(const bpm_plan_s* plan, int row, std::vector<float2>* out);
+// 3D: (P(qx, qy) - 1)/(nx ny) per band, [band][y position][x position] in the
+// output orders of the radix-16 FFTs along y and x.
+void vol_prop_table(const bpm_plan_s* plan, int row, std::vector<float2>* out);
+int validate_problem3d(const bpm_problem* p, int ny, double dy_um, double y0_um,
+                       std::string* why);
 void plain_prop_table(const bpm_plan_s* plan, int row, std::vector<double2>* out);
 void twiddle_table_f32(int n, std::vector<float4>* out);
 void twiddle_table_f64(int n, std::vector<double2>* out);
@@ -121,6 +137,11 @@ int launch_fused_layout(int logn, const RowDescF32* d_rows, int n_rows, int step
                         const float4* d_tw, int* d_status, cudaStream_t st, int layout);
 // SMs one row occupies in its cluster layout (0 if the size has none).
 int fused_cluster_sms(int logn);
+// 3D march of all rows on `st` (state: [B][2][ny][nx] c64, the field after
+// n_begin steps, replaced by the field after n_end steps without the common
+// phase); records / powers as for the 2D fused path.
+int vol_march(bpm_plan_s* plan, float2* state, float2* d_rec, double* d_pw, int n_begin,
+              int n_end, cudaStream_t st);
 int plain_march(bpm_plan_s* plan, int n_begin, int n_end, int n_phase0, void* d_records,
                 double* d_powers, cudaStream_t st);
 int launch_convert_in(const double2* src, float2* dst, size_t n, cudaStream_t st);

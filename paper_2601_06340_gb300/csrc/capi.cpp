@@ -45,7 +45,8 @@ int dev_alloc(bpm_plan_s* plan, void** p, size_t bytes, const char* what) {
 
 void free_plan_memory(bpm_plan_s* plan) {
   void** ptrs[] = {&plan->d_phasor, &plan->d_prop, &plan->d_tw, &plan->d_state,
-                   &plan->d_state2, &plan->d_rows, &plan->d_io};
+                   &plan->d_state2, &plan->d_rows, &plan->d_io, &plan->d_spec,
+                   &plan->d_twy, reinterpret_cast<void**>(&plan->d_pwpart)};
   for (void** p : ptrs) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -187,6 +188,17 @@ static int enqueue_march(bpm_plan_s* plan, PlanAux* aux, void* state, void* d_re
   if (e != cudaSuccess) return cuda_fail(e, "upload phase factors");
   double* final_pw = d_pw ? d_pw + 2 * plan->n_rec : nullptr;
   const int pw_stride = 2 * (plan->n_rec + 1);
+  if (plan->ny > 1) {
+    int rc = vol_march(plan, static_cast<float2*>(state), static_cast<float2*>(d_rec), d_pw,
+                       n_begin, n_end, st);
+    if (rc != BPM_OK) return rc;
+    return launch_finish_f32(static_cast<const float2*>(state),
+                             out_c128 ? static_cast<double2*>(out) : nullptr,
+                             out_c128 ? nullptr : static_cast<float2*>(out),
+                             reinterpret_cast<const double*>(aux->d_g), plan->nb,
+                             int(plane_of(plan)), steps, plan->dx_um * plan->dy_um, final_pw,
+                             pw_stride, st);
+  }
   if (plan->precision == BPM_FP32_FUSED) {
     std::vector<RowDescF32> rows;
     fused_rows(plan, static_cast<float2*>(state), static_cast<float2*>(d_rec), d_pw, n_begin,
@@ -224,11 +236,11 @@ const char* bpm_last_error(void) { return g_last_error.c_str(); }
 
 const char* bpm_version(void) { return "bpm-gb300 0.1 (sm_103a)"; }
 
-int bpm_plan(const bpm_problem* p, bpm_plan_t* out) {
-  if (!out) return fail(BPM_ERR_INVALID, "out is NULL");
-  *out = nullptr;
-  std::string why;
-  if (validate_problem(p, &why) != BPM_OK) return fail(BPM_ERR_INVALID, why);
+}  // extern "C"
+
+// Plan creation shared by 2D (ny = 1) and 3D plans; `p` already validated.
+static int make_plan(const bpm_problem* p, int ny, double dy_um, double y0_um,
+                     bpm_plan_t* out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "no usable CUDA device");
@@ -239,6 +251,11 @@ int bpm_plan(const bpm_problem* p, bpm_plan_t* out) {
   plan->nz = p->nz;
   plan->logn = 0;
   while ((1 << plan->logn) < p->nx) ++plan->logn;
+  plan->ny = ny;
+  plan->logny = 0;
+  while ((1 << plan->logny) < ny) ++plan->logny;
+  plan->dy_um = dy_um;
+  plan->y0_um = y0_um;
   plan->nb = p->n_energy;
   plan->record_every = p->record_every;
   plan->precision = p->precision;
@@ -257,13 +274,18 @@ int bpm_plan(const bpm_problem* p, bpm_plan_t* out) {
   compute_energy_consts(plan.get());
 
   bpm_plan_s* pl = plan.get();
-  const size_t n = pl->nx, nb = pl->nb, cs = csize(pl);
+  const size_t n = plane_of(pl), nb = pl->nb, cs = csize(pl);
+  const bool vol = pl->ny > 1;
   int rc = BPM_OK;
   auto A = [&](void** ptr, size_t bytes, const char* what) {
     if (rc == BPM_OK) rc = dev_alloc(pl, ptr, bytes, what);
   };
   A(&pl->d_prop, nb * 2 * n * cs, "propagator tables");
-  A(&pl->d_tw, n * 16, "twiddles");
+  A(&pl->d_tw, size_t(pl->nx) * 16, "twiddles");
+  if (vol) {
+    A(&pl->d_twy, size_t(pl->ny) * 16, "twiddles along y");
+    A(&pl->d_spec, nb * 2 * n * cs, "x-spectra");
+  }
   A(&pl->d_state, nb * 2 * n * cs, "state");
   if (pl->precision == BPM_FP64_PLAIN) A(&pl->d_state2, nb * 2 * n * cs, "state scratch");
   A(&pl->d_rows, nb * std::max(sizeof(RowDescF32), sizeof(RowDescF64)), "row descriptors");
@@ -277,7 +299,36 @@ int bpm_plan(const bpm_problem* p, bpm_plan_t* out) {
   }
   if (rc == BPM_OK) {
     cudaStream_t st = aux->stream;
-    if (pl->precision == BPM_FP32_FUSED) {
+    if (vol) {
+      std::vector<float4> tw, twy;
+      twiddle_table_f32(pl->nx, &tw);
+      twiddle_table_f32(pl->ny, &twy);
+      e = cudaMemcpyAsync(pl->d_tw, tw.data(), tw.size() * 16, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(pl->d_twy, twy.data(), twy.size() * 16, cudaMemcpyHostToDevice, st);
+      // per row: (a - 1, b) as float2 pairs, then the common phases as doubles
+      std::vector<float2> coup(2 * size_t(pl->nb));
+      std::vector<double> gph(pl->nb);
+      for (int r = 0; r < pl->nb; ++r) {
+        const EnergyConsts& c = pl->ec[r];
+        coup[2 * r] = make_float2(float(c.am1.real()), float(c.am1.imag()));
+        coup[2 * r + 1] = make_float2(float(c.b.real()), float(c.b.imag()));
+        gph[r] = c.gphase;
+      }
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(pl->d_rows, coup.data(), coup.size() * sizeof(float2),
+                            cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(static_cast<float2*>(pl->d_rows) + coup.size(), gph.data(),
+                            gph.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+      for (int r = 0; r < pl->nb && e == cudaSuccess; ++r) {
+        std::vector<float2> t;
+        vol_prop_table(pl, r, &t);
+        e = cudaMemcpyAsync(static_cast<float2*>(pl->d_prop) + size_t(r) * 2 * n, t.data(),
+                            t.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // t is reused
+      }
+    } else if (pl->precision == BPM_FP32_FUSED) {
       std::vector<float4> tw;
       twiddle_table_f32(pl->nx, &tw);
       e = cudaMemcpyAsync(pl->d_tw, tw.data(), n * 16, cudaMemcpyHostToDevice, st);
@@ -322,6 +373,39 @@ int bpm_plan(const bpm_problem* p, bpm_plan_t* out) {
   return BPM_OK;
 }
 
+extern "C" {
+
+int bpm_plan(const bpm_problem* p, bpm_plan_t* out) {
+  if (!out) return fail(BPM_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  std::string why;
+  if (validate_problem(p, &why) != BPM_OK) return fail(BPM_ERR_INVALID, why);
+  return make_plan(p, 1, 0.0, 0.0, out);
+}
+
+int bpm_plan3d(const bpm_problem* p, int32_t ny, double dy_um, double y0_um, bpm_plan_t* out) {
+  if (!out) return fail(BPM_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  std::string why;
+  if (validate_problem3d(p, ny, dy_um, y0_um, &why) != BPM_OK) return fail(BPM_ERR_INVALID, why);
+  return make_plan(p, ny, dy_um, y0_um, out);
+}
+
+int bpm_set_crystal_box(bpm_plan_t plan, const double* box_um) {
+  if (!plan || !box_um) return fail(BPM_ERR_INVALID, "plan / box_um is NULL");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  if (plan->pending) return fail(BPM_ERR_BUSY, "plan has pending tickets");
+  if (plan->ny <= 1) return fail(BPM_ERR_INVALID, "box crystals need a 3D plan");
+  for (int i = 0; i < 6; ++i)
+    if (!std::isfinite(box_um[i])) return fail(BPM_ERR_INVALID, "box bounds must be finite");
+  plan->crystal_kind = BPM_CRYSTAL_BOX;
+  for (int i = 0; i < 6; ++i) plan->box[i] = box_um[i];
+  plan->mask.clear();
+  plan->poly.clear();
+  plan->slices_dirty = true;
+  return BPM_OK;
+}
+
 int bpm_set_crystal(bpm_plan_t plan, int32_t kind, double asym_angle_rad, double thickness_um,
                     double surf_x_um, double surf_z_um, const uint8_t* mask,
                     const double* poly_xz_um, int32_t nv) {
@@ -348,7 +432,7 @@ int bpm_set_crystal(bpm_plan_t plan, int32_t kind, double asym_angle_rad, double
   plan->thick = thickness_um;
   plan->surf_x = surf_x_um;
   plan->surf_z = surf_z_um;
-  if (needs_mask) plan->mask.assign(mask, mask + size_t(plan->nx) * plan->nz);
+  if (needs_mask) plan->mask.assign(mask, mask + plane_of(plan) * plan->nz);
   else plan->mask.clear();
   if (kind == BPM_CRYSTAL_SLAB_AND_POLYGON) plan->poly.assign(poly_xz_um, poly_xz_um + 2 * nv);
   else plan->poly.clear();
@@ -363,7 +447,7 @@ int bpm_set_strain(bpm_plan_t plan, int32_t kind, const double* ux_um, const dou
   if (plan->pending) return fail(BPM_ERR_BUSY, "plan has pending tickets");
   if (kind < BPM_STRAIN_NONE || kind > BPM_STRAIN_EDGE_DISLOCATION)
     return fail(BPM_ERR_INVALID, "unknown strain kind");
-  const size_t cells = size_t(plan->nx) * plan->nz;
+  const size_t cells = plane_of(plan) * plan->nz;
   if (kind == BPM_STRAIN_ARRAY) {
     if (!ux_um) return fail(BPM_ERR_INVALID, "ux_um is NULL");
     for (size_t i = 0; i < cells; ++i)
@@ -418,7 +502,7 @@ int bpm_propagate(bpm_plan_t plan, const double* psi_in, double* psi_out, void* 
   cudaStream_t st = aux->stream;
   if (plan->slices_dirty && (rc = prepare_slices(plan, st)) != BPM_OK) return rc;
 
-  const size_t n = plan->nx, nb = plan->nb, cs = csize(plan);
+  const size_t n = plane_of(plan), nb = plan->nb, cs = csize(plan);
   const int nrec = plan->n_rec;
   const bool want_rec = records && nrec > 0;
   const bool want_pw = powers != nullptr;
@@ -502,7 +586,7 @@ int bpm_propagate_device(bpm_plan_t plan, const void* d_psi_in, void* d_psi_out,
   PlanAux* aux = aux_of(plan);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (plan->slices_dirty && (rc = prepare_slices(plan, aux->stream)) != BPM_OK) return rc;
-  const size_t bytes = size_t(plan->nb) * 2 * plan->nx * csize(plan);
+  const size_t bytes = size_t(plan->nb) * 2 * plane_of(plan) * csize(plan);
   void* rec = plan->n_rec > 0 ? d_records : nullptr;
   if (plan->precision == BPM_FP32_FUSED) {
     if (d_psi_out != d_psi_in) {
@@ -535,7 +619,7 @@ int bpm_fetch_slices(bpm_plan_t plan, uint8_t* mask, double* phasor) {
   PlanAux* aux = aux_of(plan);
   int rc = BPM_OK;
   if (plan->slices_dirty && (rc = prepare_slices(plan, aux->stream)) != BPM_OK) return rc;
-  const size_t cells = size_t(plan->nx) * plan->nz;
+  const size_t cells = plane_of(plan) * plan->nz;
   std::vector<double> buf;
   if (plan->precision == BPM_FP32_FUSED) {
     std::vector<float> f(2 * cells);
@@ -547,8 +631,9 @@ int bpm_fetch_slices(bpm_plan_t plan, uint8_t* mask, double* phasor) {
     cudaError_t e = cudaMemcpy(buf.data(), plan->d_phasor, cells * 16, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "fetch slices");
   }
-  const int parts = (plan->precision == BPM_FP32_FUSED && plan->logn >= kSplitLogN)
-                        ? (plan->nx >> 12) : 1;
+  const int parts =
+      (plan->ny <= 1 && plan->precision == BPM_FP32_FUSED && plan->logn >= kSplitLogN)
+          ? (plan->nx >> 12) : 1;
   const size_t nx = plan->nx, m = nx / parts;
   for (size_t c = 0; c < cells; ++c) {
     size_t src = c;

@@ -103,6 +103,28 @@ int validate_problem(const bpm_problem* p, std::string* why) {
   return BPM_OK;
 }
 
+int validate_problem3d(const bpm_problem* p, int ny, double dy_um, double y0_um,
+                       std::string* why) {
+  auto bad = [&](const std::string& m) { *why = m; return BPM_ERR_INVALID; };
+  int rc = validate_problem(p, why);
+  if (rc != BPM_OK) return rc;
+  if (p->precision != BPM_FP32_FUSED) return bad("3D plans run in BPM_FP32_FUSED");
+  if (p->nx < 256 || p->nx > 4096) return bad("3D plans need nx in [256, 4096]");
+  if (ny < 256 || ny > 1024 || (ny & (ny - 1)))
+    return bad("ny must be a power of two in [256, 1024]");
+  if (!(dy_um > 0) || !finite(dy_um)) return bad("dy_um must be > 0");
+  if (!finite(y0_um)) return bad("y0_um must be finite");
+  for (int j = 0; j < p->n_energy; ++j) {
+    double e = p->energy_ev[j];
+    double s = std::sin(p->theta_b_ref_rad) * (p->e_ref_ev / e);
+    double k = kTwoPi / (kHcEvAngstrom / e * 1e-4);
+    double qx = M_PI / (k * p->dx_um), qy = M_PI / (k * dy_um);
+    if (!((qx + s) * (qx + s) + qy * qy < 1.0))
+      return bad("evanescent modes: 1 - (qx_max + s)^2 - qy_max^2 <= 0, refine the grid");
+  }
+  return BPM_OK;
+}
+
 void compute_energy_consts(bpm_plan_s* plan) {
   plan->ec.clear();
   for (double e : plan->energies) {
@@ -200,6 +222,31 @@ void fused_prop_table(const bpm_plan_s* plan, int row, std::vector<float2>* out)
       double ph = c.dzh * delta_q(q, c.s, c.c, sign);
       cd d = expm1_i(cd(ph, 0.0)) * inv_n;
       (*out)[size_t(band) * n + pos] = float2{float(d.real()), float(d.imag())};
+    }
+  }
+}
+
+void vol_prop_table(const bpm_plan_s* plan, int row, std::vector<float2>* out) {
+  // delta_+-(qx, qy) = sqrt(1 - (qx +- s)^2 - qy^2) - cos(alpha)
+  //                  = -(qx (qx +- 2 s) + qy^2) / (sqrt(...) + cos(alpha))
+  const EnergyConsts& c = plan->ec[row];
+  const int nx = plan->nx, ny = plan->ny;
+  const double dyh = c.k_um * plan->dy_um;
+  std::vector<int> ox = fft_output_order(plan->logn), oy = fft_output_order(plan->logny);
+  const double inv = 1.0 / (double(nx) * double(ny));
+  out->assign(2 * size_t(nx) * ny, float2{0.f, 0.f});
+  for (int band = 0; band < 2; ++band) {
+    const double sign = band == 0 ? 1.0 : -1.0;
+    for (int py = 0; py < ny; ++py) {
+      const double qy = fftfreq_q(oy[py], ny, dyh);
+      for (int px = 0; px < nx; ++px) {
+        const double qx = fftfreq_q(ox[px], nx, c.dxh);
+        const double t = qx + sign * c.s;
+        const double root = std::sqrt(1.0 - t * t - qy * qy);
+        const double delta = -(qx * (qx + sign * 2.0 * c.s) + qy * qy) / (root + c.c);
+        const cd d = expm1_i(cd(c.dzh * delta, 0.0)) * inv;
+        (*out)[(size_t(band) * ny + py) * nx + px] = float2{float(d.real()), float(d.imag())};
+      }
     }
   }
 }

@@ -138,6 +138,51 @@ __global__ void prep_kernel(PrepParams p) {
   }
 }
 
+// 3D plans: cell (n, i, j) at (x_j, y_i, z_n); the 2D kinds hold at every
+// y, masks and u_x arrays are [nz][ny][nx], the box is tested in FP64.
+struct Prep3D {
+  int ny;
+  double y0, dy;
+  double box[6];
+};
+
+__global__ void prep3d_kernel(PrepParams p, Prep3D q) {
+  const size_t plane = size_t(p.nx) * q.ny;
+  const size_t total = plane * p.nz;
+  for (size_t c = blockIdx.x * size_t(blockDim.x) + threadIdx.x; c < total;
+       c += size_t(gridDim.x) * blockDim.x) {
+    const int n = int(c / plane);
+    const size_t rem = c % plane;
+    const int i = int(rem / p.nx), j = int(rem % p.nx);
+    const double x = __dadd_rn(p.x0, __dmul_rn(double(j), p.dx));
+    const double y = __dadd_rn(q.y0, __dmul_rn(double(i), q.dy));
+    const double z = __dmul_rn(double(n), p.dz);
+    bool in;
+    if (p.crystal_kind == BPM_CRYSTAL_BOX) {
+      in = x >= q.box[0] && x <= q.box[1] && y >= q.box[2] && y <= q.box[3] &&
+           z >= q.box[4] && z <= q.box[5];
+    } else if (p.crystal_kind == BPM_CRYSTAL_MASK) {
+      in = p.mask[c] != 0;
+    } else if (p.crystal_kind == BPM_CRYSTAL_SLAB_AND_MASK) {
+      PrepParams slab = p;
+      slab.crystal_kind = BPM_CRYSTAL_SLAB;
+      in = inside_cell(slab, n, j, x, z) && p.mask[c] != 0;
+    } else {
+      in = inside_cell(p, n, j, x, z);
+    }
+    float2 v = make_float2(0.f, 0.f);
+    if (in) {
+      const double u = p.strain_kind == BPM_STRAIN_ARRAY ? p.ux[c] : strain_ux(p, n, j, x, z);
+      const double theta = p.h * u;
+      const double t = theta - 6.283185307179586 * rint(theta * 0.15915494309189535);
+      float sf, cf;
+      sincosf(float(t), &sf, &cf);
+      v = make_float2(cf, sf);
+    }
+    p.out32[c] = v;
+  }
+}
+
 constexpr int kMaxPolyV = 16;
 constexpr int kMaxIv = kMaxPolyV / 2 + 1;
 
@@ -375,7 +420,7 @@ int prepare_fast(bpm_plan_s* plan, const PrepParams& q, cudaStream_t st, bool sy
 }  // namespace
 
 int prepare_slices(bpm_plan_s* plan, cudaStream_t st, bool sync) {
-  const size_t phasor_bytes = size_t(plan->nx) * plan->nz *
+  const size_t phasor_bytes = plane_of(plan) * plan->nz *
                               (plan->precision == BPM_FP32_FUSED ? 8 : 16);
   if (!plan->d_phasor) {
     cudaError_t ea = cudaMalloc(&plan->d_phasor, phasor_bytes);
@@ -411,14 +456,14 @@ int prepare_slices(bpm_plan_s* plan, cudaStream_t st, bool sync) {
   if (plan->precision == BPM_FP32_FUSED && plan->logn >= kSplitLogN) p.parts = plan->nx >> 12;
   if (plan->precision == BPM_FP32_FUSED) p.out32 = static_cast<float2*>(plan->d_phasor);
   else p.out64 = static_cast<double2*>(plan->d_phasor);
-  if (fast_path_applies(plan)) return prepare_fast(plan, p, st, sync);
+  if (plan->ny <= 1 && fast_path_applies(plan)) return prepare_fast(plan, p, st, sync);
 
   uint8_t* d_mask = nullptr;
   double* d_poly = nullptr;
   double* d_ux = nullptr;
   int rc = BPM_OK;
   cudaError_t e = cudaSuccess;
-  const size_t cells = size_t(plan->nx) * plan->nz;
+  const size_t cells = plane_of(plan) * plan->nz;
   if (!plan->mask.empty()) {
     e = cudaMalloc(&d_mask, cells);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_mask, plan->mask.data(), cells, cudaMemcpyHostToDevice, st);
@@ -442,7 +487,16 @@ int prepare_slices(bpm_plan_s* plan, cudaStream_t st, bool sync) {
     const int threads = 256;
     const size_t want = (cells + threads - 1) / threads;
     const int blocks = int(want < 65536 ? want : 65536);
-    prep_kernel<<<blocks, threads, 0, st>>>(p);
+    if (plan->ny > 1) {
+      Prep3D q{};
+      q.ny = plan->ny;
+      q.y0 = plan->y0_um;
+      q.dy = plan->dy_um;
+      for (int i = 0; i < 6; ++i) q.box[i] = plan->box[i];
+      prep3d_kernel<<<blocks, threads, 0, st>>>(p, q);
+    } else {
+      prep_kernel<<<blocks, threads, 0, st>>>(p);
+    }
     e = cudaGetLastError();
   }
   const bool temporaries = d_mask || d_poly || d_ux;

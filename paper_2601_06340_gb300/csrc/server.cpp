@@ -553,6 +553,7 @@ int bpm_submit(bpm_plan_t plan, const double* psi_in, double* psi_out, void* rec
   if (!plan || !psi_in || !psi_out || !out)
     return fail(BPM_ERR_INVALID, "plan, psi_in, psi_out and out must be non-NULL");
   *out = 0;
+  if (plan->ny > 1) return fail(BPM_ERR_INVALID, "the server takes 2D plans only");
   Server& s = srv();
   auto r = std::make_shared<Request>();
   r->plan = plan;

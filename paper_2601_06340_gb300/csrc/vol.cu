@@ -1,0 +1,144 @@
+// Launchers and host loop of the 3D march (kernels in vol_kernel.cuh).
+#include <string>
+
+#include "fused_launch.cuh"
+#include "vol_kernel.cuh"
+
+namespace bpm {
+
+namespace {
+
+template <typename K>
+int set_smem(K kernel, int bytes, bool* done, const char* what) {
+  if (*done) return BPM_OK;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  *done = true;
+  return BPM_OK;
+}
+
+template <int LX, bool EX>
+int row_launch(const VolParams& p, cudaStream_t st) {
+  using C = VolRowCfg<LX>;
+  static bool done = false;
+  int rc = set_smem(vol_row_kernel<LX, EX>, C::SMEM, &done, "cudaFuncSetAttribute(vol row)");
+  if (rc != BPM_OK) return rc;
+  vol_row_kernel<LX, EX><<<p.nb * p.ny, C::THREADS, C::SMEM, st>>>(p);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? BPM_OK : cuda_fail(e, "vol row kernel");
+}
+
+template <int LY, bool EX>
+int col_launch(const VolParams& p, cudaStream_t st) {
+  using C = VolColCfg<LY>;
+  static bool done = false;
+  int rc = set_smem(vol_col_kernel<LY, EX>, C::SMEM, &done, "cudaFuncSetAttribute(vol col)");
+  if (rc != BPM_OK) return rc;
+  vol_col_kernel<LY, EX><<<p.nb * 2 * (p.nx / C::COLS), C::THREADS, C::SMEM, st>>>(p);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? BPM_OK : cuda_fail(e, "vol column kernel");
+}
+
+template <bool EX>
+int row_dispatch(int lognx, const VolParams& p, cudaStream_t st) {
+  switch (lognx) {
+    case 8: return row_launch<8, EX>(p, st);
+    case 9: return row_launch<9, EX>(p, st);
+    case 10: return row_launch<10, EX>(p, st);
+    case 11: return row_launch<11, EX>(p, st);
+    case 12: return row_launch<12, EX>(p, st);
+    default: return fail(BPM_ERR_INVALID, "3D: unsupported nx");
+  }
+}
+
+template <bool EX>
+int col_dispatch(int logny, const VolParams& p, cudaStream_t st) {
+  switch (logny) {
+    case 8: return col_launch<8, EX>(p, st);
+    case 9: return col_launch<9, EX>(p, st);
+    case 10: return col_launch<10, EX>(p, st);
+    default: return fail(BPM_ERR_INVALID, "3D: unsupported ny");
+  }
+}
+
+// powers[r][slot][band] = dx dy * sum over lines y (in order) of the line sums
+__global__ void vol_reduce_powers(const double* __restrict__ part, double* __restrict__ pw,
+                                  int nb, int n_rec, int ny, int s0, int s1, double dxdy) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nslot = s1 - s0;
+  if (i >= nb * nslot * 2) return;
+  const int band = i & 1, rs = i >> 1;
+  const int r = rs / nslot, slot = s0 + rs % nslot;
+  const double* src = part + ((size_t(r) * n_rec + slot) * 2 + band) * ny;
+  double s = 0.0;
+  for (int y = 0; y < ny; ++y) s += src[y];
+  pw[(size_t(r) * (n_rec + 1) + slot) * 2 + band] = s * dxdy;
+}
+
+}  // namespace
+
+int vol_march(bpm_plan_s* plan, float2* state, float2* d_rec, double* d_pw, int n_begin,
+              int n_end, cudaStream_t st) {
+  const int k = plan->record_every;
+  const bool want = (d_rec || d_pw) && k > 0 && plan->n_rec > 0;
+  if (want && d_pw) {
+    const size_t bytes = size_t(plan->nb) * plan->n_rec * 2 * plan->ny * sizeof(double);
+    if (plan->pwpart_bytes < bytes) {
+      if (plan->d_pwpart) cudaFree(plan->d_pwpart);
+      plan->d_pwpart = nullptr;
+      plan->pwpart_bytes = 0;
+      cudaError_t e = cudaMalloc(&plan->d_pwpart, bytes);
+      if (e != cudaSuccess) {
+        plan->d_pwpart = nullptr;
+        cudaGetLastError();
+        return fail(BPM_ERR_OOM, "3D line power buffer");
+      }
+      plan->pwpart_bytes = bytes;
+    }
+  }
+  VolParams p{};
+  p.org = state;
+  p.spec = static_cast<float2*>(plan->d_spec);
+  p.phasor = static_cast<const float2*>(plan->d_phasor);
+  p.prop = static_cast<const float2*>(plan->d_prop);
+  p.records = want ? d_rec : nullptr;
+  p.pwpart = (want && d_pw) ? plan->d_pwpart : nullptr;
+  p.twx = static_cast<const float4*>(plan->d_tw);
+  p.twy = static_cast<const float4*>(plan->d_twy);
+  p.coup = static_cast<const float2*>(plan->d_rows);
+  p.gphase = reinterpret_cast<const double*>(static_cast<const float2*>(plan->d_rows) + 2 * plan->nb);
+  p.nb = plan->nb;
+  p.nx = plan->nx;
+  p.ny = plan->ny;
+  p.n_phase0 = n_begin;
+  p.record_every = want ? k : 0;
+  p.n_rec = plan->n_rec;
+  const bool ex = fused_exact_constants();
+  auto row = [&]() { return ex ? row_dispatch<true>(plan->logn, p, st) : row_dispatch<false>(plan->logn, p, st); };
+  auto col = [&]() { return ex ? col_dispatch<true>(plan->logny, p, st) : col_dispatch<false>(plan->logny, p, st); };
+  p.mode = 0;
+  p.n = n_begin;
+  int rc = row();
+  for (int n = n_begin; n < n_end && rc == BPM_OK; ++n) {
+    p.n = n;
+    rc = col();
+    if (rc != BPM_OK) break;
+    p.mode = (n + 1 == n_end) ? 2 : 1;
+    rc = row();
+  }
+  if (rc != BPM_OK) return rc;
+  if (p.pwpart) {
+    const int s0 = n_begin / k, s1 = n_end / k;
+    if (s1 > s0) {
+      const int items = plan->nb * (s1 - s0) * 2;
+      vol_reduce_powers<<<(items + 127) / 128, 128, 0, st>>>(
+          plan->d_pwpart, d_pw, plan->nb, plan->n_rec, plan->ny, s0, s1,
+          plan->dx_um * plan->dy_um);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(e, "3D power reduction");
+    }
+  }
+  return BPM_OK;
+}
+
+}  // namespace bpm

@@ -22,6 +22,8 @@ project's benchmark table:
                          ``serving_requests``)
 6. ``rocking_scan``      256 incidence angles over +-50 urad through one Laue
                          slab (100 um), Nx=2048, Nz=2000, one batched launch
+7. ``cube_dislocation_3d`` both transverse coordinates: a 10 um box crystal with
+                         a dislocation at 17.45 keV, 512 x 256 x 300 cells
 
 Each builder takes optional smaller ``nx`` / ``nz`` so that the same
 geometry can be run at sizes the FP64 oracle finishes in seconds.
@@ -75,6 +77,21 @@ class Workload:
     @property
     def cell_updates(self) -> int:
         return self.batch * self.nx * self.nz
+
+
+@dataclass
+class Workload3D(Workload):
+    """A workload with both transverse coordinates: fields [B][2][Ny][Nx]."""
+    ny: int = 1
+    dy_um: float = 1.0
+    y0_um: float = 0.0
+
+    @property
+    def cell_updates(self) -> int:
+        return self.batch * self.nx * self.ny * self.nz
+
+
+CRYSTAL_BOX = 6
 
 
 def gaussian_envelope(nx: int, x0_um: float, dx_um: float, centre_um: float,
@@ -262,6 +279,49 @@ def rocking_scan(nx: int = 2048, nz: int = 2000, n_angles: int = 256,
         crystal=dict(kind=CRYSTAL_SLAB, asym_angle_rad=math.pi / 2,
                      thickness_um=thickness, surf_x_um=0.0, surf_z_um=0.0),
         strain=strain, psi0=psi0, meta=dict(angles_urad=angles))
+
+
+# Si(440)-like reflection at 17.45 keV (d = a / sqrt(32), a = 5.4309 A):
+# chi values scaled from the 8 keV Si values (chi_0 ~ lambda^2, chi_h by the
+# (440) form-factor ratio) -- synthetic stand-ins, not tabulated values.
+E_440_EV = 17450.0
+D_440_UM = 5.4309e-4 / math.sqrt(32.0)
+THETA_440 = math.asin(HC_EV_ANGSTROM / E_440_EV * 1e-4 / (2.0 * D_440_UM))
+CHI0_440 = complex(-3.17e-6, 1.6e-8)
+CHIH_440 = complex(-1.45e-6, 1.2e-8)
+
+
+def cube_dislocation_3d(nx: int = 512, ny: int = 256, nz: int = 300, dx_um: float = 0.05,
+                        dy_um: float = 0.05, dz_um: float = 0.05, cube_um: float = 10.0,
+                        fwhm_um: float = 2.0, record_every: int = 0) -> Workload3D:
+    """Stand-in for the 3D example of Sec. 6 (Si(440) at 17.45 keV from a
+    10 um cube with a dislocation, 300 x 200 x 300 grid): a box crystal
+    x in [0, cube], |y| <= cube/2, z in [cube/4, 5 cube/4]; an edge
+    dislocation (b = 0.384 nm, nu = 0.28) along y through the cube centre
+    (the paper's mixed 60 deg dislocation also has a screw part, not
+    modelled); a Gaussian beam (``fwhm_um`` in x and y) at the Bragg angle
+    hitting the face x = 0 at mid-height; grid padded to powers of two.
+    """
+    x0 = -0.42 * nx * dx_um
+    y0 = -0.5 * ny * dy_um
+    s = math.sin(THETA_440)
+    c = math.cos(THETA_440)
+    z_hit = 0.75 * cube_um
+    xb = -s / c * z_hit
+    x = x0 + np.arange(nx) * dx_um
+    y = y0 + np.arange(ny) * dy_um
+    gx = np.exp(-2.0 * math.log(2.0) * ((x - xb) / (fwhm_um / c)) ** 2)
+    gy = np.exp(-2.0 * math.log(2.0) * (y / fwhm_um) ** 2)
+    psi0 = np.zeros((1, 2, ny, nx), dtype=np.complex128)
+    psi0[0, 0] = gy[:, None] * gx[None, :]
+    box = [0.0, cube_um, -0.5 * cube_um, 0.5 * cube_um, 0.25 * cube_um, 1.25 * cube_um]
+    core = (0.5 * cube_um, 0.75 * cube_um)
+    return Workload3D(
+        "cube_dislocation_3d", nx, nz, dx_um, dz_um, x0, np.array([E_440_EV]), E_440_EV,
+        THETA_440, CHI0_440, CHIH_440, record_every,
+        crystal=dict(kind=CRYSTAL_BOX, box_um=box),
+        strain=dict(kind=STRAIN_EDGE_DISLOCATION, params=[3.84e-4, 0.28, core[0], core[1]]),
+        psi0=psi0, meta=dict(cube_um=cube_um), ny=ny, dy_um=dy_um, y0_um=y0)
 
 
 @dataclass
