@@ -98,6 +98,7 @@ struct bpm_plan_s {
   void* d_twy = nullptr;          // 3D: float4 [ny] twiddles along y
   double* d_pwpart = nullptr;     // 3D: [B][n_rec][2][ny] line power sums
   size_t pwpart_bytes = 0;
+  void* vol_graph = nullptr;      // 3D: captured march (vol.cu)
   size_t device_bytes = 0;
   int pending = 0;                // tickets not yet finished
 };
@@ -142,6 +143,7 @@ int fused_cluster_sms(int logn);
 // phase); records / powers as for the 2D fused path.
 int vol_march(bpm_plan_s* plan, float2* state, float2* d_rec, double* d_pw, int n_begin,
               int n_end, cudaStream_t st);
+void vol_release(bpm_plan_s* plan);   // the captured march, if any
 int plain_march(bpm_plan_s* plan, int n_begin, int n_end, int n_phase0, void* d_records,
                 double* d_powers, cudaStream_t st);
 int launch_convert_in(const double2* src, float2* dst, size_t n, cudaStream_t st);

@@ -44,6 +44,7 @@ int dev_alloc(bpm_plan_s* plan, void** p, size_t bytes, const char* what) {
 }
 
 void free_plan_memory(bpm_plan_s* plan) {
+  vol_release(plan);
   void** ptrs[] = {&plan->d_phasor, &plan->d_prop, &plan->d_tw, &plan->d_state,
                    &plan->d_state2, &plan->d_rows, &plan->d_io, &plan->d_spec,
                    &plan->d_twy, reinterpret_cast<void**>(&plan->d_pwpart)};

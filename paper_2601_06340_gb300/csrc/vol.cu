@@ -17,12 +17,10 @@ int set_smem(K kernel, int bytes, bool* done, const char* what) {
   return BPM_OK;
 }
 
+// (shared-memory attributes are set by prepare_kernels before any launch)
 template <int LX, bool EX>
 int row_launch(const VolParams& p, cudaStream_t st) {
   using C = VolRowCfg<LX>;
-  static bool done = false;
-  int rc = set_smem(vol_row_kernel<LX, EX>, C::SMEM, &done, "cudaFuncSetAttribute(vol row)");
-  if (rc != BPM_OK) return rc;
   vol_row_kernel<LX, EX><<<p.nb * p.ny, C::THREADS, C::SMEM, st>>>(p);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? BPM_OK : cuda_fail(e, "vol row kernel");
@@ -31,12 +29,34 @@ int row_launch(const VolParams& p, cudaStream_t st) {
 template <int LY, bool EX>
 int col_launch(const VolParams& p, cudaStream_t st) {
   using C = VolColCfg<LY>;
-  static bool done = false;
-  int rc = set_smem(vol_col_kernel<LY, EX>, C::SMEM, &done, "cudaFuncSetAttribute(vol col)");
-  if (rc != BPM_OK) return rc;
   vol_col_kernel<LY, EX><<<p.nb * 2 * (p.nx / C::COLS), C::THREADS, C::SMEM, st>>>(p);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? BPM_OK : cuda_fail(e, "vol column kernel");
+}
+
+// Shared-memory attributes of the kernels a plan uses, set before any
+// capture (the first launch would set them too, but not inside a capture).
+template <bool EX>
+int prepare_kernels(int lognx, int logny) {
+  static bool done[2][16] = {};
+  auto row = [&](auto kern, int bytes) { return set_smem(kern, bytes, &done[0][lognx], "vol row"); };
+  auto col = [&](auto kern, int bytes) { return set_smem(kern, bytes, &done[1][logny], "vol col"); };
+  int rc = BPM_OK;
+  switch (lognx) {
+    case 8: rc = row(vol_row_kernel<8, EX>, VolRowCfg<8>::SMEM); break;
+    case 9: rc = row(vol_row_kernel<9, EX>, VolRowCfg<9>::SMEM); break;
+    case 10: rc = row(vol_row_kernel<10, EX>, VolRowCfg<10>::SMEM); break;
+    case 11: rc = row(vol_row_kernel<11, EX>, VolRowCfg<11>::SMEM); break;
+    case 12: rc = row(vol_row_kernel<12, EX>, VolRowCfg<12>::SMEM); break;
+    default: return fail(BPM_ERR_INVALID, "3D: unsupported nx");
+  }
+  if (rc != BPM_OK) return rc;
+  switch (logny) {
+    case 8: return col(vol_col_kernel<8, EX>, VolColCfg<8>::SMEM);
+    case 9: return col(vol_col_kernel<9, EX>, VolColCfg<9>::SMEM);
+    case 10: return col(vol_col_kernel<10, EX>, VolColCfg<10>::SMEM);
+    default: return fail(BPM_ERR_INVALID, "3D: unsupported ny");
+  }
 }
 
 template <bool EX>
@@ -75,7 +95,28 @@ __global__ void vol_reduce_powers(const double* __restrict__ part, double* __res
   pw[(size_t(r) * (n_rec + 1) + slot) * 2 + band] = s * dxdy;
 }
 
+// A march captured as a CUDA graph (two launches per step) on a private
+// stream and launched on the caller's; reused while the same call repeats.
+struct VolGraph {
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const void* state = nullptr;
+  const void* rec = nullptr;
+  const void* pw = nullptr;
+  int n_begin = -1, n_end = -1;
+};
+
 }  // namespace
+
+void vol_release(bpm_plan_s* plan) {
+  auto* g = static_cast<VolGraph*>(plan->vol_graph);
+  if (g) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->cap) cudaStreamDestroy(g->cap);
+    delete g;
+  }
+  plan->vol_graph = nullptr;
+}
 
 int vol_march(bpm_plan_s* plan, float2* state, float2* d_rec, double* d_pw, int n_begin,
               int n_end, cudaStream_t st) {
@@ -114,19 +155,78 @@ int vol_march(bpm_plan_s* plan, float2* state, float2* d_rec, double* d_pw, int 
   p.record_every = want ? k : 0;
   p.n_rec = plan->n_rec;
   const bool ex = fused_exact_constants();
-  auto row = [&]() { return ex ? row_dispatch<true>(plan->logn, p, st) : row_dispatch<false>(plan->logn, p, st); };
-  auto col = [&]() { return ex ? col_dispatch<true>(plan->logny, p, st) : col_dispatch<false>(plan->logny, p, st); };
-  p.mode = 0;
-  p.n = n_begin;
-  int rc = row();
-  for (int n = n_begin; n < n_end && rc == BPM_OK; ++n) {
-    p.n = n;
-    rc = col();
-    if (rc != BPM_OK) break;
-    p.mode = (n + 1 == n_end) ? 2 : 1;
-    rc = row();
+  cudaStream_t lst = st;   // the stream the kernels are enqueued on
+  auto row = [&]() { return ex ? row_dispatch<true>(plan->logn, p, lst) : row_dispatch<false>(plan->logn, p, lst); };
+  auto col = [&]() { return ex ? col_dispatch<true>(plan->logny, p, lst) : col_dispatch<false>(plan->logny, p, lst); };
+  auto enqueue = [&]() {
+    p.mode = 0;
+    p.n = n_begin;
+    int r = row();
+    for (int n = n_begin; n < n_end && r == BPM_OK; ++n) {
+      p.n = n;
+      r = col();
+      if (r != BPM_OK) break;
+      p.mode = (n + 1 == n_end) ? 2 : 1;
+      r = row();
+    }
+    return r;
+  };
+  // Unless the caller's stream is itself being captured, the march runs as a
+  // CUDA graph: captured on a private stream, launched on the caller's, and
+  // re-captured only when the buffers or the step range change.
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    cs = cudaStreamCaptureStatusActive;
   }
+  int rc = ex ? prepare_kernels<true>(plan->logn, plan->logny)
+              : prepare_kernels<false>(plan->logn, plan->logny);
   if (rc != BPM_OK) return rc;
+  if (cs != cudaStreamCaptureStatusNone) {
+    rc = enqueue();
+    if (rc != BPM_OK) return rc;
+  } else {
+    auto* g = static_cast<VolGraph*>(plan->vol_graph);
+    if (!g) {
+      g = new VolGraph();
+      plan->vol_graph = g;
+      cudaError_t e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
+      if (e != cudaSuccess) {
+        g->cap = nullptr;
+        return cuda_fail(e, "3D capture stream");
+      }
+    }
+    const bool hit = g->exec && g->state == state && g->rec == p.records && g->pw == p.pwpart &&
+                     g->n_begin == n_begin && g->n_end == n_end;
+    if (!hit) {
+      cudaGraph_t graph = nullptr;
+      lst = g->cap;
+      cudaError_t e = cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_fail(e, "3D march capture");
+      rc = enqueue();
+      e = cudaStreamEndCapture(g->cap, &graph);
+      lst = st;
+      if (rc != BPM_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc != BPM_OK ? rc : cuda_fail(e, "3D march capture");
+      }
+      if (g->exec) cudaGraphExecDestroy(g->exec);
+      g->exec = nullptr;
+      e = cudaGraphInstantiate(&g->exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        g->exec = nullptr;
+        return cuda_fail(e, "3D march graph instantiate");
+      }
+      g->state = state;
+      g->rec = p.records;
+      g->pw = p.pwpart;
+      g->n_begin = n_begin;
+      g->n_end = n_end;
+    }
+    cudaError_t e = cudaGraphLaunch(g->exec, st);
+    if (e != cudaSuccess) return cuda_fail(e, "3D march graph launch");
+  }
   if (p.pwpart) {
     const int s0 = n_begin / k, s1 = n_end / k;
     if (s1 > s0) {

@@ -186,24 +186,26 @@ __global__ void __launch_bounds__(VolRowCfg<LOGN>::THREADS)
 }
 
 // ---------------------------------------------------------------------------
-// Column kernel: COLS x-frequency columns of one band per CTA (256 threads:
-// COLS = 16 / 8 / 4 for Ny = 256 / 512 / 1024), T = Ny/16 threads per
-// column; lane = column fastest, so table reads and the tile copies are
-// coalesced over the COLS columns.
+// Column kernel: COLS = 4 x-frequency columns of one band per CTA (many
+// small CTAs, so a single solve spreads over the GPU), T = Ny/16 threads
+// per column; lane = column fastest, so table reads and the tile copies move
+// whole 32-byte sectors.
 template <int LOGN>
 struct VolColCfg {
   using F = F2Cfg<LOGN>;
   static constexpr int N = F::N, T = F::T, NP = F::NP;
-  static constexpr int COLS = 256 / T;
+  static constexpr int COLS = 4;
   static constexpr int THREADS = COLS * T;
-  // column stride of odd length in 8-byte words mod 16, so the 16 columns
-  // of a warp's lanes fall in different banks
-  static constexpr int PADC = N + (N >> 4) + 1;
+  // column stride = 8 mod 16 in 8-byte words: a warp is 8 rows x 4 columns,
+  // and the 4 columns land in alternate halves of the banks, so every
+  // 32-lane access spreads over the 16 bank pairs twice (2 wavefronts, the
+  // minimum for 256 bytes)
+  static constexpr int PADC = N + (N >> 4) + 8;
   static constexpr int S1 = F::S1;
   static constexpr int OFF_BUF = 0;                               // [COLS][PADC]
   static constexpr int OFF_TW1 = OFF_BUF + COLS * PADC * 8;       // [S1][16]
   static constexpr int SMEM = OFF_TW1 + S1 * 16 * 8;
-  static_assert(COLS >= 4 && THREADS == 256, "Ny in [256, 1024]");
+  static_assert(THREADS >= 64 && THREADS <= 256, "Ny in [256, 1024]");
 };
 
 template <int LOGN, bool EX>
