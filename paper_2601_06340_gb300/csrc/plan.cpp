@@ -99,6 +99,16 @@ int validate_problem(const bpm_problem* p, std::string* why) {
     double qmax = M_PI / (k * p->dx_um);
     if (!((qmax + s) * (qmax + s) < 1.0))
       return bad("evanescent modes: 1 - (q_max + s)^2 <= 0, refine the grid");
+    // Eqs. fov11-fov12 expand the step's coupling in powers of
+    // w = dz^ chi_h / cos(alpha); the series is summed in FP64, which stays
+    // accurate for |w| <= 1 (steps far shorter than the extinction length)
+    const double c = std::sqrt((1.0 - s) * (1.0 + s));
+    const double w = k * p->dz_um * std::hypot(p->chih_re, p->chih_im) / c;
+    const double phi_im = k * p->dz_um * std::fabs(p->chi0_im) / (2.0 * c);
+    if (!(w <= 1.0))
+      return bad("dz too long for the coupling expansion: |dz^ chi_h / cos(alpha)| = " +
+                 std::to_string(w) + " > 1");
+    if (!(phi_im <= 700.0)) return bad("dz too long: the per-step absorption underflows");
   }
   return BPM_OK;
 }

@@ -107,6 +107,30 @@ def gaussian_envelope(nx: int, x0_um: float, dx_um: float, centre_um: float,
     return amp * np.exp(1j * tilt_per_um * (x - centre_um))
 
 
+def slit_field(nx: int, x0_um: float, dx_um: float, centre_um: float, width_um: float,
+               tilt_per_um: float = 0.0) -> np.ndarray:
+    """Incident psi_+ shaped by a slit (section topography, Sec. 5: a 5 um
+    slit): unit amplitude on the cells whose centres lie within
+    ``width_um`` / 2 of ``centre_um``, zero elsewhere, with an optional
+    linear envelope phase; psi_- = 0.  Shape [1][2][nx]."""
+    x = x0_um + np.arange(nx, dtype=np.float64) * dx_um
+    amp = (np.abs(x - centre_um) <= 0.5 * width_um).astype(np.float64)
+    return _two_band(amp * np.exp(1j * tilt_per_um * (x - centre_um)))
+
+
+def far_field_step(exit_field: np.ndarray, nx: int, dx_um: float, x0_um: float,
+                   distance_um: float, energy_ev: float = E_REF_EV,
+                   theta_b_ref_rad: float = THETA_B_REF) -> "Workload":
+    """One free-space step of ``distance_um`` applied to a march's exit
+    field (both envelopes, each through its own angular-spectrum operator):
+    a vacuum plan with chi = 0, nz = 1, dz = distance (the far-field images
+    of Secs. 5-6 are taken 2-4 m behind the crystal)."""
+    return Workload(
+        "far_field", nx, 1, dx_um, distance_um, x0_um, np.array([energy_ev]), energy_ev,
+        theta_b_ref_rad, 0j, 0j, 0, crystal=dict(kind=CRYSTAL_VACUUM),
+        strain=dict(kind=STRAIN_NONE), psi0=np.asarray(exit_field, dtype=np.complex128))
+
+
 def _two_band(psi_plus: np.ndarray) -> np.ndarray:
     out = np.zeros((1, 2, psi_plus.shape[-1]), dtype=np.complex128)
     out[0, 0] = psi_plus

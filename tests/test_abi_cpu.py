@@ -58,6 +58,7 @@ def _problem(**kw):
     ("precision", 7, "precision"),
     ("chi0_re", float("nan"), "finite"),
     ("dx_um", 1e-5, "evanescent"),
+    ("dz_um", 100.0, "coupling expansion"),
 ])
 def test_plan_rejects_invalid_problems_on_the_host(lib, field, value, needle):
     prob, keep = _problem(**{field: value})
@@ -66,6 +67,22 @@ def test_plan_rejects_invalid_problems_on_the_host(lib, field, value, needle):
     assert rc == binding.BPM_ERR_INVALID
     assert needle in binding.bpm_last_error()
     assert h.value is None
+
+
+def test_long_free_space_step_is_valid_without_a_crystal(lib):
+    """A far-field step (chi = 0, dz of metres) passes validation; it is only
+    the coupling expansion that bounds dz."""
+    from paper_2601_06340_gb300 import inputs
+    prob, keep = _problem(dz_um=2.0e6, chi0_re=0.0, chi0_im=0.0, chih_re=0.0, chih_im=0.0,
+                          nz=1)
+    # validation happens before any device work: without a GPU the call gets
+    # past it and fails on the device (or succeeds on a GPU box)
+    h = ctypes.c_void_p()
+    rc = lib.bpm_plan(ctypes.byref(prob), ctypes.byref(h))
+    assert rc != binding.BPM_ERR_INVALID, binding.bpm_last_error()
+    if h.value:
+        lib.bpm_destroy(h)
+    assert inputs.slit_field(256, -25.6, 0.2, 0.0, 5.0).shape == (1, 2, 256)
 
 
 def test_null_arguments_are_rejected(lib):
