@@ -137,6 +137,24 @@ int bpm_set_crystal(bpm_plan_t plan, int32_t kind, double asym_angle_rad,
 int bpm_set_strain(bpm_plan_t plan, int32_t kind, const double* ux_um,
                    const double* params, int32_t n_params);
 
+/* Operator splitting of Eq. split-op for FP64 plans: the step applies
+ * A(a_1 dz) B(b_1 dz) A(a_2 dz) B(b_2 dz) ... in that order (A: the
+ * angular-spectrum propagation of each band, B: the coupling of Eqs.
+ * fov11-fov12 formed for a step of b_i dz), every stage of step n with the
+ * mask and strain of z_n.
+ *   BPM_SPLIT_FIRST_ORDER: a = (1), b = (1), Eq. fov10 (the default);
+ *   BPM_SPLIT_VERLET:      a = (0, 1), b = (1/2, 1/2);
+ *   BPM_SPLIT_FOREST_RUTH: a = (0, t, 1-2t, t), b = (t/2, (1-t)/2, (1-t)/2,
+ *                          t/2), t = 1/(2 - 2^(1/3)).
+ * FP32 (fused) and 3D plans take the first-order step only: other methods
+ * return BPM_ERR_INVALID for them.  BPM_ERR_BUSY while tickets are pending. */
+enum bpm_splitting {
+  BPM_SPLIT_FIRST_ORDER = 0,
+  BPM_SPLIT_VERLET = 1,
+  BPM_SPLIT_FOREST_RUTH = 2
+};
+int bpm_set_splitting(bpm_plan_t plan, int32_t method);
+
 /* 3D plans: the march of Eq. fov4 with both transverse coordinates (x, y)
  * and the two-beam envelopes of Eqs. fov6-fov10 (the Bragg shift k_d/2 is
  * along x only): each band goes through exp(i dz^ sqrt(1 - (qx +- s)^2 -

@@ -170,6 +170,39 @@ class MarchResult:
     powers: np.ndarray    # [B][n_rec + 1][2] float64, dx * sum |psi|^2
 
 
+FOREST_RUTH_T = 1.0 / (2.0 - 2.0 ** (1.0 / 3.0))   # 1.3512..., printed as 1.3512
+
+
+def split_stages(method: str) -> list[tuple[float, float]]:
+    """Stage coefficients (a_i, b_i) of the operator splitting of Eq.
+    split-op: the step applies A(a_1 dz), B(b_1 dz), A(a_2 dz), B(b_2 dz), ...
+    in that order, A the angular-spectrum propagation and B the coupling.
+    first_order: a = (1), b = (1) -- Eq. fov10 itself;
+    verlet:      a = (0, 1), b = (1/2, 1/2);
+    forest_ruth: a = (0, t, 1 - 2t, t), b = (t/2, (1-t)/2, (1-t)/2, t/2),
+                 t = 1 / (2 - 2^(1/3)) (the paper prints t = 1.3512)."""
+    if method == "first_order":
+        return [(1.0, 1.0)]
+    if method == "verlet":
+        return [(0.0, 0.5), (1.0, 0.5)]
+    if method == "forest_ruth":
+        t = FOREST_RUTH_T
+        return [(0.0, t / 2.0), (t, (1.0 - t) / 2.0), (1.0 - 2.0 * t, (1.0 - t) / 2.0),
+                (t, t / 2.0)]
+    raise ValueError(f"unknown splitting method {method}")
+
+
+def coupling_coefficients(plan: "EnergyPlan", frac: float, chi0: complex, chih: complex
+                          ) -> tuple[complex, complex]:
+    """(Delta_eps_0, Delta_eps_+-1) of Eqs. fov11-fov12 for a coupling step
+    of frac * dz (frac = b_i of Eq. split-op)."""
+    w = frac * plan.dzh * complex(chih) / plan.c
+    phi0 = frac * plan.dzh * complex(chi0) / (2.0 * plan.c)
+    e_phi0 = complex(math.exp(-phi0.imag) * math.cos(phi0.real),
+                     math.exp(-phi0.imag) * math.sin(phi0.real))
+    return bessel_series(0, w) * e_phi0, 1j * bessel_series(1, w) * e_phi0
+
+
 def band_power(psi: np.ndarray, dx_um: float) -> np.ndarray:
     """P = dx * sum_j |psi_j|^2 along the last axis."""
     return dx_um * np.sum(psi.real ** 2 + psi.imag ** 2, axis=-1)
@@ -177,7 +210,8 @@ def band_power(psi: np.ndarray, dx_um: float) -> np.ndarray:
 
 def march(plans: list[EnergyPlan], psi0: np.ndarray, slices, n_begin: int,
           n_end: int, record_every: int, dx_um: float,
-          prop_override: tuple[np.ndarray, np.ndarray] | None = None
+          prop_override: tuple[np.ndarray, np.ndarray] | None = None,
+          method: str = "first_order", chi: tuple[complex, complex] | None = None
           ) -> MarchResult:
     """Advance psi0 (state after ``n_begin`` steps) to the state after ``n_end``.
 
@@ -192,6 +226,10 @@ def march(plans: list[EnergyPlan], psi0: np.ndarray, slices, n_begin: int,
               [0, n_end), so a resumed march fills the later slots.
     prop_override : optional (P+, P-) replacing exp(i dz^ delta_+-) (same
               table for every row); used only by the gauge-identity test.
+    method  : operator splitting of Eq. split-op (see ``split_stages``); the
+              stages of step n all use the mask and strain of z_n (the
+              equation evaluates delta_eps at the step's z^).  Higher orders
+              need ``chi`` = (chi_0, chi_h) to form the fractional couplings.
 
     Powers: row r, record i holds the two band powers at that record; the
     last entry holds the powers of the returned state.
@@ -213,19 +251,43 @@ def march(plans: list[EnergyPlan], psi0: np.ndarray, slices, n_begin: int,
     a = np.array([p.a for p in plans])[:, None]
     b = np.array([p.b for p in plans])[:, None]
 
+    # stages: (propagator pair or None, common-phase factor, a, b) per row.
+    # A stage of a_i dz propagates with g^{a_i} exp(i a_i dz^ delta_+-); the
+    # factors g^{a_i} multiply both bands, commute with the coupling and
+    # multiply to g per step (sum a_i = 1), so higher-order schemes apply g
+    # once, after the step's last stage.
+    stages = []
+    if method == "first_order":
+        stages.append(((prop_p, prop_m), g, a, b))
+    else:
+        chi0, chih = chi
+        for frac_a, frac_b in split_stages(method):
+            props = None
+            if frac_a != 0.0:
+                props = (np.stack([np.exp(1j * frac_a * p.dzh * p.delta_plus) for p in plans]),
+                         np.stack([np.exp(1j * frac_a * p.dzh * p.delta_minus) for p in plans]))
+            ab = [coupling_coefficients(p, frac_b, chi0, chih) for p in plans]
+            stages.append((props, 1.0, np.array([x[0] for x in ab])[:, None],
+                           np.array([x[1] for x in ab])[:, None]))
+
     psi_p = psi0[:, 0, :].copy()
     psi_m = psi0[:, 1, :].copy()
     for step in range(n_begin, n_end):
-        # Free propagation of each envelope through its own band operator.
-        pp = np.fft.ifft(np.fft.fft(psi_p, axis=-1) * prop_p, axis=-1) * g
-        pm = np.fft.ifft(np.fft.fft(psi_m, axis=-1) * prop_m, axis=-1) * g
-        # Real-space coupling through chi_0, chi_h, the strain phase and Pi.
         inside, theta = slices(step)
         e_plus = np.exp(1j * theta)     # exp(+i h u_x) on Delta_eps'_{+1}
         e_minus = np.exp(-1j * theta)   # exp(-i h u_x) on Delta_eps'_{-1}
-        new_p = np.where(inside, a * pp + b * e_plus * pm, pp)
-        new_m = np.where(inside, a * pm + b * e_minus * pp, pm)
-        psi_p, psi_m = new_p, new_m
+        for props, gs, a_s, b_s in stages:
+            if props is not None:
+                # Free propagation of each envelope through its own band operator.
+                psi_p = np.fft.ifft(np.fft.fft(psi_p, axis=-1) * props[0], axis=-1) * gs
+                psi_m = np.fft.ifft(np.fft.fft(psi_m, axis=-1) * props[1], axis=-1) * gs
+            # Real-space coupling through chi_0, chi_h, the strain phase and Pi.
+            new_p = np.where(inside, a_s * psi_p + b_s * e_plus * psi_m, psi_p)
+            new_m = np.where(inside, a_s * psi_m + b_s * e_minus * psi_p, psi_m)
+            psi_p, psi_m = new_p, new_m
+        if method != "first_order":
+            psi_p = psi_p * g
+            psi_m = psi_m * g
         if record_every > 0 and (step + 1) % record_every == 0:
             slot = (step + 1) // record_every - 1
             records[:, slot, 0, :] = psi_p

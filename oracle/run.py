@@ -33,15 +33,17 @@ def crystal_for(wl) -> geometry.Crystal:
 
 
 def run_workload(wl, n_begin=0, n_end=None, rows=None, psi_in=None,
-                 record_every=None) -> bpm.MarchResult:
-    """March rows ``rows`` (default all) of ``wl`` from n_begin to n_end."""
+                 record_every=None, method="first_order") -> bpm.MarchResult:
+    """March rows ``rows`` (default all) of ``wl`` from n_begin to n_end with
+    the operator splitting ``method`` (see ``bpm.split_stages``)."""
     n_end = wl.nz if n_end is None else n_end
     plans = plans_for(wl, rows)
     psi = wl.psi0 if psi_in is None else psi_in
     if rows is not None:
         psi = np.asarray(psi)[list(rows)]
     rec = wl.record_every if record_every is None else record_every
-    return bpm.march(plans, psi, crystal_for(wl), n_begin, n_end, rec, wl.dx_um)
+    return bpm.march(plans, psi, crystal_for(wl), n_begin, n_end, rec, wl.dx_um,
+                     method=method, chi=(complex(wl.chi0), complex(wl.chih)))
 
 
 def mask_of(wl) -> np.ndarray:

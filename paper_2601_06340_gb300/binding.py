@@ -23,6 +23,7 @@ BPM_ERR_INVALID, BPM_ERR_OOM, BPM_ERR_CUDA = -1, -2, -3
 BPM_ERR_BUSY, BPM_ERR_TIMEOUT, BPM_ERR_NUMERIC = -4, -5, -6
 BPM_FP64_PLAIN, BPM_FP32_FUSED = 0, 1
 BPM_CRYSTAL_BOX = 6
+BPM_SPLIT_FIRST_ORDER, BPM_SPLIT_VERLET, BPM_SPLIT_FOREST_RUTH = 0, 1, 2
 
 _STATUS_NAMES = {0: "OK", 1: "NOT_READY", -1: "ERR_INVALID", -2: "ERR_OOM",
                  -3: "ERR_CUDA", -4: "ERR_BUSY", -5: "ERR_TIMEOUT", -6: "ERR_NUMERIC"}
@@ -55,6 +56,7 @@ _SIGS = {
     "bpm_plan": ([ctypes.POINTER(bpm_problem), ctypes.POINTER(_P)], ctypes.c_int),
     "bpm_plan3d": ([ctypes.POINTER(bpm_problem), _I, _D, _D, ctypes.POINTER(_P)], ctypes.c_int),
     "bpm_set_crystal_box": ([_P, _P], ctypes.c_int),
+    "bpm_set_splitting": ([_P, _I], ctypes.c_int),
     "bpm_set_crystal": ([_P, _I, _D, _D, _D, _D, _P, _P, _I], ctypes.c_int),
     "bpm_set_strain": ([_P, _I, _P, _P, _I], ctypes.c_int),
     "bpm_propagate": ([_P, _P, _P, _P, _P, _I, _I], ctypes.c_int),
@@ -120,6 +122,10 @@ def bpm_plan3d(problem: bpm_problem, ny: int, dy_um: float, y0_um: float) -> int
     _check(load().bpm_plan3d(ctypes.byref(problem), int(ny), float(dy_um), float(y0_um),
                              ctypes.byref(h)))
     return h.value
+
+
+def bpm_set_splitting(plan, method: int):
+    return _check(load().bpm_set_splitting(plan, int(method)))
 
 
 def bpm_set_crystal_box(plan, box_um):
@@ -220,7 +226,8 @@ class MarchOutput:
 class Plan:
     """Owns one bpm plan built from a workload (see ``inputs.Workload``)."""
 
-    def __init__(self, wl, precision: int = BPM_FP32_FUSED, record_every: int | None = None):
+    def __init__(self, wl, precision: int = BPM_FP32_FUSED, record_every: int | None = None,
+                 splitting: int = BPM_SPLIT_FIRST_ORDER):
         self.wl = wl
         self.precision = precision
         self.record_every = wl.record_every if record_every is None else record_every
@@ -247,6 +254,8 @@ class Plan:
                             c.get("surf_z_um", 0.0), c.get("mask"), c.get("polygon"))
         st = dict(wl.strain)
         bpm_set_strain(self.handle, st.pop("kind"), st.get("ux"), st.get("params"))
+        if splitting != BPM_SPLIT_FIRST_ORDER:
+            bpm_set_splitting(self.handle, splitting)
         self.n_rec = (wl.nz // self.record_every) if self.record_every > 0 else 0
 
     @property

@@ -7,6 +7,7 @@
 #include <complex>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/bpm.h"
@@ -99,6 +100,12 @@ struct bpm_plan_s {
   double* d_pwpart = nullptr;     // 3D: [B][n_rec][2][ny] line power sums
   size_t pwpart_bytes = 0;
   void* vol_graph = nullptr;      // 3D: captured march (vol.cu)
+  // operator splitting (FP64 plans): stages of one step
+  int32_t split = BPM_SPLIT_FIRST_ORDER;
+  int32_t n_stages = 0;
+  std::vector<int> stage_has_prop;   // [n_stages]: stage propagates (a_i != 0)
+  void* d_stage_rows = nullptr;      // RowDescF64 [n_stages][B]
+  void* d_stage_prop = nullptr;      // double2 [tables][B][2][nx]
   size_t device_bytes = 0;
   int pending = 0;                // tickets not yet finished
 };
@@ -122,6 +129,14 @@ void vol_prop_table(const bpm_plan_s* plan, int row, std::vector<float2>* out);
 int validate_problem3d(const bpm_problem* p, int ny, double dy_um, double y0_um,
                        std::string* why);
 void plain_prop_table(const bpm_plan_s* plan, int row, std::vector<double2>* out);
+// exp(i frac dz^ delta_+-(q)) / nx: the propagator of a stage of frac * dz
+void plain_prop_table_frac(const bpm_plan_s* plan, int row, double frac,
+                           std::vector<double2>* out);
+// (Delta_eps_0, Delta_eps_+-1) of a coupling stage of frac * dz
+void coupling_frac(const bpm_plan_s* plan, int row, double frac, std::complex<double>* a,
+                   std::complex<double>* b);
+// stage coefficients (a_i, b_i) of a splitting method
+std::vector<std::pair<double, double>> split_stages(int method);
 void twiddle_table_f32(int n, std::vector<float4>* out);
 void twiddle_table_f64(int n, std::vector<double2>* out);
 std::vector<int> fft_output_order(int logn);   // position -> frequency index

@@ -47,7 +47,8 @@ void free_plan_memory(bpm_plan_s* plan) {
   vol_release(plan);
   void** ptrs[] = {&plan->d_phasor, &plan->d_prop, &plan->d_tw, &plan->d_state,
                    &plan->d_state2, &plan->d_rows, &plan->d_io, &plan->d_spec,
-                   &plan->d_twy, reinterpret_cast<void**>(&plan->d_pwpart)};
+                   &plan->d_twy, reinterpret_cast<void**>(&plan->d_pwpart),
+                   &plan->d_stage_rows, &plan->d_stage_prop};
   for (void** p : ptrs) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -390,6 +391,67 @@ int bpm_plan3d(const bpm_problem* p, int32_t ny, double dy_um, double y0_um, bpm
   std::string why;
   if (validate_problem3d(p, ny, dy_um, y0_um, &why) != BPM_OK) return fail(BPM_ERR_INVALID, why);
   return make_plan(p, ny, dy_um, y0_um, out);
+}
+
+int bpm_set_splitting(bpm_plan_t plan, int32_t method) {
+  if (!plan) return fail(BPM_ERR_INVALID, "plan is NULL");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  if (plan->pending) return fail(BPM_ERR_BUSY, "plan has pending tickets");
+  if (method < BPM_SPLIT_FIRST_ORDER || method > BPM_SPLIT_FOREST_RUTH)
+    return fail(BPM_ERR_INVALID, "unknown splitting method");
+  if (method != BPM_SPLIT_FIRST_ORDER &&
+      (plan->precision != BPM_FP64_PLAIN || plan->ny > 1))
+    return fail(BPM_ERR_INVALID, "higher-order splitting needs a 2D BPM_FP64_PLAIN plan");
+  for (void** p : {&plan->d_stage_rows, &plan->d_stage_prop}) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+  plan->split = method;
+  plan->n_stages = 0;
+  plan->stage_has_prop.clear();
+  if (method == BPM_SPLIT_FIRST_ORDER) return BPM_OK;
+  const auto stages = split_stages(method);
+  const size_t n = plan->nx, nb = plan->nb;
+  // one table per distinct nonzero a_i
+  std::vector<double> fracs;
+  for (auto& st : stages)
+    if (st.first != 0.0 && std::find(fracs.begin(), fracs.end(), st.first) == fracs.end())
+      fracs.push_back(st.first);
+  int rc = dev_alloc(plan, &plan->d_stage_prop, fracs.size() * nb * 2 * n * sizeof(double2),
+                     "splitting propagators");
+  if (rc == BPM_OK)
+    rc = dev_alloc(plan, &plan->d_stage_rows, stages.size() * nb * sizeof(RowDescF64),
+                   "splitting stages");
+  if (rc != BPM_OK) return rc;
+  double2* tables = static_cast<double2*>(plan->d_stage_prop);
+  std::vector<RowDescF64> rows(stages.size() * nb);
+  cudaError_t e = cudaSuccess;
+  for (size_t f = 0; f < fracs.size() && e == cudaSuccess; ++f)
+    for (size_t r = 0; r < nb && e == cudaSuccess; ++r) {
+      std::vector<double2> t;
+      plain_prop_table_frac(plan, int(r), fracs[f], &t);
+      e = cudaMemcpy(tables + (f * nb + r) * 2 * n, t.data(), t.size() * sizeof(double2),
+                     cudaMemcpyHostToDevice);
+    }
+  for (size_t s = 0; s < stages.size(); ++s) {
+    const size_t f = std::find(fracs.begin(), fracs.end(), stages[s].first) - fracs.begin();
+    plan->stage_has_prop.push_back(stages[s].first != 0.0 ? 1 : 0);
+    for (size_t r = 0; r < nb; ++r) {
+      RowDescF64& d = rows[s * nb + r];
+      d.prop = stages[s].first != 0.0 ? tables + (f * nb + r) * 2 * n : nullptr;
+      std::complex<double> a, b;
+      coupling_frac(plan, int(r), stages[s].second, &a, &b);
+      d.a = make_double2(a.real(), a.imag());
+      d.b = make_double2(b.real(), b.imag());
+      d.gphase = plan->ec[r].gphase;
+    }
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpy(plan->d_stage_rows, rows.data(), rows.size() * sizeof(RowDescF64),
+                   cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "splitting tables");
+  plan->n_stages = int(stages.size());
+  return BPM_OK;
 }
 
 int bpm_set_crystal_box(bpm_plan_t plan, const double* box_um) {

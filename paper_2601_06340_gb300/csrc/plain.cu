@@ -188,14 +188,27 @@ int plain_march(bpm_plan_s* plan, int n_begin, int n_end, int n_phase0, void* d_
     if (e != cudaSuccess) return cuda_fail(e, "plain march: phase buffer");
   }
   int slot_toggle = 0;
+  // stages of one step: (propagates?, descriptors); first order = one stage
+  std::vector<std::pair<bool, const RowDescF64*>> stages;
+  if (plan->split == BPM_SPLIT_FIRST_ORDER || plan->n_stages == 0) {
+    stages.push_back({true, rows});
+  } else {
+    const RowDescF64* sr = static_cast<const RowDescF64*>(plan->d_stage_rows);
+    for (int i = 0; i < plan->n_stages; ++i)
+      stages.push_back({plan->stage_has_prop[i] != 0, sr + size_t(i) * nb});
+  }
   for (int s = n_begin; s < n_end; ++s) {
-    double2* r = fft_lines(x, y, logn, lines, tw, false, st);
-    if (r != x) std::swap(x, y);
-    prop_kernel<<<grid_for(long(lines) * n, threads), threads, 0, st>>>(x, rows, n, nb);
-    r = fft_lines(x, y, logn, lines, tw, true, st);
-    if (r != x) std::swap(x, y);
-    couple_kernel<<<grid_for(long(nb) * n, threads), threads, 0, st>>>(
-        x, rows, phasor + size_t(s) * n, n, nb);
+    for (const auto& stage : stages) {
+      if (stage.first) {
+        double2* r = fft_lines(x, y, logn, lines, tw, false, st);
+        if (r != x) std::swap(x, y);
+        prop_kernel<<<grid_for(long(lines) * n, threads), threads, 0, st>>>(x, stage.second, n, nb);
+        r = fft_lines(x, y, logn, lines, tw, true, st);
+        if (r != x) std::swap(x, y);
+      }
+      couple_kernel<<<grid_for(long(nb) * n, threads), threads, 0, st>>>(
+          x, stage.second, phasor + size_t(s) * n, n, nb);
+    }
     if (any_rec && (s + 1) % plan->record_every == 0) {
       const int slot = (s + 1) / plan->record_every - 1;
       for (int row = 0; row < nb; ++row) {

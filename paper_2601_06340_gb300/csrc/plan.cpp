@@ -261,6 +261,39 @@ void vol_prop_table(const bpm_plan_s* plan, int row, std::vector<float2>* out) {
   }
 }
 
+std::vector<std::pair<double, double>> split_stages(int method) {
+  if (method == BPM_SPLIT_VERLET) return {{0.0, 0.5}, {1.0, 0.5}};
+  if (method == BPM_SPLIT_FOREST_RUTH) {
+    const double t = 1.0 / (2.0 - std::cbrt(2.0));
+    return {{0.0, t / 2.0}, {t, (1.0 - t) / 2.0}, {1.0 - 2.0 * t, (1.0 - t) / 2.0}, {t, t / 2.0}};
+  }
+  return {{1.0, 1.0}};
+}
+
+void coupling_frac(const bpm_plan_s* plan, int row, double frac, cd* a, cd* b) {
+  const EnergyConsts& c = plan->ec[row];
+  const cd w = frac * c.w, phi0 = frac * c.phi0;
+  const cd ephi = std::exp(cd(0.0, 1.0) * phi0);
+  *a = (1.0 + bessel(0, w, true)) * ephi;
+  *b = cd(0.0, 1.0) * bessel(1, w, false) * ephi;
+}
+
+void plain_prop_table_frac(const bpm_plan_s* plan, int row, double frac,
+                           std::vector<double2>* out) {
+  const EnergyConsts& c = plan->ec[row];
+  int n = plan->nx;
+  out->assign(2 * size_t(n), double2{0.0, 0.0});
+  double inv_n = 1.0 / double(n);
+  for (int band = 0; band < 2; ++band) {
+    int sign = band == 0 ? +1 : -1;
+    for (int m = 0; m < n; ++m) {
+      double q = fftfreq_q(m, n, c.dxh);
+      double ph = frac * c.dzh * delta_q(q, c.s, c.c, sign);
+      (*out)[size_t(band) * n + m] = double2{std::cos(ph) * inv_n, std::sin(ph) * inv_n};
+    }
+  }
+}
+
 void plain_prop_table(const bpm_plan_s* plan, int row, std::vector<double2>* out) {
   const EnergyConsts& c = plan->ec[row];
   int n = plan->nx;
