@@ -212,6 +212,52 @@ def test_p5_laue_rocking_curve_matches_two_beam_theory():
     assert want.max() > 0.8 and np.abs(delta).max() > 6 * kappa
 
 
+def _bragg_reflectivity(angles_urad, dz, nx=1024, dx=0.8, fwhm=100.0, march_um=1000.0):
+    """Reflectivity of a thick symmetric Bragg slab (x in [0, 400] um) for a
+    wide Gaussian beam turned by each angle offset: P_- at the end of the
+    march over the incident P_+."""
+    nz = int(round(march_um / dz))
+    chi0, chih = complex(-1.51e-5, 3.5e-7), complex(-9.1e-6, 3.4e-7)
+    x0 = -0.75 * nx * dx
+    s, c = math.sin(THETA), math.cos(THETA)
+    k = 2.0 * math.pi / bpm.wavelength_um(E)
+    xb = -s / c * 0.35 * march_um            # hits x = 0 at 35 % of the march
+    x = x0 + dx * np.arange(nx)
+    psi0 = np.zeros((len(angles_urad), 2, nx), complex)
+    for i, a in enumerate(angles_urad):
+        psi0[i, 0] = np.exp(-2.0 * math.log(2.0) * ((x - xb) / (fwhm / c)) ** 2) * np.exp(
+            1j * k * c * a * 1e-6 * (x - xb))
+    plans = [_plan(nx, dx, dz, chi0, chih) for _ in angles_urad]
+    cr = geometry.Crystal(nx, x0, dx, dz, bpm.d_spacing_um(E, THETA)).set_crystal(
+        geometry.CRYSTAL_SLAB, asym_angle_rad=0.0, thickness_um=400.0)
+    res = bpm.march(plans, psi0, cr, 0, nz, 0, dx)
+    return res.powers[:, -1, 1] / (dx * np.sum(np.abs(psi0[:, 0]) ** 2, axis=-1))
+
+
+def test_p5b_bragg_darwin_curve():
+    """Thick symmetric Bragg crystal against the two-beam (Darwin-Prins)
+    reflectivity with absorption: R = min |eta -+ sqrt(eta^2 - 1)|^2,
+    eta = (-dtheta sin 2 theta_B - chi_0) / sqrt(chi_h chi_-h) (chi_-h = chi_h
+    for a centrosymmetric crystal): total reflection over a width
+    2|chi_h|/sin 2 theta_B = 24.8 urad centred at the refraction shift
+    -chi_0'/sin 2 theta_B = +20.5 urad.  The march's truncated coupling loses
+    power at O(dz) (P6), so the reflectivity is extrapolated to dz -> 0 from
+    dz = 0.2 and 0.1 um (first order); a 100 um beam diverges by < 1 urad.
+    The tail point and the plateau then agree to 1 % (the steep edges,
+    where a fraction of a microradian matters, are not compared)."""
+    angles = [2.0, 14.0, 20.0, 26.0]
+    r1 = _bragg_reflectivity(angles, 0.2)
+    r2 = _bragg_reflectivity(angles, 0.1)
+    got = 2.0 * r2 - r1
+    chi0, chih = complex(-1.51e-5, 3.5e-7), complex(-9.1e-6, 3.4e-7)
+    th = np.array(angles) * 1e-6
+    eta = (-th * math.sin(2.0 * THETA) - chi0) / np.sqrt(chih * chih)
+    root = np.sqrt(eta ** 2 - 1.0 + 0j)
+    want = np.minimum(np.abs(eta - root) ** 2, np.abs(eta + root) ** 2)
+    assert np.all(np.abs(got - want) <= 0.01 * np.maximum(want, 0.1)), (got, want)
+    assert got[0] < 0.2 and min(got[1:]) > 0.85       # refraction shift is +20 urad
+
+
 def _laue_modes_error(method, dz, thick=50.0):
     """max over grid modes of |R - R_two_beam| (the P5 problem)."""
     nx, dx = 64, 1.0
