@@ -293,6 +293,58 @@ def volume_run(dev, stream, barrier, max_over_ranks, world, rank, check, steps=3
     return out
 
 
+def configs_run(dev, stream, barrier, max_over_ranks, world, rank, check, steps=3):
+    """The single-solve configurations besides the headline one: the
+    symmetric Laue crystal (Nx=1024, Nz=2000) and the asymmetric Bragg slab
+    with a polygonal shape and an edge dislocation (Nx=8192, Nz=12000): the
+    fused FP32 and plain FP64 GPU paths, the FP64 oracle on one host core,
+    and both paths' errors against it."""
+    import torch
+    from paper_2601_06340_gb300 import binding, inputs
+    out = {}
+    for name, make in (("laue_perfect", inputs.laue_perfect),
+                       ("asym_dislocation", inputs.asym_dislocation)):
+        wl = make()
+        wl.record_every = 0
+        row = {"nx": wl.nx, "nz": wl.nz}
+        psi = {}
+        for prec, key in ((binding.BPM_FP32_FUSED, "fused_fp32"),
+                          (binding.BPM_FP64_PLAIN, "plain_fp64")):
+            plan = binding.Plan(wl, prec)
+            dt = torch.complex64 if prec == binding.BPM_FP32_FUSED else torch.complex128
+            x = torch.from_numpy(wl.psi0).to(dev).to(dt)
+            y = torch.empty_like(x)
+
+            def march():
+                binding.bpm_propagate_device(plan.handle, x, y, None, None, 0, wl.nz,
+                                             stream.cuda_stream)
+            march()
+            barrier()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            n = steps if prec == binding.BPM_FP32_FUSED else 1
+            a.record(stream)
+            for _ in range(n):
+                march()
+            b.record(stream)
+            barrier()
+            ms = max_over_ranks(a.elapsed_time(b)) / n
+            row[key] = {"value": world * wl.cell_updates / (ms * 1e-3), "unit": UNIT,
+                        "ms_per_march": ms}
+            psi[key] = y.cpu().numpy().astype(np.complex128)
+            plan.close()
+        row["fused_speedup"] = row["fused_fp32"]["value"] / row["plain_fp64"]["value"]
+        if check:
+            from oracle import run as orun
+            t0 = time.perf_counter()
+            ref = orun.run_workload(wl, record_every=0)
+            cpu_s = time.perf_counter() - t0
+            row["oracle_1core"] = {"value": wl.cell_updates / cpu_s, "unit": UNIT, "cores": 1}
+            row["fused_fp32"]["rel_l2_err"] = rel_l2_bands(psi["fused_fp32"], ref.psi)
+            row["plain_fp64"]["rel_l2_err"] = rel_l2_bands(psi["plain_fp64"], ref.psi)
+        out[name] = row
+    return out
+
+
 def run_reference(args, rank, world):
     """FP64 oracle on the host cores: each step is a bounded sample (the
     first `sample_steps` z-steps of the march)."""
@@ -513,6 +565,12 @@ def run_gpu(args, rks):
         rocking = rocking_run(dev, stream, barrier, max_over_ranks, world, rank,
                               check=rank == 0 and not args.skip_oracle)
 
+    # ---- the other single-solve configurations ------------------------------
+    configs = None
+    if not args.skip_configs:
+        configs = configs_run(dev, stream, barrier, max_over_ranks, world, rank,
+                              check=rank == 0 and not args.skip_oracle)
+
     # ---- 3D: both transverse coordinates -----------------------------------
     volume = None
     if not args.skip_volume:
@@ -582,6 +640,7 @@ def run_gpu(args, rks):
                            "rel_l2_err": err64, "tolerance": 1e-10,
                            "fused_speedup": value / value64},
             "batched": batched,
+            "configs": configs,
             "rocking": rocking,
             "volume": volume,
             "serving": serving,
@@ -607,6 +666,7 @@ def main():
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--skip-rocking", action="store_true")
     ap.add_argument("--skip-volume", action="store_true")
+    ap.add_argument("--skip-configs", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=440)
     ap.add_argument("--serving-rate", type=float, default=200.0)
     ap.add_argument("--capacity-requests", type=int, default=600)
