@@ -238,7 +238,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
     const uint32_t xo = xpeer + uint32_t(half * N) * 8u;
     const uint32_t xbo = xbar_peer + uint32_t(half) * 8u;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = make_float2(org[j].x + v[j].x, org[j].y + v[j].y);
+    for (int j = 0; j < 16; ++j) v[j] = cadd(org[j], v[j]);
 #pragma unroll
     for (int pp = 0; pp < 8; ++pp)
       st_async_v4(xo + uint32_t(xpair(pp, t, T)) * 8u, v[2 * pp], v[2 * pp + 1], xbo);

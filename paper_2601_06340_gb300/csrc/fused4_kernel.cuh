@@ -232,7 +232,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg::T, 1)
       const uint32_t co = c_part + uint32_t(half * M) * 8u;
       const uint32_t cbo = cbar_part + uint32_t(half) * 8u;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = make_float2(org[j].x + v[j].x, org[j].y + v[j].y);
+      for (int j = 0; j < 16; ++j) v[j] = cadd(org[j], v[j]);
 #pragma unroll
       for (int pp = 0; pp < 8; ++pp)
         st_async_v4(co + uint32_t(xpair(pp, t, T)) * 8u, v[2 * pp], v[2 * pp + 1], cbo);

@@ -27,11 +27,21 @@ constexpr float kS1l = float(kS1d - double(kS1h));
 constexpr float kHh = float(kHd);
 constexpr float kHl = float(kHd - double(kHh));
 
+// Complex add / subtract.  PACK = true: one packed FP32x2 instruction (sm_100
+// family) each; per component the result is the correctly rounded scalar
+// sum or difference (a - b is formed as b * (-1) + a, which rounds once,
+// exactly like a - b), so both forms give bit-identical results.  Packing
+// halves the issue slots of the adds; whether that pays depends on the
+// kernel (register pairing can cost moves), so kernels choose.
+template <bool PACK = true>
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) {
-  return make_float2(a.x + b.x, a.y + b.y);
+  if constexpr (PACK) return __fadd2_rn(a, b);
+  else return make_float2(a.x + b.x, a.y + b.y);
 }
+template <bool PACK = true>
 __device__ __forceinline__ float2 csub(float2 a, float2 b) {
-  return make_float2(a.x - b.x, a.y - b.y);
+  if constexpr (PACK) return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+  else return make_float2(a.x - b.x, a.y - b.y);
 }
 
 // Multiply by W4 = -i (forward) or +i (inverse): exact.
@@ -101,53 +111,55 @@ __device__ __forceinline__ float2 mul_w16_9(float2 z) {
              : cmul_k<EXACT>(z, -kC1h, kS1h, -kC1l, kS1l);
 }
 
-template <bool INV>
+template <bool INV, bool PACK = true>
 __device__ __forceinline__ void dft2(float2* v) {
   float2 a = v[0], b = v[1];
-  v[0] = cadd(a, b);
-  v[1] = csub(a, b);
+  v[0] = cadd<PACK>(a, b);
+  v[1] = csub<PACK>(a, b);
 }
 
-template <bool INV>
+// (the last two outputs add a swapped, negated pair: scalar, which folds the
+// negation into the adds)
+template <bool INV, bool PACK = true>
 __device__ __forceinline__ void dft4_inplace(float2& x0, float2& x1,
                                              float2& x2, float2& x3) {
-  float2 t0 = cadd(x0, x2), t1 = csub(x0, x2);
-  float2 t2 = cadd(x1, x3), t3 = mul_w4<INV>(csub(x1, x3));
-  x0 = cadd(t0, t2);
-  x2 = csub(t0, t2);
-  x1 = cadd(t1, t3);
-  x3 = csub(t1, t3);
+  float2 t0 = cadd<PACK>(x0, x2), t1 = csub<PACK>(x0, x2);
+  float2 t2 = cadd<PACK>(x1, x3), t3 = mul_w4<INV>(csub<PACK>(x1, x3));
+  x0 = cadd<PACK>(t0, t2);
+  x2 = csub<PACK>(t0, t2);
+  x1 = cadd<false>(t1, t3);
+  x3 = csub<false>(t1, t3);
 }
 
-template <bool INV>
+template <bool INV, bool PACK = true>
 __device__ __forceinline__ void dft4(float2* v) {
-  dft4_inplace<INV>(v[0], v[1], v[2], v[3]);
+  dft4_inplace<INV, PACK>(v[0], v[1], v[2], v[3]);
 }
 
 // 8 = 4 x 2: n = 2 n1 + n2, k = k1 + 4 k2.
-template <bool INV, bool EXACT = true>
+template <bool INV, bool EXACT = true, bool PACK = true>
 __device__ __forceinline__ void dft8(float2* v) {
-  dft4_inplace<INV>(v[0], v[2], v[4], v[6]);   // n2 = 0 -> a[k1][0] at v[2 k1]
-  dft4_inplace<INV>(v[1], v[3], v[5], v[7]);   // n2 = 1 -> a[k1][1] at v[2 k1 + 1]
+  dft4_inplace<INV, PACK>(v[0], v[2], v[4], v[6]);   // n2 = 0 -> a[k1][0] at v[2 k1]
+  dft4_inplace<INV, PACK>(v[1], v[3], v[5], v[7]);   // n2 = 1 -> a[k1][1] at v[2 k1 + 1]
   v[3] = mul_w8<INV, EXACT>(v[3]);
   v[5] = mul_w4<INV>(v[5]);
   v[7] = mul_w8_3<INV, EXACT>(v[7]);
   float2 o[8];
 #pragma unroll
   for (int k1 = 0; k1 < 4; ++k1) {
-    o[k1] = cadd(v[2 * k1], v[2 * k1 + 1]);
-    o[k1 + 4] = csub(v[2 * k1], v[2 * k1 + 1]);
+    o[k1] = cadd<PACK>(v[2 * k1], v[2 * k1 + 1]);
+    o[k1 + 4] = csub<PACK>(v[2 * k1], v[2 * k1 + 1]);
   }
 #pragma unroll
   for (int k = 0; k < 8; ++k) v[k] = o[k];
 }
 
 // 16 = 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2, inner twiddles W16^(n2 k1).
-template <bool INV, bool EXACT = true>
+template <bool INV, bool EXACT = true, bool PACK = true>
 __device__ __forceinline__ void dft16(float2* v) {
 #pragma unroll
   for (int n2 = 0; n2 < 4; ++n2)
-    dft4_inplace<INV>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+    dft4_inplace<INV, PACK>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
   // a[k1][n2] now at v[4 k1 + n2]
   v[5] = mul_w16_1<INV, EXACT>(v[5]);      // k1=1,n2=1: W^1
   v[6] = mul_w8<INV, EXACT>(v[6]);         // k1=1,n2=2: W^2
@@ -160,7 +172,7 @@ __device__ __forceinline__ void dft16(float2* v) {
   v[15] = mul_w16_9<INV, EXACT>(v[15]);    // k1=3,n2=3: W^9
 #pragma unroll
   for (int k1 = 0; k1 < 4; ++k1)
-    dft4_inplace<INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    dft4_inplace<INV, PACK>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
   // X[k1 + 4 k2] at v[4 k1 + k2]: transpose the 4x4 block.
   float2 o[16];
 #pragma unroll
@@ -171,12 +183,12 @@ __device__ __forceinline__ void dft16(float2* v) {
   for (int k = 0; k < 16; ++k) v[k] = o[k];
 }
 
-template <int R, bool INV, bool EXACT = true>
+template <int R, bool INV, bool EXACT = true, bool PACK = true>
 __device__ __forceinline__ void dft(float2* v) {
-  if constexpr (R == 2) dft2<INV>(v);
-  else if constexpr (R == 4) dft4<INV>(v);
-  else if constexpr (R == 8) dft8<INV, EXACT>(v);
-  else if constexpr (R == 16) dft16<INV, EXACT>(v);
+  if constexpr (R == 2) dft2<INV, PACK>(v);
+  else if constexpr (R == 4) dft4<INV, PACK>(v);
+  else if constexpr (R == 8) dft8<INV, EXACT, PACK>(v);
+  else if constexpr (R == 16) dft16<INV, EXACT, PACK>(v);
 }
 
 // z * w for a table twiddle t = (ch, sh, cl, sl) holding W = exp(-i a);

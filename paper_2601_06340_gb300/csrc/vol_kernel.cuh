@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(VolRowCfg<LOGN>::THREADS)
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       const float2 o = p.org[off + t + j * T];
-      v[j] = make_float2(o.x + v[j].x, o.y + v[j].y);
+      v[j] = cadd<false>(o, v[j]);   // scalar: the packed add measured slower here
     }
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
