@@ -601,7 +601,10 @@ def run_gpu(args, rks):
                 "traffic": profiled_traffic("fused_march_bragg_bent.md"),
                 "kernel": "fused3_march_kernel<12> (2-CTA cluster per solve, one band per CTA)",
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
-                "sm_frac": achieved / (peak_tflops / sms),
+                # the solve occupies one 2-CTA cluster: the fraction of those
+                # two SMs' peak
+                "cluster_sms": 2,
+                "cluster_frac": achieved / (2 * peak_tflops / sms),
                 "flops_per_cell_update": FLOPS_PER_CELL(wl.nx)}
     if batched is not None:
         ach_b = batched["value"] / world * FLOPS_PER_CELL(4096) / 1e12
