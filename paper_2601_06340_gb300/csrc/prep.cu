@@ -321,40 +321,50 @@ __global__ void fast_cols_kernel(FastParams p, ColInfo* cols) {
   cols[j] = c;
 }
 
-// One block row per z-step (grid-stride over rows); threads walk the row's
-// output positions, so the stores are contiguous in every layout.
-__global__ void fast_cells_kernel(FastParams p, const RowInfo* __restrict__ rows,
-                                  const ColInfo* __restrict__ cols, float k_disl, float q_disl,
-                                  float2* __restrict__ out) {
-  __shared__ RowInfo r;
-  const int m = p.nx / p.parts;
+// Every thread writes 4 consecutive outputs of a row (two 16-byte stores);
+// blocks stride over the rows.  The row's intervals and phase are read from
+// global memory with the same address in every lane (broadcast loads that
+// stay in L1).  Output position o of a row holds column
+// j = (o mod m) parts + o div m, m = nx / parts (a power of two).
+template <int STRAIN>
+__global__ void __launch_bounds__(256)
+    fast_cells_kernel(FastParams p, const RowInfo* __restrict__ rows,
+                      const ColInfo* __restrict__ cols, float k_disl, float q_disl, int log_m,
+                      float2* __restrict__ out) {
+  const int m_mask = (1 << log_m) - 1;
+  const int o0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (o0 >= p.nx) return;
   for (int n = blockIdx.y; n < p.nz; n += gridDim.y) {
-    __syncthreads();
-    if (threadIdx.x == 0) r = rows[n];
-    __syncthreads();
-    for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < p.nx; o += gridDim.x * blockDim.x) {
-      const int j = (o % m) * p.parts + o / m;
+    const RowInfo* r = rows + n;
+    const int nint = __ldg(&r->nint);
+    float2 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int o = o0 + u;
+      const int j = (o & m_mask) * p.parts + (o >> log_m);
       bool in = false;
-      for (int k = 0; k < r.nint; ++k) in |= (j >= r.lo[k]) & (j < r.hi[k]);
-      float2 v = make_float2(0.f, 0.f);
+      for (int k = 0; k < nint; ++k) in |= (j >= __ldg(&r->lo[k])) & (j < __ldg(&r->hi[k]));
+      v[u] = make_float2(0.f, 0.f);
       if (in) {
-        if (p.strain_kind == BPM_STRAIN_BENT) {
-          const float2 a = cols[j].ph, b = r.ph;
-          v = make_float2(fmaf(a.x, b.x, -(a.y * b.y)), fmaf(a.x, b.y, a.y * b.x));
-        } else if (p.strain_kind == BPM_STRAIN_EDGE_DISLOCATION) {
-          const float xp = cols[j].xp, zp = r.zp;
+        if constexpr (STRAIN == BPM_STRAIN_BENT) {
+          const float2 a = __ldg(&cols[j].ph), b = __ldg(&r->ph);
+          v[u] = make_float2(fmaf(a.x, b.x, -(a.y * b.y)), fmaf(a.x, b.y, a.y * b.x));
+        } else if constexpr (STRAIN == BPM_STRAIN_EDGE_DISLOCATION) {
+          const float xp = __ldg(&cols[j].xp), zp = __ldg(&r->zp);
           const float r2 = fmaf(xp, xp, zp * zp);
           float th = 0.f;
           if (r2 != 0.f) th = k_disl * (atan2f(zp, xp) + (xp * zp) * q_disl / r2);
           float sn, cs;
           sincosf(th, &sn, &cs);
-          v = make_float2(cs, sn);
+          v[u] = make_float2(cs, sn);
         } else {
-          v = make_float2(1.f, 0.f);
+          v[u] = make_float2(1.f, 0.f);
         }
       }
-      out[size_t(n) * p.nx + o] = v;
     }
+    float4* dst = reinterpret_cast<float4*>(out + size_t(n) * p.nx + o0);
+    dst[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    dst[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
   }
 }
 
@@ -402,8 +412,18 @@ int prepare_fast(bpm_plan_s* plan, const PrepParams& q, cudaStream_t st, bool sy
     const float k_disl = float(p.h * p.p0 / 6.283185307179586);
     const float q_disl = float(1.0 / (2.0 * (1.0 - p.p1)));
     const int threads = 256;
-    dim3 grid((p.nx + threads - 1) / threads, p.nz < 65535 ? p.nz : 65535);
-    fast_cells_kernel<<<grid, threads, 0, st>>>(p, d_rows, d_cols, k_disl, q_disl, q.out32);
+    int log_m = 0;
+    while ((1 << log_m) < p.nx / p.parts) ++log_m;
+    dim3 grid((p.nx + 4 * threads - 1) / (4 * threads), p.nz < 65535 ? p.nz : 65535);
+    if (p.strain_kind == BPM_STRAIN_BENT)
+      fast_cells_kernel<BPM_STRAIN_BENT><<<grid, threads, 0, st>>>(p, d_rows, d_cols, k_disl,
+                                                                  q_disl, log_m, q.out32);
+    else if (p.strain_kind == BPM_STRAIN_EDGE_DISLOCATION)
+      fast_cells_kernel<BPM_STRAIN_EDGE_DISLOCATION><<<grid, threads, 0, st>>>(
+          p, d_rows, d_cols, k_disl, q_disl, log_m, q.out32);
+    else
+      fast_cells_kernel<BPM_STRAIN_NONE><<<grid, threads, 0, st>>>(p, d_rows, d_cols, k_disl,
+                                                                  q_disl, log_m, q.out32);
     e = cudaGetLastError();
   }
   if (d_rows) cudaFreeAsync(d_rows, st);
