@@ -173,6 +173,7 @@ int launch_omega_to_t(const void* d_in, void* d_out, int nb, int nx,
                       int precision, cudaStream_t st);
 int fused_smem_bytes(int logn);
 int fused_rows_resident(int logn, int n_rows);
+int fused_launch_capacity(int logn, bool cluster);
 int fused_rows_per_cta(int logn);
 int fused_threads(int logn);
 

@@ -25,6 +25,8 @@ int fused4_launch_14(const RowDescF32*, int, int, const float4*, int*, cudaStrea
   int fused3_launch_##L(const RowDescF32*, int, int, const float4*, int*,        \
                         cudaStream_t);
 BPM_DECLARE_FUSED3(10) BPM_DECLARE_FUSED3(11) BPM_DECLARE_FUSED3(12)
+int fused3_rows_resident_10(); int fused3_rows_resident_11(); int fused3_rows_resident_12();
+int fused4_rows_resident_13(); int fused4_rows_resident_14();
 int fused_rows_resident_3(); int fused_rows_resident_4(); int fused_rows_resident_5();
 int fused_rows_resident_6(); int fused_rows_resident_7(); int fused2_rows_resident_8();
 int fused2_rows_resident_9(); int fused2_rows_resident_10(); int fused2_rows_resident_11();
@@ -157,6 +159,42 @@ int fused_rows_resident(int logn, int n_rows) {
     cache[logn] = r * sm_count();
   }
   return cache[logn];
+}
+
+// Rows one launch of the given layout keeps resident on the whole GPU:
+// clusters for the cluster kernels (N >= 8192 always, 1024..4096 when
+// `cluster`), else CTA rows per SM times the SMs.
+int fused_launch_capacity(int logn, bool cluster) {
+  static int cache[2][kMaxLogN + 1] = {};
+  const bool cl = logn >= kSplitLogN || (cluster && logn >= 10 && logn <= 12);
+  int& c = cache[cl ? 1 : 0][logn];
+  if (c == 0) {
+    if (cl) {
+      switch (logn) {
+        case 10: c = fused3_rows_resident_10(); break;
+        case 11: c = fused3_rows_resident_11(); break;
+        case 12: c = fused3_rows_resident_12(); break;
+        case 13: c = fused4_rows_resident_13(); break;
+        default: c = fused4_rows_resident_14(); break;
+      }
+    } else {
+      int r = 1;
+      switch (logn) {
+        case 3: r = fused_rows_resident_3(); break;
+        case 4: r = fused_rows_resident_4(); break;
+        case 5: r = fused_rows_resident_5(); break;
+        case 6: r = fused_rows_resident_6(); break;
+        case 7: r = fused_rows_resident_7(); break;
+        case 8: r = fused2_rows_resident_8(); break;
+        case 9: r = fused2_rows_resident_9(); break;
+        case 10: r = fused2_rows_resident_10(); break;
+        case 11: r = fused2_rows_resident_11(); break;
+        default: r = fused2_rows_resident_12(); break;
+      }
+      c = r * sm_count();
+    }
+  }
+  return c;
 }
 
 int fused_smem_bytes(int logn) { int a, b, c; fused_cfg(logn, &a, &b, &c); return a; }

@@ -74,6 +74,23 @@ int blocks_per_sm(K kernel, int threads, int smem) {
   return n > 0 ? n : 1;
 }
 
+// Clusters of a kernel with compile-time cluster dimensions that the GPU
+// keeps resident at once (cluster-occupancy query; 1 if it fails).
+template <typename K>
+int clusters_resident(K kernel, int cluster, int threads, int smem) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cluster * 64);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, (void*)kernel, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n > 0 ? n : 1;
+}
+
 // 2-CTA cluster kernel (one row per cluster, one band per CTA).
 template <int LOGN, bool EX>
 int fused3_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const float4* d_tw,
@@ -121,6 +138,14 @@ int fused4_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
 
 #define BPM_INSTANTIATE_FUSED4(P, L)                                              \
   namespace bpm {                                                                 \
+  int fused4_rows_resident_##L() {                                                \
+    if constexpr (P == 2)                                                         \
+      return clusters_resident(fused4e_march_kernel<true>, 4, F4ECfg::T,          \
+                               F4ECfg::SMEM);                                     \
+    else                                                                          \
+      return clusters_resident(fused4t_march_kernel<true>, 8, F4TCfg::T,          \
+                               F4TCfg::SMEM);                                     \
+  }                                                                               \
   int fused4_launch_##L(const RowDescF32* r, int n, int s, const float4* tw,     \
                         int* status, cudaStream_t st) {                           \
     return fused_exact_constants()                                                \
@@ -131,6 +156,10 @@ int fused4_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
 
 #define BPM_INSTANTIATE_FUSED3(L)                                                 \
   namespace bpm {                                                                 \
+  int fused3_rows_resident_##L() {                                                \
+    return clusters_resident(fused3_march_kernel<L, true>, 2, F3Cfg<L>::T,        \
+                             F3Cfg<L>::SMEM);                                     \
+  }                                                                               \
   int fused3_launch_##L(const RowDescF32* r, int n, int s, const float4* tw,     \
                         int* status, cudaStream_t st) {                           \
     return fused_exact_constants()                                                \

@@ -6,18 +6,24 @@
 // its strain-phasor stream) stay within the configured limits.  Active
 // requests are grouped into buckets by transform size (FP32) -- FP64
 // requests get a bucket each -- and every bucket runs its own pipeline on
-// its own stream: as soon as a bucket's previous epoch has finished (event
-// query, no device-wide wait), the worker retires the requests that are
-// done and launches the next epoch for the bucket's current members, so
-// requests that arrive while others run join at the next epoch of their
-// size, and sizes do not wait for each other.  All rows of one bucket with
-// the same remaining step count share one fused launch.  Device memory of
-// requests is allocated and released stream-ordered (cudaMallocAsync /
-// cudaFreeAsync), so retiring a request never stalls other buckets.
+// its own stream.  A bucket advances its members in batches: a batch takes
+// the next members in round-robin order, at most as many rows as one launch
+// of that size keeps resident on the GPU, and advances each by one chunk
+// (`epoch_steps` steps, or what is left); rows of a batch with the same
+// chunk length share one fused launch.  Two batches are kept in flight per
+// bucket, so the next one is already queued on the stream when the current
+// one ends, and a launch never holds more rows than run at once (no partial
+// last wave).  A member's chunks run in order because its batches share the
+// stream.  Requests that arrive while others run join the rotation at the
+// next batch of their size, and sizes do not wait for each other.  Device
+// memory of requests is allocated and released stream-ordered
+// (cudaMallocAsync / cudaFreeAsync), so retiring a request never stalls
+// other buckets; a request is retired only once every batch holding it has
+// completed.
 //
 // A request's arithmetic does not depend on which other requests share its
 // launches (rows are independent and each row runs the same code for the
-// same shape), so a result is the same alone and in the mix.
+// same shape and layout), so a result is the same alone and in the mix.
 #include <algorithm>
 #include <array>
 #include <chrono>
@@ -69,21 +75,32 @@ struct Request {
   cudaEvent_t out_ev = nullptr;   // results copied to the pinned staging
   void* h_stage = nullptr;        // pinned staging: psi c128, records, powers
   size_t h_stage_bytes = 0;
-  int n_done = 0;
+  int n_sched = 0;             // steps enqueued on the bucket's stream
+  int n_done = 0;              // steps of batches that have completed
+  int failed = BPM_OK;         // error of a completed batch that held it
 };
 using ReqPtr = std::shared_ptr<Request>;
 
+// One launch group in flight: its rows, completion event and status word.
+struct Batch {
+  cudaEvent_t ev = nullptr;
+  int* h_status = nullptr;      // pinned copy of the batch's status word
+  int* d_status = nullptr;
+  std::vector<std::pair<ReqPtr, int>> items;   // (request, steps)
+  int err = BPM_OK;             // a launch of the batch failed on the host
+};
+
 struct Bucket {
   cudaStream_t st = nullptr;
-  cudaEvent_t ev = nullptr;
-  int* h_status = nullptr;      // pinned copy of the epoch's status word
-  bool busy = false;
   std::vector<ReqPtr> members;
-  std::vector<std::pair<ReqPtr, int>> launched;   // (request, steps) of the epoch in flight
-  RowDescF32* d_rows = nullptr;
-  size_t cap = 0;
-  int* d_status = nullptr;
+  std::deque<Batch> inflight;   // oldest first
+  std::vector<Batch> free;      // recycled batches (event, status words)
+  size_t rr = 0;                // round-robin cursor into members
+  RowDescF32* d_rows = nullptr; // descriptors of the batch being uploaded
+  size_t cap = 0;               // (stream order keeps one buffer safe)
 };
+
+constexpr size_t kBatchesInFlight = 2;
 
 struct Server {
   std::mutex mu;
@@ -308,19 +325,35 @@ Bucket& bucket_for(Server& s, long key) {
     Bucket& b = s.buckets[key];
     b = std::move(s.spare.back());
     s.spare.pop_back();
-    b.busy = false;
     b.members.clear();
-    b.launched.clear();
+    b.rr = 0;
     return b;
   }
   Bucket& b = s.buckets[key];
   cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking);
-  cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming);
-  cudaMalloc(&b.d_status, sizeof(int));
-  cudaMemset(b.d_status, 0, sizeof(int));
-  cudaHostAlloc(reinterpret_cast<void**>(&b.h_status), sizeof(int), cudaHostAllocDefault);
-  *b.h_status = 0;
   return b;
+}
+
+Batch take_batch(Bucket& b) {
+  if (!b.free.empty()) {
+    Batch bt = std::move(b.free.back());
+    b.free.pop_back();
+    bt.items.clear();
+    bt.err = BPM_OK;
+    return bt;
+  }
+  Batch bt;
+  cudaEventCreateWithFlags(&bt.ev, cudaEventDisableTiming);
+  cudaMalloc(&bt.d_status, sizeof(int));
+  cudaHostAlloc(reinterpret_cast<void**>(&bt.h_status), sizeof(int), cudaHostAllocDefault);
+  *bt.h_status = 0;
+  return bt;
+}
+
+bool has_unscheduled(const Bucket& b) {
+  for (auto& r : b.members)
+    if (r->failed == BPM_OK && r->n_sched < r->plan->nz) return true;
+  return false;
 }
 
 // SMs the active FP32 rows would occupy in their cluster layouts.
@@ -332,36 +365,53 @@ int cluster_demand(Server& s) {
   return d;
 }
 
-// Launch the next epoch of a bucket.  Layout by load: when every active row
+// Launch the next batch of a bucket.  Layout by load: when every active row
 // can have the SMs of its cluster layout the launch is latency-first (a
 // 2-CTA cluster per row for N <= 4096); once that demand would exceed the
 // GPU, rows of N <= 4096 go one CTA per row (several rows per SM for small N),
-// which does more cell-updates per SM.
-int launch_epoch(Server& s, long key, Bucket& b) {
-  b.launched.clear();
+// which does more cell-updates per SM.  The batch takes at most as many
+// rows as that layout keeps resident, in round-robin order over the members
+// that still have steps to enqueue.
+int launch_batch(Server& s, Bucket& b) {
+  Batch bt = take_batch(b);
+  const bool fp32 = b.members.front()->plan->precision == BPM_FP32_FUSED;
+  const int logn = b.members.front()->plan->logn;   // one size per bucket
+  const int layout = fp32 && cluster_demand(s) <= s.sm_count ? -1 : 0;
+  size_t limit = b.members.size();
+  if (fp32) {
+    const bool cluster = layout < 0 && 2 * int(b.members.size()) <= s.sm_count;
+    limit = size_t(std::max(1, fused_launch_capacity(logn, cluster)));
+  }
   std::map<int, std::vector<RowDescF32>> groups;   // FP32 rows by step count
   std::vector<RowDescF32> rows;
-  for (auto& r : b.members) {
+  cudaMemsetAsync(bt.d_status, 0, sizeof(int), b.st);
+  const size_t nm = b.members.size();
+  for (size_t k = 0; k < nm && bt.items.size() < limit; ++k) {
+    ReqPtr r = b.members[(b.rr + k) % nm];
     bpm_plan_s* p = r->plan;
-    if (r->ready) {   // first epoch of this request: wait for its staging
+    if (r->failed != BPM_OK || r->n_sched >= p->nz) continue;
+    if (r->ready) {   // first batch of this request: wait for its staging
       cudaStreamWaitEvent(b.st, r->ready, 0);
       cudaEventDestroy(r->ready);
       r->ready = nullptr;
     }
-    const int steps = std::min(s.epoch_steps, p->nz - r->n_done);
-    b.launched.push_back({r, steps});
-    if (p->precision != BPM_FP32_FUSED) {
-      int err = plain_march(p, r->n_done, r->n_done + steps, 0, r->d_rec, r->d_pow, b.st);
-      if (err != BPM_OK) return err;
+    const int steps = std::min(s.epoch_steps, p->nz - r->n_sched);
+    const int n0 = r->n_sched;
+    bt.items.push_back({r, steps});
+    r->n_sched += steps;
+    if (!fp32) {
+      bt.err = plain_march(p, n0, n0 + steps, 0, r->d_rec, r->d_pow, b.st);
+      if (bt.err != BPM_OK) break;
       continue;
     }
     fused_rows(p, static_cast<float2*>(r->d_state), static_cast<float2*>(r->d_rec), r->d_pow,
-               r->n_done, r->n_done + steps, &rows);
+               n0, n0 + steps, &rows);
     for (auto& d : rows) d.n_phase0 = 0;
     auto& g = groups[steps];
     g.insert(g.end(), rows.begin(), rows.end());
   }
-  if (!groups.empty()) {
+  b.rr = nm ? (b.rr + bt.items.size()) % nm : 0;
+  if (bt.err == BPM_OK && !groups.empty()) {
     size_t total = 0;
     for (auto& kv : groups) total += kv.second.size();
     if (total > b.cap) {
@@ -371,31 +421,40 @@ int launch_epoch(Server& s, long key, Bucket& b) {
         b.d_rows = nullptr;
         b.cap = 0;
         cudaGetLastError();
-        return BPM_ERR_OOM;
+        bt.err = BPM_ERR_OOM;
       }
     }
-    const int logn = b.members.front()->plan->logn;   // one size per bucket
     if (!s.d_tw[logn]) {
       std::vector<float4> tw;
       twiddle_table_f32(1 << logn, &tw);
       cudaMalloc(&s.d_tw[logn], tw.size() * sizeof(float4));
       cudaMemcpy(s.d_tw[logn], tw.data(), tw.size() * sizeof(float4), cudaMemcpyHostToDevice);
     }
-    const int layout = cluster_demand(s) <= s.sm_count ? -1 : 0;
     size_t off = 0;
     for (auto& kv : groups) {
+      if (bt.err != BPM_OK) break;
       cudaMemcpyAsync(b.d_rows + off, kv.second.data(), kv.second.size() * sizeof(RowDescF32),
                       cudaMemcpyHostToDevice, b.st);
-      int err = launch_fused_layout(logn, b.d_rows + off, int(kv.second.size()), kv.first,
-                                    s.d_tw[logn], b.d_status, b.st, layout);
-      if (err != BPM_OK) return err;
+      bt.err = launch_fused_layout(logn, b.d_rows + off, int(kv.second.size()), kv.first,
+                                   s.d_tw[logn], bt.d_status, b.st, layout);
       off += kv.second.size();
     }
   }
-  cudaMemcpyAsync(b.h_status, b.d_status, sizeof(int), cudaMemcpyDeviceToHost, b.st);
-  cudaEventRecord(b.ev, b.st);
-  b.busy = true;
-  return BPM_OK;
+  // Even a batch whose launch failed part-way goes in flight: what was
+  // enqueued may still use its requests' memory, so they retire (failed)
+  // only after its event.
+  cudaMemcpyAsync(bt.h_status, bt.d_status, sizeof(int), cudaMemcpyDeviceToHost, b.st);
+  cudaEventRecord(bt.ev, b.st);
+  const int err = bt.err;
+  b.inflight.push_back(std::move(bt));
+  return err;
+}
+
+// Hand a request whose every scheduled batch has completed to retirement.
+void retire_or_fail(Server& s, const ReqPtr& r) {
+  const int rc = r->failed != BPM_OK ? r->failed : retire_enqueue(s, *r);
+  if (rc == BPM_OK) s.retiring.push_back(r);
+  else finish_request(s, r, rc, "request failed on the device");
 }
 
 void worker_loop() {
@@ -406,7 +465,8 @@ void worker_loop() {
     {
       std::unique_lock<std::mutex> lk(s.mu);
       bool any_work = false;
-      for (auto& kv : s.buckets) any_work = any_work || kv.second.busy || !kv.second.members.empty();
+      for (auto& kv : s.buckets)
+        any_work = any_work || !kv.second.inflight.empty() || !kv.second.members.empty();
       any_work = any_work || !s.retiring.empty();
       if (s.queue.empty() && !any_work)
         s.cv_work.wait(lk, [&] { return !s.queue.empty(); });
@@ -449,46 +509,55 @@ void worker_loop() {
     // ---- progress every bucket independently
     for (auto it = s.buckets.begin(); it != s.buckets.end();) {
       Bucket& b = it->second;
-      if (b.busy) {
-        cudaError_t q = cudaEventQuery(b.ev);
-        if (q == cudaErrorNotReady) {
-          ++it;
-          continue;
-        }
-        b.busy = false;
+      // completed batches, oldest first
+      while (!b.inflight.empty()) {
+        Batch& bt = b.inflight.front();
+        cudaError_t q = cudaEventQuery(bt.ev);
+        if (q == cudaErrorNotReady) break;
         progressed = true;
         int err = q == cudaSuccess ? BPM_OK : BPM_ERR_CUDA;
-        if (*b.h_status) {
-          *b.h_status = 0;
-          cudaMemsetAsync(b.d_status, 0, sizeof(int), b.st);
+        if (*bt.h_status) {
+          *bt.h_status = 0;
           err = BPM_ERR_TIMEOUT;
         }
+        if (bt.err != BPM_OK) err = bt.err;
         std::vector<ReqPtr> done;
-        for (auto& rs : b.launched) {
-          rs.first->n_done += rs.second;
-          if (err != BPM_OK || rs.first->n_done >= rs.first->plan->nz) done.push_back(rs.first);
+        for (auto& rs : bt.items) {
+          Request& r = *rs.first;
+          r.n_done += rs.second;
+          if (err != BPM_OK && r.failed == BPM_OK) r.failed = err;
+          // retire once nothing of it is left on the stream
+          if (r.n_done == r.n_sched && (r.failed != BPM_OK || r.n_done >= r.plan->nz))
+            done.push_back(rs.first);
         }
-        b.launched.clear();
+        bt.items.clear();
+        b.free.push_back(std::move(bt));
+        b.inflight.pop_front();
         for (auto& r : done) {
           b.members.erase(std::remove(b.members.begin(), b.members.end(), r), b.members.end());
-          const int rc = err != BPM_OK ? err : retire_enqueue(s, *r);
-          if (rc == BPM_OK) s.retiring.push_back(r);
-          else finish_request(s, r, rc, "request failed on the device");
+          retire_or_fail(s, r);
         }
       }
-      if (!b.busy && !b.members.empty()) {
-        const int err = launch_epoch(s, it->first, b);
+      while (b.inflight.size() < kBatchesInFlight && has_unscheduled(b)) {
+        const int err = launch_batch(s, b);
         progressed = true;
         if (err != BPM_OK) {
-          auto members = b.members;
-          b.members.clear();
-          b.launched.clear();
-          b.busy = false;
-          for (auto& r : members) finish_request(s, r, err, "epoch launch failed");
+          // stop scheduling; members with batches in flight (the failed one
+          // included) retire, failed, when those complete
+          std::vector<ReqPtr> idle;
+          for (auto& r : b.members) {
+            if (r->failed == BPM_OK) r->failed = err;
+            if (r->n_done == r->n_sched) idle.push_back(r);
+          }
+          for (auto& r : idle) {
+            b.members.erase(std::remove(b.members.begin(), b.members.end(), r), b.members.end());
+            finish_request(s, r, err, "batch launch failed");
+          }
+          break;
         }
       }
-      if (!b.busy && b.members.empty() && it->first < 0) {
-        // keep the stream, event and buffers for the next request (freeing
+      if (b.inflight.empty() && b.members.empty() && it->first < 0) {
+        // keep the stream, events and buffers for the next request (freeing
         // them would synchronise the device)
         s.spare.push_back(std::move(b));
         it = s.buckets.erase(it);
