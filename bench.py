@@ -553,10 +553,14 @@ def run_gpu(args, rks):
         barrier()
         msb = max_over_ranks(ab.elapsed_time(bb)) / kb
         cells_b = wb.cell_updates
+        layout, chunk = binding.bpm_launch_shape(planb.handle)
         batched = {"workload": "pulse_batched: 256 energies 9 keV +- 5 eV, Laue 300 um, "
                                "bent R=2 m, Nx=4096, Nz=6000, + energy->time IDFT",
                    "value": world * cells_b / (msb * 1e-3), "unit": UNIT,
-                   "ms_per_march": msb}
+                   "ms_per_march": msb,
+                   "launch_shape": {"layout": {1: "cluster", 0: "cta", -1: "rule"}[layout],
+                                    "rotation_chunk": chunk,
+                                    "autotune": os.environ.get("BPM_AUTOTUNE", "1") != "0"}}
         planb.close()
 
     # ---- rocking curve: incidence angles as the rows of one batch ----------

@@ -271,6 +271,20 @@ int bpm_march_f64_noalloc(void* d_psi, int32_t nx, int32_t n_rows, const void* d
                           const void* d_coupling, const void* d_phasor, int32_t n_begin,
                           int32_t n_end, void* stream);
 
+/* Launch shape of the plan's last FP32 march (the fused kernels of the
+ * step of Eq. fov10): *layout = 1 one 2-CTA cluster per row, 0 one CTA per
+ * row, -1 chosen by the fixed rule (cluster while every row gets two SMs);
+ * *chunk = steps per launch of the rotation schedule (more rows than one
+ * launch keeps resident), 0 for a single launch.  A batch march with a
+ * choice of shapes (two layouts for up to one row per two SMs at
+ * 1024 <= nx <= 4096, or rotation chunks of 64..512 steps) times each on a
+ * short march of a scratch copy of the state the first time a given
+ * (nx, rows) is marched, blocking the host for those trials, and keeps the
+ * fastest for the process; BPM_AUTOTUNE=0 in the environment, a single row
+ * or a stream under graph capture leaves the fixed rule in charge.  Either
+ * pointer may be NULL.  BPM_ERR_INVALID for a NULL plan. */
+int bpm_launch_shape(bpm_plan_t plan, int32_t* layout, int32_t* chunk);
+
 /* Release the plan and its device memory.  BPM_ERR_BUSY while tickets of
  * the plan are pending. */
 int bpm_destroy(bpm_plan_t plan);

@@ -69,6 +69,7 @@ _SIGS = {
                           ctypes.POINTER(_D)], ctypes.c_int),
     "bpm_fetch_slices": ([_P, _P, _P], ctypes.c_int),
     "bpm_march_f64_noalloc": ([_P, _I, _I, _P, _P, _P, _I, _I, _P], ctypes.c_int),
+    "bpm_launch_shape": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I)], ctypes.c_int),
     "bpm_destroy": ([_P], ctypes.c_int),
     "bpm_last_error": ([], ctypes.c_char_p),
     "bpm_version": ([], ctypes.c_char_p),
@@ -200,6 +201,14 @@ def bpm_march_f64_noalloc(d_psi, nx, n_rows, d_prop, d_coupling, d_phasor, n_beg
     return _check(load().bpm_march_f64_noalloc(_ptr(d_psi), int(nx), int(n_rows), _ptr(d_prop),
                                                 _ptr(d_coupling), _ptr(d_phasor), int(n_begin),
                                                 int(n_end), stream))
+
+
+def bpm_launch_shape(plan) -> tuple[int, int]:
+    """(layout, chunk) of the plan's last FP32 march: layout 1 cluster per
+    row, 0 CTA per row, -1 the fixed rule; chunk 0 for one launch."""
+    layout, chunk = _I(0), _I(0)
+    _check(load().bpm_launch_shape(plan, ctypes.byref(layout), ctypes.byref(chunk)))
+    return layout.value, chunk.value
 
 
 def bpm_destroy(plan):

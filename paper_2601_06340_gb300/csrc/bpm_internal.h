@@ -108,6 +108,9 @@ struct bpm_plan_s {
   void* d_stage_prop = nullptr;      // double2 [tables][B][2][nx]
   size_t device_bytes = 0;
   int pending = 0;                // tickets not yet finished
+  // launch shape of the last fused march: layout 1 cluster / 0 CTA / -1 rule,
+  // rotation chunk (0: one launch)
+  int shape_layout = -1, shape_chunk = 0;
 };
 
 namespace bpm {

@@ -2,8 +2,11 @@
 // stream-ordered marches.  See include/bpm.h for the contract.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -134,9 +137,10 @@ void phase_factors(const bpm_plan_s* plan, int steps, std::vector<double2>* out)
 // their strain slices in L2.  A remainder shorter than a chunk runs as a
 // second round of the same kind.
 static int launch_rotated(bpm_plan_s* plan, PlanAux* aux, const std::vector<RowDescF32>& rows,
-                          int n_begin, int steps, int resident, cudaStream_t st) {
+                          int n_begin, int steps, int resident, cudaStream_t st, int chunk = 0) {
   const int nb = plan->nb;
-  const int chunk = std::max(std::min(steps, 64), steps / 24);
+  if (chunk <= 0) chunk = std::max(std::min(steps, 64), steps / 24);
+  chunk = std::min(chunk, steps);
   const int full = steps / chunk, rem = steps - full * chunk;
   std::vector<RowDescF32> sched;
   struct Launch { size_t off; int count; int steps; };
@@ -177,6 +181,141 @@ static int launch_rotated(bpm_plan_s* plan, PlanAux* aux, const std::vector<RowD
   return BPM_OK;
 }
 
+// ---- launch-shape autotuning ---------------------------------------------
+// A batch march of N <= 4096 can run in more than one launch shape with the
+// same per-row arithmetic: while every row can have two SMs, one 2-CTA
+// cluster per row or one CTA per row; with more rows than one CTA-per-row
+// launch keeps resident, the rotation's chunk length (64..512 steps).  The
+// first march of a shape (N, rows) times each candidate on a short march of
+// a scratch copy of the state on the march's stream (CUDA events, best of
+// two) and keeps the fastest in a process-wide table that later marches of
+// the shape reuse.  Layout candidates differ in kernel (results agree within
+// the FP32 tolerance); chunk candidates give identical bits.  No search runs
+// while the stream is being captured into a graph, for single rows (the
+// cluster is the latency choice) or when BPM_AUTOTUNE=0: the fixed rule
+// decides.
+struct LaunchShape {
+  int layout = -1;   // 1: cluster per row, 0: CTA per row, -1: the rule
+  int chunk = 0;     // rotation chunk (CTA layout, more rows than resident)
+  bool rotated = false;
+};
+
+static std::mutex g_tune_mu;
+static std::map<std::pair<int, int>, LaunchShape> g_tune;   // (logn, rows) -> shape
+
+static bool autotune_enabled() {
+  const char* v = std::getenv("BPM_AUTOTUNE");
+  return !(v && v[0] == '0');
+}
+
+// Milliseconds of one trial march (best of two), or a large value on error.
+static double time_trial(bpm_plan_s* plan, PlanAux* aux, const LaunchShape& sh, void* scratch,
+                         int n_begin, int steps, cudaStream_t st) {
+  std::vector<RowDescF32> rows;
+  fused_rows(plan, static_cast<float2*>(scratch), nullptr, nullptr, n_begin, n_begin + steps,
+             &rows);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 1e30;
+  for (int rep = 0; rep < 2; ++rep) {
+    cudaEventRecord(e0, st);
+    int rc;
+    if (sh.rotated) {
+      rc = launch_rotated(plan, aux, rows, n_begin, steps, fused_launch_capacity(plan->logn, false),
+                          st, sh.chunk);
+    } else {
+      cudaMemcpyAsync(plan->d_rows, rows.data(), sizeof(RowDescF32) * rows.size(),
+                      cudaMemcpyHostToDevice, st);
+      rc = launch_fused_layout(plan->logn, static_cast<const RowDescF32*>(plan->d_rows), plan->nb,
+                               steps, static_cast<const float4*>(plan->d_tw), plan->d_status, st,
+                               sh.layout);
+    }
+    cudaEventRecord(e1, st);
+    if (rc != BPM_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+      cudaGetLastError();
+      best = 1e30;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    best = std::min(best, double(ms));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
+static LaunchShape choose_shape(bpm_plan_s* plan, PlanAux* aux, const void* state, int n_begin,
+                                int steps, cudaStream_t st) {
+  LaunchShape rule;
+  const int nb = plan->nb, logn = plan->logn;
+  const int resident = fused_rows_resident(logn, nb);   // 0 when the rule picks clusters
+  rule.rotated = resident > 0 && nb > resident;
+  if (logn >= kSplitLogN || nb < 2 || !autotune_enabled()) return rule;
+  int sms = 1, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // candidates, the rule's own shape first
+  std::vector<LaunchShape> cands;
+  const int cta_cap = fused_launch_capacity(logn, false);
+  if (logn >= 10 && 2 * nb <= sms) {
+    LaunchShape c;
+    c.layout = 1;
+    cands.push_back(c);
+    c.layout = 0;
+    cands.push_back(c);   // nb <= sms / 2 rows always fit one CTA-per-row launch
+  } else if (nb > cta_cap) {
+    const int rule_chunk = std::max(std::min(steps, 64), steps / 24);
+    for (int ch : {rule_chunk, 64, 128, 256, 512}) {
+      if (ch != rule_chunk && (ch == cands.front().chunk || ch >= 2 * steps)) continue;
+      LaunchShape c;
+      c.layout = 0;
+      c.rotated = true;
+      c.chunk = ch;
+      cands.push_back(c);
+    }
+  }
+  if (cands.size() < 2) return rule;
+  const std::pair<int, int> key(logn, nb);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return rule;
+  }
+  // trial length: a few chunks for the rotation, a short march for the layout
+  const int trial = std::min(steps, cands.front().rotated ? 1024 : 128);
+  const size_t bytes = size_t(nb) * 2 * plan->nx * sizeof(float2);
+  void* scratch = nullptr;
+  if (cudaMallocAsync(&scratch, bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    return rule;
+  }
+  cudaMemcpyAsync(scratch, state, bytes, cudaMemcpyDeviceToDevice, st);
+  // another shape replaces the rule's only if it is at least 2% faster
+  // (run-to-run noise of the trials is below 1%)
+  LaunchShape best = cands.front();
+  const double rule_ms = time_trial(plan, aux, cands.front(), scratch, n_begin, trial, st);
+  double best_ms = rule_ms;
+  for (size_t i = 1; i < cands.size(); ++i) {
+    const double ms = time_trial(plan, aux, cands[i], scratch, n_begin, trial, st);
+    if (ms < best_ms && ms < 0.98 * rule_ms) {
+      best_ms = ms;
+      best = cands[i];
+    }
+  }
+  cudaFreeAsync(scratch, st);
+  if (rule_ms >= 1e30) return rule;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = best;
+  return best;
+}
+
 // Enqueue the march of all rows on `st`.  state: the buffer holding the
 // state at n_begin (c64 for FP32, the plan's d_state for FP64); outputs as
 // documented for bpm_propagate_device.
@@ -205,16 +344,23 @@ static int enqueue_march(bpm_plan_s* plan, PlanAux* aux, void* state, void* d_re
     std::vector<RowDescF32> rows;
     fused_rows(plan, static_cast<float2*>(state), static_cast<float2*>(d_rec), d_pw, n_begin,
                n_end, &rows);
-    const int resident = fused_rows_resident(plan->logn, plan->nb);
+    const LaunchShape sh = choose_shape(plan, aux, state, n_begin, steps, st);
+    plan->shape_layout = sh.layout;
+    plan->shape_chunk =
+        sh.rotated ? std::min(steps, sh.chunk > 0 ? sh.chunk
+                                                  : std::max(std::min(steps, 64), steps / 24))
+                   : 0;
     int rc = BPM_OK;
-    if (resident <= 0 || plan->nb <= resident) {
+    if (!sh.rotated) {
       e = cudaMemcpyAsync(plan->d_rows, rows.data(), sizeof(RowDescF32) * rows.size(),
                           cudaMemcpyHostToDevice, st);
       if (e != cudaSuccess) return cuda_fail(e, "upload row descriptors");
-      rc = launch_fused(plan->logn, static_cast<const RowDescF32*>(plan->d_rows), plan->nb,
-                        steps, static_cast<const float4*>(plan->d_tw), plan->d_status, st);
+      rc = launch_fused_layout(plan->logn, static_cast<const RowDescF32*>(plan->d_rows), plan->nb,
+                               steps, static_cast<const float4*>(plan->d_tw), plan->d_status, st,
+                               sh.layout);
     } else {
-      rc = launch_rotated(plan, aux, rows, n_begin, steps, resident, st);
+      rc = launch_rotated(plan, aux, rows, n_begin, steps, fused_launch_capacity(plan->logn, false),
+                          st, sh.chunk);
     }
     if (rc != BPM_OK) return rc;
     return launch_finish_f32(static_cast<const float2*>(state),
@@ -710,6 +856,14 @@ int bpm_fetch_slices(bpm_plan_t plan, uint8_t* mask, double* phasor) {
       phasor[2 * c + 1] = buf[2 * src + 1];
     }
   }
+  return BPM_OK;
+}
+
+int bpm_launch_shape(bpm_plan_t plan, int32_t* layout, int32_t* chunk) {
+  if (!plan) return fail(BPM_ERR_INVALID, "plan is NULL");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  if (layout) *layout = plan->shape_layout;
+  if (chunk) *chunk = plan->shape_chunk;
   return BPM_OK;
 }
 
