@@ -42,10 +42,18 @@ WORKLOAD = ("bragg_bent: 2D symmetric Bragg, bent crystal R=1 m nu=0.28, 8 keV, 
             "theta_B=23.65 deg, 200 um slab, Nx=4096, Nz=8000, dx=0.2 um, dz=0.1 um, "
             "one energy, Gaussian 50 um FWHM")
 FLOPS_PER_CELL = lambda n: 4 * 5 * math.log2(n)      # 4 FFTs x 5 N log2 N / N
+# the single-solve march kernel by launch layout (bpm_launch_shape): name, SMs
+MARCH_KERNELS = {
+    2: ("fused4e_march_kernel<11> (4-CTA cluster per solve: two half-band parts per band)", 4),
+    1: ("fused3_march_kernel<12> (2-CTA cluster per solve, one band per CTA)", 2),
+    -1: ("fused3_march_kernel<12> (2-CTA cluster per solve, one band per CTA)", 2),
+}
+
 KERNEL_SOURCES = ["paper_2601_06340_gb300/csrc/radix.cuh",
                   "paper_2601_06340_gb300/csrc/fused_kernel.cuh",
                   "paper_2601_06340_gb300/csrc/fused2_kernel.cuh",
-                  "paper_2601_06340_gb300/csrc/fused3_kernel.cuh"]
+                  "paper_2601_06340_gb300/csrc/fused3_kernel.cuh",
+                  "paper_2601_06340_gb300/csrc/fused4_kernel.cuh"]
 
 
 def kernel_hash() -> str:
@@ -468,6 +476,7 @@ def run_gpu(args, rks):
     per_ms = [a.elapsed_time(b) for a, b in ev]
     value = world * args.steps * cells / (total_ms * 1e-3)
     clocks = clk.summary()
+    march_layout, _ = binding.bpm_launch_shape(plan32.handle)
 
     if args.only == "fused":
         if rank == 0:
@@ -558,7 +567,7 @@ def run_gpu(args, rks):
                                "bent R=2 m, Nx=4096, Nz=6000, + energy->time IDFT",
                    "value": world * cells_b / (msb * 1e-3), "unit": UNIT,
                    "ms_per_march": msb,
-                   "launch_shape": {"layout": {1: "cluster", 0: "cta", -1: "rule"}[layout],
+                   "launch_shape": {"layout": {2: "split4", 1: "cluster", 0: "cta", -1: "rule"}[layout],
                                     "rotation_chunk": chunk,
                                     "autotune": os.environ.get("BPM_AUTOTUNE", "1") != "0"}}
         planb.close()
@@ -603,12 +612,11 @@ def run_gpu(args, rks):
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops,
                 "traffic": profiled_traffic("fused_march_bragg_bent.md"),
-                "kernel": "fused3_march_kernel<12> (2-CTA cluster per solve, one band per CTA)",
+                "kernel": MARCH_KERNELS[march_layout][0],
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
-                # the solve occupies one 2-CTA cluster: the fraction of those
-                # two SMs' peak
-                "cluster_sms": 2,
-                "cluster_frac": achieved / (2 * peak_tflops / sms),
+                # the solve occupies one cluster: the fraction of its SMs' peak
+                "cluster_sms": MARCH_KERNELS[march_layout][1],
+                "cluster_frac": achieved / (MARCH_KERNELS[march_layout][1] * peak_tflops / sms),
                 "flops_per_cell_update": FLOPS_PER_CELL(wl.nx)}
     if batched is not None:
         ach_b = batched["value"] / world * FLOPS_PER_CELL(4096) / 1e12

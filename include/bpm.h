@@ -272,11 +272,13 @@ int bpm_march_f64_noalloc(void* d_psi, int32_t nx, int32_t n_rows, const void* d
                           int32_t n_end, void* stream);
 
 /* Launch shape of the plan's last FP32 march (the fused kernels of the
- * step of Eq. fov10): *layout = 1 one 2-CTA cluster per row, 0 one CTA per
- * row, -1 chosen by the fixed rule (cluster while every row gets two SMs);
+ * step of Eq. fov10): *layout = 2 one 4-CTA cluster per row (nx = 4096 as
+ * two half-band parts per band; the rule while every row gets four SMs),
+ * 1 one 2-CTA cluster per row, 0 one CTA per row, -1 chosen by the fixed
+ * rule (2-CTA cluster while every row gets two SMs, else one CTA per row);
  * *chunk = steps per launch of the rotation schedule (more rows than one
  * launch keeps resident), 0 for a single launch.  A batch march with a
- * choice of shapes (two layouts for up to one row per two SMs at
+ * choice of shapes (the layouts above for up to one row per two SMs at
  * 1024 <= nx <= 4096, or rotation chunks of 64..512 steps) times each on a
  * short march of a scratch copy of the state the first time a given
  * (nx, rows) is marched, blocking the host for those trials, and keeps the

@@ -204,8 +204,9 @@ def bpm_march_f64_noalloc(d_psi, nx, n_rows, d_prop, d_coupling, d_phasor, n_beg
 
 
 def bpm_launch_shape(plan) -> tuple[int, int]:
-    """(layout, chunk) of the plan's last FP32 march: layout 1 cluster per
-    row, 0 CTA per row, -1 the fixed rule; chunk 0 for one launch."""
+    """(layout, chunk) of the plan's last FP32 march: layout 2 four-CTA
+    cluster per row (N = 4096 half-band split), 1 two-CTA cluster per row,
+    0 CTA per row, -1 the fixed rule; chunk 0 for one launch."""
     layout, chunk = _I(0), _I(0)
     _check(load().bpm_launch_shape(plan, ctypes.byref(layout), ctypes.byref(chunk)))
     return layout.value, chunk.value

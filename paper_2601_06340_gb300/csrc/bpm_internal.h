@@ -32,6 +32,8 @@ enum : int { kStatusWaitTimeout = 1 };
 struct RowDescF32 {
   float2* state;            // [2][N] raw envelopes (common phase removed)
   const float2* prop;       // [2][N] (P(q)-1)/N in the FFT's output order
+  const float2* prop_split; // N = 4096 rows on a 4-CTA cluster: [2][3][N/2] circulant
+                            // tables of the half-band split, else null
   const float2* phasor;     // [nz][N] exp(i h u_x), (0,0) outside the crystal
   float2* records;          // [n_rec][2][N] or null
   double* powers;           // [n_rec+1][2] or null
@@ -89,6 +91,7 @@ struct bpm_plan_s {
   int device = 0;
   void* d_phasor = nullptr;       // [nz][nx] c64 (FP32) or c128 (FP64)
   void* d_prop = nullptr;         // [B][2][nx] c64 (delta form) or c128
+  void* d_prop_split = nullptr;   // [B][2][3][nx/2] c64: N = 4096 half-band split tables
   void* d_tw = nullptr;           // FP32: float4 [nx] hi/lo; FP64: double2 [nx]
   void* d_state = nullptr;        // [B][2][nx] c64 / c128
   void* d_state2 = nullptr;       // FP64 ping-pong buffer
@@ -176,6 +179,12 @@ int launch_omega_to_t(const void* d_in, void* d_out, int nb, int nx,
                       int precision, cudaStream_t st);
 int fused_smem_bytes(int logn);
 int fused_rows_resident(int logn, int n_rows);
+// Tables of the split-band form with local length 2^logm (N = 2^logm P).
+void split_prop_table(const bpm_plan_s* plan, int row, int logm, std::vector<float2>* out);
+int split_table_stride(const bpm_plan_s* plan, int logm);   // float2 per row
+// Layout codes of launch_fused_layout: -1 rule, 0 CTA per row, 1 2-CTA
+// cluster per row, 2 4-CTA cluster per row (N = 4096, half-band split).
+constexpr int kLayoutSplit4 = 2;
 int fused_launch_capacity(int logn, bool cluster);
 int fused_rows_per_cta(int logn);
 int fused_threads(int logn);

@@ -48,7 +48,7 @@ int dev_alloc(bpm_plan_s* plan, void** p, size_t bytes, const char* what) {
 
 void free_plan_memory(bpm_plan_s* plan) {
   vol_release(plan);
-  void** ptrs[] = {&plan->d_phasor, &plan->d_prop, &plan->d_tw, &plan->d_state,
+  void** ptrs[] = {&plan->d_phasor, &plan->d_prop, &plan->d_prop_split, &plan->d_tw, &plan->d_state,
                    &plan->d_state2, &plan->d_rows, &plan->d_io, &plan->d_spec,
                    &plan->d_twy, reinterpret_cast<void**>(&plan->d_pwpart),
                    &plan->d_stage_rows, &plan->d_stage_prop};
@@ -61,6 +61,21 @@ void free_plan_memory(bpm_plan_s* plan) {
 }
 
 size_t csize(const bpm_plan_s* plan) { return plan->precision == BPM_FP32_FUSED ? 8 : 16; }
+
+// float2 per row of the fused propagator tables (the split form of
+// N = 8192 carries a third table per band)
+size_t prop_stride(const bpm_plan_s* plan) {
+  if (plan->precision == BPM_FP32_FUSED && plan->ny <= 1 && plan->logn >= kSplitLogN)
+    return size_t(split_table_stride(plan, 12));
+  return 2 * size_t(plan->nx) * (plan->ny > 1 ? plan->ny : 1);
+}
+
+int device_sm_count() {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
 
 }  // namespace
 
@@ -104,7 +119,10 @@ void fused_rows(bpm_plan_s* plan, float2* state, float2* rec, double* pw, int n_
   for (int r = 0; r < plan->nb; ++r) {
     RowDescF32& d = (*out)[r];
     d.state = state + size_t(r) * 2 * n;
-    d.prop = static_cast<const float2*>(plan->d_prop) + size_t(r) * 2 * n;
+    d.prop = static_cast<const float2*>(plan->d_prop) + size_t(r) * prop_stride(plan);
+    d.prop_split = plan->d_prop_split ? static_cast<const float2*>(plan->d_prop_split) +
+                                            size_t(r) * split_table_stride(plan, 11)
+                                      : nullptr;
     d.phasor = static_cast<const float2*>(plan->d_phasor);
     d.records = rec ? rec + size_t(r) * plan->n_rec * 2 * n : nullptr;
     d.powers = pw ? pw + size_t(r) * (plan->n_rec + 1) * 2 : nullptr;
@@ -252,6 +270,16 @@ static LaunchShape choose_shape(bpm_plan_s* plan, PlanAux* aux, const void* stat
   const int nb = plan->nb, logn = plan->logn;
   const int resident = fused_rows_resident(logn, nb);   // 0 when the rule picks clusters
   rule.rotated = resident > 0 && nb > resident;
+  // N = 4096 rows that each get four SMs march fastest as half-band splits
+  // (their tables exist exactly then)
+  const bool split_ok = logn == 12 && plan->d_prop_split != nullptr;
+  const char* fv = std::getenv("BPM_FUSED_LAYOUT");
+  if (fv && (std::strcmp(fv, "cluster") == 0 || std::strcmp(fv, "cta") == 0)) return rule;
+  if (split_ok) {
+    rule.layout = kLayoutSplit4;
+    rule.rotated = false;
+    if (fv && std::strcmp(fv, "split") == 0) return rule;
+  }
   if (logn >= kSplitLogN || nb < 2 || !autotune_enabled()) return rule;
   int sms = 1, dev = 0;
   cudaGetDevice(&dev);
@@ -261,6 +289,10 @@ static LaunchShape choose_shape(bpm_plan_s* plan, PlanAux* aux, const void* stat
   const int cta_cap = fused_launch_capacity(logn, false);
   if (logn >= 10 && 2 * nb <= sms) {
     LaunchShape c;
+    if (split_ok) {
+      c.layout = kLayoutSplit4;
+      cands.push_back(c);
+    }
     c.layout = 1;
     cands.push_back(c);
     c.layout = 0;
@@ -428,7 +460,13 @@ static int make_plan(const bpm_problem* p, int ny, double dy_um, double y0_um,
   auto A = [&](void** ptr, size_t bytes, const char* what) {
     if (rc == BPM_OK) rc = dev_alloc(pl, ptr, bytes, what);
   };
-  A(&pl->d_prop, nb * 2 * n * cs, "propagator tables");
+  A(&pl->d_prop, nb * std::max(prop_stride(pl) * cs, 2 * n * cs), "propagator tables");
+  // N = 4096 rows can also march as half-band splits on 4-CTA clusters
+  // while every row gets four SMs: their tables too
+  const bool half_split = !vol && pl->precision == BPM_FP32_FUSED && pl->logn == 12 &&
+                          4 * int(nb) <= device_sm_count();
+  if (half_split)
+    A(&pl->d_prop_split, nb * size_t(split_table_stride(pl, 11)) * cs, "split propagator tables");
   A(&pl->d_tw, size_t(pl->nx) * 16, "twiddles");
   if (vol) {
     A(&pl->d_twy, size_t(pl->ny) * 16, "twiddles along y");
@@ -483,8 +521,14 @@ static int make_plan(const bpm_problem* p, int ny, double dy_um, double y0_um,
       for (int r = 0; r < pl->nb && e == cudaSuccess; ++r) {
         std::vector<float2> t;
         fused_prop_table(pl, r, &t);
-        e = cudaMemcpyAsync(static_cast<float2*>(pl->d_prop) + size_t(r) * 2 * n, t.data(),
-                            t.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(static_cast<float2*>(pl->d_prop) + size_t(r) * prop_stride(pl),
+                            t.data(), t.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && pl->d_prop_split) {
+          split_prop_table(pl, r, 11, &t);
+          e = cudaMemcpyAsync(static_cast<float2*>(pl->d_prop_split) +
+                                  size_t(r) * split_table_stride(pl, 11),
+                              t.data(), t.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
+        }
       }
     } else {
       std::vector<double2> tw;

@@ -20,6 +20,7 @@ BPM_DECLARE_FUSED(6) BPM_DECLARE_FUSED(7) BPM_DECLARE_FUSED2(8)
 BPM_DECLARE_FUSED2(9) BPM_DECLARE_FUSED2(10) BPM_DECLARE_FUSED2(11)
 BPM_DECLARE_FUSED2(12)
 int fused4_launch_13(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
+int fused4h_launch_12(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
 int fused4_launch_14(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
 #define BPM_DECLARE_FUSED3(L)                                                    \
   int fused3_launch_##L(const RowDescF32*, int, int, const float4*, int*,        \
@@ -34,17 +35,22 @@ int fused2_rows_resident_12();
 
 // Layout choice: a 2-CTA cluster per row (a whole SM per band) when every
 // row of the launch gets its own pair of SMs, else one CTA per row.  The
-// environment variable BPM_FUSED_LAYOUT=cta|cluster forces one of them.
+// environment variable BPM_FUSED_LAYOUT=cta|cluster forces one of them
+// (read at every launch).
 static int sm_count();
+
+static int forced_layout() {
+  const char* v = std::getenv("BPM_FUSED_LAYOUT");
+  if (!v) return -1;
+  if (std::strcmp(v, "cluster") == 0) return 1;
+  if (std::strcmp(v, "cta") == 0) return 0;
+  return -1;
+}
 
 static bool use_cluster_layout(int logn, int n_rows) {
   if (logn < 10 || logn > 12) return false;
-  static int forced = -2;
-  if (forced == -2) {
-    const char* v = std::getenv("BPM_FUSED_LAYOUT");
-    forced = !v ? -1 : (std::strcmp(v, "cluster") == 0 ? 1 : (std::strcmp(v, "cta") == 0 ? 0 : -1));
-  }
-  if (forced >= 0) return forced == 1;
+  const int forced = forced_layout();
+  if (forced == 0 || forced == 1) return forced == 1;
   return 2 * n_rows <= sm_count();
 }
 
@@ -61,6 +67,9 @@ int fused_cluster_sms(int logn) {
 int launch_fused_layout(int logn, const RowDescF32* d_rows, int n_rows, int steps,
                         const float4* d_tw, int* d_status, cudaStream_t st, int layout) {
   if (n_rows <= 0 || steps <= 0) return BPM_OK;
+  // (only for rows that carry the split tables: the caller checks)
+  if (logn == 12 && layout == kLayoutSplit4)
+    return fused4h_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
   const bool cluster = logn >= 10 && logn <= 12 &&
                        (layout == 1 || (layout < 0 && use_cluster_layout(logn, n_rows)));
   if (cluster) {
@@ -120,7 +129,7 @@ static void fused_cfg(int logn, int* smem, int* rows, int* threads) {
     case 10: cfg2_of<10>(smem, rows, threads); break;
     case 11: cfg2_of<11>(smem, rows, threads); break;
     case 12: cfg2_of<12>(smem, rows, threads); break;
-    case 13: cfg4_of<F4ECfg>(smem, rows, threads); break;
+    case 13: cfg4_of<F4ECfg<12>>(smem, rows, threads); break;
     default: cfg4_of<F4TCfg>(smem, rows, threads); break;
   }
 }

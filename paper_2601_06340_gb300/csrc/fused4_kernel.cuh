@@ -1,7 +1,8 @@
-// Split-band fused FP32 marches for N = 4096 P (P = 2 here, P = 4 in
-// fused4t_kernel.cuh): one row per cluster of 2P CTAs, CTA rank c = b P + h
-// advances band b on the samples x[P m + h] (m < 4096), i.e. one of the P
-// interleaved sub-sequences of its band.
+// Split-band fused FP32 marches for N = M P (P = 2 here with M = 4096 or
+// 2048, P = 4 in fused4t_kernel.cuh with M = 4096): one row per cluster of
+// 2P CTAs, CTA rank c = b P + h advances band b on the samples x[P m + h]
+// (m < M), i.e. one of the P interleaved sub-sequences of its band.  The
+// formulas below are written for M = 4096; they hold for any M.
 //
 // The length-N transform is split as N = 4096 x P (decimation in time over
 // the P sub-sequences):
@@ -25,34 +26,43 @@
 
 namespace bpm {
 
-// N = 8192 (P = 2) with one spectral exchange per step.
+// P = 2 with one spectral exchange per step.
 //
 // For P = 2 the forward combine, the propagator increment and the inverse
-// combine above collapse, per local frequency k, into a 2x2
-// circulant over the band's two halves:
-//   H_h[k] = W_N^{-h k} (E_0[k] G_h[k] + E_1[k] G_{1-h}[k]),
-//   E_0[k] = D[k] + D[k + 4096],   E_1[k] = D[k] - D[k + 4096],
-// with G_h = W_N^{h k} F_h as before (E_0, E_1 are tabulated in FP64 and
-// rounded once).  So each CTA only needs its peer's G: one exchange of 32 KB
-// per CTA instead of two all-to-all rounds.  Both exchanges of the step (G
-// within the band, psi_p across the bands) are asynchronous remote stores
-// that complete on the receiver's mbarrier (see fused3_kernel.cuh), double
+// combine above reduce, per local frequency k, to
+//   X_r = F_0 + (-1)^r W_N^k F_1,   Y_r = D(k + M r) X_r        (r = 0, 1)
+//   H_0 = Y_0 + Y_1,                H_1 = W_N^{-k} (Y_0 - Y_1)
+// so each CTA only needs its peer's local spectrum F: one exchange of M
+// values per CTA instead of two all-to-all rounds.  D(k) and D(k + M) are
+// tabulated in FP64 and rounded once each, relative to themselves.  (The
+// circulant form E_0 F_h + E_1 W^{+-k} F_{1-h}, E_{0,1} = D(k) +- D(k + M),
+// saves the twiddles but rounds a small D(k) relative to the large
+// D(k + M) it is paired with; repeated every step, that pushed 20000-step
+// marches past the FP32 tolerance.)  Both exchanges of the step (F within
+// the band, psi_p across the bands) are asynchronous remote stores that
+// complete on the receiver's mbarrier (see fused3_kernel.cuh), double
 // buffered by step parity; no cluster-wide barrier runs inside the march.
-// Buffer reuse: a half is rewritten two steps later, by a sender that has by
-// then received values the receiver computed from that half.
+// Buffer reuse: a half is rewritten two steps later, by a sender that has
+// by then received values the receiver computed from that half.
+template <int LM>
 struct F4ECfg {
-  static constexpr int M = 4096;
+  static constexpr int M = 1 << LM;
   static constexpr int N = 2 * M;
   static constexpr int T = M / 16;
+  // N = 8192 stores the strain slice per part (this CTA's samples
+  // contiguous); N = 4096 keeps the natural order of the other kernels of
+  // that size, so the CTA takes the whole slice and reads every second cell
+  static constexpr bool NAT = LM < 12;
+  static constexpr int PH = NAT ? N : M;
   static constexpr int PADM = M + (M >> 4);
   static constexpr int WARPS = T / 32;
   static constexpr int OFF_BUF = 0;                        // [PADM]
-  static constexpr int OFF_G = OFF_BUF + PADM * 8;         // [2][M] peer's G
+  static constexpr int OFF_G = OFF_BUF + PADM * 8;         // [2][M] peer's F
   static constexpr int OFF_C = OFF_G + 2 * M * 8;          // [2][M] other band's psi_p
-  static constexpr int OFF_PH = OFF_C + 2 * M * 8;         // [M] strain slice
-  static constexpr int OFF_E1 = OFF_PH + M * 8;            // [16][T] E_1 at this thread's k_j
+  static constexpr int OFF_PH = OFF_C + 2 * M * 8;         // [PH] strain slice
+  static constexpr int OFF_E1 = OFF_PH + PH * 8;           // [16][T] D(k_j + M)
   static constexpr int OFF_MBAR = OFF_E1 + M * 8;          // strain-slice barrier
-  static constexpr int OFF_GBAR = OFF_MBAR + 8;            // [2] G barriers
+  static constexpr int OFF_GBAR = OFF_MBAR + 8;            // [2] F barriers
   static constexpr int OFF_CBAR = OFF_GBAR + 16;           // [2] psi_p barriers
   static constexpr int OFF_PPEER = OFF_CBAR + 16;          // [2] peer's band-power part
   static constexpr int OFF_RECPH = OFF_PPEER + 16;
@@ -60,7 +70,25 @@ struct F4ECfg {
   static constexpr int OFF_PART = OFF_RED + WARPS * 8;
   static constexpr int SMEM = OFF_PART + 8;
   static_assert(SMEM <= 232448, "fits one SM");
+  static_assert(LM == 11 || LM == 12, "N = 4096 or 8192");
 };
+
+// Spectral index of position `pos` of the local forward transform's output
+// (digit-reversed over the pass radices 16, ..., 16, RL).
+template <int LM>
+__device__ __forceinline__ int local_freq(int pos) {
+  using F = F2Cfg<LM>;
+  int rem = pos, len = F::N, freq = 0, mult = 1;
+#pragma unroll
+  for (int p = 0; p < F::NP; ++p) {
+    const int r = F::radix(p), stride = len / r;
+    freq += (rem / stride) * mult;
+    rem %= stride;
+    mult *= r;
+    len = stride;
+  }
+  return freq;
+}
 
 __device__ __forceinline__ void st_async_f64(uint32_t raddr, double v, uint32_t rbar) {
   asm volatile(
@@ -69,14 +97,14 @@ __device__ __forceinline__ void st_async_f64(uint32_t raddr, double v, uint32_t 
       : "memory");
 }
 
-template <bool EX>
-__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg::T, 1)
+template <int LM, bool EX>
+__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
     fused4e_march_kernel(const RowDescF32* __restrict__ rows, int n_rows, int steps,
                          const float4* __restrict__ tw, int* __restrict__ status) {
   namespace cg = cooperative_groups;
-  using C = F4ECfg;
-  using F = F2Cfg<12>;
-  constexpr int L = 12, M = C::M, N = C::N, T = C::T, NP = F::NP;
+  using C = F4ECfg<LM>;
+  using F = F2Cfg<LM>;
+  constexpr int L = LM, M = C::M, N = C::N, T = C::T, NP = F::NP;
   extern __shared__ __align__(128) unsigned char smem[];
   cg::cluster_group cluster = cg::this_cluster();
 
@@ -125,17 +153,17 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg::T, 1)
     const float4 bq = __ldg(&tw[2 * (((t % F::stride(1)) * j) << 4)]);
     w1[j - 1] = make_float2(bq.x, bq.y);
   }
-  // Last-pass slice: combine twiddle W_N^{h k_j}, E_0 in registers, E_1 in
-  // shared memory (table [band][E_0 | E_1][position]).
-  float2 cw[16], e0[16];
+  // Last-pass slice: W_N^{k_j} and D(k_j) in registers, D(k_j + M) in
+  // shared memory (table [band][D(k) | D(k + M)][position]).
+  const float2* dtab = C::NAT ? d.prop_split : d.prop;
+  float2 cw[16], d0[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
-    const int pos = f2_pos<L, NP - 1>(t, j);
-    const int k = (pos >> 8) + ((pos >> 4) & 15) * 16 + (pos & 15) * 256;
-    const float4 a = __ldg(&tw[h * k]);
+    const int pos = f2_pos<L, NP - 1>(t + (j / F::radix(NP - 1)) * T, j % F::radix(NP - 1));
+    const float4 a = __ldg(&tw[local_freq<L>(pos)]);
     cw[j] = make_float2(a.x, a.y);
-    e0[j] = __ldg(&d.prop[(band * 2 + 0) * M + pos]);
-    e1s[j * T + t] = __ldg(&d.prop[(band * 2 + 1) * M + pos]);
+    d0[j] = __ldg(&dtab[(band * 2 + 0) * M + pos]);
+    e1s[j * T + t] = __ldg(&dtab[(band * 2 + 1) * M + pos]);
   }
 
   float2 v[16];
@@ -143,7 +171,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg::T, 1)
   for (int j = 0; j < 16; ++j) v[j] = d.state[band * N + 2 * (t + j * T) + h];
   cluster.sync();   // every CTA's barriers initialised before any remote store
 
-  const uint32_t slice_bytes = uint32_t(M) * 8u;
+  const uint32_t slice_bytes = uint32_t(C::PH) * 8u;
   bool timed_out = false;
   double my_part = 0.0;
   const float2 am1 = d.am1, bb = d.b;
@@ -170,7 +198,8 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg::T, 1)
     f2_store<L, 0>(buf, v, t);
     __syncthreads();
     if (lead) {
-      bulk_load(ph, d.phasor + size_t(n) * N + size_t(h) * M, slice_bytes, bar);
+      bulk_load(ph, d.phasor + size_t(n) * N + (C::NAT ? size_t(0) : size_t(h) * M), slice_bytes,
+                bar);
       mbar_expect_tx(&gbar[half], uint32_t(M) * 8u + (part_due ? 8u : 0u));
       if (part_due) {
         double s = 0.0;
@@ -185,12 +214,10 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg::T, 1)
     f2_store<L, 1>(buf, v, t);
     __syncthreads();
     f2_load<L, NP - 1>(buf, v, t);
-    dft<16, false, EX>(v);                       // v[j] = F_h[k_j]
+    f2_dft<L, NP - 1, false, EX>(v);             // v[j] = F_h[k_j]
     {
       const uint32_t go = g_peer + uint32_t(half * M) * 8u;
       const uint32_t gbo = gbar_peer + uint32_t(half) * 8u;
-#pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = cmul_f(v[j], cw[j].x, cw[j].y);   // G_h[k_j]
 #pragma unroll
       for (int pp = 0; pp < 8; ++pp)
         st_async_v4(go + uint32_t(xpair(pp, t, T)) * 8u, v[2 * pp], v[2 * pp + 1], gbo);
@@ -206,17 +233,16 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg::T, 1)
       for (int j = 0; j < 16; ++j) {
         const float4 g2 = *reinterpret_cast<const float4*>(gi + xpair(j >> 1, t, T));
         const float2 gp = (j & 1) ? make_float2(g2.z, g2.w) : make_float2(g2.x, g2.y);
-        const float2 e1 = e1s[j * T + t], a = e0[j], g = v[j];
-        float sx = fmaf(a.x, g.x, -(a.y * g.y));
-        float sy = fmaf(a.x, g.y, a.y * g.x);
-        sx = fmaf(e1.x, gp.x, sx);
-        sx = fmaf(-e1.y, gp.y, sx);
-        sy = fmaf(e1.x, gp.y, sy);
-        sy = fmaf(e1.y, gp.x, sy);
-        v[j] = cmul_f(make_float2(sx, sy), cw[j].x, -cw[j].y);
+        const float2 f0 = h ? gp : v[j], f1 = h ? v[j] : gp;
+        const float2 w1 = cmul_f(f1, cw[j].x, cw[j].y);         // W^k F_1
+        const float2 x0 = cadd(f0, w1), x1 = csub(f0, w1);
+        const float2 a = d0[j], b = e1s[j * T + t];
+        const float2 y0 = make_float2(fmaf(a.x, x0.x, -(a.y * x0.y)), fmaf(a.x, x0.y, a.y * x0.x));
+        const float2 y1 = make_float2(fmaf(b.x, x1.x, -(b.y * x1.y)), fmaf(b.x, x1.y, b.y * x1.x));
+        v[j] = h ? cmul_f(csub(y0, y1), cw[j].x, -cw[j].y) : cadd(y0, y1);
       }
     }
-    dft<16, true, EX>(v);
+    f2_dft<L, NP - 1, true, EX>(v);
     f2_store<L, NP - 1>(buf, v, t);
     __syncthreads();
     f2_load<L, 1>(buf, v, t);
@@ -243,9 +269,10 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg::T, 1)
 #pragma unroll
     for (int pp = 0; pp < 8; ++pp) {
       const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
-      v[2 * pp] = couple_cell(v[2 * pp], make_float2(q2.x, q2.y), ph[t + 2 * pp * T], band, am1, bb);
-      v[2 * pp + 1] =
-          couple_cell(v[2 * pp + 1], make_float2(q2.z, q2.w), ph[t + (2 * pp + 1) * T], band, am1, bb);
+      const int c0 = C::NAT ? 2 * (t + 2 * pp * T) + h : t + 2 * pp * T;
+      const int c1 = C::NAT ? 2 * (t + (2 * pp + 1) * T) + h : t + (2 * pp + 1) * T;
+      v[2 * pp] = couple_cell(v[2 * pp], make_float2(q2.x, q2.y), ph[c0], band, am1, bb);
+      v[2 * pp + 1] = couple_cell(v[2 * pp + 1], make_float2(q2.z, q2.w), ph[c1], band, am1, bb);
     }
 
     if (rec) {

@@ -3,28 +3,36 @@
 // one all-to-all spectral exchange per step.
 //
 // With the band split over P = 4 interleaved sub-sequences, the forward
-// recombination of the partial spectra G_h = W_N^{h k} F_h, the propagator
-// increment D = (P(q) - 1)/N and the inverse recombination collapse, per
-// local frequency k, into a circulant over the four parts:
-//   H_h[k] = W_N^{-h k} sum_{d=0..3} E_d[k] G_{(h+d) mod 4}[k],
-//   E_d[k] = sum_r W_4^{d r} D[k + 4096 r]
-// (tabulated in FP64, rounded once).  Each CTA sends its G to the three other
-// CTAs of its band and needs nothing else from them, so one exchange of
-// 3 x 32 KB per CTA replaces the two all-to-all rounds of the unfused form.
+// recombination of the partial spectra G_h = W_N^{h k} F_h (F_h the local
+// 4096-point spectrum), the propagator increment D = (P(q) - 1)/N and the
+// inverse recombination collapse, per local frequency k, into a circulant
+// over the four parts:
+//   H_h[k] = W_N^{-h k} sum_{d=0..3} E_d[k] G_{(h+d) mod 4}[k]
+//          = sum_d E_d[k] W_N^{(h'-h) k} F_{h'}[k],   h' = (h + d) mod 4,
+//   E_d[k] = sum_r W_4^{d r} D[k + 4096 r].
+// Part h keeps its own table set E_d W_N^{(h'-h) k}, tabulated in FP64 as
+// double-float pairs hi + lo: E_d mixes D values of very different size, and
+// one float would round the small ones far beyond their own size, an error
+// that repeats every step.  Each CTA sends its F to the three other CTAs of
+// its band and needs nothing else from them: one exchange of 3 x 32 KB per
+// CTA replaces the two all-to-all rounds of the unfused form, and no
+// twiddle multiply remains in the combine.
 //
-// Storage.  Shared memory holds the FFT scratch, the three received G, the
+// Storage.  Shared memory holds the FFT scratch, the three received F, the
 // other band's psi_p (double-buffered by step parity) and the strain slice:
-// 226 KB.  The 64 complex E values of a thread (4 per owned frequency) live
-// in tensor memory: written once per launch with tcgen05.st, read back in
-// chunks of two frequencies with tcgen05.ld each step (256 columns of the SM's 512).
+// 226 KB.  The 64 complex table values of a thread (4 per owned frequency,
+// hi and lo) live in tensor memory: written once per launch with
+// tcgen05.st, read back one frequency (16 columns) at a time with
+// tcgen05.ld each step, the next frequency's load in flight (all 512
+// columns of the SM).
 //
 // Synchronisation, all point to point, no cluster-wide barrier in the march:
-//   * G arrives by st.async on the receiver's mbarrier (expected bytes);
-//   * a CTA that has read its three G slots arrives remotely on each sender's
+//   * F arrives by st.async on the receiver's mbarrier (expected bytes);
+//   * a CTA that has read its three F slots arrives remotely on each sender's
 //     "free" barrier; a sender waits for all three before writing the next
-//     step's G (normally long satisfied: a whole inverse FFT lies between);
+//     step's F (normally long satisfied: a whole inverse FFT lies between);
 //   * psi_p goes to the other band as in the 2-CTA kernel (fused3_kernel.cuh).
-// Band powers: the parts of CTAs h = 1..3 ride on the next step's G to h = 0,
+// Band powers: the parts of CTAs h = 1..3 ride on the next step's F to h = 0,
 // which sums the four in a fixed order.
 #pragma once
 
@@ -40,14 +48,14 @@ struct F4TCfg {
   static constexpr int T = M / 16;
   static constexpr int PADM = M + (M >> 4);
   static constexpr int WARPS = T / 32;
-  static constexpr int TMEM_COLS = 256;                    // 2 x 128 columns per lane
+  static constexpr int TMEM_COLS = 512;                    // 2 x 256 columns per lane
   static constexpr int OFF_BUF = 0;                        // [PADM]
-  static constexpr int OFF_G = OFF_BUF + PADM * 8;         // [3][M] G of parts h+1, h+2, h+3
+  static constexpr int OFF_G = OFF_BUF + PADM * 8;         // [3][M] F of parts h+1, h+2, h+3
   static constexpr int OFF_C = OFF_G + 3 * M * 8;          // [2][M] other band's psi_p
   static constexpr int OFF_PH = OFF_C + 2 * M * 8;         // [M] strain slice
   static constexpr int OFF_MBAR = OFF_PH + M * 8;          // strain-slice barrier
-  static constexpr int OFF_GBAR = OFF_MBAR + 8;            // G arrival
-  static constexpr int OFF_FREE = OFF_GBAR + 8;            // peers have read our G
+  static constexpr int OFF_GBAR = OFF_MBAR + 8;            // F arrival
+  static constexpr int OFF_FREE = OFF_GBAR + 8;            // peers have read our F
   static constexpr int OFF_CBAR = OFF_FREE + 8;            // [2] psi_p arrival
   static constexpr int OFF_PPEER = OFF_CBAR + 16;          // [3] band-power parts (h = 0)
   static constexpr int OFF_RECPH = OFF_PPEER + 24;
@@ -160,7 +168,7 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
   double* part = reinterpret_cast<double*>(smem + C::OFF_PART);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::OFF_TMEM);
 
-  // peer e (1..3) of the band is part (h + e) & 3; our G goes to its slot
+  // peer e (1..3) of the band is part (h + e) & 3; our F goes to its slot
   // 3 - e (the receiver indexes slots by d - 1, d = sender - receiver mod 4)
   uint32_t g_to[3], gbar_to[3], free_to[3];
 #pragma unroll
@@ -187,10 +195,10 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
   tmem_fence_before();
   __syncthreads();
   tmem_fence_after();
-  // this thread's 128 columns: lanes 32 (warp mod 4) + lane, columns from 0
-  // (warps 0-3) or 128 (warps 4-7)
+  // this thread's 256 columns: lanes 32 (warp mod 4) + lane, columns from 0
+  // (warps 0-3) or 256 (warps 4-7)
   const uint32_t tbase = *tmem_slot + (uint32_t(32 * (warp & 3)) << 16) +
-                         uint32_t(warp >= 4 ? 128 : 0);
+                         uint32_t(warp >= 4 ? 256 : 0);
 
   float2 w0[15], w1[15];
 #pragma unroll
@@ -200,24 +208,23 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
     const float4 bq = __ldg(&tw[4 * (((t % F::stride(1)) * j) << 4)]);
     w1[j - 1] = make_float2(bq.x, bq.y);
   }
-  // combine twiddles W_N^{h k_j}; E_d[k_j] into tensor memory, chunk q of
-  // 4 frequencies at columns 32 q: (j - 4q) * 8 + 2 d + {re, im}
-  float2 cw[16];
+  // this part's E_d W^{(h'-h) k_j} into tensor memory, frequency j at
+  // columns 16 j + 4 d + {hi.re, hi.im, lo.re, lo.im}
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < 8; ++q) {
     float ev[32];
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
-      const int j = 4 * q + jj;
+    for (int jj = 0; jj < 2; ++jj) {
+      const int j = 2 * q + jj;
       const int pos = f2_pos<L, NP - 1>(t, j);
-      const int k = (pos >> 8) + ((pos >> 4) & 15) * 16 + (pos & 15) * 256;
-      const float4 a = __ldg(&tw[h * k]);
-      cw[j] = make_float2(a.x, a.y);
 #pragma unroll
       for (int dl = 0; dl < 4; ++dl) {
-        const float2 e = __ldg(&d.prop[(band * 4 + dl) * M + pos]);
-        ev[jj * 8 + 2 * dl] = e.x;
-        ev[jj * 8 + 2 * dl + 1] = e.y;
+        const float4 e = __ldg(reinterpret_cast<const float4*>(d.prop) +
+                               ((band * 4 + h) * 4 + dl) * M + pos);
+        ev[jj * 16 + 4 * dl] = e.x;
+        ev[jj * 16 + 4 * dl + 1] = e.y;
+        ev[jj * 16 + 4 * dl + 2] = e.z;
+        ev[jj * 16 + 4 * dl + 3] = e.w;
       }
     }
     tmem_st32(tbase + uint32_t(32 * q), ev);
@@ -270,10 +277,8 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
     __syncthreads();
     f2_load<L, NP - 1>(buf, v, t);
     dft<16, false, EX>(v);                       // v[j] = F_h[k_j]
-    // the peers have read our previous G before we overwrite their slots
+    // the peers have read our previous F before we overwrite their slots
     if (it > 0 && !timed_out && !mbar_wait_cluster(gfree, uint32_t((it - 1) & 1))) timed_out = true;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = cmul_f(v[j], cw[j].x, cw[j].y);   // G_h[k_j]
 #pragma unroll
     for (int pp = 0; pp < 8; ++pp)
 #pragma unroll
@@ -286,41 +291,40 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
       d.powers[2 * (n / d.record_every - 1) + band] =
           (((my_part + ppeer[0]) + ppeer[1]) + ppeer[2]) * d.dx_um;
     {
-      // chunk q (frequencies 2q, 2q+1) of E from tensor memory, the next
-      // chunk's load in flight while this one is used
+      // E of frequency j from tensor memory, the next frequency's load in
+      // flight while this one is used; the lo products are summed first
       float ev[2][16];
       tmem_ld16(tbase, ev[0]);
       tmem_wait16(ev[0]);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        if (q < 7) tmem_ld16(tbase + uint32_t(16 * (q + 1)), ev[(q + 1) & 1]);
-        const float* e = ev[q & 1];
-        float4 g2[3];
+      for (int j = 0; j < 16; ++j) {
+        if (j < 15) tmem_ld16(tbase + uint32_t(16 * (j + 1)), ev[(j + 1) & 1]);
+        const float* e = ev[j & 1];
+        float2 g[4];
+        g[0] = v[j];
 #pragma unroll
-        for (int dl = 1; dl < 4; ++dl)
-          g2[dl - 1] = *reinterpret_cast<const float4*>(gx + (dl - 1) * M + xpair(q, t, T));
+        for (int dl = 1; dl < 4; ++dl) g[dl] = gx[(dl - 1) * M + xpair(j >> 1, t, T) + (j & 1)];
+        float sx = fmaf(e[2], g[0].x, -(e[3] * g[0].y));
+        float sy = fmaf(e[2], g[0].y, e[3] * g[0].x);
 #pragma unroll
-        for (int jj = 0; jj < 2; ++jj) {
-          const int j = 2 * q + jj;
-          const float2 g0 = v[j];
-          float sx = fmaf(e[jj * 8], g0.x, -(e[jj * 8 + 1] * g0.y));
-          float sy = fmaf(e[jj * 8], g0.y, e[jj * 8 + 1] * g0.x);
-#pragma unroll
-          for (int dl = 1; dl < 4; ++dl) {
-            const float4 gg = g2[dl - 1];
-            const float2 g = jj ? make_float2(gg.z, gg.w) : make_float2(gg.x, gg.y);
-            const float ex = e[jj * 8 + 2 * dl], ey = e[jj * 8 + 2 * dl + 1];
-            sx = fmaf(ex, g.x, sx);
-            sx = fmaf(-ey, g.y, sx);
-            sy = fmaf(ex, g.y, sy);
-            sy = fmaf(ey, g.x, sy);
-          }
-          v[j] = cmul_f(make_float2(sx, sy), cw[j].x, -cw[j].y);
+        for (int dl = 1; dl < 4; ++dl) {
+          sx = fmaf(e[4 * dl + 2], g[dl].x, sx);
+          sx = fmaf(-e[4 * dl + 3], g[dl].y, sx);
+          sy = fmaf(e[4 * dl + 2], g[dl].y, sy);
+          sy = fmaf(e[4 * dl + 3], g[dl].x, sy);
         }
-        if (q < 7) tmem_wait16(ev[(q + 1) & 1]);
+#pragma unroll
+        for (int dl = 0; dl < 4; ++dl) {
+          sx = fmaf(e[4 * dl], g[dl].x, sx);
+          sx = fmaf(-e[4 * dl + 1], g[dl].y, sx);
+          sy = fmaf(e[4 * dl], g[dl].y, sy);
+          sy = fmaf(e[4 * dl + 1], g[dl].x, sy);
+        }
+        v[j] = make_float2(sx, sy);
+        if (j < 15) tmem_wait16(ev[(j + 1) & 1]);
       }
     }
-    __syncthreads();                             // all of our G slots read
+    __syncthreads();                             // all of our F slots read
     if (lead)
 #pragma unroll
       for (int e = 0; e < 3; ++e) mbar_arrive_remote(free_to[e]);

@@ -62,6 +62,26 @@ int fused2_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
   return BPM_OK;
 }
 
+// N = 4096 as a half-band split: one row per 4-CTA cluster, each CTA a
+// 2048-point half of one band (fused4_kernel.cuh with M = 2048).
+template <bool EX>
+int fused4h_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const float4* d_tw,
+                        int* d_status, cudaStream_t st) {
+  using C = F4ECfg<11>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(fused4e_march_kernel<11, EX>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused4h)");
+    configured = true;
+  }
+  fused4e_march_kernel<11, EX><<<4 * n_rows, C::T, C::SMEM, st>>>(d_rows, n_rows, steps, d_tw,
+                                                                  d_status);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "fused4h march launch");
+  return BPM_OK;
+}
+
 // Resident CTAs per SM of a kernel with its launch shape.
 template <typename K>
 int blocks_per_sm(K kernel, int threads, int smem) {
@@ -117,11 +137,11 @@ int fused4_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
                        int* d_status, cudaStream_t st) {
   static_assert(P == 2 || P == 4, "N = 8192 or 16384");
   auto kern = [] {
-    if constexpr (P == 2) return fused4e_march_kernel<EX>;
+    if constexpr (P == 2) return fused4e_march_kernel<12, EX>;
     else return fused4t_march_kernel<EX>;
   }();
-  constexpr int smem = P == 2 ? F4ECfg::SMEM : F4TCfg::SMEM;
-  constexpr int threads = P == 2 ? F4ECfg::T : F4TCfg::T;
+  constexpr int smem = P == 2 ? F4ECfg<12>::SMEM : F4TCfg::SMEM;
+  constexpr int threads = P == 2 ? F4ECfg<12>::T : F4TCfg::T;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -140,8 +160,8 @@ int fused4_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
   namespace bpm {                                                                 \
   int fused4_rows_resident_##L() {                                                \
     if constexpr (P == 2)                                                         \
-      return clusters_resident(fused4e_march_kernel<true>, 4, F4ECfg::T,          \
-                               F4ECfg::SMEM);                                     \
+      return clusters_resident(fused4e_march_kernel<12, true>, 4, F4ECfg<12>::T,  \
+                               F4ECfg<12>::SMEM);                                 \
     else                                                                          \
       return clusters_resident(fused4t_march_kernel<true>, 8, F4TCfg::T,          \
                                F4TCfg::SMEM);                                     \
@@ -192,5 +212,15 @@ int fused4_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
   int fused_launch_##L(const RowDescF32* r, int n, int s, const float4* tw,      \
                        int* status, cudaStream_t st) {                            \
     return fused_launch_impl<L>(r, n, s, tw, status, st);                         \
+  }                                                                               \
+  }
+
+#define BPM_INSTANTIATE_FUSED4H                                                   \
+  namespace bpm {                                                                 \
+  int fused4h_launch_12(const RowDescF32* r, int n, int s, const float4* tw,     \
+                        int* status, cudaStream_t st) {                           \
+    return fused_exact_constants()                                                \
+               ? fused4h_launch_impl<true>(r, n, s, tw, status, st)               \
+               : fused4h_launch_impl<false>(r, n, s, tw, status, st);             \
   }                                                                               \
   }

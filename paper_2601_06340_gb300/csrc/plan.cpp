@@ -189,37 +189,72 @@ std::vector<int> fft_output_order(int logn) {
   return out;
 }
 
-void fused_prop_table(const bpm_plan_s* plan, int row, std::vector<float2>* out) {
+// Split bands (N = M P), per band and local position pos of the local
+// M-point transform's digit-reversed output, with spectral index k and
+// D = (P(q) - 1)/N:
+//   P = 2: [band][D(k) | D(k + M)][pos] -- the kernel forms
+//          X_r = F_0 + (-1)^r W_N^k F_1 and D(k + M r) X_r itself, so each
+//          table value is rounded relative to itself;
+//   P = 4: [band][h][delta][pos] of E_delta[k] W_N^{s k}, s = h' - h for the
+//          sender h' = (h + delta) mod 4, E_delta[k] = sum_r W_4^{delta r}
+//          D[k + M r], as double-float pairs (hi, lo): float4 (hi.re,
+//          hi.im, lo.re, lo.im).  Part h forms sum_delta of these times the
+//          senders' local spectra F_h'.  E mixes D values of very different
+//          size, so a single float would round the small ones far beyond
+//          their own size, and that error repeats every step; hi + lo keeps
+//          it at FP64 level.
+void split_prop_table(const bpm_plan_s* plan, int row, int logm, std::vector<float2>* out) {
   const EnergyConsts& c = plan->ec[row];
-  int n = plan->nx;
-  if (plan->logn >= kSplitLogN) {
-    // Split bands (N = 4096 P, P = 2 or 4), one-exchange form:
-    // [band][delta][local position] with E_delta[k] = sum_r W_P^{delta r}
-    // D[k + 4096 r], W_P = exp(-2 pi i / P), D = (P(q) - 1)/N at the local
-    // 4096-point transform's digit-reversed position's spectral index k.
-    const int m = 1 << 12, parts = n / m;
-    std::vector<int> local = fft_output_order(12);
-    out->assign(2 * size_t(n), float2{0.f, 0.f});
-    std::vector<cd> dk(parts), w(parts);
-    for (int r = 0; r < parts; ++r) {
-      double cr, ci;
-      unit_root(r, parts, &cr, &ci);
-      w[r] = cd(cr, ci);
-    }
-    for (int band = 0; band < 2; ++band) {
-      int sign = band == 0 ? +1 : -1;
-      for (int pos = 0; pos < m; ++pos) {
-        for (int r = 0; r < parts; ++r) {
-          double q = fftfreq_q(local[pos] + m * r, n, c.dxh);
-          dk[r] = expm1_i(cd(c.dzh * delta_q(q, c.s, c.c, sign), 0.0)) * (1.0 / double(n));
-        }
-        for (int dl = 0; dl < parts; ++dl) {
-          cd e(0.0, 0.0);
-          for (int r = 0; r < parts; ++r) e += w[(dl * r) % parts] * dk[r];
-          (*out)[size_t(band) * n + size_t(dl) * m + pos] = float2{float(e.real()), float(e.imag())};
+  const int n = plan->nx, m = 1 << logm, parts = n / m;
+  std::vector<int> local = fft_output_order(logm);
+  out->assign(size_t(split_table_stride(plan, logm)), float2{0.f, 0.f});
+  std::vector<cd> dk(parts), w(parts);
+  for (int r = 0; r < parts; ++r) {
+    double cr, ci;
+    unit_root(r, parts, &cr, &ci);
+    w[r] = cd(cr, ci);
+  }
+  for (int band = 0; band < 2; ++band) {
+    int sign = band == 0 ? +1 : -1;
+    for (int pos = 0; pos < m; ++pos) {
+      for (int r = 0; r < parts; ++r) {
+        double q = fftfreq_q(local[pos] + m * r, n, c.dxh);
+        dk[r] = expm1_i(cd(c.dzh * delta_q(q, c.s, c.c, sign), 0.0)) * (1.0 / double(n));
+      }
+      if (parts == 2) {
+        for (int r = 0; r < 2; ++r)
+          (*out)[(size_t(band) * 2 + r) * m + pos] =
+              float2{float(dk[r].real()), float(dk[r].imag())};
+        continue;
+      }
+      for (int dl = 0; dl < parts; ++dl) {
+        cd e(0.0, 0.0);
+        for (int r = 0; r < parts; ++r) e += w[(dl * r) % parts] * dk[r];
+        for (int h = 0; h < parts; ++h) {
+          const int sh = h + dl < parts ? dl : dl - parts;     // h' - h
+          double wr, wi;
+          unit_root(((sh * local[pos]) % n + n) % n, n, &wr, &wi);   // W_N^{sh k}
+          const cd f = e * cd(wr, wi);
+          const float fr = float(f.real()), fi = float(f.imag());
+          const size_t at = 2 * (((size_t(band) * parts + h) * parts + dl) * m + pos);
+          (*out)[at] = float2{fr, fi};
+          (*out)[at + 1] = float2{float(f.real() - double(fr)), float(f.imag() - double(fi))};
         }
       }
     }
+  }
+}
+
+int split_table_stride(const bpm_plan_s* plan, int logm) {
+  const int parts = plan->nx >> logm;
+  return parts == 2 ? 2 * parts * (1 << logm) : 2 * parts * parts * (1 << logm) * 2;
+}
+
+void fused_prop_table(const bpm_plan_s* plan, int row, std::vector<float2>* out) {
+  const EnergyConsts& c = plan->ec[row];
+  int n = plan->nx;
+  if (plan->logn >= kSplitLogN) {   // N = 4096 P, P = 2 or 4
+    split_prop_table(plan, row, 12, out);
     return;
   }
   std::vector<int> order = fft_output_order(plan->logn);

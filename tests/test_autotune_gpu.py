@@ -30,7 +30,7 @@ def _march(wl, monkeypatch, tune):
 def test_layout_search_for_a_small_batch(bpm_lib, monkeypatch):
     wl = inputs.pulse_batched(nx=2048, nz=200, n_energy=40, record_every=60)
     out, shape = _march(wl, monkeypatch, True)
-    assert shape[0] in (0, 1) and shape[1] == 0, shape
+    assert shape[0] in (0, 1, 2) and shape[1] == 0, shape
     rule, rshape = _march(wl, monkeypatch, False)
     assert rshape == (-1, 0)
     rows = [0, 21, 39]

@@ -1,0 +1,57 @@
+"""N = 4096 solves in their three launch layouts: the half-band split on a
+4-CTA cluster (the rule while every row gets four SMs), the 2-CTA cluster
+and one CTA per row.  Each must match the oracle within the FP32 tolerance,
+on the final field alone (the stricter reading when a band has decayed) and
+on every record, over marches long enough for per-step errors to build up.
+"""
+
+import numpy as np
+import pytest
+
+from paper_2601_06340_gb300 import binding, inputs
+from parity_util import TOL_FP32, band_errors, run_ref
+
+pytestmark = pytest.mark.gpu
+
+FP32 = binding.BPM_FP32_FUSED
+
+
+def _march(wl, monkeypatch, layout):
+    if layout:
+        monkeypatch.setenv("BPM_FUSED_LAYOUT", layout)
+    else:
+        monkeypatch.delenv("BPM_FUSED_LAYOUT", raising=False)
+    with binding.Plan(wl, FP32) as plan:
+        out = plan.propagate()
+        shape = binding.bpm_launch_shape(plan.handle)
+    return out, shape
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_layouts_against_oracle(bpm_lib, monkeypatch, seed):
+    rng = np.random.default_rng(40 + seed)
+    wl = inputs.serving_request(rng, 4096, 3000)
+    wl.record_every = 700
+    ref = run_ref(wl)
+    outs = {}
+    for layout, want in ((None, 2), ("cluster", -1), ("cta", -1)):
+        out, shape = _march(wl, monkeypatch, layout)
+        assert shape[0] == want, (layout, shape)
+        final = band_errors(out.psi, ref.psi)
+        full = band_errors(out.psi, ref.psi, out.records, ref.records)
+        assert max(final) <= TOL_FP32 and max(full) <= TOL_FP32, (layout, final, full)
+        assert np.allclose(out.powers, ref.powers, rtol=1e-4, atol=1e-9 * ref.powers.max())
+        outs[layout] = out
+    # the layouts differ only by FP32 rounding
+    assert max(band_errors(outs[None].psi, outs["cluster"].psi)) <= 1e-4
+
+
+def test_split_bragg_bent_full_march(bpm_lib, monkeypatch):
+    """The 8000-step bent Bragg solve: its weak transmitted band at the
+    exit is the hardest reading of the bound."""
+    wl = inputs.bragg_bent()
+    ref = run_ref(wl)
+    out, shape = _march(wl, monkeypatch, None)
+    assert shape[0] == 2
+    final = band_errors(out.psi, ref.psi)
+    assert max(final) <= TOL_FP32, final
