@@ -294,6 +294,7 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
       // E of frequency j from tensor memory, the next frequency's load in
       // flight while this one is used; the lo products are summed first
       float ev[2][16];
+      float2 odd[3];   // the odd frequency's half of the peers' 16-byte pairs
       tmem_ld16(tbase, ev[0]);
       tmem_wait16(ev[0]);
 #pragma unroll
@@ -303,7 +304,15 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
         float2 g[4];
         g[0] = v[j];
 #pragma unroll
-        for (int dl = 1; dl < 4; ++dl) g[dl] = gx[(dl - 1) * M + xpair(j >> 1, t, T) + (j & 1)];
+        for (int dl = 1; dl < 4; ++dl) {
+          if ((j & 1) == 0) {
+            const float4 q = *reinterpret_cast<const float4*>(gx + (dl - 1) * M + xpair(j >> 1, t, T));
+            g[dl] = make_float2(q.x, q.y);
+            odd[dl - 1] = make_float2(q.z, q.w);
+          } else {
+            g[dl] = odd[dl - 1];
+          }
+        }
         float sx = fmaf(e[2], g[0].x, -(e[3] * g[0].y));
         float sy = fmaf(e[2], g[0].y, e[3] * g[0].x);
 #pragma unroll
