@@ -196,11 +196,13 @@ struct VolColCfg {
   static constexpr int N = F::N, T = F::T, NP = F::NP;
   static constexpr int COLS = 4;
   static constexpr int THREADS = COLS * T;
-  // column stride = 8 mod 16 in 8-byte words: a warp is 8 rows x 4 columns,
-  // and the 4 columns land in alternate halves of the banks, so every
-  // 32-lane access spreads over the 16 bank pairs twice (2 wavefronts, the
-  // minimum for 256 bytes)
-  static constexpr int PADC = N + (N >> 4) + 8;
+  // column stride = 4 mod 16 in 8-byte words: 8-byte accesses are served
+  // per half-warp (4 rows x 4 columns here), and the 4 columns land on
+  // 4 different quarters of the 16 bank pairs, so the tile copies and the
+  // radix-16 passes take 2 wavefronts per warp access, the minimum for 256
+  // bytes (a stride of 8 mod 16 put columns 0/2 and 1/3 on the same banks:
+  // 4 wavefronts, half of them conflicts in the profile)
+  static constexpr int PADC = N + (N >> 4) + 4;
   static constexpr int S1 = F::S1;
   static constexpr int OFF_BUF = 0;                               // [COLS][PADC]
   static constexpr int OFF_TW1 = OFF_BUF + COLS * PADC * 8;       // [S1][16]
