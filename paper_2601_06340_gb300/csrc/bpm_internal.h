@@ -186,6 +186,7 @@ int split_table_stride(const bpm_plan_s* plan, int logm);   // float2 per row
 // cluster per row, 2 4-CTA cluster per row (N = 4096, half-band split).
 constexpr int kLayoutSplit4 = 2;
 int fused_launch_capacity(int logn, bool cluster);
+int fused_split4_capacity();
 int fused_rows_per_cta(int logn);
 int fused_threads(int logn);
 

@@ -21,6 +21,7 @@ BPM_DECLARE_FUSED2(9) BPM_DECLARE_FUSED2(10) BPM_DECLARE_FUSED2(11)
 BPM_DECLARE_FUSED2(12)
 int fused4_launch_13(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
 int fused4h_launch_12(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
+int fused4h_rows_resident_12();
 int fused4_launch_14(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
 #define BPM_DECLARE_FUSED3(L)                                                    \
   int fused3_launch_##L(const RowDescF32*, int, int, const float4*, int*,        \
@@ -203,6 +204,13 @@ int fused_launch_capacity(int logn, bool cluster) {
       c = r * sm_count();
     }
   }
+  return c;
+}
+
+// Rows of N = 4096 one half-band-split launch keeps resident (4-CTA clusters).
+int fused_split4_capacity() {
+  static int c = 0;
+  if (c == 0) c = fused4h_rows_resident_12();
   return c;
 }
 

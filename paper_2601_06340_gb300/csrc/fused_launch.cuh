@@ -217,6 +217,10 @@ int fused4_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
 
 #define BPM_INSTANTIATE_FUSED4H                                                   \
   namespace bpm {                                                                 \
+  int fused4h_rows_resident_12() {                                                \
+    return clusters_resident(fused4e_march_kernel<11, true>, 4, F4ECfg<11>::T,    \
+                             F4ECfg<11>::SMEM);                                   \
+  }                                                                               \
   int fused4h_launch_12(const RowDescF32* r, int n, int s, const float4* tw,     \
                         int* status, cudaStream_t st) {                           \
     return fused_exact_constants()                                                \

@@ -367,7 +367,8 @@ int cluster_demand(Server& s) {
 
 // Launch the next batch of a bucket.  Layout by load: when every active row
 // can have the SMs of its cluster layout the launch is latency-first (a
-// 2-CTA cluster per row for N <= 4096); once that demand would exceed the
+// 2-CTA cluster per row for N <= 4096, a 4-CTA half-band split for N = 4096
+// while two more SMs per row are free); once that demand would exceed the
 // GPU, rows of N <= 4096 go one CTA per row (several rows per SM for small N),
 // which does more cell-updates per SM.  The batch takes at most as many
 // rows as that layout keeps resident, in round-robin order over the members
@@ -376,11 +377,20 @@ int launch_batch(Server& s, Bucket& b) {
   Batch bt = take_batch(b);
   const bool fp32 = b.members.front()->plan->precision == BPM_FP32_FUSED;
   const int logn = b.members.front()->plan->logn;   // one size per bucket
-  const int layout = fp32 && cluster_demand(s) <= s.sm_count ? -1 : 0;
+  const int demand = cluster_demand(s);
+  int layout = fp32 && demand <= s.sm_count ? -1 : 0;
+  // N = 4096 rows go as half-band splits (four SMs each, as bpm_propagate
+  // marches them alone) while the GPU has the two extra SMs per row
+  if (fp32 && logn == 12 && demand + 2 * int(b.members.size()) <= s.sm_count) {
+    bool tables = true;
+    for (auto& r : b.members) tables = tables && r->plan->d_prop_split != nullptr;
+    if (tables) layout = kLayoutSplit4;
+  }
   size_t limit = b.members.size();
   if (fp32) {
     const bool cluster = layout < 0 && 2 * int(b.members.size()) <= s.sm_count;
-    limit = size_t(std::max(1, fused_launch_capacity(logn, cluster)));
+    limit = size_t(std::max(1, layout == kLayoutSplit4 ? fused_split4_capacity()
+                                                       : fused_launch_capacity(logn, cluster)));
   }
   std::map<int, std::vector<RowDescF32>> groups;   // FP32 rows by step count
   std::vector<RowDescF32> rows;
