@@ -279,7 +279,7 @@ int bpm_march_f64_noalloc(void* d_psi, int32_t nx, int32_t n_rows, const void* d
  * *chunk = steps per launch of the rotation schedule (more rows than one
  * launch keeps resident), 0 for a single launch.  A batch march with a
  * choice of shapes (the layouts above for up to one row per two SMs at
- * 1024 <= nx <= 4096, or rotation chunks of 64..512 steps) times each on a
+ * 512 <= nx <= 4096, or rotation chunks of 64..512 steps) times each on a
  * short march of a scratch copy of the state the first time a given
  * (nx, rows) is marched, blocking the host for those trials, and keeps the
  * fastest for the process; BPM_AUTOTUNE=0 in the environment, a single row

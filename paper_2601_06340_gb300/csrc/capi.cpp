@@ -287,7 +287,7 @@ static LaunchShape choose_shape(bpm_plan_s* plan, PlanAux* aux, const void* stat
   // candidates, the rule's own shape first
   std::vector<LaunchShape> cands;
   const int cta_cap = fused_launch_capacity(logn, false);
-  if (logn >= 10 && 2 * nb <= sms) {
+  if (logn >= 9 && 2 * nb <= sms) {
     LaunchShape c;
     if (split_ok) {
       c.layout = kLayoutSplit4;

@@ -26,8 +26,9 @@ int fused4_launch_14(const RowDescF32*, int, int, const float4*, int*, cudaStrea
 #define BPM_DECLARE_FUSED3(L)                                                    \
   int fused3_launch_##L(const RowDescF32*, int, int, const float4*, int*,        \
                         cudaStream_t);
-BPM_DECLARE_FUSED3(10) BPM_DECLARE_FUSED3(11) BPM_DECLARE_FUSED3(12)
-int fused3_rows_resident_10(); int fused3_rows_resident_11(); int fused3_rows_resident_12();
+BPM_DECLARE_FUSED3(9) BPM_DECLARE_FUSED3(10) BPM_DECLARE_FUSED3(11) BPM_DECLARE_FUSED3(12)
+int fused3_rows_resident_9(); int fused3_rows_resident_10(); int fused3_rows_resident_11();
+int fused3_rows_resident_12();
 int fused4_rows_resident_13(); int fused4_rows_resident_14();
 int fused_rows_resident_3(); int fused_rows_resident_4(); int fused_rows_resident_5();
 int fused_rows_resident_6(); int fused_rows_resident_7(); int fused2_rows_resident_8();
@@ -49,7 +50,7 @@ static int forced_layout() {
 }
 
 static bool use_cluster_layout(int logn, int n_rows) {
-  if (logn < 10 || logn > 12) return false;
+  if (logn < 9 || logn > 12) return false;
   const int forced = forced_layout();
   if (forced == 0 || forced == 1) return forced == 1;
   return 2 * n_rows <= sm_count();
@@ -62,7 +63,7 @@ int launch_fused(int logn, const RowDescF32* d_rows, int n_rows, int steps,
 
 int fused_cluster_sms(int logn) {
   if (logn >= kSplitLogN) return 2 << (logn - 12);
-  return (logn >= 10 && logn <= 12) ? 2 : 0;
+  return (logn >= 9 && logn <= 12) ? 2 : 0;
 }
 
 int launch_fused_layout(int logn, const RowDescF32* d_rows, int n_rows, int steps,
@@ -71,10 +72,11 @@ int launch_fused_layout(int logn, const RowDescF32* d_rows, int n_rows, int step
   // (only for rows that carry the split tables: the caller checks)
   if (logn == 12 && layout == kLayoutSplit4)
     return fused4h_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
-  const bool cluster = logn >= 10 && logn <= 12 &&
+  const bool cluster = logn >= 9 && logn <= 12 &&
                        (layout == 1 || (layout < 0 && use_cluster_layout(logn, n_rows)));
   if (cluster) {
     switch (logn) {
+      case 9: return fused3_launch_9(d_rows, n_rows, steps, d_tw, d_status, st);
       case 10: return fused3_launch_10(d_rows, n_rows, steps, d_tw, d_status, st);
       case 11: return fused3_launch_11(d_rows, n_rows, steps, d_tw, d_status, st);
       default: return fused3_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
@@ -172,15 +174,16 @@ int fused_rows_resident(int logn, int n_rows) {
 }
 
 // Rows one launch of the given layout keeps resident on the whole GPU:
-// clusters for the cluster kernels (N >= 8192 always, 1024..4096 when
+// clusters for the cluster kernels (N >= 8192 always, 512..4096 when
 // `cluster`), else CTA rows per SM times the SMs.
 int fused_launch_capacity(int logn, bool cluster) {
   static int cache[2][kMaxLogN + 1] = {};
-  const bool cl = logn >= kSplitLogN || (cluster && logn >= 10 && logn <= 12);
+  const bool cl = logn >= kSplitLogN || (cluster && logn >= 9 && logn <= 12);
   int& c = cache[cl ? 1 : 0][logn];
   if (c == 0) {
     if (cl) {
       switch (logn) {
+        case 9: c = fused3_rows_resident_9(); break;
         case 10: c = fused3_rows_resident_10(); break;
         case 11: c = fused3_rows_resident_11(); break;
         case 12: c = fused3_rows_resident_12(); break;

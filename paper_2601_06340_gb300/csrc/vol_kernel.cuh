@@ -93,6 +93,15 @@ __global__ void __launch_bounds__(VolRowCfg<LOGN>::THREADS)
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = p.org[off + t + j * T];
   } else {
+    // every global read of the step is issued here, so their latencies
+    // overlap (a line is too little work to hide three in a row)
+    const float2* ph = p.phasor + size_t(p.n) * plane + size_t(y) * N;
+    float2 org[16], phv[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      org[j] = p.org[off + t + j * T];
+      phv[j] = __ldg(&ph[t + j * T]);
+    }
     // inverse FFT along x of the increment's x-spectrum
     constexpr int P = NP - 1;
     constexpr int R = F2Cfg<LOGN>::radix(P), G = F2Cfg<LOGN>::groups(P);
@@ -114,18 +123,14 @@ __global__ void __launch_bounds__(VolRowCfg<LOGN>::THREADS)
     f2_twiddle<true>(v, w0);
     dft<16, true, EX>(v);
     // psi_p = psi + increment, then the coupling with the other band (lane ^ 16)
-    const float2* ph = p.phasor + size_t(p.n) * plane + size_t(y) * N;
     const float2 am1 = p.coup[2 * r], bb = p.coup[2 * r + 1];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const float2 o = p.org[off + t + j * T];
-      v[j] = cadd<false>(o, v[j]);   // scalar: the packed add measured slower here
-    }
+    for (int j = 0; j < 16; ++j) v[j] = cadd<false>(org[j], v[j]);   // scalar: measured faster here
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       const float2 q = make_float2(__shfl_xor_sync(0xffffffffu, v[j].x, 16),
                                    __shfl_xor_sync(0xffffffffu, v[j].y, 16));
-      v[j] = couple_cell(v[j], q, ph[t + j * T], band, am1, bb);
+      v[j] = couple_cell(v[j], q, phv[j], band, am1, bb);
     }
     const int n1 = p.n + 1;
     if (p.record_every > 0 && (n1 % p.record_every) == 0 && (p.records || p.pwpart)) {
@@ -253,11 +258,21 @@ __global__ void __launch_bounds__(VolColCfg<LOGN>::THREADS)
   }
   const float2* tw1o = tw1 + (tt % C::S1);
 
-  // tile in: rows y, columns tile*COLS .. +COLS (contiguous per row)
-  for (int k = threadIdx.x; k < N * COLS; k += blockDim.x) {
-    const int yy = k / COLS, cc = k % COLS;
-    reinterpret_cast<float2*>(smem + C::OFF_BUF)[cc * C::PADC + padi(yy)] =
-        spec[size_t(yy) * p.nx + tile * COLS + cc];
+  // tile in: rows y, columns tile*COLS .. +COLS (contiguous per row); all
+  // N * COLS / THREADS = 16 loads of a thread issued before the first store
+  {
+    static_assert(N * COLS == 16 * C::THREADS, "16 tile values per thread");
+    float2 tv[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int k = threadIdx.x + i * C::THREADS;
+      tv[i] = spec[size_t(k / COLS) * p.nx + tile * COLS + k % COLS];
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int k = threadIdx.x + i * C::THREADS;
+      reinterpret_cast<float2*>(smem + C::OFF_BUF)[(k % COLS) * C::PADC + padi(k / COLS)] = tv[i];
+    }
   }
   __syncthreads();
 
