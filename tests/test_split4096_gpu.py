@@ -55,3 +55,27 @@ def test_split_bragg_bent_full_march(bpm_lib, monkeypatch):
     assert shape[0] == 2
     final = band_errors(out.psi, ref.psi)
     assert max(final) <= TOL_FP32, final
+
+
+def test_split_resume_and_small_batch(bpm_lib, monkeypatch):
+    """A march resumed half-way equals the whole march (the half-band kernel
+    reloads its state and tables per launch), and an 8-row N = 4096 batch
+    (every row still gets four SMs) matches the oracle row by row."""
+    monkeypatch.delenv("BPM_FUSED_LAYOUT", raising=False)
+    wl = inputs.bragg_bent(nx=4096, nz=1400, record_every=200)
+    with binding.Plan(wl, FP32) as plan:
+        full = plan.propagate()
+        assert binding.bpm_launch_shape(plan.handle)[0] == 2
+        first = plan.propagate(n_end=700)
+        rec = first.records.copy()
+        pw = first.powers.copy()
+        second = plan.propagate(first.psi, n_begin=700,
+                                out=binding.MarchOutput(np.empty_like(first.psi), rec, pw))
+    assert max(band_errors(second.psi, full.psi, second.records, full.records)) <= 1e-5
+    wb = inputs.pulse_batched(nx=4096, nz=300, n_energy=8, record_every=100)
+    with binding.Plan(wb, FP32) as plan:
+        out = plan.propagate()
+        assert binding.bpm_launch_shape(plan.handle)[0] in (0, 1, 2)
+    rows = [0, 7]
+    ref = run_ref(wb, rows=rows)
+    assert max(band_errors(out.psi[rows], ref.psi, out.records[rows], ref.records)) <= 2e-5
