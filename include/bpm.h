@@ -62,8 +62,8 @@ enum bpm_status {
 
 enum bpm_precision { BPM_FP64_PLAIN = 0, BPM_FP32_FUSED = 1 };
 
-/* Crystal shape Pi(x, z) (Eqs. fov11-12: 1 inside, 0 outside; Section 3
- * for the slab and its asymmetry angle, Section 6 for arbitrary shapes). */
+/* Crystal shape Pi(x, z) (Eqs. fov11-12: 1 inside, 0 outside; Section 4
+ * for the slab and its asymmetry angle, Section 7 for arbitrary shapes). */
 enum bpm_crystal_kind {
   BPM_CRYSTAL_VACUUM = 0,          /* Pi = 0 everywhere (free space)        */
   BPM_CRYSTAL_BULK = 1,            /* Pi = 1 everywhere                     */

@@ -2,10 +2,10 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-The paper defines the crystal by a 0/1 map Pi (Eqs. fov11-fov12; "Pi = 1
-inside the crystal and 0 outside"), either as a slab whose surface normal is
-set by ``asymm_angle`` (Section 3: 0 deg = Bragg, 90 deg = Laue, in between
-= asymmetric) or as an arbitrary map (Section 6).  The deformation enters
+The paper defines the crystal by a 0/1 map Pi (Eqs. fov11-fov12: 1 in the
+crystal, 0 elsewhere), either as a slab whose surface normal is
+set by ``asymm_angle`` (Section 4: 0 deg = Bragg, 90 deg = Laue, in between
+= asymmetric) or as an arbitrary map (Section 7).  The deformation enters
 only through u_x (Eq. Authier), here from
 
 * a cylindrical bend, Eq. fov110 in the configured form
