@@ -137,7 +137,7 @@ int bpm_set_crystal(bpm_plan_t plan, int32_t kind, double asym_angle_rad,
 int bpm_set_strain(bpm_plan_t plan, int32_t kind, const double* ux_um,
                    const double* params, int32_t n_params);
 
-/* Operator splitting of Eq. split-op for FP64 plans: the step applies
+/* Operator splitting of Eq. split-op: the step applies
  * A(a_1 dz) B(b_1 dz) A(a_2 dz) B(b_2 dz) ... in that order (A: the
  * angular-spectrum propagation of each band, B: the coupling of Eqs.
  * fov11-fov12 formed for a step of b_i dz), every stage of step n with the
@@ -146,8 +146,12 @@ int bpm_set_strain(bpm_plan_t plan, int32_t kind, const double* ux_um,
  *   BPM_SPLIT_VERLET:      a = (0, 1), b = (1/2, 1/2);
  *   BPM_SPLIT_FOREST_RUTH: a = (0, t, 1-2t, t), b = (t/2, (1-t)/2, (1-t)/2,
  *                          t/2), t = 1/(2 - 2^(1/3)).
- * FP32 (fused) and 3D plans take the first-order step only: other methods
- * return BPM_ERR_INVALID for them.  BPM_ERR_BUSY while tickets are pending. */
+ * FP64 plans take every method.  FP32 (fused) plans take the first-order
+ * step, and Verlet for 256 <= nx <= 4096 (one CTA per solve; half-step
+ * couplings on either side of the full-step propagation); 3D plans take the
+ * first-order step only; other combinations return BPM_ERR_INVALID.
+ * bpm_submit refuses FP32 plans set to Verlet (BPM_ERR_INVALID).
+ * BPM_ERR_BUSY while tickets are pending. */
 enum bpm_splitting {
   BPM_SPLIT_FIRST_ORDER = 0,
   BPM_SPLIT_VERLET = 1,
@@ -272,7 +276,8 @@ int bpm_march_f64_noalloc(void* d_psi, int32_t nx, int32_t n_rows, const void* d
                           int32_t n_end, void* stream);
 
 /* Launch shape of the plan's last FP32 march (the fused kernels of the
- * step of Eq. fov10): *layout = 2 one 4-CTA cluster per row (nx = 4096 as
+ * step of Eq. fov10): *layout = 3 one CTA per row with the Verlet step
+ * (plans set to BPM_SPLIT_VERLET), 2 one 4-CTA cluster per row (nx = 4096 as
  * two half-band parts per band; the rule while every row gets four SMs),
  * 1 one 2-CTA cluster per row, 0 one CTA per row, -1 chosen by the fixed
  * rule (2-CTA cluster while every row gets two SMs, else one CTA per row);

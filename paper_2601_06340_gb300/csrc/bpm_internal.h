@@ -39,6 +39,7 @@ struct RowDescF32 {
   double* powers;           // [n_rec+1][2] or null
   float2 am1;               // Delta_eps_0 - 1 inside the crystal
   float2 b;                 // Delta_eps_{+-1} inside the crystal
+  float2 am1h, bh;          // the same for half a step (second-order splitting)
   double gphase;            // common per-step phase (dz^ cos alpha) mod 2 pi
   double dx_um;
   int32_t n_begin;          // first step of this launch (absolute)
@@ -185,8 +186,11 @@ int split_table_stride(const bpm_plan_s* plan, int logm);   // float2 per row
 // Layout codes of launch_fused_layout: -1 rule, 0 CTA per row, 1 2-CTA
 // cluster per row, 2 4-CTA cluster per row (N = 4096, half-band split).
 constexpr int kLayoutSplit4 = 2;
+// one CTA per row, second-order (Verlet) step, N = 256..4096
+constexpr int kLayoutCtaHalf = 3;
 int fused_launch_capacity(int logn, bool cluster);
 int fused_split4_capacity();
+int fused_half_capacity(int logn);   // 8 <= logn <= 12
 int fused_rows_per_cta(int logn);
 int fused_threads(int logn);
 

@@ -129,6 +129,15 @@ void fused_rows(bpm_plan_s* plan, float2* state, float2* rec, double* pw, int n_
     const EnergyConsts& c = plan->ec[r];
     d.am1 = make_float2(float(c.am1.real()), float(c.am1.imag()));
     d.b = make_float2(float(c.b.real()), float(c.b.imag()));
+    if (plan->split == BPM_SPLIT_VERLET) {
+      std::complex<double> ah, bh;
+      coupling_frac(plan, r, 0.5, &ah, &bh);
+      d.am1h = make_float2(float((ah - 1.0).real()), float((ah - 1.0).imag()));
+      d.bh = make_float2(float(bh.real()), float(bh.imag()));
+    } else {
+      d.am1h = d.am1;
+      d.bh = d.b;
+    }
     d.gphase = c.gphase;
     d.dx_um = plan->dx_um;
     d.n_begin = n_begin;
@@ -155,7 +164,8 @@ void phase_factors(const bpm_plan_s* plan, int steps, std::vector<double2>* out)
 // their strain slices in L2.  A remainder shorter than a chunk runs as a
 // second round of the same kind.
 static int launch_rotated(bpm_plan_s* plan, PlanAux* aux, const std::vector<RowDescF32>& rows,
-                          int n_begin, int steps, int resident, cudaStream_t st, int chunk = 0) {
+                          int n_begin, int steps, int resident, cudaStream_t st, int chunk = 0,
+                          int layout = -1) {
   const int nb = plan->nb;
   if (chunk <= 0) chunk = std::max(std::min(steps, 64), steps / 24);
   chunk = std::min(chunk, steps);
@@ -192,8 +202,9 @@ static int launch_rotated(bpm_plan_s* plan, PlanAux* aux, const std::vector<RowD
                                   cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "upload launch schedule");
   for (const Launch& l : launches) {
-    int rc = launch_fused(plan->logn, aux->d_sched + l.off, l.count, l.steps,
-                          static_cast<const float4*>(plan->d_tw), plan->d_status, st);
+    int rc = launch_fused_layout(plan->logn, aux->d_sched + l.off, l.count, l.steps,
+                                 static_cast<const float4*>(plan->d_tw), plan->d_status, st,
+                                 layout);
     if (rc != BPM_OK) return rc;
   }
   return BPM_OK;
@@ -268,6 +279,11 @@ static LaunchShape choose_shape(bpm_plan_s* plan, PlanAux* aux, const void* stat
                                 int steps, cudaStream_t st) {
   LaunchShape rule;
   const int nb = plan->nb, logn = plan->logn;
+  if (plan->split == BPM_SPLIT_VERLET) {   // one kernel form marches this splitting
+    rule.layout = kLayoutCtaHalf;
+    rule.rotated = nb > fused_half_capacity(logn);
+    return rule;
+  }
   const int resident = fused_rows_resident(logn, nb);   // 0 when the rule picks clusters
   rule.rotated = resident > 0 && nb > resident;
   // N = 4096 rows that each get four SMs march fastest as half-band splits
@@ -391,8 +407,9 @@ static int enqueue_march(bpm_plan_s* plan, PlanAux* aux, void* state, void* d_re
                                steps, static_cast<const float4*>(plan->d_tw), plan->d_status, st,
                                sh.layout);
     } else {
-      rc = launch_rotated(plan, aux, rows, n_begin, steps, fused_launch_capacity(plan->logn, false),
-                          st, sh.chunk);
+      const int cap = sh.layout == kLayoutCtaHalf ? fused_half_capacity(plan->logn)
+                                                  : fused_launch_capacity(plan->logn, false);
+      rc = launch_rotated(plan, aux, rows, n_begin, steps, cap, st, sh.chunk, sh.layout);
     }
     if (rc != BPM_OK) return rc;
     return launch_finish_f32(static_cast<const float2*>(state),
@@ -589,9 +606,12 @@ int bpm_set_splitting(bpm_plan_t plan, int32_t method) {
   if (plan->pending) return fail(BPM_ERR_BUSY, "plan has pending tickets");
   if (method < BPM_SPLIT_FIRST_ORDER || method > BPM_SPLIT_FOREST_RUTH)
     return fail(BPM_ERR_INVALID, "unknown splitting method");
-  if (method != BPM_SPLIT_FIRST_ORDER &&
-      (plan->precision != BPM_FP64_PLAIN || plan->ny > 1))
-    return fail(BPM_ERR_INVALID, "higher-order splitting needs a 2D BPM_FP64_PLAIN plan");
+  if (method != BPM_SPLIT_FIRST_ORDER && plan->ny > 1)
+    return fail(BPM_ERR_INVALID, "higher-order splitting needs a 2D plan");
+  if (plan->precision == BPM_FP32_FUSED && method != BPM_SPLIT_FIRST_ORDER &&
+      (method != BPM_SPLIT_VERLET || plan->logn < 8 || plan->logn > 12))
+    return fail(BPM_ERR_INVALID,
+                "BPM_FP32_FUSED plans march first order, or Verlet for 256 <= nx <= 4096");
   for (void** p : {&plan->d_stage_rows, &plan->d_stage_prop}) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -599,7 +619,9 @@ int bpm_set_splitting(bpm_plan_t plan, int32_t method) {
   plan->split = method;
   plan->n_stages = 0;
   plan->stage_has_prop.clear();
-  if (method == BPM_SPLIT_FIRST_ORDER) return BPM_OK;
+  // FP32: the fused kernels take the half-step coefficients from the row
+  // descriptors, built at each march
+  if (method == BPM_SPLIT_FIRST_ORDER || plan->precision == BPM_FP32_FUSED) return BPM_OK;
   const auto stages = split_stages(method);
   const size_t n = plan->nx, nb = plan->nb;
   // one table per distinct nonzero a_i
@@ -615,14 +637,19 @@ int bpm_set_splitting(bpm_plan_t plan, int32_t method) {
   if (rc != BPM_OK) return rc;
   double2* tables = static_cast<double2*>(plan->d_stage_prop);
   std::vector<RowDescF64> rows(stages.size() * nb);
-  cudaError_t e = cudaSuccess;
-  for (size_t f = 0; f < fracs.size() && e == cudaSuccess; ++f)
-    for (size_t r = 0; r < nb && e == cudaSuccess; ++r) {
+  // Uploads are ordered on the plan's stream and waited for: a plain
+  // cudaMemcpy from pageable memory may return before its DMA has landed,
+  // and the marches run on non-blocking streams.
+  cudaStream_t st = aux_of(plan)->stream;
+  std::vector<double2> host(fracs.size() * nb * 2 * n);
+  for (size_t f = 0; f < fracs.size(); ++f)
+    for (size_t r = 0; r < nb; ++r) {
       std::vector<double2> t;
       plain_prop_table_frac(plan, int(r), fracs[f], &t);
-      e = cudaMemcpy(tables + (f * nb + r) * 2 * n, t.data(), t.size() * sizeof(double2),
-                     cudaMemcpyHostToDevice);
+      std::copy(t.begin(), t.end(), host.begin() + long((f * nb + r) * 2 * n));
     }
+  cudaError_t e = cudaMemcpyAsync(tables, host.data(), host.size() * sizeof(double2),
+                                  cudaMemcpyHostToDevice, st);
   for (size_t s = 0; s < stages.size(); ++s) {
     const size_t f = std::find(fracs.begin(), fracs.end(), stages[s].first) - fracs.begin();
     plan->stage_has_prop.push_back(stages[s].first != 0.0 ? 1 : 0);
@@ -637,8 +664,9 @@ int bpm_set_splitting(bpm_plan_t plan, int32_t method) {
     }
   }
   if (e == cudaSuccess)
-    e = cudaMemcpy(plan->d_stage_rows, rows.data(), rows.size() * sizeof(RowDescF64),
-                   cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(plan->d_stage_rows, rows.data(), rows.size() * sizeof(RowDescF64),
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "splitting tables");
   plan->n_stages = int(stages.size());
   return BPM_OK;

@@ -14,7 +14,10 @@ namespace bpm {
                        cudaStream_t);
 #define BPM_DECLARE_FUSED2(L)                                                    \
   int fused2_launch_##L(const RowDescF32*, int, int, const float4*, int*,        \
-                        cudaStream_t);
+                        cudaStream_t);                                           \
+  int fused2h_launch_##L(const RowDescF32*, int, int, const float4*, int*,       \
+                         cudaStream_t);                                          \
+  int fused2h_rows_resident_##L();
 BPM_DECLARE_FUSED(3) BPM_DECLARE_FUSED(4) BPM_DECLARE_FUSED(5)
 BPM_DECLARE_FUSED(6) BPM_DECLARE_FUSED(7) BPM_DECLARE_FUSED2(8)
 BPM_DECLARE_FUSED2(9) BPM_DECLARE_FUSED2(10) BPM_DECLARE_FUSED2(11)
@@ -72,6 +75,16 @@ int launch_fused_layout(int logn, const RowDescF32* d_rows, int n_rows, int step
   // (only for rows that carry the split tables: the caller checks)
   if (logn == 12 && layout == kLayoutSplit4)
     return fused4h_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
+  if (layout == kLayoutCtaHalf) {
+    switch (logn) {
+      case 8: return fused2h_launch_8(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 9: return fused2h_launch_9(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 10: return fused2h_launch_10(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 11: return fused2h_launch_11(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 12: return fused2h_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
+      default: return fail(BPM_ERR_INVALID, "second-order splitting needs 256 <= nx <= 4096");
+    }
+  }
   const bool cluster = logn >= 9 && logn <= 12 &&
                        (layout == 1 || (layout < 0 && use_cluster_layout(logn, n_rows)));
   if (cluster) {
@@ -208,6 +221,23 @@ int fused_launch_capacity(int logn, bool cluster) {
     }
   }
   return c;
+}
+
+// Rows one launch of the second-order (Verlet) CTA kernel keeps resident.
+int fused_half_capacity(int logn) {
+  static int cache[kMaxLogN + 1] = {};
+  if (cache[logn] == 0) {
+    int r = 1;
+    switch (logn) {
+      case 8: r = fused2h_rows_resident_8(); break;
+      case 9: r = fused2h_rows_resident_9(); break;
+      case 10: r = fused2h_rows_resident_10(); break;
+      case 11: r = fused2h_rows_resident_11(); break;
+      default: r = fused2h_rows_resident_12(); break;
+    }
+    cache[logn] = r * sm_count();
+  }
+  return cache[logn];
 }
 
 // Rows of N = 4096 one half-band-split launch keeps resident (4-CTA clusters).

@@ -27,7 +27,9 @@
 
 namespace bpm {
 
-template <int LOGN>
+// PHB: strain-slice buffers per row (2 when the step couples twice, see
+// the kernel's HALF form)
+template <int LOGN, int PHB = 1>
 struct F2Cfg {
   static constexpr int N = 1 << LOGN;
   static constexpr int E = 16;
@@ -40,9 +42,9 @@ struct F2Cfg {
   static constexpr int PADN = N + (N >> 4);
   static constexpr int OFF_BUF = 0;                                   // [ROWS][2][PADN]
   static constexpr int OFF_ORG = OFF_BUF + ROWS * 2 * PADN * 8;       // [ROWS][2][N]
-  static constexpr int OFF_PH = OFF_ORG + ROWS * 2 * N * 8;           // [ROWS][N]
-  static constexpr int OFF_MBAR = OFF_PH + ROWS * N * 8;
-  static constexpr int OFF_RECPH = OFF_MBAR + ROWS * 8;
+  static constexpr int OFF_PH = OFF_ORG + ROWS * 2 * N * 8;           // [ROWS][PHB][N]
+  static constexpr int OFF_MBAR = OFF_PH + ROWS * PHB * N * 8;        // [ROWS][PHB]
+  static constexpr int OFF_RECPH = OFF_MBAR + ROWS * PHB * 8;
   static constexpr int OFF_RED = OFF_RECPH + ROWS * 8;                // [ROWS][WPR][2] double
   static constexpr int S1 = NP >= 3 ? (N >> 8) : 1;                   // pass-1 group offsets
   static constexpr int OFF_TW1 = OFF_RED + ROWS * WPR * 2 * 8;        // [S1][16] float2
@@ -109,11 +111,45 @@ __device__ __forceinline__ void f2_twiddle(float2* v, const float2* w) {
   }
 }
 
-template <int LOGN, bool EX>
+// Coupling of this thread's 16 cells with the other band (lane ^ 16), the
+// coefficients (a - 1, b) of the step (or of its half), e = the cells' strain
+// phasors from the slice `ph`.
+template <int T>
+__device__ __forceinline__ void f2_couple(float2* v, const float2* ph, int t, int band,
+                                          float2 am1, float2 bb) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const float2 q = make_float2(__shfl_xor_sync(0xffffffffu, v[j].x, 16),
+                                 __shfl_xor_sync(0xffffffffu, v[j].y, 16));
+    float2 e = ph[t + j * T];
+    const bool inside = (e.x != 0.f) | (e.y != 0.f);
+    if (band) e.y = -e.y;
+    const float ax = inside ? am1.x : 0.f, ay = inside ? am1.y : 0.f;
+    const float cx = fmaf(bb.x, e.x, -(bb.y * e.y)), cy = fmaf(bb.x, e.y, bb.y * e.x);
+    const float2 p = v[j];
+    float rx = fmaf(ax, p.x, p.x);
+    rx = fmaf(-ay, p.y, rx);
+    rx = fmaf(cx, q.x, rx);
+    rx = fmaf(-cy, q.y, rx);
+    float ry = fmaf(ax, p.y, p.y);
+    ry = fmaf(ay, p.x, ry);
+    ry = fmaf(cx, q.y, ry);
+    ry = fmaf(cy, q.x, ry);
+    v[j] = make_float2(rx, ry);
+  }
+}
+
+// HALF = false: the first-order step of Eq. fov10 (propagate, then couple
+// with the step's coefficients).  HALF = true: the second-order (Verlet /
+// Strang) step of Eq. split-op, couple with half-step coefficients,
+// propagate, couple with half-step coefficients again, both couplings on the
+// slice of the step; the slice of step n + 1 is fetched during step n into
+// the other of two buffers.
+template <int LOGN, bool EX, bool HALF = false>
 __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 512 ? 1 : 2)
     fused2_march_kernel(const RowDescF32* __restrict__ rows, int n_rows, int steps,
                         const float4* __restrict__ tw, int* __restrict__ status) {
-  using C = F2Cfg<LOGN>;
+  using C = F2Cfg<LOGN, HALF ? 2 : 1>;
   constexpr int N = C::N, T = C::T, NP = C::NP, RL = C::RL;
   constexpr int WPB = T / 16;                  // warps per band-pair group
   // packed complex adds in the butterflies, except at N = 4096 where the
@@ -133,12 +169,15 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
 
   float2* buf = reinterpret_cast<float2*>(smem + C::OFF_BUF) + (rl * 2 + band) * C::PADN;
   float2* org = reinterpret_cast<float2*>(smem + C::OFF_ORG) + (rl * 2 + band) * N;
-  float2* ph = reinterpret_cast<float2*>(smem + C::OFF_PH) + rl * N;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::OFF_MBAR) + rl;
+  float2* ph0 = reinterpret_cast<float2*>(smem + C::OFF_PH) + rl * (HALF ? 2 : 1) * N;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::OFF_MBAR) + rl * (HALF ? 2 : 1);
   float2* recph = reinterpret_cast<float2*>(smem + C::OFF_RECPH) + rl;
   double* red = reinterpret_cast<double*>(smem + C::OFF_RED) + rl * C::WPR * 2;
 
-  if (t == 0 && band == 0) mbar_init(bar);
+  if (t == 0 && band == 0) {
+    mbar_init(bar);
+    if constexpr (HALF) mbar_init(bar + 1);
+  }
   fence_mbar_init();
 
   // Twiddles: pass 0 (group o = t) in registers; pass 1 (o = t mod S1, only
@@ -179,10 +218,21 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
   const uint32_t slice_bytes = uint32_t(N) * 8u;
   int pending_slot = -1;
   bool timed_out = false;
-  const float2 am1 = d.am1, bb = d.b;
+  const float2 am1 = HALF ? d.am1h : d.am1, bb = HALF ? d.bh : d.b;
+  if constexpr (HALF) {
+    // the first step's slice; later ones are fetched a step ahead
+    if (lead && steps > 0) bulk_load(ph0, d.phasor + size_t(d.n_begin) * N, slice_bytes, bar);
+  }
 
   for (int it = 0; it < steps; ++it) {
     const int n = d.n_begin + it;
+    float2* ph = ph0 + (HALF ? (it & 1) * N : 0);
+    if constexpr (HALF) {
+      // first half coupling, on this step's slice
+      if (active && !timed_out && !mbar_wait(bar + (it & 1), uint32_t((it >> 1) & 1)))
+        timed_out = true;
+      f2_couple<T>(v, ph, t, band, am1, bb);
+    }
     const bool rec = active && d.record_every > 0 && ((n + 1) % d.record_every) == 0 &&
                      (d.records != nullptr || d.powers != nullptr);
     if (lead && rec) {
@@ -198,7 +248,15 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
     f2_twiddle<false>(v, w0);
     f2_store<LOGN, 0>(buf, v, t);
     __syncthreads();
-    if (lead) bulk_load(ph, d.phasor + size_t(n) * N, slice_bytes, bar);
+    if constexpr (HALF) {
+      // every thread is past the couplings of step it - 1, which read the
+      // other buffer: fetch step it + 1's slice into it
+      if (lead && it + 1 < steps)
+        bulk_load(ph0 + ((it + 1) & 1) * N, d.phasor + size_t(n + 1) * N, slice_bytes,
+                  bar + ((it + 1) & 1));
+    } else {
+      if (lead) bulk_load(ph, d.phasor + size_t(n) * N, slice_bytes, bar);
+    }
     if (lead && pending_slot >= 0) {
       double s0 = 0.0, s1 = 0.0;
       for (int w = 0; w < C::WPR; ++w) {
@@ -248,27 +306,10 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
     }
 
     // ---- coupling with the other band (lane ^ 16) -------------------------
-    if (active && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const float2 q = make_float2(__shfl_xor_sync(0xffffffffu, v[j].x, 16),
-                                   __shfl_xor_sync(0xffffffffu, v[j].y, 16));
-      float2 e = ph[t + j * T];
-      const bool inside = (e.x != 0.f) | (e.y != 0.f);
-      if (band) e.y = -e.y;
-      const float ax = inside ? am1.x : 0.f, ay = inside ? am1.y : 0.f;
-      const float cx = fmaf(bb.x, e.x, -(bb.y * e.y)), cy = fmaf(bb.x, e.y, bb.y * e.x);
-      const float2 p = v[j];
-      float rx = fmaf(ax, p.x, p.x);
-      rx = fmaf(-ay, p.y, rx);
-      rx = fmaf(cx, q.x, rx);
-      rx = fmaf(-cy, q.y, rx);
-      float ry = fmaf(ax, p.y, p.y);
-      ry = fmaf(ay, p.x, ry);
-      ry = fmaf(cx, q.y, ry);
-      ry = fmaf(cy, q.x, ry);
-      v[j] = make_float2(rx, ry);
+    if constexpr (!HALF) {
+      if (active && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
     }
+    f2_couple<T>(v, ph, t, band, am1, bb);
 
     // ---- record ------------------------------------------------------------
     const bool want_pw = rec && d.powers != nullptr;

@@ -42,21 +42,22 @@ int fused_launch_impl(const RowDescF32* d_rows, int n_rows, int steps,
   return BPM_OK;
 }
 
-// Band-per-thread kernel (256 <= N <= 4096); EX selects hi+lo butterfly constants.
-template <int LOGN, bool EX>
+// Band-per-thread kernel (256 <= N <= 4096); EX selects hi+lo butterfly
+// constants, HALF the second-order (Verlet) step.
+template <int LOGN, bool EX, bool HALF = false>
 int fused2_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const float4* d_tw,
                        int* d_status, cudaStream_t st) {
-  using C = F2Cfg<LOGN>;
+  using C = F2Cfg<LOGN, HALF ? 2 : 1>;
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(fused2_march_kernel<LOGN, EX>,
+    cudaError_t e = cudaFuncSetAttribute(fused2_march_kernel<LOGN, EX, HALF>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused2)");
     configured = true;
   }
   const int grid = (n_rows + C::ROWS - 1) / C::ROWS;
-  fused2_march_kernel<LOGN, EX><<<grid, C::THREADS, C::SMEM, st>>>(d_rows, n_rows, steps, d_tw,
-                                                                  d_status);
+  fused2_march_kernel<LOGN, EX, HALF><<<grid, C::THREADS, C::SMEM, st>>>(d_rows, n_rows, steps,
+                                                                        d_tw, d_status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "fused2 march launch");
   return BPM_OK;
@@ -200,6 +201,17 @@ int fused4_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
     return fused_exact_constants()                                                \
                ? fused2_launch_impl<L, true>(r, n, s, tw, status, st)             \
                : fused2_launch_impl<L, false>(r, n, s, tw, status, st);           \
+  }                                                                               \
+  int fused2h_rows_resident_##L() {                                               \
+    using C = F2Cfg<L, 2>;                                                        \
+    return blocks_per_sm(fused2_march_kernel<L, true, true>, C::THREADS, C::SMEM) * \
+           C::ROWS;                                                               \
+  }                                                                               \
+  int fused2h_launch_##L(const RowDescF32* r, int n, int s, const float4* tw,    \
+                         int* status, cudaStream_t st) {                          \
+    return fused_exact_constants()                                                \
+               ? fused2_launch_impl<L, true, true>(r, n, s, tw, status, st)       \
+               : fused2_launch_impl<L, false, true>(r, n, s, tw, status, st);     \
   }                                                                               \
   }
 

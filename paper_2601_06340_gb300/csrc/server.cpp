@@ -437,8 +437,13 @@ int launch_batch(Server& s, Bucket& b) {
     if (!s.d_tw[logn]) {
       std::vector<float4> tw;
       twiddle_table_f32(1 << logn, &tw);
+      // ordered on the launch stream and waited for (a plain cudaMemcpy from
+      // pageable memory may return before its DMA lands, and the launches
+      // of every size run on non-blocking streams)
       cudaMalloc(&s.d_tw[logn], tw.size() * sizeof(float4));
-      cudaMemcpy(s.d_tw[logn], tw.data(), tw.size() * sizeof(float4), cudaMemcpyHostToDevice);
+      cudaMemcpyAsync(s.d_tw[logn], tw.data(), tw.size() * sizeof(float4),
+                      cudaMemcpyHostToDevice, b.st);
+      cudaStreamSynchronize(b.st);
     }
     size_t off = 0;
     for (auto& kv : groups) {
@@ -633,6 +638,8 @@ int bpm_submit(bpm_plan_t plan, const double* psi_in, double* psi_out, void* rec
     return fail(BPM_ERR_INVALID, "plan, psi_in, psi_out and out must be non-NULL");
   *out = 0;
   if (plan->ny > 1) return fail(BPM_ERR_INVALID, "the server takes 2D plans only");
+  if (plan->precision == BPM_FP32_FUSED && plan->split != BPM_SPLIT_FIRST_ORDER)
+    return fail(BPM_ERR_INVALID, "the server marches FP32 plans with first-order splitting only");
   Server& s = srv();
   auto r = std::make_shared<Request>();
   r->plan = plan;

@@ -1,10 +1,13 @@
 """Operator splitting of Eq. split-op (Verlet, Forest-Ruth) on the plain
-FP64 GPU path against the oracle; FP32 plans refuse it."""
+FP64 GPU path, and Verlet on the fused FP32 path (N = 256..4096), against
+the oracle; other combinations are refused."""
 
 import pytest
 
 from paper_2601_06340_gb300 import binding, inputs
-from parity_util import TOL_FP64, band_errors, run_ref
+import numpy as np
+
+from parity_util import TOL_FP32, TOL_FP64, band_errors, run_ref
 
 pytestmark = pytest.mark.gpu
 
@@ -33,8 +36,44 @@ def test_splitting_refused_where_not_built(bpm_lib):
     wl = inputs.laue_perfect(nx=256, nz=10)
     with binding.Plan(wl, FP32) as plan:
         binding.bpm_set_splitting(plan.handle, binding.BPM_SPLIT_FIRST_ORDER)
+        binding.bpm_set_splitting(plan.handle, binding.BPM_SPLIT_VERLET)
+        with pytest.raises(binding.BpmError):
+            binding.bpm_set_splitting(plan.handle, binding.BPM_SPLIT_FOREST_RUTH)
+        # the request server marches first-order FP32 plans only
+        with pytest.raises(binding.BpmError):
+            binding.bpm_submit(plan.handle, wl.psi0, np.empty_like(wl.psi0))
+    with binding.Plan(inputs.laue_perfect(nx=128, nz=10), FP32) as plan:
         with pytest.raises(binding.BpmError):
             binding.bpm_set_splitting(plan.handle, binding.BPM_SPLIT_VERLET)
     with binding.Plan(wl, FP64) as plan:
         with pytest.raises(binding.BpmError):
             binding.bpm_set_splitting(plan.handle, 7)
+
+
+@pytest.mark.parametrize("name", ["laue_perfect", "bragg_bent", "asym_dislocation", "pulse"])
+def test_verlet_fp32_matches_oracle(bpm_lib, name):
+    """The fused band-per-thread kernel's second-order step (half coupling,
+    propagation, half coupling on the slice of the step) against the
+    oracle's Verlet march, fields and records; rows of a batch included."""
+    wl = {"laue_perfect": lambda: inputs.laue_perfect(nx=512, nz=400, record_every=50),
+          "bragg_bent": lambda: inputs.bragg_bent(nx=4096, nz=1000, record_every=150),
+          "asym_dislocation": lambda: inputs.asym_dislocation(nx=1024, nz=500,
+                                                              record_every=100),
+          # more rows than one launch keeps resident: the rotation schedule
+          "pulse": lambda: inputs.pulse_batched(nx=4096, nz=300, n_energy=160,
+                                                record_every=100)}[name]()
+    rows = [0, wl.batch - 1]
+    ref = run_ref(wl, method="verlet", rows=rows)
+    with binding.Plan(wl, FP32, splitting=binding.BPM_SPLIT_VERLET) as plan:
+        out = plan.propagate()
+        shape = binding.bpm_launch_shape(plan.handle)
+    assert shape[0] == 3, shape
+    errs = band_errors(out.psi[rows], ref.psi, out.records[rows], ref.records)
+    assert max(errs) <= TOL_FP32, errs
+    final = band_errors(out.psi[rows], ref.psi)
+    assert max(final) <= TOL_FP32, final
+    assert np.allclose(out.powers[rows], ref.powers, rtol=1e-4, atol=1e-9 * ref.powers.max())
+    # and it is not the first-order step
+    first = run_ref(wl, rows=rows)
+    diff = max(band_errors(first.psi, ref.psi))
+    assert diff > 1e-6 and diff > max(errs), (diff, errs)
