@@ -152,10 +152,10 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
   using C = F2Cfg<LOGN, HALF ? 2 : 1>;
   constexpr int N = C::N, T = C::T, NP = C::NP, RL = C::RL;
   constexpr int WPB = T / 16;                  // warps per band-pair group
-  // packed complex adds in the butterflies, except at N = 4096 where the
-  // 128-register budget makes the register pairing cost more than it saves
-  // (measured: 54.6 vs 55.3 ms for a 256-energy batch)
-  constexpr bool PK = LOGN != 12;
+  // packed complex adds in the butterflies at every N (at N = 4096, with the
+  // 128-register budget, measured 54.9-55.0 vs 55.0-55.9 ms for a 256-energy
+  // batch against scalar adds)
+  constexpr bool PK = true;
   extern __shared__ __align__(128) unsigned char smem[];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -213,6 +213,8 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
 #pragma unroll
   for (int j = 0; j < 16; ++j)
     v[j] = active ? d.state[band * N + t + j * T] : make_float2(0.f, 0.f);
+  __shared__ int s_abort;
+  if (threadIdx.x == 0) s_abort = 0;
   __syncthreads();
 
   const uint32_t slice_bytes = uint32_t(N) * 8u;
@@ -224,13 +226,19 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
     if (lead && steps > 0) bulk_load(ph0, d.phasor + size_t(d.n_begin) * N, slice_bytes, bar);
   }
 
+  // Error path: a thread whose bounded wait expires skips this step's other
+  // waits and raises s_abort; at the next step's first barrier (or after the
+  // last step) the lead waits once more (again bounded) for its last slice
+  // copy, so none is in flight when the CTA exits, and the CTA returns.
   for (int it = 0; it < steps; ++it) {
     const int n = d.n_begin + it;
     float2* ph = ph0 + (HALF ? (it & 1) * N : 0);
     if constexpr (HALF) {
       // first half coupling, on this step's slice
-      if (active && !timed_out && !mbar_wait(bar + (it & 1), uint32_t((it >> 1) & 1)))
+      if (active && !timed_out && !mbar_wait(bar + (it & 1), uint32_t((it >> 1) & 1))) {
         timed_out = true;
+        s_abort = 1;
+      }
       f2_couple<T>(v, ph, t, band, am1, bb);
     }
     const bool rec = active && d.record_every > 0 && ((n + 1) % d.record_every) == 0 &&
@@ -248,6 +256,15 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
     f2_twiddle<false>(v, w0);
     f2_store<LOGN, 0>(buf, v, t);
     __syncthreads();
+    if (s_abort) {   // the same value for every thread (read after the barrier)
+      if (lead) {
+        // slices up to it were issued (HALF), else up to it - 1
+        if constexpr (HALF) mbar_wait(bar + (it & 1), uint32_t((it >> 1) & 1));
+        else if (it > 0) mbar_wait(bar, uint32_t((it - 1) & 1));
+      }
+      if (threadIdx.x == 0) atomicOr(status, kStatusWaitTimeout);
+      return;
+    }
     if constexpr (HALF) {
       // every thread is past the couplings of step it - 1, which read the
       // other buffer: fetch step it + 1's slice into it
@@ -307,7 +324,10 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
 
     // ---- coupling with the other band (lane ^ 16) -------------------------
     if constexpr (!HALF) {
-      if (active && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
+      if (active && !mbar_wait(bar, uint32_t(it & 1))) {
+        timed_out = true;
+        s_abort = 1;
+      }
     }
     f2_couple<T>(v, ph, t, band, am1, bb);
 
@@ -335,6 +355,11 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
   }
 
   __syncthreads();
+  if (s_abort && lead) {   // an expired wait in the last step: its slice copy
+    const int last = steps - 1;
+    if constexpr (HALF) mbar_wait(bar + (last & 1), uint32_t((last >> 1) & 1));
+    else mbar_wait(bar, uint32_t(last & 1));
+  }
   if (lead && pending_slot >= 0) {
     double s0 = 0.0, s1 = 0.0;
     for (int w = 0; w < C::WPR; ++w) {
@@ -348,7 +373,7 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
 #pragma unroll
     for (int j = 0; j < 16; ++j) d.state[band * N + t + j * T] = v[j];
   }
-  if (timed_out && lead) atomicOr(status, kStatusWaitTimeout);
+  if (s_abort && threadIdx.x == 0) atomicOr(status, kStatusWaitTimeout);
 }
 
 }  // namespace bpm

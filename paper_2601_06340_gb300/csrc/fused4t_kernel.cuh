@@ -406,7 +406,11 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
   }
 #pragma unroll
   for (int j = 0; j < 16; ++j) d.state[band * N + 4 * (t + j * T) + h] = v[j];
-  if (timed_out && lead) atomicOr(status, kStatusWaitTimeout);
+  // Error path: after an expired wait a thread skips its later waits and the
+  // march runs on to the end of the launch; the lead still issues one slice
+  // copy per step on its barrier, so waiting (again bounded) for the last
+  // step's phase leaves no copy of its own in flight when the CTA exits.
+  if (timed_out) give_up_after_march(bar, uint32_t((steps - 1) & 1), lead, status);
   tmem_fence_before();
   cluster.sync();   // peers may still read our shared memory
   tmem_fence_after();

@@ -108,6 +108,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
+// Error epilogue of the cluster kernels, out of line so that the march loop's
+// code does not change: the lead waits (again bounded) for the phase of the
+// launch's last slice copy, and every thread that gave up flags the launch.
+static __device__ __noinline__ void give_up_after_march(uint64_t* bar, uint32_t last_parity,
+                                                        bool lead, int* status) {
+  if (lead) mbar_wait(bar, last_parity);
+  atomicOr(status, kStatusWaitTimeout);
+}
+
 // ---- per-pass helpers (thread owns groups gi = t + i*T) ------------------
 template <int LOGN, int P>
 __device__ __forceinline__ int pass_pos(int gi, int j) {
@@ -254,13 +263,24 @@ __global__ void __launch_bounds__(FusedCfg<LOGN>::THREADS)
       v0[i * R0 + j] = active ? d.state[pos] : make_float2(0.f, 0.f);
       v1[i * R0 + j] = active ? d.state[N + pos] : make_float2(0.f, 0.f);
     }
+  __shared__ int s_abort;
+  if (threadIdx.x == 0) s_abort = 0;
   __syncthreads();
 
   const uint32_t slice_bytes = uint32_t(N) * 8u;
   int pending_slot = -1;            // record whose powers await reduction
   bool timed_out = false;
 
-  for (int it = 0; it < steps; ++it) {
+  // Error path: a thread whose bounded wait expires raises s_abort; at the
+  // next step's first barrier (or after the last step) each row's lead waits
+  // once more (again bounded) for its last slice copy, so none is in flight
+  // when the CTA exits, and the CTA returns.  With one thread per row and no
+  // barrier in the step (N <= 16) that thread alone leaves the march.
+  int it = 0;
+  for (; it < steps; ++it) {
+    if constexpr (NP == 1) {
+      if (timed_out) break;
+    }
     const int n = d.n_begin + it;
     const bool rec = active && d.record_every > 0 &&
                      ((n + 1) % d.record_every) == 0 &&
@@ -283,6 +303,11 @@ __global__ void __launch_bounds__(FusedCfg<LOGN>::THREADS)
       store_pass<LOGN, 0>(b0, v0, t);
       store_pass<LOGN, 0>(b1, v1, t);
       __syncthreads();
+      if (s_abort) {   // the same value for every thread (read after the barrier)
+        if (t == 0 && active && it > 0) mbar_wait(bar, uint32_t((it - 1) & 1));
+        if (threadIdx.x == 0) atomicOr(status, kStatusWaitTimeout);
+        return;
+      }
       // every thread of the row has finished the previous step's coupling:
       // the slice buffer is free for this step's copy.
       if (t == 0 && active) bulk_load(ph, d.phasor + size_t(n) * N, slice_bytes, bar);
@@ -314,7 +339,10 @@ __global__ void __launch_bounds__(FusedCfg<LOGN>::THREADS)
 
     // ---- coupling through chi_0, chi_h, the strain phase and the mask ----
     if (active) {
-      if (!mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
+      if (!mbar_wait(bar, uint32_t(it & 1))) {
+        timed_out = true;
+        s_abort = 1;
+      }
       const float2 am1 = d.am1, bb = d.b;
 #pragma unroll
       for (int i = 0; i < G0; ++i)
@@ -400,6 +428,10 @@ __global__ void __launch_bounds__(FusedCfg<LOGN>::THREADS)
   }
 
   __syncthreads();
+  {
+    const bool stopped = NP == 1 ? timed_out : s_abort != 0;
+    if (stopped && t == 0 && active && it > 0) mbar_wait(bar, uint32_t((it - 1) & 1));
+  }
   if (t == 0 && pending_slot >= 0) {
     double s0 = 0.0, s1 = 0.0;
     for (int w = 0; w < C::WARPS_PER_ROW; ++w) {
@@ -419,7 +451,7 @@ __global__ void __launch_bounds__(FusedCfg<LOGN>::THREADS)
         d.state[N + pos] = v1[i * R0 + j];
       }
   }
-  if (timed_out && t == 0) atomicOr(status, kStatusWaitTimeout);
+  if (s_abort && threadIdx.x == 0) atomicOr(status, kStatusWaitTimeout);
 }
 
 }  // namespace bpm
