@@ -302,6 +302,17 @@ const char* bpm_last_error(void);
 /* Library version string. */
 const char* bpm_version(void);
 
+/* Self-test of the bounded device wait that every march kernel uses on its
+ * mbarriers (strain-slice copies, peer data).  No counterpart in the paper.
+ * One CTA arms a barrier for bytes that no copy delivers and waits with the
+ * march kernels' bounded loop, which gives up without any fault; the kernel
+ * then sets the status bit that a march would report as BPM_ERR_TIMEOUT.
+ * *status receives that word (1: the wait expired and the kernel returned),
+ * *seconds the kernel's duration (the wait limit).  Blocks the host until
+ * the kernel ends.  BPM_ERR_INVALID for NULL pointers, BPM_ERR_CUDA if the
+ * launch failed. */
+int bpm_selftest_wait_expiry(int32_t* status, double* seconds);
+
 #ifdef __cplusplus
 }
 #endif

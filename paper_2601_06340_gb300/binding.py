@@ -73,6 +73,7 @@ _SIGS = {
     "bpm_destroy": ([_P], ctypes.c_int),
     "bpm_last_error": ([], ctypes.c_char_p),
     "bpm_version": ([], ctypes.c_char_p),
+    "bpm_selftest_wait_expiry": ([ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 }
 
 
@@ -204,12 +205,21 @@ def bpm_march_f64_noalloc(d_psi, nx, n_rows, d_prop, d_coupling, d_phasor, n_beg
 
 
 def bpm_launch_shape(plan) -> tuple[int, int]:
-    """(layout, chunk) of the plan's last FP32 march: layout 2 four-CTA
-    cluster per row (N = 4096 half-band split), 1 two-CTA cluster per row,
-    0 CTA per row, -1 the fixed rule; chunk 0 for one launch."""
+    """(layout, chunk) of the plan's last FP32 march: layout 3 CTA per row
+    with the Verlet step, 2 four-CTA cluster per row (N = 4096 half-band
+    split), 1 two-CTA cluster per row, 0 CTA per row, -1 the fixed rule;
+    chunk 0 for one launch."""
     layout, chunk = _I(0), _I(0)
     _check(load().bpm_launch_shape(plan, ctypes.byref(layout), ctypes.byref(chunk)))
     return layout.value, chunk.value
+
+
+def bpm_selftest_wait_expiry() -> tuple[int, float]:
+    """(status word, seconds) of the bounded-wait self-test kernel: status 1
+    means the wait gave up and the kernel returned."""
+    status, seconds = _I(0), ctypes.c_double(0.0)
+    _check(load().bpm_selftest_wait_expiry(ctypes.byref(status), ctypes.byref(seconds)))
+    return status.value, seconds.value
 
 
 def bpm_destroy(plan):

@@ -98,7 +98,7 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
 // Bounded wait with cluster-scope acquire (data written by a peer CTA).
 __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity) {
   uint32_t b = smem_u32(bar);
-  for (int i = 0; i < (1 << 22); ++i) {
+  for (int i = 0; i < kWaitPolls; ++i) {
     uint32_t ok;
     asm volatile(
         "{ .reg .pred p; mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2; "

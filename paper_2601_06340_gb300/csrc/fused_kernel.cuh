@@ -92,10 +92,15 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src,
       : "memory");
 }
 
+// Poll limit of every bounded mbarrier wait: a try_wait that finds the phase
+// incomplete suspends the thread for about 4 us on GB300, so the limit is
+// about one second (measured by bpm_selftest_wait_expiry).
+constexpr int kWaitPolls = 1 << 18;
+
 // Bounded wait for phase `parity` of the barrier; false on expiry.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   uint32_t b = smem_u32(bar);
-  for (int i = 0; i < (1 << 22); ++i) {
+  for (int i = 0; i < kWaitPolls; ++i) {
     uint32_t ok;
     asm volatile(
         "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "

@@ -94,6 +94,7 @@ def test_null_arguments_are_rejected(lib):
     assert lib.bpm_set_splitting(None, 1) == binding.BPM_ERR_INVALID
     assert lib.bpm_set_crystal_box(None, None) == binding.BPM_ERR_INVALID
     assert lib.bpm_launch_shape(None, None, None) == binding.BPM_ERR_INVALID
+    assert lib.bpm_selftest_wait_expiry(None, None) == binding.BPM_ERR_INVALID
     assert lib.bpm_poll(ctypes.c_uint64(12345), 0) == binding.BPM_ERR_INVALID
     assert "ticket" in binding.bpm_last_error()
 
