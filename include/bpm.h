@@ -233,6 +233,15 @@ int bpm_poll(bpm_ticket_t ticket, int32_t timeout_ms);
 int bpm_server_configure(double mem_fraction, int32_t max_active,
                          int32_t epoch_steps, int32_t max_queue);
 
+/* Test hook (no counterpart in the paper): the next `count` batch launches of
+ * FP32 requests with transform size nx fail on the host with BPM_ERR_CUDA
+ * instead of launching, as a failed kernel launch would.  The requests of
+ * that size in those batches (and the others sharing their bucket at that
+ * moment) then end with BPM_ERR_CUDA; requests of other sizes are not
+ * affected and the server takes new requests of the size afterwards.
+ * count = 0 clears it.  BPM_ERR_INVALID for a bad nx or count < 0. */
+int bpm_server_inject_launch_failure(int32_t nx, int32_t count);
+
 /* Timestamps (seconds, steady clock) of a finished or running ticket:
  * submit, admission to the device, completion (0 while not reached). */
 int bpm_ticket_times(bpm_ticket_t ticket, double* t_submit, double* t_admit,

@@ -74,6 +74,7 @@ _SIGS = {
     "bpm_last_error": ([], ctypes.c_char_p),
     "bpm_version": ([], ctypes.c_char_p),
     "bpm_selftest_wait_expiry": ([ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "bpm_server_inject_launch_failure": ([_I, _I], ctypes.c_int),
 }
 
 
@@ -184,6 +185,12 @@ def bpm_poll(ticket, timeout_ms=0) -> int:
 def bpm_server_configure(mem_fraction=0.0, max_active=0, epoch_steps=0, max_queue=0):
     return _check(load().bpm_server_configure(float(mem_fraction), int(max_active),
                                               int(epoch_steps), int(max_queue)))
+
+
+def bpm_server_inject_launch_failure(nx: int, count: int):
+    """Test hook: the next `count` FP32 batch launches of size nx fail on the
+    host with BPM_ERR_CUDA (0 clears it)."""
+    return _check(load().bpm_server_inject_launch_failure(int(nx), int(count)))
 
 
 def bpm_ticket_times(ticket):

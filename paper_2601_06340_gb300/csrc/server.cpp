@@ -26,6 +26,7 @@
 // same shape and layout), so a result is the same alone and in the mix.
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -125,6 +126,9 @@ struct Server {
   int sm_count = 1;
   bool per_request = false;  // true: one launch stream per request (else one per size)
   float4* d_tw[kMaxLogN + 1] = {};
+  // test hook: launches of FP32 batches of transform size 2^logn still to
+  // fail on the host, as if the launch had returned a CUDA error
+  std::atomic<int> inject_fail[kMaxLogN + 1] = {};
 };
 
 Server& srv() {
@@ -450,6 +454,13 @@ int launch_batch(Server& s, Bucket& b) {
       if (bt.err != BPM_OK) break;
       cudaMemcpyAsync(b.d_rows + off, kv.second.data(), kv.second.size() * sizeof(RowDescF32),
                       cudaMemcpyHostToDevice, b.st);
+      int pending = s.inject_fail[logn].load();
+      while (pending > 0 && !s.inject_fail[logn].compare_exchange_weak(pending, pending - 1)) {
+      }
+      if (pending > 0) {
+        bt.err = fail(BPM_ERR_CUDA, "injected launch failure");
+        break;
+      }
       bt.err = launch_fused_layout(logn, b.d_rows + off, int(kv.second.size()), kv.first,
                                    s.d_tw[logn], bt.d_status, b.st, layout);
       off += kv.second.size();
@@ -629,6 +640,15 @@ int bpm_server_configure(double mem_fraction, int32_t max_active, int32_t epoch_
     cudaMemGetInfo(&free_b, &total_b);
     s.budget = size_t(double(free_b) * s.mem_fraction);
   }
+  return BPM_OK;
+}
+
+int bpm_server_inject_launch_failure(int32_t nx, int32_t count) {
+  int logn = 0;
+  while (logn <= kMaxLogN && (1 << logn) < nx) ++logn;
+  if (nx < 8 || logn > kMaxLogN || (1 << logn) != nx || count < 0)
+    return fail(BPM_ERR_INVALID, "nx must be a power of two in [8, 16384], count >= 0");
+  srv().inject_fail[logn].store(count);
   return BPM_OK;
 }
 

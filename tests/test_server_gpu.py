@@ -56,6 +56,45 @@ def test_mix_equals_alone(bpm_lib):
         p.close()
 
 
+def test_injected_launch_failure_fails_only_that_size(bpm_lib):
+    # host-side fault injection: the next batch launch of N = 1024 fails as a
+    # failed kernel launch would; N = 2048 requests are not affected and the
+    # server serves N = 1024 again afterwards
+    binding.bpm_server_configure(0.6, 64, 128, 1000)
+    rng = np.random.default_rng(11)
+    wls = [inputs.serving_request(rng, nx, 400) for nx in (1024, 2048, 1024, 2048)]
+    plans, outs, tickets = [], [], []
+    binding.bpm_server_inject_launch_failure(1024, 1)
+    try:
+        for wl in wls:
+            plan = binding.Plan(wl, FP32)
+            out = np.empty_like(wl.psi0)
+            tickets.append(binding.bpm_submit(plan.handle, wl.psi0, out))
+            plans.append(plan)
+            outs.append(out)
+        codes = []
+        for t in tickets:
+            try:
+                codes.append(binding.bpm_poll(t, -1))
+            except binding.BpmError as e:
+                codes.append(e.code)
+    finally:
+        binding.bpm_server_inject_launch_failure(1024, 0)
+    assert codes[0] == binding.BPM_ERR_CUDA
+    # the second N = 1024 request failed with it if it shared the bucket then
+    assert codes[2] in (binding.BPM_OK, binding.BPM_ERR_CUDA)
+    for k in (1, 3) if codes[2] != binding.BPM_OK else (1, 2, 3):
+        assert codes[k] == binding.BPM_OK
+        assert max(band_errors(outs[k], _alone(wls[k]))) <= TOL_FP32
+    # a new N = 1024 request on a failed request's plan succeeds
+    out = np.empty_like(wls[0].psi0)
+    t = binding.bpm_submit(plans[0].handle, wls[0].psi0, out)
+    assert binding.bpm_poll(t, -1) == binding.BPM_OK
+    assert max(band_errors(out, _alone(wls[0]))) <= TOL_FP32
+    for p in plans:
+        p.close()
+
+
 def test_admission_respects_memory_budget_and_order(bpm_lib):
     # budget big enough for about one request at a time
     wl = inputs.serving_request(np.random.default_rng(5), 4096, 300)
