@@ -10,9 +10,22 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/bpm.h"
 
 namespace bpm {
+
+// NVTX range over a host-side phase (plan, slice preparation, march,
+// launch-shape trials, server admission / batches / retirement), seen by
+// Nsight tools (e.g. ncu --nvtx --nvtx-include "bpm_propagate/"); a no-op
+// without a tool attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr int kMinLogN = 3;
 constexpr int kMaxLogN = 14;          // nx <= 16384

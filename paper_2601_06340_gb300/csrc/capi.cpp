@@ -277,6 +277,7 @@ static double time_trial(bpm_plan_s* plan, PlanAux* aux, const LaunchShape& sh, 
 
 static LaunchShape choose_shape(bpm_plan_s* plan, PlanAux* aux, const void* state, int n_begin,
                                 int steps, cudaStream_t st) {
+  NvtxRange nvtx("bpm_launch_shape_search");
   LaunchShape rule;
   const int nb = plan->nb, logn = plan->logn;
   if (plan->split == BPM_SPLIT_VERLET) {   // one kernel form marches this splitting
@@ -585,6 +586,7 @@ static int make_plan(const bpm_problem* p, int ny, double dy_um, double y0_um,
 extern "C" {
 
 int bpm_plan(const bpm_problem* p, bpm_plan_t* out) {
+  NvtxRange nvtx("bpm_plan");
   if (!out) return fail(BPM_ERR_INVALID, "out is NULL");
   *out = nullptr;
   std::string why;
@@ -593,6 +595,7 @@ int bpm_plan(const bpm_problem* p, bpm_plan_t* out) {
 }
 
 int bpm_plan3d(const bpm_problem* p, int32_t ny, double dy_um, double y0_um, bpm_plan_t* out) {
+  NvtxRange nvtx("bpm_plan3d");
   if (!out) return fail(BPM_ERR_INVALID, "out is NULL");
   *out = nullptr;
   std::string why;
@@ -773,6 +776,7 @@ static int finish_status(bpm_plan_s* plan, cudaStream_t st) {
 
 int bpm_propagate(bpm_plan_t plan, const double* psi_in, double* psi_out, void* records,
                   double* powers, int32_t n_begin, int32_t n_end) {
+  NvtxRange nvtx("bpm_propagate");
   if (!plan) return fail(BPM_ERR_INVALID, "plan is NULL");
   if (!psi_in || !psi_out) return fail(BPM_ERR_INVALID, "psi_in / psi_out is NULL");
   std::lock_guard<std::mutex> lk(plan->mu);
@@ -858,6 +862,7 @@ int bpm_propagate(bpm_plan_t plan, const double* psi_in, double* psi_out, void* 
 
 int bpm_propagate_device(bpm_plan_t plan, const void* d_psi_in, void* d_psi_out, void* d_records,
                          void* d_powers, int32_t n_begin, int32_t n_end, void* stream) {
+  NvtxRange nvtx("bpm_propagate_device");
   if (!plan) return fail(BPM_ERR_INVALID, "plan is NULL");
   if (!d_psi_in || !d_psi_out) return fail(BPM_ERR_INVALID, "d_psi_in / d_psi_out is NULL");
   std::lock_guard<std::mutex> lk(plan->mu);

@@ -440,6 +440,7 @@ int prepare_fast(bpm_plan_s* plan, const PrepParams& q, cudaStream_t st, bool sy
 }  // namespace
 
 int prepare_slices(bpm_plan_s* plan, cudaStream_t st, bool sync) {
+  NvtxRange nvtx("bpm_prepare_slices");
   const size_t phasor_bytes = plane_of(plan) * plan->nz *
                               (plan->precision == BPM_FP32_FUSED ? 8 : 16);
   if (!plan->d_phasor) {

@@ -196,6 +196,7 @@ void release(Server& s, Request& r) {
 
 // Allocate and stage a request (stream-ordered on io_stream).
 int admit_device(Server& s, Request& r) {
+  NvtxRange nvtx("bpm_server_admit");
   bpm_plan_s* p = r.plan;
   const size_t n = p->nx, nb = p->nb, cs = csize_of(p);
   cudaStream_t st = s.io_stream;
@@ -246,6 +247,7 @@ int admit_device(Server& s, Request& r) {
 // Enqueue the end of a request on out_stream: common phase, conversion to
 // c128, final powers, copies into the pinned staging; completion is an event.
 int retire_enqueue(Server& s, Request& r) {
+  NvtxRange nvtx("bpm_server_retire");
   bpm_plan_s* p = r.plan;
   const size_t n = p->nx, nb = p->nb, cs = csize_of(p);
   std::vector<double2> g;
@@ -378,6 +380,7 @@ int cluster_demand(Server& s) {
 // rows as that layout keeps resident, in round-robin order over the members
 // that still have steps to enqueue.
 int launch_batch(Server& s, Bucket& b) {
+  NvtxRange nvtx("bpm_server_batch");
   Batch bt = take_batch(b);
   const bool fp32 = b.members.front()->plan->precision == BPM_FP32_FUSED;
   const int logn = b.members.front()->plan->logn;   // one size per bucket
