@@ -150,7 +150,7 @@ int bpm_set_strain(bpm_plan_t plan, int32_t kind, const double* ux_um,
  * step, and Verlet for 256 <= nx <= 4096 (one CTA per solve; half-step
  * couplings on either side of the full-step propagation); 3D plans take the
  * first-order step only; other combinations return BPM_ERR_INVALID.
- * bpm_submit refuses FP32 plans set to Verlet (BPM_ERR_INVALID).
+ * bpm_submit takes FP32 plans set to Verlet (one CTA per row as well).
  * BPM_ERR_BUSY while tickets are pending. */
 enum bpm_splitting {
   BPM_SPLIT_FIRST_ORDER = 0,

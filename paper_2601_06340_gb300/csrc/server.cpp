@@ -398,8 +398,14 @@ int launch_batch(Server& s, Bucket& b) {
     const bool cluster = layout < 0 && 2 * int(b.members.size()) <= s.sm_count;
     limit = size_t(std::max(1, layout == kLayoutSplit4 ? fused_split4_capacity()
                                                        : fused_launch_capacity(logn, cluster)));
+    // second-order (Verlet) rows march one CTA per row on the kernel's
+    // half-step form; a batch holding any stays within its residency
+    for (auto& r : b.members)
+      if (r->plan->split == BPM_SPLIT_VERLET)
+        limit = std::min(limit, size_t(std::max(1, fused_half_capacity(logn))));
   }
-  std::map<int, std::vector<RowDescF32>> groups;   // FP32 rows by step count
+  // FP32 rows by (step count, splitting): key 2 * steps + (Verlet ? 1 : 0)
+  std::map<int, std::vector<RowDescF32>> groups;
   std::vector<RowDescF32> rows;
   cudaMemsetAsync(bt.d_status, 0, sizeof(int), b.st);
   const size_t nm = b.members.size();
@@ -424,7 +430,7 @@ int launch_batch(Server& s, Bucket& b) {
     fused_rows(p, static_cast<float2*>(r->d_state), static_cast<float2*>(r->d_rec), r->d_pow,
                n0, n0 + steps, &rows);
     for (auto& d : rows) d.n_phase0 = 0;
-    auto& g = groups[steps];
+    auto& g = groups[2 * steps + (p->split == BPM_SPLIT_VERLET ? 1 : 0)];
     g.insert(g.end(), rows.begin(), rows.end());
   }
   b.rr = nm ? (b.rr + bt.items.size()) % nm : 0;
@@ -464,8 +470,10 @@ int launch_batch(Server& s, Bucket& b) {
         bt.err = fail(BPM_ERR_CUDA, "injected launch failure");
         break;
       }
-      bt.err = launch_fused_layout(logn, b.d_rows + off, int(kv.second.size()), kv.first,
-                                   s.d_tw[logn], bt.d_status, b.st, layout);
+      const bool verlet = (kv.first & 1) != 0;
+      bt.err = launch_fused_layout(logn, b.d_rows + off, int(kv.second.size()), kv.first >> 1,
+                                   s.d_tw[logn], bt.d_status, b.st,
+                                   verlet ? kLayoutCtaHalf : layout);
       off += kv.second.size();
     }
   }
@@ -661,8 +669,9 @@ int bpm_submit(bpm_plan_t plan, const double* psi_in, double* psi_out, void* rec
     return fail(BPM_ERR_INVALID, "plan, psi_in, psi_out and out must be non-NULL");
   *out = 0;
   if (plan->ny > 1) return fail(BPM_ERR_INVALID, "the server takes 2D plans only");
-  if (plan->precision == BPM_FP32_FUSED && plan->split != BPM_SPLIT_FIRST_ORDER)
-    return fail(BPM_ERR_INVALID, "the server marches FP32 plans with first-order splitting only");
+  if (plan->precision == BPM_FP32_FUSED && plan->split != BPM_SPLIT_FIRST_ORDER &&
+      plan->split != BPM_SPLIT_VERLET)
+    return fail(BPM_ERR_INVALID, "the server marches FP32 plans first order or Verlet");
   Server& s = srv();
   auto r = std::make_shared<Request>();
   r->plan = plan;

@@ -95,6 +95,30 @@ def test_injected_launch_failure_fails_only_that_size(bpm_lib):
         p.close()
 
 
+def test_verlet_requests_share_the_server_with_first_order_ones(bpm_lib):
+    # FP32 plans set to Verlet march on the one-CTA half-step kernel in their
+    # own launch group; each result equals the same plan marched alone
+    binding.bpm_server_configure(0.6, 64, 128, 1000)
+    V, F = binding.BPM_SPLIT_VERLET, binding.BPM_SPLIT_FIRST_ORDER
+    specs = [(512, V), (512, F), (1024, V), (4096, V), (4096, F), (2048, F)]
+    rng = np.random.default_rng(21)
+    wls = [inputs.serving_request(rng, nx, 300) for nx, _ in specs]
+    plans = [binding.Plan(wl, FP32, splitting=sp) for wl, (_, sp) in zip(wls, specs)]
+    outs = [np.empty_like(wl.psi0) for wl in wls]
+    try:
+        tickets = [binding.bpm_submit(p.handle, wl.psi0, o) for p, wl, o in zip(plans, wls, outs)]
+        for t in tickets:
+            assert binding.bpm_poll(t, -1) == binding.BPM_OK
+        for p, wl, o, (_, sp) in zip(plans, wls, outs, specs):
+            alone = p.propagate(records=False, powers=False).psi
+            errs = band_errors(o, alone)
+            # the same kernel and steps: Verlet rows agree to rounding
+            assert max(errs) <= (1e-6 if sp == V else TOL_FP32), (sp, errs)
+    finally:
+        for p in plans:
+            p.close()
+
+
 def test_admission_respects_memory_budget_and_order(bpm_lib):
     # budget big enough for about one request at a time
     wl = inputs.serving_request(np.random.default_rng(5), 4096, 300)

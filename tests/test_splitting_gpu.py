@@ -39,9 +39,6 @@ def test_splitting_refused_where_not_built(bpm_lib):
         binding.bpm_set_splitting(plan.handle, binding.BPM_SPLIT_VERLET)
         with pytest.raises(binding.BpmError):
             binding.bpm_set_splitting(plan.handle, binding.BPM_SPLIT_FOREST_RUTH)
-        # the request server marches first-order FP32 plans only
-        with pytest.raises(binding.BpmError):
-            binding.bpm_submit(plan.handle, wl.psi0, np.empty_like(wl.psi0))
     with binding.Plan(inputs.laue_perfect(nx=128, nz=10), FP32) as plan:
         with pytest.raises(binding.BpmError):
             binding.bpm_set_splitting(plan.handle, binding.BPM_SPLIT_VERLET)
