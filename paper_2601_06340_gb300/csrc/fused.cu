@@ -1,4 +1,5 @@
 // Dispatch of the fused FP32 march by transform size.
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 
@@ -150,13 +151,18 @@ static void fused_cfg(int logn, int* smem, int* rows, int* threads) {
   }
 }
 
+// The lazily filled caches below are atomics: the request server's worker
+// thread and callers' threads reach them concurrently (every writer stores
+// the same value).
 static int sm_count() {
-  static int sms = 0;
+  static std::atomic<int> cached{0};
+  int sms = cached.load(std::memory_order_relaxed);
   if (sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
+    cached.store(sms, std::memory_order_relaxed);
   }
   return sms;
 }
@@ -166,8 +172,9 @@ static int sm_count() {
 // layout, where every row already has its own SMs.
 int fused_rows_resident(int logn, int n_rows) {
   if (logn >= kSplitLogN || use_cluster_layout(logn, n_rows)) return 0;
-  static int cache[kMaxLogN + 1] = {};
-  if (cache[logn] == 0) {
+  static std::atomic<int> cache[kMaxLogN + 1] = {};
+  int c = cache[logn].load(std::memory_order_relaxed);
+  if (c == 0) {
     int r = 1;
     switch (logn) {
       case 3: r = fused_rows_resident_3(); break;
@@ -181,18 +188,20 @@ int fused_rows_resident(int logn, int n_rows) {
       case 11: r = fused2_rows_resident_11(); break;
       default: r = fused2_rows_resident_12(); break;
     }
-    cache[logn] = r * sm_count();
+    c = r * sm_count();
+    cache[logn].store(c, std::memory_order_relaxed);
   }
-  return cache[logn];
+  return c;
 }
 
 // Rows one launch of the given layout keeps resident on the whole GPU:
 // clusters for the cluster kernels (N >= 8192 always, 512..4096 when
 // `cluster`), else CTA rows per SM times the SMs.
 int fused_launch_capacity(int logn, bool cluster) {
-  static int cache[2][kMaxLogN + 1] = {};
+  static std::atomic<int> cache[2][kMaxLogN + 1] = {};
   const bool cl = logn >= kSplitLogN || (cluster && logn >= 9 && logn <= 12);
-  int& c = cache[cl ? 1 : 0][logn];
+  std::atomic<int>& slot = cache[cl ? 1 : 0][logn];
+  int c = slot.load(std::memory_order_relaxed);
   if (c == 0) {
     if (cl) {
       switch (logn) {
@@ -219,14 +228,16 @@ int fused_launch_capacity(int logn, bool cluster) {
       }
       c = r * sm_count();
     }
+    slot.store(c, std::memory_order_relaxed);
   }
   return c;
 }
 
 // Rows one launch of the second-order (Verlet) CTA kernel keeps resident.
 int fused_half_capacity(int logn) {
-  static int cache[kMaxLogN + 1] = {};
-  if (cache[logn] == 0) {
+  static std::atomic<int> cache[kMaxLogN + 1] = {};
+  int c = cache[logn].load(std::memory_order_relaxed);
+  if (c == 0) {
     int r = 1;
     switch (logn) {
       case 8: r = fused2h_rows_resident_8(); break;
@@ -235,15 +246,20 @@ int fused_half_capacity(int logn) {
       case 11: r = fused2h_rows_resident_11(); break;
       default: r = fused2h_rows_resident_12(); break;
     }
-    cache[logn] = r * sm_count();
+    c = r * sm_count();
+    cache[logn].store(c, std::memory_order_relaxed);
   }
-  return cache[logn];
+  return c;
 }
 
 // Rows of N = 4096 one half-band-split launch keeps resident (4-CTA clusters).
 int fused_split4_capacity() {
-  static int c = 0;
-  if (c == 0) c = fused4h_rows_resident_12();
+  static std::atomic<int> cached{0};
+  int c = cached.load(std::memory_order_relaxed);
+  if (c == 0) {
+    c = fused4h_rows_resident_12();
+    cached.store(c, std::memory_order_relaxed);
+  }
   return c;
 }
 

@@ -2,6 +2,7 @@
 // separate translation units so they compile in parallel).
 #pragma once
 
+#include <atomic>
 #include <cstdlib>
 
 #include "fused_kernel.cuh"
@@ -14,10 +15,12 @@ namespace bpm {
 
 // Butterfly-constant policy: hi+lo constants (default) unless BPM_FUSED_EXACT=0.
 inline bool fused_exact_constants() {
-  static int v = -1;
+  static std::atomic<int> cached{-1};
+  int v = cached.load(std::memory_order_relaxed);
   if (v < 0) {
     const char* e = std::getenv("BPM_FUSED_EXACT");
     v = (e && e[0] == '0') ? 0 : 1;
+    cached.store(v, std::memory_order_relaxed);
   }
   return v == 1;
 }
@@ -26,13 +29,13 @@ template <int LOGN>
 int fused_launch_impl(const RowDescF32* d_rows, int n_rows, int steps,
                       const float4* d_tw, int* d_status, cudaStream_t st) {
   using C = FusedCfg<LOGN>;
-  static bool configured = false;
-  if (!configured) {
+  static std::atomic<bool> configured{false};
+  if (!configured.load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(fused_march_kernel<LOGN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          C::SMEM);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused)");
-    configured = true;
+    configured.store(true, std::memory_order_release);
   }
   const int grid = (n_rows + C::ROWS - 1) / C::ROWS;
   fused_march_kernel<LOGN><<<grid, C::THREADS, C::SMEM, st>>>(d_rows, n_rows, steps,
@@ -48,12 +51,12 @@ template <int LOGN, bool EX, bool HALF = false>
 int fused2_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const float4* d_tw,
                        int* d_status, cudaStream_t st) {
   using C = F2Cfg<LOGN, HALF ? 2 : 1>;
-  static bool configured = false;
-  if (!configured) {
+  static std::atomic<bool> configured{false};
+  if (!configured.load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(fused2_march_kernel<LOGN, EX, HALF>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused2)");
-    configured = true;
+    configured.store(true, std::memory_order_release);
   }
   const int grid = (n_rows + C::ROWS - 1) / C::ROWS;
   fused2_march_kernel<LOGN, EX, HALF><<<grid, C::THREADS, C::SMEM, st>>>(d_rows, n_rows, steps,
@@ -69,12 +72,12 @@ template <bool EX>
 int fused4h_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const float4* d_tw,
                         int* d_status, cudaStream_t st) {
   using C = F4ECfg<11>;
-  static bool configured = false;
-  if (!configured) {
+  static std::atomic<bool> configured{false};
+  if (!configured.load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(fused4e_march_kernel<11, EX>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused4h)");
-    configured = true;
+    configured.store(true, std::memory_order_release);
   }
   fused4e_march_kernel<11, EX><<<4 * n_rows, C::T, C::SMEM, st>>>(d_rows, n_rows, steps, d_tw,
                                                                   d_status);
@@ -117,12 +120,12 @@ template <int LOGN, bool EX>
 int fused3_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const float4* d_tw,
                        int* d_status, cudaStream_t st) {
   using C = F3Cfg<LOGN>;
-  static bool configured = false;
-  if (!configured) {
+  static std::atomic<bool> configured{false};
+  if (!configured.load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(fused3_march_kernel<LOGN, EX>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused3)");
-    configured = true;
+    configured.store(true, std::memory_order_release);
   }
   fused3_march_kernel<LOGN, EX><<<2 * n_rows, C::T, C::SMEM, st>>>(d_rows, n_rows, steps, d_tw,
                                                                   d_status);
@@ -143,11 +146,11 @@ int fused4_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
   }();
   constexpr int smem = P == 2 ? F4ECfg<12>::SMEM : F4TCfg::SMEM;
   constexpr int threads = P == 2 ? F4ECfg<12>::T : F4TCfg::T;
-  static bool configured = false;
-  if (!configured) {
+  static std::atomic<bool> configured{false};
+  if (!configured.load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused4)");
-    configured = true;
+    configured.store(true, std::memory_order_release);
   }
   kern<<<2 * P * n_rows, threads, smem, st>>>(d_rows, n_rows, steps, d_tw, d_status);
   cudaError_t e = cudaGetLastError();

@@ -1,4 +1,5 @@
 // Launchers and host loop of the 3D march (kernels in vol_kernel.cuh).
+#include <atomic>
 #include <string>
 
 #include "fused_launch.cuh"
@@ -9,11 +10,11 @@ namespace bpm {
 namespace {
 
 template <typename K>
-int set_smem(K kernel, int bytes, bool* done, const char* what) {
-  if (*done) return BPM_OK;
+int set_smem(K kernel, int bytes, std::atomic<bool>* done, const char* what) {
+  if (done->load(std::memory_order_acquire)) return BPM_OK;
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return cuda_fail(e, what);
-  *done = true;
+  done->store(true, std::memory_order_release);
   return BPM_OK;
 }
 
@@ -38,7 +39,7 @@ int col_launch(const VolParams& p, cudaStream_t st) {
 // capture (the first launch would set them too, but not inside a capture).
 template <bool EX>
 int prepare_kernels(int lognx, int logny) {
-  static bool done[2][16] = {};
+  static std::atomic<bool> done[2][16] = {};   // callers' and server threads
   auto row = [&](auto kern, int bytes) { return set_smem(kern, bytes, &done[0][lognx], "vol row"); };
   auto col = [&](auto kern, int bytes) { return set_smem(kern, bytes, &done[1][logny], "vol col"); };
   int rc = BPM_OK;
