@@ -196,10 +196,21 @@ int bpm_propagate(bpm_plan_t plan, const double* psi_in, double* psi_out,
  * FP32 plans and c128 for FP64 plans (may alias).  d_records: device
  * buffer as in bpm_propagate or NULL.  d_powers: device double
  * [B][n_rec+1][2] or NULL.  The call returns after enqueueing; the caller
- * synchronises the stream before reading outputs or freeing inputs. */
+ * synchronises the stream before reading outputs or freeing inputs.
+ * Marches of one plan share its device scratch (row descriptors, phase
+ * factors, the FP64 state): enqueue them on one stream, or order the
+ * streams.  An expired bounded wait inside a march is reported by
+ * bpm_device_status (or by the plan's next bpm_propagate). */
 int bpm_propagate_device(bpm_plan_t plan, const void* d_psi_in,
                          void* d_psi_out, void* d_records, void* d_powers,
                          int32_t n_begin, int32_t n_end, void* stream);
+
+/* Status of the plan's device marches so far: reads the plan's status word
+ * on `stream` (after the work enqueued there), waits for it and clears it.
+ * BPM_ERR_TIMEOUT if a bounded device wait (strain-slice copy or peer-CTA
+ * data) expired in one of them, else BPM_OK; BPM_ERR_INVALID for a NULL
+ * plan, BPM_ERR_CUDA if the stream failed.  Blocks the host. */
+int bpm_device_status(bpm_plan_t plan, void* stream);
 
 /* Energy -> time synthesis of a batch of exit fields (Section
  * "Time-Dependent Simulation"): out[b][x][m] = (1/B) sum_j in[j][b][x]

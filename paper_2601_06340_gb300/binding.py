@@ -75,6 +75,7 @@ _SIGS = {
     "bpm_version": ([], ctypes.c_char_p),
     "bpm_selftest_wait_expiry": ([ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "bpm_server_inject_launch_failure": ([_I, _I], ctypes.c_int),
+    "bpm_device_status": ([_P, _P], ctypes.c_int),
 }
 
 
@@ -185,6 +186,12 @@ def bpm_poll(ticket, timeout_ms=0) -> int:
 def bpm_server_configure(mem_fraction=0.0, max_active=0, epoch_steps=0, max_queue=0):
     return _check(load().bpm_server_configure(float(mem_fraction), int(max_active),
                                               int(epoch_steps), int(max_queue)))
+
+
+def bpm_device_status(plan, stream=None) -> int:
+    """BPM_OK, or raises BpmError (BPM_ERR_TIMEOUT) if a bounded device wait
+    expired in the plan's device marches enqueued on `stream` so far."""
+    return _check(load().bpm_device_status(plan, stream))
 
 
 def bpm_server_inject_launch_failure(nx: int, count: int):

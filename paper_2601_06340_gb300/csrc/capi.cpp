@@ -769,7 +769,7 @@ static int finish_status(bpm_plan_s* plan, cudaStream_t st) {
   if (status & kStatusWaitTimeout) {
     cudaMemsetAsync(plan->d_status, 0, sizeof(int), st);
     cudaStreamSynchronize(st);
-    return fail(BPM_ERR_TIMEOUT, "a bounded wait for a strain slice expired on the device");
+    return fail(BPM_ERR_TIMEOUT, "a bounded wait (strain slice or peer data) expired on the device");
   }
   return BPM_OK;
 }
@@ -886,6 +886,12 @@ int bpm_propagate_device(bpm_plan_t plan, const void* d_psi_in, void* d_psi_out,
   if (e != cudaSuccess) return cuda_fail(e, "copy input");
   return enqueue_march(plan, aux, plan->d_state, rec, static_cast<double*>(d_powers), n_begin,
                        n_end, d_psi_out, true, st);
+}
+
+int bpm_device_status(bpm_plan_t plan, void* stream) {
+  if (!plan) return fail(BPM_ERR_INVALID, "plan is NULL");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  return finish_status(plan, static_cast<cudaStream_t>(stream));
 }
 
 int bpm_omega_to_t_device(const void* d_in, void* d_out, int32_t n_energy, int32_t nx,

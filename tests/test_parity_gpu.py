@@ -245,6 +245,8 @@ def test_device_api_with_torch_tensors(bpm_lib):
         pw = torch.zeros((1, plan.n_rec + 1, 2), dtype=torch.float64, device=dev)
         st = torch.cuda.current_stream()
         binding.bpm_propagate_device(plan.handle, x, y, rec, pw, 0, wl.nz, st.cuda_stream)
+        # no bounded device wait expired in the march
+        assert binding.bpm_device_status(plan.handle, st.cuda_stream) == binding.BPM_OK
         st.synchronize()
     assert np.array_equal(y.cpu().numpy().astype(np.complex128), ref.psi.astype(np.complex64))
     assert np.array_equal(rec.cpu().numpy(), ref.records)
