@@ -200,7 +200,11 @@ int bpm_propagate(bpm_plan_t plan, const double* psi_in, double* psi_out,
  * Marches of one plan share its device scratch (row descriptors, phase
  * factors, the FP64 state): enqueue them on one stream, or order the
  * streams.  An expired bounded wait inside a march is reported by
- * bpm_device_status (or by the plan's next bpm_propagate). */
+ * bpm_device_status (or by the plan's next bpm_propagate).  Not capturable
+ * into a CUDA graph: while `stream` is capturing the call returns
+ * BPM_ERR_INVALID and enqueues nothing (a march uploads per-call row
+ * descriptors and phase factors from host memory; 3D plans replay a graph
+ * of their own). */
 int bpm_propagate_device(bpm_plan_t plan, const void* d_psi_in,
                          void* d_psi_out, void* d_records, void* d_powers,
                          int32_t n_begin, int32_t n_end, void* stream);
@@ -307,8 +311,8 @@ int bpm_march_f64_noalloc(void* d_psi, int32_t nx, int32_t n_rows, const void* d
  * 512 <= nx <= 4096, or rotation chunks of 64..512 steps) times each on a
  * short march of a scratch copy of the state the first time a given
  * (nx, rows) is marched, blocking the host for those trials, and keeps the
- * fastest for the process; BPM_AUTOTUNE=0 in the environment, a single row
- * or a stream under graph capture leaves the fixed rule in charge.  Either
+ * fastest for the process; BPM_AUTOTUNE=0 in the environment or a single
+ * row leaves the fixed rule in charge.  Either
  * pointer may be NULL.  BPM_ERR_INVALID for a NULL plan. */
 int bpm_launch_shape(bpm_plan_t plan, int32_t* layout, int32_t* chunk);
 

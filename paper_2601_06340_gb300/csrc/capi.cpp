@@ -871,6 +871,14 @@ int bpm_propagate_device(bpm_plan_t plan, const void* d_psi_in, void* d_psi_out,
   if (rc != BPM_OK) return rc;
   PlanAux* aux = aux_of(plan);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // A march uploads per-call row descriptors and phase factors from host
+  // memory; a captured graph would replay those copies from freed memory,
+  // so capture is refused before anything is enqueued.
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t ce = cudaStreamIsCapturing(st, &cs);
+  if (ce != cudaSuccess) return cuda_fail(ce, "stream capture status");
+  if (cs != cudaStreamCaptureStatusNone)
+    return fail(BPM_ERR_INVALID, "bpm_propagate_device cannot be captured into a CUDA graph");
   if (plan->slices_dirty && (rc = prepare_slices(plan, aux->stream)) != BPM_OK) return rc;
   const size_t bytes = size_t(plan->nb) * 2 * plane_of(plan) * csize(plan);
   void* rec = plan->n_rec > 0 ? d_records : nullptr;

@@ -252,6 +252,32 @@ def test_device_api_with_torch_tensors(bpm_lib):
     assert np.array_equal(rec.cpu().numpy(), ref.records)
 
 
+@pytest.mark.filterwarnings("ignore:The CUDA Graph is empty")
+def test_device_api_refuses_graph_capture(bpm_lib):
+    # the march uploads per-call descriptors from host memory, which a graph
+    # would replay from freed memory: capture is refused before any work
+    torch = pytest.importorskip("torch")
+    wl = _reduced("laue_perfect")
+    dev = torch.device("cuda:0")
+    x = torch.from_numpy(wl.psi0.astype(np.complex64)).to(dev)
+    y = torch.empty_like(x)
+    with binding.Plan(wl, FP32) as plan:
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with pytest.raises(binding.BpmError) as e:
+            with torch.cuda.graph(g, stream=s):
+                binding.bpm_propagate_device(plan.handle, x, y, None, None, 0, wl.nz,
+                                             s.cuda_stream)
+        assert e.value.code == binding.BPM_ERR_INVALID
+        torch.cuda.synchronize()
+        # the plan still marches outside a capture
+        binding.bpm_propagate_device(plan.handle, x, y, None, None, 0, wl.nz,
+                                     torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+    ref = run_gpu(wl, FP32)
+    assert np.array_equal(y.cpu().numpy().astype(np.complex128), ref.psi.astype(np.complex64))
+
+
 def test_omega_to_t_matches_oracle(bpm_lib):
     torch = pytest.importorskip("torch")
     rng = np.random.default_rng(11)
