@@ -50,6 +50,11 @@ struct F2Cfg {
   static constexpr int OFF_TW1 = OFF_RED + ROWS * WPR * 2 * 8;        // [S1][16] float2
   static constexpr int SMEM = OFF_TW1 + S1 * 16 * 8;
   static_assert(LOGN >= 8 && LOGN <= 12, "band-per-thread kernel covers 256..4096");
+  // layout checks: fits one SM (227 KB); bulk-copy and 16-byte store
+  // targets 16-byte aligned; mbarriers 8-byte aligned
+  static_assert(SMEM <= 232448, "fits one SM");
+  static_assert(OFF_PH % 16 == 0 && (N * 8) % 16 == 0, "bulk copy of a slice");
+  static_assert(OFF_MBAR % 8 == 0, "mbarrier alignment");
   __host__ __device__ static constexpr int radix(int p) { return p < NP - 1 ? 16 : RL; }
   __host__ __device__ static constexpr int len(int p) { return N >> (4 * p); }
   __host__ __device__ static constexpr int stride(int p) { return len(p) / radix(p); }

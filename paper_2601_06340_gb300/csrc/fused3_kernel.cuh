@@ -43,6 +43,11 @@ struct F3Cfg {
   static constexpr int OFF_RED = OFF_RECPH + 8;           // [WARPS] double
   static constexpr int SMEM = OFF_RED + WARPS * 8;
   static_assert(LOGN >= 9 && LOGN <= 12, "cluster kernel covers 512..4096");
+  // layout checks: fits one SM (227 KB); bulk-copy and 16-byte store
+  // targets 16-byte aligned; mbarriers 8-byte aligned
+  static_assert(SMEM <= 232448, "fits one SM");
+  static_assert(OFF_X % 16 == 0 && OFF_PH % 16 == 0, "16-byte stores and bulk copy");
+  static_assert(OFF_MBAR % 8 == 0 && OFF_XBAR % 8 == 0, "mbarrier alignment");
 };
 
 __device__ __forceinline__ uint32_t mapa_u32(uint32_t addr, uint32_t rank) {

@@ -71,6 +71,13 @@ struct F4ECfg {
   static constexpr int SMEM = OFF_PART + 8;
   static_assert(SMEM <= 232448, "fits one SM");
   static_assert(LM == 11 || LM == 12, "N = 4096 or 8192");
+  // layout checks: fits one SM (227 KB); bulk-copy and 16-byte store
+  // targets 16-byte aligned; mbarriers 8-byte aligned
+  static_assert(OFF_G % 16 == 0 && OFF_C % 16 == 0 && OFF_PH % 16 == 0,
+                "16-byte stores and bulk copy");
+  static_assert(OFF_MBAR % 8 == 0 && OFF_GBAR % 8 == 0 && OFF_CBAR % 8 == 0 &&
+                    OFF_PPEER % 8 == 0,
+                "mbarrier and 8-byte store alignment");
 };
 
 // Spectral index of position `pos` of the local forward transform's output

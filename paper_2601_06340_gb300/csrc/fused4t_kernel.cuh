@@ -64,6 +64,13 @@ struct F4TCfg {
   static constexpr int OFF_TMEM = OFF_PART + 8;            // allocated TMEM address
   static constexpr int SMEM = OFF_TMEM + 8;
   static_assert(SMEM <= 232448, "fits one SM");
+  // layout checks: fits one SM (227 KB); bulk-copy and 16-byte store
+  // targets 16-byte aligned; mbarriers 8-byte aligned
+  static_assert(OFF_G % 16 == 0 && OFF_C % 16 == 0 && OFF_PH % 16 == 0,
+                "16-byte stores and bulk copy");
+  static_assert(OFF_MBAR % 8 == 0 && OFF_GBAR % 8 == 0 && OFF_FREE % 8 == 0 &&
+                    OFF_CBAR % 8 == 0 && OFF_PPEER % 8 == 0,
+                "mbarrier and 8-byte store alignment");
 };
 
 __device__ __forceinline__ void mbar_init_count(uint64_t* bar, uint32_t count) {

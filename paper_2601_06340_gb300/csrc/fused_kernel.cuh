@@ -55,6 +55,11 @@ struct FusedCfg {
   static constexpr int OFF_RECPH = OFF_MBAR + ROWS * 8;              // [ROWS] float2
   static constexpr int OFF_RED = OFF_RECPH + ROWS * 8;               // [ROWS][WARPS][2] double
   static constexpr int SMEM = OFF_RED + ROWS * WARPS_PER_ROW * 2 * 8;
+  // layout checks: fits one SM (227 KB); bulk-copy and 16-byte store
+  // targets 16-byte aligned; mbarriers 8-byte aligned
+  static_assert(SMEM <= 232448, "fits one SM");
+  static_assert(OFF_PH % 16 == 0 && (N * 8) % 16 == 0, "bulk copy of a slice");
+  static_assert(OFF_MBAR % 8 == 0, "mbarrier alignment");
 
   __host__ __device__ static constexpr int radix(int p) { return p < NP - 1 ? 16 : RL; }
   __host__ __device__ static constexpr int len(int p) { return N >> (4 * p); }

@@ -55,6 +55,7 @@ struct VolRowCfg {
   static constexpr int OFF_TW1 = OFF_BUF + 2 * PADN * 8;          // [S1][16]
   static constexpr int OFF_RED = OFF_TW1 + S1 * 16 * 8;           // [WARPS][2] double
   static constexpr int SMEM = OFF_RED + WARPS * 2 * 8;
+  static_assert(SMEM <= 232448, "fits one SM");
 };
 
 template <int LOGN, bool EX>
@@ -213,6 +214,7 @@ struct VolColCfg {
   static constexpr int OFF_TW1 = OFF_BUF + COLS * PADC * 8;       // [S1][16]
   static constexpr int SMEM = OFF_TW1 + S1 * 16 * 8;
   static_assert(THREADS >= 64 && THREADS <= 256, "Ny in [256, 1024]");
+  static_assert(SMEM <= 232448, "fits one SM");
 };
 
 template <int LOGN, bool EX>
