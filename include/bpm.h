@@ -200,11 +200,13 @@ int bpm_propagate(bpm_plan_t plan, const double* psi_in, double* psi_out,
  * Marches of one plan share its device scratch (row descriptors, phase
  * factors, the FP64 state): enqueue them on one stream, or order the
  * streams.  An expired bounded wait inside a march is reported by
- * bpm_device_status (or by the plan's next bpm_propagate).  Not capturable
- * into a CUDA graph: while `stream` is capturing the call returns
- * BPM_ERR_INVALID and enqueues nothing (a march uploads per-call row
- * descriptors and phase factors from host memory; 3D plans replay a graph
- * of their own). */
+ * bpm_device_status (or by the plan's next bpm_propagate).  Graph capture:
+ * FP32 plans (2D and 3D) may be captured into a CUDA graph once they have
+ * marched outside a capture (strain slices prepared, schedule buffers
+ * sized); the march's per-call uploads then travel as kernel parameters,
+ * so a replay repeats the captured march (same buffers, steps and launch
+ * shape -- the fixed rule's).  While `stream` is capturing, FP64 plans and
+ * plans not yet marched return BPM_ERR_INVALID and enqueue nothing. */
 int bpm_propagate_device(bpm_plan_t plan, const void* d_psi_in,
                          void* d_psi_out, void* d_records, void* d_powers,
                          int32_t n_begin, int32_t n_end, void* stream);

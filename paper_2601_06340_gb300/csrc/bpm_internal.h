@@ -182,6 +182,9 @@ void vol_release(bpm_plan_s* plan);   // the captured march, if any
 int plain_march(bpm_plan_s* plan, int n_begin, int n_end, int n_phase0, void* d_records,
                 double* d_powers, cudaStream_t st);
 int launch_convert_in(const double2* src, float2* dst, size_t n, cudaStream_t st);
+// Upload `bytes` of host memory to `dst` through kernel parameters (used
+// while the stream is being captured into a graph).
+int upload_by_params(void* dst, const void* src, size_t bytes, cudaStream_t st);
 int launch_finish_f32(const float2* state, double2* out_c128, float2* out_c64,
                       const double* gphase, int n_rows, int nx, int steps,
                       double dx, double* final_powers, int power_stride,

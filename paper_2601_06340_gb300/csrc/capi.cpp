@@ -163,6 +163,25 @@ void phase_factors(const bpm_plan_s* plan, int steps, std::vector<double2>* out)
 // no row appears twice in a launch, and rows sweeping the same z-range share
 // their strain slices in L2.  A remainder shorter than a chunk runs as a
 // second round of the same kind.
+// Host-to-device upload on the march's stream: a plain async copy, or, while
+// the stream is being captured into a graph, kernel parameters (which the
+// graph keeps; a captured copy would re-read the host memory at replay).
+static bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+static int upload(void* dst, const void* src, size_t bytes, cudaStream_t st, bool captured,
+                  const char* what) {
+  if (captured) return upload_by_params(dst, src, bytes, st);
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+  return e == cudaSuccess ? BPM_OK : cuda_fail(e, what);
+}
+
 static int launch_rotated(bpm_plan_s* plan, PlanAux* aux, const std::vector<RowDescF32>& rows,
                           int n_begin, int steps, int resident, cudaStream_t st, int chunk = 0,
                           int layout = -1) {
@@ -189,7 +208,11 @@ static int launch_rotated(bpm_plan_s* plan, PlanAux* aux, const std::vector<RowD
   };
   round(0, full, chunk);
   if (rem > 0) round(full, full + 1, rem);
+  const bool captured = capturing(st);
   if (aux->sched_cap < sched.size()) {
+    if (captured)
+      return fail(BPM_ERR_INVALID,
+                  "march the plan once outside the graph capture first (launch schedule)");
     if (aux->d_sched) cudaFree(aux->d_sched);
     aux->d_sched = nullptr;
     aux->sched_cap = 0;
@@ -198,9 +221,9 @@ static int launch_rotated(bpm_plan_s* plan, PlanAux* aux, const std::vector<RowD
     if (rc != BPM_OK) return rc;
     aux->sched_cap = sched.size();
   }
-  cudaError_t e = cudaMemcpyAsync(aux->d_sched, sched.data(), sched.size() * sizeof(RowDescF32),
-                                  cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e, "upload launch schedule");
+  int urc = upload(aux->d_sched, sched.data(), sched.size() * sizeof(RowDescF32), st, captured,
+                   "upload launch schedule");
+  if (urc != BPM_OK) return urc;
   for (const Launch& l : launches) {
     int rc = launch_fused_layout(plan->logn, aux->d_sched + l.off, l.count, l.steps,
                                  static_cast<const float4*>(plan->d_tw), plan->d_status, st,
@@ -371,11 +394,12 @@ static LaunchShape choose_shape(bpm_plan_s* plan, PlanAux* aux, const void* stat
 static int enqueue_march(bpm_plan_s* plan, PlanAux* aux, void* state, void* d_rec, double* d_pw,
                          int n_begin, int n_end, void* out, bool out_c128, cudaStream_t st) {
   const int steps = n_end - n_begin;
+  const bool captured = capturing(st);
   std::vector<double2> g;
   phase_factors(plan, steps, &g);
-  cudaError_t e = cudaMemcpyAsync(aux->d_g, g.data(), sizeof(double2) * plan->nb,
-                                  cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e, "upload phase factors");
+  int urc = upload(aux->d_g, g.data(), sizeof(double2) * plan->nb, st, captured,
+                   "upload phase factors");
+  if (urc != BPM_OK) return urc;
   double* final_pw = d_pw ? d_pw + 2 * plan->n_rec : nullptr;
   const int pw_stride = 2 * (plan->n_rec + 1);
   if (plan->ny > 1) {
@@ -401,9 +425,9 @@ static int enqueue_march(bpm_plan_s* plan, PlanAux* aux, void* state, void* d_re
                    : 0;
     int rc = BPM_OK;
     if (!sh.rotated) {
-      e = cudaMemcpyAsync(plan->d_rows, rows.data(), sizeof(RowDescF32) * rows.size(),
-                          cudaMemcpyHostToDevice, st);
-      if (e != cudaSuccess) return cuda_fail(e, "upload row descriptors");
+      rc = upload(plan->d_rows, rows.data(), sizeof(RowDescF32) * rows.size(), st, captured,
+                  "upload row descriptors");
+      if (rc != BPM_OK) return rc;
       rc = launch_fused_layout(plan->logn, static_cast<const RowDescF32*>(plan->d_rows), plan->nb,
                                steps, static_cast<const float4*>(plan->d_tw), plan->d_status, st,
                                sh.layout);
@@ -871,14 +895,20 @@ int bpm_propagate_device(bpm_plan_t plan, const void* d_psi_in, void* d_psi_out,
   if (rc != BPM_OK) return rc;
   PlanAux* aux = aux_of(plan);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // A march uploads per-call row descriptors and phase factors from host
-  // memory; a captured graph would replay those copies from freed memory,
-  // so capture is refused before anything is enqueued.
+  // Under graph capture the march's per-call uploads go through kernel
+  // parameters (see upload); what cannot be captured is refused before
+  // anything is enqueued: FP64 plans (their march uploads per-record phase
+  // factors and swaps buffers on the host) and plans whose strain slices
+  // still have to be prepared (allocation and a host wait).
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaError_t ce = cudaStreamIsCapturing(st, &cs);
   if (ce != cudaSuccess) return cuda_fail(ce, "stream capture status");
-  if (cs != cudaStreamCaptureStatusNone)
-    return fail(BPM_ERR_INVALID, "bpm_propagate_device cannot be captured into a CUDA graph");
+  if (cs != cudaStreamCaptureStatusNone) {
+    if (plan->precision != BPM_FP32_FUSED)
+      return fail(BPM_ERR_INVALID, "FP64 plans cannot be captured into a CUDA graph");
+    if (plan->slices_dirty)
+      return fail(BPM_ERR_INVALID, "march the plan once outside the graph capture first");
+  }
   if (plan->slices_dirty && (rc = prepare_slices(plan, aux->stream)) != BPM_OK) return rc;
   const size_t bytes = size_t(plan->nb) * 2 * plane_of(plan) * csize(plan);
   void* rec = plan->n_rec > 0 ? d_records : nullptr;

@@ -1,5 +1,8 @@
 // Input conversion, output finishing (common phase, final powers) and the
 // energy -> time synthesis of a batch of exit fields.
+#include <algorithm>
+#include <cstring>
+
 #include "bpm_internal.h"
 
 namespace bpm {
@@ -146,6 +149,36 @@ int launch_omega_to_t(const void* d_in, void* d_out, int nb, int nx, int precisi
     }
   }
   return e == cudaSuccess ? BPM_OK : cuda_fail(e, "omega_to_t");
+}
+
+namespace {
+
+// Host bytes carried to the device as a kernel parameter: a launch captured
+// into a CUDA graph keeps its parameters, so the graph replays the data it
+// was captured with (a captured copy from host memory would read that
+// memory again at every replay).  3840 bytes keep a launch's parameters
+// (chunk, pointer, count) within the 4 KB parameter space.
+struct ParamChunk {
+  unsigned char b[3840];
+};
+
+__global__ void param_copy_kernel(unsigned char* dst, ParamChunk c, int bytes) {
+  for (int i = threadIdx.x; i < bytes; i += blockDim.x) dst[i] = c.b[i];
+}
+
+}  // namespace
+
+int upload_by_params(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  const unsigned char* from = static_cast<const unsigned char*>(src);
+  unsigned char* to = static_cast<unsigned char*>(dst);
+  for (size_t off = 0; off < bytes; off += sizeof(ParamChunk)) {
+    ParamChunk c;
+    const size_t n = std::min(bytes - off, sizeof(ParamChunk));
+    std::memcpy(c.b, from + off, n);
+    param_copy_kernel<<<1, 256, 0, st>>>(to + off, c, int(n));
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? BPM_OK : cuda_fail(e, "upload by kernel parameters");
 }
 
 }  // namespace bpm

@@ -252,30 +252,85 @@ def test_device_api_with_torch_tensors(bpm_lib):
     assert np.array_equal(rec.cpu().numpy(), ref.records)
 
 
+def _capture_case(name):
+    rng = np.random.default_rng(8)
+    if name == "cluster N=1024":
+        return inputs.serving_request(rng, 1024, 300), binding.BPM_SPLIT_FIRST_ORDER
+    if name == "split N=4096":
+        return inputs.serving_request(rng, 4096, 300), binding.BPM_SPLIT_FIRST_ORDER
+    if name == "rotated batch 160x4096":
+        return (inputs.pulse_batched(nx=4096, nz=300, n_energy=160, record_every=100),
+                binding.BPM_SPLIT_FIRST_ORDER)
+    if name == "Verlet N=1024":
+        return inputs.serving_request(rng, 1024, 300), binding.BPM_SPLIT_VERLET
+    return (inputs.cube_dislocation_3d(nx=256, ny=256, nz=40, dx_um=0.08, dy_um=0.08,
+                                       dz_um=0.1, cube_um=5.0, fwhm_um=1.5, record_every=10),
+            binding.BPM_SPLIT_FIRST_ORDER)
+
+
+@pytest.mark.parametrize("name", ["cluster N=1024", "split N=4096", "rotated batch 160x4096",
+                                  "Verlet N=1024", "3D 256x256"])
+def test_device_api_graph_capture_replays(bpm_lib, monkeypatch, name):
+    """A device-API march captured into a CUDA graph (its per-call uploads go
+    through kernel parameters) replays to the same bits as the march run
+    directly, twice in a row."""
+    torch = pytest.importorskip("torch")
+    monkeypatch.setenv("BPM_AUTOTUNE", "0")   # both marches take the fixed rule's shape
+    wl, split = _capture_case(name)
+    dev = torch.device("cuda:0")
+    x = torch.from_numpy(wl.psi0.astype(np.complex64)).to(dev)
+    with binding.Plan(wl, FP32, splitting=split) as plan:
+        shape_rec = (wl.batch, plan.n_rec) + tuple(wl.psi0.shape[1:])
+        outs = [(torch.empty_like(x), torch.zeros(shape_rec, dtype=torch.complex64, device=dev),
+                 torch.zeros((wl.batch, plan.n_rec + 1, 2), dtype=torch.float64, device=dev))
+                for _ in range(2)]
+        s = torch.cuda.Stream()
+        y, rec, pw = outs[0]
+        binding.bpm_propagate_device(plan.handle, x, y, rec, pw, 0, wl.nz, s.cuda_stream)
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        y2, rec2, pw2 = outs[1]
+        with torch.cuda.graph(g, stream=s):
+            binding.bpm_propagate_device(plan.handle, x, y2, rec2, pw2, 0, wl.nz, s.cuda_stream)
+        for _ in range(2):
+            y2.zero_()
+            rec2.zero_()
+            pw2.zero_()
+            g.replay()
+            torch.cuda.synchronize()
+            assert torch.equal(y2, y) and torch.equal(rec2, rec) and torch.equal(pw2, pw)
+        assert binding.bpm_device_status(plan.handle, s.cuda_stream) == binding.BPM_OK
+        del g
+    assert torch.isfinite(torch.view_as_real(y)).all() and y.abs().max() > 0
+
+
 @pytest.mark.filterwarnings("ignore:The CUDA Graph is empty")
-def test_device_api_refuses_graph_capture(bpm_lib):
-    # the march uploads per-call descriptors from host memory, which a graph
-    # would replay from freed memory: capture is refused before any work
+def test_device_api_capture_refusals(bpm_lib):
+    """What cannot be captured is refused before anything is enqueued: FP64
+    plans, and plans whose strain slices are not prepared yet."""
     torch = pytest.importorskip("torch")
     wl = _reduced("laue_perfect")
     dev = torch.device("cuda:0")
-    x = torch.from_numpy(wl.psi0.astype(np.complex64)).to(dev)
-    y = torch.empty_like(x)
-    with binding.Plan(wl, FP32) as plan:
-        s = torch.cuda.Stream()
-        g = torch.cuda.CUDAGraph()
-        with pytest.raises(binding.BpmError) as e:
-            with torch.cuda.graph(g, stream=s):
-                binding.bpm_propagate_device(plan.handle, x, y, None, None, 0, wl.nz,
-                                             s.cuda_stream)
-        assert e.value.code == binding.BPM_ERR_INVALID
-        torch.cuda.synchronize()
-        # the plan still marches outside a capture
-        binding.bpm_propagate_device(plan.handle, x, y, None, None, 0, wl.nz,
-                                     torch.cuda.current_stream().cuda_stream)
-        torch.cuda.synchronize()
-    ref = run_gpu(wl, FP32)
-    assert np.array_equal(y.cpu().numpy().astype(np.complex128), ref.psi.astype(np.complex64))
+    for precision, dtype in ((FP64, torch.complex128), (FP32, torch.complex64)):
+        x = torch.from_numpy(wl.psi0.astype(np.complex128)).to(dev).to(dtype)
+        y = torch.empty_like(x)
+        with binding.Plan(wl, precision) as plan:   # never marched: slices not prepared
+            s = torch.cuda.Stream()
+            g = torch.cuda.CUDAGraph()
+            with pytest.raises(binding.BpmError) as e:
+                with torch.cuda.graph(g, stream=s):
+                    binding.bpm_propagate_device(plan.handle, x, y, None, None, 0, wl.nz,
+                                                 s.cuda_stream)
+            assert e.value.code == binding.BPM_ERR_INVALID
+            torch.cuda.synchronize()
+            # the plan still marches outside a capture
+            binding.bpm_propagate_device(plan.handle, x, y, None, None, 0, wl.nz,
+                                         torch.cuda.current_stream().cuda_stream)
+            torch.cuda.synchronize()
+        ref = run_gpu(wl, precision)
+        got = y.cpu().numpy().astype(np.complex128)
+        assert np.array_equal(got, ref.psi if precision == FP64 else
+                              ref.psi.astype(np.complex64).astype(np.complex128))
 
 
 def test_omega_to_t_matches_oracle(bpm_lib):
