@@ -147,8 +147,9 @@ int bpm_set_strain(bpm_plan_t plan, int32_t kind, const double* ux_um,
  *   BPM_SPLIT_FOREST_RUTH: a = (0, t, 1-2t, t), b = (t/2, (1-t)/2, (1-t)/2,
  *                          t/2), t = 1/(2 - 2^(1/3)).
  * FP64 plans take every method.  FP32 (fused) plans take the first-order
- * step, and Verlet for 256 <= nx <= 4096 (one CTA per solve; half-step
- * couplings on either side of the full-step propagation); 3D plans take the
+ * step, and Verlet for 256 <= nx <= 4096 (half-step couplings on either
+ * side of the full-step propagation; one CTA per solve, or at nx = 4096
+ * one 2-CTA cluster per solve while every solve gets two SMs); 3D plans take the
  * first-order step only; other combinations return BPM_ERR_INVALID.
  * bpm_submit takes FP32 plans set to Verlet (one CTA per row as well).
  * BPM_ERR_BUSY while tickets are pending. */
@@ -302,8 +303,9 @@ int bpm_march_f64_noalloc(void* d_psi, int32_t nx, int32_t n_rows, const void* d
                           int32_t n_end, void* stream);
 
 /* Launch shape of the plan's last FP32 march (the fused kernels of the
- * step of Eq. fov10): *layout = 3 one CTA per row with the Verlet step
- * (plans set to BPM_SPLIT_VERLET), 2 one 4-CTA cluster per row (nx = 4096 as
+ * step of Eq. fov10): *layout = 4 one 2-CTA cluster per row with the Verlet
+ * step, 3 one CTA per row with the Verlet step (plans set to
+ * BPM_SPLIT_VERLET), 2 one 4-CTA cluster per row (nx = 4096 as
  * two half-band parts per band; the rule while every row gets four SMs),
  * 1 one 2-CTA cluster per row, 0 one CTA per row, -1 chosen by the fixed
  * rule (2-CTA cluster while every row gets two SMs, else one CTA per row);

@@ -204,9 +204,12 @@ int split_table_stride(const bpm_plan_s* plan, int logm);   // float2 per row
 constexpr int kLayoutSplit4 = 2;
 // one CTA per row, second-order (Verlet) step, N = 256..4096
 constexpr int kLayoutCtaHalf = 3;
+// one 2-CTA cluster per row, second-order (Verlet) step, N = 512..4096
+constexpr int kLayoutClusterHalf = 4;
 int fused_launch_capacity(int logn, bool cluster);
 int fused_split4_capacity();
 int fused_half_capacity(int logn);   // 8 <= logn <= 12
+int fused_cluster_half_capacity(int logn);   // 9 <= logn <= 12
 int fused_rows_per_cta(int logn);
 int fused_threads(int logn);
 

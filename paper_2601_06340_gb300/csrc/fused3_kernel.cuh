@@ -25,7 +25,9 @@
 
 namespace bpm {
 
-template <int LOGN>
+// PHB: strain-slice buffers (2 for the second-order step, which couples
+// with the slices of two steps at a time)
+template <int LOGN, int PHB = 1>
 struct F3Cfg {
   static constexpr int N = 1 << LOGN;
   static constexpr int T = N / 16;
@@ -36,9 +38,9 @@ struct F3Cfg {
   static constexpr int WARPS = T / 32;
   static constexpr int OFF_BUF = 0;                       // [PADN]
   static constexpr int OFF_X = OFF_BUF + PADN * 8;        // [2][N] exchange
-  static constexpr int OFF_PH = OFF_X + 2 * N * 8;        // [N]
-  static constexpr int OFF_MBAR = OFF_PH + N * 8;          // strain slice barrier
-  static constexpr int OFF_XBAR = OFF_MBAR + 8;            // [2] exchange barriers
+  static constexpr int OFF_PH = OFF_X + 2 * N * 8;        // [PHB][N]
+  static constexpr int OFF_MBAR = OFF_PH + PHB * N * 8;    // [PHB] strain slice barriers
+  static constexpr int OFF_XBAR = OFF_MBAR + 8 * PHB;      // [2] exchange barriers
   static constexpr int OFF_RECPH = OFF_XBAR + 16;
   static constexpr int OFF_RED = OFF_RECPH + 8;           // [WARPS] double
   static constexpr int SMEM = OFF_RED + WARPS * 8;
@@ -116,12 +118,19 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity
   return false;
 }
 
-template <int LOGN, bool EX>
+// HALF = false: the first-order step of Eq. fov10.  HALF = true: the
+// second-order (Verlet) step of Eq. split-op, half-step coupling on the
+// step's slice, propagation, half-step coupling again.  After the psi_p swap
+// a CTA holds both bands at its points, so it applies step n's second half
+// to both and step n + 1's first half to its own band with no further
+// exchange; the launch's first half-step takes the other band from the
+// state in global memory.  Records are taken after step n's second half.
+template <int LOGN, bool EX, bool HALF = false>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
     fused3_march_kernel(const RowDescF32* __restrict__ rows, int n_rows, int steps,
                         const float4* __restrict__ tw, int* __restrict__ status) {
   namespace cg = cooperative_groups;
-  using C = F3Cfg<LOGN>;
+  using C = F3Cfg<LOGN, HALF ? 2 : 1>;
   using F = F2Cfg<LOGN>;   // same pass geometry (E = 16 points per thread)
   constexpr int N = C::N, T = C::T, NP = C::NP, RL = C::RL, GL = C::G_LAST;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -147,6 +156,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
 
   if (lead) {
     mbar_init(bar);
+    if constexpr (HALF) mbar_init(bar + 1);
     mbar_init(&xbar[0]);
     mbar_init(&xbar[1]);
   }
@@ -180,7 +190,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
   const uint32_t slice_bytes = uint32_t(N) * 8u;
   int pending_slot = -1;
   bool timed_out = false;
-  const float2 am1 = d.am1, bb = d.b;
+  const float2 am1 = HALF ? d.am1h : d.am1, bb = HALF ? d.bh : d.b;
+  if constexpr (HALF) {
+    // the launch's first half-step, on the slice of its first step (buffer
+    // 0); later slices are fetched a step ahead into the other buffer
+    if (lead) bulk_load(ph, d.phasor + size_t(d.n_begin) * N, slice_bytes, bar);
+    float2 q[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) q[j] = d.state[(band ^ 1) * N + t + j * T];
+    if (!mbar_wait(bar, 0u)) timed_out = true;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = couple_cell(v[j], q[j], ph[t + j * T], band, am1, bb);
+  }
 
   for (int it = 0; it < steps; ++it) {
     const int n = d.n_begin + it;
@@ -199,7 +220,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
     f2_twiddle<false>(v, w0);
     f2_store<LOGN, 0>(buf, v, t);
     __syncthreads();
-    if (lead) bulk_load(ph, d.phasor + size_t(n) * N, slice_bytes, bar);
+    if constexpr (HALF) {
+      // every thread is past step it - 1's couplings, which read the buffer
+      // of slice it - 1: fetch slice it + 1 into it
+      if (lead && it + 1 < steps)
+        bulk_load(ph + ((it + 1) & 1) * N, d.phasor + size_t(n + 1) * N, slice_bytes,
+                  bar + ((it + 1) & 1));
+    } else {
+      if (lead) bulk_load(ph, d.phasor + size_t(n) * N, slice_bytes, bar);
+    }
     if (lead && pending_slot >= 0) {
       double s = 0.0;
       for (int w = 0; w < C::WARPS; ++w) s += red[w];
@@ -251,33 +280,74 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
     // bounded wait, not one per step; the host reports BPM_ERR_TIMEOUT)
     if (!timed_out && !mbar_wait_cluster(&xbar[half], uint32_t((it >> 1) & 1))) timed_out = true;
 
-    if (!timed_out && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
     const float2* xi = xb + half * N;
-#pragma unroll
-    for (int pp = 0; pp < 8; ++pp) {
-      const float4 q2 = *reinterpret_cast<const float4*>(xi + xpair(pp, t, T));
-      v[2 * pp] = couple_cell(v[2 * pp], make_float2(q2.x, q2.y), ph[t + 2 * pp * T], band, am1, bb);
-      v[2 * pp + 1] =
-          couple_cell(v[2 * pp + 1], make_float2(q2.z, q2.w), ph[t + (2 * pp + 1) * T], band, am1, bb);
-    }
-
-    if (rec) {
-      const int slot = (n + 1) / d.record_every - 1;
-      const float2 g = *recph;
+    if constexpr (HALF) {
+      const bool next = it + 1 < steps;
+      if (next && !timed_out &&
+          !mbar_wait(bar + ((it + 1) & 1), uint32_t(((it + 1) >> 1) & 1)))
+        timed_out = true;
+      const float2* phc = ph + (it & 1) * N;
+      const float2* phn = ph + ((it + 1) & 1) * N;
+      const float2 g = rec ? *recph : make_float2(1.f, 0.f);
+      const int slot = rec ? (n + 1) / d.record_every - 1 : 0;
+      float2* r0 = (rec && d.records) ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
       float s = 0.f;
-      float2* r0 = d.records ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const float2 p = v[j];
-        s = fmaf(p.x, p.x, fmaf(p.y, p.y, s));
-        if (r0) r0[t + j * T] = make_float2(fmaf(p.x, g.x, -(p.y * g.y)), fmaf(p.x, g.y, p.y * g.x));
+      for (int pp = 0; pp < 8; ++pp) {
+        const float4 q2 = *reinterpret_cast<const float4*>(xi + xpair(pp, t, T));
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int j = 2 * pp + k;
+          const float2 p = v[j], q = k ? make_float2(q2.z, q2.w) : make_float2(q2.x, q2.y);
+          const float2 e = phc[t + j * T];
+          const float2 c = couple_cell(p, q, e, band, am1, bb);   // step it, second half
+          if (rec) {
+            s = fmaf(c.x, c.x, fmaf(c.y, c.y, s));
+            if (r0) r0[t + j * T] = make_float2(fmaf(c.x, g.x, -(c.y * g.y)), fmaf(c.x, g.y, c.y * g.x));
+          }
+          if (next) {   // step it + 1, first half, with the other band's value
+            const float2 co = couple_cell(q, p, e, band ^ 1, am1, bb);
+            v[j] = couple_cell(c, co, phn[t + j * T], band, am1, bb);
+          } else {
+            v[j] = c;
+          }
+        }
       }
-      if (d.powers) {
+      if (rec && d.powers) {
         double ds = s;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, off);
         if (lane == 0) red[warp] = ds;
         if (lead) pending_slot = slot;
+      }
+    } else {
+      if (!timed_out && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
+  #pragma unroll
+      for (int pp = 0; pp < 8; ++pp) {
+        const float4 q2 = *reinterpret_cast<const float4*>(xi + xpair(pp, t, T));
+        v[2 * pp] = couple_cell(v[2 * pp], make_float2(q2.x, q2.y), ph[t + 2 * pp * T], band, am1, bb);
+        v[2 * pp + 1] =
+            couple_cell(v[2 * pp + 1], make_float2(q2.z, q2.w), ph[t + (2 * pp + 1) * T], band, am1, bb);
+      }
+
+      if (rec) {
+        const int slot = (n + 1) / d.record_every - 1;
+        const float2 g = *recph;
+        float s = 0.f;
+        float2* r0 = d.records ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
+  #pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float2 p = v[j];
+          s = fmaf(p.x, p.x, fmaf(p.y, p.y, s));
+          if (r0) r0[t + j * T] = make_float2(fmaf(p.x, g.x, -(p.y * g.y)), fmaf(p.x, g.y, p.y * g.x));
+        }
+        if (d.powers) {
+          double ds = s;
+  #pragma unroll
+          for (int off = 16; off > 0; off >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, off);
+          if (lane == 0) red[warp] = ds;
+          if (lead) pending_slot = slot;
+        }
       }
     }
   }
@@ -294,7 +364,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
   // march runs on to the end of the launch; the lead still issues one slice
   // copy per step on its barrier, so waiting (again bounded) for the last
   // step's phase leaves no copy of its own in flight when the CTA exits.
-  if (timed_out) give_up_after_march(bar, uint32_t((steps - 1) & 1), lead, status);
+  if (timed_out) {
+    if constexpr (HALF)   // the last slice copy: step steps - 1, in its buffer
+      give_up_after_march(bar + ((steps - 1) & 1), uint32_t(((steps - 1) >> 1) & 1), lead, status);
+    else
+      give_up_after_march(bar, uint32_t((steps - 1) & 1), lead, status);
+  }
   cluster.sync();   // the peer may still read our exchange buffer: stay resident
 }
 

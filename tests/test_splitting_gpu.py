@@ -47,11 +47,17 @@ def test_splitting_refused_where_not_built(bpm_lib):
             binding.bpm_set_splitting(plan.handle, 7)
 
 
+@pytest.mark.parametrize("layout", ["rule", "cta", "cluster"])
 @pytest.mark.parametrize("name", ["laue_perfect", "bragg_bent", "asym_dislocation", "pulse"])
-def test_verlet_fp32_matches_oracle(bpm_lib, name):
-    """The fused band-per-thread kernel's second-order step (half coupling,
-    propagation, half coupling on the slice of the step) against the
-    oracle's Verlet march, fields and records; rows of a batch included."""
+def test_verlet_fp32_matches_oracle(bpm_lib, monkeypatch, name, layout):
+    """The fused kernels' second-order step (half coupling, propagation, half
+    coupling on the slice of the step) against the oracle's Verlet march,
+    fields and records; rows of a batch included.  A single N = 4096 row
+    takes the 2-CTA cluster form by rule (layout 4), everything else the
+    one-CTA form (3); BPM_FUSED_LAYOUT=cta|cluster forces either (the
+    cluster form only while every row gets two SMs)."""
+    if layout != "rule":
+        monkeypatch.setenv("BPM_FUSED_LAYOUT", layout)
     wl = {"laue_perfect": lambda: inputs.laue_perfect(nx=512, nz=400, record_every=50),
           "bragg_bent": lambda: inputs.bragg_bent(nx=4096, nz=1000, record_every=150),
           "asym_dislocation": lambda: inputs.asym_dislocation(nx=1024, nz=500,
@@ -64,7 +70,8 @@ def test_verlet_fp32_matches_oracle(bpm_lib, name):
     with binding.Plan(wl, FP32, splitting=binding.BPM_SPLIT_VERLET) as plan:
         out = plan.propagate()
         shape = binding.bpm_launch_shape(plan.handle)
-    assert shape[0] == 3, shape
+    cluster = wl.batch == 1 and (layout == "cluster" or (layout == "rule" and wl.nx == 4096))
+    assert shape[0] == (4 if cluster else 3), shape
     errs = band_errors(out.psi[rows], ref.psi, out.records[rows], ref.records)
     assert max(errs) <= TOL_FP32, errs
     final = band_errors(out.psi[rows], ref.psi)
