@@ -148,8 +148,8 @@ int bpm_set_strain(bpm_plan_t plan, int32_t kind, const double* ux_um,
  *                          t/2), t = 1/(2 - 2^(1/3)).
  * FP64 plans take every method.  FP32 (fused) plans take the first-order
  * step, and Verlet for 256 <= nx <= 4096 (half-step couplings on either
- * side of the full-step propagation; one CTA per solve, or at nx = 4096
- * one 2-CTA cluster per solve while every solve gets two SMs); 3D plans take the
+ * side of the full-step propagation; one 2-CTA cluster per solve while
+ * every solve gets two SMs and nx != 2048, else one CTA per solve); 3D plans take the
  * first-order step only; other combinations return BPM_ERR_INVALID.
  * bpm_submit takes FP32 plans set to Verlet (one CTA per row as well).
  * BPM_ERR_BUSY while tickets are pending. */

@@ -304,19 +304,18 @@ static LaunchShape choose_shape(bpm_plan_s* plan, PlanAux* aux, const void* stat
   LaunchShape rule;
   const int nb = plan->nb, logn = plan->logn;
   if (plan->split == BPM_SPLIT_VERLET) {
-    // the second-order forms: a 2-CTA cluster per row at N = 4096 while
-    // every row gets two SMs (measured per 8000-step solve: 41.3 ms against
-    // 50.4 ms on one CTA), else one CTA per row (at N = 512..2048 the
-    // cluster form's three couplings per point overflow the instruction
-    // cache: 30-38 ms against 28.4-28.7 ms); BPM_FUSED_LAYOUT=cluster|cta
-    // forces either
+    // the second-order forms: a 2-CTA cluster per row while every row gets
+    // two SMs, else one CTA per row; measured per 8000-step single solve,
+    // cluster against one CTA: N = 512 23.5 / 28.3 ms, 1024 25.9 / 29.1,
+    // 2048 29.8 / 28.7 (one CTA kept there), 4096 42.6 / 50.6;
+    // BPM_FUSED_LAYOUT=cluster|cta forces either
     int sms = 1, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const char* fv = std::getenv("BPM_FUSED_LAYOUT");
     const bool cta = fv && std::strcmp(fv, "cta") == 0;
     const bool cl = fv && std::strcmp(fv, "cluster") == 0;
-    if (!cta && (cl || logn == 12) && logn >= 9 && 2 * nb <= sms &&
+    if (!cta && (cl || logn != 11) && logn >= 9 && 2 * nb <= sms &&
         nb <= fused_cluster_half_capacity(logn)) {
       rule.layout = kLayoutClusterHalf;
       return rule;

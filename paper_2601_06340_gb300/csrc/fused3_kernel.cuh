@@ -292,27 +292,37 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
       const int slot = rec ? (n + 1) / d.record_every - 1 : 0;
       float2* r0 = (rec && d.records) ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
       float s = 0.f;
+      // Three couplings per point, unrolled over the thread's 16 points,
+      // overflow the instruction cache; they run as a loop over shared
+      // memory instead (buf is free once every thread is past the inverse
+      // pass 0, and free again for the next step once every thread has
+      // taken its points back).
+      __syncthreads();
 #pragma unroll
+      for (int j = 0; j < 16; ++j) buf[t + j * T] = v[j];
+#pragma unroll 1
       for (int pp = 0; pp < 8; ++pp) {
         const float4 q2 = *reinterpret_cast<const float4*>(xi + xpair(pp, t, T));
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-          const int j = 2 * pp + k;
-          const float2 p = v[j], q = k ? make_float2(q2.z, q2.w) : make_float2(q2.x, q2.y);
-          const float2 e = phc[t + j * T];
-          const float2 c = couple_cell(p, q, e, band, am1, bb);   // step it, second half
+          const int at = t + (2 * pp + k) * T;
+          const float2 p = buf[at], q = k ? make_float2(q2.z, q2.w) : make_float2(q2.x, q2.y);
+          const float2 e = phc[at];
+          float2 c = couple_cell(p, q, e, band, am1, bb);   // step it, second half
           if (rec) {
             s = fmaf(c.x, c.x, fmaf(c.y, c.y, s));
-            if (r0) r0[t + j * T] = make_float2(fmaf(c.x, g.x, -(c.y * g.y)), fmaf(c.x, g.y, c.y * g.x));
+            if (r0) r0[at] = make_float2(fmaf(c.x, g.x, -(c.y * g.y)), fmaf(c.x, g.y, c.y * g.x));
           }
           if (next) {   // step it + 1, first half, with the other band's value
             const float2 co = couple_cell(q, p, e, band ^ 1, am1, bb);
-            v[j] = couple_cell(c, co, phn[t + j * T], band, am1, bb);
-          } else {
-            v[j] = c;
+            c = couple_cell(c, co, phn[at], band, am1, bb);
           }
+          buf[at] = c;
         }
       }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = buf[t + j * T];
+      __syncthreads();
       if (rec && d.powers) {
         double ds = s;
 #pragma unroll
