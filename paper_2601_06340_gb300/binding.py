@@ -219,8 +219,9 @@ def bpm_march_f64_noalloc(d_psi, nx, n_rows, d_prop, d_coupling, d_phasor, n_beg
 
 
 def bpm_launch_shape(plan) -> tuple[int, int]:
-    """(layout, chunk) of the plan's last FP32 march: layout 3 CTA per row
-    with the Verlet step, 2 four-CTA cluster per row (N = 4096 half-band
+    """(layout, chunk) of the plan's last FP32 march: layouts 5, 4, 3 the
+    Verlet step on the N = 4096 half-band split, a two-CTA cluster or one
+    CTA per row; 2 four-CTA cluster per row (N = 4096 half-band
     split), 1 two-CTA cluster per row, 0 CTA per row, -1 the fixed rule;
     chunk 0 for one launch."""
     layout, chunk = _I(0), _I(0)

@@ -206,10 +206,13 @@ constexpr int kLayoutSplit4 = 2;
 constexpr int kLayoutCtaHalf = 3;
 // one 2-CTA cluster per row, second-order (Verlet) step, N = 512..4096
 constexpr int kLayoutClusterHalf = 4;
+// one 4-CTA cluster per row (N = 4096 half-band split), second-order step
+constexpr int kLayoutSplit4Half = 5;
 int fused_launch_capacity(int logn, bool cluster);
 int fused_split4_capacity();
 int fused_half_capacity(int logn);   // 8 <= logn <= 12
 int fused_cluster_half_capacity(int logn);   // 9 <= logn <= 12
+int fused_split4_half_capacity();            // N = 4096
 int fused_rows_per_cta(int logn);
 int fused_threads(int logn);
 

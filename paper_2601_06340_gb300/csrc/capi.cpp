@@ -315,6 +315,12 @@ static LaunchShape choose_shape(bpm_plan_s* plan, PlanAux* aux, const void* stat
     const char* fv = std::getenv("BPM_FUSED_LAYOUT");
     const bool cta = fv && std::strcmp(fv, "cta") == 0;
     const bool cl = fv && std::strcmp(fv, "cluster") == 0;
+    // N = 4096 rows that each get four SMs: the half-band split
+    if (!cta && !cl && logn == 12 && plan->d_prop_split != nullptr && 4 * nb <= sms &&
+        nb <= fused_split4_half_capacity()) {
+      rule.layout = kLayoutSplit4Half;
+      return rule;
+    }
     if (!cta && (cl || logn != 11) && logn >= 9 && 2 * nb <= sms &&
         nb <= fused_cluster_half_capacity(logn)) {
       rule.layout = kLayoutClusterHalf;

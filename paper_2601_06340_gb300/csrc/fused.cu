@@ -31,6 +31,8 @@ BPM_DECLARE_FUSED2(12)
 int fused4_launch_13(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
 int fused4h_launch_12(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
 int fused4h_rows_resident_12();
+int fused4hh_launch_12(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
+int fused4hh_rows_resident_12();
 int fused4_launch_14(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
 #define BPM_DECLARE_FUSED3(L)                                                    \
   int fused3_launch_##L(const RowDescF32*, int, int, const float4*, int*,        \
@@ -81,6 +83,10 @@ int launch_fused_layout(int logn, const RowDescF32* d_rows, int n_rows, int step
   // (only for rows that carry the split tables: the caller checks)
   if (logn == 12 && layout == kLayoutSplit4)
     return fused4h_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
+  if (layout == kLayoutSplit4Half) {
+    if (logn != 12) return fail(BPM_ERR_INVALID, "second-order split layout needs nx = 4096");
+    return fused4hh_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
+  }
   if (layout == kLayoutClusterHalf) {
     switch (logn) {
       case 9: return fused3h_launch_9(d_rows, n_rows, steps, d_tw, d_status, st);
@@ -279,6 +285,17 @@ int fused_cluster_half_capacity(int logn) {
       default: c = fused3h_rows_resident_12(); break;
     }
     cache[logn].store(c, std::memory_order_relaxed);
+  }
+  return c;
+}
+
+// Rows of N = 4096 one second-order half-band-split launch keeps resident.
+int fused_split4_half_capacity() {
+  static std::atomic<int> cached{0};
+  int c = cached.load(std::memory_order_relaxed);
+  if (c == 0) {
+    c = fused4hh_rows_resident_12();
+    cached.store(c, std::memory_order_relaxed);
   }
   return c;
 }

@@ -44,7 +44,8 @@ namespace bpm {
 // buffered by step parity; no cluster-wide barrier runs inside the march.
 // Buffer reuse: a half is rewritten two steps later, by a sender that has
 // by then received values the receiver computed from that half.
-template <int LM>
+// PHB: strain-slice buffers (2 for the second-order step, N = 4096 only)
+template <int LM, int PHB = 1>
 struct F4ECfg {
   static constexpr int M = 1 << LM;
   static constexpr int N = 2 * M;
@@ -59,10 +60,10 @@ struct F4ECfg {
   static constexpr int OFF_BUF = 0;                        // [PADM]
   static constexpr int OFF_G = OFF_BUF + PADM * 8;         // [2][M] peer's F
   static constexpr int OFF_C = OFF_G + 2 * M * 8;          // [2][M] other band's psi_p
-  static constexpr int OFF_PH = OFF_C + 2 * M * 8;         // [PH] strain slice
-  static constexpr int OFF_E1 = OFF_PH + PH * 8;           // [16][T] D(k_j + M)
-  static constexpr int OFF_MBAR = OFF_E1 + M * 8;          // strain-slice barrier
-  static constexpr int OFF_GBAR = OFF_MBAR + 8;            // [2] F barriers
+  static constexpr int OFF_PH = OFF_C + 2 * M * 8;         // [PHB][PH] strain slices
+  static constexpr int OFF_E1 = OFF_PH + PHB * PH * 8;     // [16][T] D(k_j + M)
+  static constexpr int OFF_MBAR = OFF_E1 + M * 8;          // [PHB] strain-slice barriers
+  static constexpr int OFF_GBAR = OFF_MBAR + 8 * PHB;      // [2] F barriers
   static constexpr int OFF_CBAR = OFF_GBAR + 16;           // [2] psi_p barriers
   static constexpr int OFF_PPEER = OFF_CBAR + 16;          // [2] peer's band-power part
   static constexpr int OFF_RECPH = OFF_PPEER + 16;
@@ -104,12 +105,18 @@ __device__ __forceinline__ void st_async_f64(uint32_t raddr, double v, uint32_t 
       : "memory");
 }
 
-template <int LM, bool EX>
+// HALF = true (N = 4096 only): the second-order (Verlet) step, as in the
+// 2-CTA cluster kernel: after the psi_p swap a CTA holds both bands at its
+// samples, applies step n's second half-coupling to both and step n + 1's
+// first half to its own band (a loop over shared memory); the launch's
+// first half-step reads the other band from global memory.
+template <int LM, bool EX, bool HALF = false>
 __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
     fused4e_march_kernel(const RowDescF32* __restrict__ rows, int n_rows, int steps,
                          const float4* __restrict__ tw, int* __restrict__ status) {
   namespace cg = cooperative_groups;
-  using C = F4ECfg<LM>;
+  static_assert(!HALF || LM == 11, "the second-order form is built for N = 4096");
+  using C = F4ECfg<LM, HALF ? 2 : 1>;
   using F = F2Cfg<LM>;
   constexpr int L = LM, M = C::M, N = C::N, T = C::T, NP = F::NP;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -145,6 +152,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
 
   if (lead) {
     mbar_init(bar);
+    if constexpr (HALF) mbar_init(bar + 1);
     mbar_init(&gbar[0]);
     mbar_init(&gbar[1]);
     mbar_init(&cbar[0]);
@@ -181,8 +189,20 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
   const uint32_t slice_bytes = uint32_t(C::PH) * 8u;
   bool timed_out = false;
   double my_part = 0.0;
-  const float2 am1 = d.am1, bb = d.b;
+  const float2 am1 = HALF ? d.am1h : d.am1, bb = HALF ? d.bh : d.b;
   const bool pow_on = d.powers != nullptr && d.record_every > 0;
+  if constexpr (HALF) {
+    // the launch's first half-step on the slice of its first step (buffer
+    // 0); later slices are fetched a step ahead into the other buffer
+    if (lead) bulk_load(ph, d.phasor + size_t(d.n_begin) * N, slice_bytes, bar);
+    float2 q[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) q[j] = d.state[(band ^ 1) * N + 2 * (t + j * T) + h];
+    if (!mbar_wait(bar, 0u)) timed_out = true;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      v[j] = couple_cell(v[j], q[j], ph[2 * (t + j * T) + h], band, am1, bb);
+  }
 
   for (int it = 0; it < steps; ++it) {
     const int n = d.n_begin + it;
@@ -205,8 +225,16 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
     f2_store<L, 0>(buf, v, t);
     __syncthreads();
     if (lead) {
-      bulk_load(ph, d.phasor + size_t(n) * N + (C::NAT ? size_t(0) : size_t(h) * M), slice_bytes,
-                bar);
+      if constexpr (HALF) {
+        // every thread is past step it - 1's couplings, which read the
+        // buffer of slice it - 1: fetch slice it + 1 into it
+        if (it + 1 < steps)
+          bulk_load(ph + ((it + 1) & 1) * C::PH, d.phasor + size_t(n + 1) * N, slice_bytes,
+                    bar + ((it + 1) & 1));
+      } else {
+        bulk_load(ph, d.phasor + size_t(n) * N + (C::NAT ? size_t(0) : size_t(h) * M),
+                  slice_bytes, bar);
+      }
       mbar_expect_tx(&gbar[half], uint32_t(M) * 8u + (part_due ? 8u : 0u));
       if (part_due) {
         double s = 0.0;
@@ -271,35 +299,86 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
         st_async_v4(co + uint32_t(xpair(pp, t, T)) * 8u, v[2 * pp], v[2 * pp + 1], cbo);
     }
     if (!timed_out && !mbar_wait_cluster(&cbar[half], uint32_t((it >> 1) & 1))) timed_out = true;
-    if (!timed_out && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
-    const float2* ci = cb + half * M;
-#pragma unroll
-    for (int pp = 0; pp < 8; ++pp) {
-      const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
-      const int c0 = C::NAT ? 2 * (t + 2 * pp * T) + h : t + 2 * pp * T;
-      const int c1 = C::NAT ? 2 * (t + (2 * pp + 1) * T) + h : t + (2 * pp + 1) * T;
-      v[2 * pp] = couple_cell(v[2 * pp], make_float2(q2.x, q2.y), ph[c0], band, am1, bb);
-      v[2 * pp + 1] = couple_cell(v[2 * pp + 1], make_float2(q2.z, q2.w), ph[c1], band, am1, bb);
-    }
-
-    if (rec) {
-      const int slot = (n + 1) / d.record_every - 1;
-      const float2 g = *recph;
+    if constexpr (HALF) {
+      const bool next = it + 1 < steps;
+      if (next && !timed_out &&
+          !mbar_wait(bar + ((it + 1) & 1), uint32_t(((it + 1) >> 1) & 1)))
+        timed_out = true;
+      const float2* ci = cb + half * M;
+      const float2* phc = ph + (it & 1) * C::PH;
+      const float2* phn = ph + ((it + 1) & 1) * C::PH;
+      const float2 g = rec ? *recph : make_float2(1.f, 0.f);
+      const int slot = rec ? (n + 1) / d.record_every - 1 : 0;
+      float2* r0 = (rec && d.records) ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
       float s = 0.f;
-      float2* r0 = d.records ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
+      // a loop over shared memory (three couplings per point unrolled over
+      // 16 points would overflow the instruction cache); buf is free once
+      // every thread is past the inverse pass 0, and again for the next
+      // step once every thread has taken its points back
+      __syncthreads();
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const float2 p = v[j];
-        s = fmaf(p.x, p.x, fmaf(p.y, p.y, s));
-        if (r0)
-          r0[2 * (t + j * T) + h] =
-              make_float2(fmaf(p.x, g.x, -(p.y * g.y)), fmaf(p.x, g.y, p.y * g.x));
+      for (int j = 0; j < 16; ++j) buf[t + j * T] = v[j];
+#pragma unroll 1
+      for (int pp = 0; pp < 8; ++pp) {
+        const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int j = 2 * pp + k;
+          const int cell = 2 * (t + j * T) + h;
+          const float2 p = buf[t + j * T], q = k ? make_float2(q2.z, q2.w) : make_float2(q2.x, q2.y);
+          const float2 e = phc[cell];
+          float2 c = couple_cell(p, q, e, band, am1, bb);   // step it, second half
+          if (rec) {
+            s = fmaf(c.x, c.x, fmaf(c.y, c.y, s));
+            if (r0) r0[cell] = make_float2(fmaf(c.x, g.x, -(c.y * g.y)), fmaf(c.x, g.y, c.y * g.x));
+          }
+          if (next) {   // step it + 1, first half, with the other band's value
+            const float2 co = couple_cell(q, p, e, band ^ 1, am1, bb);
+            c = couple_cell(c, co, phn[cell], band, am1, bb);
+          }
+          buf[t + j * T] = c;
+        }
       }
-      if (d.powers) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = buf[t + j * T];
+      __syncthreads();
+      if (rec && d.powers) {
         double ds = s;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, off);
         if (lane == 0) red[warp] = ds;   // summed by the lead after the next barrier
+      }
+    } else {
+      if (!timed_out && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
+      const float2* ci = cb + half * M;
+  #pragma unroll
+      for (int pp = 0; pp < 8; ++pp) {
+        const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
+        const int c0 = C::NAT ? 2 * (t + 2 * pp * T) + h : t + 2 * pp * T;
+        const int c1 = C::NAT ? 2 * (t + (2 * pp + 1) * T) + h : t + (2 * pp + 1) * T;
+        v[2 * pp] = couple_cell(v[2 * pp], make_float2(q2.x, q2.y), ph[c0], band, am1, bb);
+        v[2 * pp + 1] = couple_cell(v[2 * pp + 1], make_float2(q2.z, q2.w), ph[c1], band, am1, bb);
+      }
+
+      if (rec) {
+        const int slot = (n + 1) / d.record_every - 1;
+        const float2 g = *recph;
+        float s = 0.f;
+        float2* r0 = d.records ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
+  #pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float2 p = v[j];
+          s = fmaf(p.x, p.x, fmaf(p.y, p.y, s));
+          if (r0)
+            r0[2 * (t + j * T) + h] =
+                make_float2(fmaf(p.x, g.x, -(p.y * g.y)), fmaf(p.x, g.y, p.y * g.x));
+        }
+        if (d.powers) {
+          double ds = s;
+  #pragma unroll
+          for (int off = 16; off > 0; off >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, off);
+          if (lane == 0) red[warp] = ds;   // summed by the lead after the next barrier
+        }
       }
     }
   }
@@ -323,7 +402,12 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
   // march runs on to the end of the launch; the lead still issues one slice
   // copy per step on its barrier, so waiting (again bounded) for the last
   // step's phase leaves no copy of its own in flight when the CTA exits.
-  if (timed_out) give_up_after_march(bar, uint32_t((steps - 1) & 1), lead, status);
+  if (timed_out) {
+    if constexpr (HALF)   // the last slice copy: step steps - 1, in its buffer
+      give_up_after_march(bar + ((steps - 1) & 1), uint32_t(((steps - 1) >> 1) & 1), lead, status);
+    else
+      give_up_after_march(bar, uint32_t((steps - 1) & 1), lead, status);
+  }
   cluster.sync();   // peers may still read our shared memory
 }
 

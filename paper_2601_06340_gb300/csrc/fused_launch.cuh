@@ -68,19 +68,19 @@ int fused2_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
 
 // N = 4096 as a half-band split: one row per 4-CTA cluster, each CTA a
 // 2048-point half of one band (fused4_kernel.cuh with M = 2048).
-template <bool EX>
+template <bool EX, bool HALF = false>
 int fused4h_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const float4* d_tw,
                         int* d_status, cudaStream_t st) {
-  using C = F4ECfg<11>;
+  using C = F4ECfg<11, HALF ? 2 : 1>;
   static std::atomic<bool> configured{false};
   if (!configured.load(std::memory_order_acquire)) {
-    cudaError_t e = cudaFuncSetAttribute(fused4e_march_kernel<11, EX>,
+    cudaError_t e = cudaFuncSetAttribute(fused4e_march_kernel<11, EX, HALF>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused4h)");
     configured.store(true, std::memory_order_release);
   }
-  fused4e_march_kernel<11, EX><<<4 * n_rows, C::T, C::SMEM, st>>>(d_rows, n_rows, steps, d_tw,
-                                                                  d_status);
+  fused4e_march_kernel<11, EX, HALF><<<4 * n_rows, C::T, C::SMEM, st>>>(d_rows, n_rows, steps,
+                                                                        d_tw, d_status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "fused4h march launch");
   return BPM_OK;
@@ -256,5 +256,20 @@ int fused4_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
     return fused_exact_constants()                                                \
                ? fused4h_launch_impl<true>(r, n, s, tw, status, st)               \
                : fused4h_launch_impl<false>(r, n, s, tw, status, st);             \
+  }                                                                               \
+  }
+
+// second-order (Verlet) form of the N = 4096 half-band split
+#define BPM_INSTANTIATE_FUSED4HH                                                  \
+  namespace bpm {                                                                 \
+  int fused4hh_rows_resident_12() {                                               \
+    return clusters_resident(fused4e_march_kernel<11, true, true>, 4,             \
+                             F4ECfg<11, 2>::T, F4ECfg<11, 2>::SMEM);              \
+  }                                                                               \
+  int fused4hh_launch_12(const RowDescF32* r, int n, int s, const float4* tw,    \
+                         int* status, cudaStream_t st) {                          \
+    return fused_exact_constants()                                                \
+               ? fused4h_launch_impl<true, true>(r, n, s, tw, status, st)         \
+               : fused4h_launch_impl<false, true>(r, n, s, tw, status, st);       \
   }                                                                               \
   }

@@ -27,7 +27,7 @@ CASES = {
     "fused N=64": (lambda: _serving(64), FP32, binding.BPM_SPLIT_FIRST_ORDER),
     "fused2 N=512 batch of 200": (lambda: inputs.rocking_scan(nx=512, nz=300, n_angles=200),
                                   FP32, binding.BPM_SPLIT_FIRST_ORDER),
-    "Verlet N=4096 (2-CTA cluster)": (lambda: _serving(4096), FP32, binding.BPM_SPLIT_VERLET),
+    "Verlet N=4096 (half-band split)": (lambda: _serving(4096), FP32, binding.BPM_SPLIT_VERLET),
     "Verlet batch of 200 (one CTA per row)": (lambda: inputs.rocking_scan(nx=512, nz=300, n_angles=200),
                                               FP32, binding.BPM_SPLIT_VERLET),
     "fused3 N=1024": (lambda: _serving(1024), FP32, binding.BPM_SPLIT_FIRST_ORDER),

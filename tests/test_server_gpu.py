@@ -95,9 +95,10 @@ def test_injected_launch_failure_fails_only_that_size(bpm_lib):
         p.close()
 
 
-def test_verlet_requests_share_the_server_with_first_order_ones(bpm_lib):
+def test_verlet_requests_share_the_server_with_first_order_ones(bpm_lib, monkeypatch):
     # FP32 plans set to Verlet march on the one-CTA half-step kernel in their
-    # own launch group; each result equals the same plan marched alone
+    # own launch group; each result equals the same plan marched alone (on
+    # the same kernel for Verlet rows: the solo march is forced to one CTA)
     binding.bpm_server_configure(0.6, 64, 128, 1000)
     V, F = binding.BPM_SPLIT_VERLET, binding.BPM_SPLIT_FIRST_ORDER
     specs = [(512, V), (512, F), (1024, V), (4096, V), (4096, F), (2048, F)]
@@ -109,6 +110,7 @@ def test_verlet_requests_share_the_server_with_first_order_ones(bpm_lib):
         tickets = [binding.bpm_submit(p.handle, wl.psi0, o) for p, wl, o in zip(plans, wls, outs)]
         for t in tickets:
             assert binding.bpm_poll(t, -1) == binding.BPM_OK
+        monkeypatch.setenv("BPM_FUSED_LAYOUT", "cta")
         for p, wl, o, (_, sp) in zip(plans, wls, outs, specs):
             alone = p.propagate(records=False, powers=False).psi
             errs = band_errors(o, alone)

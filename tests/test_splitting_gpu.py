@@ -47,15 +47,28 @@ def test_splitting_refused_where_not_built(bpm_lib):
             binding.bpm_set_splitting(plan.handle, 7)
 
 
+def _verlet_layout(wl, layout):
+    """Launch layout the Verlet rule (or a forced layout) gives: 5 the
+    N = 4096 half-band split, 4 the 2-CTA cluster, 3 one CTA per row."""
+    if layout == "cta" or wl.batch > 1:
+        return 3
+    if layout == "cluster":
+        return 4
+    if wl.nx == 4096:
+        return 5
+    return 3 if wl.nx == 2048 else 4
+
+
 @pytest.mark.parametrize("layout", ["rule", "cta", "cluster"])
 @pytest.mark.parametrize("name", ["laue_perfect", "bragg_bent", "asym_dislocation", "pulse"])
 def test_verlet_fp32_matches_oracle(bpm_lib, monkeypatch, name, layout):
     """The fused kernels' second-order step (half coupling, propagation, half
     coupling on the slice of the step) against the oracle's Verlet march,
     fields and records; rows of a batch included.  A single row takes the
-    2-CTA cluster form by rule (layout 4) except at N = 2048, batches the
-    one-CTA form (3); BPM_FUSED_LAYOUT=cta|cluster forces either (the
-    cluster form only while every row gets two SMs)."""
+    half-band split at N = 4096 by rule, the 2-CTA cluster form elsewhere
+    except at N = 2048, batches the one-CTA form; BPM_FUSED_LAYOUT=cta|cluster
+    forces either of the latter (the cluster form only while every row gets
+    two SMs)."""
     if layout != "rule":
         monkeypatch.setenv("BPM_FUSED_LAYOUT", layout)
     wl = {"laue_perfect": lambda: inputs.laue_perfect(nx=512, nz=400, record_every=50),
@@ -70,8 +83,7 @@ def test_verlet_fp32_matches_oracle(bpm_lib, monkeypatch, name, layout):
     with binding.Plan(wl, FP32, splitting=binding.BPM_SPLIT_VERLET) as plan:
         out = plan.propagate()
         shape = binding.bpm_launch_shape(plan.handle)
-    cluster = wl.batch == 1 and (layout == "cluster" or (layout == "rule" and wl.nx != 2048))
-    assert shape[0] == (4 if cluster else 3), shape
+    assert shape[0] == _verlet_layout(wl, layout), shape
     errs = band_errors(out.psi[rows], ref.psi, out.records[rows], ref.records)
     assert max(errs) <= TOL_FP32, errs
     final = band_errors(out.psi[rows], ref.psi)
