@@ -93,3 +93,17 @@ def test_verlet_fp32_matches_oracle(bpm_lib, monkeypatch, name, layout):
     first = run_ref(wl, rows=rows)
     diff = max(band_errors(first.psi, ref.psi))
     assert diff > 1e-6 and diff > max(errs), (diff, errs)
+
+
+def test_verlet_fp32_full_size_bragg(bpm_lib):
+    """The full-size single-solve workload (Bragg, bent, Nx = 4096,
+    Nz = 8000) with second-order splitting on the half-band split kernel
+    against the oracle's Verlet march: fields, records and powers."""
+    wl = inputs.bragg_bent()
+    ref = run_ref(wl, method="verlet")
+    with binding.Plan(wl, FP32, splitting=binding.BPM_SPLIT_VERLET) as plan:
+        out = plan.propagate()
+        assert binding.bpm_launch_shape(plan.handle)[0] == 5
+    errs = band_errors(out.psi, ref.psi, out.records, ref.records)
+    assert max(errs) <= TOL_FP32, errs
+    assert np.allclose(out.powers, ref.powers, rtol=1e-4, atol=1e-9 * ref.powers.max())
