@@ -43,6 +43,8 @@ class Plan3D:
     qy: np.ndarray            # [Ny]
     prop_plus: np.ndarray     # [Ny][Nx] exp(i dz^ delta_+(qx, qy))
     prop_minus: np.ndarray    # [Ny][Nx] exp(i dz^ delta_-(qx, qy))
+    delta_plus: np.ndarray    # [Ny][Nx] delta_+(qx, qy) (fractional steps of Eq. split-op)
+    delta_minus: np.ndarray   # [Ny][Nx] delta_-(qx, qy)
 
 
 def energy_plan3d(energy_ev: float, e_ref_ev: float, theta_b_ref_rad: float,
@@ -54,12 +56,13 @@ def energy_plan3d(energy_ev: float, e_ref_ev: float, theta_b_ref_rad: float,
     qx = 2.0 * math.pi * np.fft.fftfreq(nx, d=base.dxh)
     qy = 2.0 * math.pi * np.fft.fftfreq(ny, d=dyh)
     QX, QY = np.meshgrid(qx, qy)          # [Ny][Nx]
-    props = []
+    props, deltas = [], []
     for sign in (+1.0, -1.0):
         root = np.sqrt(1.0 - (QX + sign * s) ** 2 - QY ** 2)
         delta = -(QX * (QX + sign * 2.0 * s) + QY ** 2) / (root + c)
+        deltas.append(delta)
         props.append(np.exp(1j * dzh * delta))
-    return Plan3D(base, dyh, qx, qy, props[0], props[1])
+    return Plan3D(base, dyh, qx, qy, props[0], props[1], deltas[0], deltas[1])
 
 
 class Crystal3D:
@@ -121,10 +124,15 @@ class Crystal3D:
 
 
 def march3d(plans: list[Plan3D], psi0: np.ndarray, slices, n_begin: int, n_end: int,
-            record_every: int, dx_um: float, dy_um: float) -> bpm.MarchResult:
+            record_every: int, dx_um: float, dy_um: float, method: str = "first_order",
+            chi: tuple[complex, complex] | None = None) -> bpm.MarchResult:
     """Eq. fov10 on [B][2][Ny][Nx] fields: each envelope through its own 2D
     angular-spectrum operator, then the pointwise two-beam coupling.
-    Records / powers as in ``bpm.march`` (powers = dx dy sum |psi|^2)."""
+    Records / powers as in ``bpm.march`` (powers = dx dy sum |psi|^2).
+    ``method`` selects the operator splitting of Eq. split-op as in
+    ``bpm.march`` (stages of step n on the slice of z_n; a stage of a_i dz
+    propagates with exp(i a_i dz^ delta_+-) and the common phase g is applied
+    once per step); ``chi`` = (chi_0, chi_h) is needed for it."""
     psi0 = np.asarray(psi0, dtype=np.complex128)
     nb, nbands, ny, nx = psi0.shape
     assert nbands == 2 and len(plans) == nb
@@ -140,17 +148,42 @@ def march3d(plans: list[Plan3D], psi0: np.ndarray, slices, n_begin: int, n_end: 
     def power(f):
         return dx_um * dy_um * np.sum(f.real ** 2 + f.imag ** 2, axis=(-2, -1))
 
+    # stages: (propagator pair or None, a, b) per row; first order keeps the
+    # plan's propagators and applies g with them
+    stages = []
+    if method != "first_order":
+        chi0, chih = chi
+        for frac_a, frac_b in bpm.split_stages(method):
+            props = None
+            if frac_a != 0.0:
+                props = (np.stack([np.exp(1j * frac_a * p.base.dzh * p.delta_plus) for p in plans]),
+                         np.stack([np.exp(1j * frac_a * p.base.dzh * p.delta_minus) for p in plans]))
+            ab = [bpm.coupling_coefficients(p.base, frac_b, chi0, chih) for p in plans]
+            stages.append((props, np.array([x[0] for x in ab])[:, None, None],
+                           np.array([x[1] for x in ab])[:, None, None]))
+
     psi_p = psi0[:, 0].copy()
     psi_m = psi0[:, 1].copy()
     for step in range(n_begin, n_end):
-        pp = np.fft.ifft2(np.fft.fft2(psi_p) * prop_p) * g
-        pm = np.fft.ifft2(np.fft.fft2(psi_m) * prop_m) * g
         inside, theta = slices(step)
         e_plus = np.exp(1j * theta)
         e_minus = np.exp(-1j * theta)
-        new_p = np.where(inside, a * pp + b * e_plus * pm, pp)
-        new_m = np.where(inside, a * pm + b * e_minus * pp, pm)
-        psi_p, psi_m = new_p, new_m
+        if method == "first_order":
+            pp = np.fft.ifft2(np.fft.fft2(psi_p) * prop_p) * g
+            pm = np.fft.ifft2(np.fft.fft2(psi_m) * prop_m) * g
+            new_p = np.where(inside, a * pp + b * e_plus * pm, pp)
+            new_m = np.where(inside, a * pm + b * e_minus * pp, pm)
+            psi_p, psi_m = new_p, new_m
+        else:
+            for props, a_s, b_s in stages:
+                if props is not None:
+                    psi_p = np.fft.ifft2(np.fft.fft2(psi_p) * props[0])
+                    psi_m = np.fft.ifft2(np.fft.fft2(psi_m) * props[1])
+                new_p = np.where(inside, a_s * psi_p + b_s * e_plus * psi_m, psi_p)
+                new_m = np.where(inside, a_s * psi_m + b_s * e_minus * psi_p, psi_m)
+                psi_p, psi_m = new_p, new_m
+            psi_p = psi_p * g
+            psi_m = psi_m * g
         if record_every > 0 and (step + 1) % record_every == 0:
             slot = (step + 1) // record_every - 1
             records[:, slot, 0] = psi_p

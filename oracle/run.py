@@ -51,8 +51,10 @@ def mask_of(wl) -> np.ndarray:
     return np.stack([cr.inside(n) for n in range(wl.nz)])
 
 
-def run_workload3d(wl, n_begin=0, n_end=None, psi_in=None, record_every=None):
-    """March a 3D workload (fields [B][2][Ny][Nx]) from n_begin to n_end."""
+def run_workload3d(wl, n_begin=0, n_end=None, psi_in=None, record_every=None,
+                   method="first_order"):
+    """March a 3D workload (fields [B][2][Ny][Nx]) from n_begin to n_end with
+    the operator splitting ``method`` (see ``bpm.split_stages``)."""
     from . import bpm3d
     n_end = wl.nz if n_end is None else n_end
     plans = [bpm3d.energy_plan3d(float(e), wl.e_ref_ev, wl.theta_b_ref_rad, complex(wl.chi0),
@@ -74,4 +76,5 @@ def run_workload3d(wl, n_begin=0, n_end=None, psi_in=None, record_every=None):
     cr.set_strain(s.pop("kind"), ux3=s.get("ux"), params=s.get("params"))
     psi = wl.psi0 if psi_in is None else psi_in
     rec = wl.record_every if record_every is None else record_every
-    return bpm3d.march3d(plans, psi, cr, n_begin, n_end, rec, wl.dx_um, wl.dy_um)
+    return bpm3d.march3d(plans, psi, cr, n_begin, n_end, rec, wl.dx_um, wl.dy_um,
+                         method=method, chi=(complex(wl.chi0), complex(wl.chih)))
