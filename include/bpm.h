@@ -151,8 +151,9 @@ int bpm_set_strain(bpm_plan_t plan, int32_t kind, const double* ux_um,
  * side of the full-step propagation; at nx = 4096 one 4-CTA half-band split
  * per solve while every solve gets four SMs, else one 2-CTA cluster per
  * solve while every solve gets two SMs and nx != 2048, else one CTA per
- * solve); 3D plans take the
- * first-order step only; other combinations return BPM_ERR_INVALID.
+ * solve); 3D plans take the first-order step and Verlet (the row kernel,
+ * which holds both bands of a line, applies the half-step couplings);
+ * other combinations return BPM_ERR_INVALID.
  * bpm_submit takes FP32 plans set to Verlet (one CTA per row as well).
  * BPM_ERR_BUSY while tickets are pending. */
 enum bpm_splitting {

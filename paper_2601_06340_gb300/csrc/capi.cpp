@@ -571,6 +571,18 @@ static int make_plan(const bpm_problem* p, int ny, double dy_um, double y0_um,
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(static_cast<float2*>(pl->d_rows) + coup.size(), gph.data(),
                             gph.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+      // then (a - 1, b) of a half step, for the second-order splitting
+      std::vector<float2> coup_half(2 * size_t(pl->nb));
+      for (int r = 0; r < pl->nb; ++r) {
+        std::complex<double> ah, bh;
+        coupling_frac(pl, r, 0.5, &ah, &bh);
+        coup_half[2 * r] = make_float2(float((ah - 1.0).real()), float((ah - 1.0).imag()));
+        coup_half[2 * r + 1] = make_float2(float(bh.real()), float(bh.imag()));
+      }
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(static_cast<float2*>(pl->d_rows) + 3 * size_t(pl->nb),
+                            coup_half.data(), coup_half.size() * sizeof(float2),
+                            cudaMemcpyHostToDevice, st);
       for (int r = 0; r < pl->nb && e == cudaSuccess; ++r) {
         std::vector<float2> t;
         vol_prop_table(pl, r, &t);
@@ -655,8 +667,8 @@ int bpm_set_splitting(bpm_plan_t plan, int32_t method) {
   if (plan->pending) return fail(BPM_ERR_BUSY, "plan has pending tickets");
   if (method < BPM_SPLIT_FIRST_ORDER || method > BPM_SPLIT_FOREST_RUTH)
     return fail(BPM_ERR_INVALID, "unknown splitting method");
-  if (method != BPM_SPLIT_FIRST_ORDER && plan->ny > 1)
-    return fail(BPM_ERR_INVALID, "higher-order splitting needs a 2D plan");
+  if (method == BPM_SPLIT_FOREST_RUTH && plan->ny > 1)
+    return fail(BPM_ERR_INVALID, "3D plans march first order or Verlet");
   if (plan->precision == BPM_FP32_FUSED && method != BPM_SPLIT_FIRST_ORDER &&
       (method != BPM_SPLIT_VERLET || plan->logn < 8 || plan->logn > 12))
     return fail(BPM_ERR_INVALID,

@@ -19,10 +19,10 @@ int set_smem(K kernel, int bytes, std::atomic<bool>* done, const char* what) {
 }
 
 // (shared-memory attributes are set by prepare_kernels before any launch)
-template <int LX, bool EX>
+template <int LX, bool EX, bool HALF>
 int row_launch(const VolParams& p, cudaStream_t st) {
   using C = VolRowCfg<LX>;
-  vol_row_kernel<LX, EX><<<p.nb * p.ny, C::THREADS, C::SMEM, st>>>(p);
+  vol_row_kernel<LX, EX, HALF><<<p.nb * p.ny, C::THREADS, C::SMEM, st>>>(p);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? BPM_OK : cuda_fail(e, "vol row kernel");
 }
@@ -39,8 +39,9 @@ int col_launch(const VolParams& p, cudaStream_t st) {
 // capture (the first launch would set them too, but not inside a capture).
 template <bool EX>
 int prepare_kernels(int lognx, int logny) {
-  static std::atomic<bool> done[2][16] = {};   // callers' and server threads
+  static std::atomic<bool> done[3][16] = {};   // callers' and server threads
   auto row = [&](auto kern, int bytes) { return set_smem(kern, bytes, &done[0][lognx], "vol row"); };
+  auto rowh = [&](auto kern, int bytes) { return set_smem(kern, bytes, &done[2][lognx], "vol row"); };
   auto col = [&](auto kern, int bytes) { return set_smem(kern, bytes, &done[1][logny], "vol col"); };
   int rc = BPM_OK;
   switch (lognx) {
@@ -52,6 +53,14 @@ int prepare_kernels(int lognx, int logny) {
     default: return fail(BPM_ERR_INVALID, "3D: unsupported nx");
   }
   if (rc != BPM_OK) return rc;
+  switch (lognx) {   // the second-order form of the row kernel
+    case 8: rc = rowh(vol_row_kernel<8, EX, true>, VolRowCfg<8>::SMEM); break;
+    case 9: rc = rowh(vol_row_kernel<9, EX, true>, VolRowCfg<9>::SMEM); break;
+    case 10: rc = rowh(vol_row_kernel<10, EX, true>, VolRowCfg<10>::SMEM); break;
+    case 11: rc = rowh(vol_row_kernel<11, EX, true>, VolRowCfg<11>::SMEM); break;
+    default: rc = rowh(vol_row_kernel<12, EX, true>, VolRowCfg<12>::SMEM); break;
+  }
+  if (rc != BPM_OK) return rc;
   switch (logny) {
     case 8: return col(vol_col_kernel<8, EX>, VolColCfg<8>::SMEM);
     case 9: return col(vol_col_kernel<9, EX>, VolColCfg<9>::SMEM);
@@ -61,13 +70,23 @@ int prepare_kernels(int lognx, int logny) {
 }
 
 template <bool EX>
-int row_dispatch(int lognx, const VolParams& p, cudaStream_t st) {
+int row_dispatch(int lognx, const VolParams& p, cudaStream_t st, bool half) {
+  if (half) {
+    switch (lognx) {
+      case 8: return row_launch<8, EX, true>(p, st);
+      case 9: return row_launch<9, EX, true>(p, st);
+      case 10: return row_launch<10, EX, true>(p, st);
+      case 11: return row_launch<11, EX, true>(p, st);
+      case 12: return row_launch<12, EX, true>(p, st);
+      default: return fail(BPM_ERR_INVALID, "3D: unsupported nx");
+    }
+  }
   switch (lognx) {
-    case 8: return row_launch<8, EX>(p, st);
-    case 9: return row_launch<9, EX>(p, st);
-    case 10: return row_launch<10, EX>(p, st);
-    case 11: return row_launch<11, EX>(p, st);
-    case 12: return row_launch<12, EX>(p, st);
+    case 8: return row_launch<8, EX, false>(p, st);
+    case 9: return row_launch<9, EX, false>(p, st);
+    case 10: return row_launch<10, EX, false>(p, st);
+    case 11: return row_launch<11, EX, false>(p, st);
+    case 12: return row_launch<12, EX, false>(p, st);
     default: return fail(BPM_ERR_INVALID, "3D: unsupported nx");
   }
 }
@@ -105,6 +124,7 @@ struct VolGraph {
   const void* rec = nullptr;
   const void* pw = nullptr;
   int n_begin = -1, n_end = -1;
+  bool half = false;   // second-order splitting
 };
 
 }  // namespace
@@ -149,6 +169,7 @@ int vol_march(bpm_plan_s* plan, float2* state, float2* d_rec, double* d_pw, int 
   p.twy = static_cast<const float4*>(plan->d_twy);
   p.coup = static_cast<const float2*>(plan->d_rows);
   p.gphase = reinterpret_cast<const double*>(static_cast<const float2*>(plan->d_rows) + 2 * plan->nb);
+  p.coup_half = static_cast<const float2*>(plan->d_rows) + 3 * plan->nb;
   p.nb = plan->nb;
   p.nx = plan->nx;
   p.ny = plan->ny;
@@ -157,7 +178,11 @@ int vol_march(bpm_plan_s* plan, float2* state, float2* d_rec, double* d_pw, int 
   p.n_rec = plan->n_rec;
   const bool ex = fused_exact_constants();
   cudaStream_t lst = st;   // the stream the kernels are enqueued on
-  auto row = [&]() { return ex ? row_dispatch<true>(plan->logn, p, lst) : row_dispatch<false>(plan->logn, p, lst); };
+  const bool half = plan->split == BPM_SPLIT_VERLET;
+  auto row = [&]() {
+    return ex ? row_dispatch<true>(plan->logn, p, lst, half)
+              : row_dispatch<false>(plan->logn, p, lst, half);
+  };
   auto col = [&]() { return ex ? col_dispatch<true>(plan->logny, p, lst) : col_dispatch<false>(plan->logny, p, lst); };
   auto enqueue = [&]() {
     p.mode = 0;
@@ -198,7 +223,7 @@ int vol_march(bpm_plan_s* plan, float2* state, float2* d_rec, double* d_pw, int 
       }
     }
     const bool hit = g->exec && g->state == state && g->rec == p.records && g->pw == p.pwpart &&
-                     g->n_begin == n_begin && g->n_end == n_end;
+                     g->n_begin == n_begin && g->n_end == n_end && g->half == half;
     if (!hit) {
       cudaGraph_t graph = nullptr;
       lst = g->cap;
@@ -224,6 +249,7 @@ int vol_march(bpm_plan_s* plan, float2* state, float2* d_rec, double* d_pw, int 
       g->pw = p.pwpart;
       g->n_begin = n_begin;
       g->n_end = n_end;
+      g->half = half;
     }
     cudaError_t e = cudaGraphLaunch(g->exec, st);
     if (e != cudaSuccess) return cuda_fail(e, "3D march graph launch");

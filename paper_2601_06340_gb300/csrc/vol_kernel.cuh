@@ -33,6 +33,7 @@ struct VolParams {
   const float4* twx;       // [Nx] hi/lo twiddles
   const float4* twy;       // [Ny]
   const float2* coup;      // [B][2]: (a - 1, b) per row
+  const float2* coup_half; // [B][2]: the same for half a step (second-order splitting)
   const double* gphase;    // [B]
   int nb, nx, ny;
   int n;                   // absolute step of this launch
@@ -58,7 +59,12 @@ struct VolRowCfg {
   static_assert(SMEM <= 232448, "fits one SM");
 };
 
-template <int LOGN, bool EX>
+// HALF = true: the second-order (Verlet) step of Eq. split-op.  The CTA
+// holds both bands of its line, so the launch's first step starts with a
+// half-step coupling (mode 0) and every step ends with its second half and,
+// unless it is the launch's last, the next step's first half; records are
+// taken after the second half.
+template <int LOGN, bool EX, bool HALF = false>
 __global__ void __launch_bounds__(VolRowCfg<LOGN>::THREADS)
     vol_row_kernel(VolParams p) {
   using C = VolRowCfg<LOGN>;
@@ -93,6 +99,18 @@ __global__ void __launch_bounds__(VolRowCfg<LOGN>::THREADS)
   if (p.mode == 0) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = p.org[off + t + j * T];
+    if constexpr (HALF) {   // the launch's first half-step, on the slice of its first step
+      const float2* ph = p.phasor + size_t(p.n) * plane + size_t(y) * N;
+      const float2 am1 = p.coup_half[2 * r], bb = p.coup_half[2 * r + 1];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float2 q = make_float2(__shfl_xor_sync(0xffffffffu, v[j].x, 16),
+                                     __shfl_xor_sync(0xffffffffu, v[j].y, 16));
+        v[j] = couple_cell(v[j], q, __ldg(&ph[t + j * T]), band, am1, bb);
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) p.org[off + t + j * T] = v[j];
+    }
   } else {
     // every global read of the step is issued here, so their latencies
     // overlap (a line is too little work to hide three in a row)
@@ -102,6 +120,13 @@ __global__ void __launch_bounds__(VolRowCfg<LOGN>::THREADS)
     for (int j = 0; j < 16; ++j) {
       org[j] = p.org[off + t + j * T];
       phv[j] = __ldg(&ph[t + j * T]);
+    }
+    [[maybe_unused]] float2 phn[16];   // second order: the next step's slice
+    if constexpr (HALF) {
+      if (p.mode == 1) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) phn[j] = __ldg(&ph[plane + t + j * T]);
+      }
     }
     // inverse FFT along x of the increment's x-spectrum
     constexpr int P = NP - 1;
@@ -124,7 +149,8 @@ __global__ void __launch_bounds__(VolRowCfg<LOGN>::THREADS)
     f2_twiddle<true>(v, w0);
     dft<16, true, EX>(v);
     // psi_p = psi + increment, then the coupling with the other band (lane ^ 16)
-    const float2 am1 = p.coup[2 * r], bb = p.coup[2 * r + 1];
+    const float2 am1 = HALF ? p.coup_half[2 * r] : p.coup[2 * r];
+    const float2 bb = HALF ? p.coup_half[2 * r + 1] : p.coup[2 * r + 1];
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = cadd<false>(org[j], v[j]);   // scalar: measured faster here
 #pragma unroll
@@ -160,6 +186,16 @@ __global__ void __launch_bounds__(VolRowCfg<LOGN>::THREADS)
           double tot = 0.0;
           for (int w = 0; w < C::WARPS; ++w) tot += red[2 * w + threadIdx.x];
           p.pwpart[((size_t(r) * p.n_rec + slot) * 2 + threadIdx.x) * p.ny + y] = tot;
+        }
+      }
+    }
+    if constexpr (HALF) {
+      if (p.mode == 1) {   // the next step's first half, on its slice
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float2 q = make_float2(__shfl_xor_sync(0xffffffffu, v[j].x, 16),
+                                       __shfl_xor_sync(0xffffffffu, v[j].y, 16));
+          v[j] = couple_cell(v[j], q, phn[j], band, am1, bb);
         }
       }
     }

@@ -96,3 +96,23 @@ def test_vol_rejects_bad_sizes_and_server(bpm_lib):
         out = np.empty_like(wl.psi0)
         with pytest.raises(binding.BpmError):
             binding.bpm_submit(plan.handle, wl.psi0, out)
+
+
+def test_vol_verlet_matches_oracle(bpm_lib):
+    """Second-order (Verlet) splitting on the 3D path against the 3D
+    oracle's Verlet march: fields, records, powers; a resumed march equals
+    the whole one; and the scheme differs from the first-order step."""
+    wl = _small(nz=60, record_every=20)
+    ref = orun.run_workload3d(wl, method="verlet")
+    with binding.Plan(wl, FP32, splitting=binding.BPM_SPLIT_VERLET) as plan:
+        out = plan.propagate()
+        half = plan.propagate(n_end=30, records=False).psi
+        rest = plan.propagate(psi_in=half, n_begin=30, records=False).psi
+    err = _rel(out.psi, ref.psi)
+    assert err <= TOL_FP32, err
+    for r in range(ref.records.shape[1]):
+        assert _rel(out.records[:, r], ref.records[:, r]) <= TOL_FP32, r
+    assert np.allclose(out.powers, ref.powers, rtol=2 * TOL_FP32, atol=1e-12 * ref.powers.max())
+    assert _rel(rest, out.psi) <= 1e-5
+    first = orun.run_workload3d(wl)
+    assert _rel(first.psi, ref.psi) > max(1e-6, 10 * err)
