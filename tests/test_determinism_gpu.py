@@ -39,6 +39,10 @@ CASES = {
                                                       dy_um=0.08, dz_um=0.1, cube_um=5.0,
                                                       fwhm_um=1.5, record_every=10),
                    FP32, binding.BPM_SPLIT_FIRST_ORDER),
+    "3D 256x256 Verlet": (lambda: inputs.cube_dislocation_3d(nx=256, ny=256, nz=40, dx_um=0.08,
+                                                             dy_um=0.08, dz_um=0.1, cube_um=5.0,
+                                                             fwhm_um=1.5, record_every=10),
+                          FP32, binding.BPM_SPLIT_VERLET),
 }
 
 

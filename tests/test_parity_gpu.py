@@ -267,11 +267,12 @@ def _capture_case(name):
         return inputs.serving_request(rng, 4096, 300), binding.BPM_SPLIT_VERLET
     return (inputs.cube_dislocation_3d(nx=256, ny=256, nz=40, dx_um=0.08, dy_um=0.08,
                                        dz_um=0.1, cube_um=5.0, fwhm_um=1.5, record_every=10),
-            binding.BPM_SPLIT_FIRST_ORDER)
+            binding.BPM_SPLIT_VERLET if name.endswith("Verlet") else binding.BPM_SPLIT_FIRST_ORDER)
 
 
 @pytest.mark.parametrize("name", ["cluster N=1024", "split N=4096", "rotated batch 160x4096",
-                                  "Verlet N=1024", "Verlet N=4096", "3D 256x256"])
+                                  "Verlet N=1024", "Verlet N=4096", "3D 256x256",
+                                  "3D 256x256 Verlet"])
 def test_device_api_graph_capture_replays(bpm_lib, monkeypatch, name):
     """A device-API march captured into a CUDA graph (its per-call uploads go
     through kernel parameters) replays to the same bits as the march run
