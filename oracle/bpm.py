@@ -27,7 +27,7 @@ approach"):
   where psi_p+- is each envelope propagated through its own angular-spectrum
   operator exp(i dz^ sqrt(1 - kx^2)) centred on its own carrier.
 
-Readings where the paper is silent or ambiguous (all listed in the design doc):
+Readings where the paper is silent or ambiguous:
 
 * FFT convention: numpy's (forward kernel e^{-2 pi i m j / N}).  With it the
   + envelope's spectrum sits at kx = q + s, so its propagator uses

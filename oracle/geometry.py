@@ -16,7 +16,7 @@ only through u_x (Eq. Authier), here from
   u_x = b / (2 pi) [atan2(z', x') + x' z' / (2 (1 - nu) (x'^2 + z'^2))];
 * a user array.
 
-Readings (listed in DESIGN.md):
+Readings of the paper taken here:
 
 * Pi is binary; a cell is inside when its centre x_j = x0 + j dx,
   z_n = n dz is inside (slab test with <= on both faces, even-odd rule with
