@@ -223,10 +223,14 @@ int bpm_propagate_device(bpm_plan_t plan, const void* d_psi_in,
 int bpm_device_status(bpm_plan_t plan, void* stream);
 
 /* Energy -> time synthesis of a batch of exit fields (Section
- * "Time-Dependent Simulation"): out[b][x][m] = (1/B) sum_j in[j][b][x]
- * exp(+2 pi i j m / B) over the B rows (energies ascending), B a power of
- * two in [2, 4096].  Device buffers, c64 if precision == BPM_FP32_FUSED
- * else c128; in: [B][2][nx], out: [2][nx][B].  Asynchronous on stream. */
+ * "Time-Dependent Simulation"): out[b][x][m] = sum_j in[j][b][x]
+ * exp(-2 pi i j m / B) over the B rows (energies E_j = E_0 + j dE,
+ * ascending), i.e. the superposition of the monochromatic solutions with
+ * time dependence exp(-i omega_j t) (Eq. fov4: a forward wave advances by
+ * exp(+i k dz)) relative to the carrier exp(-i omega_0 t), sampled at
+ * t_m = m h / (B dE).  B a power of two in [2, 4096].  Device buffers, c64
+ * if precision == BPM_FP32_FUSED else c128; in: [B][2][nx], out:
+ * [2][nx][B].  Asynchronous on stream. */
 int bpm_omega_to_t_device(const void* d_in, void* d_out, int32_t n_energy,
                           int32_t nx, int32_t precision, void* stream);
 

@@ -12,20 +12,23 @@ anything here, and this package imports nothing from the product path.
 
 Modules
 -------
+``fft``       the discrete Fourier transform written out: the O(N^2)
+              definition for N <= 256, radix-2 decimation in time above
+              (no library FFT on the march's path).
 ``bpm``       plan scalars (Eqs. fov3-fov12), Bessel series, the first-order
-              two-beam march (Eq. fov10), powers and records.
+              two-beam march (Eq. fov10) and the splitting schemes of Eq.
+              split-op, powers and records.
 ``geometry``  crystal-shape masks (slab of any asymmetry angle, polygon) and
               displacement fields (cylindrical bend, Eq. fov110; edge
               dislocation, Eq. fov120 with the Burgers vector normal to the
               line), and the strain phase h*u_x of Eq. (Authier).
-``timeaxis``  the energy -> time transform of a batch of exit fields
+``timeaxis``  the energy -> time synthesis of a batch of exit fields
               (Section "Time-Dependent Simulation of Reflection").
 ``bpm3d``     the same march with both transverse coordinates (x, y):
               2D angular-spectrum propagators, box crystals, 3D arrays.
 
 Every function is pinned by a ``-m "not gpu"`` test in
-``tests/test_oracle_pins.py`` (3D: ``tests/test_oracle3d_pins.py``) against closed forms, invariants, brute force
-or a library routine.  The one function without such a pin is
-``timeaxis.omega_to_t`` beyond its DFT definition: its physical time axis
-reading is stated in its docstring.
+``tests/test_oracle_pins.py`` (3D: ``tests/test_oracle3d_pins.py``) against
+closed forms, physical laws, invariants, brute force or an independent
+library routine; none is left unpinned.
 """

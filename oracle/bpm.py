@@ -29,7 +29,8 @@ approach"):
 
 Readings where the paper is silent or ambiguous:
 
-* FFT convention: numpy's (forward kernel e^{-2 pi i m j / N}).  With it the
+* FFT convention: forward kernel e^{-2 pi i m j / N} (numpy's), computed by
+  the oracle's own DFT / radix-2 FFT (``oracle.fft``).  With it the
   + envelope's spectrum sits at kx = q + s, so its propagator uses
   sqrt(1 - (q + s)^2) and the - envelope's uses sqrt(1 - (q - s)^2).  The
   paper's "p_-+" pairing is the same statement under the opposite sign
@@ -52,6 +53,8 @@ import math
 from dataclasses import dataclass
 
 import numpy as np
+
+from . import fft as dft
 
 # h*c in eV * Angstrom (CODATA 2018: h and c exact, e exact).
 HC_EV_ANGSTROM = 12398.419843320026
@@ -146,7 +149,7 @@ def energy_plan(energy_ev: float, e_ref_ev: float, theta_b_ref_rad: float,
     b = 1j * bessel_series(1, w) * e_phi0
 
     # Angular-spectrum propagators of Eq. fov10, each centred on its carrier.
-    q = TWO_PI * np.fft.fftfreq(nx, d=dxh)
+    q = TWO_PI * dft.fftfreq(nx, dxh)
     root_plus = np.sqrt(1.0 - (q + s) ** 2)
     root_minus = np.sqrt(1.0 - (q - s) ** 2)
     delta_plus = -q * (q + 2.0 * s) / (root_plus + c)
@@ -258,7 +261,7 @@ def march(plans: list[EnergyPlan], psi0: np.ndarray, slices, n_begin: int,
     # once, after the step's last stage.
     stages = []
     if method == "first_order":
-        stages.append(((prop_p, prop_m), g, a, b))
+        stages.append(((prop_p, prop_m), g[:, :, None], a, b))
     else:
         chi0, chih = chi
         for frac_a, frac_b in split_stages(method):
@@ -270,30 +273,34 @@ def march(plans: list[EnergyPlan], psi0: np.ndarray, slices, n_begin: int,
             stages.append((props, 1.0, np.array([x[0] for x in ab])[:, None],
                            np.array([x[1] for x in ab])[:, None]))
 
-    psi_p = psi0[:, 0, :].copy()
-    psi_m = psi0[:, 1, :].copy()
+    # band axis 1: psi[:, 0] = psi_+, psi[:, 1] = psi_-; each band's
+    # propagator table sits at the same index of the stacked tables.
+    stage_props = [None if props is None else np.stack(props, axis=1)
+                   for props, _, _, _ in stages]
+    psi = psi0.copy()
     for step in range(n_begin, n_end):
         inside, theta = slices(step)
         e_plus = np.exp(1j * theta)     # exp(+i h u_x) on Delta_eps'_{+1}
         e_minus = np.exp(-1j * theta)   # exp(-i h u_x) on Delta_eps'_{-1}
-        for props, gs, a_s, b_s in stages:
+        for (_, gs, a_s, b_s), props in zip(stages, stage_props):
             if props is not None:
                 # Free propagation of each envelope through its own band operator.
-                psi_p = np.fft.ifft(np.fft.fft(psi_p, axis=-1) * props[0], axis=-1) * gs
-                psi_m = np.fft.ifft(np.fft.fft(psi_m, axis=-1) * props[1], axis=-1) * gs
+                psi = dft.ifft(dft.fft(psi) * props) * gs
+            psi_p, psi_m = psi[:, 0], psi[:, 1]
             # Real-space coupling through chi_0, chi_h, the strain phase and Pi.
             new_p = np.where(inside, a_s * psi_p + b_s * e_plus * psi_m, psi_p)
             new_m = np.where(inside, a_s * psi_m + b_s * e_minus * psi_p, psi_m)
-            psi_p, psi_m = new_p, new_m
+            psi = np.stack([new_p, new_m], axis=1)
         if method != "first_order":
-            psi_p = psi_p * g
-            psi_m = psi_m * g
+            psi = psi * g[:, :, None]
+        psi_p, psi_m = psi[:, 0], psi[:, 1]
         if record_every > 0 and (step + 1) % record_every == 0:
             slot = (step + 1) // record_every - 1
             records[:, slot, 0, :] = psi_p
             records[:, slot, 1, :] = psi_m
             powers[:, slot, 0] = band_power(psi_p, dx_um)
             powers[:, slot, 1] = band_power(psi_m, dx_um)
+    psi_p, psi_m = psi[:, 0], psi[:, 1]
     powers[:, n_rec, 0] = band_power(psi_p, dx_um)
     powers[:, n_rec, 1] = band_power(psi_m, dx_um)
     return MarchResult(np.stack([psi_p, psi_m], axis=1), records, powers)

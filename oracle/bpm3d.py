@@ -16,7 +16,7 @@ with both transverse coordinates:
 * band powers are dx dy sum |psi|^2.
 
 The paper says the generalisation from (x, z) is straightforward (Sec. 2)
-and runs 3D cases (Sec. 6).  Readings: numpy's fft2 over (y, x);
+and runs 3D cases (Sec. 6).  Readings: the 2D DFT over (y, x) (the oracle's own, ``oracle.fft``);
 qx = 2 pi fftfreq(Nx, dx^), qy = 2 pi fftfreq(Ny, dy^); cells at
 (x_j, y_i, z_n) = (x0 + j dx, y0 + i dy, n dz); the 2D crystal kinds and
 strain fields apply at every y; a box crystal {x0 <= x <= x1, y0 <= y <= y1,
@@ -31,6 +31,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import bpm, geometry
+from . import fft as dft
 
 CRYSTAL_BOX = 6
 
@@ -53,8 +54,8 @@ def energy_plan3d(energy_ev: float, e_ref_ev: float, theta_b_ref_rad: float,
     base = bpm.energy_plan(energy_ev, e_ref_ev, theta_b_ref_rad, chi0, chih, nx, dx_um, dz_um)
     s, c, dzh = base.s, base.c, base.dzh
     dyh = base.k_um * dy_um
-    qx = 2.0 * math.pi * np.fft.fftfreq(nx, d=base.dxh)
-    qy = 2.0 * math.pi * np.fft.fftfreq(ny, d=dyh)
+    qx = 2.0 * math.pi * dft.fftfreq(nx, base.dxh)
+    qy = 2.0 * math.pi * dft.fftfreq(ny, dyh)
     QX, QY = np.meshgrid(qx, qy)          # [Ny][Nx]
     props, deltas = [], []
     for sign in (+1.0, -1.0):
@@ -169,16 +170,16 @@ def march3d(plans: list[Plan3D], psi0: np.ndarray, slices, n_begin: int, n_end: 
         e_plus = np.exp(1j * theta)
         e_minus = np.exp(-1j * theta)
         if method == "first_order":
-            pp = np.fft.ifft2(np.fft.fft2(psi_p) * prop_p) * g
-            pm = np.fft.ifft2(np.fft.fft2(psi_m) * prop_m) * g
+            pp = dft.ifft2(dft.fft2(psi_p) * prop_p) * g
+            pm = dft.ifft2(dft.fft2(psi_m) * prop_m) * g
             new_p = np.where(inside, a * pp + b * e_plus * pm, pp)
             new_m = np.where(inside, a * pm + b * e_minus * pp, pm)
             psi_p, psi_m = new_p, new_m
         else:
             for props, a_s, b_s in stages:
                 if props is not None:
-                    psi_p = np.fft.ifft2(np.fft.fft2(psi_p) * props[0])
-                    psi_m = np.fft.ifft2(np.fft.fft2(psi_m) * props[1])
+                    psi_p = dft.ifft2(dft.fft2(psi_p) * props[0])
+                    psi_m = dft.ifft2(dft.fft2(psi_m) * props[1])
                 new_p = np.where(inside, a_s * psi_p + b_s * e_plus * psi_m, psi_p)
                 new_m = np.where(inside, a_s * psi_m + b_s * e_minus * psi_p, psi_m)
                 psi_p, psi_m = new_p, new_m

@@ -45,8 +45,11 @@ __global__ void finish_kernel(const TIn* __restrict__ state, double2* __restrict
 }
 
 // Energy -> time: for each (band, x) line, out[band][x][m] =
-// (1/B) sum_j in[j][band][x] exp(+2 pi i j m / B), by a radix-2 Stockham
-// transform in shared memory.  A block handles `tx` consecutive x of one band.
+// sum_j in[j][band][x] exp(-2 pi i j m / B) -- the superposition of the
+// monochromatic solutions, each with time dependence exp(-i omega_j t)
+// (Eq. fov4 advances a forward wave by exp(+i k dz)) -- by a radix-2
+// Stockham transform in shared memory.  A block handles `tx` consecutive x
+// of one band.
 template <typename C, typename R>
 __global__ void omega_to_t_kernel(const C* __restrict__ in, C* __restrict__ out, int nb,
                                   int logb, int nx, int tx) {
@@ -68,11 +71,11 @@ __global__ void omega_to_t_kernel(const C* __restrict__ in, C* __restrict__ out,
       const int k = j % ns;
       const C u = a[xi * nb + j];
       C v = a[xi * nb + j + half];
-      // w = exp(+i pi k / ns)
+      // w = exp(-i pi k / ns)
       R sw, cw;
       if constexpr (sizeof(R) == 8) sincospi(double(k) / double(ns), &sw, &cw);
       else sincospif(float(k) / float(ns), &sw, &cw);
-      v = C{v.x * cw - v.y * sw, v.x * sw + v.y * cw};
+      v = C{v.x * cw + v.y * sw, v.y * cw - v.x * sw};
       const int base = (j / ns) * ns * 2 + k;
       b[xi * nb + base] = C{u.x + v.x, u.y + v.y};
       b[xi * nb + base + ns] = C{u.x - v.x, u.y - v.y};
@@ -82,11 +85,9 @@ __global__ void omega_to_t_kernel(const C* __restrict__ in, C* __restrict__ out,
     a = b;
     b = t;
   }
-  const R scale = R(1) / R(nb);
   for (int c = threadIdx.x; c < nb * tx; c += blockDim.x) {
     const int xi = c / nb, m = c % nb;
-    const C v = a[xi * nb + m];
-    out[(size_t(band) * nx + x0 + xi) * nb + m] = C{v.x * scale, v.y * scale};
+    out[(size_t(band) * nx + x0 + xi) * nb + m] = a[xi * nb + m];
   }
 }
 

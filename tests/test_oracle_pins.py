@@ -13,6 +13,7 @@ import pytest
 import scipy.special
 
 from oracle import bpm, geometry, timeaxis
+from oracle import fft as dft
 
 E = 8000.0
 THETA = math.radians(23.65)
@@ -31,22 +32,34 @@ def _crystal(nx, x0, dx, dz, kind):
 
 # ---------------------------------------------------------------- P1 -------
 def test_p1_fft_convention_and_q_grid():
-    """The oracle's q_m is the wave number of DFT bin m (numpy convention):
-    a sampled plane wave exp(i q_m x^) transforms to a single spike at m, and
-    numpy's FFT equals the brute-force DFT sum with the e^{-2 pi i m j/N}
-    kernel."""
+    """The oracle's own transforms (``oracle.fft``): the O(N^2) definition
+    and the radix-2 FFT equal a brute-force sum with the e^{-2 pi i m j/N}
+    kernel written out term by term here (N = 8..512) and numpy's FFT, an
+    independent library routine (N up to 16384); the inverse undoes the
+    forward transform.  The oracle's q_m is the wave number of DFT bin m:
+    a sampled plane wave exp(i q_m x^) transforms to a single spike at m."""
     rng = np.random.default_rng(1)
-    for n in (8, 16, 64, 256):
+    for n in (8, 16, 64, 256, 512):
         x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
-        jj = np.arange(n)
-        brute = np.array([np.sum(x * np.exp(-2j * np.pi * m * jj / n))
-                          for m in range(n)])
-        assert np.max(np.abs(np.fft.fft(x) - brute)) <= 1e-12 * np.max(np.abs(brute))
+        brute = np.zeros(n, dtype=np.complex128)
+        for m in range(n):
+            for j in range(n):
+                ang = -2.0 * math.pi * ((m * j) % n) / n
+                brute[m] += x[j] * complex(math.cos(ang), math.sin(ang))
+        assert np.max(np.abs(dft.fft(x) - brute)) <= 1e-13 * np.max(np.abs(brute))
+    for n in (8, 256, 512, 1024, 4096, 16384):
+        x = rng.standard_normal((3, 2, n)) + 1j * rng.standard_normal((3, 2, n))
+        ref = np.fft.fft(x, axis=-1)
+        assert np.max(np.abs(dft.fft(x) - ref)) <= 2e-15 * np.max(np.abs(ref))
+        assert np.max(np.abs(dft.ifft(ref) - x)) <= 2e-15 * np.max(np.abs(x))
+        assert np.allclose(dft.fftfreq(n, 0.37), np.fft.fftfreq(n, 0.37), rtol=1e-15, atol=0)
+    y = rng.standard_normal((3, 32, 512)) + 1j * rng.standard_normal((3, 32, 512))
+    assert np.max(np.abs(dft.fft2(y) - np.fft.fft2(y))) <= 1e-14 * np.max(np.abs(np.fft.fft2(y)))
     nx, dx = 64, 0.3
     p = _plan(nx, dx, 0.05)
     xh = p.k_um * (-7.0 + np.arange(nx) * dx)
     for m in (0, 1, 5, nx // 2 - 1, nx // 2, nx // 2 + 3, nx - 1):
-        spec = np.fft.fft(np.exp(1j * p.q[m] * xh))
+        spec = dft.fft(np.exp(1j * p.q[m] * xh))
         others = np.delete(np.abs(spec), m)
         assert abs(abs(spec[m]) - nx) < 1e-9 and np.max(others) < 1e-9
 
@@ -551,7 +564,100 @@ def test_edge_dislocation_burgers_circuit():
 
 
 # ---------------------------------------------------- time axis -------------
-def test_omega_to_t_matches_direct_sum():
+# Physical constants typed here independently of the oracle's own.
+C_UM_PER_FS = 0.299792458                  # speed of light, um / fs (exact)
+HBAR_EV_FS = 6.62607015e-34 / 1.602176634e-19 * 1e15 / (2.0 * math.pi)
+
+
+def _vacuum_pulse(n_energy=64, de=10.0 / 256, e0=9000.0, sigma_ev=0.1, nx=512, dx=0.5,
+                  dz=0.1, nsteps=100, fwhm=60.0):
+    """A transform-limited pulse (Gaussian spectrum, flat phase) crossing the
+    origin at t = 0 along the Bragg direction of e0, marched through vacuum
+    (chi = 0) by the oracle, one energy per row (theta_B per energy, fixed
+    incident direction: row j's envelope tilt (sin theta_0 - s_j) k_j)."""
+    energies = e0 + de * (np.arange(n_energy) - n_energy // 2)
+    s0 = math.sin(THETA) * E / e0
+    theta0 = math.asin(s0)
+    x = (np.arange(nx) - nx // 2) * dx
+    plans, psi0 = [], np.zeros((n_energy, 2, nx), dtype=np.complex128)
+    for j, ej in enumerate(energies):
+        p = bpm.energy_plan(float(ej), E, THETA, 0j, 0j, nx, dx, dz)
+        plans.append(p)
+        amp = math.exp(-((ej - e0) ** 2) / (4.0 * sigma_ev ** 2))
+        beam = np.exp(-2.0 * math.log(2.0) * (x * math.cos(theta0)) ** 2 / fwhm ** 2)
+        psi0[j, 0] = amp * beam * np.exp(1j * p.k_um * (s0 - p.s) * x)
+
+    def vacuum(n):
+        return np.zeros(nx, dtype=bool), np.zeros(nx)
+    out = bpm.march(plans, psi0, vacuum, 0, nsteps, 0, dx)
+    return energies, theta0, x, psi0, out.psi
+
+
+def _peak_time(t, intensity):
+    """Time of the maximum of a sampled periodic pulse, refined by a parabola
+    through the three samples around it."""
+    m = int(np.argmax(intensity))
+    nb = len(intensity)
+    ym, y0, yp = intensity[(m - 1) % nb], intensity[m], intensity[(m + 1) % nb]
+    frac = 0.5 * (ym - yp) / (ym - 2.0 * y0 + yp)
+    return (m + frac) * (t[1] - t[0])
+
+
+def test_time_axis_a_pulse_through_vacuum_arrives_after_its_flight_time():
+    """A pulse marched a distance L through vacuum must reach the point x of
+    the exit plane at t = (x sin theta_0 + L cos theta_0) / c: the plane wave
+    front moving along (sin theta_0, cos theta_0) at the speed of light,
+    later than it entered, never earlier.  Fixes the sign of the exponent,
+    the ascending energy order and the time step h / (B dE) (a flipped sign
+    puts the peak at -t, i.e. at window - t)."""
+    nsteps, dz = 100, 0.1
+    energies, theta0, x, psi_in, psi_out = _vacuum_pulse(nsteps=nsteps, dz=dz)
+    t = timeaxis.time_axis_fs(energies)
+    window = t[1] * len(t)
+    length = nsteps * dz
+    for label, field, zz in (("entrance", psi_in, 0.0), ("exit", psi_out, length)):
+        sig = timeaxis.omega_to_t(field)            # [2][N][B]
+        for xi in (-10.0, 0.0, 12.0):
+            j = int(np.argmin(np.abs(x - xi)))
+            want = (x[j] * math.sin(theta0) + zz * math.cos(theta0)) / C_UM_PER_FS
+            got = _peak_time(t, np.abs(sig[0, j]) ** 2)
+            diff = (got - want + 0.5 * window) % window - 0.5 * window
+            assert abs(diff) < 0.05 * t[1], (label, xi, got, want)
+    # the flight over L = 10 um takes about 31 fs: far from its mirror image
+    assert 25.0 < length * math.cos(theta0) / C_UM_PER_FS < 0.5 * window
+
+
+def test_time_axis_pulse_duration_is_the_transform_limit():
+    """A Gaussian spectrum of intensity RMS sigma_E and flat phase is a pulse
+    of intensity RMS duration hbar / (2 sigma_E) (time-bandwidth product of
+    a Gaussian): fixes the scale of the time axis independently of the
+    flight time."""
+    sigma_ev = 0.1
+    energies, _, x, psi_in, _ = _vacuum_pulse(sigma_ev=sigma_ev, nsteps=1)
+    t = timeaxis.time_axis_fs(energies)
+    sig = timeaxis.omega_to_t(psi_in)
+    j = int(np.argmin(np.abs(x)))
+    inten = np.abs(sig[0, j]) ** 2
+    window = t[1] * len(t)
+    tc = (t + 0.5 * window) % window - 0.5 * window     # centred on t = 0
+    mean = np.sum(tc * inten) / np.sum(inten)
+    rms = math.sqrt(np.sum((tc - mean) ** 2 * inten) / np.sum(inten))
+    assert abs(rms / (HBAR_EV_FS / (2.0 * sigma_ev)) - 1.0) < 1e-3
+
+
+def test_time_axis_a_monochromatic_field_keeps_its_amplitude():
+    """One energy alone is a monochromatic wave: its amplitude is the same at
+    every instant and equals the solve's own (superposition of the
+    monochromatic solutions, no rescaling); B lines of equal energy spacing
+    are orthogonal over the window (Parseval: sum_m |psi(t_m)|^2 =
+    B sum_j |psi_j|^2)."""
     rng = np.random.default_rng(10)
-    f = rng.standard_normal((12, 2, 5)) + 1j * rng.standard_normal((12, 2, 5))
-    assert np.max(np.abs(timeaxis.omega_to_t(f) - timeaxis.omega_to_t_direct(f))) < 1e-14
+    nb, nx = 32, 5
+    f = np.zeros((nb, 2, nx), dtype=np.complex128)
+    f[7] = rng.standard_normal((2, nx)) + 1j * rng.standard_normal((2, nx))
+    out = timeaxis.omega_to_t(f)
+    assert np.max(np.abs(np.abs(out) - np.abs(f[7])[:, :, None])) < 1e-14
+    g = rng.standard_normal((nb, 2, nx)) + 1j * rng.standard_normal((nb, 2, nx))
+    lhs = np.sum(np.abs(timeaxis.omega_to_t(g)) ** 2, axis=-1)
+    rhs = nb * np.sum(np.abs(g) ** 2, axis=0)
+    assert np.max(np.abs(lhs / rhs - 1.0)) < 1e-13
