@@ -167,7 +167,7 @@ int bpm_set_splitting(bpm_plan_t plan, int32_t method);
  * and the two-beam envelopes of Eqs. fov6-fov10 (the Bragg shift k_d/2 is
  * along x only): each band goes through exp(i dz^ sqrt(1 - (qx +- s)^2 -
  * qy^2)), qy = 2 pi fftfreq(ny, dy^), and the coupling is pointwise in (x, y)
- * (Sec. 2; the paper's 3D cases, Sec. 6).  `problem` as for bpm_plan with
+ * (Sec. 2; the paper's 3D cases, Sec. 7).  `problem` as for bpm_plan with
  * precision BPM_FP32_FUSED and nx a power of two in [256, 4096]; ny a power
  * of two in [256, 1024], dy_um > 0, y0_um the y of the first cell.  Every
  * field of the other calls then carries [ny][nx] per band: psi [B][2][ny][nx],

@@ -16,7 +16,7 @@ with both transverse coordinates:
 * band powers are dx dy sum |psi|^2.
 
 The paper says the generalisation from (x, z) is straightforward (Sec. 2)
-and runs 3D cases (Sec. 6).  Readings: the 2D DFT over (y, x) (the oracle's own, ``oracle.fft``);
+and runs 3D cases (Sec. 7).  Readings: the 2D DFT over (y, x) (the oracle's own, ``oracle.fft``);
 qx = 2 pi fftfreq(Nx, dx^), qy = 2 pi fftfreq(Ny, dy^); cells at
 (x_j, y_i, z_n) = (x0 + j dx, y0 + i dy, n dz); the 2D crystal kinds and
 strain fields apply at every y; a box crystal {x0 <= x <= x1, y0 <= y <= y1,

@@ -69,6 +69,20 @@ struct RowDescF64 {
   double gphase;
 };
 
+// Per-plan runtime buffers of the march entry points (capi.cpp): the plan's
+// stream, the host-API record / power buffers, the common phase factors and
+// the rotated launch schedule.
+struct PlanAux {
+  cudaStream_t stream = nullptr;
+  void* d_rec = nullptr;      // host-API record buffer
+  size_t rec_bytes = 0;
+  double* d_pow = nullptr;    // host-API powers buffer
+  size_t pow_bytes = 0;
+  double2* d_g = nullptr;     // [B] common phase factors
+  RowDescF32* d_sched = nullptr;  // rotated launch schedule
+  size_t sched_cap = 0;
+};
+
 // FP64 constants of one photon energy (Eqs. fov4-fov12).
 struct EnergyConsts {
   double e_ev, k_um, s, c, dzh, dxh;
@@ -128,6 +142,7 @@ struct bpm_plan_s {
   // launch shape of the last fused march: layout 1 cluster / 0 CTA / -1 rule,
   // rotation chunk (0: one launch)
   int shape_layout = -1, shape_chunk = 0;
+  bpm::PlanAux aux;
 };
 
 namespace bpm {

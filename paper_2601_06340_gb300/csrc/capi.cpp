@@ -79,37 +79,7 @@ int device_sm_count() {
 
 }  // namespace
 
-// Per-plan auxiliaries that are not part of the public struct layout.
-struct PlanAux {
-  cudaStream_t stream = nullptr;
-  void* d_rec = nullptr;      // host-API record buffer
-  size_t rec_bytes = 0;
-  double* d_pow = nullptr;    // host-API powers buffer
-  size_t pow_bytes = 0;
-  double2* d_g = nullptr;     // [B] common phase factors
-  RowDescF32* d_sched = nullptr;  // rotated launch schedule
-  size_t sched_cap = 0;
-};
-
-static PlanAux* aux_of(bpm_plan_s* plan);
-
-}  // namespace bpm
-
-using namespace bpm;
-
-// Aux storage lives in a side table keyed by plan pointer (keeps the plan
-// struct plain).
-#include <unordered_map>
-static std::mutex g_aux_mu;
-static std::unordered_map<bpm_plan_s*, std::unique_ptr<PlanAux>> g_aux;
-
-namespace bpm {
-static PlanAux* aux_of(bpm_plan_s* plan) {
-  std::lock_guard<std::mutex> lk(g_aux_mu);
-  auto& slot = g_aux[plan];
-  if (!slot) slot = std::make_unique<PlanAux>();
-  return slot.get();
-}
+inline PlanAux* aux_of(bpm_plan_s* plan) { return &plan->aux; }
 
 // Build the fused row descriptors for rows [0, B) of `plan`.
 void fused_rows(bpm_plan_s* plan, float2* state, float2* rec, double* pw, int n_begin,
@@ -474,6 +444,8 @@ static int enqueue_march(bpm_plan_s* plan, PlanAux* aux, void* state, void* d_re
 
 }  // namespace bpm
 
+using namespace bpm;
+
 extern "C" {
 
 const char* bpm_last_error(void) { return g_last_error.c_str(); }
@@ -633,8 +605,6 @@ static int make_plan(const bpm_problem* p, int ny, double dy_um, double y0_um,
     if (aux->stream) cudaStreamDestroy(aux->stream);
     if (aux->d_g) cudaFree(aux->d_g);
     free_plan_memory(pl);
-    std::lock_guard<std::mutex> lk(g_aux_mu);
-    g_aux.erase(pl);
     return rc;
   }
   *out = plan.release();
@@ -1038,10 +1008,6 @@ int bpm_destroy(bpm_plan_t plan) {
   if (aux->d_g) cudaFree(aux->d_g);
   if (aux->d_sched) cudaFree(aux->d_sched);
   free_plan_memory(plan);
-  {
-    std::lock_guard<std::mutex> lk(g_aux_mu);
-    g_aux.erase(plan);
-  }
   delete plan;
   return BPM_OK;
 }

@@ -344,10 +344,15 @@ extern "C" int bpm_march_f64_noalloc(void* d_psi, int32_t nx, int32_t n_rows,
   int logn = 0;
   while ((1 << logn) < nx) ++logn;
   const int lines = 2 * n_rows;
+  // An error left pending by earlier, unrelated work is not this call's:
+  // clear it so the checks below see only this call's launches.
+  cudaGetLastError();
   noalloc_twiddle_kernel<<<(nx + 255) / 256, 256, 0, st>>>(sym.twiddles, nx);
   noalloc_rows_kernel<<<(n_rows + 127) / 128, 128, 0, st>>>(
       sym.rows, static_cast<const double2*>(d_prop), static_cast<const double2*>(d_coupling), nx,
       n_rows);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "noalloc march: table set-up launch");
   double2* user = static_cast<double2*>(d_psi);
   double2* x = user;
   double2* y = sym.scratch;

@@ -681,20 +681,24 @@ int bpm_submit(bpm_plan_t plan, const double* psi_in, double* psi_out, void* rec
   r->records = records;
   r->powers = powers;
   {
+    // The check and the reservation are one critical section: of two
+    // threads submitting on the same plan, exactly one gets the plan.
     std::lock_guard<std::mutex> lk(plan->mu);
     if (plan->pending > 0)
       return fail(BPM_ERR_BUSY, "the plan already has a request in flight");
+    plan->pending += 1;
     r->footprint = footprint_of(plan, records != nullptr && plan->n_rec > 0);
   }
+  auto release = [plan](int code, const char* why) {
+    std::lock_guard<std::mutex> pk(plan->mu);
+    plan->pending -= 1;
+    return fail(code, why);
+  };
   std::lock_guard<std::mutex> lk(s.mu);
   ensure_started(s);
   if (r->footprint > s.budget)
-    return fail(BPM_ERR_OOM, "request needs more device memory than the server budget");
-  if (int(s.queue.size()) >= s.max_queue) return fail(BPM_ERR_BUSY, "server queue is full");
-  {
-    std::lock_guard<std::mutex> pk(plan->mu);
-    plan->pending += 1;
-  }
+    return release(BPM_ERR_OOM, "request needs more device memory than the server budget");
+  if (int(s.queue.size()) >= s.max_queue) return release(BPM_ERR_BUSY, "server queue is full");
   r->id = s.next_id++;
   r->t_submit = now_s();
   s.tickets[r->id] = r;

@@ -318,7 +318,7 @@ CHIH_440 = complex(-1.45e-6, 1.2e-8)
 def cube_dislocation_3d(nx: int = 512, ny: int = 256, nz: int = 300, dx_um: float = 0.05,
                         dy_um: float = 0.05, dz_um: float = 0.05, cube_um: float = 10.0,
                         fwhm_um: float = 2.0, record_every: int = 0) -> Workload3D:
-    """Stand-in for the 3D example of Sec. 6 (Si(440) at 17.45 keV from a
+    """Stand-in for the 3D example of Sec. 7 (Si(440) at 17.45 keV from a
     10 um cube with a dislocation, 300 x 200 x 300 grid): a box crystal
     x in [0, cube], |y| <= cube/2, z in [cube/4, 5 cube/4]; an edge
     dislocation (b = 0.384 nm, nu = 0.28) along y through the cube centre

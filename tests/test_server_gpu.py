@@ -199,3 +199,37 @@ def test_poll_timeout_and_collection(bpm_lib):
             assert binding.bpm_poll(t, -1) == binding.BPM_OK
         with pytest.raises(binding.BpmError):
             binding.bpm_poll(t, 0)           # already collected
+
+
+def test_concurrent_submits_on_one_plan_admit_exactly_one(bpm_lib):
+    """Two threads submit on the same plan at the same moment: the plan takes
+    one request at a time, so exactly one submit is accepted and the other
+    returns BPM_ERR_BUSY (never both: two requests would share the plan's
+    device state).  Repeated so that the two calls overlap in most trials."""
+    import ctypes
+    import threading
+    binding.bpm_server_configure(0.6, 64, 128, 1000)
+    rng = np.random.default_rng(5)
+    wl = inputs.serving_request(rng, 512, 64)
+    lib = binding.load()
+    psi_in = np.ascontiguousarray(wl.psi0)
+    with binding.Plan(wl, FP32) as plan:
+        for _ in range(40):
+            outs = [np.empty_like(psi_in) for _ in range(2)]
+            tickets = [ctypes.c_uint64(0) for _ in range(2)]
+            codes = [None, None]
+            go = threading.Barrier(2)
+
+            def submit(i):
+                go.wait()
+                codes[i] = lib.bpm_submit(plan.handle, binding._ptr(psi_in),
+                                          binding._ptr(outs[i]), None, None,
+                                          ctypes.byref(tickets[i]))
+            th = [threading.Thread(target=submit, args=(i,)) for i in range(2)]
+            for t in th:
+                t.start()
+            for t in th:
+                t.join()
+            assert sorted(codes) == [binding.BPM_ERR_BUSY, binding.BPM_OK], codes
+            won = codes.index(binding.BPM_OK)
+            assert binding.bpm_poll(tickets[won].value, -1) == binding.BPM_OK

@@ -3,8 +3,9 @@ based march (bpm_propagate_device on an FP64 plan).
 
 Callers that cannot allocate device memory use the allocation-free entry
 point with their own buffers; its working memory is static and shared by
-every call, so it is called twice in a row here to show that the second
-call does not depend on what the first one left behind."""
+every call.  A first call of another size (other twiddles, row descriptors
+and scratch contents) precedes two checked calls in a row, so a call that
+depended on what an earlier one left behind would fail here."""
 
 import math
 
@@ -41,6 +42,20 @@ def test_noalloc_march_matches_plan_march_on_two_calls(bpm_lib):
     gph = math.fmod(p.dzh * p.c, 2 * math.pi)
     ang = math.fmod(wl.nz * gph, 2 * math.pi)
     g = complex(math.cos(ang), math.sin(ang))
+    # A call of another size first (nx = 2048, two rows, random data): it
+    # leaves different twiddles, row descriptors and scratch behind.
+    rng = np.random.default_rng(3)
+    nd, rd, sd = 2048, 2, 5
+
+    def crand(*shape):
+        return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    dummy_psi = torch.from_numpy(crand(rd, 2, nd)).to(dev)
+    dummy_prop = torch.from_numpy(np.exp(1j * rng.uniform(0, 6.28, (rd, 2, nd))) / nd).to(dev)
+    dummy_ab = torch.from_numpy(0.5 * crand(rd, 2)).to(dev)
+    dummy_ph = torch.from_numpy(np.exp(1j * rng.uniform(0, 6.28, (sd, nd)))).to(dev)
+    binding.bpm_march_f64_noalloc(dummy_psi, nd, rd, dummy_prop, dummy_ab, dummy_ph, 0, sd,
+                                  st.cuda_stream)
+    st.synchronize()
     for _ in range(2):
         y = torch.from_numpy(wl.psi0.copy()).to(dev)
         binding.bpm_march_f64_noalloc(y, wl.nx, 1, d_prop, d_ab, d_ph, 0, wl.nz, st.cuda_stream)
