@@ -103,9 +103,12 @@ def ifft2(spec: np.ndarray) -> np.ndarray:
 
 
 def fftfreq(n: int, d: float) -> np.ndarray:
-    """Frequencies of the DFT bins in cycles per unit of d: m / (n d) for
-    m < n/2 and (m - n) / (n d) from m = n/2 on (bin n/2 is the negative
-    Nyquist frequency for even n)."""
+    """Frequencies of the DFT bins in cycles per unit of d: the signed bin
+    index (m for m < n/2, m - n from m = n/2 on; bin n/2 is the negative
+    Nyquist frequency for even n) times the bin spacing 1 / (n d).  Formed
+    as index * spacing, so q is rounded the same way wherever it is formed:
+    a metre-long free-space step turns q into phases of ~1e7 rad, where one
+    ulp of q is already a phase error of ~1e-9."""
     m = np.arange(n)
     signed = np.where(m < (n + 1) // 2, m, m - n)
-    return signed / (n * d)
+    return signed * (1.0 / (n * d))

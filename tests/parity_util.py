@@ -43,3 +43,29 @@ def run_gpu(wl, precision, n_begin=0, n_end=None, psi_in=None):
 
 def run_ref(wl, **kw):
     return oracle_run.run_workload(wl, **kw)
+
+
+_POOL = None
+
+
+def oracle_pool():
+    """A process pool for oracle marches, started with 'spawn' (never forked
+    from a process that holds a CUDA context).  The oracle is single-threaded
+    numpy, so independent marches run side by side on the host cores while
+    the GPU works."""
+    global _POOL
+    if _POOL is None:
+        import concurrent.futures
+        import multiprocessing
+        import os
+        workers = max(1, min(8, (os.cpu_count() or 2) - 1))
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ.setdefault(var, "1")    # one core per oracle worker
+        _POOL = concurrent.futures.ProcessPoolExecutor(
+            workers, mp_context=multiprocessing.get_context("spawn"))
+    return _POOL
+
+
+def submit_ref(wl, **kw):
+    """The oracle march of ``wl`` in the pool (a future of its MarchResult)."""
+    return oracle_pool().submit(oracle_run.run_workload, wl, **kw)

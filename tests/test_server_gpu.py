@@ -233,3 +233,35 @@ def test_concurrent_submits_on_one_plan_admit_exactly_one(bpm_lib):
             assert sorted(codes) == [binding.BPM_ERR_BUSY, binding.BPM_OK], codes
             won = codes.index(binding.BPM_OK)
             assert binding.bpm_poll(tickets[won].value, -1) == binding.BPM_OK
+
+
+def test_served_mix_matches_oracle(bpm_lib):
+    """Requests of every transform size the server takes (512..16384, two
+    each, 500-3000 steps) plus three long ones (512 x 20000, 2048 x 12000,
+    4096 x 8000), submitted together so that they overlap on the GPU: every
+    served result against the FP64 oracle at the FP32 bound (not only
+    against the same request run alone)."""
+    from parity_util import submit_ref
+    binding.bpm_server_configure(0.6, 64, 256, 1000)
+    rng = np.random.default_rng(29)
+    sizes = [(nx, int(rng.integers(500, 3001)))
+             for nx in (512, 1024, 2048, 4096, 8192, 16384) for _ in range(2)]
+    sizes += [(512, 20000), (2048, 12000), (4096, 8000)]
+    reqs = [inputs.serving_request(rng, nx, nz) for nx, nz in sizes]
+    refs = [submit_ref(wl, record_every=0) for wl in reqs]
+    plans, outs, tickets = [], [], []
+    for wl in reqs:
+        plan = binding.Plan(wl, FP32)
+        out = np.empty_like(wl.psi0)
+        tickets.append(binding.bpm_submit(plan.handle, wl.psi0, out))
+        plans.append(plan)
+        outs.append(out)
+    for t in tickets:
+        assert binding.bpm_poll(t, -1) == binding.BPM_OK
+    for p in plans:
+        p.close()
+    worst = []
+    for wl, out, fut in zip(reqs, outs, refs):
+        errs = band_errors(out, fut.result().psi)
+        worst.append((max(errs), wl.nx, wl.nz))
+        assert max(errs) <= TOL_FP32, (wl.nx, wl.nz, errs)
