@@ -124,6 +124,85 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def host_info():
+    """Core count and CPU model of the host (for the CPU baselines)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model,
+            "machine": os.uname().machine}
+
+
+def oracle_job(wl, kw, three_d=False):
+    """One oracle march in a pool worker: (MarchResult, seconds)."""
+    from oracle import run as orun
+    t0 = time.perf_counter()
+    res = orun.run_workload3d(wl, **kw) if three_d else orun.run_workload(wl, **kw)
+    return res, time.perf_counter() - t0
+
+
+def _warm_worker(_):
+    import oracle.run  # noqa: F401  (imports done before a timed batch)
+    return os.getpid()
+
+
+def row_workload(wl, r: int):
+    """Row r of a batched workload as a one-row workload (so that a pool
+    task carries one row's input, not the whole batch's)."""
+    import dataclasses
+    return dataclasses.replace(wl, energies_ev=np.asarray(wl.energies_ev)[r:r + 1],
+                               psi0=np.asarray(wl.psi0)[r:r + 1])
+
+
+def make_oracle_pool(workers: int):
+    """Process pool for oracle marches, started with 'spawn' (the oracle is
+    single-threaded numpy; one worker per host core)."""
+    import concurrent.futures
+    import multiprocessing
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(var, "1")
+    pool = concurrent.futures.ProcessPoolExecutor(
+        workers, mp_context=multiprocessing.get_context("spawn"))
+    list(pool.map(_warm_worker, range(workers)))
+    return pool
+
+
+def cpu_baselines(pool, workers: int, head_steps: int, batch_steps: int):
+    """The oracle, as it stands, on bounded samples: the headline solve on
+    one core (its march is sequential in z) and the pulse batch on every
+    host core in parallel over energies (one row per core)."""
+    from oracle import run as orun
+    from paper_2601_06340_gb300 import inputs
+    info = host_info()
+    wl = inputs.bragg_bent()
+    t0 = time.perf_counter()
+    orun.run_workload(wl, 0, head_steps, record_every=0)
+    dt = time.perf_counter() - t0
+    head = {"value": wl.nx * head_steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {head_steps} of the {wl.nz} z-steps of the bragg_bent march "
+                      f"(Nx={wl.nx}), numpy float64, single thread", **info}
+    wb = inputs.pulse_batched(nz=batch_steps)
+    rows = list(range(0, wb.batch, max(1, wb.batch // workers)))[:workers]
+    tasks = [row_workload(wb, r) for r in rows]
+    t0 = time.perf_counter()
+    futs = [pool.submit(oracle_job, w, dict(record_every=0)) for w in tasks]
+    for f in futs:
+        f.result()
+    dt = time.perf_counter() - t0
+    batch = {"value": len(rows) * wb.nx * batch_steps / dt, "unit": UNIT,
+             "cores": workers, "kind": "oracle",
+             "sample": f"{len(rows)} of the 256 energy rows of pulse_batched (Nx={wb.nx}), "
+                       f"first {batch_steps} of 6000 z-steps each, one row per process, "
+                       f"{workers} processes in parallel, numpy float64", **info}
+    return head, batch
+
+
 def rel_l2_bands(got, ref):
     out = []
     for b in range(2):
@@ -133,11 +212,21 @@ def rel_l2_bands(got, ref):
 
 
 # --------------------------------------------------------------------------
-def serving_run(n_requests: int, rate: float, warm: int = 40, n_check: int = 8):
+def serving_sample(n_requests: int, warm: int, n: int) -> list[int]:
+    """Indices of the timed requests whose results are checked (seeded)."""
+    rng = np.random.default_rng(7)
+    n = min(n, n_requests - warm)
+    return sorted(int(i) for i in rng.choice(np.arange(warm, n_requests), n, replace=False))
+
+
+def serving_run(n_requests: int, rate: float, warm: int = 40, n_check: int = 8,
+                oracle_refs=None):
     """Replay a seeded Poisson stream of mixed solves (Nx 512..16384) in real
     time through bpm_submit / bpm_poll; latency = completion - submission as
     stamped by the server.  The first `warm` requests are excluded from the
-    statistics.  `n_check` sampled requests are re-run alone for parity."""
+    statistics.  `n_check` sampled requests are re-run alone for parity, and
+    the requests in `oracle_refs` (index -> future of the oracle march) are
+    compared with the oracle."""
     import threading
     from paper_2601_06340_gb300 import binding, inputs
     FP32 = binding.BPM_FP32_FUSED
@@ -170,9 +259,8 @@ def serving_run(n_requests: int, rate: float, warm: int = 40, n_check: int = 8):
     span = times[:, 2].max() - times[:, 0].min()
     cells = sum(r.workload.cell_updates for r in reqs[warm:])
     flops = sum(r.workload.cell_updates * FLOPS_PER_CELL(r.workload.nx) for r in reqs[warm:])
-    rng = np.random.default_rng(7)
     errs = []
-    for i in sorted(rng.choice(np.arange(warm, len(reqs)), n_check, replace=False)):
+    for i in serving_sample(len(reqs), warm, n_check):
         alone = plans[i].propagate(records=False, powers=False).psi
         for b in range(2):
             den = np.linalg.norm(alone[0, b])
@@ -180,6 +268,15 @@ def serving_run(n_requests: int, rate: float, warm: int = 40, n_check: int = 8):
                 errs.append(float(np.linalg.norm(outs[i][0, b] - alone[0, b]) / den))
     for p in plans:
         p.close()
+    vs_oracle = None
+    if oracle_refs:
+        per = []
+        for i, fut in sorted(oracle_refs.items()):
+            ref, _ = fut.result()
+            per.append(max(rel_l2_bands(outs[i], ref.psi)))
+        vs_oracle = {"requests": len(per), "max_rel_l2": max(per),
+                     "median_rel_l2": float(np.median(per)), "tolerance": 2e-4,
+                     "sample": "seeded uniform draw among the timed requests"}
     per_nx = {}
     svc_ms = (times[:, 2] - times[:, 1]) * 1e3
     for nx in sorted({r.workload.nx for r in reqs[warm:]}):
@@ -199,7 +296,8 @@ def serving_run(n_requests: int, rate: float, warm: int = 40, n_check: int = 8):
                            "p99": float(np.percentile(lat_ms, 99)),
                            "max": float(lat_ms.max())},
             "queue_wait_ms_p99": float(np.percentile(wait_ms, 99)),
-            "alone_vs_mix_max_rel_l2": max(errs) if errs else None}
+            "alone_vs_mix_max_rel_l2": max(errs) if errs else None,
+            "vs_oracle": vs_oracle}
 
 
 def curve_fwhm(x: np.ndarray, y: np.ndarray) -> float:
@@ -218,7 +316,11 @@ def curve_fwhm(x: np.ndarray, y: np.ndarray) -> float:
     return float(xr - xl)
 
 
-def rocking_run(dev, stream, barrier, max_over_ranks, world, rank, check, steps=3):
+ROCKING_ROWS = [128, 140]
+BATCH_ROWS = [0, 131, 255]
+
+
+def rocking_run(dev, stream, barrier, max_over_ranks, world, rank, refs=None, steps=3):
     """256 incidence angles of a Laue slab as the rows of one batched march;
     reflectivity per row from the FP64 band powers."""
     import torch
@@ -250,19 +352,16 @@ def rocking_run(dev, stream, barrier, max_over_ranks, world, rank, check, steps=
            "reflectivity": {"peak": float(refl.max()),
                             "peak_angle_urad": float(angles[int(np.argmax(refl))]),
                             "fwhm_urad": curve_fwhm(angles, refl)}}
-    if check:
-        from oracle import run as orun
-        rows = [128, 140]
-        ref = orun.run_workload(wr, rows=rows)
-        got = y.cpu().numpy().astype(np.complex128)[rows]
-        errs = [rel_l2_bands(got[i:i + 1], ref.psi[i:i + 1]) for i in range(len(rows))]
+    if refs:
+        got = y.cpu().numpy().astype(np.complex128)
+        errs = [rel_l2_bands(got[r:r + 1], f.result()[0].psi) for r, f in zip(ROCKING_ROWS, refs)]
         out["rel_l2_err_sampled_rows"] = [max(e[0] for e in errs), max(e[1] for e in errs)]
-        out["sampled_rows"] = rows
+        out["sampled_rows"] = ROCKING_ROWS
     plan.close()
     return out
 
 
-def volume_run(dev, stream, barrier, max_over_ranks, world, rank, check, steps=3):
+def volume_run(dev, stream, barrier, max_over_ranks, world, rank, ref=None, steps=3):
     """The 3D stand-in workload (both transverse coordinates): one solve of
     512 x 256 x 300 cells.  The paper's only timing (its 3D example, 300 x 200
     x 300 cells, ~13 s on a Perlmutter node) is quoted as context."""
@@ -291,17 +390,15 @@ def volume_run(dev, stream, barrier, max_over_ranks, world, rank, check, steps=3
            "launches_per_march": 2 * wv.nz + 2,
            "paper_context": {"seconds": 13.0, "grid": "300 x 200 x 300",
                              "hardware": "one Perlmutter node (CPU vs GPU not stated)"}}
-    if check:
-        from oracle import run as orun
-        t0 = time.perf_counter()
-        ref = orun.run_workload3d(wv, record_every=0)
-        out["oracle_seconds_1core"] = time.perf_counter() - t0
-        out["rel_l2_err"] = rel_l2_bands(y.cpu().numpy().astype(np.complex128), ref.psi)
+    if ref is not None:
+        res, sec = ref.result()
+        out["oracle_seconds_1core"] = sec
+        out["rel_l2_err"] = rel_l2_bands(y.cpu().numpy().astype(np.complex128), res.psi)
     plan.close()
     return out
 
 
-def configs_run(dev, stream, barrier, max_over_ranks, world, rank, check, steps=3):
+def configs_run(dev, stream, barrier, max_over_ranks, world, rank, refs=None, steps=3):
     """The single-solve configurations besides the headline one: the
     symmetric Laue crystal (Nx=1024, Nz=2000) and the asymmetric Bragg slab
     with a polygonal shape and an edge dislocation (Nx=8192, Nz=12000): the
@@ -341,11 +438,8 @@ def configs_run(dev, stream, barrier, max_over_ranks, world, rank, check, steps=
             psi[key] = y.cpu().numpy().astype(np.complex128)
             plan.close()
         row["fused_speedup"] = row["fused_fp32"]["value"] / row["plain_fp64"]["value"]
-        if check:
-            from oracle import run as orun
-            t0 = time.perf_counter()
-            ref = orun.run_workload(wl, record_every=0)
-            cpu_s = time.perf_counter() - t0
+        if refs:
+            ref, cpu_s = refs[name].result()
             row["oracle_1core"] = {"value": wl.cell_updates / cpu_s, "unit": UNIT, "cores": 1}
             row["fused_fp32"]["rel_l2_err"] = rel_l2_bands(psi["fused_fp32"], ref.psi)
             row["plain_fp64"]["rel_l2_err"] = rel_l2_bands(psi["plain_fp64"], ref.psi)
@@ -407,14 +501,14 @@ def run_gpu(args, rks):
         return
 
     if args.only == "volume":
-        r = volume_run(dev, stream, barrier, max_over_ranks, world, rank, check=False,
+        r = volume_run(dev, stream, barrier, max_over_ranks, world, rank, ref=None,
                        steps=args.steps)
         if rank == 0:
             print(json.dumps({"only": "volume", **r}), flush=True)
         return
 
     if args.only == "rocking":
-        r = rocking_run(dev, stream, barrier, max_over_ranks, world, rank, check=False,
+        r = rocking_run(dev, stream, barrier, max_over_ranks, world, rank, refs=None,
                         steps=args.steps)
         if rank == 0:
             print(json.dumps({"only": "rocking", **r}), flush=True)
@@ -445,6 +539,36 @@ def run_gpu(args, rks):
 
     wl = inputs.bragg_bent()
     cells = wl.cell_updates
+
+    # ---- the oracle on the host cores: CPU baselines first (idle host), then
+    # every parity reference of this run in a spawn pool, beside the GPU work
+    pool, jobs = None, {}
+    cpu_baseline = batch_cpu = None
+    if rank == 0 and not args.skip_oracle:
+        workers = max(1, os.cpu_count() or 1)
+        pool = make_oracle_pool(workers)
+        cpu_baseline, batch_cpu = cpu_baselines(pool, workers, args.ref_sample_steps,
+                                                args.batch_sample_steps)
+        sub = lambda w, **kw: pool.submit(oracle_job, w, kw)
+        jobs["head"] = sub(wl, record_every=0)
+        if not args.skip_batched:
+            wb_all = inputs.pulse_batched()
+            jobs["batched"] = [sub(row_workload(wb_all, r), record_every=0) for r in BATCH_ROWS]
+        if not args.skip_rocking:
+            wr_all = inputs.rocking_scan()
+            jobs["rocking"] = [sub(row_workload(wr_all, r)) for r in ROCKING_ROWS]
+        if not args.skip_configs:
+            jobs["configs"] = {"laue_perfect": sub(inputs.laue_perfect(), record_every=0),
+                               "asym_dislocation": sub(inputs.asym_dislocation(),
+                                                       record_every=0)}
+        if not args.skip_volume:
+            jobs["volume"] = pool.submit(oracle_job, inputs.cube_dislocation_3d(),
+                                         dict(record_every=0), True)
+        if not args.skip_serving and args.serving_check > 0:
+            reqs = inputs.serving_requests(args.serving_requests, rate_per_s=args.serving_rate)
+            jobs["serving"] = {i: sub(reqs[i].workload, record_every=0)
+                               for i in serving_sample(len(reqs), 40, args.serving_check)}
+
     plan32 = binding.Plan(wl, FP32)
     n_rec = plan32.n_rec
     x = torch.from_numpy(wl.psi0.astype(np.complex64)).to(dev)
@@ -485,18 +609,20 @@ def run_gpu(args, rks):
         plan32.close()
         return
 
+    # ---- measured arithmetic peaks (the roofline denominators) ------------
+    with ClockSampler(dev.index) as clk_peak:
+        f32a, _ = binding.bpm_fp_peak(binding.BPM_PEAK_FP32_FFMA, 96000)
+        f32b, _ = binding.bpm_fp_peak(binding.BPM_PEAK_FP32_FFMA2, 48000)
+        f64, _ = binding.bpm_fp_peak(binding.BPM_PEAK_FP64_DFMA, 1500)
+    peaks = {"fp32_tflops": max(f32a, f32b) / 1e12, "fp32_ffma_tflops": f32a / 1e12,
+             "fp32_ffma2_tflops": f32b / 1e12, "fp64_tflops": f64 / 1e12,
+             "sm_mhz": clk_peak.summary().get("sm_mhz"),
+             "how": "bpm_fp_peak: 8 CTAs x 256 threads per SM, 8 independent FMA chains per "
+                    "thread, CUDA events, after a warm-up launch; 1 FMA = 2 flops"}
+
     # ---- parity on the timed workload (oracle on the host) ----------------
     fused_psi = y.cpu().numpy().astype(np.complex128)
-    ref = None
-    cpu_baseline = None
-    if rank == 0 and not args.skip_oracle:
-        from oracle import run as orun
-        t0 = time.perf_counter()
-        ref = orun.run_workload(wl, record_every=0)
-        cpu_s = time.perf_counter() - t0
-        cpu_baseline = {"value": cells / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
-                        "sample": "the whole bragg_bent march (Nx=4096, Nz=8000) once, "
-                                  "numpy float64, single thread"}
+    ref = jobs["head"].result()[0] if "head" in jobs else None
     err32 = rel_l2_bands(fused_psi, ref.psi) if ref is not None else None
 
     # ---- end to end through the host C-ABI (pinned host buffers) ----------
@@ -564,36 +690,53 @@ def run_gpu(args, rks):
         cells_b = wb.cell_updates
         layout, chunk = binding.bpm_launch_shape(planb.handle)
         batched = {"workload": "pulse_batched: 256 energies 9 keV +- 5 eV, Laue 300 um, "
-                               "bent R=2 m, Nx=4096, Nz=6000, + energy->time IDFT",
+                               "bent R=2 m, Nx=4096, Nz=6000, + energy->time synthesis",
                    "value": world * cells_b / (msb * 1e-3), "unit": UNIT,
-                   "ms_per_march": msb,
+                   "ms_per_march": msb, "cpu_baseline": batch_cpu,
                    "launch_shape": {"layout": {2: "split4", 1: "cluster", 0: "cta", -1: "rule"}[layout],
                                     "rotation_chunk": chunk,
                                     "autotune": os.environ.get("BPM_AUTOTUNE", "1") != "0"}}
+        if "batched" in jobs:
+            gotb = yb.cpu().numpy().astype(np.complex128)
+            eb = [rel_l2_bands(gotb[r:r + 1], f.result()[0].psi)
+                  for r, f in zip(BATCH_ROWS, jobs["batched"])]
+            batched["rel_l2_err_sampled_rows"] = [max(e[0] for e in eb), max(e[1] for e in eb)]
+            batched["sampled_rows"] = BATCH_ROWS
+            batched["tolerance"] = 2e-4
         planb.close()
 
     # ---- rocking curve: incidence angles as the rows of one batch ----------
     rocking = None
     if not args.skip_rocking:
         rocking = rocking_run(dev, stream, barrier, max_over_ranks, world, rank,
-                              check=rank == 0 and not args.skip_oracle)
+                              refs=jobs.get("rocking"))
 
     # ---- the other single-solve configurations ------------------------------
     configs = None
     if not args.skip_configs:
         configs = configs_run(dev, stream, barrier, max_over_ranks, world, rank,
-                              check=rank == 0 and not args.skip_oracle)
+                              refs=jobs.get("configs"))
 
     # ---- 3D: both transverse coordinates -----------------------------------
     volume = None
     if not args.skip_volume:
         volume = volume_run(dev, stream, barrier, max_over_ranks, world, rank,
-                            check=rank == 0 and not args.skip_oracle)
+                            ref=jobs.get("volume"))
 
     # ---- serving: Poisson stream of mixed solves through submit/poll ------
     serving = None
     if not args.skip_serving and rank == 0:
-        serving = serving_run(args.serving_requests, args.serving_rate)
+        # the host must be quiet for a real-time replay: wait for the pool
+        for key in ("head", "batched", "rocking", "configs", "volume"):
+            fl = jobs.get(key)
+            for f in (fl.values() if isinstance(fl, dict) else fl if isinstance(fl, list)
+                      else [fl] if fl is not None else []):
+                f.result()
+        if "serving" in jobs:
+            for f in jobs["serving"].values():
+                f.result()
+        serving = serving_run(args.serving_requests, args.serving_rate,
+                              oracle_refs=jobs.get("serving"))
         # the same mix arriving far faster than it can be served: the GPU
         # stays saturated, so the throughput is the server's capacity
         sat = serving_run(args.capacity_requests, args.capacity_rate, warm=0, n_check=0)
@@ -606,14 +749,18 @@ def run_gpu(args, rks):
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     max_mhz = clocks.get("sm_max_mhz") or 2070.0
-    peak_tflops = sms * 128 * 2 * max_mhz * 1e6 / 1e12
+    derived_tflops = sms * 128 * 2 * max_mhz * 1e6 / 1e12
+    peak_tflops = peaks["fp32_tflops"]
     avg_launch_s = float(np.mean(per_ms)) * 1e-3
     achieved = cells * FLOPS_PER_CELL(wl.nx) / avg_launch_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops,
                 "traffic": profiled_traffic("fused_march_bragg_bent.md"),
                 "kernel": MARCH_KERNELS[march_layout][0],
-                "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
+                "peak_basis": "measured: FP32 FMA throughput kernel (bpm_fp_peak, the faster "
+                              "of FFMA and packed FFMA2) on this GPU in this run",
+                "peak_derived": derived_tflops,
+                "peak_derived_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
                 # the solve occupies one cluster: the fraction of its SMs' peak
                 "cluster_sms": MARCH_KERNELS[march_layout][1],
                 "cluster_frac": achieved / (MARCH_KERNELS[march_layout][1] * peak_tflops / sms),
@@ -653,7 +800,16 @@ def run_gpu(args, rks):
                            "p99": float(np.percentile(lat, 99))},
             "fp64_plain": {"value": value64, "unit": UNIT, "ms_per_step": ms64,
                            "rel_l2_err": err64, "tolerance": 1e-10,
-                           "fused_speedup": value / value64},
+                           "fused_speedup": value / value64,
+                           "roofline": {"bound": "fp64 alu / launches",
+                                        "achieved": value64 * FLOPS_PER_CELL(wl.nx) / 1e12,
+                                        "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
+                                        "frac": value64 * FLOPS_PER_CELL(wl.nx) / 1e12
+                                        / peaks["fp64_tflops"],
+                                        "launches_per_step": 2 * (wl.nx.bit_length() // 2) + 2,
+                                        "peak_basis": "measured: FP64 DFMA throughput kernel "
+                                                      "(bpm_fp_peak)"}},
+            "peaks": peaks,
             "batched": batched,
             "configs": configs,
             "rocking": rocking,
@@ -667,6 +823,8 @@ def run_gpu(args, rks):
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
+    if pool is not None:
+        pool.shutdown(wait=False, cancel_futures=True)
 
 
 def main():
@@ -675,7 +833,12 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--ref-sample-steps", type=int, default=1000)
+    ap.add_argument("--ref-sample-steps", type=int, default=2000,
+                    help="z-steps of the oracle's headline sample (CPU baseline)")
+    ap.add_argument("--batch-sample-steps", type=int, default=1500,
+                    help="z-steps per energy row of the oracle's all-cores batch sample")
+    ap.add_argument("--serving-check", type=int, default=32,
+                    help="served requests compared with the oracle")
     ap.add_argument("--skip-oracle", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")

@@ -349,6 +349,23 @@ const char* bpm_version(void);
  * launch failed. */
 int bpm_selftest_wait_expiry(int32_t* status, double* seconds);
 
+/* Measured arithmetic peak of the current device: the denominator of the
+ * march kernels' roofline fractions (the march is bound by FP32 ALU work;
+ * FP64 explains the plain path).  No counterpart in the paper.  Every SM
+ * runs eight 256-thread CTAs whose threads each carry eight independent
+ * multiply-add chains for iters x 16 rounds; one FMA is two flops (a packed
+ * FFMA2 four).  *flops_per_s receives the rate of the timed launch (after a
+ * warm-up launch of iters / 8 rounds), *seconds its CUDA-event duration, at
+ * whatever clock the GPU runs.  Blocks the host.  BPM_ERR_INVALID for NULL
+ * pointers, an unknown kind or iters outside [1, 2^22]; BPM_ERR_CUDA if a
+ * launch failed. */
+enum bpm_peak_kind {
+  BPM_PEAK_FP64_DFMA = 0,
+  BPM_PEAK_FP32_FFMA = 1,
+  BPM_PEAK_FP32_FFMA2 = 2
+};
+int bpm_fp_peak(int32_t kind, int32_t iters, double* flops_per_s, double* seconds);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,6 +76,7 @@ _SIGS = {
     "bpm_selftest_wait_expiry": ([ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "bpm_server_inject_launch_failure": ([_I, _I], ctypes.c_int),
     "bpm_device_status": ([_P, _P], ctypes.c_int),
+    "bpm_fp_peak": ([_I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)], ctypes.c_int),
 }
 
 
@@ -235,6 +236,17 @@ def bpm_selftest_wait_expiry() -> tuple[int, float]:
     status, seconds = _I(0), ctypes.c_double(0.0)
     _check(load().bpm_selftest_wait_expiry(ctypes.byref(status), ctypes.byref(seconds)))
     return status.value, seconds.value
+
+
+BPM_PEAK_FP64_DFMA, BPM_PEAK_FP32_FFMA, BPM_PEAK_FP32_FFMA2 = 0, 1, 2
+
+
+def bpm_fp_peak(kind: int, iters: int) -> tuple[float, float]:
+    """(flops/s, seconds) of the FMA-throughput kernel of `kind` on the
+    current device (one FMA = 2 flops, a packed FFMA2 = 4)."""
+    rate, sec = _D(0.0), _D(0.0)
+    _check(load().bpm_fp_peak(int(kind), int(iters), ctypes.byref(rate), ctypes.byref(sec)))
+    return rate.value, sec.value
 
 
 def bpm_destroy(plan):

@@ -137,3 +137,10 @@ def test_workloads_are_seeded_and_shaped():
     assert all(r2.arrival_s > r1.arrival_s for r1, r2 in zip(reqs, reqs[1:]))
     assert {r.workload.nx for r in inputs.serving_requests(200)} <= {
         512, 1024, 2048, 4096, 8192, 16384}
+
+
+def test_fp_peak_argument_checks(lib):
+    rate, sec = ctypes.c_double(), ctypes.c_double()
+    assert lib.bpm_fp_peak(1, 100, None, ctypes.byref(sec)) == binding.BPM_ERR_INVALID
+    assert lib.bpm_fp_peak(3, 100, ctypes.byref(rate), ctypes.byref(sec)) == binding.BPM_ERR_INVALID
+    assert lib.bpm_fp_peak(1, 0, ctypes.byref(rate), ctypes.byref(sec)) == binding.BPM_ERR_INVALID
