@@ -147,14 +147,17 @@ int bpm_set_strain(bpm_plan_t plan, int32_t kind, const double* ux_um,
  *   BPM_SPLIT_FOREST_RUTH: a = (0, t, 1-2t, t), b = (t/2, (1-t)/2, (1-t)/2,
  *                          t/2), t = 1/(2 - 2^(1/3)).
  * FP64 plans take every method.  FP32 (fused) plans take the first-order
- * step, and Verlet for 256 <= nx <= 4096 (half-step couplings on either
- * side of the full-step propagation; at nx = 4096 one 4-CTA half-band split
- * per solve while every solve gets four SMs, else one 2-CTA cluster per
- * solve while every solve gets two SMs and nx != 2048, else one CTA per
- * solve); 3D plans take the first-order step and Verlet (the row kernel,
- * which holds both bands of a line, applies the half-step couplings);
- * other combinations return BPM_ERR_INVALID.
- * bpm_submit takes FP32 plans set to Verlet (one CTA per row as well).
+ * step, and for nx <= 4096 Verlet (half-step couplings on either side of
+ * the full-step propagation; at nx = 4096 one 4-CTA half-band split per
+ * solve while every solve gets four SMs, else one 2-CTA cluster per solve
+ * while every solve gets two SMs and 512 <= nx != 2048, else one CTA per
+ * solve) and Forest-Ruth (one CTA per solve: the leading coupling, then
+ * three propagate-and-couple stages with the propagator increments of t dz
+ * and (1 - 2t) dz, tabulated here once); 3D plans take the first-order step
+ * and Verlet (the row kernel, which holds both bands of a line, applies the
+ * half-step couplings); other combinations return BPM_ERR_INVALID.
+ * bpm_submit takes FP32 plans set to Verlet (one CTA per row as well), not
+ * Forest-Ruth.
  * BPM_ERR_BUSY while tickets are pending. */
 enum bpm_splitting {
   BPM_SPLIT_FIRST_ORDER = 0,
@@ -310,7 +313,8 @@ int bpm_march_f64_noalloc(void* d_psi, int32_t nx, int32_t n_rows, const void* d
                           int32_t n_end, void* stream);
 
 /* Launch shape of the plan's last FP32 march (the fused kernels of the
- * step of Eq. fov10): *layout = 5 one 4-CTA half-band split per row with
+ * step of Eq. fov10): *layout = 6 one CTA per row with the Forest-Ruth step
+ * (plans set to BPM_SPLIT_FOREST_RUTH), 5 one 4-CTA half-band split per row with
  * the Verlet step (nx = 4096), 4 one 2-CTA cluster per row with the Verlet
  * step, 3 one CTA per row with the Verlet step (plans set to
  * BPM_SPLIT_VERLET), 2 one 4-CTA cluster per row (nx = 4096 as

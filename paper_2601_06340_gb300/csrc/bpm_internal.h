@@ -136,7 +136,8 @@ struct bpm_plan_s {
   int32_t n_stages = 0;
   std::vector<int> stage_has_prop;   // [n_stages]: stage propagates (a_i != 0)
   void* d_stage_rows = nullptr;      // RowDescF64 [n_stages][B]
-  void* d_stage_prop = nullptr;      // double2 [tables][B][2][nx]
+  void* d_stage_prop = nullptr;      // FP64: double2 [tables][B][2][nx]; FP32 Forest-Ruth:
+                                     // float2 [B][2 tables][2][nx] (t dz, (1 - 2t) dz)
   size_t device_bytes = 0;
   int pending = 0;                // tickets not yet finished
   // launch shape of the last fused march: layout 1 cluster / 0 CTA / -1 rule,
@@ -158,6 +159,10 @@ int cuda_fail(cudaError_t e, const char* what);
 int validate_problem(const bpm_problem* p, std::string* why);
 void compute_energy_consts(bpm_plan_s* plan);
 void fused_prop_table(const bpm_plan_s* plan, int row, std::vector<float2>* out);
+// (P^frac - 1)/N per band in the fused FFT's output order (nx <= 4096): the
+// propagator increment of a stage of frac * dz
+void fused_prop_table_frac(const bpm_plan_s* plan, int row, double frac,
+                           std::vector<float2>* out);
 // 3D: (P(qx, qy) - 1)/(nx ny) per band, [band][y position][x position] in the
 // output orders of the radix-16 FFTs along y and x.
 void vol_prop_table(const bpm_plan_s* plan, int row, std::vector<float2>* out);
@@ -217,15 +222,18 @@ int split_table_stride(const bpm_plan_s* plan, int logm);   // float2 per row
 // Layout codes of launch_fused_layout: -1 rule, 0 CTA per row, 1 2-CTA
 // cluster per row, 2 4-CTA cluster per row (N = 4096, half-band split).
 constexpr int kLayoutSplit4 = 2;
-// one CTA per row, second-order (Verlet) step, N = 256..4096
+// one CTA per row, second-order (Verlet) step, N <= 4096
 constexpr int kLayoutCtaHalf = 3;
 // one 2-CTA cluster per row, second-order (Verlet) step, N = 512..4096
 constexpr int kLayoutClusterHalf = 4;
 // one 4-CTA cluster per row (N = 4096 half-band split), second-order step
 constexpr int kLayoutSplit4Half = 5;
+// one CTA per row, fourth-order (Forest-Ruth) step, N <= 4096
+constexpr int kLayoutCtaFR = 6;
 int fused_launch_capacity(int logn, bool cluster);
 int fused_split4_capacity();
-int fused_half_capacity(int logn);   // 8 <= logn <= 12
+int fused_half_capacity(int logn);   // logn <= 12
+int fused_fr_capacity(int logn);     // logn <= 12
 int fused_cluster_half_capacity(int logn);   // 9 <= logn <= 12
 int fused_split4_half_capacity();            // N = 4096
 int fused_rows_per_cta(int logn);

@@ -90,6 +90,8 @@ void fused_rows(bpm_plan_s* plan, float2* state, float2* rec, double* pw, int n_
     RowDescF32& d = (*out)[r];
     d.state = state + size_t(r) * 2 * n;
     d.prop = static_cast<const float2*>(plan->d_prop) + size_t(r) * prop_stride(plan);
+    if (plan->split == BPM_SPLIT_FOREST_RUTH)   // [2 tables][2][N] per row
+      d.prop = static_cast<const float2*>(plan->d_stage_prop) + size_t(r) * 4 * n;
     d.prop_split = plan->d_prop_split ? static_cast<const float2*>(plan->d_prop_split) +
                                             size_t(r) * split_table_stride(plan, 11)
                                       : nullptr;
@@ -99,11 +101,19 @@ void fused_rows(bpm_plan_s* plan, float2* state, float2* rec, double* pw, int n_
     const EnergyConsts& c = plan->ec[r];
     d.am1 = make_float2(float(c.am1.real()), float(c.am1.imag()));
     d.b = make_float2(float(c.b.real()), float(c.b.imag()));
-    if (plan->split == BPM_SPLIT_VERLET) {
+    if (plan->split == BPM_SPLIT_VERLET || plan->split == BPM_SPLIT_FOREST_RUTH) {
+      // Verlet: (am1h, bh) for half a step.  Forest-Ruth: (am1h, bh) for the
+      // outer couplings (t/2), (am1, b) for the two inner ones ((1 - t)/2).
+      const auto stg = split_stages(plan->split);
       std::complex<double> ah, bh;
-      coupling_frac(plan, r, 0.5, &ah, &bh);
+      coupling_frac(plan, r, stg.front().second, &ah, &bh);
       d.am1h = make_float2(float((ah - 1.0).real()), float((ah - 1.0).imag()));
       d.bh = make_float2(float(bh.real()), float(bh.imag()));
+      if (plan->split == BPM_SPLIT_FOREST_RUTH) {
+        coupling_frac(plan, r, stg[1].second, &ah, &bh);
+        d.am1 = make_float2(float((ah - 1.0).real()), float((ah - 1.0).imag()));
+        d.b = make_float2(float(bh.real()), float(bh.imag()));
+      }
     } else {
       d.am1h = d.am1;
       d.bh = d.b;
@@ -273,6 +283,17 @@ static LaunchShape choose_shape(bpm_plan_s* plan, PlanAux* aux, const void* stat
   NvtxRange nvtx("bpm_launch_shape_search");
   LaunchShape rule;
   const int nb = plan->nb, logn = plan->logn;
+  if (plan->split == BPM_SPLIT_FOREST_RUTH) {
+    // the fourth-order form: one CTA per row (three propagations per step)
+    rule.layout = kLayoutCtaFR;
+    rule.rotated = nb > fused_fr_capacity(logn);
+    return rule;
+  }
+  if (plan->split == BPM_SPLIT_VERLET && logn >= kSplitLogN) {
+    // N = 8192, 16384: the split-band clusters with the second-order step
+    rule.layout = kLayoutSplit4Half;
+    return rule;
+  }
   if (plan->split == BPM_SPLIT_VERLET) {
     // the second-order forms: a 2-CTA cluster per row while every row gets
     // two SMs, else one CTA per row; measured per 8000-step single solve,
@@ -425,6 +446,7 @@ static int enqueue_march(bpm_plan_s* plan, PlanAux* aux, void* state, void* d_re
                                sh.layout);
     } else {
       const int cap = sh.layout == kLayoutCtaHalf ? fused_half_capacity(plan->logn)
+                      : sh.layout == kLayoutCtaFR ? fused_fr_capacity(plan->logn)
                                                   : fused_launch_capacity(plan->logn, false);
       rc = launch_rotated(plan, aux, rows, n_begin, steps, cap, st, sh.chunk, sh.layout);
     }
@@ -639,22 +661,44 @@ int bpm_set_splitting(bpm_plan_t plan, int32_t method) {
     return fail(BPM_ERR_INVALID, "unknown splitting method");
   if (method == BPM_SPLIT_FOREST_RUTH && plan->ny > 1)
     return fail(BPM_ERR_INVALID, "3D plans march first order or Verlet");
-  if (plan->precision == BPM_FP32_FUSED && method != BPM_SPLIT_FIRST_ORDER &&
-      (method != BPM_SPLIT_VERLET || plan->logn < 8 || plan->logn > 12))
+  if (plan->precision == BPM_FP32_FUSED && method == BPM_SPLIT_FOREST_RUTH && plan->logn > 12)
     return fail(BPM_ERR_INVALID,
-                "BPM_FP32_FUSED plans march first order, or Verlet for 256 <= nx <= 4096");
+                "BPM_FP32_FUSED plans march Forest-Ruth for nx <= 4096 (Verlet at every nx)");
   for (void** p : {&plan->d_stage_rows, &plan->d_stage_prop}) {
     if (*p) cudaFree(*p);
     *p = nullptr;
   }
-  plan->split = method;
+  plan->split = BPM_SPLIT_FIRST_ORDER;
   plan->n_stages = 0;
   plan->stage_has_prop.clear();
-  // FP32: the fused kernels take the half-step coefficients from the row
-  // descriptors, built at each march
-  if (method == BPM_SPLIT_FIRST_ORDER || plan->precision == BPM_FP32_FUSED) return BPM_OK;
   const auto stages = split_stages(method);
   const size_t n = plan->nx, nb = plan->nb;
+  if (plan->precision == BPM_FP32_FUSED) {
+    // the fused kernels take the coupling coefficients from the row
+    // descriptors, built at each march; Forest-Ruth also needs the
+    // propagator increments of its t dz and (1 - 2t) dz stages
+    if (method == BPM_SPLIT_FOREST_RUTH) {
+      int rc = dev_alloc(plan, &plan->d_stage_prop, nb * 4 * n * sizeof(float2),
+                         "splitting propagators");
+      if (rc != BPM_OK) return rc;
+      std::vector<float2> host(nb * 4 * n);
+      for (size_t r = 0; r < nb; ++r)
+        for (int k = 0; k < 2; ++k) {
+          std::vector<float2> tab;
+          fused_prop_table_frac(plan, int(r), stages[1 + k].first, &tab);
+          std::copy(tab.begin(), tab.end(), host.begin() + long((r * 2 + k) * 2 * n));
+        }
+      cudaStream_t st = aux_of(plan)->stream;
+      cudaError_t e = cudaMemcpyAsync(plan->d_stage_prop, host.data(),
+                                      host.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_fail(e, "splitting tables");
+    }
+    plan->split = method;
+    return BPM_OK;
+  }
+  plan->split = method;
+  if (method == BPM_SPLIT_FIRST_ORDER) return BPM_OK;
   // one table per distinct nonzero a_i
   std::vector<double> fracs;
   for (auto& st : stages)

@@ -12,13 +12,22 @@ namespace bpm {
 
 #define BPM_DECLARE_FUSED(L)                                                     \
   int fused_launch_##L(const RowDescF32*, int, int, const float4*, int*,         \
-                       cudaStream_t);
+                       cudaStream_t);                                            \
+  int fusedh_launch_##L(const RowDescF32*, int, int, const float4*, int*,        \
+                        cudaStream_t);                                           \
+  int fusedf_launch_##L(const RowDescF32*, int, int, const float4*, int*,        \
+                        cudaStream_t);                                           \
+  int fusedh_rows_resident_##L();                                                \
+  int fusedf_rows_resident_##L();
 #define BPM_DECLARE_FUSED2(L)                                                    \
   int fused2_launch_##L(const RowDescF32*, int, int, const float4*, int*,        \
                         cudaStream_t);                                           \
   int fused2h_launch_##L(const RowDescF32*, int, int, const float4*, int*,       \
                          cudaStream_t);                                          \
-  int fused2h_rows_resident_##L();
+  int fused2h_rows_resident_##L();                                               \
+  int fused2f_launch_##L(const RowDescF32*, int, int, const float4*, int*,       \
+                         cudaStream_t);                                          \
+  int fused2f_rows_resident_##L();
 #define BPM_DECLARE_FUSED3H(L)                                                   \
   int fused3h_launch_##L(const RowDescF32*, int, int, const float4*, int*,       \
                          cudaStream_t);                                          \
@@ -34,6 +43,8 @@ int fused4h_rows_resident_12();
 int fused4hh_launch_12(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
 int fused4hh_rows_resident_12();
 int fused4_launch_14(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
+int fused4v_launch_13(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
+int fused4v_launch_14(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
 #define BPM_DECLARE_FUSED3(L)                                                    \
   int fused3_launch_##L(const RowDescF32*, int, int, const float4*, int*,        \
                         cudaStream_t);
@@ -84,8 +95,13 @@ int launch_fused_layout(int logn, const RowDescF32* d_rows, int n_rows, int step
   if (logn == 12 && layout == kLayoutSplit4)
     return fused4h_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
   if (layout == kLayoutSplit4Half) {
-    if (logn != 12) return fail(BPM_ERR_INVALID, "second-order split layout needs nx = 4096");
-    return fused4hh_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
+    switch (logn) {
+      case 12: return fused4hh_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 13: return fused4v_launch_13(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 14: return fused4v_launch_14(d_rows, n_rows, steps, d_tw, d_status, st);
+      default:
+        return fail(BPM_ERR_INVALID, "second-order split layout needs nx = 4096, 8192 or 16384");
+    }
   }
   if (layout == kLayoutClusterHalf) {
     switch (logn) {
@@ -96,14 +112,34 @@ int launch_fused_layout(int logn, const RowDescF32* d_rows, int n_rows, int step
       default: return fail(BPM_ERR_INVALID, "second-order cluster layout needs 512 <= nx <= 4096");
     }
   }
+  if (layout == kLayoutCtaFR) {
+    switch (logn) {
+      case 3: return fusedf_launch_3(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 4: return fusedf_launch_4(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 5: return fusedf_launch_5(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 6: return fusedf_launch_6(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 7: return fusedf_launch_7(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 8: return fused2f_launch_8(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 9: return fused2f_launch_9(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 10: return fused2f_launch_10(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 11: return fused2f_launch_11(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 12: return fused2f_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
+      default: return fail(BPM_ERR_INVALID, "fourth-order splitting needs nx <= 4096");
+    }
+  }
   if (layout == kLayoutCtaHalf) {
     switch (logn) {
+      case 3: return fusedh_launch_3(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 4: return fusedh_launch_4(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 5: return fusedh_launch_5(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 6: return fusedh_launch_6(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 7: return fusedh_launch_7(d_rows, n_rows, steps, d_tw, d_status, st);
       case 8: return fused2h_launch_8(d_rows, n_rows, steps, d_tw, d_status, st);
       case 9: return fused2h_launch_9(d_rows, n_rows, steps, d_tw, d_status, st);
       case 10: return fused2h_launch_10(d_rows, n_rows, steps, d_tw, d_status, st);
       case 11: return fused2h_launch_11(d_rows, n_rows, steps, d_tw, d_status, st);
       case 12: return fused2h_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
-      default: return fail(BPM_ERR_INVALID, "second-order splitting needs 256 <= nx <= 4096");
+      default: return fail(BPM_ERR_INVALID, "second-order splitting needs nx <= 4096");
     }
   }
   const bool cluster = logn >= 9 && logn <= 12 &&
@@ -254,12 +290,40 @@ int fused_launch_capacity(int logn, bool cluster) {
 }
 
 // Rows one launch of the second-order (Verlet) CTA kernel keeps resident.
+int fused_fr_capacity(int logn) {
+  static std::atomic<int> cache[kMaxLogN + 1] = {};
+  int c = cache[logn].load(std::memory_order_relaxed);
+  if (c == 0) {
+    int r = 1;
+    switch (logn) {
+      case 3: r = fusedf_rows_resident_3(); break;
+      case 4: r = fusedf_rows_resident_4(); break;
+      case 5: r = fusedf_rows_resident_5(); break;
+      case 6: r = fusedf_rows_resident_6(); break;
+      case 7: r = fusedf_rows_resident_7(); break;
+      case 8: r = fused2f_rows_resident_8(); break;
+      case 9: r = fused2f_rows_resident_9(); break;
+      case 10: r = fused2f_rows_resident_10(); break;
+      case 11: r = fused2f_rows_resident_11(); break;
+      default: r = fused2f_rows_resident_12(); break;
+    }
+    c = r * sm_count();
+    cache[logn].store(c, std::memory_order_relaxed);
+  }
+  return c;
+}
+
 int fused_half_capacity(int logn) {
   static std::atomic<int> cache[kMaxLogN + 1] = {};
   int c = cache[logn].load(std::memory_order_relaxed);
   if (c == 0) {
     int r = 1;
     switch (logn) {
+      case 3: r = fusedh_rows_resident_3(); break;
+      case 4: r = fusedh_rows_resident_4(); break;
+      case 5: r = fusedh_rows_resident_5(); break;
+      case 6: r = fusedh_rows_resident_6(); break;
+      case 7: r = fusedh_rows_resident_7(); break;
       case 8: r = fused2h_rows_resident_8(); break;
       case 9: r = fused2h_rows_resident_9(); break;
       case 10: r = fused2h_rows_resident_10(); break;

@@ -144,16 +144,29 @@ __device__ __forceinline__ void f2_couple(float2* v, const float2* ph, int t, in
   }
 }
 
-// HALF = false: the first-order step of Eq. fov10 (propagate, then couple
-// with the step's coefficients).  HALF = true: the second-order (Verlet /
-// Strang) step of Eq. split-op, couple with half-step coefficients,
-// propagate, couple with half-step coefficients again, both couplings on the
-// slice of the step; the slice of step n + 1 is fetched during step n into
-// the other of two buffers.
-template <int LOGN, bool EX, bool HALF = false>
+// Operator splitting of the step (Eq. split-op), SCH:
+//   kSchFirst  the first-order step of Eq. fov10: propagate, then couple
+//              with the step's coefficients (am1, b);
+//   kSchVerlet the second-order (Verlet / Strang) step: couple with the
+//              half-step coefficients (am1h, bh), propagate, couple with
+//              them again;
+//   kSchForestRuth the fourth-order step: couple (t/2), then three stages of
+//              propagate + couple with the propagators of t dz, (1 - 2t) dz
+//              and t dz and the couplings ((1 - t)/2, (1 - t)/2, t/2);
+//              the row's table holds (P^t - 1)/N then (P^(1-2t) - 1)/N per
+//              band, (am1, b) are the (1 - t)/2 coefficients and
+//              (am1h, bh) the t/2 ones.
+// Every coupling of step n uses the slice of step n.  The second- and
+// fourth-order forms couple before the first propagation, so the slice of
+// step n + 1 is fetched during step n into the other of two buffers.
+constexpr int kSchFirst = 0, kSchVerlet = 1, kSchForestRuth = 2;
+
+template <int LOGN, bool EX, int SCH = kSchFirst>
 __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 512 ? 1 : 2)
     fused2_march_kernel(const RowDescF32* __restrict__ rows, int n_rows, int steps,
                         const float4* __restrict__ tw, int* __restrict__ status) {
+  constexpr bool HALF = SCH != kSchFirst;          // couples before propagating
+  constexpr int STAGES = SCH == kSchForestRuth ? 3 : 1;
   using C = F2Cfg<LOGN, HALF ? 2 : 1>;
   constexpr int N = C::N, T = C::T, NP = C::NP, RL = C::RL;
   constexpr int WPB = T / 16;                  // warps per band-pair group
@@ -203,17 +216,19 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
   }
   const float2* tw1o = tw1 + (t % C::S1);
 
-  // this thread's slice of (P - 1)/N in the last pass, for the whole launch
+  // this thread's slice of (P - 1)/N in the last pass (for the whole launch;
+  // the fourth-order step reloads it per stage, see below)
   float2 pr[16];
-  {
+  auto load_table = [&](const float2* tab) {
     constexpr int P = NP - 1;
 #pragma unroll
     for (int i = 0; i < C::groups(P); ++i)
 #pragma unroll
       for (int j = 0; j < RL; ++j)
-        pr[i * RL + j] = active ? __ldg(&d.prop[band * N + f2_pos<LOGN, P>(t + i * T, j)])
+        pr[i * RL + j] = active ? __ldg(&tab[band * N + f2_pos<LOGN, P>(t + i * T, j)])
                                 : make_float2(0.f, 0.f);
-  }
+  };
+  load_table(d.prop);
   float2 v[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j)
@@ -225,7 +240,6 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
   const uint32_t slice_bytes = uint32_t(N) * 8u;
   int pending_slot = -1;
   bool timed_out = false;
-  const float2 am1 = HALF ? d.am1h : d.am1, bb = HALF ? d.bh : d.b;
   if constexpr (HALF) {
     // the first step's slice; later ones are fetched a step ahead
     if (lead && steps > 0) bulk_load(ph0, d.phasor + size_t(d.n_begin) * N, slice_bytes, bar);
@@ -244,7 +258,7 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
         timed_out = true;
         s_abort = 1;
       }
-      f2_couple<T>(v, ph, t, band, am1, bb);
+      f2_couple<T>(v, ph, t, band, d.am1h, d.bh);
     }
     const bool rec = active && d.record_every > 0 && ((n + 1) % d.record_every) == 0 &&
                      (d.records != nullptr || d.powers != nullptr);
@@ -254,14 +268,21 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
       sincos(ang, &sa, &ca);
       *recph = make_float2(float(ca), float(sa));
     }
-    // park the field of this step; forward pass 0
+#pragma unroll 1
+    for (int sg = 0; sg < STAGES; ++sg) {
+    if constexpr (SCH == kSchForestRuth) {
+      // the stage's table: (P^t - 1)/N for stages 0 and 2, (P^(1-2t) - 1)/N
+      // for stage 1 (read from L2 while the forward passes run)
+      if (sg > 0) load_table(d.prop + (sg == 1 ? 2 * N : 0));
+    }
+    // park the field of this stage; forward pass 0
 #pragma unroll
     for (int j = 0; j < 16; ++j) org[t + j * T] = v[j];
     dft<16, false, EX, PK>(v);
     f2_twiddle<false>(v, w0);
     f2_store<LOGN, 0>(buf, v, t);
     __syncthreads();
-    if (s_abort) {   // the same value for every thread (read after the barrier)
+    if (sg == 0 && s_abort) {   // the same value for every thread (read after the barrier)
       if (lead) {
         // slices up to it were issued (HALF), else up to it - 1
         if constexpr (HALF) mbar_wait(bar + (it & 1), uint32_t((it >> 1) & 1));
@@ -273,7 +294,7 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
     if constexpr (HALF) {
       // every thread is past the couplings of step it - 1, which read the
       // other buffer: fetch step it + 1's slice into it
-      if (lead && it + 1 < steps)
+      if (lead && sg == 0 && it + 1 < steps)
         bulk_load(ph0 + ((it + 1) & 1) * N, d.phasor + size_t(n + 1) * N, slice_bytes,
                   bar + ((it + 1) & 1));
     } else {
@@ -328,25 +349,32 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
     }
 
     // ---- coupling with the other band (lane ^ 16) -------------------------
-    if constexpr (!HALF) {
+    if constexpr (SCH == kSchFirst) {
       if (active && !mbar_wait(bar, uint32_t(it & 1))) {
         timed_out = true;
         s_abort = 1;
       }
+      f2_couple<T>(v, ph, t, band, d.am1, d.b);
+    } else if constexpr (SCH == kSchVerlet) {
+      f2_couple<T>(v, ph, t, band, d.am1h, d.bh);
+    } else {
+      const bool last = sg == STAGES - 1;
+      f2_couple<T>(v, ph, t, band, last ? d.am1h : d.am1, last ? d.bh : d.b);
     }
-    f2_couple<T>(v, ph, t, band, am1, bb);
+    }   // stages (the fourth-order step ends on the t dz table, which its
+        // next step starts with)
 
     // ---- record ------------------------------------------------------------
     const bool want_pw = rec && d.powers != nullptr;
     if (rec) {
       const int slot = (n + 1) / d.record_every - 1;
       const float2 g = *recph;
-      float s = 0.f;
+      double s = 0.0;
       float2* r0 = d.records ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const float2 p = v[j];
-        s = fmaf(p.x, p.x, fmaf(p.y, p.y, s));
+        s = pow_acc(s, p);
         if (r0) r0[t + j * T] = make_float2(fmaf(p.x, g.x, -(p.y * g.y)), fmaf(p.x, g.y, p.y * g.x));
       }
       if (want_pw) {

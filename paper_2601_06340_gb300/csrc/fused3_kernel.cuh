@@ -291,7 +291,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
       const float2 g = rec ? *recph : make_float2(1.f, 0.f);
       const int slot = rec ? (n + 1) / d.record_every - 1 : 0;
       float2* r0 = (rec && d.records) ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
-      float s = 0.f;
+      double s = 0.0;
       // Three couplings per point, unrolled over the thread's 16 points,
       // overflow the instruction cache; they run as a loop over shared
       // memory instead (buf is free once every thread is past the inverse
@@ -310,7 +310,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
           const float2 e = phc[at];
           float2 c = couple_cell(p, q, e, band, am1, bb);   // step it, second half
           if (rec) {
-            s = fmaf(c.x, c.x, fmaf(c.y, c.y, s));
+            s = pow_acc(s, c);
             if (r0) r0[at] = make_float2(fmaf(c.x, g.x, -(c.y * g.y)), fmaf(c.x, g.y, c.y * g.x));
           }
           if (next) {   // step it + 1, first half, with the other band's value
@@ -343,12 +343,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
       if (rec) {
         const int slot = (n + 1) / d.record_every - 1;
         const float2 g = *recph;
-        float s = 0.f;
+        double s = 0.0;
         float2* r0 = d.records ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
   #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const float2 p = v[j];
-          s = fmaf(p.x, p.x, fmaf(p.y, p.y, s));
+          s = pow_acc(s, p);
           if (r0) r0[t + j * T] = make_float2(fmaf(p.x, g.x, -(p.y * g.y)), fmaf(p.x, g.y, p.y * g.x));
         }
         if (d.powers) {

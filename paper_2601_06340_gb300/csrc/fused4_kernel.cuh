@@ -62,8 +62,8 @@ struct F4ECfg {
   static constexpr int OFF_C = OFF_G + 2 * M * 8;          // [2][M] other band's psi_p
   static constexpr int OFF_PH = OFF_C + 2 * M * 8;         // [PHB][PH] strain slices
   static constexpr int OFF_E1 = OFF_PH + PHB * PH * 8;     // [16][T] D(k_j + M)
-  static constexpr int OFF_MBAR = OFF_E1 + M * 8;          // [PHB] strain-slice barriers
-  static constexpr int OFF_GBAR = OFF_MBAR + 8 * PHB;      // [2] F barriers
+  static constexpr int OFF_MBAR = OFF_E1 + M * 8;          // [2] strain-slice barriers
+  static constexpr int OFF_GBAR = OFF_MBAR + 16;           // [2] F barriers
   static constexpr int OFF_CBAR = OFF_GBAR + 16;           // [2] psi_p barriers
   static constexpr int OFF_PPEER = OFF_CBAR + 16;          // [2] peer's band-power part
   static constexpr int OFF_RECPH = OFF_PPEER + 16;
@@ -105,18 +105,26 @@ __device__ __forceinline__ void st_async_f64(uint32_t raddr, double v, uint32_t 
       : "memory");
 }
 
-// HALF = true (N = 4096 only): the second-order (Verlet) step, as in the
-// 2-CTA cluster kernel: after the psi_p swap a CTA holds both bands at its
-// samples, applies step n's second half-coupling to both and step n + 1's
-// first half to its own band (a loop over shared memory); the launch's
-// first half-step reads the other band from global memory.
+// HALF = true: the second-order (Verlet) step, as in the 2-CTA cluster
+// kernel: after the psi_p swap a CTA holds both bands at its samples,
+// applies step n's second half-coupling to both and step n + 1's first half
+// to its own band (a loop over shared memory); the launch's first half-step
+// reads the other band from global memory.  Step n + 1's slice: at N = 4096
+// a second slice buffer, fetched a step ahead; at N = 8192 there is no room
+// for one, so the CTA's part of it is copied into the half of the peer
+// spectrum buffer that step n has finished with (gx[n & 1]: read by this
+// step's combine, rewritten by the peer only at step n + 2, after it has
+// received this CTA's step n + 1 spectrum), issued once every thread is past
+// the combine and awaited at the coupling.
 template <int LM, bool EX, bool HALF = false>
 __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
     fused4e_march_kernel(const RowDescF32* __restrict__ rows, int n_rows, int steps,
                          const float4* __restrict__ tw, int* __restrict__ status) {
   namespace cg = cooperative_groups;
-  static_assert(!HALF || LM == 11, "the second-order form is built for N = 4096");
-  using C = F4ECfg<LM, HALF ? 2 : 1>;
+  // second-order step with the next slice staged in the peer spectrum
+  // buffer (N = 8192) instead of a second slice buffer (N = 4096)
+  constexpr bool HALF_G = HALF && LM == 12;
+  using C = F4ECfg<LM, (HALF && !HALF_G) ? 2 : 1>;
   using F = F2Cfg<LM>;
   constexpr int L = LM, M = C::M, N = C::N, T = C::T, NP = F::NP;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -152,7 +160,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
 
   if (lead) {
     mbar_init(bar);
-    if constexpr (HALF) mbar_init(bar + 1);
+    if constexpr (HALF) mbar_init(bar + 1);   // N = 8192: the next-slice copies
     mbar_init(&gbar[0]);
     mbar_init(&gbar[1]);
     mbar_init(&cbar[0]);
@@ -194,14 +202,18 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
   if constexpr (HALF) {
     // the launch's first half-step on the slice of its first step (buffer
     // 0); later slices are fetched a step ahead into the other buffer
-    if (lead) bulk_load(ph, d.phasor + size_t(d.n_begin) * N, slice_bytes, bar);
+    // (N = 8192: into the free half of the peer spectrum buffer)
+    if (lead)
+      bulk_load(ph, d.phasor + size_t(d.n_begin) * N + (C::NAT ? size_t(0) : size_t(h) * M),
+                slice_bytes, bar);
     float2 q[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) q[j] = d.state[(band ^ 1) * N + 2 * (t + j * T) + h];
     if (!mbar_wait(bar, 0u)) timed_out = true;
 #pragma unroll
     for (int j = 0; j < 16; ++j)
-      v[j] = couple_cell(v[j], q[j], ph[2 * (t + j * T) + h], band, am1, bb);
+      v[j] = couple_cell(v[j], q[j], ph[C::NAT ? 2 * (t + j * T) + h : t + j * T], band, am1,
+                         bb);
   }
 
   for (int it = 0; it < steps; ++it) {
@@ -225,7 +237,14 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
     f2_store<L, 0>(buf, v, t);
     __syncthreads();
     if (lead) {
-      if constexpr (HALF) {
+      if constexpr (HALF_G) {
+        // this step's slice into the one buffer (phase it + 1: the launch's
+        // first half-step took phase 0); the next one goes to L2 now and to
+        // the peer spectrum buffer once the combine is done
+        bulk_load(ph, d.phasor + size_t(n) * N + size_t(h) * M, slice_bytes, bar);
+        if (it + 1 < steps) bulk_prefetch_l2(d.phasor + size_t(n + 1) * N + size_t(h) * M,
+                                             slice_bytes);
+      } else if constexpr (HALF) {
         // every thread is past step it - 1's couplings, which read the
         // buffer of slice it - 1: fetch slice it + 1 into it
         if (it + 1 < steps)
@@ -280,6 +299,12 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
     f2_dft<L, NP - 1, true, EX>(v);
     f2_store<L, NP - 1>(buf, v, t);
     __syncthreads();
+    if constexpr (HALF_G) {
+      // every thread is past the combine, the last reader of gx[half]
+      if (lead && it + 1 < steps)
+        bulk_load(gx + half * M, d.phasor + size_t(n + 1) * N + size_t(h) * M, slice_bytes,
+                  bar + 1);
+    }
     f2_load<L, 1>(buf, v, t);
     f2_twiddle<true>(v, w1);
     dft<16, true, EX>(v);
@@ -301,16 +326,21 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
     if (!timed_out && !mbar_wait_cluster(&cbar[half], uint32_t((it >> 1) & 1))) timed_out = true;
     if constexpr (HALF) {
       const bool next = it + 1 < steps;
-      if (next && !timed_out &&
-          !mbar_wait(bar + ((it + 1) & 1), uint32_t(((it + 1) >> 1) & 1)))
-        timed_out = true;
+      if constexpr (HALF_G) {
+        if (!timed_out && !mbar_wait(bar, uint32_t((it + 1) & 1))) timed_out = true;
+        if (next && !timed_out && !mbar_wait(bar + 1, uint32_t(it & 1))) timed_out = true;
+      } else {
+        if (next && !timed_out &&
+            !mbar_wait(bar + ((it + 1) & 1), uint32_t(((it + 1) >> 1) & 1)))
+          timed_out = true;
+      }
       const float2* ci = cb + half * M;
-      const float2* phc = ph + (it & 1) * C::PH;
-      const float2* phn = ph + ((it + 1) & 1) * C::PH;
+      const float2* phc = HALF_G ? ph : ph + (it & 1) * C::PH;
+      const float2* phn = HALF_G ? gx + half * M : ph + ((it + 1) & 1) * C::PH;
       const float2 g = rec ? *recph : make_float2(1.f, 0.f);
       const int slot = rec ? (n + 1) / d.record_every - 1 : 0;
       float2* r0 = (rec && d.records) ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
-      float s = 0.f;
+      double s = 0.0;
       // a loop over shared memory (three couplings per point unrolled over
       // 16 points would overflow the instruction cache); buf is free once
       // every thread is past the inverse pass 0, and again for the next
@@ -324,13 +354,15 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
           const int j = 2 * pp + k;
-          const int cell = 2 * (t + j * T) + h;
+          const int cell = C::NAT ? 2 * (t + j * T) + h : t + j * T;
           const float2 p = buf[t + j * T], q = k ? make_float2(q2.z, q2.w) : make_float2(q2.x, q2.y);
           const float2 e = phc[cell];
           float2 c = couple_cell(p, q, e, band, am1, bb);   // step it, second half
           if (rec) {
-            s = fmaf(c.x, c.x, fmaf(c.y, c.y, s));
-            if (r0) r0[cell] = make_float2(fmaf(c.x, g.x, -(c.y * g.y)), fmaf(c.x, g.y, c.y * g.x));
+            s = pow_acc(s, c);
+            if (r0)   // records in natural order
+              r0[2 * (t + j * T) + h] =
+                  make_float2(fmaf(c.x, g.x, -(c.y * g.y)), fmaf(c.x, g.y, c.y * g.x));
           }
           if (next) {   // step it + 1, first half, with the other band's value
             const float2 co = couple_cell(q, p, e, band ^ 1, am1, bb);
@@ -363,12 +395,12 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
       if (rec) {
         const int slot = (n + 1) / d.record_every - 1;
         const float2 g = *recph;
-        float s = 0.f;
+        double s = 0.0;
         float2* r0 = d.records ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
   #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const float2 p = v[j];
-          s = fmaf(p.x, p.x, fmaf(p.y, p.y, s));
+          s = pow_acc(s, p);
           if (r0)
             r0[2 * (t + j * T) + h] =
                 make_float2(fmaf(p.x, g.x, -(p.y * g.y)), fmaf(p.x, g.y, p.y * g.x));
@@ -403,10 +435,16 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
   // copy per step on its barrier, so waiting (again bounded) for the last
   // step's phase leaves no copy of its own in flight when the CTA exits.
   if (timed_out) {
-    if constexpr (HALF)   // the last slice copy: step steps - 1, in its buffer
+    if constexpr (HALF_G) {
+      // the slice copies: phase `steps` of bar (phase 0 was the launch's
+      // first half-step), phase steps - 2 of the next-slice barrier
+      if (lead && steps >= 2) mbar_wait(bar + 1, uint32_t(steps & 1));
+      give_up_after_march(bar, uint32_t(steps & 1), lead, status);
+    } else if constexpr (HALF) {   // the last slice copy: step steps - 1, in its buffer
       give_up_after_march(bar + ((steps - 1) & 1), uint32_t(((steps - 1) >> 1) & 1), lead, status);
-    else
+    } else {
       give_up_after_march(bar, uint32_t((steps - 1) & 1), lead, status);
+    }
   }
   cluster.sync();   // peers may still read our shared memory
 }

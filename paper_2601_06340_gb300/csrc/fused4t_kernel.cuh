@@ -53,8 +53,8 @@ struct F4TCfg {
   static constexpr int OFF_G = OFF_BUF + PADM * 8;         // [3][M] F of parts h+1, h+2, h+3
   static constexpr int OFF_C = OFF_G + 3 * M * 8;          // [2][M] other band's psi_p
   static constexpr int OFF_PH = OFF_C + 2 * M * 8;         // [M] strain slice
-  static constexpr int OFF_MBAR = OFF_PH + M * 8;          // strain-slice barrier
-  static constexpr int OFF_GBAR = OFF_MBAR + 8;            // F arrival
+  static constexpr int OFF_MBAR = OFF_PH + M * 8;          // [2] strain-slice barriers
+  static constexpr int OFF_GBAR = OFF_MBAR + 16;           // F arrival
   static constexpr int OFF_FREE = OFF_GBAR + 8;            // peers have read our F
   static constexpr int OFF_CBAR = OFF_FREE + 8;            // [2] psi_p arrival
   static constexpr int OFF_PPEER = OFF_CBAR + 16;          // [3] band-power parts (h = 0)
@@ -142,7 +142,14 @@ __device__ __forceinline__ void tmem_wait16(float* v) {
                : "memory");
 }
 
-template <bool EX>
+// HALF = true: the second-order (Verlet) step, as in fused4_kernel.cuh: the
+// couplings of step n's second half (both bands) and of step n + 1's first
+// half (own band) after the psi_p swap, the launch's first half-step on the
+// other band read from global memory.  Step n + 1's slice is copied into the
+// peer spectrum slot 0 once the combine has read it; the receiver's "free"
+// arrival for that slot's sender waits until the couplings have used the
+// slice (the sender needs it only before sending its step n + 1 spectrum).
+template <bool EX, bool HALF = false>
 __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
     fused4t_march_kernel(const RowDescF32* __restrict__ rows, int n_rows, int steps,
                          const float4* __restrict__ tw, int* __restrict__ status) {
@@ -192,6 +199,7 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
 
   if (lead) {
     mbar_init(bar);
+    if constexpr (HALF) mbar_init(bar + 1);   // the next-slice copies
     mbar_init(gbar);
     mbar_init_count(gfree, 3);
     mbar_init(&cbar[0]);
@@ -246,8 +254,19 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
   const uint32_t slice_bytes = uint32_t(M) * 8u;
   bool timed_out = false;
   double my_part = 0.0;
-  const float2 am1 = d.am1, bb = d.b;
+  const float2 am1 = HALF ? d.am1h : d.am1, bb = HALF ? d.bh : d.b;
   const bool pow_on = d.powers != nullptr && d.record_every > 0;
+  if constexpr (HALF) {
+    // the launch's first half-step on the slice of its first step (phase 0
+    // of the slice barrier), the other band from global memory
+    if (lead) bulk_load(ph, d.phasor + size_t(d.n_begin) * N + size_t(h) * M, slice_bytes, bar);
+    float2 q[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) q[j] = d.state[(band ^ 1) * N + 4 * (t + j * T) + h];
+    if (!mbar_wait(bar, 0u)) timed_out = true;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = couple_cell(v[j], q[j], ph[t + j * T], band, am1, bb);
+  }
 
   for (int it = 0; it < steps; ++it) {
     const int n = d.n_begin + it;
@@ -269,7 +288,10 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
     f2_store<L, 0>(buf, v, t);
     __syncthreads();
     if (lead) {
+      // (second order: phase it + 1, the launch's first half-step took 0)
       bulk_load(ph, d.phasor + size_t(n) * N + size_t(h) * M, slice_bytes, bar);
+      if (HALF && it + 1 < steps)
+        bulk_prefetch_l2(d.phasor + size_t(n + 1) * N + size_t(h) * M, slice_bytes);
       mbar_expect_tx(gbar, 3u * uint32_t(M) * 8u + ((part_due && h == 0) ? 24u : 0u));
       if (part_due) {
         double s = 0.0;
@@ -341,9 +363,14 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
       }
     }
     __syncthreads();                             // all of our F slots read
-    if (lead)
+    if (lead) {
+      // second order: slot 0 holds step n + 1's slice until the couplings;
+      // its sender is released after them
 #pragma unroll
-      for (int e = 0; e < 3; ++e) mbar_arrive_remote(free_to[e]);
+      for (int e = HALF ? 1 : 0; e < 3; ++e) mbar_arrive_remote(free_to[e]);
+      if (HALF && it + 1 < steps)
+        bulk_load(gx, d.phasor + size_t(n + 1) * N + size_t(h) * M, slice_bytes, bar + 1);
+    }
     dft<16, true, EX>(v);
     f2_store<L, NP - 1>(buf, v, t);
     __syncthreads();
@@ -366,6 +393,54 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
         st_async_v4(co + uint32_t(xpair(pp, t, T)) * 8u, v[2 * pp], v[2 * pp + 1], cbo);
     }
     if (!timed_out && !mbar_wait_cluster(&cbar[half], uint32_t((it >> 1) & 1))) timed_out = true;
+    if constexpr (HALF) {
+      const bool next = it + 1 < steps;
+      if (!timed_out && !mbar_wait(bar, uint32_t((it + 1) & 1))) timed_out = true;
+      if (next && !timed_out && !mbar_wait(bar + 1, uint32_t(it & 1))) timed_out = true;
+      const float2* ci = cb + half * M;
+      const float2* phn = gx;                    // slot 0: step n + 1's slice
+      const float2 g = rec ? *recph : make_float2(1.f, 0.f);
+      const int slot = rec ? (n + 1) / d.record_every - 1 : 0;
+      float2* r0 = (rec && d.records) ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
+      double s = 0.0;
+      // a loop over shared memory, as in fused4_kernel.cuh
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < 16; ++j) buf[t + j * T] = v[j];
+#pragma unroll 1
+      for (int pp = 0; pp < 8; ++pp) {
+        const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int j = 2 * pp + k;
+          const int cell = t + j * T;
+          const float2 p = buf[cell], q = k ? make_float2(q2.z, q2.w) : make_float2(q2.x, q2.y);
+          const float2 e = ph[cell];
+          float2 cc = couple_cell(p, q, e, band, am1, bb);   // step it, second half
+          if (rec) {
+            s = pow_acc(s, cc);
+            if (r0)   // records in natural order
+              r0[4 * cell + h] =
+                  make_float2(fmaf(cc.x, g.x, -(cc.y * g.y)), fmaf(cc.x, g.y, cc.y * g.x));
+          }
+          if (next) {   // step it + 1, first half, with the other band's value
+            const float2 co = couple_cell(q, p, e, band ^ 1, am1, bb);
+            cc = couple_cell(cc, co, phn[cell], band, am1, bb);
+          }
+          buf[cell] = cc;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = buf[t + j * T];
+      __syncthreads();
+      if (lead) mbar_arrive_remote(free_to[0]);   // slot 0 is free again
+      if (rec && d.powers) {
+        double ds = s;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, off);
+        if (lane == 0) red[warp] = ds;   // summed by the lead after the next barrier
+      }
+    } else {
     if (!timed_out && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
     const float2* ci = cb + half * M;
 #pragma unroll
@@ -379,12 +454,12 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
     if (rec) {
       const int slot = (n + 1) / d.record_every - 1;
       const float2 g = *recph;
-      float s = 0.f;
+      double s = 0.0;
       float2* r0 = d.records ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const float2 p = v[j];
-        s = fmaf(p.x, p.x, fmaf(p.y, p.y, s));
+        s = pow_acc(s, p);
         if (r0)
           r0[4 * (t + j * T) + h] =
               make_float2(fmaf(p.x, g.x, -(p.y * g.y)), fmaf(p.x, g.y, p.y * g.x));
@@ -396,6 +471,7 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
         if (lane == 0) red[warp] = ds;   // summed by the lead after the next barrier
       }
     }
+    }   // first-order coupling
   }
 
   __syncthreads();
@@ -417,7 +493,16 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
   // march runs on to the end of the launch; the lead still issues one slice
   // copy per step on its barrier, so waiting (again bounded) for the last
   // step's phase leaves no copy of its own in flight when the CTA exits.
-  if (timed_out) give_up_after_march(bar, uint32_t((steps - 1) & 1), lead, status);
+  if (timed_out) {
+    if constexpr (HALF) {
+      // phase `steps` of the slice barrier (phase 0 was the launch's first
+      // half-step) and phase steps - 2 of the next-slice barrier
+      if (lead && steps >= 2) mbar_wait(bar + 1, uint32_t(steps & 1));
+      give_up_after_march(bar, uint32_t(steps & 1), lead, status);
+    } else {
+      give_up_after_march(bar, uint32_t((steps - 1) & 1), lead, status);
+    }
+  }
   tmem_fence_before();
   cluster.sync();   // peers may still read our shared memory
   tmem_fence_after();

@@ -37,7 +37,9 @@
 
 namespace bpm {
 
-template <int LOGN>
+// PHB: strain-slice buffers per row (2 when the step couples before it
+// propagates: the next step's slice is fetched a step ahead)
+template <int LOGN, int PHB = 1>
 struct FusedCfg {
   static constexpr int N = 1 << LOGN;
   static constexpr int E = N < 16 ? N : 16;          // points per band per thread
@@ -50,9 +52,9 @@ struct FusedCfg {
   static constexpr int WARPS_PER_ROW = T >= 32 ? T / 32 : 1;
   // shared memory layout per CTA (bytes)
   static constexpr int OFF_BUF = 0;                                  // [ROWS][2][PADN] float2
-  static constexpr int OFF_PH = OFF_BUF + ROWS * 2 * PADN * 8;       // [ROWS][N] float2
-  static constexpr int OFF_MBAR = OFF_PH + ROWS * N * 8;             // [ROWS] u64
-  static constexpr int OFF_RECPH = OFF_MBAR + ROWS * 8;              // [ROWS] float2
+  static constexpr int OFF_PH = OFF_BUF + ROWS * 2 * PADN * 8;       // [ROWS][PHB][N] float2
+  static constexpr int OFF_MBAR = OFF_PH + ROWS * PHB * N * 8;       // [ROWS][PHB] u64
+  static constexpr int OFF_RECPH = OFF_MBAR + ROWS * PHB * 8;        // [ROWS] float2
   static constexpr int OFF_RED = OFF_RECPH + ROWS * 8;               // [ROWS][WARPS][2] double
   static constexpr int SMEM = OFF_RED + ROWS * WARPS_PER_ROW * 2 * 8;
   // layout checks: fits one SM (227 KB); bulk-copy and 16-byte store
@@ -95,6 +97,12 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src,
       "[%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(b)
       : "memory");
+}
+
+// Asynchronous prefetch of `bytes` of global memory into L2 (16-byte aligned
+// address, size a multiple of 16); nothing to wait for.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
 // Poll limit of every bounded mbarrier wait: a try_wait that finds the phase
@@ -237,12 +245,62 @@ __device__ __forceinline__ void last_pass(float2* v0, float2* v1, int t,
   dft_pass<LOGN, P, true>(v0, v1);
 }
 
+// Coupling of Eq. fov10 on this thread's cells of both bands, coefficients
+// (a - 1, b) of the (fractional) step, e the cells' strain phasors.
 template <int LOGN>
+__device__ __forceinline__ void couple_both(float2* v0, float2* v1, const float2* ph, int t,
+                                            float2 am1, float2 bb) {
+  using C = FusedCfg<LOGN>;
+  constexpr int T = C::T, R0 = C::radix(0), G0 = C::groups(0), S0 = C::stride(0);
+#pragma unroll
+  for (int i = 0; i < G0; ++i)
+#pragma unroll
+    for (int j = 0; j < R0; ++j) {
+      const int pos = (t + i * T) + j * S0;
+      const float2 e = ph[pos];
+      const bool inside = (e.x != 0.f) | (e.y != 0.f);
+      const float ax = inside ? am1.x : 0.f, ay = inside ? am1.y : 0.f;
+      // b e and b conj(e)
+      const float2 bp = make_float2(fmaf(bb.x, e.x, -(bb.y * e.y)),
+                                    fmaf(bb.x, e.y, bb.y * e.x));
+      const float2 bm = make_float2(fmaf(bb.x, e.x, bb.y * e.y),
+                                    fmaf(bb.y, e.x, -(bb.x * e.y)));
+      const float2 p = v0[i * R0 + j], m = v1[i * R0 + j];
+      float px = fmaf(ax, p.x, p.x);
+      px = fmaf(-ay, p.y, px);
+      px = fmaf(bp.x, m.x, px);
+      px = fmaf(-bp.y, m.y, px);
+      float py = fmaf(ax, p.y, p.y);
+      py = fmaf(ay, p.x, py);
+      py = fmaf(bp.x, m.y, py);
+      py = fmaf(bp.y, m.x, py);
+      float mx = fmaf(ax, m.x, m.x);
+      mx = fmaf(-ay, m.y, mx);
+      mx = fmaf(bm.x, p.x, mx);
+      mx = fmaf(-bm.y, p.y, mx);
+      float my = fmaf(ax, m.y, m.y);
+      my = fmaf(ay, m.x, my);
+      my = fmaf(bm.x, p.y, my);
+      my = fmaf(bm.y, p.x, my);
+      v0[i * R0 + j] = make_float2(px, py);
+      v1[i * R0 + j] = make_float2(mx, my);
+    }
+}
+
+// SCH: the operator splitting of the step, as in fused2_kernel.cuh (0 the
+// first-order step of Eq. fov10; 1 Verlet: couple with (am1h, bh),
+// propagate, couple with (am1h, bh); 2 Forest-Ruth: couple with (am1h, bh)
+// = t/2, then propagate t dz / couple (am1, b) = (1 - t)/2, propagate
+// (1 - 2t) dz / couple (am1, b), propagate t dz / couple (am1h, bh), the
+// row's table holding the increments of t dz then (1 - 2t) dz per band).
+template <int LOGN, int SCH = 0>
 __global__ void __launch_bounds__(FusedCfg<LOGN>::THREADS)
     fused_march_kernel(const RowDescF32* __restrict__ rows, int n_rows,
                        int steps, const float4* __restrict__ tw,
                        int* __restrict__ status) {
-  using C = FusedCfg<LOGN>;
+  constexpr bool HALF = SCH != 0;                  // couples before propagating
+  constexpr int STAGES = SCH == 2 ? 3 : 1;
+  using C = FusedCfg<LOGN, HALF ? 2 : 1>;
   constexpr int N = C::N, T = C::T, NP = C::NP, R0 = C::radix(0);
   constexpr int G0 = C::groups(0), S0 = C::stride(0);
   extern __shared__ __align__(128) unsigned char smem[];
@@ -255,12 +313,15 @@ __global__ void __launch_bounds__(FusedCfg<LOGN>::THREADS)
 
   float2* b0 = reinterpret_cast<float2*>(smem + C::OFF_BUF) + rl * 2 * C::PADN;
   float2* b1 = b0 + C::PADN;
-  float2* ph = reinterpret_cast<float2*>(smem + C::OFF_PH) + rl * N;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::OFF_MBAR) + rl;
+  float2* ph0 = reinterpret_cast<float2*>(smem + C::OFF_PH) + rl * (HALF ? 2 : 1) * N;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::OFF_MBAR) + rl * (HALF ? 2 : 1);
   float2* recph = reinterpret_cast<float2*>(smem + C::OFF_RECPH) + rl;
   double* red = reinterpret_cast<double*>(smem + C::OFF_RED) + rl * C::WARPS_PER_ROW * 2;
 
-  if (t == 0) mbar_init(bar);
+  if (t == 0) {
+    mbar_init(bar);
+    if constexpr (HALF) mbar_init(bar + 1);
+  }
   fence_mbar_init();
 
   // Registers: pass-0 groups of both bands, natural positions gi + j*S0.
@@ -280,18 +341,24 @@ __global__ void __launch_bounds__(FusedCfg<LOGN>::THREADS)
   const uint32_t slice_bytes = uint32_t(N) * 8u;
   int pending_slot = -1;            // record whose powers await reduction
   bool timed_out = false;
+  if constexpr (HALF) {
+    // the first step's slice; later ones are fetched a step ahead
+    if (t == 0 && active && steps > 0)
+      bulk_load(ph0, d.phasor + size_t(d.n_begin) * N, slice_bytes, bar);
+  }
 
   // Error path: a thread whose bounded wait expires raises s_abort; at the
   // next step's first barrier (or after the last step) each row's lead waits
-  // once more (again bounded) for its last slice copy, so none is in flight
-  // when the CTA exits, and the CTA returns.  With one thread per row and no
-  // barrier in the step (N <= 16) that thread alone leaves the march.
+  // once more (again bounded) for its slice copies in flight, so none is in
+  // flight when the CTA exits, and the CTA returns.  With one thread per row
+  // and no barrier in the step (N <= 16) that thread alone leaves the march.
   int it = 0;
   for (; it < steps; ++it) {
     if constexpr (NP == 1) {
       if (timed_out) break;
     }
     const int n = d.n_begin + it;
+    float2* ph = ph0 + (HALF ? (it & 1) * N : 0);
     const bool rec = active && d.record_every > 0 &&
                      ((n + 1) % d.record_every) == 0 &&
                      (d.records != nullptr || d.powers != nullptr);
@@ -302,97 +369,108 @@ __global__ void __launch_bounds__(FusedCfg<LOGN>::THREADS)
       sincos(ang, &sa, &ca);
       *recph = make_float2(float(ca), float(sa));
     }
-
-    if constexpr (NP == 1) {
-      if (t == 0 && active) bulk_load(ph, d.phasor + size_t(n) * N, slice_bytes, bar);
-      last_pass<LOGN>(v0, v1, t, d.prop);
-    } else {
-      // forward pass 0: DFT + twiddle, to shared memory
-      dft_pass<LOGN, 0, false>(v0, v1);
-      twiddle_pass<LOGN, 0, false>(v0, v1, t, tw);
-      store_pass<LOGN, 0>(b0, v0, t);
-      store_pass<LOGN, 0>(b1, v1, t);
-      __syncthreads();
-      if (s_abort) {   // the same value for every thread (read after the barrier)
-        if (t == 0 && active && it > 0) mbar_wait(bar, uint32_t((it - 1) & 1));
-        if (threadIdx.x == 0) atomicOr(status, kStatusWaitTimeout);
-        return;
+    if constexpr (HALF) {
+      // one thread per row (N <= 16) has no barrier in the step: it is past
+      // its own couplings of step it - 1, so the other buffer is free
+      if constexpr (NP == 1) {
+        if (t == 0 && active && it + 1 < steps)
+          bulk_load(ph0 + ((it + 1) & 1) * N, d.phasor + size_t(n + 1) * N, slice_bytes,
+                    bar + ((it + 1) & 1));
       }
-      // every thread of the row has finished the previous step's coupling:
-      // the slice buffer is free for this step's copy.
-      if (t == 0 && active) bulk_load(ph, d.phasor + size_t(n) * N, slice_bytes, bar);
-      if (t == 0 && pending_slot >= 0) {
-        double s0 = 0.0, s1 = 0.0;
-        for (int w = 0; w < C::WARPS_PER_ROW; ++w) {
-          s0 += red[2 * w];
-          s1 += red[2 * w + 1];
+      // the leading coupling, on this step's slice
+      if (active) {
+        if (!timed_out && !mbar_wait(bar + (it & 1), uint32_t((it >> 1) & 1))) {
+          timed_out = true;
+          s_abort = 1;
         }
-        d.powers[2 * pending_slot] = s0 * d.dx_um;
-        d.powers[2 * pending_slot + 1] = s1 * d.dx_um;
-        pending_slot = -1;
+        couple_both<LOGN>(v0, v1, ph, t, d.am1h, d.bh);
       }
-      if constexpr (NP >= 3) fwd_mid<LOGN, 1>(b0, b1, v0, v1, t, tw);
-      if constexpr (NP >= 4) fwd_mid<LOGN, 2>(b0, b1, v0, v1, t, tw);
-      load_pass<LOGN, NP - 1>(b0, v0, t);
-      load_pass<LOGN, NP - 1>(b1, v1, t);
-      last_pass<LOGN>(v0, v1, t, d.prop);
-      store_pass<LOGN, NP - 1>(b0, v0, t);
-      store_pass<LOGN, NP - 1>(b1, v1, t);
-      __syncthreads();
-      if constexpr (NP >= 4) inv_mid<LOGN, 2>(b0, b1, v0, v1, t, tw);
-      if constexpr (NP >= 3) inv_mid<LOGN, 1>(b0, b1, v0, v1, t, tw);
-      load_pass<LOGN, 0>(b0, v0, t);
-      load_pass<LOGN, 0>(b1, v1, t);
-      twiddle_pass<LOGN, 0, true>(v0, v1, t, tw);
-      dft_pass<LOGN, 0, true>(v0, v1);
     }
 
-    // ---- coupling through chi_0, chi_h, the strain phase and the mask ----
-    if (active) {
-      if (!mbar_wait(bar, uint32_t(it & 1))) {
-        timed_out = true;
-        s_abort = 1;
-      }
-      const float2 am1 = d.am1, bb = d.b;
-#pragma unroll
-      for (int i = 0; i < G0; ++i)
-#pragma unroll
-        for (int j = 0; j < R0; ++j) {
-          const int pos = (t + i * T) + j * S0;
-          const float2 e = ph[pos];
-          const bool inside = (e.x != 0.f) | (e.y != 0.f);
-          const float ax = inside ? am1.x : 0.f, ay = inside ? am1.y : 0.f;
-          // b e and b conj(e)
-          const float2 bp = make_float2(fmaf(bb.x, e.x, -(bb.y * e.y)),
-                                        fmaf(bb.x, e.y, bb.y * e.x));
-          const float2 bm = make_float2(fmaf(bb.x, e.x, bb.y * e.y),
-                                        fmaf(bb.y, e.x, -(bb.x * e.y)));
-          const float2 p = v0[i * R0 + j], m = v1[i * R0 + j];
-          float px = fmaf(ax, p.x, p.x);
-          px = fmaf(-ay, p.y, px);
-          px = fmaf(bp.x, m.x, px);
-          px = fmaf(-bp.y, m.y, px);
-          float py = fmaf(ax, p.y, p.y);
-          py = fmaf(ay, p.x, py);
-          py = fmaf(bp.x, m.y, py);
-          py = fmaf(bp.y, m.x, py);
-          float mx = fmaf(ax, m.x, m.x);
-          mx = fmaf(-ay, m.y, mx);
-          mx = fmaf(bm.x, p.x, mx);
-          mx = fmaf(-bm.y, p.y, mx);
-          float my = fmaf(ax, m.y, m.y);
-          my = fmaf(ay, m.x, my);
-          my = fmaf(bm.x, p.y, my);
-          my = fmaf(bm.y, p.x, my);
-          v0[i * R0 + j] = make_float2(px, py);
-          v1[i * R0 + j] = make_float2(mx, my);
+#pragma unroll 1
+    for (int sg = 0; sg < STAGES; ++sg) {
+      // the stage's propagator increments: (P - 1)/N of the whole step, or
+      // for Forest-Ruth those of t dz (stages 0, 2) and (1 - 2t) dz (stage 1)
+      const float2* tab = d.prop + ((SCH == 2 && sg == 1) ? 2 * N : 0);
+      if constexpr (NP == 1) {
+        if constexpr (!HALF) {
+          if (t == 0 && active) bulk_load(ph, d.phasor + size_t(n) * N, slice_bytes, bar);
         }
-    }
+        last_pass<LOGN>(v0, v1, t, tab);
+      } else {
+        // forward pass 0: DFT + twiddle, to shared memory
+        dft_pass<LOGN, 0, false>(v0, v1);
+        twiddle_pass<LOGN, 0, false>(v0, v1, t, tw);
+        store_pass<LOGN, 0>(b0, v0, t);
+        store_pass<LOGN, 0>(b1, v1, t);
+        __syncthreads();
+        if (sg == 0) {
+          if (s_abort) {   // the same value for every thread (read after the barrier)
+            if (t == 0 && active) {
+              // slices up to it were issued (HALF), else up to it - 1
+              if constexpr (HALF) mbar_wait(bar + (it & 1), uint32_t((it >> 1) & 1));
+              else if (it > 0) mbar_wait(bar, uint32_t((it - 1) & 1));
+            }
+            if (threadIdx.x == 0) atomicOr(status, kStatusWaitTimeout);
+            return;
+          }
+          // every thread of the row has finished the previous step's
+          // couplings: the slice buffer they read is free
+          if constexpr (HALF) {
+            if (t == 0 && active && it + 1 < steps)
+              bulk_load(ph0 + ((it + 1) & 1) * N, d.phasor + size_t(n + 1) * N, slice_bytes,
+                        bar + ((it + 1) & 1));
+          } else {
+            if (t == 0 && active) bulk_load(ph, d.phasor + size_t(n) * N, slice_bytes, bar);
+          }
+          if (t == 0 && pending_slot >= 0) {
+            double s0 = 0.0, s1 = 0.0;
+            for (int w = 0; w < C::WARPS_PER_ROW; ++w) {
+              s0 += red[2 * w];
+              s1 += red[2 * w + 1];
+            }
+            d.powers[2 * pending_slot] = s0 * d.dx_um;
+            d.powers[2 * pending_slot + 1] = s1 * d.dx_um;
+            pending_slot = -1;
+          }
+        }
+        if constexpr (NP >= 3) fwd_mid<LOGN, 1>(b0, b1, v0, v1, t, tw);
+        if constexpr (NP >= 4) fwd_mid<LOGN, 2>(b0, b1, v0, v1, t, tw);
+        load_pass<LOGN, NP - 1>(b0, v0, t);
+        load_pass<LOGN, NP - 1>(b1, v1, t);
+        last_pass<LOGN>(v0, v1, t, tab);
+        store_pass<LOGN, NP - 1>(b0, v0, t);
+        store_pass<LOGN, NP - 1>(b1, v1, t);
+        __syncthreads();
+        if constexpr (NP >= 4) inv_mid<LOGN, 2>(b0, b1, v0, v1, t, tw);
+        if constexpr (NP >= 3) inv_mid<LOGN, 1>(b0, b1, v0, v1, t, tw);
+        load_pass<LOGN, 0>(b0, v0, t);
+        load_pass<LOGN, 0>(b1, v1, t);
+        twiddle_pass<LOGN, 0, true>(v0, v1, t, tw);
+        dft_pass<LOGN, 0, true>(v0, v1);
+      }
+
+      // ---- coupling through chi_0, chi_h, the strain phase and the mask --
+      if (active) {
+        if constexpr (!HALF) {
+          if (!mbar_wait(bar, uint32_t(it & 1))) {
+            timed_out = true;
+            s_abort = 1;
+          }
+          couple_both<LOGN>(v0, v1, ph, t, d.am1, d.b);
+        } else if constexpr (SCH == 1) {
+          couple_both<LOGN>(v0, v1, ph, t, d.am1h, d.bh);
+        } else {
+          const bool last = sg == STAGES - 1;
+          couple_both<LOGN>(v0, v1, ph, t, last ? d.am1h : d.am1, last ? d.bh : d.b);
+        }
+      }
+    }   // stages
 
     // ---- record: coalesced write of psi * g^k, band powers ----------------
     const bool want_pw = rec && d.powers != nullptr;
     const int slot = rec ? (n + 1) / d.record_every - 1 : 0;
-    float s0 = 0.f, s1 = 0.f;
+    double s0 = 0.0, s1 = 0.0;
     if (rec) {
       const float2 g = *recph;
       float2* r0 = d.records ? d.records + size_t(slot) * 2 * N : nullptr;
@@ -402,8 +480,8 @@ __global__ void __launch_bounds__(FusedCfg<LOGN>::THREADS)
         for (int j = 0; j < R0; ++j) {
           const int pos = (t + i * T) + j * S0;
           const float2 p = v0[i * R0 + j], m = v1[i * R0 + j];
-          s0 = fmaf(p.x, p.x, fmaf(p.y, p.y, s0));
-          s1 = fmaf(m.x, m.x, fmaf(m.y, m.y, s1));
+          s0 = pow_acc(s0, p);
+          s1 = pow_acc(s1, m);
           if (r0) {
             r0[pos] = make_float2(fmaf(p.x, g.x, -(p.y * g.y)), fmaf(p.x, g.y, p.y * g.x));
             r0[N + pos] = make_float2(fmaf(m.x, g.x, -(m.y * g.y)), fmaf(m.x, g.y, m.y * g.x));
@@ -440,7 +518,18 @@ __global__ void __launch_bounds__(FusedCfg<LOGN>::THREADS)
   __syncthreads();
   {
     const bool stopped = NP == 1 ? timed_out : s_abort != 0;
-    if (stopped && t == 0 && active && it > 0) mbar_wait(bar, uint32_t((it - 1) & 1));
+    if (stopped && t == 0 && active) {
+      if constexpr (HALF) {
+        // the copy whose wait expired (step it - 1 for one thread per row,
+        // which leaves at the start of step it; the last step otherwise)
+        // and, for one thread per row, the one issued a step ahead
+        const int last = NP == 1 ? it - 1 : steps - 1;
+        if (last >= 0) mbar_wait(bar + (last & 1), uint32_t((last >> 1) & 1));
+        if (NP == 1 && it < steps) mbar_wait(bar + (it & 1), uint32_t((it >> 1) & 1));
+      } else if (it > 0) {
+        mbar_wait(bar, uint32_t((it - 1) & 1));
+      }
+    }
   }
   if (t == 0 && pending_slot >= 0) {
     double s0 = 0.0, s1 = 0.0;

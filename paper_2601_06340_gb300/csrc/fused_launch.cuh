@@ -25,42 +25,43 @@ inline bool fused_exact_constants() {
   return v == 1;
 }
 
-template <int LOGN>
+// Both-bands-per-thread kernel (N <= 128); SCH the operator splitting.
+template <int LOGN, int SCH = 0>
 int fused_launch_impl(const RowDescF32* d_rows, int n_rows, int steps,
                       const float4* d_tw, int* d_status, cudaStream_t st) {
-  using C = FusedCfg<LOGN>;
+  using C = FusedCfg<LOGN, SCH != 0 ? 2 : 1>;
   static std::atomic<bool> configured{false};
   if (!configured.load(std::memory_order_acquire)) {
-    cudaError_t e = cudaFuncSetAttribute(fused_march_kernel<LOGN>,
+    cudaError_t e = cudaFuncSetAttribute(fused_march_kernel<LOGN, SCH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          C::SMEM);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused)");
     configured.store(true, std::memory_order_release);
   }
   const int grid = (n_rows + C::ROWS - 1) / C::ROWS;
-  fused_march_kernel<LOGN><<<grid, C::THREADS, C::SMEM, st>>>(d_rows, n_rows, steps,
-                                                              d_tw, d_status);
+  fused_march_kernel<LOGN, SCH><<<grid, C::THREADS, C::SMEM, st>>>(d_rows, n_rows, steps,
+                                                                   d_tw, d_status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "fused march launch");
   return BPM_OK;
 }
 
 // Band-per-thread kernel (256 <= N <= 4096); EX selects hi+lo butterfly
-// constants, HALF the second-order (Verlet) step.
-template <int LOGN, bool EX, bool HALF = false>
+// constants, SCH the operator splitting (first order, Verlet, Forest-Ruth).
+template <int LOGN, bool EX, int SCH = kSchFirst>
 int fused2_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const float4* d_tw,
                        int* d_status, cudaStream_t st) {
-  using C = F2Cfg<LOGN, HALF ? 2 : 1>;
+  using C = F2Cfg<LOGN, SCH != kSchFirst ? 2 : 1>;
   static std::atomic<bool> configured{false};
   if (!configured.load(std::memory_order_acquire)) {
-    cudaError_t e = cudaFuncSetAttribute(fused2_march_kernel<LOGN, EX, HALF>,
+    cudaError_t e = cudaFuncSetAttribute(fused2_march_kernel<LOGN, EX, SCH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused2)");
     configured.store(true, std::memory_order_release);
   }
   const int grid = (n_rows + C::ROWS - 1) / C::ROWS;
-  fused2_march_kernel<LOGN, EX, HALF><<<grid, C::THREADS, C::SMEM, st>>>(d_rows, n_rows, steps,
-                                                                        d_tw, d_status);
+  fused2_march_kernel<LOGN, EX, SCH><<<grid, C::THREADS, C::SMEM, st>>>(d_rows, n_rows, steps,
+                                                                       d_tw, d_status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "fused2 march launch");
   return BPM_OK;
@@ -136,13 +137,14 @@ int fused3_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
 
 // Split-band cluster kernels for N = 4096 P (cluster of 2P CTAs per row):
 // both run the one-exchange form (P = 4 with its tables in tensor memory).
-template <int P, bool EX>
+// HALF: the second-order (Verlet) step.
+template <int P, bool EX, bool HALF = false>
 int fused4_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const float4* d_tw,
                        int* d_status, cudaStream_t st) {
   static_assert(P == 2 || P == 4, "N = 8192 or 16384");
   auto kern = [] {
-    if constexpr (P == 2) return fused4e_march_kernel<12, EX>;
-    else return fused4t_march_kernel<EX>;
+    if constexpr (P == 2) return fused4e_march_kernel<12, EX, HALF>;
+    else return fused4t_march_kernel<EX, HALF>;
   }();
   constexpr int smem = P == 2 ? F4ECfg<12>::SMEM : F4TCfg::SMEM;
   constexpr int threads = P == 2 ? F4ECfg<12>::T : F4TCfg::T;
@@ -175,6 +177,12 @@ int fused4_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
     return fused_exact_constants()                                                \
                ? fused4_launch_impl<P, true>(r, n, s, tw, status, st)             \
                : fused4_launch_impl<P, false>(r, n, s, tw, status, st);           \
+  }                                                                               \
+  int fused4v_launch_##L(const RowDescF32* r, int n, int s, const float4* tw,    \
+                         int* status, cudaStream_t st) {                          \
+    return fused_exact_constants()                                                \
+               ? fused4_launch_impl<P, true, true>(r, n, s, tw, status, st)       \
+               : fused4_launch_impl<P, false, true>(r, n, s, tw, status, st);     \
   }                                                                               \
   }
 
@@ -222,14 +230,25 @@ int fused4_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
   }                                                                               \
   int fused2h_rows_resident_##L() {                                               \
     using C = F2Cfg<L, 2>;                                                        \
-    return blocks_per_sm(fused2_march_kernel<L, true, true>, C::THREADS, C::SMEM) * \
-           C::ROWS;                                                               \
+    return blocks_per_sm(fused2_march_kernel<L, true, kSchVerlet>, C::THREADS,    \
+                         C::SMEM) * C::ROWS;                                      \
   }                                                                               \
   int fused2h_launch_##L(const RowDescF32* r, int n, int s, const float4* tw,    \
                          int* status, cudaStream_t st) {                          \
     return fused_exact_constants()                                                \
-               ? fused2_launch_impl<L, true, true>(r, n, s, tw, status, st)       \
-               : fused2_launch_impl<L, false, true>(r, n, s, tw, status, st);     \
+               ? fused2_launch_impl<L, true, kSchVerlet>(r, n, s, tw, status, st) \
+               : fused2_launch_impl<L, false, kSchVerlet>(r, n, s, tw, status, st); \
+  }                                                                               \
+  int fused2f_rows_resident_##L() {                                               \
+    using C = F2Cfg<L, 2>;                                                        \
+    return blocks_per_sm(fused2_march_kernel<L, true, kSchForestRuth>, C::THREADS, \
+                         C::SMEM) * C::ROWS;                                      \
+  }                                                                               \
+  int fused2f_launch_##L(const RowDescF32* r, int n, int s, const float4* tw,    \
+                         int* status, cudaStream_t st) {                          \
+    return fused_exact_constants()                                                \
+               ? fused2_launch_impl<L, true, kSchForestRuth>(r, n, s, tw, status, st) \
+               : fused2_launch_impl<L, false, kSchForestRuth>(r, n, s, tw, status, st); \
   }                                                                               \
   }
 
@@ -242,6 +261,22 @@ int fused4_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
   int fused_launch_##L(const RowDescF32* r, int n, int s, const float4* tw,      \
                        int* status, cudaStream_t st) {                            \
     return fused_launch_impl<L>(r, n, s, tw, status, st);                         \
+  }                                                                               \
+  int fusedh_rows_resident_##L() {                                                \
+    using C = FusedCfg<L, 2>;                                                     \
+    return blocks_per_sm(fused_march_kernel<L, 1>, C::THREADS, C::SMEM) * C::ROWS; \
+  }                                                                               \
+  int fusedh_launch_##L(const RowDescF32* r, int n, int s, const float4* tw,     \
+                        int* status, cudaStream_t st) {                           \
+    return fused_launch_impl<L, 1>(r, n, s, tw, status, st);                      \
+  }                                                                               \
+  int fusedf_rows_resident_##L() {                                                \
+    using C = FusedCfg<L, 2>;                                                     \
+    return blocks_per_sm(fused_march_kernel<L, 2>, C::THREADS, C::SMEM) * C::ROWS; \
+  }                                                                               \
+  int fusedf_launch_##L(const RowDescF32* r, int n, int s, const float4* tw,     \
+                        int* status, cudaStream_t st) {                           \
+    return fused_launch_impl<L, 2>(r, n, s, tw, status, st);                      \
   }                                                                               \
   }
 

@@ -271,6 +271,24 @@ void fused_prop_table(const bpm_plan_s* plan, int row, std::vector<float2>* out)
   }
 }
 
+void fused_prop_table_frac(const bpm_plan_s* plan, int row, double frac,
+                           std::vector<float2>* out) {
+  const EnergyConsts& c = plan->ec[row];
+  const int n = plan->nx;
+  std::vector<int> order = fft_output_order(plan->logn);
+  out->assign(2 * size_t(n), float2{0.f, 0.f});
+  const double inv_n = 1.0 / double(n);
+  for (int band = 0; band < 2; ++band) {
+    const int sign = band == 0 ? +1 : -1;
+    for (int pos = 0; pos < n; ++pos) {
+      const double q = fftfreq_q(order[pos], n, c.dxh);
+      const double ph = frac * c.dzh * delta_q(q, c.s, c.c, sign);
+      const cd d = expm1_i(cd(ph, 0.0)) * inv_n;
+      (*out)[size_t(band) * n + pos] = float2{float(d.real()), float(d.imag())};
+    }
+  }
+}
+
 void vol_prop_table(const bpm_plan_s* plan, int row, std::vector<float2>* out) {
   // delta_+-(qx, qy) = sqrt(1 - (qx +- s)^2 - qy^2) - cos(alpha)
   //                  = -(qx (qx +- 2 s) + qy^2) / (sqrt(...) + cos(alpha))

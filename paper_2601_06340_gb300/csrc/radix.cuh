@@ -27,6 +27,12 @@ constexpr float kS1l = float(kS1d - double(kS1h));
 constexpr float kHh = float(kHd);
 constexpr float kHl = float(kHd - double(kHh));
 
+// |p|^2 added to an FP64 band-power sum: the squares of FP32 values are
+// exact in FP64, so the sum's only roundings are its FP64 additions.
+__device__ __forceinline__ double pow_acc(double s, float2 p) {
+  return fma(double(p.x), double(p.x), fma(double(p.y), double(p.y), s));
+}
+
 // Complex add / subtract.  PACK = true: one packed FP32x2 instruction (sm_100
 // family) each; per component the result is the correctly rounded scalar
 // sum or difference (a - b is formed as b * (-1) + a, which rounds once,

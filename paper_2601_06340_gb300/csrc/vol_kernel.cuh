@@ -166,14 +166,14 @@ __global__ void __launch_bounds__(VolRowCfg<LOGN>::THREADS)
       double sa, ca;
       sincos(ang, &sa, &ca);
       const float2 g = make_float2(float(ca), float(sa));
-      float s = 0.f;
+      double s = 0.0;
       float2* r0 = p.records ? p.records + ((size_t(r) * p.n_rec + slot) * 2 + band) * plane +
                                    size_t(y) * N
                              : nullptr;
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const float2 q = v[j];
-        s = fmaf(q.x, q.x, fmaf(q.y, q.y, s));
+        s = pow_acc(s, q);
         if (r0) r0[t + j * T] = make_float2(fmaf(q.x, g.x, -(q.y * g.y)), fmaf(q.x, g.y, q.y * g.x));
       }
       if (p.pwpart) {

@@ -4,8 +4,8 @@ A batch that can run as one 2-CTA cluster per row or one CTA per row, or as a
 rotation with several chunk lengths, is timed in each shape on its first
 march and runs in the fastest.  The chosen shape must be one of the
 candidates, the result must match the oracle, and rotation chunks must not
-change a single bit (rows are independent and each chunk resumes from the
-stored FP32 state).
+change a single bit of the fields and records (rows are independent and each
+chunk resumes from the stored FP32 state).
 """
 
 import numpy as np
@@ -53,7 +53,10 @@ def test_rotation_chunk_search_is_bit_exact(bpm_lib, monkeypatch):
     assert rshape == (-1, 64)
     assert np.array_equal(out.psi, rule.psi)
     assert np.array_equal(out.records, rule.records)
-    assert np.array_equal(out.powers, rule.powers)
+    # the rule runs a rotation's short tail launches on the 2-CTA cluster
+    # kernel, which sums the same FP64 per-thread partial powers in another
+    # tree order: equal to FP64 rounding, not bit for bit
+    assert np.allclose(out.powers, rule.powers, rtol=1e-14, atol=0)
     rows = [7, 199]
     ref = run_ref(wl, rows=rows)
     assert max(band_errors(out.psi[rows], ref.psi)) <= 2e-5

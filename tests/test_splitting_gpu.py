@@ -1,6 +1,6 @@
 """Operator splitting of Eq. split-op (Verlet, Forest-Ruth) on the plain
-FP64 GPU path, and Verlet on the fused FP32 path (N = 256..4096), against
-the oracle; other combinations are refused."""
+FP64 GPU path, and Verlet and Forest-Ruth on the fused FP32 path
+(N = 8..4096), against the oracle; other combinations are refused."""
 
 import pytest
 
@@ -37,11 +37,11 @@ def test_splitting_refused_where_not_built(bpm_lib):
     with binding.Plan(wl, FP32) as plan:
         binding.bpm_set_splitting(plan.handle, binding.BPM_SPLIT_FIRST_ORDER)
         binding.bpm_set_splitting(plan.handle, binding.BPM_SPLIT_VERLET)
+        binding.bpm_set_splitting(plan.handle, binding.BPM_SPLIT_FOREST_RUTH)
+    with binding.Plan(inputs.serving_request(np.random.default_rng(1), 8192, 10), FP32) as plan:
+        binding.bpm_set_splitting(plan.handle, binding.BPM_SPLIT_VERLET)
         with pytest.raises(binding.BpmError):
             binding.bpm_set_splitting(plan.handle, binding.BPM_SPLIT_FOREST_RUTH)
-    with binding.Plan(inputs.laue_perfect(nx=128, nz=10), FP32) as plan:
-        with pytest.raises(binding.BpmError):
-            binding.bpm_set_splitting(plan.handle, binding.BPM_SPLIT_VERLET)
     with binding.Plan(wl, FP64) as plan:
         with pytest.raises(binding.BpmError):
             binding.bpm_set_splitting(plan.handle, 7)
@@ -107,3 +107,89 @@ def test_verlet_fp32_full_size_bragg(bpm_lib):
     errs = band_errors(out.psi, ref.psi, out.records, ref.records)
     assert max(errs) <= TOL_FP32, errs
     assert np.allclose(out.powers, ref.powers, rtol=1e-4, atol=1e-9 * ref.powers.max())
+
+
+@pytest.mark.parametrize("nx", [8, 16, 32, 64, 128])
+@pytest.mark.parametrize("method", ["verlet", "forest_ruth"])
+def test_small_n_splitting_fp32_matches_oracle(bpm_lib, nx, method):
+    """N <= 128 (both bands per thread, several rows per CTA): Verlet and
+    Forest-Ruth on random two-band fields through a masked, strained bulk
+    with a ragged record tail, a batch of rows with different energies."""
+    rng = np.random.default_rng(nx + 7)
+    nz = 37
+    wl = inputs.pulse_batched(nx=nx, nz=nz, n_energy=5, dx_um=0.4, record_every=12)
+    wl.psi0 = rng.standard_normal((5, 2, nx)) + 1j * rng.standard_normal((5, 2, nx))
+    wl.crystal = dict(kind=inputs.CRYSTAL_MASK, mask=(rng.uniform(size=(nz, nx)) < 0.8))
+    wl.strain = dict(kind=inputs.STRAIN_ARRAY, ux=rng.uniform(-1e-3, 1e-3, (nz, nx)))
+    ref = run_ref(wl, method=method)
+    with binding.Plan(wl, FP32, splitting=METHODS[method]) as plan:
+        out = plan.propagate()
+        shape = binding.bpm_launch_shape(plan.handle)
+    assert shape[0] == (3 if method == "verlet" else 6), shape
+    errs = band_errors(out.psi, ref.psi, out.records, ref.records)
+    assert max(errs) <= 2e-6, errs
+    assert np.allclose(out.powers, ref.powers, rtol=1e-5, atol=1e-9 * ref.powers.max())
+    first = run_ref(wl)
+    assert max(band_errors(first.psi, ref.psi)) > 1e3 * max(errs)
+
+
+@pytest.mark.parametrize("name", ["n256", "laue_perfect", "bragg_bent", "asym_dislocation",
+                                  "pulse"])
+def test_forest_ruth_fp32_matches_oracle(bpm_lib, name):
+    """The fused band-per-thread kernel's fourth-order step (coupling t/2,
+    then propagate t dz / couple (1-t)/2, propagate (1-2t) dz / couple
+    (1-t)/2, propagate t dz / couple t/2, all on the slice of the step)
+    against the oracle's Forest-Ruth march: fields, records and powers, rows
+    of a rotated batch included.  It must differ from both the first-order
+    and the Verlet march by more than its own error."""
+    wl = {"n256": lambda: inputs.laue_perfect(nx=256, nz=300, dx_um=0.8, record_every=70),
+          "laue_perfect": lambda: inputs.laue_perfect(nx=512, nz=400, record_every=50),
+          "bragg_bent": lambda: inputs.bragg_bent(nx=4096, nz=1000, record_every=150),
+          "asym_dislocation": lambda: inputs.asym_dislocation(nx=1024, nz=500,
+                                                              record_every=100),
+          # more rows than one launch keeps resident: the rotation schedule
+          "pulse": lambda: inputs.pulse_batched(nx=4096, nz=300, n_energy=160,
+                                                record_every=100)}[name]()
+    rows = [0, wl.batch - 1]
+    ref = run_ref(wl, method="forest_ruth", rows=rows)
+    with binding.Plan(wl, FP32, splitting=binding.BPM_SPLIT_FOREST_RUTH) as plan:
+        out = plan.propagate()
+        shape = binding.bpm_launch_shape(plan.handle)
+    assert shape[0] == 6, shape
+    if wl.batch > 1:
+        assert shape[1] > 0, shape       # rotated
+    errs = band_errors(out.psi[rows], ref.psi, out.records[rows], ref.records)
+    assert max(errs) <= TOL_FP32, errs
+    final = band_errors(out.psi[rows], ref.psi)
+    assert max(final) <= TOL_FP32, final
+    assert np.allclose(out.powers[rows], ref.powers, rtol=1e-4, atol=1e-9 * ref.powers.max())
+    for other in ("first_order", "verlet"):
+        alt = run_ref(wl, rows=rows, method=other)
+        diff = max(band_errors(alt.psi, ref.psi))
+        assert diff > 1e-6 and diff > max(errs), (other, diff, errs)
+
+
+@pytest.mark.parametrize("nx", [8192, 16384])
+@pytest.mark.parametrize("seed", [11, 2])
+def test_verlet_split_band_matches_oracle(bpm_lib, nx, seed):
+    """N = 8192 and 16384 (bands split over 2 and 4 CTAs per band) with the
+    second-order step: the couplings of step n's second half and step
+    n + 1's first half after the psi_p swap, step n + 1's slice staged in
+    the peer spectrum buffer.  A bent symmetric Bragg request (seed 11) and
+    a dislocated asymmetric one (seed 2) against the oracle's Verlet march:
+    fields, records and powers, and a resumed march equal to the whole."""
+    wl = inputs.serving_request(np.random.default_rng(seed), nx, 600)
+    wl.record_every = 150
+    ref = run_ref(wl, method="verlet")
+    with binding.Plan(wl, FP32, splitting=binding.BPM_SPLIT_VERLET) as plan:
+        out = plan.propagate()
+        assert binding.bpm_launch_shape(plan.handle)[0] == 5
+        first = plan.propagate(n_begin=0, n_end=250)
+        rest = plan.propagate(psi_in=first.psi, n_begin=250, n_end=wl.nz)
+    errs = band_errors(out.psi, ref.psi, out.records, ref.records)
+    assert max(errs) <= TOL_FP32, errs
+    assert np.allclose(out.powers, ref.powers, rtol=1e-4, atol=1e-9 * ref.powers.max())
+    assert max(band_errors(rest.psi, ref.psi)) <= TOL_FP32
+    fo = run_ref(wl)
+    diff = max(band_errors(fo.psi, ref.psi))
+    assert diff > 1e-6 and diff > max(errs), (diff, errs)
