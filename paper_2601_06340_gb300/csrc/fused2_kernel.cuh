@@ -27,8 +27,9 @@
 
 namespace bpm {
 
-// PHB: strain-slice buffers per row (2 when the step couples twice, see
-// the kernel's HALF form)
+// PHB: strain-slice buffers per row (2 when the step couples before it
+// propagates: the second- and fourth-order forms fetch the next step's
+// slice a step ahead)
 template <int LOGN, int PHB = 1>
 struct F2Cfg {
   static constexpr int N = 1 << LOGN;
