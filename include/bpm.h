@@ -153,7 +153,11 @@ int bpm_set_strain(bpm_plan_t plan, int32_t kind, const double* ux_um,
  * while every solve gets two SMs and 512 <= nx != 2048, else one CTA per
  * solve) and Forest-Ruth (one CTA per solve: the leading coupling, then
  * three propagate-and-couple stages with the propagator increments of t dz
- * and (1 - 2t) dz, tabulated here once); 3D plans take the first-order step
+ * and (1 - 2t) dz, tabulated here once), and for nx = 8192, 16384 Verlet
+ * (one split-band cluster per solve) and Forest-Ruth stage by stage (per
+ * step a coupling launch and three one-step launches of the first-order
+ * split-band kernel with the stage's tables; several times slower, and
+ * refused under stream capture); 3D plans take the first-order step
  * and Verlet (the row kernel, which holds both bands of a line, applies the
  * half-step couplings); other combinations return BPM_ERR_INVALID.
  * bpm_submit takes FP32 plans set to Verlet (one CTA per row as well), not
@@ -313,9 +317,10 @@ int bpm_march_f64_noalloc(void* d_psi, int32_t nx, int32_t n_rows, const void* d
                           int32_t n_end, void* stream);
 
 /* Launch shape of the plan's last FP32 march (the fused kernels of the
- * step of Eq. fov10): *layout = 6 one CTA per row with the Forest-Ruth step
- * (plans set to BPM_SPLIT_FOREST_RUTH), 5 one 4-CTA half-band split per row with
- * the Verlet step (nx = 4096), 4 one 2-CTA cluster per row with the Verlet
+ * step of Eq. fov10): *layout = 7 the Forest-Ruth step stage by stage
+ * (nx >= 8192), 6 one CTA per row with the Forest-Ruth step (plans set to
+ * BPM_SPLIT_FOREST_RUTH), 5 one split-band cluster per row with
+ * the Verlet step (nx = 4096, 8192, 16384), 4 one 2-CTA cluster per row with the Verlet
  * step, 3 one CTA per row with the Verlet step (plans set to
  * BPM_SPLIT_VERLET), 2 one 4-CTA cluster per row (nx = 4096 as
  * two half-band parts per band; the rule while every row gets four SMs),

@@ -218,6 +218,9 @@ int fused_smem_bytes(int logn);
 int fused_rows_resident(int logn, int n_rows);
 // Tables of the split-band form with local length 2^logm (N = 2^logm P).
 void split_prop_table(const bpm_plan_s* plan, int row, int logm, std::vector<float2>* out);
+// the same tables for a propagation of frac * dz (a stage of Eq. split-op)
+void split_prop_table_frac(const bpm_plan_s* plan, int row, int logm, double frac,
+                           std::vector<float2>* out);
 int split_table_stride(const bpm_plan_s* plan, int logm);   // float2 per row
 // Layout codes of launch_fused_layout: -1 rule, 0 CTA per row, 1 2-CTA
 // cluster per row, 2 4-CTA cluster per row (N = 4096, half-band split).
@@ -230,6 +233,13 @@ constexpr int kLayoutClusterHalf = 4;
 constexpr int kLayoutSplit4Half = 5;
 // one CTA per row, fourth-order (Forest-Ruth) step, N <= 4096
 constexpr int kLayoutCtaFR = 6;
+// the fourth-order step stage by stage (N = 8192, 16384): a coupling launch
+// and three one-step launches of the split-band kernels per step
+constexpr int kLayoutStagedFR = 7;
+// Coupling alone (the leading coupling of a step), on rows[0..nb): each row's
+// state [2][nx], the slice of step n of its stream (stored per part for
+// nx >= 8192), coefficients (am1h, bh).
+int launch_couple_only(const RowDescF32* d_rows, int nb, int nx, int n, cudaStream_t st);
 int fused_launch_capacity(int logn, bool cluster);
 int fused_split4_capacity();
 int fused_half_capacity(int logn);   // logn <= 12

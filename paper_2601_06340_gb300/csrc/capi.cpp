@@ -81,6 +81,12 @@ int device_sm_count() {
 
 inline PlanAux* aux_of(bpm_plan_s* plan) { return &plan->aux; }
 
+// float2 per Forest-Ruth stage table of one row: (P^a - 1)/N per band in the
+// fused FFT's output order, or the split-band tables for nx >= 8192
+size_t fr_table_stride(const bpm_plan_s* plan) {
+  return plan->logn >= kSplitLogN ? size_t(split_table_stride(plan, 12)) : 2 * size_t(plan->nx);
+}
+
 // Build the fused row descriptors for rows [0, B) of `plan`.
 void fused_rows(bpm_plan_s* plan, float2* state, float2* rec, double* pw, int n_begin,
                 int n_end, std::vector<RowDescF32>* out) {
@@ -90,8 +96,8 @@ void fused_rows(bpm_plan_s* plan, float2* state, float2* rec, double* pw, int n_
     RowDescF32& d = (*out)[r];
     d.state = state + size_t(r) * 2 * n;
     d.prop = static_cast<const float2*>(plan->d_prop) + size_t(r) * prop_stride(plan);
-    if (plan->split == BPM_SPLIT_FOREST_RUTH)   // [2 tables][2][N] per row
-      d.prop = static_cast<const float2*>(plan->d_stage_prop) + size_t(r) * 4 * n;
+    if (plan->split == BPM_SPLIT_FOREST_RUTH)   // [2 tables][table] per row: t dz, (1-2t) dz
+      d.prop = static_cast<const float2*>(plan->d_stage_prop) + size_t(r) * 2 * fr_table_stride(plan);
     d.prop_split = plan->d_prop_split ? static_cast<const float2*>(plan->d_prop_split) +
                                             size_t(r) * split_table_stride(plan, 11)
                                       : nullptr;
@@ -401,6 +407,71 @@ static LaunchShape choose_shape(bpm_plan_s* plan, PlanAux* aux, const void* stat
   return best;
 }
 
+// Forest-Ruth at nx >= 8192, stage by stage: per step a coupling launch (t/2
+// on the step's slice) and three one-step launches of the first-order
+// split-band kernel, with the propagator tables of t dz, (1 - 2t) dz, t dz and
+// the couplings (1 - t)/2, (1 - t)/2, t/2, all on the step's slice; records
+// and powers in the third.  The row descriptors of every (step, stage) are
+// built once and uploaded as one schedule.
+static int march_staged_fr(bpm_plan_s* plan, PlanAux* aux, void* state, void* d_rec,
+                           double* d_pw, int n_begin, int n_end, bool captured, cudaStream_t st) {
+  if (captured)
+    return fail(BPM_ERR_INVALID,
+                "Forest-Ruth plans with nx >= 8192 march stage by stage; not under capture");
+  const int nb = plan->nb, steps = n_end - n_begin;
+  std::vector<RowDescF32> rows;
+  fused_rows(plan, static_cast<float2*>(state), static_cast<float2*>(d_rec), d_pw, n_begin,
+             n_end, &rows);
+  const size_t ts = fr_table_stride(plan);
+  // the schedule of up to `chunk` steps at a time (stream order keeps a
+  // chunk's launches ahead of the next upload into the same buffer)
+  const int chunk = std::min(steps, 1024);
+  const size_t cap = size_t(chunk) * 3 * nb;
+  if (aux->sched_cap < cap) {
+    if (aux->d_sched) cudaFree(aux->d_sched);
+    aux->d_sched = nullptr;
+    aux->sched_cap = 0;
+    int rc = dev_alloc(plan, reinterpret_cast<void**>(&aux->d_sched), cap * sizeof(RowDescF32),
+                       "launch schedule");
+    if (rc != BPM_OK) return rc;
+    aux->sched_cap = cap;
+  }
+  plan->shape_layout = kLayoutStagedFR;
+  plan->shape_chunk = 0;
+  const float4* tw = static_cast<const float4*>(plan->d_tw);
+  std::vector<RowDescF32> sched(cap);
+  int rc = BPM_OK;
+  for (int i0 = 0; i0 < steps && rc == BPM_OK; i0 += chunk) {
+    const int len = std::min(chunk, steps - i0);
+    for (int k = 0; k < len; ++k)
+      for (int sg = 0; sg < 3; ++sg)
+        for (int r = 0; r < nb; ++r) {
+          RowDescF32 d = rows[r];
+          d.n_begin = n_begin + i0 + k;
+          d.n_end = d.n_begin + 1;
+          d.n_phase0 = n_begin;
+          if (sg == 1) d.prop = rows[r].prop + ts;       // (1 - 2t) dz
+          if (sg == 2) {                                  // the outer coupling t/2
+            d.am1 = rows[r].am1h;
+            d.b = rows[r].bh;
+          } else {
+            d.record_every = 0;                           // records after the last stage
+          }
+          sched[(size_t(k) * 3 + sg) * nb + r] = d;
+        }
+    rc = upload(aux->d_sched, sched.data(), size_t(len) * 3 * nb * sizeof(RowDescF32), st, false,
+                "upload launch schedule");
+    for (int k = 0; k < len && rc == BPM_OK; ++k) {
+      const RowDescF32* base = aux->d_sched + size_t(k) * 3 * nb;
+      rc = launch_couple_only(base, nb, plan->nx, n_begin + i0 + k, st);
+      for (int sg = 0; sg < 3 && rc == BPM_OK; ++sg)
+        rc = launch_fused_layout(plan->logn, base + size_t(sg) * nb, nb, 1, tw, plan->d_status,
+                                 st, -1);
+    }
+  }
+  return rc;
+}
+
 // Enqueue the march of all rows on `st`.  state: the buffer holding the
 // state at n_begin (c64 for FP32, the plan's d_state for FP64); outputs as
 // documented for bpm_propagate_device.
@@ -425,6 +496,16 @@ static int enqueue_march(bpm_plan_s* plan, PlanAux* aux, void* state, void* d_re
                              reinterpret_cast<const double*>(aux->d_g), plan->nb,
                              int(plane_of(plan)), steps, plan->dx_um * plan->dy_um, final_pw,
                              pw_stride, st);
+  }
+  if (plan->precision == BPM_FP32_FUSED && plan->split == BPM_SPLIT_FOREST_RUTH &&
+      plan->logn >= kSplitLogN) {
+    int rc = march_staged_fr(plan, aux, state, d_rec, d_pw, n_begin, n_end, captured, st);
+    if (rc != BPM_OK) return rc;
+    return launch_finish_f32(static_cast<const float2*>(state),
+                             out_c128 ? static_cast<double2*>(out) : nullptr,
+                             out_c128 ? nullptr : static_cast<float2*>(out),
+                             reinterpret_cast<const double*>(aux->d_g), plan->nb, plan->nx, steps,
+                             plan->dx_um, final_pw, pw_stride, st);
   }
   if (plan->precision == BPM_FP32_FUSED) {
     std::vector<RowDescF32> rows;
@@ -661,9 +742,6 @@ int bpm_set_splitting(bpm_plan_t plan, int32_t method) {
     return fail(BPM_ERR_INVALID, "unknown splitting method");
   if (method == BPM_SPLIT_FOREST_RUTH && plan->ny > 1)
     return fail(BPM_ERR_INVALID, "3D plans march first order or Verlet");
-  if (plan->precision == BPM_FP32_FUSED && method == BPM_SPLIT_FOREST_RUTH && plan->logn > 12)
-    return fail(BPM_ERR_INVALID,
-                "BPM_FP32_FUSED plans march Forest-Ruth for nx <= 4096 (Verlet at every nx)");
   for (void** p : {&plan->d_stage_rows, &plan->d_stage_prop}) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -678,15 +756,19 @@ int bpm_set_splitting(bpm_plan_t plan, int32_t method) {
     // descriptors, built at each march; Forest-Ruth also needs the
     // propagator increments of its t dz and (1 - 2t) dz stages
     if (method == BPM_SPLIT_FOREST_RUTH) {
-      int rc = dev_alloc(plan, &plan->d_stage_prop, nb * 4 * n * sizeof(float2),
+      const size_t ts = fr_table_stride(plan);
+      int rc = dev_alloc(plan, &plan->d_stage_prop, nb * 2 * ts * sizeof(float2),
                          "splitting propagators");
       if (rc != BPM_OK) return rc;
-      std::vector<float2> host(nb * 4 * n);
+      std::vector<float2> host(nb * 2 * ts);
       for (size_t r = 0; r < nb; ++r)
         for (int k = 0; k < 2; ++k) {
           std::vector<float2> tab;
-          fused_prop_table_frac(plan, int(r), stages[1 + k].first, &tab);
-          std::copy(tab.begin(), tab.end(), host.begin() + long((r * 2 + k) * 2 * n));
+          if (plan->logn >= kSplitLogN)
+            split_prop_table_frac(plan, int(r), 12, stages[1 + k].first, &tab);
+          else
+            fused_prop_table_frac(plan, int(r), stages[1 + k].first, &tab);
+          std::copy(tab.begin(), tab.end(), host.begin() + long((r * 2 + k) * ts));
         }
       cudaStream_t st = aux_of(plan)->stream;
       cudaError_t e = cudaMemcpyAsync(plan->d_stage_prop, host.data(),

@@ -204,6 +204,11 @@ std::vector<int> fft_output_order(int logn) {
 //          their own size, and that error repeats every step; hi + lo keeps
 //          it at FP64 level.
 void split_prop_table(const bpm_plan_s* plan, int row, int logm, std::vector<float2>* out) {
+  split_prop_table_frac(plan, row, logm, 1.0, out);
+}
+
+void split_prop_table_frac(const bpm_plan_s* plan, int row, int logm, double frac,
+                           std::vector<float2>* out) {
   const EnergyConsts& c = plan->ec[row];
   const int n = plan->nx, m = 1 << logm, parts = n / m;
   std::vector<int> local = fft_output_order(logm);
@@ -219,7 +224,7 @@ void split_prop_table(const bpm_plan_s* plan, int row, int logm, std::vector<flo
     for (int pos = 0; pos < m; ++pos) {
       for (int r = 0; r < parts; ++r) {
         double q = fftfreq_q(local[pos] + m * r, n, c.dxh);
-        dk[r] = expm1_i(cd(c.dzh * delta_q(q, c.s, c.c, sign), 0.0)) * (1.0 / double(n));
+        dk[r] = expm1_i(cd(frac * c.dzh * delta_q(q, c.s, c.c, sign), 0.0)) * (1.0 / double(n));
       }
       if (parts == 2) {
         for (int r = 0; r < 2; ++r)

@@ -91,7 +91,57 @@ __global__ void omega_to_t_kernel(const C* __restrict__ in, C* __restrict__ out,
   }
 }
 
+// The coupling of Eq. fov10 alone, for a step of the coefficients (am1h,
+// bh) of each row: psi_+ <- psi_+ + (a-1) psi_+ + b e psi_-, psi_- <- psi_- +
+// (a-1) psi_- + b conj(e) psi_+ (old values on the right) inside the crystal
+// (e != 0), e the slice of step n.  One thread per cell; split plans
+// (nx >= 8192) store the slice per part: column x = P m + h at h (nx/P) + m.
+__global__ void couple_only_kernel(const RowDescF32* __restrict__ rows, int nb, int nx, int n,
+                                   int log_parts) {
+  const int row = blockIdx.y;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nb || x >= nx) return;
+  const RowDescF32 d = rows[row];
+  const int m_len = nx >> log_parts;
+  const int h = x & ((1 << log_parts) - 1), m = x >> log_parts;
+  const float2 e = d.phasor[size_t(n) * nx + size_t(h) * m_len + m];
+  if (e.x == 0.f && e.y == 0.f) return;
+  const float2 p = d.state[x], q = d.state[nx + x];
+  const float2 am1 = d.am1h, bb = d.bh;
+  const float cx = fmaf(bb.x, e.x, -(bb.y * e.y)), cy = fmaf(bb.x, e.y, bb.y * e.x);   // b e
+  const float dx = fmaf(bb.x, e.x, bb.y * e.y), dy = fmaf(bb.y, e.x, -(bb.x * e.y));   // b conj(e)
+  float rx = fmaf(am1.x, p.x, p.x);
+  rx = fmaf(-am1.y, p.y, rx);
+  rx = fmaf(cx, q.x, rx);
+  rx = fmaf(-cy, q.y, rx);
+  float ry = fmaf(am1.x, p.y, p.y);
+  ry = fmaf(am1.y, p.x, ry);
+  ry = fmaf(cx, q.y, ry);
+  ry = fmaf(cy, q.x, ry);
+  float sx = fmaf(am1.x, q.x, q.x);
+  sx = fmaf(-am1.y, q.y, sx);
+  sx = fmaf(dx, p.x, sx);
+  sx = fmaf(-dy, p.y, sx);
+  float sy = fmaf(am1.x, q.y, q.y);
+  sy = fmaf(am1.y, q.x, sy);
+  sy = fmaf(dx, p.y, sy);
+  sy = fmaf(dy, p.x, sy);
+  d.state[x] = make_float2(rx, ry);
+  d.state[nx + x] = make_float2(sx, sy);
+}
+
 }  // namespace
+
+int launch_couple_only(const RowDescF32* d_rows, int nb, int nx, int n, cudaStream_t st) {
+  int log_parts = 0;
+  while ((4096 << log_parts) < nx) ++log_parts;   // parts of 4096 columns (nx >= 8192)
+  if (nx < 8192) log_parts = 0;
+  const int threads = 256;
+  dim3 grid((nx + threads - 1) / threads, nb);
+  couple_only_kernel<<<grid, threads, 0, st>>>(d_rows, nb, nx, n, log_parts);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? BPM_OK : cuda_fail(e, "coupling launch");
+}
 
 int launch_convert_in(const double2* src, float2* dst, size_t n, cudaStream_t st) {
   const int threads = 256;
