@@ -44,12 +44,16 @@ WORKLOAD = ("bragg_bent: 2D symmetric Bragg, bent crystal R=1 m nu=0.28, 8 keV, 
 FLOPS_PER_CELL = lambda n: 4 * 5 * math.log2(n)      # 4 FFTs x 5 N log2 N / N
 # the single-solve march kernel by launch layout (bpm_launch_shape): name, SMs
 MARCH_KERNELS = {
-    2: ("fused4e_march_kernel<11> (4-CTA cluster per solve: two half-band parts per band)", 4),
+    2: ("fused4s_march_kernel (4-CTA cluster per solve: two half-band parts per band, "
+        "8 points per thread)", 4),
+    8: ("fused4e_march_kernel<11> (4-CTA cluster per solve: two half-band parts per band, "
+        "16 points per thread)", 4),
     1: ("fused3_march_kernel<12> (2-CTA cluster per solve, one band per CTA)", 2),
     -1: ("fused3_march_kernel<12> (2-CTA cluster per solve, one band per CTA)", 2),
 }
 
 KERNEL_SOURCES = ["paper_2601_06340_gb300/csrc/radix.cuh",
+                  "paper_2601_06340_gb300/csrc/fused4s_kernel.cuh",
                   "paper_2601_06340_gb300/csrc/fused_kernel.cuh",
                   "paper_2601_06340_gb300/csrc/fused2_kernel.cuh",
                   "paper_2601_06340_gb300/csrc/fused3_kernel.cuh",

@@ -338,6 +338,10 @@ static LaunchShape choose_shape(bpm_plan_s* plan, PlanAux* aux, const void* stat
     rule.layout = kLayoutSplit4;
     rule.rotated = false;
     if (fv && std::strcmp(fv, "split") == 0) return rule;
+    if (fv && std::strcmp(fv, "split16") == 0) {
+      rule.layout = kLayoutSplit4S;
+      return rule;
+    }
   }
   if (logn >= kSplitLogN || nb < 2 || !autotune_enabled()) return rule;
   int sms = 1, dev = 0;

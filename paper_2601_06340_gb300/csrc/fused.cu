@@ -39,7 +39,8 @@ BPM_DECLARE_FUSED2(9) BPM_DECLARE_FUSED2(10) BPM_DECLARE_FUSED2(11)
 BPM_DECLARE_FUSED2(12)
 int fused4_launch_13(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
 int fused4h_launch_12(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
-int fused4h_rows_resident_12();
+int fused4s_launch_12(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
+int fused4s_rows_resident_12();
 int fused4hh_launch_12(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
 int fused4hh_rows_resident_12();
 int fused4_launch_14(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
@@ -92,7 +93,11 @@ int launch_fused_layout(int logn, const RowDescF32* d_rows, int n_rows, int step
                         const float4* d_tw, int* d_status, cudaStream_t st, int layout) {
   if (n_rows <= 0 || steps <= 0) return BPM_OK;
   // (only for rows that carry the split tables: the caller checks)
+  // the half-band split: 8 points per thread (the rule), or the 16-point
+  // form of fused4e_march_kernel<11> when forced
   if (logn == 12 && layout == kLayoutSplit4)
+    return fused4s_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
+  if (logn == 12 && layout == kLayoutSplit4S)
     return fused4h_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
   if (layout == kLayoutSplit4Half) {
     switch (logn) {
@@ -369,7 +374,7 @@ int fused_split4_capacity() {
   static std::atomic<int> cached{0};
   int c = cached.load(std::memory_order_relaxed);
   if (c == 0) {
-    c = fused4h_rows_resident_12();
+    c = fused4s_rows_resident_12();
     cached.store(c, std::memory_order_relaxed);
   }
   return c;

@@ -1,0 +1,377 @@
+// N = 4096 as a half-band split (as in fused4_kernel.cuh, P = 2, M = 2048)
+// with 8 points per thread: 256 threads per CTA, two warps per scheduler.
+//
+// The 4-CTA cluster layout is the one of fused4e_march_kernel<11>: CTA rank
+// c = 2 band + h holds the samples x[2 m + h] of band b; one exchange of the
+// local spectrum F with the other half of the band per step, then
+//   X_r = F_0 + (-1)^r W_N^k F_1,   Y_r = D(k + M r) X_r,
+//   H_0 = Y_0 + Y_1,                H_1 = W_N^{-k} (Y_0 - Y_1),
+// and one swap of psi_p with the CTA of the other band.  The local
+// 2048-point transform runs as radix 8, 8, 8, 4 passes (decimation in
+// frequency, digit-reversed output; the inverse mirrors it), so each thread
+// does half the serial work of the 16-point form and each scheduler has two
+// warps to issue from, at the price of one more shared-memory pass per
+// transform.  The propagator increments D(k), D(k + M) come from the plan's
+// half-band tables, which are stored in the 16-point form's output order:
+// each thread looks its frequencies up once per launch.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "fused4_kernel.cuh"
+
+namespace bpm {
+
+// Pass structure of a 2^LM-point transform with 8 points per thread.
+template <int LM>
+struct F8Cfg {
+  static constexpr int N = 1 << LM;
+  static constexpr int E = 8;
+  static constexpr int T = N / E;
+  static constexpr int NP = (LM + 2) / 3;
+  static constexpr int RL = 1 << (LM - 3 * (NP - 1));
+  __host__ __device__ static constexpr int radix(int p) { return p < NP - 1 ? 8 : RL; }
+  __host__ __device__ static constexpr int len(int p) { return N >> (3 * p); }
+  __host__ __device__ static constexpr int stride(int p) { return len(p) / radix(p); }
+  __host__ __device__ static constexpr int groups(int p) { return E / radix(p); }
+};
+
+template <int LM, int P>
+__device__ __forceinline__ int f8_pos(int gi, int j) {
+  using C = F8Cfg<LM>;
+  constexpr int S = C::stride(P), L = C::len(P);
+  return (gi / S) * L + (gi % S) + j * S;
+}
+
+// Shared-memory address of transform position p: within each row of 16
+// float2 (eight 16-byte bank pairs twice), the position is XOR-ed with
+// 4 ((p >> 5) & 3) + ((p >> 4) & 3).  With it the half-warps of all four
+// pass patterns (stride 256 and 32: consecutive; stride 4: 32 a + b + 4 j;
+// stride 1: 4 l + j) touch 16 distinct bank pairs; a pad of one slot per 16
+// left the stride-4 pass 2-way conflicted.
+__device__ __forceinline__ int swz8(int p) { return p ^ (((p >> 3) & 12) | ((p >> 4) & 3)); }
+
+template <int LM, int P>
+__device__ __forceinline__ void f8_store(float2* buf, const float2* v, int t) {
+  using C = F8Cfg<LM>;
+  constexpr int R = C::radix(P), G = C::groups(P);
+#pragma unroll
+  for (int i = 0; i < G; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) buf[swz8(f8_pos<LM, P>(t + i * C::T, j))] = v[i * R + j];
+}
+
+template <int LM, int P>
+__device__ __forceinline__ void f8_load(const float2* buf, float2* v, int t) {
+  using C = F8Cfg<LM>;
+  constexpr int R = C::radix(P), G = C::groups(P);
+#pragma unroll
+  for (int i = 0; i < G; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) v[i * R + j] = buf[swz8(f8_pos<LM, P>(t + i * C::T, j))];
+}
+
+template <int LM, int P, bool INV, bool EX>
+__device__ __forceinline__ void f8_dft(float2* v) {
+  using C = F8Cfg<LM>;
+  constexpr int R = C::radix(P), G = C::groups(P);
+#pragma unroll
+  for (int i = 0; i < G; ++i) dft<R, INV, EX>(v + i * R);
+}
+
+// radix-8 twiddle pass with register twiddles w[j-1] = W^{o j}
+template <bool INV>
+__device__ __forceinline__ void f8_twiddle(float2* v, const float2* w) {
+#pragma unroll
+  for (int j = 1; j < 8; ++j) {
+    const float2 t = w[j - 1];
+    v[j] = INV ? cmul_f(v[j], t.x, -t.y) : cmul_f(v[j], t.x, t.y);
+  }
+}
+
+// Spectral index of position `pos` of the forward transform's output.
+template <typename Cfg>
+__device__ __forceinline__ int cfg_freq(int pos) {
+  int rem = pos, len = Cfg::N, freq = 0, mult = 1;
+#pragma unroll
+  for (int p = 0; p < Cfg::NP; ++p) {
+    const int r = Cfg::radix(p), stride = len / r;
+    freq += (rem / stride) * mult;
+    rem %= stride;
+    mult *= r;
+    len = stride;
+  }
+  return freq;
+}
+
+// Position of frequency k in the 16-point form's output order (radices 16,
+// 16, 8 for 2048 points): the inverse of local_freq<11>.
+__device__ __forceinline__ int pos16_of_freq2048(int k) {
+  return (k & 15) * 128 + ((k >> 4) & 15) * 8 + (k >> 8);
+}
+
+struct F4SCfg {
+  static constexpr int M = 2048;
+  static constexpr int N = 2 * M;
+  static constexpr int T = M / 8;
+  static constexpr int PADM = M + (M >> 4);
+  static constexpr int WARPS = T / 32;
+  static constexpr int OFF_BUF = 0;                        // [PADM]
+  static constexpr int OFF_G = OFF_BUF + PADM * 8;         // [2][M] peer's F
+  static constexpr int OFF_C = OFF_G + 2 * M * 8;          // [2][M] other band's psi_p
+  static constexpr int OFF_PH = OFF_C + 2 * M * 8;         // [N] strain slice (natural order)
+  static constexpr int OFF_E1 = OFF_PH + N * 8;            // [8][T] D(k_j + M)
+  static constexpr int OFF_MBAR = OFF_E1 + M * 8;          // strain-slice barrier
+  static constexpr int OFF_GBAR = OFF_MBAR + 8;            // [2] F barriers
+  static constexpr int OFF_CBAR = OFF_GBAR + 16;           // [2] psi_p barriers
+  static constexpr int OFF_PPEER = OFF_CBAR + 16;          // [2] peer's band-power part
+  static constexpr int OFF_RECPH = OFF_PPEER + 16;
+  static constexpr int OFF_RED = OFF_RECPH + 8;            // [WARPS] double
+  static constexpr int OFF_PART = OFF_RED + WARPS * 8;
+  static constexpr int SMEM = OFF_PART + 8;
+  static_assert(SMEM <= 232448, "fits one SM");
+  static_assert(OFF_G % 16 == 0 && OFF_C % 16 == 0 && OFF_PH % 16 == 0,
+                "16-byte stores and bulk copy");
+  static_assert(OFF_MBAR % 8 == 0 && OFF_GBAR % 8 == 0 && OFF_CBAR % 8 == 0 &&
+                    OFF_PPEER % 8 == 0,
+                "mbarrier and 8-byte store alignment");
+};
+
+template <bool EX>
+__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg::T, 1)
+    fused4s_march_kernel(const RowDescF32* __restrict__ rows, int n_rows, int steps,
+                         const float4* __restrict__ tw, int* __restrict__ status) {
+  namespace cg = cooperative_groups;
+  using C = F4SCfg;
+  using F = F8Cfg<11>;
+  constexpr int L = 11, M = C::M, N = C::N, T = C::T, NP = F::NP, RL = F::RL;
+  static_assert(NP == 4 && RL == 4, "2048 = 8 x 8 x 8 x 4");
+  extern __shared__ __align__(128) unsigned char smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+
+  const int c = int(cluster.block_rank());
+  const int band = c >> 1, h = c & 1;
+  const int row = blockIdx.x >> 2;
+  const int t = threadIdx.x;
+  const int lane = t & 31, warp = t >> 5;
+  const RowDescF32 d = rows[row < n_rows ? row : 0];
+  const bool lead = t == 0;
+
+  float2* buf = reinterpret_cast<float2*>(smem + C::OFF_BUF);
+  float2* gx = reinterpret_cast<float2*>(smem + C::OFF_G);
+  float2* cb = reinterpret_cast<float2*>(smem + C::OFF_C);
+  float2* ph = reinterpret_cast<float2*>(smem + C::OFF_PH);
+  float2* e1s = reinterpret_cast<float2*>(smem + C::OFF_E1);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::OFF_MBAR);
+  uint64_t* gbar = reinterpret_cast<uint64_t*>(smem + C::OFF_GBAR);
+  uint64_t* cbar = reinterpret_cast<uint64_t*>(smem + C::OFF_CBAR);
+  double* ppeer = reinterpret_cast<double*>(smem + C::OFF_PPEER);
+  float2* recph = reinterpret_cast<float2*>(smem + C::OFF_RECPH);
+  double* red = reinterpret_cast<double*>(smem + C::OFF_RED);
+  double* part = reinterpret_cast<double*>(smem + C::OFF_PART);
+  const uint32_t peer = uint32_t(c ^ 1);       // same band, other half of the samples
+  const uint32_t partner = uint32_t(c ^ 2);    // other band, same samples
+  const uint32_t g_peer = mapa_u32(smem_u32(gx), peer);
+  const uint32_t gbar_peer = mapa_u32(smem_u32(gbar), peer);
+  const uint32_t pp_peer = mapa_u32(smem_u32(ppeer), peer);
+  const uint32_t c_part = mapa_u32(smem_u32(cb), partner);
+  const uint32_t cbar_part = mapa_u32(smem_u32(cbar), partner);
+
+  if (lead) {
+    mbar_init(bar);
+    mbar_init(&gbar[0]);
+    mbar_init(&gbar[1]);
+    mbar_init(&cbar[0]);
+    mbar_init(&cbar[1]);
+  }
+  fence_mbar_init();
+
+  // twiddles of passes 0, 1, 2: W_{len(p)}^{o j}, o = t mod stride(p),
+  // from the W_N table (N = 2M): index 2 o j M / len(p)
+  float2 w0[7], w1[7], w2[7];
+#pragma unroll
+  for (int j = 1; j < 8; ++j) {
+    const float4 a = __ldg(&tw[2 * ((t % F::stride(0)) * j) * (M / F::len(0))]);
+    w0[j - 1] = make_float2(a.x, a.y);
+    const float4 b1 = __ldg(&tw[2 * ((t % F::stride(1)) * j) * (M / F::len(1))]);
+    w1[j - 1] = make_float2(b1.x, b1.y);
+    const float4 b2 = __ldg(&tw[2 * ((t % F::stride(2)) * j) * (M / F::len(2))]);
+    w2[j - 1] = make_float2(b2.x, b2.y);
+  }
+  // Last-pass slice: W_N^{k_j} and D(k_j) in registers, D(k_j + M) in shared
+  // memory; the plan's table [band][D(k) | D(k + M)][position] is in the
+  // 16-point form's output order.
+  float2 cw[8], d0[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int pos = f8_pos<L, NP - 1>(t + (j / RL) * T, j % RL);
+    const int k = cfg_freq<F>(pos);
+    const int p16 = pos16_of_freq2048(k);
+    const float4 a = __ldg(&tw[k]);
+    cw[j] = make_float2(a.x, a.y);
+    d0[j] = __ldg(&d.prop_split[(band * 2 + 0) * M + p16]);
+    e1s[j * T + t] = __ldg(&d.prop_split[(band * 2 + 1) * M + p16]);
+  }
+
+  float2 v[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = d.state[band * N + 2 * (t + j * T) + h];
+  cluster.sync();   // every CTA's barriers initialised before any remote store
+
+  const uint32_t slice_bytes = uint32_t(N) * 8u;
+  bool timed_out = false;
+  double my_part = 0.0;
+  const float2 am1 = d.am1, bb = d.b;
+  const bool pow_on = d.powers != nullptr && d.record_every > 0;
+
+  for (int it = 0; it < steps; ++it) {
+    const int n = d.n_begin + it;
+    const int half = it & 1;
+    const bool rec = d.record_every > 0 && ((n + 1) % d.record_every) == 0 &&
+                     (d.records != nullptr || d.powers != nullptr);
+    // the previous step was a record: its band-power part rides on this step's F
+    const bool part_due = pow_on && it > 0 && (n % d.record_every) == 0;
+    if (lead && rec) {
+      double ang = fmod(double(n + 1 - d.n_phase0) * d.gphase, 6.283185307179586);
+      double sa, ca;
+      sincos(ang, &sa, &ca);
+      *recph = make_float2(float(ca), float(sa));
+    }
+    float2 org[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) org[j] = v[j];
+    dft<8, false, EX>(v);
+    f8_twiddle<false>(v, w0);
+    f8_store<L, 0>(buf, v, t);
+    __syncthreads();
+    if (lead) {
+      bulk_load(ph, d.phasor + size_t(n) * N, slice_bytes, bar);
+      mbar_expect_tx(&gbar[half], uint32_t(M) * 8u + (part_due ? 8u : 0u));
+      if (part_due) {
+        double s = 0.0;
+        for (int w = 0; w < C::WARPS; ++w) s += red[w];
+        my_part = s;
+        st_async_f64(pp_peer + uint32_t(half) * 8u, s, gbar_peer + uint32_t(half) * 8u);
+      }
+    }
+    f8_load<L, 1>(buf, v, t);
+    dft<8, false, EX>(v);
+    f8_twiddle<false>(v, w1);
+    f8_store<L, 1>(buf, v, t);
+    __syncthreads();
+    f8_load<L, 2>(buf, v, t);
+    dft<8, false, EX>(v);
+    f8_twiddle<false>(v, w2);
+    f8_store<L, 2>(buf, v, t);
+    __syncthreads();
+    f8_load<L, NP - 1>(buf, v, t);
+    f8_dft<L, NP - 1, false, EX>(v);              // v[j] = F_h[k_j]
+    {
+      const uint32_t go = g_peer + uint32_t(half * M) * 8u;
+      const uint32_t gbo = gbar_peer + uint32_t(half) * 8u;
+#pragma unroll
+      for (int pp = 0; pp < 4; ++pp)
+        st_async_v4(go + uint32_t(xpair(pp, t, T)) * 8u, v[2 * pp], v[2 * pp + 1], gbo);
+    }
+    // (no barrier before the inverse pass rewrites buf: each thread's
+    // last-pass positions are its own in both directions)
+    if (!timed_out && !mbar_wait_cluster(&gbar[half], uint32_t((it >> 1) & 1))) timed_out = true;
+    if (lead && part_due && h == 0)
+      d.powers[2 * (n / d.record_every - 1) + band] = (my_part + ppeer[half]) * d.dx_um;
+    {
+      const float2* gi = gx + half * M;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float4 g2 = *reinterpret_cast<const float4*>(gi + xpair(j >> 1, t, T));
+        const float2 gp = (j & 1) ? make_float2(g2.z, g2.w) : make_float2(g2.x, g2.y);
+        const float2 f0 = h ? gp : v[j], f1 = h ? v[j] : gp;
+        const float2 w1k = cmul_f(f1, cw[j].x, cw[j].y);        // W^k F_1
+        const float2 x0 = cadd(f0, w1k), x1 = csub(f0, w1k);
+        const float2 a = d0[j], b = e1s[j * T + t];
+        const float2 y0 = make_float2(fmaf(a.x, x0.x, -(a.y * x0.y)), fmaf(a.x, x0.y, a.y * x0.x));
+        const float2 y1 = make_float2(fmaf(b.x, x1.x, -(b.y * x1.y)), fmaf(b.x, x1.y, b.y * x1.x));
+        v[j] = h ? cmul_f(csub(y0, y1), cw[j].x, -cw[j].y) : cadd(y0, y1);
+      }
+    }
+    f8_dft<L, NP - 1, true, EX>(v);
+    f8_store<L, NP - 1>(buf, v, t);
+    __syncthreads();
+    f8_load<L, 2>(buf, v, t);
+    f8_twiddle<true>(v, w2);
+    dft<8, true, EX>(v);
+    f8_store<L, 2>(buf, v, t);
+    __syncthreads();
+    f8_load<L, 1>(buf, v, t);
+    f8_twiddle<true>(v, w1);
+    dft<8, true, EX>(v);
+    f8_store<L, 1>(buf, v, t);
+    __syncthreads();
+    f8_load<L, 0>(buf, v, t);
+    f8_twiddle<true>(v, w0);
+    dft<8, true, EX>(v);
+    {
+      if (lead) mbar_expect_tx(&cbar[half], uint32_t(M) * 8u);
+      const uint32_t co = c_part + uint32_t(half * M) * 8u;
+      const uint32_t cbo = cbar_part + uint32_t(half) * 8u;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = cadd(org[j], v[j]);
+#pragma unroll
+      for (int pp = 0; pp < 4; ++pp)
+        st_async_v4(co + uint32_t(xpair(pp, t, T)) * 8u, v[2 * pp], v[2 * pp + 1], cbo);
+    }
+    if (!timed_out && !mbar_wait_cluster(&cbar[half], uint32_t((it >> 1) & 1))) timed_out = true;
+    if (!timed_out && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
+    {
+      const float2* ci = cb + half * M;
+#pragma unroll
+      for (int pp = 0; pp < 4; ++pp) {
+        const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
+        const int c0 = 2 * (t + 2 * pp * T) + h, c1 = 2 * (t + (2 * pp + 1) * T) + h;
+        v[2 * pp] = couple_cell(v[2 * pp], make_float2(q2.x, q2.y), ph[c0], band, am1, bb);
+        v[2 * pp + 1] = couple_cell(v[2 * pp + 1], make_float2(q2.z, q2.w), ph[c1], band, am1, bb);
+      }
+    }
+    if (rec) {
+      const int slot = (n + 1) / d.record_every - 1;
+      const float2 g = *recph;
+      double s = 0.0;
+      float2* r0 = d.records ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float2 p = v[j];
+        s = pow_acc(s, p);
+        if (r0)
+          r0[2 * (t + j * T) + h] =
+              make_float2(fmaf(p.x, g.x, -(p.y * g.y)), fmaf(p.x, g.y, p.y * g.x));
+      }
+      if (d.powers) {
+        double ds = s;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, off);
+        if (lane == 0) red[warp] = ds;   // summed by the lead after the next barrier
+      }
+    }
+  }
+
+  __syncthreads();
+  // the band power of a record in the launch's last step has no next step
+  // to ride on: exchange it through the cluster's shared memory
+  const bool last_due = pow_on && steps > 0 && ((d.n_begin + steps) % d.record_every) == 0;
+  if (lead && last_due) {
+    double s = 0.0;
+    for (int w = 0; w < C::WARPS; ++w) s += red[w];
+    *part = s;
+  }
+  cluster.sync();
+  if (lead && last_due && h == 0)
+    d.powers[2 * ((d.n_begin + steps) / d.record_every - 1) + band] =
+        (*part + *cluster.map_shared_rank(part, int(peer))) * d.dx_um;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) d.state[band * N + 2 * (t + j * T) + h] = v[j];
+  // Error path: as in fused4e_march_kernel (the lead still issues one slice
+  // copy per step, so it waits, bounded, for the last step's phase).
+  if (timed_out) give_up_after_march(bar, uint32_t((steps - 1) & 1), lead, status);
+  cluster.sync();   // peers may still read our shared memory
+}
+
+}  // namespace bpm

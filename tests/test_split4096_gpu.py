@@ -1,6 +1,6 @@
-"""N = 4096 solves in their three launch layouts: the half-band split on a
-4-CTA cluster (the rule while every row gets four SMs), the 2-CTA cluster
-and one CTA per row.  Each must match the oracle within the FP32 tolerance,
+"""N = 4096 solves in their launch layouts: the half-band split on a 4-CTA
+cluster with 8 points per thread (the rule while every row gets four SMs)
+or 16 (forced), the 2-CTA cluster and one CTA per row.  Each must match the oracle within the FP32 tolerance,
 on the final field alone (the stricter reading when a band has decayed) and
 on every record, over marches long enough for per-step errors to build up.
 """
@@ -34,7 +34,7 @@ def test_layouts_against_oracle(bpm_lib, monkeypatch, seed):
     wl.record_every = 700
     ref = run_ref(wl)
     outs = {}
-    for layout, want in ((None, 2), ("cluster", -1), ("cta", -1)):
+    for layout, want in ((None, 2), ("split16", 8), ("cluster", -1), ("cta", -1)):
         out, shape = _march(wl, monkeypatch, layout)
         assert shape[0] == want, (layout, shape)
         final = band_errors(out.psi, ref.psi)
@@ -79,3 +79,21 @@ def test_split_resume_and_small_batch(bpm_lib, monkeypatch):
     rows = [0, 7]
     ref = run_ref(wb, rows=rows)
     assert max(band_errors(out.psi[rows], ref.psi, out.records[rows], ref.records)) <= 2e-5
+
+
+def test_split16_bragg_bent_full_march(bpm_lib, monkeypatch):
+    """The 16-points-per-thread form of the half-band split (forced; the rule
+    takes the 8-point form) on the 8000-step bent Bragg solve: fields,
+    records and powers against the oracle, and a march resumed at step 3000
+    through the host API also within the bound."""
+    wl = inputs.bragg_bent()
+    ref = run_ref(wl)
+    out, shape = _march(wl, monkeypatch, "split16")
+    assert shape[0] == 8
+    assert max(band_errors(out.psi, ref.psi)) <= TOL_FP32
+    assert max(band_errors(out.psi, ref.psi, out.records, ref.records)) <= TOL_FP32
+    assert np.allclose(out.powers, ref.powers, rtol=1e-4, atol=1e-9 * ref.powers.max())
+    with binding.Plan(wl, FP32) as plan:
+        first = plan.propagate(n_end=3000)
+        rest = plan.propagate(first.psi, n_begin=3000)
+    assert max(band_errors(rest.psi, ref.psi)) <= TOL_FP32
