@@ -284,6 +284,26 @@ int bpm_ticket_times(bpm_ticket_t ticket, double* t_submit, double* t_admit,
  * the crystal).  Either pointer may be NULL.  For inspection and tests. */
 int bpm_fetch_slices(bpm_plan_t plan, uint8_t* mask, double* phasor);
 
+/* Form of the plan's prepared slices (the crystal mask Pi and the strain
+ * phasor of Eq. fov10 per step).  *form = 1: separable -- FP32 2D plans of a
+ * vacuum, bulk or slab crystal with no strain or the bent-crystal strain,
+ * whose phase h u = h x'^2/(2R) + h nu z'^2/(2R) is a column term plus a row
+ * term: the plan keeps one row per z-step (the inside interval and the row
+ * phasor, 96 bytes) and one phasor per column, and the fused kernels form
+ * each cell's phasor (column x row inside the interval, 0 outside) as they
+ * couple; 0: the per-cell stream (c64 per cell for FP32 plans, c128 for
+ * FP64 plans); -1: not prepared yet (slices are prepared at the first march
+ * after bpm_set_crystal / bpm_set_strain).  Eligible plans take the
+ * separable form while 2 x rows <= the GPU's SM count (rows that march
+ * latency-bound); larger batches keep the stream, which all their rows
+ * share.  BPM_SLICE_STREAM=1 (0) in the environment when the slices are
+ * prepared forces the stream (the separable) form of eligible plans.  The
+ * two forms hold the same cells bit for bit (bpm_fetch_slices); the kernels
+ * fold the row phasor into the coupling coefficient, so marches agree to
+ * FP32 rounding.  *bytes = the device bytes of the slice data.  Either
+ * pointer may be NULL.  BPM_ERR_INVALID for a NULL plan. */
+int bpm_slice_form(bpm_plan_t plan, int32_t* form, int64_t* bytes);
+
 /* Allocation-free FP64 march.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory -- code that
  * runs where cudaMalloc is not allowed or not wanted (a host callback, a

@@ -70,6 +70,7 @@ _SIGS = {
     "bpm_fetch_slices": ([_P, _P, _P], ctypes.c_int),
     "bpm_march_f64_noalloc": ([_P, _I, _I, _P, _P, _P, _I, _I, _P], ctypes.c_int),
     "bpm_launch_shape": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I)], ctypes.c_int),
+    "bpm_slice_form": ([_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "bpm_destroy": ([_P], ctypes.c_int),
     "bpm_last_error": ([], ctypes.c_char_p),
     "bpm_version": ([], ctypes.c_char_p),
@@ -230,6 +231,15 @@ def bpm_launch_shape(plan) -> tuple[int, int]:
     layout, chunk = _I(0), _I(0)
     _check(load().bpm_launch_shape(plan, ctypes.byref(layout), ctypes.byref(chunk)))
     return layout.value, chunk.value
+
+
+def bpm_slice_form(plan) -> tuple[int, int]:
+    """(form, bytes) of the plan's prepared slices: form 1 separable (one
+    row per z-step and one phasor per column; the kernels form each cell),
+    0 the per-cell stream, -1 not prepared yet; bytes of device memory."""
+    form, nbytes = _I(0), ctypes.c_int64(0)
+    _check(load().bpm_slice_form(plan, ctypes.byref(form), ctypes.byref(nbytes)))
+    return form.value, nbytes.value
 
 
 def bpm_selftest_wait_expiry() -> tuple[int, float]:

@@ -39,6 +39,25 @@ constexpr double kHcEvAngstrom = 12398.419843320026;
 // Device status word bits (per launch).
 enum : int { kStatusWaitTimeout = 1 };
 
+// Inside intervals of one z-step of an analytic crystal (slab, or slab cut
+// by a polygon with up to 16 vertices: at most 9 runs of inside columns).
+constexpr int kMaxIv = 9;
+
+// One z-step of the separable slice form.  For a bent or unstrained crystal
+// whose mask is a union of column intervals per step, the strain phasor of
+// cell (j, n) is col[j] * ph_n inside and (0, 0) outside (h u = h x'^2/(2R)
+// + h nu z'^2/(2R), each term reduced in FP64): the kernels form it from
+// this row and a per-column table instead of reading a per-cell stream.
+// The first 16 bytes hold everything a row with one interval needs.
+struct alignas(16) SepRow {
+  float2 ph;                // exp(i h nu z'^2/(2R)) (bent), (1, 0) unstrained
+  int lo0, hi0;             // first inside interval [lo0, hi0) (0, 0: none)
+  int nint;                 // number of intervals
+  int lo[kMaxIv], hi[kMaxIv];   // all intervals, natural column indices
+  float zp;                 // dislocation core offset z - z_core (slice preparation)
+};
+static_assert(sizeof(SepRow) == 96, "bulk-copied rows: a multiple of 16 bytes");
+
 // One batch row of a fused FP32 launch.  Everything the kernel needs for a
 // row is here, so rows of different plans (different energies, strain
 // streams, step ranges) can share one launch.
@@ -47,7 +66,10 @@ struct RowDescF32 {
   const float2* prop;       // [2][N] (P(q)-1)/N in the FFT's output order
   const float2* prop_split; // N = 4096 rows on a 4-CTA cluster: [2][3][N/2] circulant
                             // tables of the half-band split, else null
-  const float2* phasor;     // [nz][N] exp(i h u_x), (0,0) outside the crystal
+  const float2* phasor;     // [nz][N] exp(i h u_x), (0,0) outside the crystal; null in
+                            // the separable form
+  const SepRow* srows;      // separable form: [nz] rows, else null
+  const float2* scols;      // separable form: [N] column phasors in the stream's order
   float2* records;          // [n_rec][2][N] or null
   double* powers;           // [n_rec+1][2] or null
   float2 am1;               // Delta_eps_0 - 1 inside the crystal
@@ -118,6 +140,10 @@ struct bpm_plan_s {
   // device
   int device = 0;
   void* d_phasor = nullptr;       // [nz][nx] c64 (FP32) or c128 (FP64)
+  // separable slice form (FP32 plans, bent or unstrained analytic crystals):
+  // [nz] SepRow then [nx] float2 column phasors, in place of d_phasor
+  void* d_sep = nullptr;
+  bool sep_slices = false;        // the last prepared slices are separable
   void* d_prop = nullptr;         // [B][2][nx] c64 (delta form) or c128
   void* d_prop_split = nullptr;   // [B][2][3][nx/2] c64: N = 4096 half-band split tables
   void* d_tw = nullptr;           // FP32: float4 [nx] hi/lo; FP64: double2 [nx]
@@ -185,6 +211,18 @@ std::vector<int> fft_output_order(int logn);   // position -> frequency index
 // Prepare mask + strain phasor on `st`; with sync = false the call returns
 // once the work is enqueued (temporaries, if any, still force a wait).
 int prepare_slices(bpm_plan_s* plan, cudaStream_t st, bool sync = true);
+// Whether the plan's slices take the separable form (FP32 2D plans of a
+// vacuum, bulk or slab crystal with bent or no strain, while 2 x rows <= the
+// SM count; BPM_SLICE_STREAM=1 / 0 forces the stream / separable form), and
+// the device bytes of either form.
+bool sep_slices_apply(const bpm_plan_s* plan);
+size_t slice_data_bytes(const bpm_plan_s* plan);
+inline size_t sep_bytes(const bpm_plan_s* p) {
+  return size_t(p->nz) * sizeof(SepRow) + size_t(p->nx) * 8;
+}
+// Write the per-cell stream of separable slices (the values the stream
+// form would hold, bit for bit) to out [nz][nx] c64 in the stream's order.
+int expand_sep_slices(const bpm_plan_s* plan, float2* out, cudaStream_t st);
 int launch_fused(int logn, const RowDescF32* d_rows, int n_rows, int steps,
                  const float4* d_tw, int* d_status, cudaStream_t st);
 // layout: -1 automatic, 0 one CTA per row, 1 two-CTA cluster per row (only

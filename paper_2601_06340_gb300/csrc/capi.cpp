@@ -48,7 +48,7 @@ int dev_alloc(bpm_plan_s* plan, void** p, size_t bytes, const char* what) {
 
 void free_plan_memory(bpm_plan_s* plan) {
   vol_release(plan);
-  void** ptrs[] = {&plan->d_phasor, &plan->d_prop, &plan->d_prop_split, &plan->d_tw, &plan->d_state,
+  void** ptrs[] = {&plan->d_phasor, &plan->d_sep, &plan->d_prop, &plan->d_prop_split, &plan->d_tw, &plan->d_state,
                    &plan->d_state2, &plan->d_rows, &plan->d_io, &plan->d_spec,
                    &plan->d_twy, reinterpret_cast<void**>(&plan->d_pwpart),
                    &plan->d_stage_rows, &plan->d_stage_prop};
@@ -101,7 +101,15 @@ void fused_rows(bpm_plan_s* plan, float2* state, float2* rec, double* pw, int n_
     d.prop_split = plan->d_prop_split ? static_cast<const float2*>(plan->d_prop_split) +
                                             size_t(r) * split_table_stride(plan, 11)
                                       : nullptr;
-    d.phasor = static_cast<const float2*>(plan->d_phasor);
+    if (plan->sep_slices) {
+      d.phasor = nullptr;
+      d.srows = static_cast<const SepRow*>(plan->d_sep);
+      d.scols = reinterpret_cast<const float2*>(d.srows + plan->nz);
+    } else {
+      d.phasor = static_cast<const float2*>(plan->d_phasor);
+      d.srows = nullptr;
+      d.scols = nullptr;
+    }
     d.records = rec ? rec + size_t(r) * plan->n_rec * 2 * n : nullptr;
     d.powers = pw ? pw + size_t(r) * (plan->n_rec + 1) * 2 : nullptr;
     const EnergyConsts& c = plan->ec[r];
@@ -1087,7 +1095,27 @@ int bpm_fetch_slices(bpm_plan_t plan, uint8_t* mask, double* phasor) {
   std::vector<double> buf;
   if (plan->precision == BPM_FP32_FUSED) {
     std::vector<float> f(2 * cells);
-    cudaError_t e = cudaMemcpy(f.data(), plan->d_phasor, cells * 8, cudaMemcpyDeviceToHost);
+    const void* src = plan->d_phasor;
+    float2* d_tmp = nullptr;
+    if (plan->sep_slices) {   // the cells the kernels form from the separable tables
+      cudaError_t e = cudaMalloc(&d_tmp, cells * 8);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(e, "fetch slices");
+      }
+      rc = expand_sep_slices(plan, d_tmp, aux->stream);
+      if (rc == BPM_OK) {
+        e = cudaStreamSynchronize(aux->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "fetch slices");
+      }
+      if (rc != BPM_OK) {
+        cudaFree(d_tmp);
+        return rc;
+      }
+      src = d_tmp;
+    }
+    cudaError_t e = cudaMemcpy(f.data(), src, cells * 8, cudaMemcpyDeviceToHost);
+    if (d_tmp) cudaFree(d_tmp);
     if (e != cudaSuccess) return cuda_fail(e, "fetch slices");
     buf.assign(f.begin(), f.end());
   } else {
@@ -1110,6 +1138,20 @@ int bpm_fetch_slices(bpm_plan_t plan, uint8_t* mask, double* phasor) {
       phasor[2 * c] = buf[2 * src];
       phasor[2 * c + 1] = buf[2 * src + 1];
     }
+  }
+  return BPM_OK;
+}
+
+int bpm_slice_form(bpm_plan_t plan, int32_t* form, int64_t* bytes) {
+  if (!plan) return fail(BPM_ERR_INVALID, "plan is NULL");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  const bool ready = !plan->slices_dirty;
+  if (form) *form = !ready ? -1 : plan->sep_slices ? 1 : 0;
+  if (bytes) {
+    *bytes = !ready ? 0
+             : plan->sep_slices
+                 ? int64_t(sep_bytes(plan))
+                 : int64_t(plane_of(plan) * plan->nz * (plan->precision == BPM_FP32_FUSED ? 8 : 16));
   }
   return BPM_OK;
 }

@@ -49,8 +49,14 @@ struct F2Cfg {
   static constexpr int OFF_RED = OFF_RECPH + ROWS * 8;                // [ROWS][WPR][2] double
   static constexpr int S1 = NP >= 3 ? (N >> 8) : 1;                   // pass-1 group offsets
   static constexpr int OFF_TW1 = OFF_RED + ROWS * WPR * 2 * 8;        // [S1][16] float2
-  static constexpr int SMEM = OFF_TW1 + S1 * 16 * 8;
+  static constexpr int OFF_SROW = (OFF_TW1 + S1 * 16 * 8 + 15) / 16 * 16;   // [ROWS][PHB]
+  static constexpr int SMEM = OFF_SROW + ROWS * PHB * 16;
   static_assert(LOGN >= 8 && LOGN <= 12, "band-per-thread kernel covers 256..4096");
+  // Three passes (N = 512..4096): pass 1 and the last pass (groups as in
+  // f2_group) of the 16 threads of a band in a warp address positions
+  // [256 a, 256 a + 256) of that band's buffer only, so the barriers between
+  // them (either direction) are warp barriers
+  static constexpr bool TAIL_WARP = NP >= 3;
   // layout checks: fits one SM (227 KB); bulk-copy and 16-byte store
   // targets 16-byte aligned; mbarriers 8-byte aligned
   static_assert(SMEM <= 232448, "fits one SM");
@@ -69,24 +75,43 @@ __device__ __forceinline__ int f2_pos(int gi, int j) {
   return (gi / S) * L + (gi % S) + j * S;
 }
 
-template <int LOGN, int P>
+// Group i of thread t in pass P.  WL (warp-local tail): the last pass's
+// groups are taken as 16 G (t / 16) + 16 i + t mod 16 (G groups per thread)
+// instead of t + i T, so that the 16 threads t = 16 a .. 16 a + 15 address
+// positions [256 a, 256 a + 256) in the last pass as they do in pass 1
+// (stride N / 256 <= 16): between pass 1 and the last pass only those 16
+// threads exchange data, and a warp (one or two such groups) synchronizes
+// with itself alone.  Both directions and every table lookup of the last
+// pass must use the same choice.
+template <int LOGN, int P, bool WL = false>
+__device__ __forceinline__ int f2_group(int t, int i) {
+  using C = F2Cfg<LOGN>;
+  if constexpr (WL && P == C::NP - 1 && C::RL < 16)
+    return (t >> 4) * (16 * C::groups(P)) + i * 16 + (t & 15);
+  else
+    return t + i * C::T;
+}
+
+template <int LOGN, int P, bool WL = false>
 __device__ __forceinline__ void f2_store(float2* buf, const float2* v, int t) {
   using C = F2Cfg<LOGN>;
   constexpr int R = C::radix(P), G = C::groups(P);
 #pragma unroll
   for (int i = 0; i < G; ++i)
 #pragma unroll
-    for (int j = 0; j < R; ++j) buf[padi(f2_pos<LOGN, P>(t + i * C::T, j))] = v[i * R + j];
+    for (int j = 0; j < R; ++j)
+      buf[padi(f2_pos<LOGN, P>(f2_group<LOGN, P, WL>(t, i), j))] = v[i * R + j];
 }
 
-template <int LOGN, int P>
+template <int LOGN, int P, bool WL = false>
 __device__ __forceinline__ void f2_load(const float2* buf, float2* v, int t) {
   using C = F2Cfg<LOGN>;
   constexpr int R = C::radix(P), G = C::groups(P);
 #pragma unroll
   for (int i = 0; i < G; ++i)
 #pragma unroll
-    for (int j = 0; j < R; ++j) v[i * R + j] = buf[padi(f2_pos<LOGN, P>(t + i * C::T, j))];
+    for (int j = 0; j < R; ++j)
+      v[i * R + j] = buf[padi(f2_pos<LOGN, P>(f2_group<LOGN, P, WL>(t, i), j))];
 }
 
 template <int LOGN, int P, bool INV, bool EX, bool PACK = true>
@@ -119,15 +144,21 @@ __device__ __forceinline__ void f2_twiddle(float2* v, const float2* w) {
 
 // Coupling of this thread's 16 cells with the other band (lane ^ 16), the
 // coefficients (a - 1, b) of the step (or of its half), e = the cells' strain
-// phasors from the slice `ph`.
-template <int T>
-__device__ __forceinline__ void f2_couple(float2* v, const float2* ph, int t, int band,
-                                          float2 am1, float2 bb) {
+// phasors from the slice `ph` (separable slices: sr != null, ph the column
+// phasors and sr the step's row head).
+template <int T, bool SEP>
+__device__ __forceinline__ void f2_couple_cells(float2* v, const float2* ph, const float4* sr,
+                                                int t, int band, float2 am1, float2 bb) {
+  SepHead sh{};
+  if constexpr (SEP) {
+    sh = sep_head(sr);
+    bb = sep_b(bb, sh, band);
+  }
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
     const float2 q = make_float2(__shfl_xor_sync(0xffffffffu, v[j].x, 16),
                                  __shfl_xor_sync(0xffffffffu, v[j].y, 16));
-    float2 e = ph[t + j * T];
+    float2 e = SEP ? sep_cell(sh, ph[t + j * T], t + j * T) : ph[t + j * T];
     const bool inside = (e.x != 0.f) | (e.y != 0.f);
     if (band) e.y = -e.y;
     const float ax = inside ? am1.x : 0.f, ay = inside ? am1.y : 0.f;
@@ -143,6 +174,13 @@ __device__ __forceinline__ void f2_couple(float2* v, const float2* ph, int t, in
     ry = fmaf(cy, q.x, ry);
     v[j] = make_float2(rx, ry);
   }
+}
+
+template <int T>
+__device__ __forceinline__ void f2_couple(float2* v, const float2* ph, const float4* sr, int t,
+                                          int band, float2 am1, float2 bb) {
+  if (sr) f2_couple_cells<T, true>(v, ph, sr, t, band, am1, bb);
+  else f2_couple_cells<T, false>(v, ph, sr, t, band, am1, bb);
 }
 
 // Operator splitting of the step (Eq. split-op), SCH:
@@ -192,12 +230,17 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::OFF_MBAR) + rl * (HALF ? 2 : 1);
   float2* recph = reinterpret_cast<float2*>(smem + C::OFF_RECPH) + rl;
   double* red = reinterpret_cast<double*>(smem + C::OFF_RED) + rl * C::WPR * 2;
+  float4* srow0 = reinterpret_cast<float4*>(smem + C::OFF_SROW) + rl * (HALF ? 2 : 1);
+  const bool sep = d.srows != nullptr;
 
   if (t == 0 && band == 0) {
     mbar_init(bar);
     if constexpr (HALF) mbar_init(bar + 1);
   }
   fence_mbar_init();
+  // separable slices: the column phasors stay in buffer 0 for the launch
+  if (sep && active)
+    for (int k = band * T + t; k < N; k += 2 * T) ph0[k] = __ldg(&d.scols[k]);
 
   // Twiddles: pass 0 (group o = t) in registers; pass 1 (o = t mod S1, only
   // S1 distinct groups) from a small shared table W_{N/16}^{o j}.
@@ -226,7 +269,8 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
     for (int i = 0; i < C::groups(P); ++i)
 #pragma unroll
       for (int j = 0; j < RL; ++j)
-        pr[i * RL + j] = active ? __ldg(&tab[band * N + f2_pos<LOGN, P>(t + i * T, j)])
+        pr[i * RL + j] = active ? __ldg(&tab[band * N + f2_pos<LOGN, P>(
+                                                f2_group<LOGN, P, C::TAIL_WARP>(t, i), j)])
                                 : make_float2(0.f, 0.f);
   };
   load_table(d.prop);
@@ -241,9 +285,14 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
   const uint32_t slice_bytes = uint32_t(N) * 8u;
   int pending_slot = -1;
   bool timed_out = false;
+  // slice of step n into buffer `slot` (separable: the row head only)
+  auto fetch = [&](int n, int slot) {
+    if (sep) bulk_load(srow0 + slot, d.srows + n, kSepHeadBytes, bar + slot);
+    else bulk_load(ph0 + slot * N, d.phasor + size_t(n) * N, slice_bytes, bar + slot);
+  };
   if constexpr (HALF) {
     // the first step's slice; later ones are fetched a step ahead
-    if (lead && steps > 0) bulk_load(ph0, d.phasor + size_t(d.n_begin) * N, slice_bytes, bar);
+    if (lead && steps > 0) fetch(d.n_begin, 0);
   }
 
   // Error path: a thread whose bounded wait expires skips this step's other
@@ -252,14 +301,16 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
   // copy, so none is in flight when the CTA exits, and the CTA returns.
   for (int it = 0; it < steps; ++it) {
     const int n = d.n_begin + it;
-    float2* ph = ph0 + (HALF ? (it & 1) * N : 0);
+    // the step's slice (separable: the column phasors and the row head)
+    const float2* ph = ph0 + ((HALF && !sep) ? (it & 1) * N : 0);
+    const float4* sr = sep ? srow0 + (HALF ? (it & 1) : 0) : nullptr;
     if constexpr (HALF) {
       // first half coupling, on this step's slice
       if (active && !timed_out && !mbar_wait(bar + (it & 1), uint32_t((it >> 1) & 1))) {
         timed_out = true;
         s_abort = 1;
       }
-      f2_couple<T>(v, ph, t, band, d.am1h, d.bh);
+      f2_couple<T>(v, ph, sr, t, band, d.am1h, d.bh);
     }
     const bool rec = active && d.record_every > 0 && ((n + 1) % d.record_every) == 0 &&
                      (d.records != nullptr || d.powers != nullptr);
@@ -295,11 +346,9 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
     if constexpr (HALF) {
       // every thread is past the couplings of step it - 1, which read the
       // other buffer: fetch step it + 1's slice into it
-      if (lead && sg == 0 && it + 1 < steps)
-        bulk_load(ph0 + ((it + 1) & 1) * N, d.phasor + size_t(n + 1) * N, slice_bytes,
-                  bar + ((it + 1) & 1));
+      if (lead && sg == 0 && it + 1 < steps) fetch(n + 1, (it + 1) & 1);
     } else {
-      if (lead) bulk_load(ph, d.phasor + size_t(n) * N, slice_bytes, bar);
+      if (lead) fetch(n, 0);
     }
     if (lead && pending_slot >= 0) {
       double s0 = 0.0, s1 = 0.0;
@@ -316,12 +365,12 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
       dft<16, false, EX, PK>(v);
       f2_twiddle_s<false, C::S1>(v, tw1o);
       f2_store<LOGN, 1>(buf, v, t);
-      __syncthreads();
+      tail_sync<C::TAIL_WARP>();
     }
     // last pass: forward DFT, (P - 1)/N, inverse DFT
     {
       constexpr int P = NP - 1;
-      f2_load<LOGN, P>(buf, v, t);
+      f2_load<LOGN, P, C::TAIL_WARP>(buf, v, t);
       f2_dft<LOGN, P, false, EX, PK>(v);
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
@@ -329,8 +378,8 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
         v[k] = make_float2(fmaf(x.x, dd.x, -(x.y * dd.y)), fmaf(x.x, dd.y, x.y * dd.x));
       }
       f2_dft<LOGN, P, true, EX, PK>(v);
-      f2_store<LOGN, P>(buf, v, t);
-      __syncthreads();
+      f2_store<LOGN, P, C::TAIL_WARP>(buf, v, t);
+      tail_sync<C::TAIL_WARP>();
     }
     if constexpr (NP >= 3) {
       f2_load<LOGN, 1>(buf, v, t);
@@ -355,12 +404,12 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
         timed_out = true;
         s_abort = 1;
       }
-      f2_couple<T>(v, ph, t, band, d.am1, d.b);
+      f2_couple<T>(v, ph, sr, t, band, d.am1, d.b);
     } else if constexpr (SCH == kSchVerlet) {
-      f2_couple<T>(v, ph, t, band, d.am1h, d.bh);
+      f2_couple<T>(v, ph, sr, t, band, d.am1h, d.bh);
     } else {
       const bool last = sg == STAGES - 1;
-      f2_couple<T>(v, ph, t, band, last ? d.am1h : d.am1, last ? d.bh : d.b);
+      f2_couple<T>(v, ph, sr, t, band, last ? d.am1h : d.am1, last ? d.bh : d.b);
     }
     }   // stages (the fourth-order step ends on the t dz table, which its
         // next step starts with)

@@ -43,7 +43,8 @@ struct F3Cfg {
   static constexpr int OFF_XBAR = OFF_MBAR + 8 * PHB;      // [2] exchange barriers
   static constexpr int OFF_RECPH = OFF_XBAR + 16;
   static constexpr int OFF_RED = OFF_RECPH + 8;           // [WARPS] double
-  static constexpr int SMEM = OFF_RED + WARPS * 8;
+  static constexpr int OFF_SROW = (OFF_RED + WARPS * 8 + 15) / 16 * 16;   // [PHB] row heads
+  static constexpr int SMEM = OFF_SROW + PHB * 16;
   static_assert(LOGN >= 9 && LOGN <= 12, "cluster kernel covers 512..4096");
   // layout checks: fits one SM (227 KB); bulk-copy and 16-byte store
   // targets 16-byte aligned; mbarriers 8-byte aligned
@@ -150,6 +151,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
   uint64_t* xbar = reinterpret_cast<uint64_t*>(smem + C::OFF_XBAR);
   float2* recph = reinterpret_cast<float2*>(smem + C::OFF_RECPH);
   double* red = reinterpret_cast<double*>(smem + C::OFF_RED);
+  float4* srow0 = reinterpret_cast<float4*>(smem + C::OFF_SROW);
+  const bool sep = d.srows != nullptr;
   const uint32_t peer = uint32_t(band ^ 1);
   const uint32_t xpeer = mapa_u32(smem_u32(xb), peer);          // peer's exchange buffer
   const uint32_t xbar_peer = mapa_u32(smem_u32(xbar), peer);    // peer's exchange barriers
@@ -180,27 +183,44 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
   for (int i = 0; i < GL; ++i)
 #pragma unroll
     for (int j = 0; j < RL; ++j)
-      pr[i * RL + j] = __ldg(&d.prop[band * N + f2_pos<LOGN, NP - 1>(t + i * T, j)]);
+      pr[i * RL + j] = __ldg(&d.prop[band * N + f2_pos<LOGN, NP - 1>(
+                                             f2_group<LOGN, NP - 1, (NP >= 3)>(t, i), j)]);
 
   float2 v[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = d.state[band * N + t + j * T];
+  // separable slices: the column phasors stay in buffer 0 for the launch
+  if (sep)
+    for (int k = t; k < N; k += T) ph[k] = __ldg(&d.scols[k]);
   cluster.sync();   // peers initialised (mbarriers, shared memory) before any exchange
 
   const uint32_t slice_bytes = uint32_t(N) * 8u;
   int pending_slot = -1;
   bool timed_out = false;
   const float2 am1 = HALF ? d.am1h : d.am1, bb = HALF ? d.bh : d.b;
+  // slice of step n into buffer `slot` (separable: the row head only)
+  auto fetch = [&](int n, int slot) {
+    if (sep) bulk_load(srow0 + slot, d.srows + n, kSepHeadBytes, bar + slot);
+    else bulk_load(ph + slot * N, d.phasor + size_t(n) * N, slice_bytes, bar + slot);
+  };
   if constexpr (HALF) {
     // the launch's first half-step, on the slice of its first step (buffer
     // 0); later slices are fetched a step ahead into the other buffer
-    if (lead) bulk_load(ph, d.phasor + size_t(d.n_begin) * N, slice_bytes, bar);
+    if (lead) fetch(d.n_begin, 0);
     float2 q[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) q[j] = d.state[(band ^ 1) * N + t + j * T];
     if (!mbar_wait(bar, 0u)) timed_out = true;
+    const SepHead sh = sep ? sep_head(srow0) : SepHead{};
+    auto first_half = [&](auto S) {
+      constexpr bool SEP = decltype(S)::value;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = couple_cell(v[j], q[j], ph[t + j * T], band, am1, bb);
+      for (int j = 0; j < 16; ++j)
+        v[j] = couple_cell(v[j], q[j], slice_at<SEP>(ph, sh, t + j * T, t + j * T), band, am1,
+                           slice_b<SEP>(bb, sh, band));
+    };
+    if (sep) first_half(BoolC<true>{});
+    else first_half(BoolC<false>{});
   }
 
   for (int it = 0; it < steps; ++it) {
@@ -223,11 +243,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
     if constexpr (HALF) {
       // every thread is past step it - 1's couplings, which read the buffer
       // of slice it - 1: fetch slice it + 1 into it
-      if (lead && it + 1 < steps)
-        bulk_load(ph + ((it + 1) & 1) * N, d.phasor + size_t(n + 1) * N, slice_bytes,
-                  bar + ((it + 1) & 1));
+      if (lead && it + 1 < steps) fetch(n + 1, (it + 1) & 1);
     } else {
-      if (lead) bulk_load(ph, d.phasor + size_t(n) * N, slice_bytes, bar);
+      if (lead) fetch(n, 0);
     }
     if (lead && pending_slot >= 0) {
       double s = 0.0;
@@ -235,16 +253,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
       d.powers[2 * pending_slot + band] = s * d.dx_um;
       pending_slot = -1;
     }
+    // (three passes: pass 1 and the last pass of warp w address positions
+    // [512 w, 512 w + 512) only, the last pass's groups as in f2_group, so
+    // the barriers between them are the warp's)
+    constexpr bool TW = NP >= 3;
     if constexpr (NP >= 3) {
       f2_load<LOGN, 1>(buf, v, t);
       dft<16, false, EX>(v);
       f2_twiddle<false>(v, w1);
       f2_store<LOGN, 1>(buf, v, t);
-      __syncthreads();
+      tail_sync<TW>();
     }
     {
       constexpr int P = NP - 1;
-      f2_load<LOGN, P>(buf, v, t);
+      f2_load<LOGN, P, TW>(buf, v, t);
       f2_dft<LOGN, P, false, EX>(v);
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
@@ -252,8 +274,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
         v[k] = make_float2(fmaf(x.x, dd.x, -(x.y * dd.y)), fmaf(x.x, dd.y, x.y * dd.x));
       }
       f2_dft<LOGN, P, true, EX>(v);
-      f2_store<LOGN, P>(buf, v, t);
-      __syncthreads();
+      f2_store<LOGN, P, TW>(buf, v, t);
+      tail_sync<TW>();
     }
     if constexpr (NP >= 3) {
       f2_load<LOGN, 1>(buf, v, t);
@@ -286,8 +308,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
       if (next && !timed_out &&
           !mbar_wait(bar + ((it + 1) & 1), uint32_t(((it + 1) >> 1) & 1)))
         timed_out = true;
-      const float2* phc = ph + (it & 1) * N;
-      const float2* phn = ph + ((it + 1) & 1) * N;
+      // (separable: both couplings read the column phasors of buffer 0 and
+      // the row heads of steps it and it + 1)
+      const float2* phc = ph + (sep ? 0 : (it & 1) * N);
+      const float2* phn = ph + (sep ? 0 : ((it + 1) & 1) * N);
+      const SepHead shc = sep ? sep_head(srow0 + (it & 1)) : SepHead{};
+      const SepHead shn = (sep && next) ? sep_head(srow0 + ((it + 1) & 1)) : SepHead{};
       const float2 g = rec ? *recph : make_float2(1.f, 0.f);
       const int slot = rec ? (n + 1) / d.record_every - 1 : 0;
       float2* r0 = (rec && d.records) ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
@@ -300,26 +326,33 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
       __syncthreads();
 #pragma unroll
       for (int j = 0; j < 16; ++j) buf[t + j * T] = v[j];
+      auto three_halves = [&](auto S) {
+        constexpr bool SEP = decltype(S)::value;
+        const float2 bc = slice_b<SEP>(bb, shc, band), bo = slice_b<SEP>(bb, shc, band ^ 1);
+        const float2 bn = slice_b<SEP>(bb, shn, band);
 #pragma unroll 1
-      for (int pp = 0; pp < 8; ++pp) {
-        const float4 q2 = *reinterpret_cast<const float4*>(xi + xpair(pp, t, T));
+        for (int pp = 0; pp < 8; ++pp) {
+          const float4 q2 = *reinterpret_cast<const float4*>(xi + xpair(pp, t, T));
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int at = t + (2 * pp + k) * T;
-          const float2 p = buf[at], q = k ? make_float2(q2.z, q2.w) : make_float2(q2.x, q2.y);
-          const float2 e = phc[at];
-          float2 c = couple_cell(p, q, e, band, am1, bb);   // step it, second half
-          if (rec) {
-            s = pow_acc(s, c);
-            if (r0) r0[at] = make_float2(fmaf(c.x, g.x, -(c.y * g.y)), fmaf(c.x, g.y, c.y * g.x));
+          for (int k = 0; k < 2; ++k) {
+            const int at = t + (2 * pp + k) * T;
+            const float2 p = buf[at], q = k ? make_float2(q2.z, q2.w) : make_float2(q2.x, q2.y);
+            const float2 e = slice_at<SEP>(phc, shc, at, at);
+            float2 c = couple_cell(p, q, e, band, am1, bc);   // step it, second half
+            if (rec) {
+              s = pow_acc(s, c);
+              if (r0) r0[at] = make_float2(fmaf(c.x, g.x, -(c.y * g.y)), fmaf(c.x, g.y, c.y * g.x));
+            }
+            if (next) {   // step it + 1, first half, with the other band's value
+              const float2 co = couple_cell(q, p, e, band ^ 1, am1, bo);
+              c = couple_cell(c, co, slice_at<SEP>(phn, shn, at, at), band, am1, bn);
+            }
+            buf[at] = c;
           }
-          if (next) {   // step it + 1, first half, with the other band's value
-            const float2 co = couple_cell(q, p, e, band ^ 1, am1, bb);
-            c = couple_cell(c, co, phn[at], band, am1, bb);
-          }
-          buf[at] = c;
         }
-      }
+      };
+      if (sep) three_halves(BoolC<true>{});
+      else three_halves(BoolC<false>{});
 #pragma unroll
       for (int j = 0; j < 16; ++j) v[j] = buf[t + j * T];
       __syncthreads();
@@ -332,13 +365,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
       }
     } else {
       if (!timed_out && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
-  #pragma unroll
-      for (int pp = 0; pp < 8; ++pp) {
-        const float4 q2 = *reinterpret_cast<const float4*>(xi + xpair(pp, t, T));
-        v[2 * pp] = couple_cell(v[2 * pp], make_float2(q2.x, q2.y), ph[t + 2 * pp * T], band, am1, bb);
-        v[2 * pp + 1] =
-            couple_cell(v[2 * pp + 1], make_float2(q2.z, q2.w), ph[t + (2 * pp + 1) * T], band, am1, bb);
-      }
+      const SepHead sh = sep ? sep_head(srow0) : SepHead{};
+      auto couple_all = [&](auto S) {
+        constexpr bool SEP = decltype(S)::value;
+        const float2 bs = slice_b<SEP>(bb, sh, band);
+#pragma unroll
+        for (int pp = 0; pp < 8; ++pp) {
+          const float4 q2 = *reinterpret_cast<const float4*>(xi + xpair(pp, t, T));
+          const int c0 = t + 2 * pp * T, c1 = t + (2 * pp + 1) * T;
+          v[2 * pp] = couple_cell(v[2 * pp], make_float2(q2.x, q2.y),
+                                  slice_at<SEP>(ph, sh, c0, c0), band, am1, bs);
+          v[2 * pp + 1] = couple_cell(v[2 * pp + 1], make_float2(q2.z, q2.w),
+                                      slice_at<SEP>(ph, sh, c1, c1), band, am1, bs);
+        }
+      };
+      if (sep) couple_all(BoolC<true>{});
+      else couple_all(BoolC<false>{});
 
       if (rec) {
         const int slot = (n + 1) / d.record_every - 1;

@@ -69,7 +69,8 @@ struct F4ECfg {
   static constexpr int OFF_RECPH = OFF_PPEER + 16;
   static constexpr int OFF_RED = OFF_RECPH + 8;            // [WARPS] double
   static constexpr int OFF_PART = OFF_RED + WARPS * 8;
-  static constexpr int SMEM = OFF_PART + 8;
+  static constexpr int OFF_SROW = (OFF_PART + 8 + 15) / 16 * 16;   // [2] row heads
+  static constexpr int SMEM = OFF_SROW + 2 * 16;
   static_assert(SMEM <= 232448, "fits one SM");
   static_assert(LM == 11 || LM == 12, "N = 4096 or 8192");
   // layout checks: fits one SM (227 KB); bulk-copy and 16-byte store
@@ -116,6 +117,10 @@ __device__ __forceinline__ void st_async_f64(uint32_t raddr, double v, uint32_t 
 // step's combine, rewritten by the peer only at step n + 2, after it has
 // received this CTA's step n + 1 spectrum), issued once every thread is past
 // the combine and awaited at the coupling.
+// Separable slices: the column phasors of the CTA's samples stay in the
+// slice buffer for the launch (position m holds column 2m + h), and every
+// slice copy above carries the step's row head instead, into row-head slot
+// 0 (slot 1 for the next step's), on the same barriers.
 template <int LM, bool EX, bool HALF = false>
 __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
     fused4e_march_kernel(const RowDescF32* __restrict__ rows, int n_rows, int steps,
@@ -150,6 +155,8 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
   float2* recph = reinterpret_cast<float2*>(smem + C::OFF_RECPH);
   double* red = reinterpret_cast<double*>(smem + C::OFF_RED);
   double* part = reinterpret_cast<double*>(smem + C::OFF_PART);
+  float4* srow0 = reinterpret_cast<float4*>(smem + C::OFF_SROW);
+  const bool sep = d.srows != nullptr;
   const uint32_t peer = uint32_t(c ^ 1);       // same band, other half of the samples
   const uint32_t partner = uint32_t(c ^ 2);    // other band, same samples
   const uint32_t g_peer = mapa_u32(smem_u32(gx), peer);
@@ -182,7 +189,8 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
   float2 cw[16], d0[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
-    const int pos = f2_pos<L, NP - 1>(t + (j / F::radix(NP - 1)) * T, j % F::radix(NP - 1));
+    const int pos = f2_pos<L, NP - 1>(f2_group<L, NP - 1, true>(t, j / F::radix(NP - 1)),
+                                      j % F::radix(NP - 1));
     const float4 a = __ldg(&tw[local_freq<L>(pos)]);
     cw[j] = make_float2(a.x, a.y);
     d0[j] = __ldg(&dtab[(band * 2 + 0) * M + pos]);
@@ -192,6 +200,14 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
   float2 v[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = d.state[band * N + 2 * (t + j * T) + h];
+  // separable slices: column 2m + h at position m (the stream keeps it at
+  // 2m + h for N = 4096, at h M + m for N = 8192)
+  if (sep)
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int m = t + j * T;
+      ph[m] = __ldg(&d.scols[C::NAT ? 2 * m + h : h * M + m]);
+    }
   cluster.sync();   // every CTA's barriers initialised before any remote store
 
   const uint32_t slice_bytes = uint32_t(C::PH) * 8u;
@@ -199,21 +215,34 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
   double my_part = 0.0;
   const float2 am1 = HALF ? d.am1h : d.am1, bb = HALF ? d.bh : d.b;
   const bool pow_on = d.powers != nullptr && d.record_every > 0;
+  // step n's slice (the CTA's part of it) into `dst` (separable: its row
+  // head into row-head slot `slot`)
+  auto fetch = [&](int n, float2* dst, int slot, uint64_t* b) {
+    if (sep) bulk_load(srow0 + slot, d.srows + n, kSepHeadBytes, b);
+    else bulk_load(dst, d.phasor + size_t(n) * N + (C::NAT ? size_t(0) : size_t(h) * M),
+                   slice_bytes, b);
+  };
   if constexpr (HALF) {
     // the launch's first half-step on the slice of its first step (buffer
     // 0); later slices are fetched a step ahead into the other buffer
     // (N = 8192: into the free half of the peer spectrum buffer)
-    if (lead)
-      bulk_load(ph, d.phasor + size_t(d.n_begin) * N + (C::NAT ? size_t(0) : size_t(h) * M),
-                slice_bytes, bar);
+    if (lead) fetch(d.n_begin, ph, 0, bar);
     float2 q[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) q[j] = d.state[(band ^ 1) * N + 2 * (t + j * T) + h];
     if (!mbar_wait(bar, 0u)) timed_out = true;
+    const SepHead sh = sep ? sep_head(srow0) : SepHead{};
+    auto first_half = [&](auto S) {
+      constexpr bool SEP = decltype(S)::value;
 #pragma unroll
-    for (int j = 0; j < 16; ++j)
-      v[j] = couple_cell(v[j], q[j], ph[C::NAT ? 2 * (t + j * T) + h : t + j * T], band, am1,
-                         bb);
+      for (int j = 0; j < 16; ++j) {
+        const int m = t + j * T;
+        v[j] = couple_cell(v[j], q[j], slice_at<SEP>(ph, sh, (SEP || !C::NAT) ? m : 2 * m + h, 2 * m + h),
+                           band, am1, slice_b<SEP>(bb, sh, band));
+      }
+    };
+    if (sep) first_half(BoolC<true>{});
+    else first_half(BoolC<false>{});
   }
 
   for (int it = 0; it < steps; ++it) {
@@ -241,18 +270,16 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
         // this step's slice into the one buffer (phase it + 1: the launch's
         // first half-step took phase 0); the next one goes to L2 now and to
         // the peer spectrum buffer once the combine is done
-        bulk_load(ph, d.phasor + size_t(n) * N + size_t(h) * M, slice_bytes, bar);
-        if (it + 1 < steps) bulk_prefetch_l2(d.phasor + size_t(n + 1) * N + size_t(h) * M,
-                                             slice_bytes);
+        fetch(n, ph, 0, bar);
+        if (!sep && it + 1 < steps)
+          bulk_prefetch_l2(d.phasor + size_t(n + 1) * N + size_t(h) * M, slice_bytes);
       } else if constexpr (HALF) {
         // every thread is past step it - 1's couplings, which read the
         // buffer of slice it - 1: fetch slice it + 1 into it
         if (it + 1 < steps)
-          bulk_load(ph + ((it + 1) & 1) * C::PH, d.phasor + size_t(n + 1) * N, slice_bytes,
-                    bar + ((it + 1) & 1));
+          fetch(n + 1, ph + ((it + 1) & 1) * C::PH, (it + 1) & 1, bar + ((it + 1) & 1));
       } else {
-        bulk_load(ph, d.phasor + size_t(n) * N + (C::NAT ? size_t(0) : size_t(h) * M),
-                  slice_bytes, bar);
+        fetch(n, ph, 0, bar);
       }
       mbar_expect_tx(&gbar[half], uint32_t(M) * 8u + (part_due ? 8u : 0u));
       if (part_due) {
@@ -266,8 +293,11 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
     dft<16, false, EX>(v);
     f2_twiddle<false>(v, w1);
     f2_store<L, 1>(buf, v, t);
-    __syncthreads();
-    f2_load<L, NP - 1>(buf, v, t);
+    // (passes 1 and 2 of warp w address positions [512 w, 512 w + 512) only,
+    // the last pass's groups as in f2_group: the barriers between them are
+    // the warp's)
+    __syncwarp();
+    f2_load<L, NP - 1, true>(buf, v, t);
     f2_dft<L, NP - 1, false, EX>(v);             // v[j] = F_h[k_j]
     {
       const uint32_t go = g_peer + uint32_t(half * M) * 8u;
@@ -297,13 +327,13 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
       }
     }
     f2_dft<L, NP - 1, true, EX>(v);
-    f2_store<L, NP - 1>(buf, v, t);
-    __syncthreads();
+    f2_store<L, NP - 1, true>(buf, v, t);
+    // (the next-slice copy of the second-order step waits for every thread
+    // to be past the combine)
+    tail_sync<!HALF_G>();
     if constexpr (HALF_G) {
       // every thread is past the combine, the last reader of gx[half]
-      if (lead && it + 1 < steps)
-        bulk_load(gx + half * M, d.phasor + size_t(n + 1) * N + size_t(h) * M, slice_bytes,
-                  bar + 1);
+      if (lead && it + 1 < steps) fetch(n + 1, gx + half * M, 1, bar + 1);
     }
     f2_load<L, 1>(buf, v, t);
     f2_twiddle<true>(v, w1);
@@ -335,8 +365,13 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
           timed_out = true;
       }
       const float2* ci = cb + half * M;
-      const float2* phc = HALF_G ? ph : ph + (it & 1) * C::PH;
-      const float2* phn = HALF_G ? gx + half * M : ph + ((it + 1) & 1) * C::PH;
+      // (separable: both couplings read the column phasors of buffer 0 and
+      // the row heads of steps it and it + 1)
+      const float2* phc = (HALF_G || sep) ? ph : ph + (it & 1) * C::PH;
+      const float2* phn = sep ? ph : HALF_G ? gx + half * M : ph + ((it + 1) & 1) * C::PH;
+      const SepHead shc = sep ? sep_head(srow0 + (HALF_G ? 0 : (it & 1))) : SepHead{};
+      const SepHead shn =
+          (sep && next) ? sep_head(srow0 + (HALF_G ? 1 : ((it + 1) & 1))) : SepHead{};
       const float2 g = rec ? *recph : make_float2(1.f, 0.f);
       const int slot = rec ? (n + 1) / d.record_every - 1 : 0;
       float2* r0 = (rec && d.records) ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
@@ -348,29 +383,36 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
       __syncthreads();
 #pragma unroll
       for (int j = 0; j < 16; ++j) buf[t + j * T] = v[j];
+      auto three_halves = [&](auto S) {
+        constexpr bool SEP = decltype(S)::value;
+        const float2 bc = slice_b<SEP>(bb, shc, band), bo = slice_b<SEP>(bb, shc, band ^ 1);
+        const float2 bn = slice_b<SEP>(bb, shn, band);
 #pragma unroll 1
-      for (int pp = 0; pp < 8; ++pp) {
-        const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
+        for (int pp = 0; pp < 8; ++pp) {
+          const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int j = 2 * pp + k;
-          const int cell = C::NAT ? 2 * (t + j * T) + h : t + j * T;
-          const float2 p = buf[t + j * T], q = k ? make_float2(q2.z, q2.w) : make_float2(q2.x, q2.y);
-          const float2 e = phc[cell];
-          float2 c = couple_cell(p, q, e, band, am1, bb);   // step it, second half
-          if (rec) {
-            s = pow_acc(s, c);
-            if (r0)   // records in natural order
-              r0[2 * (t + j * T) + h] =
-                  make_float2(fmaf(c.x, g.x, -(c.y * g.y)), fmaf(c.x, g.y, c.y * g.x));
+          for (int k = 0; k < 2; ++k) {
+            const int j = 2 * pp + k;
+            const int m = t + j * T;
+            const int cell = (SEP || !C::NAT) ? m : 2 * m + h;
+            const float2 p = buf[m], q = k ? make_float2(q2.z, q2.w) : make_float2(q2.x, q2.y);
+            const float2 e = slice_at<SEP>(phc, shc, cell, 2 * m + h);
+            float2 c = couple_cell(p, q, e, band, am1, bc);   // step it, second half
+            if (rec) {
+              s = pow_acc(s, c);
+              if (r0)   // records in natural order
+                r0[2 * m + h] = make_float2(fmaf(c.x, g.x, -(c.y * g.y)), fmaf(c.x, g.y, c.y * g.x));
+            }
+            if (next) {   // step it + 1, first half, with the other band's value
+              const float2 co = couple_cell(q, p, e, band ^ 1, am1, bo);
+              c = couple_cell(c, co, slice_at<SEP>(phn, shn, cell, 2 * m + h), band, am1, bn);
+            }
+            buf[m] = c;
           }
-          if (next) {   // step it + 1, first half, with the other band's value
-            const float2 co = couple_cell(q, p, e, band ^ 1, am1, bb);
-            c = couple_cell(c, co, phn[cell], band, am1, bb);
-          }
-          buf[t + j * T] = c;
         }
-      }
+      };
+      if (sep) three_halves(BoolC<true>{});
+      else three_halves(BoolC<false>{});
 #pragma unroll
       for (int j = 0; j < 16; ++j) v[j] = buf[t + j * T];
       __syncthreads();
@@ -383,14 +425,24 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
     } else {
       if (!timed_out && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
       const float2* ci = cb + half * M;
-  #pragma unroll
-      for (int pp = 0; pp < 8; ++pp) {
-        const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
-        const int c0 = C::NAT ? 2 * (t + 2 * pp * T) + h : t + 2 * pp * T;
-        const int c1 = C::NAT ? 2 * (t + (2 * pp + 1) * T) + h : t + (2 * pp + 1) * T;
-        v[2 * pp] = couple_cell(v[2 * pp], make_float2(q2.x, q2.y), ph[c0], band, am1, bb);
-        v[2 * pp + 1] = couple_cell(v[2 * pp + 1], make_float2(q2.z, q2.w), ph[c1], band, am1, bb);
-      }
+      const SepHead sh = sep ? sep_head(srow0) : SepHead{};
+      auto couple_all = [&](auto S) {
+        constexpr bool SEP = decltype(S)::value;
+        const float2 bs = slice_b<SEP>(bb, sh, band);
+#pragma unroll
+        for (int pp = 0; pp < 8; ++pp) {
+          const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
+          const int m0 = t + 2 * pp * T, m1 = t + (2 * pp + 1) * T;
+          const int c0 = (SEP || !C::NAT) ? m0 : 2 * m0 + h;
+          const int c1 = (SEP || !C::NAT) ? m1 : 2 * m1 + h;
+          v[2 * pp] = couple_cell(v[2 * pp], make_float2(q2.x, q2.y),
+                                  slice_at<SEP>(ph, sh, c0, 2 * m0 + h), band, am1, bs);
+          v[2 * pp + 1] = couple_cell(v[2 * pp + 1], make_float2(q2.z, q2.w),
+                                      slice_at<SEP>(ph, sh, c1, 2 * m1 + h), band, am1, bs);
+        }
+      };
+      if (sep) couple_all(BoolC<true>{});
+      else couple_all(BoolC<false>{});
 
       if (rec) {
         const int slot = (n + 1) / d.record_every - 1;

@@ -11,9 +11,15 @@
 // frequency, digit-reversed output; the inverse mirrors it), so each thread
 // does half the serial work of the 16-point form and each scheduler has two
 // warps to issue from, at the price of one more shared-memory pass per
-// transform.  The propagator increments D(k), D(k + M) come from the plan's
-// half-band tables, which are stored in the 16-point form's output order:
-// each thread looks its frequencies up once per launch.
+// transform.  Passes 1-3 of a warp stay within its own 256 positions (see
+// s4_group), so of the eight passes of a step only the two next to pass 0
+// end in a CTA barrier; the others end in the warp's own.  Thread t sends
+// and receives the slots of thread t in both exchanges, so each warp has
+// its own pair of exchange barriers and waits only for the same warp of
+// the peer (the peer's slowest warp no longer holds up the others).  The propagator
+// increments D(k), D(k + M) come from the plan's half-band tables, which are
+// stored in the 16-point form's output order: each thread looks its
+// frequencies up once per launch.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -122,13 +128,14 @@ struct F4SCfg {
   static constexpr int OFF_PH = OFF_C + 2 * M * 8;         // [N] strain slice (natural order)
   static constexpr int OFF_E1 = OFF_PH + N * 8;            // [8][T] D(k_j + M)
   static constexpr int OFF_MBAR = OFF_E1 + M * 8;          // strain-slice barrier
-  static constexpr int OFF_GBAR = OFF_MBAR + 8;            // [2] F barriers
-  static constexpr int OFF_CBAR = OFF_GBAR + 16;           // [2] psi_p barriers
-  static constexpr int OFF_PPEER = OFF_CBAR + 16;          // [2] peer's band-power part
+  static constexpr int OFF_GBAR = OFF_MBAR + 8;            // [2][WARPS] F barriers
+  static constexpr int OFF_CBAR = OFF_GBAR + 16 * WARPS;   // [2][WARPS] psi_p barriers
+  static constexpr int OFF_PPEER = OFF_CBAR + 16 * WARPS;  // [2] peer's band-power part
   static constexpr int OFF_RECPH = OFF_PPEER + 16;
   static constexpr int OFF_RED = OFF_RECPH + 8;            // [WARPS] double
   static constexpr int OFF_PART = OFF_RED + WARPS * 8;
-  static constexpr int SMEM = OFF_PART + 8;
+  static constexpr int OFF_SROW = (OFF_PART + 8 + 15) / 16 * 16;   // row head
+  static constexpr int SMEM = OFF_SROW + 16;
   static_assert(SMEM <= 232448, "fits one SM");
   static_assert(OFF_G % 16 == 0 && OFF_C % 16 == 0 && OFF_PH % 16 == 0,
                 "16-byte stores and bulk copy");
@@ -136,6 +143,28 @@ struct F4SCfg {
                     OFF_PPEER % 8 == 0,
                 "mbarrier and 8-byte store alignment");
 };
+
+// Groups of the last pass (radix 4, two per thread), chosen so that passes
+// 1, 2 and 3 of warp w all stay within positions [256 w, 256 w + 256): group
+// i of thread t is 64 (t / 32) + 32 i + t mod 32.  Pass 1 (stride 32) and
+// pass 2 (stride 4) of warp w already address only that block, so between
+// passes 1, 2 and 3 (in both directions) a warp waits for itself alone; only
+// the passes to and from pass 0 (stride 256) need the whole CTA.
+__device__ __forceinline__ int s4_group(int t, int i) { return (t >> 5) * 64 + i * 32 + (t & 31); }
+
+__device__ __forceinline__ void s4_store_last(float2* buf, const float2* v, int t) {
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) buf[swz8(s4_group(t, i) * 4 + j)] = v[i * 4 + j];
+}
+
+__device__ __forceinline__ void s4_load_last(const float2* buf, float2* v, int t) {
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[i * 4 + j] = buf[swz8(s4_group(t, i) * 4 + j)];
+}
 
 template <bool EX>
 __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg::T, 1)
@@ -169,6 +198,8 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg::T, 1)
   float2* recph = reinterpret_cast<float2*>(smem + C::OFF_RECPH);
   double* red = reinterpret_cast<double*>(smem + C::OFF_RED);
   double* part = reinterpret_cast<double*>(smem + C::OFF_PART);
+  float4* srow = reinterpret_cast<float4*>(smem + C::OFF_SROW);
+  const bool sep = d.srows != nullptr;
   const uint32_t peer = uint32_t(c ^ 1);       // same band, other half of the samples
   const uint32_t partner = uint32_t(c ^ 2);    // other band, same samples
   const uint32_t g_peer = mapa_u32(smem_u32(gx), peer);
@@ -179,10 +210,10 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg::T, 1)
 
   if (lead) {
     mbar_init(bar);
-    mbar_init(&gbar[0]);
-    mbar_init(&gbar[1]);
-    mbar_init(&cbar[0]);
-    mbar_init(&cbar[1]);
+    for (int i = 0; i < 2 * C::WARPS; ++i) {
+      mbar_init(&gbar[i]);
+      mbar_init(&cbar[i]);
+    }
   }
   fence_mbar_init();
 
@@ -204,7 +235,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg::T, 1)
   float2 cw[8], d0[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    const int pos = f8_pos<L, NP - 1>(t + (j / RL) * T, j % RL);
+    const int pos = s4_group(t, j / RL) * RL + j % RL;
     const int k = cfg_freq<F>(pos);
     const int p16 = pos16_of_freq2048(k);
     const float4 a = __ldg(&tw[k]);
@@ -216,6 +247,11 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg::T, 1)
   float2 v[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) v[j] = d.state[band * N + 2 * (t + j * T) + h];
+  // separable slices: the phasor of column 2m + h at position m of the slice
+  // buffer for the launch (each thread reads its own points: no conflicts)
+  if (sep)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) ph[t + j * T] = __ldg(&d.scols[2 * (t + j * T) + h]);
   cluster.sync();   // every CTA's barriers initialised before any remote store
 
   const uint32_t slice_bytes = uint32_t(N) * 8u;
@@ -245,37 +281,43 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg::T, 1)
     f8_store<L, 0>(buf, v, t);
     __syncthreads();
     if (lead) {
-      bulk_load(ph, d.phasor + size_t(n) * N, slice_bytes, bar);
-      mbar_expect_tx(&gbar[half], uint32_t(M) * 8u + (part_due ? 8u : 0u));
-      if (part_due) {
+      // the step's slice (separable: its row head)
+      if (sep) bulk_load(srow, d.srows + n, kSepHeadBytes, bar);
+      else bulk_load(ph, d.phasor + size_t(n) * N, slice_bytes, bar);
+      if (part_due) {   // rides on the peer's warp-0 F barrier
         double s = 0.0;
         for (int w = 0; w < C::WARPS; ++w) s += red[w];
         my_part = s;
-        st_async_f64(pp_peer + uint32_t(half) * 8u, s, gbar_peer + uint32_t(half) * 8u);
+        st_async_f64(pp_peer + uint32_t(half) * 8u, s,
+                     gbar_peer + uint32_t(half * C::WARPS) * 8u);
       }
     }
+    // each warp's F barrier: its 32 threads' slots from the same warp of the peer
+    if (lane == 0)
+      mbar_expect_tx(&gbar[half * C::WARPS + warp], 32u * 8u * 8u + ((lead && part_due) ? 8u : 0u));
     f8_load<L, 1>(buf, v, t);
     dft<8, false, EX>(v);
     f8_twiddle<false>(v, w1);
     f8_store<L, 1>(buf, v, t);
-    __syncthreads();
+    __syncwarp();
     f8_load<L, 2>(buf, v, t);
     dft<8, false, EX>(v);
     f8_twiddle<false>(v, w2);
     f8_store<L, 2>(buf, v, t);
-    __syncthreads();
-    f8_load<L, NP - 1>(buf, v, t);
+    __syncwarp();
+    s4_load_last(buf, v, t);
     f8_dft<L, NP - 1, false, EX>(v);              // v[j] = F_h[k_j]
     {
       const uint32_t go = g_peer + uint32_t(half * M) * 8u;
-      const uint32_t gbo = gbar_peer + uint32_t(half) * 8u;
+      const uint32_t gbo = gbar_peer + uint32_t(half * C::WARPS + warp) * 8u;
 #pragma unroll
       for (int pp = 0; pp < 4; ++pp)
         st_async_v4(go + uint32_t(xpair(pp, t, T)) * 8u, v[2 * pp], v[2 * pp + 1], gbo);
     }
     // (no barrier before the inverse pass rewrites buf: each thread's
     // last-pass positions are its own in both directions)
-    if (!timed_out && !mbar_wait_cluster(&gbar[half], uint32_t((it >> 1) & 1))) timed_out = true;
+    if (!timed_out && !mbar_wait_cluster(&gbar[half * C::WARPS + warp], uint32_t((it >> 1) & 1)))
+      timed_out = true;
     if (lead && part_due && h == 0)
       d.powers[2 * (n / d.record_every - 1) + band] = (my_part + ppeer[half]) * d.dx_um;
     {
@@ -294,13 +336,13 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg::T, 1)
       }
     }
     f8_dft<L, NP - 1, true, EX>(v);
-    f8_store<L, NP - 1>(buf, v, t);
-    __syncthreads();
+    s4_store_last(buf, v, t);
+    __syncwarp();
     f8_load<L, 2>(buf, v, t);
     f8_twiddle<true>(v, w2);
     dft<8, true, EX>(v);
     f8_store<L, 2>(buf, v, t);
-    __syncthreads();
+    __syncwarp();
     f8_load<L, 1>(buf, v, t);
     f8_twiddle<true>(v, w1);
     dft<8, true, EX>(v);
@@ -310,26 +352,37 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg::T, 1)
     f8_twiddle<true>(v, w0);
     dft<8, true, EX>(v);
     {
-      if (lead) mbar_expect_tx(&cbar[half], uint32_t(M) * 8u);
+      if (lane == 0) mbar_expect_tx(&cbar[half * C::WARPS + warp], 32u * 8u * 8u);
       const uint32_t co = c_part + uint32_t(half * M) * 8u;
-      const uint32_t cbo = cbar_part + uint32_t(half) * 8u;
+      const uint32_t cbo = cbar_part + uint32_t(half * C::WARPS + warp) * 8u;
 #pragma unroll
       for (int j = 0; j < 8; ++j) v[j] = cadd(org[j], v[j]);
 #pragma unroll
       for (int pp = 0; pp < 4; ++pp)
         st_async_v4(co + uint32_t(xpair(pp, t, T)) * 8u, v[2 * pp], v[2 * pp + 1], cbo);
     }
-    if (!timed_out && !mbar_wait_cluster(&cbar[half], uint32_t((it >> 1) & 1))) timed_out = true;
+    if (!timed_out && !mbar_wait_cluster(&cbar[half * C::WARPS + warp], uint32_t((it >> 1) & 1)))
+      timed_out = true;
     if (!timed_out && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
     {
       const float2* ci = cb + half * M;
+      const SepHead sh = sep ? sep_head(srow) : SepHead{};
+      auto couple_all = [&](auto S) {
+        constexpr bool SEP = decltype(S)::value;
+        const float2 bs = slice_b<SEP>(bb, sh, band);
 #pragma unroll
-      for (int pp = 0; pp < 4; ++pp) {
-        const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
-        const int c0 = 2 * (t + 2 * pp * T) + h, c1 = 2 * (t + (2 * pp + 1) * T) + h;
-        v[2 * pp] = couple_cell(v[2 * pp], make_float2(q2.x, q2.y), ph[c0], band, am1, bb);
-        v[2 * pp + 1] = couple_cell(v[2 * pp + 1], make_float2(q2.z, q2.w), ph[c1], band, am1, bb);
-      }
+        for (int pp = 0; pp < 4; ++pp) {
+          const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
+          const int m0 = t + 2 * pp * T, m1 = t + (2 * pp + 1) * T;
+          const int c0 = 2 * m0 + h, c1 = 2 * m1 + h;
+          v[2 * pp] = couple_cell(v[2 * pp], make_float2(q2.x, q2.y),
+                                  slice_at<SEP>(ph, sh, SEP ? m0 : c0, c0), band, am1, bs);
+          v[2 * pp + 1] = couple_cell(v[2 * pp + 1], make_float2(q2.z, q2.w),
+                                      slice_at<SEP>(ph, sh, SEP ? m1 : c1, c1), band, am1, bs);
+        }
+      };
+      if (sep) couple_all(BoolC<true>{});
+      else couple_all(BoolC<false>{});
     }
     if (rec) {
       const int slot = (n + 1) / d.record_every - 1;

@@ -62,7 +62,8 @@ struct F4TCfg {
   static constexpr int OFF_RED = OFF_RECPH + 8;            // [WARPS] double
   static constexpr int OFF_PART = OFF_RED + WARPS * 8;
   static constexpr int OFF_TMEM = OFF_PART + 8;            // allocated TMEM address
-  static constexpr int SMEM = OFF_TMEM + 8;
+  static constexpr int OFF_SROW = (OFF_TMEM + 8 + 15) / 16 * 16;   // [2] row heads
+  static constexpr int SMEM = OFF_SROW + 2 * 16;
   static_assert(SMEM <= 232448, "fits one SM");
   // layout checks: fits one SM (227 KB); bulk-copy and 16-byte store
   // targets 16-byte aligned; mbarriers 8-byte aligned
@@ -184,6 +185,11 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
 
   // peer e (1..3) of the band is part (h + e) & 3; our F goes to its slot
   // 3 - e (the receiver indexes slots by d - 1, d = sender - receiver mod 4)
+  // separable slices: the column phasors of the CTA's samples (column
+  // 4m + h at position m, as in the stream) stay in the slice buffer; every
+  // slice copy carries the step's row head instead (slot 1: the next step's)
+  float4* srow0 = reinterpret_cast<float4*>(smem + C::OFF_SROW);
+  const bool sep = d.srows != nullptr;
   uint32_t g_to[3], gbar_to[3], free_to[3];
 #pragma unroll
   for (int e = 1; e <= 3; ++e) {
@@ -249,6 +255,9 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
   float2 v[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = d.state[band * N + 4 * (t + j * T) + h];
+  if (sep)
+#pragma unroll
+    for (int j = 0; j < 16; ++j) ph[t + j * T] = __ldg(&d.scols[h * M + t + j * T]);
   cluster.sync();   // every CTA's barriers initialised before any remote operation
 
   const uint32_t slice_bytes = uint32_t(M) * 8u;
@@ -256,16 +265,32 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
   double my_part = 0.0;
   const float2 am1 = HALF ? d.am1h : d.am1, bb = HALF ? d.bh : d.b;
   const bool pow_on = d.powers != nullptr && d.record_every > 0;
+  // step n's slice (this part of it) into `dst`, separable: its row head
+  // into row-head slot `slot`
+  auto fetch = [&](int n, float2* dst, int slot, uint64_t* b) {
+    if (sep) bulk_load(srow0 + slot, d.srows + n, kSepHeadBytes, b);
+    else bulk_load(dst, d.phasor + size_t(n) * N + size_t(h) * M, slice_bytes, b);
+  };
   if constexpr (HALF) {
     // the launch's first half-step on the slice of its first step (phase 0
     // of the slice barrier), the other band from global memory
-    if (lead) bulk_load(ph, d.phasor + size_t(d.n_begin) * N + size_t(h) * M, slice_bytes, bar);
+    if (lead) fetch(d.n_begin, ph, 0, bar);
     float2 q[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) q[j] = d.state[(band ^ 1) * N + 4 * (t + j * T) + h];
     if (!mbar_wait(bar, 0u)) timed_out = true;
+    const SepHead sh = sep ? sep_head(srow0) : SepHead{};
+    auto first_half = [&](auto S) {
+      constexpr bool SEP = decltype(S)::value;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = couple_cell(v[j], q[j], ph[t + j * T], band, am1, bb);
+      for (int j = 0; j < 16; ++j) {
+        const int m = t + j * T;
+        v[j] = couple_cell(v[j], q[j], slice_at<SEP>(ph, sh, m, 4 * m + h), band, am1,
+                           slice_b<SEP>(bb, sh, band));
+      }
+    };
+    if (sep) first_half(BoolC<true>{});
+    else first_half(BoolC<false>{});
   }
 
   for (int it = 0; it < steps; ++it) {
@@ -289,8 +314,8 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
     __syncthreads();
     if (lead) {
       // (second order: phase it + 1, the launch's first half-step took 0)
-      bulk_load(ph, d.phasor + size_t(n) * N + size_t(h) * M, slice_bytes, bar);
-      if (HALF && it + 1 < steps)
+      fetch(n, ph, 0, bar);
+      if (HALF && !sep && it + 1 < steps)
         bulk_prefetch_l2(d.phasor + size_t(n + 1) * N + size_t(h) * M, slice_bytes);
       mbar_expect_tx(gbar, 3u * uint32_t(M) * 8u + ((part_due && h == 0) ? 24u : 0u));
       if (part_due) {
@@ -303,7 +328,9 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
     dft<16, false, EX>(v);
     f2_twiddle<false>(v, w1);
     f2_store<L, 1>(buf, v, t);
-    __syncthreads();
+    // (passes 1 and 2 of warp w address positions [512 w, 512 w + 512) only:
+    // the barriers between them are the warp's)
+    __syncwarp();
     f2_load<L, NP - 1>(buf, v, t);
     dft<16, false, EX>(v);                       // v[j] = F_h[k_j]
     // the peers have read our previous F before we overwrite their slots
@@ -368,12 +395,11 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
       // its sender is released after them
 #pragma unroll
       for (int e = HALF ? 1 : 0; e < 3; ++e) mbar_arrive_remote(free_to[e]);
-      if (HALF && it + 1 < steps)
-        bulk_load(gx, d.phasor + size_t(n + 1) * N + size_t(h) * M, slice_bytes, bar + 1);
+      if (HALF && it + 1 < steps) fetch(n + 1, gx, 1, bar + 1);
     }
     dft<16, true, EX>(v);
     f2_store<L, NP - 1>(buf, v, t);
-    __syncthreads();
+    __syncwarp();
     f2_load<L, 1>(buf, v, t);
     f2_twiddle<true>(v, w1);
     dft<16, true, EX>(v);
@@ -398,7 +424,9 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
       if (!timed_out && !mbar_wait(bar, uint32_t((it + 1) & 1))) timed_out = true;
       if (next && !timed_out && !mbar_wait(bar + 1, uint32_t(it & 1))) timed_out = true;
       const float2* ci = cb + half * M;
-      const float2* phn = gx;                    // slot 0: step n + 1's slice
+      const float2* phn = sep ? ph : gx;         // slot 0: step n + 1's slice
+      const SepHead shc = sep ? sep_head(srow0) : SepHead{};
+      const SepHead shn = (sep && next) ? sep_head(srow0 + 1) : SepHead{};
       const float2 g = rec ? *recph : make_float2(1.f, 0.f);
       const int slot = rec ? (n + 1) / d.record_every - 1 : 0;
       float2* r0 = (rec && d.records) ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
@@ -407,29 +435,36 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
       __syncthreads();
 #pragma unroll
       for (int j = 0; j < 16; ++j) buf[t + j * T] = v[j];
+      auto three_halves = [&](auto S) {
+        constexpr bool SEP = decltype(S)::value;
+        const float2 bc = slice_b<SEP>(bb, shc, band), bo = slice_b<SEP>(bb, shc, band ^ 1);
+        const float2 bn = slice_b<SEP>(bb, shn, band);
 #pragma unroll 1
-      for (int pp = 0; pp < 8; ++pp) {
-        const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
+        for (int pp = 0; pp < 8; ++pp) {
+          const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int j = 2 * pp + k;
-          const int cell = t + j * T;
-          const float2 p = buf[cell], q = k ? make_float2(q2.z, q2.w) : make_float2(q2.x, q2.y);
-          const float2 e = ph[cell];
-          float2 cc = couple_cell(p, q, e, band, am1, bb);   // step it, second half
-          if (rec) {
-            s = pow_acc(s, cc);
-            if (r0)   // records in natural order
-              r0[4 * cell + h] =
-                  make_float2(fmaf(cc.x, g.x, -(cc.y * g.y)), fmaf(cc.x, g.y, cc.y * g.x));
+          for (int k = 0; k < 2; ++k) {
+            const int j = 2 * pp + k;
+            const int cell = t + j * T;
+            const float2 p = buf[cell], q = k ? make_float2(q2.z, q2.w) : make_float2(q2.x, q2.y);
+            const float2 e = slice_at<SEP>(ph, shc, cell, 4 * cell + h);
+            float2 cc = couple_cell(p, q, e, band, am1, bc);   // step it, second half
+            if (rec) {
+              s = pow_acc(s, cc);
+              if (r0)   // records in natural order
+                r0[4 * cell + h] =
+                    make_float2(fmaf(cc.x, g.x, -(cc.y * g.y)), fmaf(cc.x, g.y, cc.y * g.x));
+            }
+            if (next) {   // step it + 1, first half, with the other band's value
+              const float2 co = couple_cell(q, p, e, band ^ 1, am1, bo);
+              cc = couple_cell(cc, co, slice_at<SEP>(phn, shn, cell, 4 * cell + h), band, am1, bn);
+            }
+            buf[cell] = cc;
           }
-          if (next) {   // step it + 1, first half, with the other band's value
-            const float2 co = couple_cell(q, p, e, band ^ 1, am1, bb);
-            cc = couple_cell(cc, co, phn[cell], band, am1, bb);
-          }
-          buf[cell] = cc;
         }
-      }
+      };
+      if (sep) three_halves(BoolC<true>{});
+      else three_halves(BoolC<false>{});
 #pragma unroll
       for (int j = 0; j < 16; ++j) v[j] = buf[t + j * T];
       __syncthreads();
@@ -443,13 +478,22 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
     } else {
     if (!timed_out && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
     const float2* ci = cb + half * M;
+    const SepHead sh = sep ? sep_head(srow0) : SepHead{};
+    auto couple_all = [&](auto S) {
+      constexpr bool SEP = decltype(S)::value;
+      const float2 bs = slice_b<SEP>(bb, sh, band);
 #pragma unroll
-    for (int pp = 0; pp < 8; ++pp) {
-      const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
-      v[2 * pp] = couple_cell(v[2 * pp], make_float2(q2.x, q2.y), ph[t + 2 * pp * T], band, am1, bb);
-      v[2 * pp + 1] =
-          couple_cell(v[2 * pp + 1], make_float2(q2.z, q2.w), ph[t + (2 * pp + 1) * T], band, am1, bb);
-    }
+      for (int pp = 0; pp < 8; ++pp) {
+        const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
+        const int m0 = t + 2 * pp * T, m1 = t + (2 * pp + 1) * T;
+        v[2 * pp] = couple_cell(v[2 * pp], make_float2(q2.x, q2.y),
+                                slice_at<SEP>(ph, sh, m0, 4 * m0 + h), band, am1, bs);
+        v[2 * pp + 1] = couple_cell(v[2 * pp + 1], make_float2(q2.z, q2.w),
+                                    slice_at<SEP>(ph, sh, m1, 4 * m1 + h), band, am1, bs);
+      }
+    };
+    if (sep) couple_all(BoolC<true>{});
+    else couple_all(BoolC<false>{});
 
     if (rec) {
       const int slot = (n + 1) / d.record_every - 1;

@@ -56,7 +56,9 @@ struct FusedCfg {
   static constexpr int OFF_MBAR = OFF_PH + ROWS * PHB * N * 8;       // [ROWS][PHB] u64
   static constexpr int OFF_RECPH = OFF_MBAR + ROWS * PHB * 8;        // [ROWS] float2
   static constexpr int OFF_RED = OFF_RECPH + ROWS * 8;               // [ROWS][WARPS][2] double
-  static constexpr int SMEM = OFF_RED + ROWS * WARPS_PER_ROW * 2 * 8;
+  static constexpr int OFF_SROW =                                    // [ROWS][PHB] row heads
+      (OFF_RED + ROWS * WARPS_PER_ROW * 2 * 8 + 15) / 16 * 16;
+  static constexpr int SMEM = OFF_SROW + ROWS * PHB * 16;
   // layout checks: fits one SM (227 KB); bulk-copy and 16-byte store
   // targets 16-byte aligned; mbarriers 8-byte aligned
   static_assert(SMEM <= 232448, "fits one SM");
@@ -104,6 +106,71 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src,
 __device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
+
+// ---- separable slices ----------------------------------------------------
+// Rows of a plan whose slices take the separable form (bent or unstrained
+// slab crystals; SepRow) keep the column phasors of their points in the
+// slice buffer for the whole launch and fetch, per step, only the first 16
+// bytes of the step's row (one bulk copy on the slice barrier, in place of
+// the slice): the row's phase term and its inside interval [lo, hi).  The
+// cell's phasor e = col * row enters the coupling only through b e (band +)
+// and b conj(e) (band -), so the row phasor is folded into the coupling
+// coefficient once per step, (b row) col and (b conj(row)) conj(col): per
+// cell the same multiply count as with the stream, the product rounded in
+// another order (the two forms agree to FP32 rounding).
+constexpr uint32_t kSepHeadBytes = 16;
+
+struct SepHead {
+  float2 ph;
+  int lo, hi;
+};
+
+__device__ __forceinline__ SepHead sep_head(const float4* slot) {
+  const float4 h = *slot;
+  return {make_float2(h.x, h.y), __float_as_int(h.z), __float_as_int(h.w)};
+}
+
+// The cell's column phasor inside [lo, hi) (natural column j), (0, 0) outside.
+__device__ __forceinline__ float2 sep_cell(const SepHead& h, float2 col, int j) {
+  const bool in = (j >= h.lo) & (j < h.hi);
+  return in ? col : make_float2(0.f, 0.f);
+}
+
+// b row (band 0) or b conj(row) (band 1): the coupling coefficient of the
+// step with the row phasor folded in.
+__device__ __forceinline__ float2 sep_b(float2 bb, const SepHead& h, int band) {
+  const float2 r = band ? make_float2(h.ph.x, -h.ph.y) : h.ph;
+  return make_float2(fmaf(bb.x, r.x, -(bb.y * r.y)), fmaf(bb.x, r.y, bb.y * r.x));
+}
+
+// What the coupling of stream position c (natural column j) multiplies by b:
+// the slice's phasor, or (SEP) the column phasor ph[c] inside the interval.
+template <bool SEP>
+__device__ __forceinline__ float2 slice_at(const float2* ph, const SepHead& sh, int c, int j) {
+  if constexpr (SEP) return sep_cell(sh, ph[c], j);
+  else return ph[c];
+}
+
+// The coupling coefficient to go with slice_at<SEP> for band `band`.
+template <bool SEP>
+__device__ __forceinline__ float2 slice_b(float2 bb, const SepHead& sh, int band) {
+  if constexpr (SEP) return sep_b(bb, sh, band);
+  else return bb;
+}
+
+// Barrier between two FFT passes: the warp's own when both passes of every
+// warp address only positions that warp owns (WARP), else the CTA's.
+template <bool WARP>
+__device__ __forceinline__ void tail_sync() {
+  if constexpr (WARP) __syncwarp();
+  else __syncthreads();
+}
+
+// Compile-time flag for generic lambdas that run a loop in both slice forms.
+template <bool B>
+struct BoolC {
+  static constexpr bool value = B;
+};
 
 // Poll limit of every bounded mbarrier wait: a try_wait that finds the phase
 // incomplete suspends the thread for about 4 us on GB300, so the limit is
@@ -247,24 +314,30 @@ __device__ __forceinline__ void last_pass(float2* v0, float2* v1, int t,
 
 // Coupling of Eq. fov10 on this thread's cells of both bands, coefficients
 // (a - 1, b) of the (fractional) step, e the cells' strain phasors.
+// Separable slices (sr != null): ph holds the column phasors, sr this
+// step's row head.
 template <int LOGN>
-__device__ __forceinline__ void couple_both(float2* v0, float2* v1, const float2* ph, int t,
-                                            float2 am1, float2 bb) {
+__device__ __forceinline__ void couple_both(float2* v0, float2* v1, const float2* ph,
+                                            const float4* sr, int t, float2 am1, float2 bb) {
   using C = FusedCfg<LOGN>;
   constexpr int T = C::T, R0 = C::radix(0), G0 = C::groups(0), S0 = C::stride(0);
+  SepHead sh{};
+  if (sr) sh = sep_head(sr);
+  // b for b e and for b conj(e) (separable: with the row phasor folded in)
+  const float2 b0 = sr ? sep_b(bb, sh, 0) : bb, b1 = sr ? sep_b(bb, sh, 1) : bb;
 #pragma unroll
   for (int i = 0; i < G0; ++i)
 #pragma unroll
     for (int j = 0; j < R0; ++j) {
       const int pos = (t + i * T) + j * S0;
-      const float2 e = ph[pos];
+      const float2 e = sr ? sep_cell(sh, ph[pos], pos) : ph[pos];
       const bool inside = (e.x != 0.f) | (e.y != 0.f);
       const float ax = inside ? am1.x : 0.f, ay = inside ? am1.y : 0.f;
       // b e and b conj(e)
-      const float2 bp = make_float2(fmaf(bb.x, e.x, -(bb.y * e.y)),
-                                    fmaf(bb.x, e.y, bb.y * e.x));
-      const float2 bm = make_float2(fmaf(bb.x, e.x, bb.y * e.y),
-                                    fmaf(bb.y, e.x, -(bb.x * e.y)));
+      const float2 bp = make_float2(fmaf(b0.x, e.x, -(b0.y * e.y)),
+                                    fmaf(b0.x, e.y, b0.y * e.x));
+      const float2 bm = make_float2(fmaf(b1.x, e.x, b1.y * e.y),
+                                    fmaf(b1.y, e.x, -(b1.x * e.y)));
       const float2 p = v0[i * R0 + j], m = v1[i * R0 + j];
       float px = fmaf(ax, p.x, p.x);
       px = fmaf(-ay, p.y, px);
@@ -317,12 +390,17 @@ __global__ void __launch_bounds__(FusedCfg<LOGN>::THREADS)
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::OFF_MBAR) + rl * (HALF ? 2 : 1);
   float2* recph = reinterpret_cast<float2*>(smem + C::OFF_RECPH) + rl;
   double* red = reinterpret_cast<double*>(smem + C::OFF_RED) + rl * C::WARPS_PER_ROW * 2;
+  float4* srow0 = reinterpret_cast<float4*>(smem + C::OFF_SROW) + rl * (HALF ? 2 : 1);
+  const bool sep = d.srows != nullptr;
 
   if (t == 0) {
     mbar_init(bar);
     if constexpr (HALF) mbar_init(bar + 1);
   }
   fence_mbar_init();
+  // separable slices: the column phasors stay in buffer 0 for the launch
+  if (sep && active)
+    for (int k = t; k < N; k += T) ph0[k] = __ldg(&d.scols[k]);
 
   // Registers: pass-0 groups of both bands, natural positions gi + j*S0.
   float2 v0[C::E], v1[C::E];
@@ -341,10 +419,14 @@ __global__ void __launch_bounds__(FusedCfg<LOGN>::THREADS)
   const uint32_t slice_bytes = uint32_t(N) * 8u;
   int pending_slot = -1;            // record whose powers await reduction
   bool timed_out = false;
+  // slice of step n into buffer `slot` (separable: the row head only)
+  auto fetch = [&](int n, int slot) {
+    if (sep) bulk_load(srow0 + slot, d.srows + n, kSepHeadBytes, bar + slot);
+    else bulk_load(ph0 + slot * N, d.phasor + size_t(n) * N, slice_bytes, bar + slot);
+  };
   if constexpr (HALF) {
     // the first step's slice; later ones are fetched a step ahead
-    if (t == 0 && active && steps > 0)
-      bulk_load(ph0, d.phasor + size_t(d.n_begin) * N, slice_bytes, bar);
+    if (t == 0 && active && steps > 0) fetch(d.n_begin, 0);
   }
 
   // Error path: a thread whose bounded wait expires raises s_abort; at the
@@ -358,7 +440,9 @@ __global__ void __launch_bounds__(FusedCfg<LOGN>::THREADS)
       if (timed_out) break;
     }
     const int n = d.n_begin + it;
-    float2* ph = ph0 + (HALF ? (it & 1) * N : 0);
+    // the step's slice (separable: the column phasors and the row head)
+    const float2* ph = ph0 + ((HALF && !sep) ? (it & 1) * N : 0);
+    const float4* sr = sep ? srow0 + (HALF ? (it & 1) : 0) : nullptr;
     const bool rec = active && d.record_every > 0 &&
                      ((n + 1) % d.record_every) == 0 &&
                      (d.records != nullptr || d.powers != nullptr);
@@ -373,9 +457,7 @@ __global__ void __launch_bounds__(FusedCfg<LOGN>::THREADS)
       // one thread per row (N <= 16) has no barrier in the step: it is past
       // its own couplings of step it - 1, so the other buffer is free
       if constexpr (NP == 1) {
-        if (t == 0 && active && it + 1 < steps)
-          bulk_load(ph0 + ((it + 1) & 1) * N, d.phasor + size_t(n + 1) * N, slice_bytes,
-                    bar + ((it + 1) & 1));
+        if (t == 0 && active && it + 1 < steps) fetch(n + 1, (it + 1) & 1);
       }
       // the leading coupling, on this step's slice
       if (active) {
@@ -383,7 +465,7 @@ __global__ void __launch_bounds__(FusedCfg<LOGN>::THREADS)
           timed_out = true;
           s_abort = 1;
         }
-        couple_both<LOGN>(v0, v1, ph, t, d.am1h, d.bh);
+        couple_both<LOGN>(v0, v1, ph, sr, t, d.am1h, d.bh);
       }
     }
 
@@ -394,7 +476,7 @@ __global__ void __launch_bounds__(FusedCfg<LOGN>::THREADS)
       const float2* tab = d.prop + ((SCH == 2 && sg == 1) ? 2 * N : 0);
       if constexpr (NP == 1) {
         if constexpr (!HALF) {
-          if (t == 0 && active) bulk_load(ph, d.phasor + size_t(n) * N, slice_bytes, bar);
+          if (t == 0 && active) fetch(n, 0);
         }
         last_pass<LOGN>(v0, v1, t, tab);
       } else {
@@ -417,11 +499,9 @@ __global__ void __launch_bounds__(FusedCfg<LOGN>::THREADS)
           // every thread of the row has finished the previous step's
           // couplings: the slice buffer they read is free
           if constexpr (HALF) {
-            if (t == 0 && active && it + 1 < steps)
-              bulk_load(ph0 + ((it + 1) & 1) * N, d.phasor + size_t(n + 1) * N, slice_bytes,
-                        bar + ((it + 1) & 1));
+            if (t == 0 && active && it + 1 < steps) fetch(n + 1, (it + 1) & 1);
           } else {
-            if (t == 0 && active) bulk_load(ph, d.phasor + size_t(n) * N, slice_bytes, bar);
+            if (t == 0 && active) fetch(n, 0);
           }
           if (t == 0 && pending_slot >= 0) {
             double s0 = 0.0, s1 = 0.0;
@@ -457,12 +537,12 @@ __global__ void __launch_bounds__(FusedCfg<LOGN>::THREADS)
             timed_out = true;
             s_abort = 1;
           }
-          couple_both<LOGN>(v0, v1, ph, t, d.am1, d.b);
+          couple_both<LOGN>(v0, v1, ph, sr, t, d.am1, d.b);
         } else if constexpr (SCH == 1) {
-          couple_both<LOGN>(v0, v1, ph, t, d.am1h, d.bh);
+          couple_both<LOGN>(v0, v1, ph, sr, t, d.am1h, d.bh);
         } else {
           const bool last = sg == STAGES - 1;
-          couple_both<LOGN>(v0, v1, ph, t, last ? d.am1h : d.am1, last ? d.bh : d.b);
+          couple_both<LOGN>(v0, v1, ph, sr, t, last ? d.am1h : d.am1, last ? d.bh : d.b);
         }
       }
     }   // stages

@@ -95,7 +95,8 @@ __global__ void omega_to_t_kernel(const C* __restrict__ in, C* __restrict__ out,
 // bh) of each row: psi_+ <- psi_+ + (a-1) psi_+ + b e psi_-, psi_- <- psi_- +
 // (a-1) psi_- + b conj(e) psi_+ (old values on the right) inside the crystal
 // (e != 0), e the slice of step n.  One thread per cell; split plans
-// (nx >= 8192) store the slice per part: column x = P m + h at h (nx/P) + m.
+// (nx >= 8192) store the slice per part: column x = P m + h at h (nx/P) + m
+// (the column phasors of separable slices likewise).
 __global__ void couple_only_kernel(const RowDescF32* __restrict__ rows, int nb, int nx, int n,
                                    int log_parts) {
   const int row = blockIdx.y;
@@ -104,12 +105,24 @@ __global__ void couple_only_kernel(const RowDescF32* __restrict__ rows, int nb, 
   const RowDescF32 d = rows[row];
   const int m_len = nx >> log_parts;
   const int h = x & ((1 << log_parts) - 1), m = x >> log_parts;
-  const float2 e = d.phasor[size_t(n) * nx + size_t(h) * m_len + m];
+  const float2 am1 = d.am1h;
+  float2 e, b0 = d.bh, b1 = d.bh;   // b e = b0 e, b conj(e) = b1 conj(e)
+  if (d.srows) {
+    // separable slices: e the column phasor inside [lo0, hi0), the row
+    // phasor folded into b (b row, b conj(row)) as in the fused kernels
+    const SepRow* r = d.srows + n;
+    if (x < r->lo0 || x >= r->hi0) return;
+    e = d.scols[size_t(h) * m_len + m];
+    const float2 rp = r->ph, bb = d.bh;
+    b0 = make_float2(fmaf(bb.x, rp.x, -(bb.y * rp.y)), fmaf(bb.x, rp.y, bb.y * rp.x));
+    b1 = make_float2(fmaf(bb.x, rp.x, bb.y * rp.y), fmaf(bb.x, -rp.y, bb.y * rp.x));
+  } else {
+    e = d.phasor[size_t(n) * nx + size_t(h) * m_len + m];
+  }
   if (e.x == 0.f && e.y == 0.f) return;
   const float2 p = d.state[x], q = d.state[nx + x];
-  const float2 am1 = d.am1h, bb = d.bh;
-  const float cx = fmaf(bb.x, e.x, -(bb.y * e.y)), cy = fmaf(bb.x, e.y, bb.y * e.x);   // b e
-  const float dx = fmaf(bb.x, e.x, bb.y * e.y), dy = fmaf(bb.y, e.x, -(bb.x * e.y));   // b conj(e)
+  const float cx = fmaf(b0.x, e.x, -(b0.y * e.y)), cy = fmaf(b0.x, e.y, b0.y * e.x);   // b e
+  const float dx = fmaf(b1.x, e.x, b1.y * e.y), dy = fmaf(b1.y, e.x, -(b1.x * e.y));   // b conj(e)
   float rx = fmaf(am1.x, p.x, p.x);
   rx = fmaf(-am1.y, p.y, rx);
   rx = fmaf(cx, q.x, rx);

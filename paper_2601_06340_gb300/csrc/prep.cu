@@ -30,7 +30,17 @@
 //     error about |h b / 2 pi| x 1e-6 rad).
 // This removes the per-cell FP64 work, which on this GPU costs far more than
 // the march of the same cells.
+//
+// Separable form: a vacuum, bulk or slab crystal (one inside interval per
+// step) with no strain or the bent-crystal strain needs no per-cell data at
+// all.  Such FP32 2D plans keep the rows of fast_rows_kernel (the interval
+// and the row phasor, SepRow) and the column phasors (in the stream's
+// order), and the fused kernels form each cell as they couple -- the same
+// FP32 product and the same decision as sep_cells_kernel, which writes the
+// stream of the same crystal bit for bit (for bpm_fetch_slices).  A bent
+// 16384 x 20000 request then holds 2 MB of slices instead of 2.6 GB.
 #include <cmath>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -184,7 +194,7 @@ __global__ void prep3d_kernel(PrepParams p, Prep3D q) {
 }
 
 constexpr int kMaxPolyV = 16;
-constexpr int kMaxIv = kMaxPolyV / 2 + 1;
+static_assert(kMaxIv == kMaxPolyV / 2 + 1, "intervals of a row cut by the polygon");
 
 struct FastParams {
   int nx, nz, parts;
@@ -195,13 +205,6 @@ struct FastParams {
   double poly[2 * kMaxPolyV];
   int strain_kind;
   double p0, p1, p2, p3, h;
-};
-
-struct RowInfo {      // one z-step
-  int nint;
-  int lo[kMaxIv], hi[kMaxIv];   // inside columns: the union of [lo, hi)
-  float2 ph;                    // bent: exp(i h nu z'^2 / (2R)), reduced in FP64
-  float zp;                     // dislocation: z - z_core
 };
 
 struct ColInfo {      // one column
@@ -234,11 +237,14 @@ __device__ double unit_phase(double a) {   // a reduced to [-pi, pi] in FP64
   return a - 6.283185307179586 * rint(a * 0.15915494309189535);
 }
 
-__global__ void fast_rows_kernel(FastParams p, RowInfo* rows) {
+// One thread per z-step: the row's inside intervals (the union of [lo, hi))
+// and its phase term.
+__global__ void fast_rows_kernel(FastParams p, SepRow* rows) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= p.nz) return;
   const double z = __dmul_rn(double(n), p.dz);
-  RowInfo r{};
+  SepRow r{};
+  r.ph = make_float2(1.f, 0.f);
   int slo = 0, shi = 0;   // slab (or whole-row) interval
   if (p.crystal_kind == BPM_CRYSTAL_BULK) {
     shi = p.nx;
@@ -292,6 +298,10 @@ __global__ void fast_rows_kernel(FastParams p, RowInfo* rows) {
     r.lo[0] = slo;
     r.hi[0] = shi;
   }
+  if (r.nint > 0) {
+    r.lo0 = r.lo[0];
+    r.hi0 = r.hi[0];
+  }
   if (p.strain_kind == BPM_STRAIN_BENT) {
     const double zp = z - p.p3;
     const double b = unit_phase(p.h * (p.p1 * (zp * zp) / (2.0 * p.p0)));
@@ -304,11 +314,15 @@ __global__ void fast_rows_kernel(FastParams p, RowInfo* rows) {
   rows[n] = r;
 }
 
-__global__ void fast_cols_kernel(FastParams p, ColInfo* cols) {
+// One thread per column: its phase term (cols, natural order) and, for the
+// separable form, the column phasor at the stream's position of column j,
+// (j mod parts) m + j div parts (scols).  Either output may be null.
+__global__ void fast_cols_kernel(FastParams p, ColInfo* cols, float2* scols) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= p.nx) return;
   const double x = x_of(p, j);
   ColInfo c{};
+  c.ph = make_float2(1.f, 0.f);
   if (p.strain_kind == BPM_STRAIN_BENT) {
     const double xp = x - p.p2;
     const double a = unit_phase(p.h * ((xp * xp) / (2.0 * p.p0)));
@@ -318,7 +332,36 @@ __global__ void fast_cols_kernel(FastParams p, ColInfo* cols) {
   } else if (p.strain_kind == BPM_STRAIN_EDGE_DISLOCATION) {
     c.xp = float(x - p.p2);
   }
-  cols[j] = c;
+  if (cols) cols[j] = c;
+  if (scols) {
+    const int m = p.nx / p.parts;
+    scols[(j % p.parts) * m + j / p.parts] = c.ph;
+  }
+}
+
+// The per-cell stream of the separable form: position o of row n holds
+// column j = (o mod m) parts + o div m; its phasor col[j] row[n] inside the
+// row's intervals, (0, 0) outside -- the product and the decisions the fused
+// kernels form from the same tables, and the values fast_cells_kernel
+// writes for a bent or unstrained crystal.
+__global__ void __launch_bounds__(256)
+    sep_cells_kernel(const SepRow* __restrict__ rows, const float2* __restrict__ scols, int nx,
+                     int nz, int parts, float2* __restrict__ out) {
+  const int m = nx / parts;
+  for (int n = blockIdx.y; n < nz; n += gridDim.y) {
+    const SepRow* r = rows + n;
+    const int nint = __ldg(&r->nint);
+    const float2 rp = __ldg(&r->ph);
+    for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < nx; o += gridDim.x * blockDim.x) {
+      const int j = (o % m) * parts + o / m;
+      bool in = false;
+      for (int k = 0; k < nint; ++k) in |= (j >= __ldg(&r->lo[k])) & (j < __ldg(&r->hi[k]));
+      const float2 a = __ldg(&scols[o]);
+      out[size_t(n) * nx + o] =
+          in ? make_float2(fmaf(a.x, rp.x, -(a.y * rp.y)), fmaf(a.x, rp.y, a.y * rp.x))
+             : make_float2(0.f, 0.f);
+    }
+  }
 }
 
 // Every thread writes 4 consecutive outputs of a row (two 16-byte stores);
@@ -328,14 +371,14 @@ __global__ void fast_cols_kernel(FastParams p, ColInfo* cols) {
 // j = (o mod m) parts + o div m, m = nx / parts (a power of two).
 template <int STRAIN>
 __global__ void __launch_bounds__(256)
-    fast_cells_kernel(FastParams p, const RowInfo* __restrict__ rows,
+    fast_cells_kernel(FastParams p, const SepRow* __restrict__ rows,
                       const ColInfo* __restrict__ cols, float k_disl, float q_disl, int log_m,
                       float2* __restrict__ out) {
   const int m_mask = (1 << log_m) - 1;
   const int o0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
   if (o0 >= p.nx) return;
   for (int n = blockIdx.y; n < p.nz; n += gridDim.y) {
-    const RowInfo* r = rows + n;
+    const SepRow* r = rows + n;
     const int nint = __ldg(&r->nint);
     float2 v[4];
 #pragma unroll
@@ -380,7 +423,9 @@ bool fast_path_applies(const bpm_plan_s* plan) {
                         sk == BPM_STRAIN_EDGE_DISLOCATION);
 }
 
-int prepare_fast(bpm_plan_s* plan, const PrepParams& q, cudaStream_t st, bool sync) {
+// sep: write the separable form (rows and column phasors) to plan->d_sep
+// instead of the per-cell stream.
+int prepare_fast(bpm_plan_s* plan, const PrepParams& q, cudaStream_t st, bool sync, bool sep) {
   FastParams p{};
   p.nx = q.nx;
   p.nz = q.nz;
@@ -402,13 +447,25 @@ int prepare_fast(bpm_plan_s* plan, const PrepParams& q, cudaStream_t st, bool sy
   p.p2 = q.p2;
   p.p3 = q.p3;
   p.h = q.h;
-  RowInfo* d_rows = nullptr;
+  SepRow* d_rows = nullptr;
   ColInfo* d_cols = nullptr;
-  cudaError_t e = cudaMallocAsync(&d_rows, size_t(p.nz) * sizeof(RowInfo), st);
+  cudaError_t e = cudaSuccess;
+  if (sep) {
+    d_rows = static_cast<SepRow*>(plan->d_sep);
+    float2* d_scols = reinterpret_cast<float2*>(d_rows + p.nz);
+    fast_rows_kernel<<<(p.nz + 127) / 128, 128, 0, st>>>(p, d_rows);
+    fast_cols_kernel<<<(p.nx + 255) / 256, 256, 0, st>>>(p, nullptr, d_scols);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && sync) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "slice preparation (separable form)");
+    plan->slices_dirty = false;
+    return BPM_OK;
+  }
+  e = cudaMallocAsync(&d_rows, size_t(p.nz) * sizeof(SepRow), st);
   if (e == cudaSuccess) e = cudaMallocAsync(&d_cols, size_t(p.nx) * sizeof(ColInfo), st);
   if (e == cudaSuccess) {
     fast_rows_kernel<<<(p.nz + 127) / 128, 128, 0, st>>>(p, d_rows);
-    fast_cols_kernel<<<(p.nx + 255) / 256, 256, 0, st>>>(p, d_cols);
+    fast_cols_kernel<<<(p.nx + 255) / 256, 256, 0, st>>>(p, d_cols, nullptr);
     const float k_disl = float(p.h * p.p0 / 6.283185307179586);
     const float q_disl = float(1.0 / (2.0 * (1.0 - p.p1)));
     const int threads = 256;
@@ -439,19 +496,61 @@ int prepare_fast(bpm_plan_s* plan, const PrepParams& q, cudaStream_t st, bool sy
 
 }  // namespace
 
+bool sep_slices_apply(const bpm_plan_s* plan) {
+  if (plan->precision != BPM_FP32_FUSED || plan->ny > 1) return false;
+  // one inside interval per step at most (the kernels test [lo0, hi0))
+  const int k = plan->crystal_kind;
+  if (k != BPM_CRYSTAL_VACUUM && k != BPM_CRYSTAL_BULK && k != BPM_CRYSTAL_SLAB) return false;
+  if (plan->strain_kind != BPM_STRAIN_NONE && plan->strain_kind != BPM_STRAIN_BENT) return false;
+  const char* e = std::getenv("BPM_SLICE_STREAM");
+  if (e && e[0] == '1') return false;
+  if (e && e[0] == '0') return true;
+  // Rows that each get two SMs or more (single solves, served requests,
+  // small batches) march latency-bound: the separable form saves the stream
+  // (memory, preparation, DRAM) and measured 3 % faster on the 4096 x 8000
+  // solve.  Batches that fill the GPU are bound by instruction issue, share
+  // one stream between all rows, and ran 8 % slower with the per-cell
+  // interval test (256 rows, N = 2048 and 4096): they keep the stream.
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    sms = v > 0 ? v : 1;
+  }
+  return 2 * plan->nb <= sms;
+}
+
+size_t slice_data_bytes(const bpm_plan_s* plan) {
+  if (sep_slices_apply(plan)) return sep_bytes(plan);
+  return plane_of(plan) * plan->nz * (plan->precision == BPM_FP32_FUSED ? 8 : 16);
+}
+
+int expand_sep_slices(const bpm_plan_s* plan, float2* out, cudaStream_t st) {
+  if (!plan->sep_slices || !plan->d_sep) return fail(BPM_ERR_INVALID, "no separable slices");
+  const int parts = plan->logn >= kSplitLogN ? plan->nx >> 12 : 1;
+  const SepRow* rows = static_cast<const SepRow*>(plan->d_sep);
+  const float2* scols = reinterpret_cast<const float2*>(rows + plan->nz);
+  dim3 grid((plan->nx + 255) / 256, plan->nz < 65535 ? plan->nz : 65535);
+  sep_cells_kernel<<<grid, 256, 0, st>>>(rows, scols, plan->nx, plan->nz, parts, out);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? BPM_OK : cuda_fail(e, "sep_cells_kernel");
+}
+
 int prepare_slices(bpm_plan_s* plan, cudaStream_t st, bool sync) {
   NvtxRange nvtx("bpm_prepare_slices");
-  const size_t phasor_bytes = plane_of(plan) * plan->nz *
-                              (plan->precision == BPM_FP32_FUSED ? 8 : 16);
-  if (!plan->d_phasor) {
-    cudaError_t ea = cudaMalloc(&plan->d_phasor, phasor_bytes);
+  const bool sep = sep_slices_apply(plan);
+  void** dst = sep ? &plan->d_sep : &plan->d_phasor;
+  if (!*dst) {
+    cudaError_t ea = cudaMalloc(dst, slice_data_bytes(plan));
     if (ea != cudaSuccess) {
-      plan->d_phasor = nullptr;
+      *dst = nullptr;
       cudaGetLastError();
       return fail(ea == cudaErrorMemoryAllocation ? BPM_ERR_OOM : BPM_ERR_CUDA,
                   "cudaMalloc(strain phasor): " + std::string(cudaGetErrorString(ea)));
     }
   }
+  plan->sep_slices = false;   // set again once the separable form is written
   PrepParams p{};
   p.nx = plan->nx;
   p.nz = plan->nz;
@@ -477,7 +576,12 @@ int prepare_slices(bpm_plan_s* plan, cudaStream_t st, bool sync) {
   if (plan->precision == BPM_FP32_FUSED && plan->logn >= kSplitLogN) p.parts = plan->nx >> 12;
   if (plan->precision == BPM_FP32_FUSED) p.out32 = static_cast<float2*>(plan->d_phasor);
   else p.out64 = static_cast<double2*>(plan->d_phasor);
-  if (plan->ny <= 1 && fast_path_applies(plan)) return prepare_fast(plan, p, st, sync);
+  if (sep) {
+    const int rc = prepare_fast(plan, p, st, sync, true);
+    plan->sep_slices = rc == BPM_OK;
+    return rc;
+  }
+  if (plan->ny <= 1 && fast_path_applies(plan)) return prepare_fast(plan, p, st, sync, false);
 
   uint8_t* d_mask = nullptr;
   double* d_poly = nullptr;

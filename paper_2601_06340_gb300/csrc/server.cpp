@@ -3,7 +3,9 @@
 // A worker thread owns the device side.  Requests wait in arrival order and
 // are admitted while the number of active requests and their device
 // footprint (state, staging, records, powers and, if the plan has none yet,
-// its strain-phasor stream) stay within the configured limits.  Active
+// its slice memory: the strain-phasor stream, or the separable rows and
+// column phasors of a bent or unstrained analytic crystal) stay within the
+// configured limits.  Active
 // requests are grouped into buckets by transform size (FP32) -- FP64
 // requests get a bucket each -- and every bucket runs its own pipeline on
 // its own stream.  A bucket advances its members in batches: a batch takes
@@ -66,7 +68,7 @@ struct Request {
   double t_submit = 0, t_admit = 0, t_done = 0;
   // device side
   size_t footprint = 0;
-  bool owns_phasor = false;
+  void** owned_slices = nullptr;   // the plan's slice memory this request allocated
   void* d_state = nullptr;     // c64 (FP32); FP64 requests march in their plan's state
   void* d_rec = nullptr;
   double* d_pow = nullptr;
@@ -138,6 +140,12 @@ Server& srv() {
 
 size_t csize_of(const bpm_plan_s* p) { return p->precision == BPM_FP32_FUSED ? 8 : 16; }
 
+// The plan holds device memory for its slices in the form it will prepare
+// (the per-cell stream, or the separable rows and columns).
+bool slices_resident(const bpm_plan_s* p) {
+  return sep_slices_apply(p) ? p->d_sep != nullptr : p->d_phasor != nullptr;
+}
+
 size_t footprint_of(const bpm_plan_s* p, bool need_rec) {
   const size_t n = p->nx, nb = p->nb, cs = csize_of(p);
   size_t b = nb * 2 * n * cs                       // state
@@ -145,7 +153,7 @@ size_t footprint_of(const bpm_plan_s* p, bool need_rec) {
              + nb * size_t(p->n_rec + 1) * 2 * 8   // powers
              + nb * 16;                            // phase factors
   if (need_rec) b += nb * size_t(p->n_rec) * 2 * n * cs;
-  if (!p->d_phasor) b += size_t(p->nz) * n * cs;
+  if (!slices_resident(p)) b += slice_data_bytes(p);
   return b;
 }
 
@@ -206,9 +214,10 @@ int admit_device(Server& s, Request& r) {
   };
   {
     std::lock_guard<std::mutex> lk(p->mu);
-    if (!p->d_phasor) {
-      A(&p->d_phasor, size_t(p->nz) * n * cs);
-      r.owns_phasor = (e == cudaSuccess);
+    if (!slices_resident(p)) {
+      void** dst = sep_slices_apply(p) ? &p->d_sep : &p->d_phasor;
+      A(dst, slice_data_bytes(p));
+      if (e == cudaSuccess) r.owned_slices = dst;
       p->slices_dirty = true;
     }
     if (e == cudaSuccess && p->slices_dirty) {
@@ -307,9 +316,9 @@ void finish_request(Server& s, const ReqPtr& r, int status, const std::string& m
   release(s, *r);
   {
     std::lock_guard<std::mutex> lk(r->plan->mu);
-    if (r->owns_phasor) {
-      cudaFreeAsync(r->plan->d_phasor, s.io_stream);
-      r->plan->d_phasor = nullptr;
+    if (r->owned_slices) {
+      cudaFreeAsync(*r->owned_slices, s.io_stream);
+      *r->owned_slices = nullptr;
       r->plan->slices_dirty = true;
     }
     r->plan->pending -= 1;

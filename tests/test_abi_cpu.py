@@ -94,6 +94,7 @@ def test_null_arguments_are_rejected(lib):
     assert lib.bpm_set_splitting(None, 1) == binding.BPM_ERR_INVALID
     assert lib.bpm_set_crystal_box(None, None) == binding.BPM_ERR_INVALID
     assert lib.bpm_launch_shape(None, None, None) == binding.BPM_ERR_INVALID
+    assert lib.bpm_slice_form(None, None, None) == binding.BPM_ERR_INVALID
     assert lib.bpm_selftest_wait_expiry(None, None) == binding.BPM_ERR_INVALID
     assert lib.bpm_device_status(None, None) == binding.BPM_ERR_INVALID
     assert lib.bpm_server_inject_launch_failure(1000, 1) == binding.BPM_ERR_INVALID

@@ -52,6 +52,13 @@ def test_20000_step_split_band_march_matches_oracle(bpm_lib, long_refs, nx, seed
     wl = _request(nx, seed)
     with binding.Plan(wl, FP32) as plan:
         out = plan.propagate()
+        form, nbytes = binding.bpm_slice_form(plan.handle)
+    # the bent request keeps separable slices (about 2 MB instead of the
+    # 1.3-2.6 GB per-cell stream), the dislocated one the stream
+    if wl.strain["kind"] == inputs.STRAIN_BENT:
+        assert (form, nbytes) == (1, NZ * 96 + nx * 8)
+    else:
+        assert (form, nbytes) == (0, NZ * nx * 8)
     ref = long_refs[(nx, seed)].result()
     errs = band_errors(out.psi, ref.psi, out.records, ref.records)
     assert max(errs) <= TOL_FP32, (nx, seed, errs)
