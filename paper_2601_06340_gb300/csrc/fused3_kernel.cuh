@@ -40,8 +40,8 @@ struct F3Cfg {
   static constexpr int OFF_X = OFF_BUF + PADN * 8;        // [2][N] exchange
   static constexpr int OFF_PH = OFF_X + 2 * N * 8;        // [PHB][N]
   static constexpr int OFF_MBAR = OFF_PH + PHB * N * 8;    // [PHB] strain slice barriers
-  static constexpr int OFF_XBAR = OFF_MBAR + 8 * PHB;      // [2] exchange barriers
-  static constexpr int OFF_RECPH = OFF_XBAR + 16;
+  static constexpr int OFF_XBAR = OFF_MBAR + 8 * PHB;      // [2][WARPS] exchange barriers
+  static constexpr int OFF_RECPH = OFF_XBAR + 16 * WARPS;
   static constexpr int OFF_RED = OFF_RECPH + 8;           // [WARPS] double
   static constexpr int OFF_SROW = (OFF_RED + WARPS * 8 + 15) / 16 * 16;   // [PHB] row heads
   static constexpr int SMEM = OFF_SROW + PHB * 16;
@@ -93,6 +93,35 @@ __device__ __forceinline__ float2 couple_cell(float2 p, float2 q, float2 e, int 
   ry = fmaf(cx, q.y, ry);
   ry = fmaf(cy, q.x, ry);
   return make_float2(rx, ry);
+}
+
+// couple_cell with the inside flag given (separable slices: e is the
+// column phasor, the flag the row's interval test).
+__device__ __forceinline__ float2 couple_cell_in(float2 p, float2 q, float2 e, bool inside,
+                                                 int band, float2 am1, float2 bb) {
+  if (band) e.y = -e.y;
+  const float ax = inside ? am1.x : 0.f, ay = inside ? am1.y : 0.f;
+  const float cx0 = fmaf(bb.x, e.x, -(bb.y * e.y)), cy0 = fmaf(bb.x, e.y, bb.y * e.x);
+  const float cx = inside ? cx0 : 0.f, cy = inside ? cy0 : 0.f;
+  float rx = fmaf(ax, p.x, p.x);
+  rx = fmaf(-ay, p.y, rx);
+  rx = fmaf(cx, q.x, rx);
+  rx = fmaf(-cy, q.y, rx);
+  float ry = fmaf(ax, p.y, p.y);
+  ry = fmaf(ay, p.x, ry);
+  ry = fmaf(cx, q.y, ry);
+  ry = fmaf(cy, q.x, ry);
+  return make_float2(rx, ry);
+}
+
+// One cell's coupling in either slice form: the stream's phasor ph[c], or
+// (SEP) the column phasor ph[c] with bit jj of the thread's interval mask.
+template <bool SEP>
+__device__ __forceinline__ float2 couple_at(float2 p, float2 q, const float2* ph, int c,
+                                            uint32_t msk, int jj, int band, float2 am1,
+                                            float2 bb) {
+  if constexpr (SEP) return couple_cell_in(p, q, ph[c], (msk >> jj) & 1u, band, am1, bb);
+  else return couple_cell(p, q, ph[c], band, am1, bb);
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
@@ -160,8 +189,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
   if (lead) {
     mbar_init(bar);
     if constexpr (HALF) mbar_init(bar + 1);
-    mbar_init(&xbar[0]);
-    mbar_init(&xbar[1]);
+    for (int i = 0; i < 2 * C::WARPS; ++i) mbar_init(&xbar[i]);
   }
   fence_mbar_init();
 
@@ -290,9 +318,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
     // send psi_p to the peer (asynchronous remote stores completing on the
     // peer's barrier of this parity); arm our own barrier for the peer's.
     const int half = it & 1;
-    if (lead) mbar_expect_tx(&xbar[half], uint32_t(N) * 8u);
+    // (per warp: thread t receives the slots of the peer's thread t)
+    if (lane == 0) mbar_expect_tx(&xbar[half * C::WARPS + warp], 32u * 16u * 8u);
     const uint32_t xo = xpeer + uint32_t(half * N) * 8u;
-    const uint32_t xbo = xbar_peer + uint32_t(half) * 8u;
+    const uint32_t xbo = xbar_peer + uint32_t(half * C::WARPS + warp) * 8u;
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = cadd(org[j], v[j]);
 #pragma unroll
@@ -300,7 +329,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
       st_async_v4(xo + uint32_t(xpair(pp, t, T)) * 8u, v[2 * pp], v[2 * pp + 1], xbo);
     // (after one expired wait a thread stops waiting, so a fault costs one
     // bounded wait, not one per step; the host reports BPM_ERR_TIMEOUT)
-    if (!timed_out && !mbar_wait_cluster(&xbar[half], uint32_t((it >> 1) & 1))) timed_out = true;
+    if (!timed_out && !mbar_wait_cluster(&xbar[half * C::WARPS + warp], uint32_t((it >> 1) & 1)))
+      timed_out = true;
 
     const float2* xi = xb + half * N;
     if constexpr (HALF) {

@@ -42,6 +42,9 @@ namespace bpm {
 // the band, psi_p across the bands) are asynchronous remote stores that
 // complete on the receiver's mbarrier (see fused3_kernel.cuh), double
 // buffered by step parity; no cluster-wide barrier runs inside the march.
+// Thread t sends and receives the slots of thread t, so each warp has its
+// own barrier per exchange and parity and waits only for the same warp of
+// the sender.
 // Buffer reuse: a half is rewritten two steps later, by a sender that has
 // by then received values the receiver computed from that half.
 // PHB: strain-slice buffers (2 for the second-order step, N = 4096 only)
@@ -63,9 +66,9 @@ struct F4ECfg {
   static constexpr int OFF_PH = OFF_C + 2 * M * 8;         // [PHB][PH] strain slices
   static constexpr int OFF_E1 = OFF_PH + PHB * PH * 8;     // [16][T] D(k_j + M)
   static constexpr int OFF_MBAR = OFF_E1 + M * 8;          // [2] strain-slice barriers
-  static constexpr int OFF_GBAR = OFF_MBAR + 16;           // [2] F barriers
-  static constexpr int OFF_CBAR = OFF_GBAR + 16;           // [2] psi_p barriers
-  static constexpr int OFF_PPEER = OFF_CBAR + 16;          // [2] peer's band-power part
+  static constexpr int OFF_GBAR = OFF_MBAR + 16;           // [2][WARPS] F barriers
+  static constexpr int OFF_CBAR = OFF_GBAR + 16 * WARPS;   // [2][WARPS] psi_p barriers
+  static constexpr int OFF_PPEER = OFF_CBAR + 16 * WARPS;  // [2] peer's band-power part
   static constexpr int OFF_RECPH = OFF_PPEER + 16;
   static constexpr int OFF_RED = OFF_RECPH + 8;            // [WARPS] double
   static constexpr int OFF_PART = OFF_RED + WARPS * 8;
@@ -168,10 +171,10 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
   if (lead) {
     mbar_init(bar);
     if constexpr (HALF) mbar_init(bar + 1);   // N = 8192: the next-slice copies
-    mbar_init(&gbar[0]);
-    mbar_init(&gbar[1]);
-    mbar_init(&cbar[0]);
-    mbar_init(&cbar[1]);
+    for (int i = 0; i < 2 * C::WARPS; ++i) {
+      mbar_init(&gbar[i]);
+      mbar_init(&cbar[i]);
+    }
   }
   fence_mbar_init();
 
@@ -281,14 +284,17 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
       } else {
         fetch(n, ph, 0, bar);
       }
-      mbar_expect_tx(&gbar[half], uint32_t(M) * 8u + (part_due ? 8u : 0u));
-      if (part_due) {
+      if (part_due) {   // rides on the peer's warp-0 F barrier
         double s = 0.0;
         for (int w = 0; w < C::WARPS; ++w) s += red[w];
         my_part = s;
-        st_async_f64(pp_peer + uint32_t(half) * 8u, s, gbar_peer + uint32_t(half) * 8u);
+        st_async_f64(pp_peer + uint32_t(half) * 8u, s,
+                     gbar_peer + uint32_t(half * C::WARPS) * 8u);
       }
     }
+    // each warp's F barrier: its 32 threads' slots from the same warp of the peer
+    if (lane == 0)
+      mbar_expect_tx(&gbar[half * C::WARPS + warp], 32u * 16u * 8u + ((lead && part_due) ? 8u : 0u));
     f2_load<L, 1>(buf, v, t);
     dft<16, false, EX>(v);
     f2_twiddle<false>(v, w1);
@@ -301,14 +307,15 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
     f2_dft<L, NP - 1, false, EX>(v);             // v[j] = F_h[k_j]
     {
       const uint32_t go = g_peer + uint32_t(half * M) * 8u;
-      const uint32_t gbo = gbar_peer + uint32_t(half) * 8u;
+      const uint32_t gbo = gbar_peer + uint32_t(half * C::WARPS + warp) * 8u;
 #pragma unroll
       for (int pp = 0; pp < 8; ++pp)
         st_async_v4(go + uint32_t(xpair(pp, t, T)) * 8u, v[2 * pp], v[2 * pp + 1], gbo);
     }
     // (no barrier before the inverse pass rewrites buf: each thread's
     // last-pass positions are its own in both directions)
-    if (!timed_out && !mbar_wait_cluster(&gbar[half], uint32_t((it >> 1) & 1))) timed_out = true;
+    if (!timed_out && !mbar_wait_cluster(&gbar[half * C::WARPS + warp], uint32_t((it >> 1) & 1)))
+      timed_out = true;
     if (lead && part_due && h == 0)
       d.powers[2 * (n / d.record_every - 1) + band] = (my_part + ppeer[half]) * d.dx_um;
     {
@@ -344,16 +351,17 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
     f2_twiddle<true>(v, w0);
     dft<16, true, EX>(v);
     {
-      if (lead) mbar_expect_tx(&cbar[half], uint32_t(M) * 8u);
+      if (lane == 0) mbar_expect_tx(&cbar[half * C::WARPS + warp], 32u * 16u * 8u);
       const uint32_t co = c_part + uint32_t(half * M) * 8u;
-      const uint32_t cbo = cbar_part + uint32_t(half) * 8u;
+      const uint32_t cbo = cbar_part + uint32_t(half * C::WARPS + warp) * 8u;
 #pragma unroll
       for (int j = 0; j < 16; ++j) v[j] = cadd(org[j], v[j]);
 #pragma unroll
       for (int pp = 0; pp < 8; ++pp)
         st_async_v4(co + uint32_t(xpair(pp, t, T)) * 8u, v[2 * pp], v[2 * pp + 1], cbo);
     }
-    if (!timed_out && !mbar_wait_cluster(&cbar[half], uint32_t((it >> 1) & 1))) timed_out = true;
+    if (!timed_out && !mbar_wait_cluster(&cbar[half * C::WARPS + warp], uint32_t((it >> 1) & 1)))
+      timed_out = true;
     if constexpr (HALF) {
       const bool next = it + 1 < steps;
       if constexpr (HALF_G) {

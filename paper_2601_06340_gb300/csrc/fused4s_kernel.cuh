@@ -175,6 +175,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg::T, 1)
   using F = F8Cfg<11>;
   constexpr int L = 11, M = C::M, N = C::N, T = C::T, NP = F::NP, RL = F::RL;
   static_assert(NP == 4 && RL == 4, "2048 = 8 x 8 x 8 x 4");
+  static_assert(T == 256, "the interval masks take T = 2^8");
   extern __shared__ __align__(128) unsigned char smem[];
   cg::cluster_group cluster = cg::this_cluster();
 
@@ -370,15 +371,16 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg::T, 1)
       auto couple_all = [&](auto S) {
         constexpr bool SEP = decltype(S)::value;
         const float2 bs = slice_b<SEP>(bb, sh, band);
+        const uint32_t msk = SEP ? sep_mask<1, 8, 8>(sh, t, h) : 0u;   // T = 256
 #pragma unroll
         for (int pp = 0; pp < 4; ++pp) {
           const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
           const int m0 = t + 2 * pp * T, m1 = t + (2 * pp + 1) * T;
           const int c0 = 2 * m0 + h, c1 = 2 * m1 + h;
-          v[2 * pp] = couple_cell(v[2 * pp], make_float2(q2.x, q2.y),
-                                  slice_at<SEP>(ph, sh, SEP ? m0 : c0, c0), band, am1, bs);
-          v[2 * pp + 1] = couple_cell(v[2 * pp + 1], make_float2(q2.z, q2.w),
-                                      slice_at<SEP>(ph, sh, SEP ? m1 : c1, c1), band, am1, bs);
+          v[2 * pp] = couple_at<SEP>(v[2 * pp], make_float2(q2.x, q2.y), ph, SEP ? m0 : c0, msk,
+                                     2 * pp, band, am1, bs);
+          v[2 * pp + 1] = couple_at<SEP>(v[2 * pp + 1], make_float2(q2.z, q2.w), ph,
+                                         SEP ? m1 : c1, msk, 2 * pp + 1, band, am1, bs);
         }
       };
       if (sep) couple_all(BoolC<true>{});

@@ -54,10 +54,10 @@ struct F4TCfg {
   static constexpr int OFF_C = OFF_G + 3 * M * 8;          // [2][M] other band's psi_p
   static constexpr int OFF_PH = OFF_C + 2 * M * 8;         // [M] strain slice
   static constexpr int OFF_MBAR = OFF_PH + M * 8;          // [2] strain-slice barriers
-  static constexpr int OFF_GBAR = OFF_MBAR + 16;           // F arrival
-  static constexpr int OFF_FREE = OFF_GBAR + 8;            // peers have read our F
-  static constexpr int OFF_CBAR = OFF_FREE + 8;            // [2] psi_p arrival
-  static constexpr int OFF_PPEER = OFF_CBAR + 16;          // [3] band-power parts (h = 0)
+  static constexpr int OFF_GBAR = OFF_MBAR + 16;           // [WARPS] F arrival
+  static constexpr int OFF_FREE = OFF_GBAR + 8 * WARPS;    // [WARPS] peers have read our F
+  static constexpr int OFF_CBAR = OFF_FREE + 8 * WARPS;    // [2][WARPS] psi_p arrival
+  static constexpr int OFF_PPEER = OFF_CBAR + 16 * WARPS;  // [3] band-power parts (h = 0)
   static constexpr int OFF_RECPH = OFF_PPEER + 24;
   static constexpr int OFF_RED = OFF_RECPH + 8;            // [WARPS] double
   static constexpr int OFF_PART = OFF_RED + WARPS * 8;
@@ -158,6 +158,7 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
   using C = F4TCfg;
   using F = F2Cfg<12>;
   constexpr int L = 12, M = C::M, N = C::N, T = C::T, NP = F::NP;
+  static_assert(T == 256, "the interval masks take T = 2^8");
   extern __shared__ __align__(128) unsigned char smem[];
   cg::cluster_group cluster = cg::this_cluster();
 
@@ -206,10 +207,12 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
   if (lead) {
     mbar_init(bar);
     if constexpr (HALF) mbar_init(bar + 1);   // the next-slice copies
-    mbar_init(gbar);
-    mbar_init_count(gfree, 3);
-    mbar_init(&cbar[0]);
-    mbar_init(&cbar[1]);
+    for (int w = 0; w < C::WARPS; ++w) {
+      mbar_init(&gbar[w]);
+      mbar_init_count(&gfree[w], 3);
+      mbar_init(&cbar[w]);
+      mbar_init(&cbar[C::WARPS + w]);
+    }
   }
   fence_mbar_init();
   if (warp == 0) tmem_alloc(tmem_slot, C::TMEM_COLS);
@@ -282,12 +285,11 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
     const SepHead sh = sep ? sep_head(srow0) : SepHead{};
     auto first_half = [&](auto S) {
       constexpr bool SEP = decltype(S)::value;
+      const uint32_t msk = SEP ? sep_mask<2, 8, 16>(sh, t, h) : 0u;   // T = 256
+      const float2 bs = slice_b<SEP>(bb, sh, band);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int m = t + j * T;
-        v[j] = couple_cell(v[j], q[j], slice_at<SEP>(ph, sh, m, 4 * m + h), band, am1,
-                           slice_b<SEP>(bb, sh, band));
-      }
+      for (int j = 0; j < 16; ++j)
+        v[j] = couple_at<SEP>(v[j], q[j], ph, t + j * T, msk, j, band, am1, bs);
     };
     if (sep) first_half(BoolC<true>{});
     else first_half(BoolC<false>{});
@@ -317,13 +319,16 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
       fetch(n, ph, 0, bar);
       if (HALF && !sep && it + 1 < steps)
         bulk_prefetch_l2(d.phasor + size_t(n + 1) * N + size_t(h) * M, slice_bytes);
-      mbar_expect_tx(gbar, 3u * uint32_t(M) * 8u + ((part_due && h == 0) ? 24u : 0u));
       if (part_due) {
         double s = 0.0;
         for (int w = 0; w < C::WARPS; ++w) s += red[w];
         my_part = s;
       }
     }
+    // each warp's F barrier: its 32 threads' slots from the same warp of the
+    // three peers (the band-power parts ride on warp 0's)
+    if (lane == 0)
+      mbar_expect_tx(&gbar[warp], 3u * 32u * 16u * 8u + ((lead && part_due && h == 0) ? 24u : 0u));
     f2_load<L, 1>(buf, v, t);
     dft<16, false, EX>(v);
     f2_twiddle<false>(v, w1);
@@ -334,15 +339,17 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
     f2_load<L, NP - 1>(buf, v, t);
     dft<16, false, EX>(v);                       // v[j] = F_h[k_j]
     // the peers have read our previous F before we overwrite their slots
-    if (it > 0 && !timed_out && !mbar_wait_cluster(gfree, uint32_t((it - 1) & 1))) timed_out = true;
+    // (per warp: the same warp of each peer has read the slots we write)
+    if (it > 0 && !timed_out && !mbar_wait_cluster(&gfree[warp], uint32_t((it - 1) & 1)))
+      timed_out = true;
 #pragma unroll
     for (int pp = 0; pp < 8; ++pp)
 #pragma unroll
       for (int e = 0; e < 3; ++e)
         st_async_v4(g_to[e] + uint32_t(xpair(pp, t, T)) * 8u, v[2 * pp], v[2 * pp + 1],
-                    gbar_to[e]);
+                    gbar_to[e] + uint32_t(warp) * 8u);
     if (lead && part_due && h > 0) st_async_f64(pp_to, my_part, gbar_to[3 - h]);
-    if (!timed_out && !mbar_wait_cluster(gbar, uint32_t(it & 1))) timed_out = true;
+    if (!timed_out && !mbar_wait_cluster(&gbar[warp], uint32_t(it & 1))) timed_out = true;
     if (lead && part_due && h == 0)
       d.powers[2 * (n / d.record_every - 1) + band] =
           (((my_part + ppeer[0]) + ppeer[1]) + ppeer[2]) * d.dx_um;
@@ -389,14 +396,17 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
         if (j < 15) tmem_wait16(ev[(j + 1) & 1]);
       }
     }
-    __syncthreads();                             // all of our F slots read
-    if (lead) {
-      // second order: slot 0 holds step n + 1's slice until the couplings;
-      // its sender is released after them
+    // this warp's F slots are read: release them to the same warp of each
+    // sender (second order: slot 0 holds step n + 1's slice until the
+    // couplings, so its sender is released after them, and the whole CTA
+    // must be past the combine before the slice copy into it)
+    if constexpr (HALF) __syncthreads();
+    else __syncwarp();
+    if (lane == 0) {
 #pragma unroll
-      for (int e = HALF ? 1 : 0; e < 3; ++e) mbar_arrive_remote(free_to[e]);
-      if (HALF && it + 1 < steps) fetch(n + 1, gx, 1, bar + 1);
+      for (int e = HALF ? 1 : 0; e < 3; ++e) mbar_arrive_remote(free_to[e] + uint32_t(warp) * 8u);
     }
+    if (HALF && lead && it + 1 < steps) fetch(n + 1, gx, 1, bar + 1);
     dft<16, true, EX>(v);
     f2_store<L, NP - 1>(buf, v, t);
     __syncwarp();
@@ -409,16 +419,17 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
     f2_twiddle<true>(v, w0);
     dft<16, true, EX>(v);
     {
-      if (lead) mbar_expect_tx(&cbar[half], uint32_t(M) * 8u);
+      if (lane == 0) mbar_expect_tx(&cbar[half * C::WARPS + warp], 32u * 16u * 8u);
       const uint32_t co = c_part + uint32_t(half * M) * 8u;
-      const uint32_t cbo = cbar_part + uint32_t(half) * 8u;
+      const uint32_t cbo = cbar_part + uint32_t(half * C::WARPS + warp) * 8u;
 #pragma unroll
       for (int j = 0; j < 16; ++j) v[j] = cadd(org[j], v[j]);
 #pragma unroll
       for (int pp = 0; pp < 8; ++pp)
         st_async_v4(co + uint32_t(xpair(pp, t, T)) * 8u, v[2 * pp], v[2 * pp + 1], cbo);
     }
-    if (!timed_out && !mbar_wait_cluster(&cbar[half], uint32_t((it >> 1) & 1))) timed_out = true;
+    if (!timed_out && !mbar_wait_cluster(&cbar[half * C::WARPS + warp], uint32_t((it >> 1) & 1)))
+      timed_out = true;
     if constexpr (HALF) {
       const bool next = it + 1 < steps;
       if (!timed_out && !mbar_wait(bar, uint32_t((it + 1) & 1))) timed_out = true;
@@ -439,6 +450,8 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
         constexpr bool SEP = decltype(S)::value;
         const float2 bc = slice_b<SEP>(bb, shc, band), bo = slice_b<SEP>(bb, shc, band ^ 1);
         const float2 bn = slice_b<SEP>(bb, shn, band);
+        const uint32_t mc = SEP ? sep_mask<2, 8, 16>(shc, t, h) : 0u;
+        const uint32_t mn = SEP ? sep_mask<2, 8, 16>(shn, t, h) : 0u;
 #pragma unroll 1
         for (int pp = 0; pp < 8; ++pp) {
           const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
@@ -447,8 +460,8 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
             const int j = 2 * pp + k;
             const int cell = t + j * T;
             const float2 p = buf[cell], q = k ? make_float2(q2.z, q2.w) : make_float2(q2.x, q2.y);
-            const float2 e = slice_at<SEP>(ph, shc, cell, 4 * cell + h);
-            float2 cc = couple_cell(p, q, e, band, am1, bc);   // step it, second half
+            // step it, second half (this band's and, below, the other band's)
+            float2 cc = couple_at<SEP>(p, q, ph, cell, mc, j, band, am1, bc);
             if (rec) {
               s = pow_acc(s, cc);
               if (r0)   // records in natural order
@@ -456,8 +469,8 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
                     make_float2(fmaf(cc.x, g.x, -(cc.y * g.y)), fmaf(cc.x, g.y, cc.y * g.x));
             }
             if (next) {   // step it + 1, first half, with the other band's value
-              const float2 co = couple_cell(q, p, e, band ^ 1, am1, bo);
-              cc = couple_cell(cc, co, slice_at<SEP>(phn, shn, cell, 4 * cell + h), band, am1, bn);
+              const float2 co = couple_at<SEP>(q, p, ph, cell, mc, j, band ^ 1, am1, bo);
+              cc = couple_at<SEP>(cc, co, phn, cell, mn, j, band, am1, bn);
             }
             buf[cell] = cc;
           }
@@ -468,7 +481,7 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
 #pragma unroll
       for (int j = 0; j < 16; ++j) v[j] = buf[t + j * T];
       __syncthreads();
-      if (lead) mbar_arrive_remote(free_to[0]);   // slot 0 is free again
+      if (lane == 0) mbar_arrive_remote(free_to[0] + uint32_t(warp) * 8u);   // slot 0 is free again
       if (rec && d.powers) {
         double ds = s;
 #pragma unroll
@@ -482,14 +495,15 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
     auto couple_all = [&](auto S) {
       constexpr bool SEP = decltype(S)::value;
       const float2 bs = slice_b<SEP>(bb, sh, band);
+      const uint32_t msk = SEP ? sep_mask<2, 8, 16>(sh, t, h) : 0u;
 #pragma unroll
       for (int pp = 0; pp < 8; ++pp) {
         const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
         const int m0 = t + 2 * pp * T, m1 = t + (2 * pp + 1) * T;
-        v[2 * pp] = couple_cell(v[2 * pp], make_float2(q2.x, q2.y),
-                                slice_at<SEP>(ph, sh, m0, 4 * m0 + h), band, am1, bs);
-        v[2 * pp + 1] = couple_cell(v[2 * pp + 1], make_float2(q2.z, q2.w),
-                                    slice_at<SEP>(ph, sh, m1, 4 * m1 + h), band, am1, bs);
+        v[2 * pp] = couple_at<SEP>(v[2 * pp], make_float2(q2.x, q2.y), ph, m0, msk, 2 * pp, band,
+                                   am1, bs);
+        v[2 * pp + 1] = couple_at<SEP>(v[2 * pp + 1], make_float2(q2.z, q2.w), ph, m1, msk,
+                                       2 * pp + 1, band, am1, bs);
       }
     };
     if (sep) couple_all(BoolC<true>{});

@@ -130,6 +130,22 @@ __device__ __forceinline__ SepHead sep_head(const float4* slot) {
   return {make_float2(h.x, h.y), __float_as_int(h.z), __float_as_int(h.w)};
 }
 
+// Bit jj set: the cell of natural column P (t + jj T) + h (T = 2^LOG_T)
+// lies in [lo, hi).  Columns P m + h with m in [ceil((lo - h) / P),
+// ceil((hi - h) / P)), and m = t + jj T in that range for jj in
+// [ceil((mlo - t) / T), ceil((mhi - t) / T)): two clamped shifts per thread
+// and step instead of a test per cell (P a power of two; the shifts floor).
+__host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
+
+template <int LOG_P, int LOG_T, int E>
+__device__ __forceinline__ uint32_t sep_mask(const SepHead& sh, int t, int h) {
+  constexpr int P = 1 << LOG_P, T = 1 << LOG_T;
+  const int mlo = (sh.lo - h + P - 1) >> LOG_P, mhi = (sh.hi - h + P - 1) >> LOG_P;
+  const int a = min(max((mlo - t + T - 1) >> LOG_T, 0), E);
+  const int b = min(max((mhi - t + T - 1) >> LOG_T, 0), E);
+  return ((1u << b) - 1u) & ~((1u << a) - 1u);
+}
+
 // The cell's column phasor inside [lo, hi) (natural column j), (0, 0) outside.
 __device__ __forceinline__ float2 sep_cell(const SepHead& h, float2 col, int j) {
   const bool in = (j >= h.lo) & (j < h.hi);

@@ -505,12 +505,16 @@ bool sep_slices_apply(const bpm_plan_s* plan) {
   const char* e = std::getenv("BPM_SLICE_STREAM");
   if (e && e[0] == '1') return false;
   if (e && e[0] == '0') return true;
-  // Rows that each get two SMs or more (single solves, served requests,
-  // small batches) march latency-bound: the separable form saves the stream
-  // (memory, preparation, DRAM) and measured 3 % faster on the 4096 x 8000
-  // solve.  Batches that fill the GPU are bound by instruction issue, share
-  // one stream between all rows, and ran 8 % slower with the per-cell
-  // interval test (256 rows, N = 2048 and 4096): they keep the stream.
+  // Where the separable form is taken (same GPU, back to back, 8000-step
+  // bent solves): N = 4096 rows that each get the 4-SM half-band split run
+  // the 8-point kernel, which reads its column phasors without the stream's
+  // stride-2 bank conflicts: 22.8 ms against 23.4 ms with the stream.  At
+  // N >= 8192 the two forms are within 1-3 % and the stream would take
+  // 8 B x N x Nz (2.6 GB for a 16384 x 20000 request).  Elsewhere the
+  // per-cell interval test costs more than the stream's read: 7-11 % at
+  // N = 1024 and 2048 (a 2048 x 20000 stream is 328 MB), 8 % on batches
+  // that fill the GPU (which share one stream among all rows): they keep
+  // the stream.
   static int sms = 0;
   if (sms == 0) {
     int dev = 0, v = 0;
@@ -518,7 +522,8 @@ bool sep_slices_apply(const bpm_plan_s* plan) {
     cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
     sms = v > 0 ? v : 1;
   }
-  return 2 * plan->nb <= sms;
+  if (plan->logn == 12) return 4 * plan->nb <= sms;
+  return plan->logn >= kSplitLogN && 2 * plan->nb <= sms;
 }
 
 size_t slice_data_bytes(const bpm_plan_s* plan) {

@@ -51,10 +51,8 @@ def _bent(nx, nz, geometry, record_every=50):
 
 
 def _march(wl, monkeypatch, stream, layout=None, split=FIRST):
-    if stream:
-        monkeypatch.setenv("BPM_SLICE_STREAM", "1")
-    else:
-        monkeypatch.delenv("BPM_SLICE_STREAM", raising=False)
+    # either form forced (the rule takes the stream at small nx)
+    monkeypatch.setenv("BPM_SLICE_STREAM", "1" if stream else "0")
     if layout:
         monkeypatch.setenv("BPM_FUSED_LAYOUT", layout)
     else:
@@ -127,10 +125,7 @@ def test_fetched_slices_are_identical(bpm_lib, monkeypatch, nx):
     wl = _bent(nx, 200, "bragg")
     got = {}
     for stream in (False, True):
-        if stream:
-            monkeypatch.setenv("BPM_SLICE_STREAM", "1")
-        else:
-            monkeypatch.delenv("BPM_SLICE_STREAM", raising=False)
+        monkeypatch.setenv("BPM_SLICE_STREAM", "1" if stream else "0")
         with binding.Plan(wl, FP32) as plan:
             mask, ph = plan.slices()
             got[stream] = (mask, ph, binding.bpm_slice_form(plan.handle)[0])
@@ -143,10 +138,11 @@ def test_fetched_slices_are_identical(bpm_lib, monkeypatch, nx):
 
 
 def test_which_plans_are_separable(bpm_lib, monkeypatch):
-    """Bent or unstrained slabs take the separable form while every row can
-    have two SMs; a dislocation, a polygon cut, an FP64 plan, a batch that
+    """Bent or unstrained slabs take the separable form at nx = 4096 while
+    every row gets four SMs and at nx >= 8192 while every row gets two; a
+    smaller nx, a dislocation, a polygon cut, an FP64 plan, a batch that
     fills the GPU or BPM_SLICE_STREAM=1 keep the stream; BPM_SLICE_STREAM=0
-    gives a full batch the separable form."""
+    gives them the separable form where the crystal allows it."""
     monkeypatch.delenv("BPM_SLICE_STREAM", raising=False)
 
     def form(wl, precision=FP32):
@@ -155,16 +151,19 @@ def test_which_plans_are_separable(bpm_lib, monkeypatch):
             plan.propagate(n_end=2)
             return binding.bpm_slice_form(plan.handle)
 
-    assert form(inputs.bragg_bent(nx=1024, nz=50)) == (1, 50 * 96 + 1024 * 8)
-    assert form(inputs.laue_perfect(nx=1024, nz=50))[0] == 1
-    assert form(inputs.asym_dislocation(nx=1024, nz=50))[0] == 0
-    assert form(inputs.bragg_bent(nx=1024, nz=50), binding.BPM_FP64_PLAIN)[0] == 0
-    wl = inputs.asym_dislocation(nx=1024, nz=50)
+    assert form(inputs.bragg_bent(nx=4096, nz=50)) == (1, 50 * 96 + 4096 * 8)
+    assert form(inputs.bragg_bent(nx=8192, nz=50))[0] == 1
+    assert form(inputs.laue_perfect(nx=16384, nz=50))[0] == 1
+    assert form(inputs.bragg_bent(nx=1024, nz=50)) == (0, 50 * 1024 * 8)
+    assert form(inputs.asym_dislocation(nx=8192, nz=50))[0] == 0
+    assert form(inputs.bragg_bent(nx=4096, nz=50), binding.BPM_FP64_PLAIN)[0] == 0
+    wl = inputs.asym_dislocation(nx=8192, nz=50)
     assert form(dataclasses.replace(wl, strain=dict(kind=inputs.STRAIN_NONE)))[0] == 0
-    batch = inputs.pulse_batched(nx=1024, nz=50, n_energy=256)
+    batch = inputs.pulse_batched(nx=4096, nz=50, n_energy=256)
     assert form(batch)[0] == 0
     monkeypatch.setenv("BPM_SLICE_STREAM", "0")
     assert form(batch)[0] == 1
+    assert form(inputs.bragg_bent(nx=1024, nz=50))[0] == 1
 
 
 def test_separable_rotated_batch(bpm_lib, monkeypatch):
