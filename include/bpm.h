@@ -294,8 +294,9 @@ int bpm_fetch_slices(bpm_plan_t plan, uint8_t* mask, double* phasor);
  * couple; 0: the per-cell stream (c64 per cell for FP32 plans, c128 for
  * FP64 plans); -1: not prepared yet (slices are prepared at the first march
  * after bpm_set_crystal / bpm_set_strain).  Eligible plans take the
- * separable form where it pays: nx = 4096 while 4 x rows <= the GPU's SM
- * count (the half-band split), nx >= 8192 while 2 x rows <= the SM count
+ * separable form where it pays: nx = 4096 first-order plans while 4 x rows
+ * <= the GPU's SM count (the half-band split), nx >= 8192 while 2 x rows <=
+ * the SM count
  * (a stream of 8 B per cell: 2.6 GB for 16384 x 20000); smaller nx and
  * batches that fill the GPU keep the stream (faster there; a batch shares
  * it among its rows).  BPM_SLICE_STREAM=1 (0) in the environment when the

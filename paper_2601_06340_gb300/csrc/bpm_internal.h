@@ -212,8 +212,9 @@ std::vector<int> fft_output_order(int logn);   // position -> frequency index
 // once the work is enqueued (temporaries, if any, still force a wait).
 int prepare_slices(bpm_plan_s* plan, cudaStream_t st, bool sync = true);
 // Whether the plan's slices take the separable form (FP32 2D plans of a
-// vacuum, bulk or slab crystal with bent or no strain, at nx = 4096 while
-// 4 x rows <= the SM count and at nx >= 8192 while 2 x rows <= it;
+// vacuum, bulk or slab crystal with bent or no strain, at nx = 4096 for the
+// first-order step while 4 x rows <= the SM count and at nx >= 8192 while
+// 2 x rows <= it;
 // BPM_SLICE_STREAM=1 / 0 forces the stream / separable form), and the
 // device bytes of either form.
 bool sep_slices_apply(const bpm_plan_s* plan);

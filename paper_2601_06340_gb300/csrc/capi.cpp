@@ -789,6 +789,10 @@ int bpm_set_splitting(bpm_plan_t plan, int32_t method) {
       if (e != cudaSuccess) return cuda_fail(e, "splitting tables");
     }
     plan->split = method;
+    // the slice form depends on the step form (nx = 4096): prepare again if
+    // it changes
+    if (!plan->slices_dirty && plan->sep_slices != sep_slices_apply(plan))
+      plan->slices_dirty = true;
     return BPM_OK;
   }
   plan->split = method;

@@ -1,6 +1,7 @@
 // Dispatch of the fused FP32 march by transform size.
 #include <atomic>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 
 #include "fused_kernel.cuh"
@@ -43,6 +44,8 @@ int fused4s_launch_12(const RowDescF32*, int, int, const float4*, int*, cudaStre
 int fused4s_rows_resident_12();
 int fused4hh_launch_12(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
 int fused4hh_rows_resident_12();
+int fused4sh_launch_12(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
+int fused4sh_rows_resident_12();
 int fused4_launch_14(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
 int fused4v_launch_13(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
 int fused4v_launch_14(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
@@ -70,6 +73,13 @@ static int forced_layout() {
   if (std::strcmp(v, "cluster") == 0) return 1;
   if (std::strcmp(v, "cta") == 0) return 0;
   return -1;
+}
+
+// BPM_FUSED_LAYOUT=split16: the N = 4096 half-band split with 16 points per
+// thread (fused4e_march_kernel<11>) instead of 8.
+static bool split16_forced() {
+  const char* v = std::getenv("BPM_FUSED_LAYOUT");
+  return v && std::strcmp(v, "split16") == 0;
 }
 
 static bool use_cluster_layout(int logn, int n_rows) {
@@ -101,7 +111,9 @@ int launch_fused_layout(int logn, const RowDescF32* d_rows, int n_rows, int step
     return fused4h_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
   if (layout == kLayoutSplit4Half) {
     switch (logn) {
-      case 12: return fused4hh_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 12:   // 8 points per thread unless the 16-point form is forced
+        return split16_forced() ? fused4hh_launch_12(d_rows, n_rows, steps, d_tw, d_status, st)
+                                : fused4sh_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
       case 13: return fused4v_launch_13(d_rows, n_rows, steps, d_tw, d_status, st);
       case 14: return fused4v_launch_14(d_rows, n_rows, steps, d_tw, d_status, st);
       default:
@@ -363,7 +375,7 @@ int fused_split4_half_capacity() {
   static std::atomic<int> cached{0};
   int c = cached.load(std::memory_order_relaxed);
   if (c == 0) {
-    c = fused4hh_rows_resident_12();
+    c = std::min(fused4sh_rows_resident_12(), fused4hh_rows_resident_12());
     cached.store(c, std::memory_order_relaxed);
   }
   return c;

@@ -116,6 +116,9 @@ __device__ __forceinline__ int pos16_of_freq2048(int k) {
   return (k & 15) * 128 + ((k >> 4) & 15) * 8 + (k >> 8);
 }
 
+// PHB: strain-slice buffers (2 for the second-order step, which couples
+// with the slices of two steps at a time)
+template <int PHB = 1>
 struct F4SCfg {
   static constexpr int M = 2048;
   static constexpr int N = 2 * M;
@@ -125,17 +128,17 @@ struct F4SCfg {
   static constexpr int OFF_BUF = 0;                        // [PADM]
   static constexpr int OFF_G = OFF_BUF + PADM * 8;         // [2][M] peer's F
   static constexpr int OFF_C = OFF_G + 2 * M * 8;          // [2][M] other band's psi_p
-  static constexpr int OFF_PH = OFF_C + 2 * M * 8;         // [N] strain slice (natural order)
-  static constexpr int OFF_E1 = OFF_PH + N * 8;            // [8][T] D(k_j + M)
-  static constexpr int OFF_MBAR = OFF_E1 + M * 8;          // strain-slice barrier
-  static constexpr int OFF_GBAR = OFF_MBAR + 8;            // [2][WARPS] F barriers
+  static constexpr int OFF_PH = OFF_C + 2 * M * 8;         // [PHB][N] strain slices (natural order)
+  static constexpr int OFF_E1 = OFF_PH + PHB * N * 8;      // [8][T] D(k_j + M)
+  static constexpr int OFF_MBAR = OFF_E1 + M * 8;          // [PHB] strain-slice barriers
+  static constexpr int OFF_GBAR = OFF_MBAR + 8 * PHB;      // [2][WARPS] F barriers
   static constexpr int OFF_CBAR = OFF_GBAR + 16 * WARPS;   // [2][WARPS] psi_p barriers
   static constexpr int OFF_PPEER = OFF_CBAR + 16 * WARPS;  // [2] peer's band-power part
   static constexpr int OFF_RECPH = OFF_PPEER + 16;
   static constexpr int OFF_RED = OFF_RECPH + 8;            // [WARPS] double
   static constexpr int OFF_PART = OFF_RED + WARPS * 8;
-  static constexpr int OFF_SROW = (OFF_PART + 8 + 15) / 16 * 16;   // row head
-  static constexpr int SMEM = OFF_SROW + 16;
+  static constexpr int OFF_SROW = (OFF_PART + 8 + 15) / 16 * 16;   // [2] row heads
+  static constexpr int SMEM = OFF_SROW + 2 * 16;
   static_assert(SMEM <= 232448, "fits one SM");
   static_assert(OFF_G % 16 == 0 && OFF_C % 16 == 0 && OFF_PH % 16 == 0,
                 "16-byte stores and bulk copy");
@@ -166,12 +169,20 @@ __device__ __forceinline__ void s4_load_last(const float2* buf, float2* v, int t
     for (int j = 0; j < 4; ++j) v[i * 4 + j] = buf[swz8(s4_group(t, i) * 4 + j)];
 }
 
-template <bool EX>
-__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg::T, 1)
+// HALF = true: the second-order (Verlet) step of Eq. split-op, as in the
+// 2-CTA cluster kernel: after the psi_p swap a CTA holds both bands at its
+// samples, so it applies step n's second half-coupling to both and step
+// n + 1's first half to its own band (8 points per thread: in registers);
+// the launch's first half-step reads the other band from global memory.
+// Step n + 1's slice is fetched a step ahead into the second buffer
+// (separable slices: its row head into the second row-head slot).  Records
+// are taken after step n's second half.
+template <bool EX, bool HALF = false>
+__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg<>::T, 1)
     fused4s_march_kernel(const RowDescF32* __restrict__ rows, int n_rows, int steps,
                          const float4* __restrict__ tw, int* __restrict__ status) {
   namespace cg = cooperative_groups;
-  using C = F4SCfg;
+  using C = F4SCfg<HALF ? 2 : 1>;
   using F = F8Cfg<11>;
   constexpr int L = 11, M = C::M, N = C::N, T = C::T, NP = F::NP, RL = F::RL;
   static_assert(NP == 4 && RL == 4, "2048 = 8 x 8 x 8 x 4");
@@ -211,6 +222,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg::T, 1)
 
   if (lead) {
     mbar_init(bar);
+    if constexpr (HALF) mbar_init(bar + 1);
     for (int i = 0; i < 2 * C::WARPS; ++i) {
       mbar_init(&gbar[i]);
       mbar_init(&cbar[i]);
@@ -258,8 +270,35 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg::T, 1)
   const uint32_t slice_bytes = uint32_t(N) * 8u;
   bool timed_out = false;
   double my_part = 0.0;
-  const float2 am1 = d.am1, bb = d.b;
+  const float2 am1 = HALF ? d.am1h : d.am1, bb = HALF ? d.bh : d.b;
   const bool pow_on = d.powers != nullptr && d.record_every > 0;
+  // step n's slice into buffer `slot` (separable: its row head into row-head
+  // slot `slot`; the column phasors stay in buffer 0)
+  auto fetch = [&](int n, int slot) {
+    if (sep) bulk_load(srow + slot, d.srows + n, kSepHeadBytes, bar + slot);
+    else bulk_load(ph + slot * N, d.phasor + size_t(n) * N, slice_bytes, bar + slot);
+  };
+  if constexpr (HALF) {
+    // the launch's first half-step, on the slice of its first step
+    if (lead) fetch(d.n_begin, 0);
+    float2 q[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) q[j] = d.state[(band ^ 1) * N + 2 * (t + j * T) + h];
+    if (!mbar_wait(bar, 0u)) timed_out = true;
+    const SepHead sh = sep ? sep_head(srow) : SepHead{};
+    auto first_half = [&](auto S) {
+      constexpr bool SEP = decltype(S)::value;
+      const uint32_t msk = SEP ? sep_mask<1, 8, 8>(sh, t, h) : 0u;
+      const float2 bs = slice_b<SEP>(bb, sh, band);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int m = t + j * T;
+        v[j] = couple_at<SEP>(v[j], q[j], ph, SEP ? m : 2 * m + h, msk, j, band, am1, bs);
+      }
+    };
+    if (sep) first_half(BoolC<true>{});
+    else first_half(BoolC<false>{});
+  }
 
   for (int it = 0; it < steps; ++it) {
     const int n = d.n_begin + it;
@@ -282,9 +321,14 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg::T, 1)
     f8_store<L, 0>(buf, v, t);
     __syncthreads();
     if (lead) {
-      // the step's slice (separable: its row head)
-      if (sep) bulk_load(srow, d.srows + n, kSepHeadBytes, bar);
-      else bulk_load(ph, d.phasor + size_t(n) * N, slice_bytes, bar);
+      // the step's slice (separable: its row head); second order: every
+      // thread is past step it - 1's couplings, which read the other
+      // buffer: fetch step it + 1's slice into it
+      if constexpr (HALF) {
+        if (it + 1 < steps) fetch(n + 1, (it + 1) & 1);
+      } else {
+        fetch(n, 0);
+      }
       if (part_due) {   // rides on the peer's warp-0 F barrier
         double s = 0.0;
         for (int w = 0; w < C::WARPS; ++w) s += red[w];
@@ -364,6 +408,62 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg::T, 1)
     }
     if (!timed_out && !mbar_wait_cluster(&cbar[half * C::WARPS + warp], uint32_t((it >> 1) & 1)))
       timed_out = true;
+    if constexpr (HALF) {
+      const bool next = it + 1 < steps;
+      if (next && !timed_out &&
+          !mbar_wait(bar + ((it + 1) & 1), uint32_t(((it + 1) >> 1) & 1)))
+        timed_out = true;
+      const float2* ci = cb + half * M;
+      // (separable: the column phasors of buffer 0 and the row heads of
+      // steps it and it + 1)
+      const float2* phc = ph + (sep ? 0 : (it & 1) * N);
+      const float2* phn = ph + (sep ? 0 : ((it + 1) & 1) * N);
+      const SepHead shc = sep ? sep_head(srow + (it & 1)) : SepHead{};
+      const SepHead shn = (sep && next) ? sep_head(srow + ((it + 1) & 1)) : SepHead{};
+      const float2 g = rec ? *recph : make_float2(1.f, 0.f);
+      const int slot = rec ? (n + 1) / d.record_every - 1 : 0;
+      float2* r0 = (rec && d.records) ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
+      double s = 0.0;
+      auto three_halves = [&](auto S) {
+        constexpr bool SEP = decltype(S)::value;
+        const float2 bc = slice_b<SEP>(bb, shc, band), bo = slice_b<SEP>(bb, shc, band ^ 1);
+        const float2 bn = slice_b<SEP>(bb, shn, band);
+        const uint32_t mc = SEP ? sep_mask<1, 8, 8>(shc, t, h) : 0u;
+        const uint32_t mn = SEP ? sep_mask<1, 8, 8>(shn, t, h) : 0u;
+#pragma unroll
+        for (int pp = 0; pp < 4; ++pp) {
+          const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const int j = 2 * pp + k;
+            const int m = t + j * T;
+            const int cell = SEP ? m : 2 * m + h;
+            const float2 p = v[j], q = k ? make_float2(q2.z, q2.w) : make_float2(q2.x, q2.y);
+            // step it, second half (this band's and, below, the other band's)
+            float2 c = couple_at<SEP>(p, q, phc, cell, mc, j, band, am1, bc);
+            if (rec) {
+              s = pow_acc(s, c);
+              if (r0)   // records in natural order
+                r0[2 * m + h] = make_float2(fmaf(c.x, g.x, -(c.y * g.y)), fmaf(c.x, g.y, c.y * g.x));
+            }
+            if (next) {   // step it + 1, first half, with the other band's value
+              const float2 co = couple_at<SEP>(q, p, phc, cell, mc, j, band ^ 1, am1, bo);
+              c = couple_at<SEP>(c, co, phn, cell, mn, j, band, am1, bn);
+            }
+            v[j] = c;
+          }
+        }
+      };
+      if (sep) three_halves(BoolC<true>{});
+      else three_halves(BoolC<false>{});
+      if (rec && d.powers) {
+        double ds = s;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, off);
+        if (lane == 0) red[warp] = ds;   // summed by the lead after the next barrier
+      }
+      continue;
+    }
     if (!timed_out && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
     {
       const float2* ci = cb + half * M;
@@ -424,8 +524,14 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg::T, 1)
 #pragma unroll
   for (int j = 0; j < 8; ++j) d.state[band * N + 2 * (t + j * T) + h] = v[j];
   // Error path: as in fused4e_march_kernel (the lead still issues one slice
-  // copy per step, so it waits, bounded, for the last step's phase).
-  if (timed_out) give_up_after_march(bar, uint32_t((steps - 1) & 1), lead, status);
+  // copy per step, so it waits, bounded, for the last step's phase; second
+  // order: the copy of step steps - 1's slice, into its buffer).
+  if (timed_out) {
+    if constexpr (HALF)
+      give_up_after_march(bar + ((steps - 1) & 1), uint32_t(((steps - 1) >> 1) & 1), lead, status);
+    else
+      give_up_after_march(bar, uint32_t((steps - 1) & 1), lead, status);
+  }
   cluster.sync();   // peers may still read our shared memory
 }
 

@@ -508,7 +508,9 @@ bool sep_slices_apply(const bpm_plan_s* plan) {
   // Where the separable form is taken (same GPU, back to back, 8000-step
   // bent solves): N = 4096 rows that each get the 4-SM half-band split run
   // the 8-point kernel, which reads its column phasors without the stream's
-  // stride-2 bank conflicts: 22.8 ms against 23.4 ms with the stream.  At
+  // stride-2 bank conflicts: 22.8 ms against 23.4 ms with the stream (its
+  // Verlet form, with three couplings per step, 27.0 against 26.2 ms: the
+  // stream there).  At
   // N >= 8192 the two forms are within 1-3 % and the stream would take
   // 8 B x N x Nz (2.6 GB for a 16384 x 20000 request).  Elsewhere the
   // per-cell interval test costs more than the stream's read: 7-11 % at
@@ -522,7 +524,7 @@ bool sep_slices_apply(const bpm_plan_s* plan) {
     cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
     sms = v > 0 ? v : 1;
   }
-  if (plan->logn == 12) return 4 * plan->nb <= sms;
+  if (plan->logn == 12) return plan->split == BPM_SPLIT_FIRST_ORDER && 4 * plan->nb <= sms;
   return plan->logn >= kSplitLogN && 2 * plan->nb <= sms;
 }
 

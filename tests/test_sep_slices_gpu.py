@@ -78,7 +78,8 @@ CASES = [
     (1024, 300, "cluster", VERLET, 4),
     (4096, 400, None, FIRST, 2),         # half-band split, 8 points per thread
     (4096, 400, "split16", FIRST, 8),    # half-band split, 16 points per thread
-    (4096, 400, None, VERLET, 5),
+    (4096, 400, None, VERLET, 5),        # the 8-point split's Verlet form
+    (4096, 400, "split16", VERLET, 5),   # the 16-point split's Verlet form
     (8192, 300, None, FIRST, -1),        # split band, two parts
     (8192, 300, None, VERLET, 5),
     (8192, 120, None, FR, 7),            # stage by stage (coupling-only launches)
@@ -138,20 +139,24 @@ def test_fetched_slices_are_identical(bpm_lib, monkeypatch, nx):
 
 
 def test_which_plans_are_separable(bpm_lib, monkeypatch):
-    """Bent or unstrained slabs take the separable form at nx = 4096 while
-    every row gets four SMs and at nx >= 8192 while every row gets two; a
+    """Bent or unstrained slabs take the separable form at nx = 4096 (first
+    order) while every row gets four SMs and at nx >= 8192 while every row
+    gets two; a
     smaller nx, a dislocation, a polygon cut, an FP64 plan, a batch that
     fills the GPU or BPM_SLICE_STREAM=1 keep the stream; BPM_SLICE_STREAM=0
     gives them the separable form where the crystal allows it."""
     monkeypatch.delenv("BPM_SLICE_STREAM", raising=False)
 
-    def form(wl, precision=FP32):
-        with binding.Plan(wl, precision) as plan:
+    def form(wl, precision=FP32, split=FIRST):
+        with binding.Plan(wl, precision, splitting=split) as plan:
             assert binding.bpm_slice_form(plan.handle)[0] == -1   # prepared at the first march
             plan.propagate(n_end=2)
             return binding.bpm_slice_form(plan.handle)
 
     assert form(inputs.bragg_bent(nx=4096, nz=50)) == (1, 50 * 96 + 4096 * 8)
+    # the N = 4096 Verlet form marches faster on the stream
+    assert form(inputs.bragg_bent(nx=4096, nz=50), split=VERLET)[0] == 0
+    assert form(inputs.bragg_bent(nx=8192, nz=50), split=VERLET)[0] == 1
     assert form(inputs.bragg_bent(nx=8192, nz=50))[0] == 1
     assert form(inputs.laue_perfect(nx=16384, nz=50))[0] == 1
     assert form(inputs.bragg_bent(nx=1024, nz=50)) == (0, 50 * 1024 * 8)
@@ -184,3 +189,17 @@ def test_separable_rotated_batch(bpm_lib, monkeypatch):
     ref = submit_ref(wb, rows=rows).result()
     errs = band_errors(out["0"].psi[rows], ref.psi, out["0"].records[rows], ref.records)
     assert max(errs) <= TOL_FP32, errs
+
+
+def test_splitting_change_reprepares_the_slices(bpm_lib, monkeypatch):
+    """The N = 4096 slice form follows the step form: switching a prepared
+    first-order plan to Verlet prepares the stream at its next march."""
+    monkeypatch.delenv("BPM_SLICE_STREAM", raising=False)
+    wl = inputs.bragg_bent(nx=4096, nz=40)
+    with binding.Plan(wl, FP32) as plan:
+        plan.propagate(n_end=2)
+        assert binding.bpm_slice_form(plan.handle)[0] == 1
+        binding.bpm_set_splitting(plan.handle, VERLET)
+        assert binding.bpm_slice_form(plan.handle)[0] == -1
+        plan.propagate(n_end=2)
+        assert binding.bpm_slice_form(plan.handle)[0] == 0
