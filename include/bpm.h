@@ -341,7 +341,10 @@ int bpm_march_f64_noalloc(void* d_psi, int32_t nx, int32_t n_rows, const void* d
                           int32_t n_end, void* stream);
 
 /* Launch shape of the plan's last FP32 march (the fused kernels of the
- * step of Eq. fov10): *layout = 7 the Forest-Ruth step stage by stage
+ * step of Eq. fov10): *layout = 9 the Forest-Ruth step on one 4-CTA
+ * cluster per row (nx = 4096 half-band split, while every row gets four
+ * SMs), 8 the nx = 4096 half-band split with 16 points per thread (forced
+ * by BPM_FUSED_LAYOUT=split16), 7 the Forest-Ruth step stage by stage
  * (nx >= 8192), 6 one CTA per row with the Forest-Ruth step (plans set to
  * BPM_SPLIT_FOREST_RUTH), 5 one split-band cluster per row with
  * the Verlet step (nx = 4096, 8192, 16384), 4 one 2-CTA cluster per row with the Verlet

@@ -164,6 +164,8 @@ struct bpm_plan_s {
   void* d_stage_rows = nullptr;      // RowDescF64 [n_stages][B]
   void* d_stage_prop = nullptr;      // FP64: double2 [tables][B][2][nx]; FP32 Forest-Ruth:
                                      // float2 [B][2 tables][2][nx] (t dz, (1 - 2t) dz)
+  void* d_stage_prop_split = nullptr;   // FP32 Forest-Ruth at nx = 4096 on the half-band
+                                        // split: float2 [B][2 tables][half-band table]
   size_t device_bytes = 0;
   int pending = 0;                // tickets not yet finished
   // launch shape of the last fused march: layout 1 cluster / 0 CTA / -1 rule,
@@ -281,6 +283,9 @@ constexpr int kLayoutStagedFR = 7;
 // thread (fused4e_march_kernel<11>); layout 2 runs the 8-point form
 // (fused4s_kernel.cuh), measured 5 % faster
 constexpr int kLayoutSplit4S = 8;
+// one 4-CTA cluster per row (N = 4096 half-band split, 8 points per thread),
+// fourth-order (Forest-Ruth) step
+constexpr int kLayoutSplit4FR = 9;
 // Coupling alone (the leading coupling of a step), on rows[0..nb): each row's
 // state [2][nx], the slice of step n of its stream (stored per part for
 // nx >= 8192), coefficients (am1h, bh).
@@ -291,6 +296,7 @@ int fused_half_capacity(int logn);   // logn <= 12
 int fused_fr_capacity(int logn);     // logn <= 12
 int fused_cluster_half_capacity(int logn);   // 9 <= logn <= 12
 int fused_split4_half_capacity();            // N = 4096
+int fused_split4_fr_capacity();              // N = 4096
 int fused_rows_per_cta(int logn);
 int fused_threads(int logn);
 

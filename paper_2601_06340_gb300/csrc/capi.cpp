@@ -51,7 +51,7 @@ void free_plan_memory(bpm_plan_s* plan) {
   void** ptrs[] = {&plan->d_phasor, &plan->d_sep, &plan->d_prop, &plan->d_prop_split, &plan->d_tw, &plan->d_state,
                    &plan->d_state2, &plan->d_rows, &plan->d_io, &plan->d_spec,
                    &plan->d_twy, reinterpret_cast<void**>(&plan->d_pwpart),
-                   &plan->d_stage_rows, &plan->d_stage_prop};
+                   &plan->d_stage_rows, &plan->d_stage_prop, &plan->d_stage_prop_split};
   for (void** p : ptrs) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -101,6 +101,10 @@ void fused_rows(bpm_plan_s* plan, float2* state, float2* rec, double* pw, int n_
     d.prop_split = plan->d_prop_split ? static_cast<const float2*>(plan->d_prop_split) +
                                             size_t(r) * split_table_stride(plan, 11)
                                       : nullptr;
+    if (plan->split == BPM_SPLIT_FOREST_RUTH && plan->d_stage_prop_split)
+      // [2 tables][half-band table] per row: t dz, (1 - 2t) dz
+      d.prop_split = static_cast<const float2*>(plan->d_stage_prop_split) +
+                     size_t(r) * 2 * split_table_stride(plan, 11);
     if (plan->sep_slices) {
       d.phasor = nullptr;
       d.srows = static_cast<const SepRow*>(plan->d_sep);
@@ -298,7 +302,20 @@ static LaunchShape choose_shape(bpm_plan_s* plan, PlanAux* aux, const void* stat
   LaunchShape rule;
   const int nb = plan->nb, logn = plan->logn;
   if (plan->split == BPM_SPLIT_FOREST_RUTH) {
-    // the fourth-order form: one CTA per row (three propagations per step)
+    // the fourth-order form: N = 4096 rows that each get four SMs on the
+    // half-band split (three propagations per step; the 8000-step bent solve
+    // measured 85.0 ms against 200.3 ms on one CTA), else one CTA per row;
+    // BPM_FUSED_LAYOUT=cta forces the latter
+    int sms = 1, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const char* fv = std::getenv("BPM_FUSED_LAYOUT");
+    const bool cta = fv && std::strcmp(fv, "cta") == 0;
+    if (!cta && logn == 12 && plan->d_stage_prop_split != nullptr && 4 * nb <= sms &&
+        nb <= fused_split4_fr_capacity()) {
+      rule.layout = kLayoutSplit4FR;
+      return rule;
+    }
     rule.layout = kLayoutCtaFR;
     rule.rotated = nb > fused_fr_capacity(logn);
     return rule;
@@ -754,7 +771,7 @@ int bpm_set_splitting(bpm_plan_t plan, int32_t method) {
     return fail(BPM_ERR_INVALID, "unknown splitting method");
   if (method == BPM_SPLIT_FOREST_RUTH && plan->ny > 1)
     return fail(BPM_ERR_INVALID, "3D plans march first order or Verlet");
-  for (void** p : {&plan->d_stage_rows, &plan->d_stage_prop}) {
+  for (void** p : {&plan->d_stage_rows, &plan->d_stage_prop, &plan->d_stage_prop_split}) {
     if (*p) cudaFree(*p);
     *p = nullptr;
   }
@@ -787,6 +804,25 @@ int bpm_set_splitting(bpm_plan_t plan, int32_t method) {
                                       host.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) return cuda_fail(e, "splitting tables");
+      if (plan->d_prop_split) {
+        // nx = 4096 rows that get four SMs: the half-band split's tables of
+        // the t dz and (1 - 2t) dz propagations
+        const size_t hs = size_t(split_table_stride(plan, 11));
+        rc = dev_alloc(plan, &plan->d_stage_prop_split, nb * 2 * hs * sizeof(float2),
+                       "splitting propagators (half-band split)");
+        if (rc != BPM_OK) return rc;
+        std::vector<float2> hh(nb * 2 * hs);
+        for (size_t r = 0; r < nb; ++r)
+          for (int k = 0; k < 2; ++k) {
+            std::vector<float2> tab;
+            split_prop_table_frac(plan, int(r), 11, stages[1 + k].first, &tab);
+            std::copy(tab.begin(), tab.end(), hh.begin() + long((r * 2 + k) * hs));
+          }
+        e = cudaMemcpyAsync(plan->d_stage_prop_split, hh.data(), hh.size() * sizeof(float2),
+                            cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "splitting tables");
+      }
     }
     plan->split = method;
     // the slice form depends on the step form (nx = 4096): prepare again if

@@ -46,6 +46,8 @@ int fused4hh_launch_12(const RowDescF32*, int, int, const float4*, int*, cudaStr
 int fused4hh_rows_resident_12();
 int fused4sh_launch_12(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
 int fused4sh_rows_resident_12();
+int fused4sf_launch_12(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
+int fused4sf_rows_resident_12();
 int fused4_launch_14(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
 int fused4v_launch_13(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
 int fused4v_launch_14(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
@@ -109,6 +111,10 @@ int launch_fused_layout(int logn, const RowDescF32* d_rows, int n_rows, int step
     return fused4s_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
   if (logn == 12 && layout == kLayoutSplit4S)
     return fused4h_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
+  if (layout == kLayoutSplit4FR) {
+    if (logn != 12) return fail(BPM_ERR_INVALID, "fourth-order split layout needs nx = 4096");
+    return fused4sf_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
+  }
   if (layout == kLayoutSplit4Half) {
     switch (logn) {
       case 12:   // 8 points per thread unless the 16-point form is forced
@@ -376,6 +382,17 @@ int fused_split4_half_capacity() {
   int c = cached.load(std::memory_order_relaxed);
   if (c == 0) {
     c = std::min(fused4sh_rows_resident_12(), fused4hh_rows_resident_12());
+    cached.store(c, std::memory_order_relaxed);
+  }
+  return c;
+}
+
+// Rows of N = 4096 one fourth-order half-band-split launch keeps resident.
+int fused_split4_fr_capacity() {
+  static std::atomic<int> cached{0};
+  int c = cached.load(std::memory_order_relaxed);
+  if (c == 0) {
+    c = fused4sf_rows_resident_12();
     cached.store(c, std::memory_order_relaxed);
   }
   return c;

@@ -46,7 +46,7 @@ struct F2Cfg {
   static constexpr int OFF_PH = OFF_ORG + ROWS * 2 * N * 8;           // [ROWS][PHB][N]
   static constexpr int OFF_MBAR = OFF_PH + ROWS * PHB * N * 8;        // [ROWS][PHB]
   static constexpr int OFF_RECPH = OFF_MBAR + ROWS * PHB * 8;
-  static constexpr int OFF_RED = OFF_RECPH + ROWS * 8;                // [ROWS][WPR][2] double
+  static constexpr int OFF_RED = OFF_RECPH + ROWS * 16;               // [ROWS][WPR][2] double
   static constexpr int S1 = NP >= 3 ? (N >> 8) : 1;                   // pass-1 group offsets
   static constexpr int OFF_TW1 = OFF_RED + ROWS * WPR * 2 * 8;        // [S1][16] float2
   static constexpr int OFF_SROW = (OFF_TW1 + S1 * 16 * 8 + 15) / 16 * 16;   // [ROWS][PHB]
@@ -228,7 +228,9 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
   float2* org = reinterpret_cast<float2*>(smem + C::OFF_ORG) + (rl * 2 + band) * N;
   float2* ph0 = reinterpret_cast<float2*>(smem + C::OFF_PH) + rl * (HALF ? 2 : 1) * N;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::OFF_MBAR) + rl * (HALF ? 2 : 1);
-  float2* recph = reinterpret_cast<float2*>(smem + C::OFF_RECPH) + rl;
+  // the records' common phase, two slots by step parity: the lead writes a
+  // record step's phase while a slower warp may still read the previous one
+  float2* recph = reinterpret_cast<float2*>(smem + C::OFF_RECPH) + 2 * rl;
   double* red = reinterpret_cast<double*>(smem + C::OFF_RED) + rl * C::WPR * 2;
   float4* srow0 = reinterpret_cast<float4*>(smem + C::OFF_SROW) + rl * (HALF ? 2 : 1);
   const bool sep = d.srows != nullptr;
@@ -318,7 +320,7 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
       double ang = fmod(double(n + 1 - d.n_phase0) * d.gphase, 6.283185307179586);
       double sa, ca;
       sincos(ang, &sa, &ca);
-      *recph = make_float2(float(ca), float(sa));
+      recph[(n + 1) & 1] = make_float2(float(ca), float(sa));
     }
 #pragma unroll 1
     for (int sg = 0; sg < STAGES; ++sg) {
@@ -418,7 +420,7 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
     const bool want_pw = rec && d.powers != nullptr;
     if (rec) {
       const int slot = (n + 1) / d.record_every - 1;
-      const float2 g = *recph;
+      const float2 g = recph[(n + 1) & 1];
       double s = 0.0;
       float2* r0 = d.records ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
 #pragma unroll

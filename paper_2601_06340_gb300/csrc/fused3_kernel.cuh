@@ -42,7 +42,7 @@ struct F3Cfg {
   static constexpr int OFF_MBAR = OFF_PH + PHB * N * 8;    // [PHB] strain slice barriers
   static constexpr int OFF_XBAR = OFF_MBAR + 8 * PHB;      // [2][WARPS] exchange barriers
   static constexpr int OFF_RECPH = OFF_XBAR + 16 * WARPS;
-  static constexpr int OFF_RED = OFF_RECPH + 8;           // [WARPS] double
+  static constexpr int OFF_RED = OFF_RECPH + 16;          // [WARPS] double
   static constexpr int OFF_SROW = (OFF_RED + WARPS * 8 + 15) / 16 * 16;   // [PHB] row heads
   static constexpr int SMEM = OFF_SROW + PHB * 16;
   static_assert(LOGN >= 9 && LOGN <= 12, "cluster kernel covers 512..4096");
@@ -178,6 +178,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
   float2* ph = reinterpret_cast<float2*>(smem + C::OFF_PH);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::OFF_MBAR);
   uint64_t* xbar = reinterpret_cast<uint64_t*>(smem + C::OFF_XBAR);
+  // the records' common phase, two slots by step parity: the lead writes a
+  // record step's phase while a slower warp may still read the previous one
   float2* recph = reinterpret_cast<float2*>(smem + C::OFF_RECPH);
   double* red = reinterpret_cast<double*>(smem + C::OFF_RED);
   float4* srow0 = reinterpret_cast<float4*>(smem + C::OFF_SROW);
@@ -259,7 +261,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
       double ang = fmod(double(n + 1 - d.n_phase0) * d.gphase, 6.283185307179586);
       double sa, ca;
       sincos(ang, &sa, &ca);
-      *recph = make_float2(float(ca), float(sa));
+      recph[(n + 1) & 1] = make_float2(float(ca), float(sa));
     }
     float2 org[16];
 #pragma unroll
@@ -344,7 +346,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
       const float2* phn = ph + (sep ? 0 : ((it + 1) & 1) * N);
       const SepHead shc = sep ? sep_head(srow0 + (it & 1)) : SepHead{};
       const SepHead shn = (sep && next) ? sep_head(srow0 + ((it + 1) & 1)) : SepHead{};
-      const float2 g = rec ? *recph : make_float2(1.f, 0.f);
+      const float2 g = rec ? recph[(n + 1) & 1] : make_float2(1.f, 0.f);
       const int slot = rec ? (n + 1) / d.record_every - 1 : 0;
       float2* r0 = (rec && d.records) ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
       double s = 0.0;
@@ -414,7 +416,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
 
       if (rec) {
         const int slot = (n + 1) / d.record_every - 1;
-        const float2 g = *recph;
+        const float2 g = recph[(n + 1) & 1];
         double s = 0.0;
         float2* r0 = d.records ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
   #pragma unroll

@@ -70,7 +70,7 @@ struct F4ECfg {
   static constexpr int OFF_CBAR = OFF_GBAR + 16 * WARPS;   // [2][WARPS] psi_p barriers
   static constexpr int OFF_PPEER = OFF_CBAR + 16 * WARPS;  // [2] peer's band-power part
   static constexpr int OFF_RECPH = OFF_PPEER + 16;
-  static constexpr int OFF_RED = OFF_RECPH + 8;            // [WARPS] double
+  static constexpr int OFF_RED = OFF_RECPH + 16;           // [WARPS] double
   static constexpr int OFF_PART = OFF_RED + WARPS * 8;
   static constexpr int OFF_SROW = (OFF_PART + 8 + 15) / 16 * 16;   // [2] row heads
   static constexpr int SMEM = OFF_SROW + 2 * 16;
@@ -155,6 +155,8 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
   uint64_t* gbar = reinterpret_cast<uint64_t*>(smem + C::OFF_GBAR);
   uint64_t* cbar = reinterpret_cast<uint64_t*>(smem + C::OFF_CBAR);
   double* ppeer = reinterpret_cast<double*>(smem + C::OFF_PPEER);
+  // the records' common phase, two slots by step parity: the lead writes a
+  // record step's phase while a slower warp may still read the previous one
   float2* recph = reinterpret_cast<float2*>(smem + C::OFF_RECPH);
   double* red = reinterpret_cast<double*>(smem + C::OFF_RED);
   double* part = reinterpret_cast<double*>(smem + C::OFF_PART);
@@ -259,7 +261,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
       double ang = fmod(double(n + 1 - d.n_phase0) * d.gphase, 6.283185307179586);
       double sa, ca;
       sincos(ang, &sa, &ca);
-      *recph = make_float2(float(ca), float(sa));
+      recph[(n + 1) & 1] = make_float2(float(ca), float(sa));
     }
     float2 org[16];
 #pragma unroll
@@ -380,7 +382,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
       const SepHead shc = sep ? sep_head(srow0 + (HALF_G ? 0 : (it & 1))) : SepHead{};
       const SepHead shn =
           (sep && next) ? sep_head(srow0 + (HALF_G ? 1 : ((it + 1) & 1))) : SepHead{};
-      const float2 g = rec ? *recph : make_float2(1.f, 0.f);
+      const float2 g = rec ? recph[(n + 1) & 1] : make_float2(1.f, 0.f);
       const int slot = rec ? (n + 1) / d.record_every - 1 : 0;
       float2* r0 = (rec && d.records) ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
       double s = 0.0;
@@ -454,7 +456,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
 
       if (rec) {
         const int slot = (n + 1) / d.record_every - 1;
-        const float2 g = *recph;
+        const float2 g = recph[(n + 1) & 1];
         double s = 0.0;
         float2* r0 = d.records ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
   #pragma unroll

@@ -135,7 +135,7 @@ struct F4SCfg {
   static constexpr int OFF_CBAR = OFF_GBAR + 16 * WARPS;   // [2][WARPS] psi_p barriers
   static constexpr int OFF_PPEER = OFF_CBAR + 16 * WARPS;  // [2] peer's band-power part
   static constexpr int OFF_RECPH = OFF_PPEER + 16;
-  static constexpr int OFF_RED = OFF_RECPH + 8;            // [WARPS] double
+  static constexpr int OFF_RED = OFF_RECPH + 16;           // [WARPS] double
   static constexpr int OFF_PART = OFF_RED + WARPS * 8;
   static constexpr int OFF_SROW = (OFF_PART + 8 + 15) / 16 * 16;   // [2] row heads
   static constexpr int SMEM = OFF_SROW + 2 * 16;
@@ -169,19 +169,26 @@ __device__ __forceinline__ void s4_load_last(const float2* buf, float2* v, int t
     for (int j = 0; j < 4; ++j) v[i * 4 + j] = buf[swz8(s4_group(t, i) * 4 + j)];
 }
 
-// HALF = true: the second-order (Verlet) step of Eq. split-op, as in the
-// 2-CTA cluster kernel: after the psi_p swap a CTA holds both bands at its
-// samples, so it applies step n's second half-coupling to both and step
-// n + 1's first half to its own band (8 points per thread: in registers);
-// the launch's first half-step reads the other band from global memory.
-// Step n + 1's slice is fetched a step ahead into the second buffer
-// (separable slices: its row head into the second row-head slot).  Records
-// are taken after step n's second half.
-template <bool EX, bool HALF = false>
+// SCH, the operator splitting of Eq. split-op (as in fused2_kernel.cuh):
+// kSchFirst the first-order step; kSchVerlet the second-order step: after
+// the psi_p swap a CTA holds both bands at its samples, so it applies step
+// n's second half-coupling to both and step n + 1's first half to its own
+// band (8 points per thread: in registers); the launch's first half-step
+// reads the other band from global memory; kSchForestRuth the fourth-order
+// step: the same with three propagations per step (t dz, (1 - 2t) dz, t dz,
+// each with its own half-band tables: the row's prop_split holds those of t
+// dz then those of (1 - 2t) dz) and the inner couplings ((1 - t)/2, in
+// (am1, b)) after the first two; (am1h, bh) are the outer couplings (t/2).
+// The splitting forms fetch step n + 1's slice a step ahead into the second
+// buffer (separable slices: its row head into the second row-head slot);
+// records are taken after step n's last coupling.
+template <bool EX, int SCH = kSchFirst>
 __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg<>::T, 1)
     fused4s_march_kernel(const RowDescF32* __restrict__ rows, int n_rows, int steps,
                          const float4* __restrict__ tw, int* __restrict__ status) {
   namespace cg = cooperative_groups;
+  constexpr bool HALF = SCH != kSchFirst;           // couples before propagating
+  constexpr int STAGES = SCH == kSchForestRuth ? 3 : 1;
   using C = F4SCfg<HALF ? 2 : 1>;
   using F = F8Cfg<11>;
   constexpr int L = 11, M = C::M, N = C::N, T = C::T, NP = F::NP, RL = F::RL;
@@ -207,6 +214,8 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg<>::T, 1)
   uint64_t* gbar = reinterpret_cast<uint64_t*>(smem + C::OFF_GBAR);
   uint64_t* cbar = reinterpret_cast<uint64_t*>(smem + C::OFF_CBAR);
   double* ppeer = reinterpret_cast<double*>(smem + C::OFF_PPEER);
+  // the records' common phase, two slots by step parity: the lead writes a
+  // record step's phase while a slower warp may still read the previous one
   float2* recph = reinterpret_cast<float2*>(smem + C::OFF_RECPH);
   double* red = reinterpret_cast<double*>(smem + C::OFF_RED);
   double* part = reinterpret_cast<double*>(smem + C::OFF_PART);
@@ -246,16 +255,20 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg<>::T, 1)
   // memory; the plan's table [band][D(k) | D(k + M)][position] is in the
   // 16-point form's output order.
   float2 cw[8], d0[8];
+  auto load_tables = [&](const float2* tab) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int p16 = pos16_of_freq2048(cfg_freq<F>(s4_group(t, j / RL) * RL + j % RL));
+      d0[j] = __ldg(&tab[(band * 2 + 0) * M + p16]);
+      e1s[j * T + t] = __ldg(&tab[(band * 2 + 1) * M + p16]);
+    }
+  };
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    const int pos = s4_group(t, j / RL) * RL + j % RL;
-    const int k = cfg_freq<F>(pos);
-    const int p16 = pos16_of_freq2048(k);
-    const float4 a = __ldg(&tw[k]);
+    const float4 a = __ldg(&tw[cfg_freq<F>(s4_group(t, j / RL) * RL + j % RL)]);
     cw[j] = make_float2(a.x, a.y);
-    d0[j] = __ldg(&d.prop_split[(band * 2 + 0) * M + p16]);
-    e1s[j * T + t] = __ldg(&d.prop_split[(band * 2 + 1) * M + p16]);
   }
+  load_tables(d.prop_split);
 
   float2 v[8];
 #pragma unroll
@@ -270,7 +283,10 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg<>::T, 1)
   const uint32_t slice_bytes = uint32_t(N) * 8u;
   bool timed_out = false;
   double my_part = 0.0;
+  // (am1, bb): the step's coupling, or the outer ones of a splitting form;
+  // (am1i, bbi): Forest-Ruth's inner couplings
   const float2 am1 = HALF ? d.am1h : d.am1, bb = HALF ? d.bh : d.b;
+  [[maybe_unused]] const float2 am1i = d.am1, bbi = d.b;
   const bool pow_on = d.powers != nullptr && d.record_every > 0;
   // step n's slice into buffer `slot` (separable: its row head into row-head
   // slot `slot`; the column phasors stay in buffer 0)
@@ -302,7 +318,6 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg<>::T, 1)
 
   for (int it = 0; it < steps; ++it) {
     const int n = d.n_begin + it;
-    const int half = it & 1;
     const bool rec = d.record_every > 0 && ((n + 1) % d.record_every) == 0 &&
                      (d.records != nullptr || d.powers != nullptr);
     // the previous step was a record: its band-power part rides on this step's F
@@ -311,7 +326,18 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg<>::T, 1)
       double ang = fmod(double(n + 1 - d.n_phase0) * d.gphase, 6.283185307179586);
       double sa, ca;
       sincos(ang, &sa, &ca);
-      *recph = make_float2(float(ca), float(sa));
+      recph[(n + 1) & 1] = make_float2(float(ca), float(sa));
+    }
+#pragma unroll 1
+    for (int sg = 0; sg < STAGES; ++sg) {
+    // exchange index of the stage: buffer halves and barrier phases
+    const int ex = it * STAGES + sg;
+    const int half = ex & 1;
+    const uint32_t xpar = uint32_t((ex >> 1) & 1);
+    if constexpr (SCH == kSchForestRuth) {
+      // the stage's tables: (P^t - 1)/N for stages 0 and 2, (P^(1-2t) - 1)/N
+      // for stage 1 (each thread rewrites only its own D(k + M) slots)
+      if (sg > 0) load_tables(d.prop_split + (sg == 1 ? 4 * M : 0));
     }
     float2 org[8];
 #pragma unroll
@@ -320,9 +346,9 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg<>::T, 1)
     f8_twiddle<false>(v, w0);
     f8_store<L, 0>(buf, v, t);
     __syncthreads();
-    if (lead) {
-      // the step's slice (separable: its row head); second order: every
-      // thread is past step it - 1's couplings, which read the other
+    if (lead && sg == 0) {
+      // the step's slice (separable: its row head); the splitting forms:
+      // every thread is past step it - 1's couplings, which read the other
       // buffer: fetch step it + 1's slice into it
       if constexpr (HALF) {
         if (it + 1 < steps) fetch(n + 1, (it + 1) & 1);
@@ -339,7 +365,8 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg<>::T, 1)
     }
     // each warp's F barrier: its 32 threads' slots from the same warp of the peer
     if (lane == 0)
-      mbar_expect_tx(&gbar[half * C::WARPS + warp], 32u * 8u * 8u + ((lead && part_due) ? 8u : 0u));
+      mbar_expect_tx(&gbar[half * C::WARPS + warp],
+                     32u * 8u * 8u + ((lead && part_due && sg == 0) ? 8u : 0u));
     f8_load<L, 1>(buf, v, t);
     dft<8, false, EX>(v);
     f8_twiddle<false>(v, w1);
@@ -361,9 +388,8 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg<>::T, 1)
     }
     // (no barrier before the inverse pass rewrites buf: each thread's
     // last-pass positions are its own in both directions)
-    if (!timed_out && !mbar_wait_cluster(&gbar[half * C::WARPS + warp], uint32_t((it >> 1) & 1)))
-      timed_out = true;
-    if (lead && part_due && h == 0)
+    if (!timed_out && !mbar_wait_cluster(&gbar[half * C::WARPS + warp], xpar)) timed_out = true;
+    if (lead && part_due && sg == 0 && h == 0)
       d.powers[2 * (n / d.record_every - 1) + band] = (my_part + ppeer[half]) * d.dx_um;
     {
       const float2* gi = gx + half * M;
@@ -406,67 +432,84 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg<>::T, 1)
       for (int pp = 0; pp < 4; ++pp)
         st_async_v4(co + uint32_t(xpair(pp, t, T)) * 8u, v[2 * pp], v[2 * pp + 1], cbo);
     }
-    if (!timed_out && !mbar_wait_cluster(&cbar[half * C::WARPS + warp], uint32_t((it >> 1) & 1)))
-      timed_out = true;
+    if (!timed_out && !mbar_wait_cluster(&cbar[half * C::WARPS + warp], xpar)) timed_out = true;
+    const float2* ci = cb + half * M;
     if constexpr (HALF) {
-      const bool next = it + 1 < steps;
-      if (next && !timed_out &&
-          !mbar_wait(bar + ((it + 1) & 1), uint32_t(((it + 1) >> 1) & 1)))
-        timed_out = true;
-      const float2* ci = cb + half * M;
       // (separable: the column phasors of buffer 0 and the row heads of
       // steps it and it + 1)
       const float2* phc = ph + (sep ? 0 : (it & 1) * N);
-      const float2* phn = ph + (sep ? 0 : ((it + 1) & 1) * N);
       const SepHead shc = sep ? sep_head(srow + (it & 1)) : SepHead{};
-      const SepHead shn = (sep && next) ? sep_head(srow + ((it + 1) & 1)) : SepHead{};
-      const float2 g = rec ? *recph : make_float2(1.f, 0.f);
-      const int slot = rec ? (n + 1) / d.record_every - 1 : 0;
-      float2* r0 = (rec && d.records) ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
-      double s = 0.0;
-      auto three_halves = [&](auto S) {
-        constexpr bool SEP = decltype(S)::value;
-        const float2 bc = slice_b<SEP>(bb, shc, band), bo = slice_b<SEP>(bb, shc, band ^ 1);
-        const float2 bn = slice_b<SEP>(bb, shn, band);
-        const uint32_t mc = SEP ? sep_mask<1, 8, 8>(shc, t, h) : 0u;
-        const uint32_t mn = SEP ? sep_mask<1, 8, 8>(shn, t, h) : 0u;
+      if (sg < STAGES - 1) {
+        // Forest-Ruth, after the first two propagations: the inner
+        // couplings ((1 - t)/2) on this step's slice
+        auto couple_inner = [&](auto S) {
+          constexpr bool SEP = decltype(S)::value;
+          const float2 bs = slice_b<SEP>(bbi, shc, band);
+          const uint32_t msk = SEP ? sep_mask<1, 8, 8>(shc, t, h) : 0u;
 #pragma unroll
-        for (int pp = 0; pp < 4; ++pp) {
-          const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
-#pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            const int j = 2 * pp + k;
-            const int m = t + j * T;
-            const int cell = SEP ? m : 2 * m + h;
-            const float2 p = v[j], q = k ? make_float2(q2.z, q2.w) : make_float2(q2.x, q2.y);
-            // step it, second half (this band's and, below, the other band's)
-            float2 c = couple_at<SEP>(p, q, phc, cell, mc, j, band, am1, bc);
-            if (rec) {
-              s = pow_acc(s, c);
-              if (r0)   // records in natural order
-                r0[2 * m + h] = make_float2(fmaf(c.x, g.x, -(c.y * g.y)), fmaf(c.x, g.y, c.y * g.x));
-            }
-            if (next) {   // step it + 1, first half, with the other band's value
-              const float2 co = couple_at<SEP>(q, p, phc, cell, mc, j, band ^ 1, am1, bo);
-              c = couple_at<SEP>(c, co, phn, cell, mn, j, band, am1, bn);
-            }
-            v[j] = c;
+          for (int pp = 0; pp < 4; ++pp) {
+            const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
+            const int m0 = t + 2 * pp * T, m1 = t + (2 * pp + 1) * T;
+            v[2 * pp] = couple_at<SEP>(v[2 * pp], make_float2(q2.x, q2.y), phc,
+                                       SEP ? m0 : 2 * m0 + h, msk, 2 * pp, band, am1i, bs);
+            v[2 * pp + 1] = couple_at<SEP>(v[2 * pp + 1], make_float2(q2.z, q2.w), phc,
+                                           SEP ? m1 : 2 * m1 + h, msk, 2 * pp + 1, band, am1i, bs);
           }
-        }
-      };
-      if (sep) three_halves(BoolC<true>{});
-      else three_halves(BoolC<false>{});
-      if (rec && d.powers) {
-        double ds = s;
+        };
+        if (sep) couple_inner(BoolC<true>{});
+        else couple_inner(BoolC<false>{});
+      } else {
+        const bool next = it + 1 < steps;
+        if (next && !timed_out &&
+            !mbar_wait(bar + ((it + 1) & 1), uint32_t(((it + 1) >> 1) & 1)))
+          timed_out = true;
+        const float2* phn = ph + (sep ? 0 : ((it + 1) & 1) * N);
+        const SepHead shn = (sep && next) ? sep_head(srow + ((it + 1) & 1)) : SepHead{};
+        const float2 g = rec ? recph[(n + 1) & 1] : make_float2(1.f, 0.f);
+        const int slot = rec ? (n + 1) / d.record_every - 1 : 0;
+        float2* r0 = (rec && d.records) ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
+        double s = 0.0;
+        auto three_halves = [&](auto S) {
+          constexpr bool SEP = decltype(S)::value;
+          const float2 bc = slice_b<SEP>(bb, shc, band), bo = slice_b<SEP>(bb, shc, band ^ 1);
+          const float2 bn = slice_b<SEP>(bb, shn, band);
+          const uint32_t mc = SEP ? sep_mask<1, 8, 8>(shc, t, h) : 0u;
+          const uint32_t mn = SEP ? sep_mask<1, 8, 8>(shn, t, h) : 0u;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, off);
-        if (lane == 0) red[warp] = ds;   // summed by the lead after the next barrier
+          for (int pp = 0; pp < 4; ++pp) {
+            const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+              const int j = 2 * pp + k;
+              const int m = t + j * T;
+              const int cell = SEP ? m : 2 * m + h;
+              const float2 p = v[j], q = k ? make_float2(q2.z, q2.w) : make_float2(q2.x, q2.y);
+              // step it, last coupling (this band's and, below, the other band's)
+              float2 c = couple_at<SEP>(p, q, phc, cell, mc, j, band, am1, bc);
+              if (rec) {
+                s = pow_acc(s, c);
+                if (r0)   // records in natural order
+                  r0[2 * m + h] = make_float2(fmaf(c.x, g.x, -(c.y * g.y)), fmaf(c.x, g.y, c.y * g.x));
+              }
+              if (next) {   // step it + 1, first coupling, with the other band's value
+                const float2 co = couple_at<SEP>(q, p, phc, cell, mc, j, band ^ 1, am1, bo);
+                c = couple_at<SEP>(c, co, phn, cell, mn, j, band, am1, bn);
+              }
+              v[j] = c;
+            }
+          }
+        };
+        if (sep) three_halves(BoolC<true>{});
+        else three_halves(BoolC<false>{});
+        if (rec && d.powers) {
+          double ds = s;
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, off);
+          if (lane == 0) red[warp] = ds;   // summed by the lead after the next barrier
+        }
       }
-      continue;
-    }
-    if (!timed_out && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
-    {
-      const float2* ci = cb + half * M;
+    } else {
+      if (!timed_out && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
       const SepHead sh = sep ? sep_head(srow) : SepHead{};
       auto couple_all = [&](auto S) {
         constexpr bool SEP = decltype(S)::value;
@@ -485,27 +528,29 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg<>::T, 1)
       };
       if (sep) couple_all(BoolC<true>{});
       else couple_all(BoolC<false>{});
-    }
-    if (rec) {
-      const int slot = (n + 1) / d.record_every - 1;
-      const float2 g = *recph;
-      double s = 0.0;
-      float2* r0 = d.records ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
+      if (rec) {
+        const int slot = (n + 1) / d.record_every - 1;
+        const float2 g = recph[(n + 1) & 1];
+        double s = 0.0;
+        float2* r0 = d.records ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const float2 p = v[j];
-        s = pow_acc(s, p);
-        if (r0)
-          r0[2 * (t + j * T) + h] =
-              make_float2(fmaf(p.x, g.x, -(p.y * g.y)), fmaf(p.x, g.y, p.y * g.x));
-      }
-      if (d.powers) {
-        double ds = s;
+        for (int j = 0; j < 8; ++j) {
+          const float2 p = v[j];
+          s = pow_acc(s, p);
+          if (r0)
+            r0[2 * (t + j * T) + h] =
+                make_float2(fmaf(p.x, g.x, -(p.y * g.y)), fmaf(p.x, g.y, p.y * g.x));
+        }
+        if (d.powers) {
+          double ds = s;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, off);
-        if (lane == 0) red[warp] = ds;   // summed by the lead after the next barrier
+          for (int off = 16; off > 0; off >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, off);
+          if (lane == 0) red[warp] = ds;   // summed by the lead after the next barrier
+        }
       }
     }
+    }   // stages (the Forest-Ruth step ends on the t dz tables, which its
+        // next step starts with)
   }
 
   __syncthreads();

@@ -54,8 +54,8 @@ struct FusedCfg {
   static constexpr int OFF_BUF = 0;                                  // [ROWS][2][PADN] float2
   static constexpr int OFF_PH = OFF_BUF + ROWS * 2 * PADN * 8;       // [ROWS][PHB][N] float2
   static constexpr int OFF_MBAR = OFF_PH + ROWS * PHB * N * 8;       // [ROWS][PHB] u64
-  static constexpr int OFF_RECPH = OFF_MBAR + ROWS * PHB * 8;        // [ROWS] float2
-  static constexpr int OFF_RED = OFF_RECPH + ROWS * 8;               // [ROWS][WARPS][2] double
+  static constexpr int OFF_RECPH = OFF_MBAR + ROWS * PHB * 8;        // [ROWS][2] float2
+  static constexpr int OFF_RED = OFF_RECPH + ROWS * 16;              // [ROWS][WARPS][2] double
   static constexpr int OFF_SROW =                                    // [ROWS][PHB] row heads
       (OFF_RED + ROWS * WARPS_PER_ROW * 2 * 8 + 15) / 16 * 16;
   static constexpr int SMEM = OFF_SROW + ROWS * PHB * 16;
@@ -404,7 +404,9 @@ __global__ void __launch_bounds__(FusedCfg<LOGN>::THREADS)
   float2* b1 = b0 + C::PADN;
   float2* ph0 = reinterpret_cast<float2*>(smem + C::OFF_PH) + rl * (HALF ? 2 : 1) * N;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::OFF_MBAR) + rl * (HALF ? 2 : 1);
-  float2* recph = reinterpret_cast<float2*>(smem + C::OFF_RECPH) + rl;
+  // the records' common phase, two slots by step parity: the lead writes a
+  // record step's phase while a slower warp may still read the previous one
+  float2* recph = reinterpret_cast<float2*>(smem + C::OFF_RECPH) + 2 * rl;
   double* red = reinterpret_cast<double*>(smem + C::OFF_RED) + rl * C::WARPS_PER_ROW * 2;
   float4* srow0 = reinterpret_cast<float4*>(smem + C::OFF_SROW) + rl * (HALF ? 2 : 1);
   const bool sep = d.srows != nullptr;
@@ -467,7 +469,7 @@ __global__ void __launch_bounds__(FusedCfg<LOGN>::THREADS)
       double ang = fmod(double(n + 1 - d.n_phase0) * d.gphase, 6.283185307179586);
       double sa, ca;
       sincos(ang, &sa, &ca);
-      *recph = make_float2(float(ca), float(sa));
+      recph[(n + 1) & 1] = make_float2(float(ca), float(sa));
     }
     if constexpr (HALF) {
       // one thread per row (N <= 16) has no barrier in the step: it is past
@@ -568,7 +570,7 @@ __global__ void __launch_bounds__(FusedCfg<LOGN>::THREADS)
     const int slot = rec ? (n + 1) / d.record_every - 1 : 0;
     double s0 = 0.0, s1 = 0.0;
     if (rec) {
-      const float2 g = *recph;
+      const float2 g = recph[(n + 1) & 1];
       float2* r0 = d.records ? d.records + size_t(slot) * 2 * N : nullptr;
 #pragma unroll
       for (int i = 0; i < G0; ++i)

@@ -89,20 +89,20 @@ int fused4h_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const f
 }
 
 // N = 4096 as a half-band split with 8 points per thread (fused4s_kernel.cuh);
-// HALF the second-order step.
-template <bool EX, bool HALF = false>
+// SCH the operator splitting.
+template <bool EX, int SCH = kSchFirst>
 int fused4s_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const float4* d_tw,
                         int* d_status, cudaStream_t st) {
-  using C = F4SCfg<HALF ? 2 : 1>;
+  using C = F4SCfg<SCH != kSchFirst ? 2 : 1>;
   static std::atomic<bool> configured{false};
   if (!configured.load(std::memory_order_acquire)) {
-    cudaError_t e = cudaFuncSetAttribute(fused4s_march_kernel<EX, HALF>,
+    cudaError_t e = cudaFuncSetAttribute(fused4s_march_kernel<EX, SCH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused4s)");
     configured.store(true, std::memory_order_release);
   }
-  fused4s_march_kernel<EX, HALF><<<4 * n_rows, C::T, C::SMEM, st>>>(d_rows, n_rows, steps, d_tw,
-                                                                    d_status);
+  fused4s_march_kernel<EX, SCH><<<4 * n_rows, C::T, C::SMEM, st>>>(d_rows, n_rows, steps, d_tw,
+                                                                   d_status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "fused4s march launch");
   return BPM_OK;
@@ -340,13 +340,23 @@ int fused4_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
                : fused4s_launch_impl<false>(r, n, s, tw, status, st);             \
   }                                                                               \
   int fused4sh_rows_resident_12() {                                               \
-    return clusters_resident(fused4s_march_kernel<true, true>, 4, F4SCfg<2>::T,   \
-                             F4SCfg<2>::SMEM);                                    \
+    return clusters_resident(fused4s_march_kernel<true, kSchVerlet>, 4,           \
+                             F4SCfg<2>::T, F4SCfg<2>::SMEM);                      \
   }                                                                               \
   int fused4sh_launch_12(const RowDescF32* r, int n, int s, const float4* tw,    \
                          int* status, cudaStream_t st) {                          \
     return fused_exact_constants()                                                \
-               ? fused4s_launch_impl<true, true>(r, n, s, tw, status, st)         \
-               : fused4s_launch_impl<false, true>(r, n, s, tw, status, st);       \
+               ? fused4s_launch_impl<true, kSchVerlet>(r, n, s, tw, status, st)   \
+               : fused4s_launch_impl<false, kSchVerlet>(r, n, s, tw, status, st); \
+  }                                                                               \
+  int fused4sf_rows_resident_12() {                                               \
+    return clusters_resident(fused4s_march_kernel<true, kSchForestRuth>, 4,       \
+                             F4SCfg<2>::T, F4SCfg<2>::SMEM);                      \
+  }                                                                               \
+  int fused4sf_launch_12(const RowDescF32* r, int n, int s, const float4* tw,    \
+                         int* status, cudaStream_t st) {                          \
+    return fused_exact_constants()                                                \
+               ? fused4s_launch_impl<true, kSchForestRuth>(r, n, s, tw, status, st) \
+               : fused4s_launch_impl<false, kSchForestRuth>(r, n, s, tw, status, st); \
   }                                                                               \
   }

@@ -79,6 +79,7 @@ CASES = [
     (4096, 400, None, FIRST, 2),         # half-band split, 8 points per thread
     (4096, 400, "split16", FIRST, 8),    # half-band split, 16 points per thread
     (4096, 400, None, VERLET, 5),        # the 8-point split's Verlet form
+    (4096, 200, None, FR, 9),            # the 8-point split's Forest-Ruth form
     (4096, 400, "split16", VERLET, 5),   # the 16-point split's Verlet form
     (8192, 300, None, FIRST, -1),        # split band, two parts
     (8192, 300, None, VERLET, 5),
