@@ -151,13 +151,16 @@ int bpm_set_strain(bpm_plan_t plan, int32_t kind, const double* ux_um,
  * the full-step propagation; at nx = 4096 one 4-CTA half-band split per
  * solve while every solve gets four SMs, else one 2-CTA cluster per solve
  * while every solve gets two SMs and 512 <= nx != 2048, else one CTA per
- * solve) and Forest-Ruth (one CTA per solve: the leading coupling, then
- * three propagate-and-couple stages with the propagator increments of t dz
- * and (1 - 2t) dz, tabulated here once), and for nx = 8192, 16384 Verlet
- * (one split-band cluster per solve) and Forest-Ruth stage by stage (per
- * step a coupling launch and three one-step launches of the first-order
- * split-band kernel with the stage's tables; several times slower, and
- * refused under stream capture); 3D plans take the first-order step
+ * solve) and Forest-Ruth (the leading coupling, then three
+ * propagate-and-couple stages with the propagator increments of t dz and
+ * (1 - 2t) dz, tabulated here once; at nx = 4096 one 4-CTA half-band split
+ * per solve while every solve gets four SMs, else one CTA per solve), for
+ * nx = 8192 Verlet and Forest-Ruth on one split-band cluster per solve, and
+ * for nx = 16384 Verlet (one split-band cluster per solve) and Forest-Ruth
+ * stage by stage (per step a coupling launch and three one-step launches
+ * of the first-order split-band kernel with the stage's tables; several
+ * times slower, and refused under stream capture; BPM_FUSED_LAYOUT=staged
+ * takes it at nx = 8192 too); 3D plans take the first-order step
  * and Verlet (the row kernel, which holds both bands of a line, applies the
  * half-step couplings); other combinations return BPM_ERR_INVALID.
  * bpm_submit takes FP32 plans set to Verlet (one CTA per row as well), not
@@ -343,9 +346,10 @@ int bpm_march_f64_noalloc(void* d_psi, int32_t nx, int32_t n_rows, const void* d
 /* Launch shape of the plan's last FP32 march (the fused kernels of the
  * step of Eq. fov10): *layout = 9 the Forest-Ruth step on one 4-CTA
  * cluster per row (nx = 4096 half-band split, while every row gets four
- * SMs), 8 the nx = 4096 half-band split with 16 points per thread (forced
- * by BPM_FUSED_LAYOUT=split16), 7 the Forest-Ruth step stage by stage
- * (nx >= 8192), 6 one CTA per row with the Forest-Ruth step (plans set to
+ * SMs; nx = 8192 split band), 8 the nx = 4096 half-band split with 16
+ * points per thread (forced by BPM_FUSED_LAYOUT=split16), 7 the Forest-Ruth
+ * step stage by stage (nx = 16384, or nx = 8192 with
+ * BPM_FUSED_LAYOUT=staged), 6 one CTA per row with the Forest-Ruth step (plans set to
  * BPM_SPLIT_FOREST_RUTH), 5 one split-band cluster per row with
  * the Verlet step (nx = 4096, 8192, 16384), 4 one 2-CTA cluster per row with the Verlet
  * step, 3 one CTA per row with the Verlet step (plans set to

@@ -222,10 +222,11 @@ def bpm_march_f64_noalloc(d_psi, nx, n_rows, d_prop, d_coupling, d_phasor, n_beg
 
 def bpm_launch_shape(plan) -> tuple[int, int]:
     """(layout, chunk) of the plan's last FP32 march: layout 9 the
-    Forest-Ruth step on the N = 4096 half-band split, 8 the 16-point form of
-    that split (forced), 7 the Forest-Ruth step stage by stage (nx >= 8192),
-    6 the Forest-Ruth step on one CTA per row; layouts 5, 4, 3 the
-    Verlet step on the N = 4096 half-band split, a two-CTA cluster or one
+    Forest-Ruth step on the N = 4096 half-band split or the N = 8192 split
+    band, 8 the 16-point form of the N = 4096 split (forced), 7 the
+    Forest-Ruth step stage by stage (N = 16384; N = 8192 forced), 6 the
+    Forest-Ruth step on one CTA per row; layouts 5, 4, 3 the Verlet step on
+    a split-band cluster (N = 4096, 8192, 16384), a two-CTA cluster or one
     CTA per row; 2 four-CTA cluster per row (N = 4096 half-band
     split), 1 two-CTA cluster per row, 0 CTA per row, -1 the fixed rule;
     chunk 0 for one launch."""

@@ -164,8 +164,9 @@ struct bpm_plan_s {
   void* d_stage_rows = nullptr;      // RowDescF64 [n_stages][B]
   void* d_stage_prop = nullptr;      // FP64: double2 [tables][B][2][nx]; FP32 Forest-Ruth:
                                      // float2 [B][2 tables][2][nx] (t dz, (1 - 2t) dz)
-  void* d_stage_prop_split = nullptr;   // FP32 Forest-Ruth at nx = 4096 on the half-band
-                                        // split: float2 [B][2 tables][half-band table]
+  void* d_stage_prop_split = nullptr;   // FP32 Forest-Ruth on the split kernels (nx = 4096
+                                        // half-band split, nx = 8192 split band): float2
+                                        // [B][2 tables][split table in thread order]
   size_t device_bytes = 0;
   int pending = 0;                // tickets not yet finished
   // launch shape of the last fused march: layout 1 cluster / 0 CTA / -1 rule,
@@ -276,15 +277,16 @@ constexpr int kLayoutClusterHalf = 4;
 constexpr int kLayoutSplit4Half = 5;
 // one CTA per row, fourth-order (Forest-Ruth) step, N <= 4096
 constexpr int kLayoutCtaFR = 6;
-// the fourth-order step stage by stage (N = 8192, 16384): a coupling launch
-// and three one-step launches of the split-band kernels per step
+// the fourth-order step stage by stage (N = 16384; N = 8192 when
+// BPM_FUSED_LAYOUT=staged): a coupling launch and three one-step launches
+// of the split-band kernels per step
 constexpr int kLayoutStagedFR = 7;
 // one 4-CTA cluster per row (N = 4096 half-band split) with 16 points per
 // thread (fused4e_march_kernel<11>); layout 2 runs the 8-point form
 // (fused4s_kernel.cuh), measured 5 % faster
 constexpr int kLayoutSplit4S = 8;
-// one 4-CTA cluster per row (N = 4096 half-band split, 8 points per thread),
-// fourth-order (Forest-Ruth) step
+// fourth-order (Forest-Ruth) step on one 4-CTA cluster per row: the N = 4096
+// half-band split (8 points per thread) or the N = 8192 split band
 constexpr int kLayoutSplit4FR = 9;
 // Coupling alone (the leading coupling of a step), on rows[0..nb): each row's
 // state [2][nx], the slice of step n of its stream (stored per part for
@@ -297,6 +299,9 @@ int fused_fr_capacity(int logn);     // logn <= 12
 int fused_cluster_half_capacity(int logn);   // 9 <= logn <= 12
 int fused_split4_half_capacity();            // N = 4096
 int fused_split4_fr_capacity();              // N = 4096
+// Positions of the Forest-Ruth stage tables in the split kernels' thread
+// order (logn 12: the half-band split, 13: the split band), M per band table.
+int fr_split_table_order(int logn, std::vector<int>* pos);
 int fused_rows_per_cta(int logn);
 int fused_threads(int logn);
 

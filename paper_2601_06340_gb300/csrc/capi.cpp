@@ -102,9 +102,9 @@ void fused_rows(bpm_plan_s* plan, float2* state, float2* rec, double* pw, int n_
                                             size_t(r) * split_table_stride(plan, 11)
                                       : nullptr;
     if (plan->split == BPM_SPLIT_FOREST_RUTH && plan->d_stage_prop_split)
-      // [2 tables][half-band table] per row: t dz, (1 - 2t) dz
+      // [2 tables][split table in thread order] per row: t dz, (1 - 2t) dz
       d.prop_split = static_cast<const float2*>(plan->d_stage_prop_split) +
-                     size_t(r) * 2 * split_table_stride(plan, 11);
+                     size_t(r) * 2 * split_table_stride(plan, plan->logn == kSplitLogN ? 12 : 11);
     if (plan->sep_slices) {
       d.phasor = nullptr;
       d.srows = static_cast<const SepRow*>(plan->d_sep);
@@ -296,6 +296,18 @@ static double time_trial(bpm_plan_s* plan, PlanAux* aux, const LaunchShape& sh, 
   return best;
 }
 
+// Forest-Ruth plans that march stage by stage: N = 16384, and N = 8192 when
+// BPM_FUSED_LAYOUT=staged (N = 8192 otherwise runs the split band's fused
+// fourth-order form).
+static bool fr_staged(const bpm_plan_s* plan) {
+  if (plan->precision != BPM_FP32_FUSED || plan->split != BPM_SPLIT_FOREST_RUTH ||
+      plan->logn < kSplitLogN)
+    return false;
+  if (plan->logn > kSplitLogN || plan->d_stage_prop_split == nullptr) return true;
+  const char* fv = std::getenv("BPM_FUSED_LAYOUT");
+  return fv && std::strcmp(fv, "staged") == 0;
+}
+
 static LaunchShape choose_shape(bpm_plan_s* plan, PlanAux* aux, const void* state, int n_begin,
                                 int steps, cudaStream_t st) {
   NvtxRange nvtx("bpm_launch_shape_search");
@@ -309,6 +321,10 @@ static LaunchShape choose_shape(bpm_plan_s* plan, PlanAux* aux, const void* stat
     int sms = 1, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (logn == kSplitLogN) {   // N = 8192 (staged plans do not get here)
+      rule.layout = kLayoutSplit4FR;
+      return rule;
+    }
     const char* fv = std::getenv("BPM_FUSED_LAYOUT");
     const bool cta = fv && std::strcmp(fv, "cta") == 0;
     if (!cta && logn == 12 && plan->d_stage_prop_split != nullptr && 4 * nb <= sms &&
@@ -526,8 +542,7 @@ static int enqueue_march(bpm_plan_s* plan, PlanAux* aux, void* state, void* d_re
                              int(plane_of(plan)), steps, plan->dx_um * plan->dy_um, final_pw,
                              pw_stride, st);
   }
-  if (plan->precision == BPM_FP32_FUSED && plan->split == BPM_SPLIT_FOREST_RUTH &&
-      plan->logn >= kSplitLogN) {
+  if (fr_staged(plan)) {
     int rc = march_staged_fr(plan, aux, state, d_rec, d_pw, n_begin, n_end, captured, st);
     if (rc != BPM_OK) return rc;
     return launch_finish_f32(static_cast<const float2*>(state),
@@ -804,19 +819,27 @@ int bpm_set_splitting(bpm_plan_t plan, int32_t method) {
                                       host.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) return cuda_fail(e, "splitting tables");
-      if (plan->d_prop_split) {
-        // nx = 4096 rows that get four SMs: the half-band split's tables of
-        // the t dz and (1 - 2t) dz propagations
-        const size_t hs = size_t(split_table_stride(plan, 11));
+      if (plan->d_prop_split || plan->logn == kSplitLogN) {
+        // the split kernels' fused forms (nx = 4096 rows that get four SMs,
+        // nx = 8192): the tables of the t dz and (1 - 2t) dz propagations,
+        // [band][D(k) | D(k + M)] in the kernels' thread order
+        const int slog = plan->logn == kSplitLogN ? 12 : 11;
+        std::vector<int> pos;
+        rc = fr_split_table_order(plan->logn, &pos);
+        if (rc != BPM_OK) return rc;
+        const size_t hs = size_t(split_table_stride(plan, slog)), m = pos.size();
+        if (hs != 4 * m) return fail(BPM_ERR_INVALID, "split table layout");
         rc = dev_alloc(plan, &plan->d_stage_prop_split, nb * 2 * hs * sizeof(float2),
-                       "splitting propagators (half-band split)");
+                       "splitting propagators (split kernels)");
         if (rc != BPM_OK) return rc;
         std::vector<float2> hh(nb * 2 * hs);
         for (size_t r = 0; r < nb; ++r)
           for (int k = 0; k < 2; ++k) {
             std::vector<float2> tab;
-            split_prop_table_frac(plan, int(r), 11, stages[1 + k].first, &tab);
-            std::copy(tab.begin(), tab.end(), hh.begin() + long((r * 2 + k) * hs));
+            split_prop_table_frac(plan, int(r), slog, stages[1 + k].first, &tab);
+            float2* dst = hh.data() + (r * 2 + k) * hs;
+            for (size_t q = 0; q < 4; ++q)
+              for (size_t i = 0; i < m; ++i) dst[q * m + i] = tab[q * m + size_t(pos[i])];
           }
         e = cudaMemcpyAsync(plan->d_stage_prop_split, hh.data(), hh.size() * sizeof(float2),
                             cudaMemcpyHostToDevice, st);

@@ -3,11 +3,13 @@
 #include <cstdlib>
 #include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "fused_kernel.cuh"
 #include "fused2_kernel.cuh"
 #include "fused4_kernel.cuh"
 #include "fused4t_kernel.cuh"
+#include "fused4s_kernel.cuh"
 
 namespace bpm {
 
@@ -48,6 +50,7 @@ int fused4sh_launch_12(const RowDescF32*, int, int, const float4*, int*, cudaStr
 int fused4sh_rows_resident_12();
 int fused4sf_launch_12(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
 int fused4sf_rows_resident_12();
+int fused4f_launch_13(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
 int fused4_launch_14(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
 int fused4v_launch_13(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
 int fused4v_launch_14(const RowDescF32*, int, int, const float4*, int*, cudaStream_t);
@@ -112,8 +115,12 @@ int launch_fused_layout(int logn, const RowDescF32* d_rows, int n_rows, int step
   if (logn == 12 && layout == kLayoutSplit4S)
     return fused4h_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
   if (layout == kLayoutSplit4FR) {
-    if (logn != 12) return fail(BPM_ERR_INVALID, "fourth-order split layout needs nx = 4096");
-    return fused4sf_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
+    switch (logn) {
+      case 12: return fused4sf_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 13: return fused4f_launch_13(d_rows, n_rows, steps, d_tw, d_status, st);
+      default:
+        return fail(BPM_ERR_INVALID, "fourth-order split layout needs nx = 4096 or 8192");
+    }
   }
   if (layout == kLayoutSplit4Half) {
     switch (logn) {
@@ -385,6 +392,29 @@ int fused_split4_half_capacity() {
     cached.store(c, std::memory_order_relaxed);
   }
   return c;
+}
+
+// Positions of the Forest-Ruth stage tables in the split kernels' thread
+// order: entry j T + t of a band's D(k) or D(k + M) table (M entries) holds
+// the position that thread t reads as its point j of the last pass, in the
+// N = 4096 half-band split (8 points per thread) or the N = 8192 split band
+// (16), computed by the kernels' own mapping.
+int fr_split_table_order(int logn, std::vector<int>* pos) {
+  if (logn == 12) {
+    using C = F4SCfg<>;
+    pos->assign(C::M, 0);
+    for (int j = 0; j < C::M / C::T; ++j)
+      for (int t = 0; t < C::T; ++t) (*pos)[j * C::T + t] = s4_table_pos(t, j);
+    return BPM_OK;
+  }
+  if (logn == 13) {
+    using C = F4ECfg<12>;
+    pos->assign(C::M, 0);
+    for (int j = 0; j < C::M / C::T; ++j)
+      for (int t = 0; t < C::T; ++t) (*pos)[j * C::T + t] = f4e_table_pos<12>(t, j);
+    return BPM_OK;
+  }
+  return fail(BPM_ERR_INVALID, "thread-order tables exist for nx = 4096 and 8192 only");
 }
 
 // Rows of N = 4096 one fourth-order half-band-split launch keeps resident.

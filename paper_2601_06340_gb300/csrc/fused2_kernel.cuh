@@ -69,7 +69,7 @@ struct F2Cfg {
 };
 
 template <int LOGN, int P>
-__device__ __forceinline__ int f2_pos(int gi, int j) {
+__host__ __device__ __forceinline__ int f2_pos(int gi, int j) {
   using C = F2Cfg<LOGN>;
   constexpr int S = C::stride(P), L = C::len(P);
   return (gi / S) * L + (gi % S) + j * S;
@@ -84,7 +84,7 @@ __device__ __forceinline__ int f2_pos(int gi, int j) {
 // with itself alone.  Both directions and every table lookup of the last
 // pass must use the same choice.
 template <int LOGN, int P, bool WL = false>
-__device__ __forceinline__ int f2_group(int t, int i) {
+__host__ __device__ __forceinline__ int f2_group(int t, int i) {
   using C = F2Cfg<LOGN>;
   if constexpr (WL && P == C::NP - 1 && C::RL < 16)
     return (t >> 4) * (16 * C::groups(P)) + i * 16 + (t & 15);

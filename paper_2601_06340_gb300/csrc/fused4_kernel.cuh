@@ -102,6 +102,17 @@ __device__ __forceinline__ int local_freq(int pos) {
   return freq;
 }
 
+// Table position of thread t's point j of the last pass (the local
+// transform's output order), where the plan's split tables hold D(k_j) and
+// D(k_j + M).  (The Forest-Ruth stage tables are kept in thread order
+// instead: entry j T + t.)
+template <int LM>
+__host__ __device__ __forceinline__ int f4e_table_pos(int t, int j) {
+  using F = F2Cfg<LM>;
+  constexpr int R = F::radix(F::NP - 1);
+  return f2_pos<LM, F::NP - 1>(f2_group<LM, F::NP - 1, true>(t, j / R), j % R);
+}
+
 __device__ __forceinline__ void st_async_f64(uint32_t raddr, double v, uint32_t rbar) {
   asm volatile(
       "st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(raddr),
@@ -124,11 +135,22 @@ __device__ __forceinline__ void st_async_f64(uint32_t raddr, double v, uint32_t 
 // slice buffer for the launch (position m holds column 2m + h), and every
 // slice copy above carries the step's row head instead, into row-head slot
 // 0 (slot 1 for the next step's), on the same barriers.
-template <int LM, bool EX, bool HALF = false>
+// SCH, the operator splitting of Eq. split-op (as in fused2_kernel.cuh):
+// kSchFirst the first-order step, kSchVerlet the second-order step above,
+// kSchForestRuth (N = 8192) the fourth-order step as in fused4s_kernel.cuh:
+// three propagations per step with the tables of t dz, (1 - 2t) dz, t dz
+// (the row's prop_split holds those of t dz, then those of (1 - 2t) dz, in
+// thread order) and the inner couplings (1 - t)/2, in (am1, b), on the
+// step's slice after the first two; the next slice is staged in the peer
+// spectrum half of the last propagation, whose couplings read it.
+template <int LM, bool EX, int SCH = kSchFirst>
 __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
     fused4e_march_kernel(const RowDescF32* __restrict__ rows, int n_rows, int steps,
                          const float4* __restrict__ tw, int* __restrict__ status) {
   namespace cg = cooperative_groups;
+  constexpr bool HALF = SCH != kSchFirst;           // couples before propagating
+  constexpr int STAGES = SCH == kSchForestRuth ? 3 : 1;
+  static_assert(SCH != kSchForestRuth || LM == 12, "the fourth-order form is N = 8192's");
   // second-order step with the next slice staged in the peer spectrum
   // buffer (N = 8192) instead of a second slice buffer (N = 4096)
   constexpr bool HALF_G = HALF && LM == 12;
@@ -192,15 +214,27 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
   // shared memory (table [band][D(k) | D(k + M)][position]).
   const float2* dtab = C::NAT ? d.prop_split : d.prop;
   float2 cw[16], d0[16];
+  // Forest-Ruth: a stage's tables, [band][D(k) | D(k + M)][j T + t] in
+  // thread order (the row's prop_split), so that a warp's loads are
+  // coalesced (each thread rewrites only its own D(k + M) slots)
+  [[maybe_unused]] auto load_tables = [&](const float2* tab) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      d0[j] = __ldg(&tab[(band * 2 + 0) * M + j * T + t]);
+      e1s[j * T + t] = __ldg(&tab[(band * 2 + 1) * M + j * T + t]);
+    }
+  };
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
-    const int pos = f2_pos<L, NP - 1>(f2_group<L, NP - 1, true>(t, j / F::radix(NP - 1)),
-                                      j % F::radix(NP - 1));
+    const int pos = f4e_table_pos<L>(t, j);
     const float4 a = __ldg(&tw[local_freq<L>(pos)]);
     cw[j] = make_float2(a.x, a.y);
-    d0[j] = __ldg(&dtab[(band * 2 + 0) * M + pos]);
-    e1s[j * T + t] = __ldg(&dtab[(band * 2 + 1) * M + pos]);
+    if constexpr (SCH != kSchForestRuth) {
+      d0[j] = __ldg(&dtab[(band * 2 + 0) * M + pos]);
+      e1s[j * T + t] = __ldg(&dtab[(band * 2 + 1) * M + pos]);
+    }
   }
+  if constexpr (SCH == kSchForestRuth) load_tables(d.prop_split);
 
   float2 v[16];
 #pragma unroll
@@ -218,7 +252,10 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
   const uint32_t slice_bytes = uint32_t(C::PH) * 8u;
   bool timed_out = false;
   double my_part = 0.0;
+  // (am1, bb): the step's coupling, or the outer ones of a splitting form;
+  // (am1i, bbi): Forest-Ruth's inner couplings
   const float2 am1 = HALF ? d.am1h : d.am1, bb = HALF ? d.bh : d.b;
+  [[maybe_unused]] const float2 am1i = d.am1, bbi = d.b;
   const bool pow_on = d.powers != nullptr && d.record_every > 0;
   // step n's slice (the CTA's part of it) into `dst` (separable: its row
   // head into row-head slot `slot`)
@@ -252,7 +289,6 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
 
   for (int it = 0; it < steps; ++it) {
     const int n = d.n_begin + it;
-    const int half = it & 1;
     const bool rec = d.record_every > 0 && ((n + 1) % d.record_every) == 0 &&
                      (d.records != nullptr || d.powers != nullptr);
     // the previous step was a record: its band-power part rides on this step's G
@@ -263,6 +299,18 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
       sincos(ang, &sa, &ca);
       recph[(n + 1) & 1] = make_float2(float(ca), float(sa));
     }
+    // one stage of the step (Forest-Ruth: three; the others: one, with no
+    // loop around it)
+    auto stage = [&](const int sg) {
+    // exchange index of the stage: buffer halves and barrier phases
+    const int ex = it * STAGES + sg;
+    const int half = ex & 1;
+    const uint32_t xpar = uint32_t((ex >> 1) & 1);
+    if constexpr (SCH == kSchForestRuth) {
+      // the stage's tables: (P^t - 1)/N for stages 0 and 2, (P^(1-2t) - 1)/N
+      // for stage 1
+      if (sg > 0) load_tables(d.prop_split + (sg == 1 ? 4 * M : 0));
+    }
     float2 org[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) org[j] = v[j];
@@ -270,7 +318,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
     f2_twiddle<false>(v, w0);
     f2_store<L, 0>(buf, v, t);
     __syncthreads();
-    if (lead) {
+    if (lead && sg == 0) {
       if constexpr (HALF_G) {
         // this step's slice into the one buffer (phase it + 1: the launch's
         // first half-step took phase 0); the next one goes to L2 now and to
@@ -296,7 +344,8 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
     }
     // each warp's F barrier: its 32 threads' slots from the same warp of the peer
     if (lane == 0)
-      mbar_expect_tx(&gbar[half * C::WARPS + warp], 32u * 16u * 8u + ((lead && part_due) ? 8u : 0u));
+      mbar_expect_tx(&gbar[half * C::WARPS + warp],
+                     32u * 16u * 8u + ((lead && part_due && sg == 0) ? 8u : 0u));
     f2_load<L, 1>(buf, v, t);
     dft<16, false, EX>(v);
     f2_twiddle<false>(v, w1);
@@ -316,9 +365,8 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
     }
     // (no barrier before the inverse pass rewrites buf: each thread's
     // last-pass positions are its own in both directions)
-    if (!timed_out && !mbar_wait_cluster(&gbar[half * C::WARPS + warp], uint32_t((it >> 1) & 1)))
-      timed_out = true;
-    if (lead && part_due && h == 0)
+    if (!timed_out && !mbar_wait_cluster(&gbar[half * C::WARPS + warp], xpar)) timed_out = true;
+    if (lead && part_due && sg == 0 && h == 0)
       d.powers[2 * (n / d.record_every - 1) + band] = (my_part + ppeer[half]) * d.dx_um;
     {
       const float2* gi = gx + half * M;
@@ -337,12 +385,13 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
     }
     f2_dft<L, NP - 1, true, EX>(v);
     f2_store<L, NP - 1, true>(buf, v, t);
-    // (the next-slice copy of the second-order step waits for every thread
-    // to be past the combine)
-    tail_sync<!HALF_G>();
-    if constexpr (HALF_G) {
-      // every thread is past the combine, the last reader of gx[half]
+    if (HALF_G && sg == STAGES - 1) {
+      // the next-slice copy of a splitting form waits for every thread to be
+      // past the combine, the last reader of gx[half]
+      __syncthreads();
       if (lead && it + 1 < steps) fetch(n + 1, gx + half * M, 1, bar + 1);
+    } else {
+      __syncwarp();
     }
     f2_load<L, 1>(buf, v, t);
     f2_twiddle<true>(v, w1);
@@ -362,12 +411,12 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
       for (int pp = 0; pp < 8; ++pp)
         st_async_v4(co + uint32_t(xpair(pp, t, T)) * 8u, v[2 * pp], v[2 * pp + 1], cbo);
     }
-    if (!timed_out && !mbar_wait_cluster(&cbar[half * C::WARPS + warp], uint32_t((it >> 1) & 1)))
-      timed_out = true;
+    if (!timed_out && !mbar_wait_cluster(&cbar[half * C::WARPS + warp], xpar)) timed_out = true;
     if constexpr (HALF) {
-      const bool next = it + 1 < steps;
+      const bool last = sg == STAGES - 1;
+      const bool next = last && it + 1 < steps;
       if constexpr (HALF_G) {
-        if (!timed_out && !mbar_wait(bar, uint32_t((it + 1) & 1))) timed_out = true;
+        if (sg == 0 && !timed_out && !mbar_wait(bar, uint32_t((it + 1) & 1))) timed_out = true;
         if (next && !timed_out && !mbar_wait(bar + 1, uint32_t(it & 1))) timed_out = true;
       } else {
         if (next && !timed_out &&
@@ -375,62 +424,84 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
           timed_out = true;
       }
       const float2* ci = cb + half * M;
-      // (separable: both couplings read the column phasors of buffer 0 and
+      // (separable: the couplings read the column phasors of buffer 0 and
       // the row heads of steps it and it + 1)
       const float2* phc = (HALF_G || sep) ? ph : ph + (it & 1) * C::PH;
-      const float2* phn = sep ? ph : HALF_G ? gx + half * M : ph + ((it + 1) & 1) * C::PH;
       const SepHead shc = sep ? sep_head(srow0 + (HALF_G ? 0 : (it & 1))) : SepHead{};
-      const SepHead shn =
-          (sep && next) ? sep_head(srow0 + (HALF_G ? 1 : ((it + 1) & 1))) : SepHead{};
-      const float2 g = rec ? recph[(n + 1) & 1] : make_float2(1.f, 0.f);
-      const int slot = rec ? (n + 1) / d.record_every - 1 : 0;
-      float2* r0 = (rec && d.records) ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
-      double s = 0.0;
-      // a loop over shared memory (three couplings per point unrolled over
-      // 16 points would overflow the instruction cache); buf is free once
-      // every thread is past the inverse pass 0, and again for the next
-      // step once every thread has taken its points back
-      __syncthreads();
+      if (STAGES > 1 && !last) {
+        // Forest-Ruth, after the first two propagations: the inner
+        // couplings ((1 - t)/2) on this step's slice
+        auto couple_inner = [&](auto S) {
+          constexpr bool SEP = decltype(S)::value;
+          const float2 bs = slice_b<SEP>(bbi, shc, band);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) buf[t + j * T] = v[j];
-      auto three_halves = [&](auto S) {
-        constexpr bool SEP = decltype(S)::value;
-        const float2 bc = slice_b<SEP>(bb, shc, band), bo = slice_b<SEP>(bb, shc, band ^ 1);
-        const float2 bn = slice_b<SEP>(bb, shn, band);
-#pragma unroll 1
-        for (int pp = 0; pp < 8; ++pp) {
-          const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
-#pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            const int j = 2 * pp + k;
-            const int m = t + j * T;
-            const int cell = (SEP || !C::NAT) ? m : 2 * m + h;
-            const float2 p = buf[m], q = k ? make_float2(q2.z, q2.w) : make_float2(q2.x, q2.y);
-            const float2 e = slice_at<SEP>(phc, shc, cell, 2 * m + h);
-            float2 c = couple_cell(p, q, e, band, am1, bc);   // step it, second half
-            if (rec) {
-              s = pow_acc(s, c);
-              if (r0)   // records in natural order
-                r0[2 * m + h] = make_float2(fmaf(c.x, g.x, -(c.y * g.y)), fmaf(c.x, g.y, c.y * g.x));
-            }
-            if (next) {   // step it + 1, first half, with the other band's value
-              const float2 co = couple_cell(q, p, e, band ^ 1, am1, bo);
-              c = couple_cell(c, co, slice_at<SEP>(phn, shn, cell, 2 * m + h), band, am1, bn);
-            }
-            buf[m] = c;
+          for (int pp = 0; pp < 8; ++pp) {
+            const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
+            const int m0 = t + 2 * pp * T, m1 = t + (2 * pp + 1) * T;
+            const int c0 = (SEP || !C::NAT) ? m0 : 2 * m0 + h;
+            const int c1 = (SEP || !C::NAT) ? m1 : 2 * m1 + h;
+            v[2 * pp] = couple_cell(v[2 * pp], make_float2(q2.x, q2.y),
+                                    slice_at<SEP>(phc, shc, c0, 2 * m0 + h), band, am1i, bs);
+            v[2 * pp + 1] = couple_cell(v[2 * pp + 1], make_float2(q2.z, q2.w),
+                                        slice_at<SEP>(phc, shc, c1, 2 * m1 + h), band, am1i, bs);
           }
+        };
+        if (sep) couple_inner(BoolC<true>{});
+        else couple_inner(BoolC<false>{});
+      } else {
+        const float2* phn = sep ? ph : HALF_G ? gx + half * M : ph + ((it + 1) & 1) * C::PH;
+        const SepHead shn =
+            (sep && next) ? sep_head(srow0 + (HALF_G ? 1 : ((it + 1) & 1))) : SepHead{};
+        const float2 g = rec ? recph[(n + 1) & 1] : make_float2(1.f, 0.f);
+        const int slot = rec ? (n + 1) / d.record_every - 1 : 0;
+        float2* r0 = (rec && d.records) ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
+        double s = 0.0;
+        // a loop over shared memory (three couplings per point unrolled over
+        // 16 points would overflow the instruction cache); buf is free once
+        // every thread is past the inverse pass 0, and again for the next
+        // step once every thread has taken its points back
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) buf[t + j * T] = v[j];
+        auto three_halves = [&](auto S) {
+          constexpr bool SEP = decltype(S)::value;
+          const float2 bc = slice_b<SEP>(bb, shc, band), bo = slice_b<SEP>(bb, shc, band ^ 1);
+          const float2 bn = slice_b<SEP>(bb, shn, band);
+#pragma unroll 1
+          for (int pp = 0; pp < 8; ++pp) {
+            const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+              const int j = 2 * pp + k;
+              const int m = t + j * T;
+              const int cell = (SEP || !C::NAT) ? m : 2 * m + h;
+              const float2 p = buf[m], q = k ? make_float2(q2.z, q2.w) : make_float2(q2.x, q2.y);
+              const float2 e = slice_at<SEP>(phc, shc, cell, 2 * m + h);
+              float2 c = couple_cell(p, q, e, band, am1, bc);   // step it, second half
+              if (rec) {
+                s = pow_acc(s, c);
+                if (r0)   // records in natural order
+                  r0[2 * m + h] = make_float2(fmaf(c.x, g.x, -(c.y * g.y)), fmaf(c.x, g.y, c.y * g.x));
+              }
+              if (next) {   // step it + 1, first half, with the other band's value
+                const float2 co = couple_cell(q, p, e, band ^ 1, am1, bo);
+                c = couple_cell(c, co, slice_at<SEP>(phn, shn, cell, 2 * m + h), band, am1, bn);
+              }
+              buf[m] = c;
+            }
+          }
+        };
+        if (sep) three_halves(BoolC<true>{});
+        else three_halves(BoolC<false>{});
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = buf[t + j * T];
+        __syncthreads();
+        if (rec && d.powers) {
+          double ds = s;
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, off);
+          if (lane == 0) red[warp] = ds;   // summed by the lead after the next barrier
         }
-      };
-      if (sep) three_halves(BoolC<true>{});
-      else three_halves(BoolC<false>{});
-#pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = buf[t + j * T];
-      __syncthreads();
-      if (rec && d.powers) {
-        double ds = s;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, off);
-        if (lane == 0) red[warp] = ds;   // summed by the lead after the next barrier
       }
     } else {
       if (!timed_out && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
@@ -459,7 +530,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
         const float2 g = recph[(n + 1) & 1];
         double s = 0.0;
         float2* r0 = d.records ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
-  #pragma unroll
+#pragma unroll
         for (int j = 0; j < 16; ++j) {
           const float2 p = v[j];
           s = pow_acc(s, p);
@@ -469,12 +540,20 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
         }
         if (d.powers) {
           double ds = s;
-  #pragma unroll
+#pragma unroll
           for (int off = 16; off > 0; off >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, off);
           if (lane == 0) red[warp] = ds;   // summed by the lead after the next barrier
         }
       }
     }
+    };
+    if constexpr (STAGES == 1) {
+      stage(0);
+    } else {
+#pragma unroll 1
+      for (int sg = 0; sg < STAGES; ++sg) stage(sg);
+    }   // (the Forest-Ruth step ends on the t dz tables, which its next step
+        // starts with)
   }
 
   __syncthreads();

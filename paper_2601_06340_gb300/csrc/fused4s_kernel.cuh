@@ -97,7 +97,7 @@ __device__ __forceinline__ void f8_twiddle(float2* v, const float2* w) {
 
 // Spectral index of position `pos` of the forward transform's output.
 template <typename Cfg>
-__device__ __forceinline__ int cfg_freq(int pos) {
+__host__ __device__ __forceinline__ int cfg_freq(int pos) {
   int rem = pos, len = Cfg::N, freq = 0, mult = 1;
 #pragma unroll
   for (int p = 0; p < Cfg::NP; ++p) {
@@ -112,7 +112,7 @@ __device__ __forceinline__ int cfg_freq(int pos) {
 
 // Position of frequency k in the 16-point form's output order (radices 16,
 // 16, 8 for 2048 points): the inverse of local_freq<11>.
-__device__ __forceinline__ int pos16_of_freq2048(int k) {
+__host__ __device__ __forceinline__ int pos16_of_freq2048(int k) {
   return (k & 15) * 128 + ((k >> 4) & 15) * 8 + (k >> 8);
 }
 
@@ -153,7 +153,18 @@ struct F4SCfg {
 // pass 2 (stride 4) of warp w already address only that block, so between
 // passes 1, 2 and 3 (in both directions) a warp waits for itself alone; only
 // the passes to and from pass 0 (stride 256) need the whole CTA.
-__device__ __forceinline__ int s4_group(int t, int i) { return (t >> 5) * 64 + i * 32 + (t & 31); }
+__host__ __device__ __forceinline__ int s4_group(int t, int i) {
+  return (t >> 5) * 64 + i * 32 + (t & 31);
+}
+
+// Table position of thread t's point j of the last pass: the 16-point
+// form's output position of its frequency k_j, where the plan's half-band
+// tables hold D(k_j) and D(k_j + M).  (The Forest-Ruth stage tables are kept
+// in thread order instead: entry j T + t.)
+__host__ __device__ __forceinline__ int s4_table_pos(int t, int j) {
+  using F = F8Cfg<11>;
+  return pos16_of_freq2048(cfg_freq<F>(s4_group(t, j / F::RL) * F::RL + j % F::RL));
+}
 
 __device__ __forceinline__ void s4_store_last(float2* buf, const float2* v, int t) {
 #pragma unroll
@@ -255,25 +266,28 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4SCfg<>::T, 1)
   // memory; the plan's table [band][D(k) | D(k + M)][position] is in the
   // 16-point form's output order.
   float2 cw[8], d0[8];
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int k = cfg_freq<F>(s4_group(t, j / RL) * RL + j % RL);
-    const int p16 = pos16_of_freq2048(k);
-    const float4 a = __ldg(&tw[k]);
-    cw[j] = make_float2(a.x, a.y);
-    d0[j] = __ldg(&d.prop_split[(band * 2 + 0) * M + p16]);
-    e1s[j * T + t] = __ldg(&d.prop_split[(band * 2 + 1) * M + p16]);
-  }
-  // Forest-Ruth: a stage's tables (each thread rewrites only its own
-  // D(k + M) slots)
+  // Forest-Ruth: a stage's tables, [band][D(k) | D(k + M)][j T + t] in
+  // thread order, so that a warp's loads are coalesced (each thread
+  // rewrites only its own D(k + M) slots)
   [[maybe_unused]] auto load_tables = [&](const float2* tab) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const int p16 = pos16_of_freq2048(cfg_freq<F>(s4_group(t, j / RL) * RL + j % RL));
-      d0[j] = __ldg(&tab[(band * 2 + 0) * M + p16]);
-      e1s[j * T + t] = __ldg(&tab[(band * 2 + 1) * M + p16]);
+      d0[j] = __ldg(&tab[(band * 2 + 0) * M + j * T + t]);
+      e1s[j * T + t] = __ldg(&tab[(band * 2 + 1) * M + j * T + t]);
     }
   };
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int k = cfg_freq<F>(s4_group(t, j / RL) * RL + j % RL);
+    const float4 a = __ldg(&tw[k]);
+    cw[j] = make_float2(a.x, a.y);
+    if constexpr (SCH != kSchForestRuth) {
+      const int p16 = s4_table_pos(t, j);
+      d0[j] = __ldg(&d.prop_split[(band * 2 + 0) * M + p16]);
+      e1s[j * T + t] = __ldg(&d.prop_split[(band * 2 + 1) * M + p16]);
+    }
+  }
+  if constexpr (SCH == kSchForestRuth) load_tables(d.prop_split);
 
   float2 v[8];
 #pragma unroll

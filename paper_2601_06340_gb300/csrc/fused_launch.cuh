@@ -73,16 +73,17 @@ int fused2_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
 template <bool EX, bool HALF = false>
 int fused4h_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const float4* d_tw,
                         int* d_status, cudaStream_t st) {
+  constexpr int SCH = HALF ? kSchVerlet : kSchFirst;
   using C = F4ECfg<11, HALF ? 2 : 1>;
   static std::atomic<bool> configured{false};
   if (!configured.load(std::memory_order_acquire)) {
-    cudaError_t e = cudaFuncSetAttribute(fused4e_march_kernel<11, EX, HALF>,
+    cudaError_t e = cudaFuncSetAttribute(fused4e_march_kernel<11, EX, SCH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused4h)");
     configured.store(true, std::memory_order_release);
   }
-  fused4e_march_kernel<11, EX, HALF><<<4 * n_rows, C::T, C::SMEM, st>>>(d_rows, n_rows, steps,
-                                                                        d_tw, d_status);
+  fused4e_march_kernel<11, EX, SCH><<<4 * n_rows, C::T, C::SMEM, st>>>(d_rows, n_rows, steps,
+                                                                       d_tw, d_status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "fused4h march launch");
   return BPM_OK;
@@ -158,14 +159,15 @@ int fused3_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
 
 // Split-band cluster kernels for N = 4096 P (cluster of 2P CTAs per row):
 // both run the one-exchange form (P = 4 with its tables in tensor memory).
-// HALF: the second-order (Verlet) step.
-template <int P, bool EX, bool HALF = false>
+// SCH: the operator splitting (Forest-Ruth: P = 2 only).
+template <int P, bool EX, int SCH = kSchFirst>
 int fused4_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const float4* d_tw,
                        int* d_status, cudaStream_t st) {
   static_assert(P == 2 || P == 4, "N = 8192 or 16384");
+  static_assert(P == 2 || SCH != kSchForestRuth, "fourth-order split band: N = 8192");
   auto kern = [] {
-    if constexpr (P == 2) return fused4e_march_kernel<12, EX, HALF>;
-    else return fused4t_march_kernel<EX, HALF>;
+    if constexpr (P == 2) return fused4e_march_kernel<12, EX, SCH>;
+    else return fused4t_march_kernel<EX, SCH != kSchFirst>;
   }();
   constexpr int smem = P == 2 ? F4ECfg<12>::SMEM : F4TCfg::SMEM;
   constexpr int threads = P == 2 ? F4ECfg<12>::T : F4TCfg::T;
@@ -202,8 +204,23 @@ int fused4_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
   int fused4v_launch_##L(const RowDescF32* r, int n, int s, const float4* tw,    \
                          int* status, cudaStream_t st) {                          \
     return fused_exact_constants()                                                \
-               ? fused4_launch_impl<P, true, true>(r, n, s, tw, status, st)       \
-               : fused4_launch_impl<P, false, true>(r, n, s, tw, status, st);     \
+               ? fused4_launch_impl<P, true, kSchVerlet>(r, n, s, tw, status, st) \
+               : fused4_launch_impl<P, false, kSchVerlet>(r, n, s, tw, status, st); \
+  }                                                                               \
+  }
+
+// fourth-order (Forest-Ruth) form of the N = 8192 split band
+#define BPM_INSTANTIATE_FUSED4F                                                   \
+  namespace bpm {                                                                 \
+  int fused4f_rows_resident_13() {                                                \
+    return clusters_resident(fused4e_march_kernel<12, true, kSchForestRuth>, 4,  \
+                             F4ECfg<12>::T, F4ECfg<12>::SMEM);                    \
+  }                                                                               \
+  int fused4f_launch_13(const RowDescF32* r, int n, int s, const float4* tw,     \
+                        int* status, cudaStream_t st) {                           \
+    return fused_exact_constants()                                                \
+               ? fused4_launch_impl<2, true, kSchForestRuth>(r, n, s, tw, status, st) \
+               : fused4_launch_impl<2, false, kSchForestRuth>(r, n, s, tw, status, st); \
   }                                                                               \
   }
 
@@ -315,7 +332,7 @@ int fused4_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
 #define BPM_INSTANTIATE_FUSED4HH                                                  \
   namespace bpm {                                                                 \
   int fused4hh_rows_resident_12() {                                               \
-    return clusters_resident(fused4e_march_kernel<11, true, true>, 4,             \
+    return clusters_resident(fused4e_march_kernel<11, true, kSchVerlet>, 4,       \
                              F4ECfg<11, 2>::T, F4ECfg<11, 2>::SMEM);              \
   }                                                                               \
   int fused4hh_launch_12(const RowDescF32* r, int n, int s, const float4* tw,    \

@@ -22,7 +22,8 @@ VERLET = binding.BPM_SPLIT_VERLET
 FR = binding.BPM_SPLIT_FOREST_RUTH
 
 # (nx, BPM_FUSED_LAYOUT, splitting): one CTA, the 2-CTA cluster, the
-# half-band split (8 and 16 points per thread), the split bands
+# half-band split (8 and 16 points per thread), the split bands (N = 8192
+# with each step form: the next slice staged in the peer spectrum buffer)
 CASES = [
     (64, None, FIRST),
     (1024, "cta", FIRST),
@@ -33,6 +34,8 @@ CASES = [
     (4096, None, VERLET),
     (4096, None, FR),
     (8192, None, FIRST),
+    (8192, None, VERLET),
+    (8192, None, FR),
     (16384, None, FIRST),
 ]
 

@@ -83,7 +83,8 @@ CASES = [
     (4096, 400, "split16", VERLET, 5),   # the 16-point split's Verlet form
     (8192, 300, None, FIRST, -1),        # split band, two parts
     (8192, 300, None, VERLET, 5),
-    (8192, 120, None, FR, 7),            # stage by stage (coupling-only launches)
+    (8192, 120, None, FR, 9),            # the split band's Forest-Ruth form
+    (8192, 120, "staged", FR, 7),        # stage by stage (coupling-only launches)
     (16384, 300, None, FIRST, -1),       # split band, four parts (TMEM tables)
     (16384, 300, None, VERLET, 5),
 ]
@@ -96,8 +97,8 @@ GEOMETRIES = ["bragg", "laue"]
 @pytest.fixture(scope="module")
 def sep_refs():
     """The oracle marches of every case, started at once in the spawn pool."""
-    return {(g, c[0], c[1], c[3]): submit_ref(_bent(c[0], c[1], g), method=METHOD[c[3]])
-            for g in GEOMETRIES for c in CASES}
+    keys = {(g, c[0], c[1], c[3]) for g in GEOMETRIES for c in CASES}
+    return {k: submit_ref(_bent(k[1], k[2], k[0]), method=METHOD[k[3]]) for k in sorted(keys)}
 
 
 @pytest.mark.parametrize("geometry", GEOMETRIES)

@@ -196,19 +196,33 @@ def test_verlet_split_band_matches_oracle(bpm_lib, nx, seed):
     assert diff > 1e-6 and diff > max(errs), (diff, errs)
 
 
-@pytest.mark.parametrize("nx", [8192, 16384])
-def test_forest_ruth_split_band_matches_oracle(bpm_lib, nx):
-    """N = 8192 and 16384 with the fourth-order step run stage by stage (a
-    coupling launch and three one-step launches of the split-band kernel per
-    step): a dislocated asymmetric Bragg request against the oracle's
-    Forest-Ruth march, fields, records and powers; different from the
-    first-order and Verlet marches by more than its own error."""
+@pytest.mark.parametrize("nx,layout,want", [
+    (8192, None, 9),        # the split band's fused fourth-order form
+    (8192, "staged", 7),    # stage by stage, forced
+    (16384, None, 7),       # stage by stage
+])
+def test_forest_ruth_split_band_matches_oracle(bpm_lib, monkeypatch, nx, layout, want):
+    """N = 8192 with the fourth-order step fused into the split-band kernel
+    (three propagations per step, each with its own tables, in one launch),
+    and N = 16384 (or 8192, forced) run stage by stage (a coupling launch
+    and three one-step launches of the split-band kernel per step): a
+    dislocated asymmetric Bragg request against the oracle's Forest-Ruth
+    march, fields, records and powers, and a resumed march equal to the
+    whole; different from the first-order and Verlet marches by more than
+    its own error."""
+    if layout:
+        monkeypatch.setenv("BPM_FUSED_LAYOUT", layout)
+    else:
+        monkeypatch.delenv("BPM_FUSED_LAYOUT", raising=False)
     wl = inputs.serving_request(np.random.default_rng(2), nx, 200)
     wl.record_every = 60
     ref = run_ref(wl, method="forest_ruth")
     with binding.Plan(wl, FP32, splitting=binding.BPM_SPLIT_FOREST_RUTH) as plan:
         out = plan.propagate()
-        assert binding.bpm_launch_shape(plan.handle) == (7, 0)
+        assert binding.bpm_launch_shape(plan.handle) == (want, 0)
+        first = plan.propagate(n_begin=0, n_end=77)
+        rest = plan.propagate(psi_in=first.psi, n_begin=77, n_end=wl.nz)
+    assert max(band_errors(rest.psi, ref.psi)) <= TOL_FP32
     errs = band_errors(out.psi, ref.psi, out.records, ref.records)
     assert max(errs) <= TOL_FP32, errs
     assert np.allclose(out.powers, ref.powers, rtol=1e-4, atol=1e-9 * ref.powers.max())
