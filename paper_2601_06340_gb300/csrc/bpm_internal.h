@@ -302,6 +302,9 @@ int fused_split4_fr_capacity();              // N = 4096
 // Positions of the Forest-Ruth stage tables in the split kernels' thread
 // order (logn 12: the half-band split, 13: the split band), M per band table.
 int fr_split_table_order(int logn, std::vector<int>* pos);
+// ... and of the one-CTA kernels (thread order for 256 <= nx <= 4096,
+// position order below), nx per band table.
+int fr_cta_table_order(int logn, std::vector<int>* pos);
 int fused_rows_per_cta(int logn);
 int fused_threads(int logn);
 

@@ -801,18 +801,26 @@ int bpm_set_splitting(bpm_plan_t plan, int32_t method) {
     // propagator increments of its t dz and (1 - 2t) dz stages
     if (method == BPM_SPLIT_FOREST_RUTH) {
       const size_t ts = fr_table_stride(plan);
-      int rc = dev_alloc(plan, &plan->d_stage_prop, nb * 2 * ts * sizeof(float2),
-                         "splitting propagators");
+      // nx <= 4096: [band][nx] in the one-CTA kernels' thread order
+      std::vector<int> cpos;
+      int rc = plan->logn < kSplitLogN ? fr_cta_table_order(plan->logn, &cpos) : BPM_OK;
+      if (rc != BPM_OK) return rc;
+      rc = dev_alloc(plan, &plan->d_stage_prop, nb * 2 * ts * sizeof(float2),
+                     "splitting propagators");
       if (rc != BPM_OK) return rc;
       std::vector<float2> host(nb * 2 * ts);
       for (size_t r = 0; r < nb; ++r)
         for (int k = 0; k < 2; ++k) {
           std::vector<float2> tab;
-          if (plan->logn >= kSplitLogN)
+          float2* dst = host.data() + (r * 2 + k) * ts;
+          if (plan->logn >= kSplitLogN) {
             split_prop_table_frac(plan, int(r), 12, stages[1 + k].first, &tab);
-          else
+            std::copy(tab.begin(), tab.end(), dst);
+          } else {
             fused_prop_table_frac(plan, int(r), stages[1 + k].first, &tab);
-          std::copy(tab.begin(), tab.end(), host.begin() + long((r * 2 + k) * ts));
+            for (size_t b = 0; b < 2; ++b)
+              for (size_t i = 0; i < n; ++i) dst[b * n + i] = tab[b * n + size_t(cpos[i])];
+          }
         }
       cudaStream_t st = aux_of(plan)->stream;
       cudaError_t e = cudaMemcpyAsync(plan->d_stage_prop, host.data(),

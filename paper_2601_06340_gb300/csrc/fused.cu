@@ -417,6 +417,33 @@ int fr_split_table_order(int logn, std::vector<int>* pos) {
   return fail(BPM_ERR_INVALID, "thread-order tables exist for nx = 4096 and 8192 only");
 }
 
+template <int LOGN>
+static void f2_table_order(std::vector<int>* pos) {
+  using C = F2Cfg<LOGN>;
+  pos->assign(C::N, 0);
+  for (int k = 0; k < C::E; ++k)
+    for (int t = 0; t < C::T; ++t) (*pos)[k * C::T + t] = f2_table_pos<LOGN>(t, k);
+}
+
+// Positions of the Forest-Ruth stage tables of the one-CTA kernels: for
+// 256 <= N <= 4096 the band-per-thread kernel's thread order (entry k T + t
+// of a band's table holds the position of thread t's point k of the last
+// pass), for N <= 128 the position order itself.
+int fr_cta_table_order(int logn, std::vector<int>* pos) {
+  switch (logn) {
+    case 8: f2_table_order<8>(pos); return BPM_OK;
+    case 9: f2_table_order<9>(pos); return BPM_OK;
+    case 10: f2_table_order<10>(pos); return BPM_OK;
+    case 11: f2_table_order<11>(pos); return BPM_OK;
+    case 12: f2_table_order<12>(pos); return BPM_OK;
+    default: break;
+  }
+  if (logn < 3 || logn > 7) return fail(BPM_ERR_INVALID, "one-CTA tables exist for nx <= 4096");
+  pos->resize(size_t(1) << logn);
+  for (size_t i = 0; i < pos->size(); ++i) (*pos)[i] = int(i);
+  return BPM_OK;
+}
+
 // Rows of N = 4096 one fourth-order half-band-split launch keeps resident.
 int fused_split4_fr_capacity() {
   static std::atomic<int> cached{0};

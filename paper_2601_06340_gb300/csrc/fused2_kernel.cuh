@@ -92,6 +92,16 @@ __host__ __device__ __forceinline__ int f2_group(int t, int i) {
     return t + i * C::T;
 }
 
+// Table position of thread t's point k = i RL + j of the last pass, where
+// the plan's propagator tables hold (P - 1)/N per band.  (The Forest-Ruth
+// stage tables are kept in thread order instead: entry k T + t of a band.)
+template <int LOGN>
+__host__ __device__ __forceinline__ int f2_table_pos(int t, int k) {
+  using C = F2Cfg<LOGN>;
+  constexpr int P = C::NP - 1;
+  return f2_pos<LOGN, P>(f2_group<LOGN, P, C::TAIL_WARP>(t, k / C::RL), k % C::RL);
+}
+
 template <int LOGN, int P, bool WL = false>
 __device__ __forceinline__ void f2_store(float2* buf, const float2* v, int t) {
   using C = F2Cfg<LOGN>;
@@ -263,17 +273,15 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
   const float2* tw1o = tw1 + (t % C::S1);
 
   // this thread's slice of (P - 1)/N in the last pass (for the whole launch;
-  // the fourth-order step reloads it per stage, see below)
+  // the fourth-order step reloads it per stage, see below, from its stage
+  // tables in thread order, so that a warp's loads are coalesced)
   float2 pr[16];
   auto load_table = [&](const float2* tab) {
-    constexpr int P = NP - 1;
 #pragma unroll
-    for (int i = 0; i < C::groups(P); ++i)
-#pragma unroll
-      for (int j = 0; j < RL; ++j)
-        pr[i * RL + j] = active ? __ldg(&tab[band * N + f2_pos<LOGN, P>(
-                                                f2_group<LOGN, P, C::TAIL_WARP>(t, i), j)])
-                                : make_float2(0.f, 0.f);
+    for (int k = 0; k < 16; ++k) {
+      const int at = SCH == kSchForestRuth ? k * T + t : f2_table_pos<LOGN>(t, k);
+      pr[k] = active ? __ldg(&tab[band * N + at]) : make_float2(0.f, 0.f);
+    }
   };
   load_table(d.prop);
   float2 v[16];
