@@ -470,6 +470,63 @@ def configs_run(dev, stream, barrier, max_over_ranks, world, rank, refs=None, st
     return out
 
 
+SPLIT_CHECK_STEPS = 600
+SPLIT_SIZES = (4096, 8192)
+SPLIT_METHODS = (("first_order", "BPM_SPLIT_FIRST_ORDER"), ("verlet", "BPM_SPLIT_VERLET"),
+                 ("forest_ruth", "BPM_SPLIT_FOREST_RUTH"))
+
+
+def split_workload(nx: int):
+    """The bent Bragg solve (Nz = 8000) at Nx = 4096 (the headline workload)
+    or 8192 (dx halved: the same 819 um window at twice the resolution)."""
+    from paper_2601_06340_gb300 import inputs
+    return inputs.bragg_bent(nx=nx, dx_um=min(0.2, 800.0 / nx))
+
+
+def splitting_run(dev, stream, barrier, max_over_ranks, world, rank, refs=None, steps=3):
+    """The operator splittings of Eq. split-op on the fused FP32 path: each
+    scheme's whole 8000-step march of the bent solve at Nx = 4096 and 8192
+    (the launch shape the rule picks), and the error of its first
+    SPLIT_CHECK_STEPS steps against the oracle's march with the same scheme."""
+    import torch
+    from paper_2601_06340_gb300 import binding
+    out = {}
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for nx in SPLIT_SIZES:
+        wl = split_workload(nx)
+        wl.record_every = 0
+        row = {"nx": wl.nx, "nz": wl.nz}
+        for name, const in SPLIT_METHODS:
+            plan = binding.Plan(wl, binding.BPM_FP32_FUSED, splitting=getattr(binding, const))
+            x = torch.from_numpy(wl.psi0.astype(np.complex64)).to(dev)
+            y = torch.empty_like(x)
+
+            def march(n_end=wl.nz):
+                binding.bpm_propagate_device(plan.handle, x, y, None, None, 0, n_end,
+                                             stream.cuda_stream)
+            march()
+            barrier()
+            ev = timed_ms(march, steps, stream, flush)
+            barrier()
+            ms = max_over_ranks(sum(elapsed(ev))) / steps
+            r = {"value": world * wl.cell_updates / (ms * 1e-3), "unit": UNIT,
+                 "ms_per_march": ms, "us_per_step": 1e3 * ms / wl.nz,
+                 "launch_layout": binding.bpm_launch_shape(plan.handle)[0],
+                 "slice_form": ["stream", "separable"][binding.bpm_slice_form(plan.handle)[0]]}
+            if refs:
+                march(SPLIT_CHECK_STEPS)
+                torch.cuda.synchronize()
+                ref, _ = refs[(nx, name)].result()
+                r["rel_l2_err_first_%d_steps" % SPLIT_CHECK_STEPS] = rel_l2_bands(
+                    y.cpu().numpy().astype(np.complex128), ref.psi)
+            row[name] = r
+            plan.close()
+        out[str(nx)] = row
+    out["tolerance"] = 2e-4
+    out["l2"] = L2_NOTE
+    return out
+
+
 def run_reference(args, rank, world):
     """FP64 oracle on the host cores: each step is a bounded sample (the
     first `sample_steps` z-steps of the march)."""
@@ -588,6 +645,10 @@ def run_gpu(args, rks):
             jobs["configs"] = {"laue_perfect": sub(inputs.laue_perfect(), record_every=0),
                                "asym_dislocation": sub(inputs.asym_dislocation(),
                                                        record_every=0)}
+        if not args.skip_splitting:
+            jobs["splitting"] = {(nx, name): sub(split_workload(nx), record_every=0,
+                                                 n_end=SPLIT_CHECK_STEPS, method=name)
+                                 for nx in SPLIT_SIZES for name, _ in SPLIT_METHODS}
         if not args.skip_volume:
             jobs["volume"] = pool.submit(oracle_job, inputs.cube_dislocation_3d(),
                                          dict(record_every=0), True)
@@ -737,6 +798,12 @@ def run_gpu(args, rks):
         configs = configs_run(dev, stream, barrier, max_over_ranks, world, rank,
                               refs=jobs.get("configs"))
 
+    # ---- operator splittings (Eq. split-op) on the fused path --------------
+    splitting = None
+    if not args.skip_splitting:
+        splitting = splitting_run(dev, stream, barrier, max_over_ranks, world, rank,
+                                  refs=jobs.get("splitting"))
+
     # ---- 3D: both transverse coordinates -----------------------------------
     volume = None
     if not args.skip_volume:
@@ -747,7 +814,7 @@ def run_gpu(args, rks):
     serving = None
     if not args.skip_serving and rank == 0:
         # the host must be quiet for a real-time replay: wait for the pool
-        for key in ("head", "batched", "rocking", "configs", "volume"):
+        for key in ("head", "batched", "rocking", "configs", "splitting", "volume"):
             fl = jobs.get(key)
             for f in (fl.values() if isinstance(fl, dict) else fl if isinstance(fl, list)
                       else [fl] if fl is not None else []):
@@ -832,6 +899,7 @@ def run_gpu(args, rks):
             "peaks": peaks,
             "batched": batched,
             "configs": configs,
+            "splitting": splitting,
             "rocking": rocking,
             "volume": volume,
             "serving": serving,
@@ -863,6 +931,7 @@ def main():
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--skip-rocking", action="store_true")
+    ap.add_argument("--skip-splitting", action="store_true")
     ap.add_argument("--skip-volume", action="store_true")
     ap.add_argument("--skip-configs", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=440)

@@ -230,3 +230,19 @@ def test_forest_ruth_split_band_matches_oracle(bpm_lib, monkeypatch, nx, layout,
         alt = run_ref(wl, method=other)
         diff = max(band_errors(alt.psi, ref.psi))
         assert diff > 1e-6 and diff > max(errs), (other, diff, errs)
+
+
+def test_forest_ruth_split_band_batch(bpm_lib, monkeypatch):
+    """Several N = 8192 rows on the split band's fused fourth-order form (one
+    4-CTA cluster per row, each row with its own energy and stage tables):
+    sampled rows against the oracle's Forest-Ruth march."""
+    monkeypatch.delenv("BPM_FUSED_LAYOUT", raising=False)
+    wb = inputs.pulse_batched(nx=8192, nz=150, n_energy=3, record_every=50)
+    rows = [0, 2]
+    ref = run_ref(wb, method="forest_ruth", rows=rows)
+    with binding.Plan(wb, FP32, splitting=binding.BPM_SPLIT_FOREST_RUTH) as plan:
+        out = plan.propagate()
+        assert binding.bpm_launch_shape(plan.handle) == (9, 0)
+    errs = band_errors(out.psi[rows], ref.psi, out.records[rows], ref.records)
+    assert max(errs) <= TOL_FP32, errs
+    assert np.allclose(out.powers[rows], ref.powers, rtol=1e-4, atol=1e-9 * ref.powers.max())
