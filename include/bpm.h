@@ -219,8 +219,10 @@ int bpm_propagate(bpm_plan_t plan, const double* psi_in, double* psi_out,
  * marched outside a capture (strain slices prepared, schedule buffers
  * sized); the march's per-call uploads then travel as kernel parameters,
  * so a replay repeats the captured march (same buffers, steps and launch
- * shape -- the fixed rule's).  While `stream` is capturing, FP64 plans and
- * plans not yet marched return BPM_ERR_INVALID and enqueue nothing. */
+ * shape -- the fixed rule's).  While `stream` is capturing, FP64 plans,
+ * Forest-Ruth plans that march stage by stage (nx = 16384, or 8192 with
+ * BPM_FUSED_LAYOUT=staged) and plans not yet marched return BPM_ERR_INVALID
+ * and enqueue nothing. */
 int bpm_propagate_device(bpm_plan_t plan, const void* d_psi_in,
                          void* d_psi_out, void* d_records, void* d_powers,
                          int32_t n_begin, int32_t n_end, void* stream);

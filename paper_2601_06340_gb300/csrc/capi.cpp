@@ -1111,14 +1111,19 @@ int bpm_propagate_device(bpm_plan_t plan, const void* d_psi_in, void* d_psi_out,
   // Under graph capture the march's per-call uploads go through kernel
   // parameters (see upload); what cannot be captured is refused before
   // anything is enqueued: FP64 plans (their march uploads per-record phase
-  // factors and swaps buffers on the host) and plans whose strain slices
-  // still have to be prepared (allocation and a host wait).
+  // factors and swaps buffers on the host), Forest-Ruth plans that march
+  // stage by stage (their schedule is uploaded in chunks from the host) and
+  // plans whose strain slices still have to be prepared (allocation and a
+  // host wait).
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaError_t ce = cudaStreamIsCapturing(st, &cs);
   if (ce != cudaSuccess) return cuda_fail(ce, "stream capture status");
   if (cs != cudaStreamCaptureStatusNone) {
     if (plan->precision != BPM_FP32_FUSED)
       return fail(BPM_ERR_INVALID, "FP64 plans cannot be captured into a CUDA graph");
+    if (fr_staged(plan))
+      return fail(BPM_ERR_INVALID,
+                  "Forest-Ruth plans that march stage by stage cannot be captured");
     if (plan->slices_dirty)
       return fail(BPM_ERR_INVALID, "march the plan once outside the graph capture first");
   }

@@ -265,14 +265,18 @@ def _capture_case(name):
         return inputs.serving_request(rng, 1024, 300), binding.BPM_SPLIT_VERLET
     if name == "Verlet N=4096":
         return inputs.serving_request(rng, 4096, 300), binding.BPM_SPLIT_VERLET
+    if name == "Forest-Ruth N=4096":
+        return inputs.serving_request(rng, 4096, 200), binding.BPM_SPLIT_FOREST_RUTH
+    if name == "Forest-Ruth N=8192":
+        return inputs.serving_request(rng, 8192, 200), binding.BPM_SPLIT_FOREST_RUTH
     return (inputs.cube_dislocation_3d(nx=256, ny=256, nz=40, dx_um=0.08, dy_um=0.08,
                                        dz_um=0.1, cube_um=5.0, fwhm_um=1.5, record_every=10),
             binding.BPM_SPLIT_VERLET if name.endswith("Verlet") else binding.BPM_SPLIT_FIRST_ORDER)
 
 
 @pytest.mark.parametrize("name", ["cluster N=1024", "split N=4096", "rotated batch 160x4096",
-                                  "Verlet N=1024", "Verlet N=4096", "3D 256x256",
-                                  "3D 256x256 Verlet"])
+                                  "Verlet N=1024", "Verlet N=4096", "Forest-Ruth N=4096",
+                                  "Forest-Ruth N=8192", "3D 256x256", "3D 256x256 Verlet"])
 def test_device_api_graph_capture_replays(bpm_lib, monkeypatch, name):
     """A device-API march captured into a CUDA graph (its per-call uploads go
     through kernel parameters) replays to the same bits as the march run
@@ -334,6 +338,34 @@ def test_device_api_capture_refusals(bpm_lib):
         got = y.cpu().numpy().astype(np.complex128)
         assert np.array_equal(got, ref.psi if precision == FP64 else
                               ref.psi.astype(np.complex64).astype(np.complex128))
+
+
+@pytest.mark.filterwarnings("ignore:The CUDA Graph is empty")
+def test_staged_forest_ruth_capture_refused(bpm_lib):
+    """A Forest-Ruth plan that marches stage by stage (N = 16384) is refused
+    under capture before anything is enqueued, and still marches outside."""
+    torch = pytest.importorskip("torch")
+    wl = inputs.serving_request(np.random.default_rng(3), 16384, 20)
+    dev = torch.device("cuda:0")
+    x = torch.from_numpy(wl.psi0.astype(np.complex64)).to(dev)
+    y = torch.empty_like(x)
+    with binding.Plan(wl, FP32, splitting=binding.BPM_SPLIT_FOREST_RUTH) as plan:
+        s = torch.cuda.Stream()
+        binding.bpm_propagate_device(plan.handle, x, y, None, None, 0, wl.nz, s.cuda_stream)
+        s.synchronize()
+        assert binding.bpm_launch_shape(plan.handle)[0] == 7
+        first = y.clone()
+        g = torch.cuda.CUDAGraph()
+        with pytest.raises(binding.BpmError) as e:
+            with torch.cuda.graph(g, stream=s):
+                binding.bpm_propagate_device(plan.handle, x, y, None, None, 0, wl.nz,
+                                             s.cuda_stream)
+        assert e.value.code == binding.BPM_ERR_INVALID
+        torch.cuda.synchronize()
+        binding.bpm_propagate_device(plan.handle, x, y, None, None, 0, wl.nz,
+                                     torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert torch.equal(y, first)
 
 
 def test_omega_to_t_matches_oracle(bpm_lib):
