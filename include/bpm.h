@@ -154,7 +154,9 @@ int bpm_set_strain(bpm_plan_t plan, int32_t kind, const double* ux_um,
  * solve) and Forest-Ruth (the leading coupling, then three
  * propagate-and-couple stages with the propagator increments of t dz and
  * (1 - 2t) dz, tabulated here once; at nx = 4096 one 4-CTA half-band split
- * per solve while every solve gets four SMs, else one CTA per solve), for
+ * per solve while every solve gets four SMs, for 512 <= nx <= 4096 one
+ * 2-CTA cluster per solve while every solve gets two SMs, else one CTA per
+ * solve), for
  * nx = 8192 Verlet and Forest-Ruth on one split-band cluster per solve, and
  * for nx = 16384 Verlet (one split-band cluster per solve) and Forest-Ruth
  * stage by stage (per step a coupling launch and three one-step launches
@@ -346,7 +348,9 @@ int bpm_march_f64_noalloc(void* d_psi, int32_t nx, int32_t n_rows, const void* d
                           int32_t n_end, void* stream);
 
 /* Launch shape of the plan's last FP32 march (the fused kernels of the
- * step of Eq. fov10): *layout = 9 the Forest-Ruth step on one 4-CTA
+ * step of Eq. fov10): *layout = 10 the Forest-Ruth step on one 2-CTA
+ * cluster per row (512 <= nx <= 4096, while every row gets two SMs), 9 the
+ * Forest-Ruth step on one 4-CTA
  * cluster per row (nx = 4096 half-band split, while every row gets four
  * SMs; nx = 8192 split band), 8 the nx = 4096 half-band split with 16
  * points per thread (forced by BPM_FUSED_LAYOUT=split16), 7 the Forest-Ruth

@@ -221,7 +221,8 @@ def bpm_march_f64_noalloc(d_psi, nx, n_rows, d_prop, d_coupling, d_phasor, n_beg
 
 
 def bpm_launch_shape(plan) -> tuple[int, int]:
-    """(layout, chunk) of the plan's last FP32 march: layout 9 the
+    """(layout, chunk) of the plan's last FP32 march: layout 10 the
+    Forest-Ruth step on a two-CTA cluster per row (N = 512-4096), 9 the
     Forest-Ruth step on the N = 4096 half-band split or the N = 8192 split
     band, 8 the 16-point form of the N = 4096 split (forced), 7 the
     Forest-Ruth step stage by stage (N = 16384; N = 8192 forced), 6 the

@@ -288,6 +288,8 @@ constexpr int kLayoutSplit4S = 8;
 // fourth-order (Forest-Ruth) step on one 4-CTA cluster per row: the N = 4096
 // half-band split (8 points per thread) or the N = 8192 split band
 constexpr int kLayoutSplit4FR = 9;
+// one 2-CTA cluster per row, fourth-order (Forest-Ruth) step, N = 512..4096
+constexpr int kLayoutClusterFR = 10;
 // Coupling alone (the leading coupling of a step), on rows[0..nb): each row's
 // state [2][nx], the slice of step n of its stream (stored per part for
 // nx >= 8192), coefficients (am1h, bh).
@@ -297,6 +299,7 @@ int fused_split4_capacity();
 int fused_half_capacity(int logn);   // logn <= 12
 int fused_fr_capacity(int logn);     // logn <= 12
 int fused_cluster_half_capacity(int logn);   // 9 <= logn <= 12
+int fused_cluster_fr_capacity(int logn);     // 9 <= logn <= 12
 int fused_split4_half_capacity();            // N = 4096
 int fused_split4_fr_capacity();              // N = 4096
 // Positions of the Forest-Ruth stage tables in the split kernels' thread

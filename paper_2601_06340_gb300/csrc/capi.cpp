@@ -316,8 +316,11 @@ static LaunchShape choose_shape(bpm_plan_s* plan, PlanAux* aux, const void* stat
   if (plan->split == BPM_SPLIT_FOREST_RUTH) {
     // the fourth-order form: N = 4096 rows that each get four SMs on the
     // half-band split (three propagations per step; the 8000-step bent solve
-    // measured 85.0 ms against 200.3 ms on one CTA), else one CTA per row;
-    // BPM_FUSED_LAYOUT=cta forces the latter
+    // measured 70.0 ms against 140 ms on one CTA), rows of 512 <= N <= 4096
+    // that each get two SMs on the 2-CTA cluster (per step against one CTA:
+    // N = 512 6.5 / 10.7 us, 1024 7.0 / 11.4, 2048 7.7 / 10.5, 4096 12.0 /
+    // 17.5), else one CTA per row; BPM_FUSED_LAYOUT=cta|cluster forces
+    // either
     int sms = 1, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -327,9 +330,15 @@ static LaunchShape choose_shape(bpm_plan_s* plan, PlanAux* aux, const void* stat
     }
     const char* fv = std::getenv("BPM_FUSED_LAYOUT");
     const bool cta = fv && std::strcmp(fv, "cta") == 0;
-    if (!cta && logn == 12 && plan->d_stage_prop_split != nullptr && 4 * nb <= sms &&
+    const bool cl = fv && std::strcmp(fv, "cluster") == 0;
+    if (!cta && !cl && logn == 12 && plan->d_stage_prop_split != nullptr && 4 * nb <= sms &&
         nb <= fused_split4_fr_capacity()) {
       rule.layout = kLayoutSplit4FR;
+      return rule;
+    }
+    if (!cta && logn >= 9 && logn <= 12 && 2 * nb <= sms &&
+        nb <= fused_cluster_fr_capacity(logn)) {
+      rule.layout = kLayoutClusterFR;
       return rule;
     }
     rule.layout = kLayoutCtaFR;

@@ -36,6 +36,11 @@ namespace bpm {
                          cudaStream_t);                                          \
   int fused3h_rows_resident_##L();
 BPM_DECLARE_FUSED3H(9) BPM_DECLARE_FUSED3H(10) BPM_DECLARE_FUSED3H(11) BPM_DECLARE_FUSED3H(12)
+#define BPM_DECLARE_FUSED3F(L)                                                   \
+  int fused3f_launch_##L(const RowDescF32*, int, int, const float4*, int*,       \
+                         cudaStream_t);                                          \
+  int fused3f_rows_resident_##L();
+BPM_DECLARE_FUSED3F(9) BPM_DECLARE_FUSED3F(10) BPM_DECLARE_FUSED3F(11) BPM_DECLARE_FUSED3F(12)
 BPM_DECLARE_FUSED(3) BPM_DECLARE_FUSED(4) BPM_DECLARE_FUSED(5)
 BPM_DECLARE_FUSED(6) BPM_DECLARE_FUSED(7) BPM_DECLARE_FUSED2(8)
 BPM_DECLARE_FUSED2(9) BPM_DECLARE_FUSED2(10) BPM_DECLARE_FUSED2(11)
@@ -140,6 +145,15 @@ int launch_fused_layout(int logn, const RowDescF32* d_rows, int n_rows, int step
       case 11: return fused3h_launch_11(d_rows, n_rows, steps, d_tw, d_status, st);
       case 12: return fused3h_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
       default: return fail(BPM_ERR_INVALID, "second-order cluster layout needs 512 <= nx <= 4096");
+    }
+  }
+  if (layout == kLayoutClusterFR) {
+    switch (logn) {
+      case 9: return fused3f_launch_9(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 10: return fused3f_launch_10(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 11: return fused3f_launch_11(d_rows, n_rows, steps, d_tw, d_status, st);
+      case 12: return fused3f_launch_12(d_rows, n_rows, steps, d_tw, d_status, st);
+      default: return fail(BPM_ERR_INVALID, "fourth-order cluster layout needs 512 <= nx <= 4096");
     }
   }
   if (layout == kLayoutCtaFR) {
@@ -377,6 +391,23 @@ int fused_cluster_half_capacity(int logn) {
       case 10: c = fused3h_rows_resident_10(); break;
       case 11: c = fused3h_rows_resident_11(); break;
       default: c = fused3h_rows_resident_12(); break;
+    }
+    cache[logn].store(c, std::memory_order_relaxed);
+  }
+  return c;
+}
+
+// Rows one launch of the fourth-order (Forest-Ruth) 2-CTA cluster kernel
+// keeps resident (clusters).
+int fused_cluster_fr_capacity(int logn) {
+  static std::atomic<int> cache[kMaxLogN + 1] = {};
+  int c = cache[logn].load(std::memory_order_relaxed);
+  if (c == 0) {
+    switch (logn) {
+      case 9: c = fused3f_rows_resident_9(); break;
+      case 10: c = fused3f_rows_resident_10(); break;
+      case 11: c = fused3f_rows_resident_11(); break;
+      default: c = fused3f_rows_resident_12(); break;
     }
     cache[logn].store(c, std::memory_order_relaxed);
   }

@@ -155,11 +155,19 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity
 // to both and step n + 1's first half to its own band with no further
 // exchange; the launch's first half-step takes the other band from the
 // state in global memory.  Records are taken after step n's second half.
-template <int LOGN, bool EX, bool HALF = false>
+// SCH, the operator splitting (as in fused2_kernel.cuh): kSchFirst (HALF =
+// false above), kSchVerlet (HALF = true), kSchForestRuth: three
+// propagations per step with the tables of t dz, (1 - 2t) dz, t dz (the
+// row's prop holds those of t dz, then those of (1 - 2t) dz, in the
+// band-per-thread kernels' thread order) and the inner couplings
+// (1 - t)/2, in (am1, b), on the step's slice after the first two.
+template <int LOGN, bool EX, int SCH = kSchFirst>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
     fused3_march_kernel(const RowDescF32* __restrict__ rows, int n_rows, int steps,
                         const float4* __restrict__ tw, int* __restrict__ status) {
   namespace cg = cooperative_groups;
+  constexpr bool HALF = SCH != kSchFirst;           // couples before propagating
+  constexpr int STAGES = SCH == kSchForestRuth ? 3 : 1;
   using C = F3Cfg<LOGN, HALF ? 2 : 1>;
   using F = F2Cfg<LOGN>;   // same pass geometry (E = 16 points per thread)
   constexpr int N = C::N, T = C::T, NP = C::NP, RL = C::RL, GL = C::G_LAST;
@@ -207,14 +215,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
       w1[j - 1] = make_float2(0.f, 0.f);
     }
   }
-  // this thread's slice of (P - 1)/N in the last pass, for the whole launch
+  // this thread's slice of (P - 1)/N in the last pass (for the whole launch;
+  // Forest-Ruth reloads it per stage from its stage tables in thread order)
+  static_assert(GL * RL == 16 && F::TAIL_WARP == (NP >= 3), "the band-per-thread geometry");
   float2 pr[16];
+  auto load_table = [&](const float2* tab) {
 #pragma unroll
-  for (int i = 0; i < GL; ++i)
-#pragma unroll
-    for (int j = 0; j < RL; ++j)
-      pr[i * RL + j] = __ldg(&d.prop[band * N + f2_pos<LOGN, NP - 1>(
-                                             f2_group<LOGN, NP - 1, (NP >= 3)>(t, i), j)]);
+    for (int k = 0; k < 16; ++k)
+      pr[k] = __ldg(&tab[band * N + (SCH == kSchForestRuth ? k * T + t
+                                                             : f2_table_pos<LOGN>(t, k))]);
+  };
+  load_table(d.prop);
 
   float2 v[16];
 #pragma unroll
@@ -227,7 +238,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
   const uint32_t slice_bytes = uint32_t(N) * 8u;
   int pending_slot = -1;
   bool timed_out = false;
+  // (am1, bb): the step's coupling, or the outer ones of a splitting form;
+  // (am1i, bbi): Forest-Ruth's inner couplings
   const float2 am1 = HALF ? d.am1h : d.am1, bb = HALF ? d.bh : d.b;
+  [[maybe_unused]] const float2 am1i = d.am1, bbi = d.b;
   // slice of step n into buffer `slot` (separable: the row head only)
   auto fetch = [&](int n, int slot) {
     if (sep) bulk_load(srow0 + slot, d.srows + n, kSepHeadBytes, bar + slot);
@@ -263,6 +277,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
       sincos(ang, &sa, &ca);
       recph[(n + 1) & 1] = make_float2(float(ca), float(sa));
     }
+    // one stage of the step (Forest-Ruth: three; the others: one, with no
+    // loop around it)
+    auto stage = [&](const int sg) {
+    // exchange index of the stage: buffer half and barrier phase
+    const int ex = it * STAGES + sg;
+    if constexpr (SCH == kSchForestRuth) {
+      // the stage's table: (P^t - 1)/N for stages 0 and 2, (P^(1-2t) - 1)/N
+      // for stage 1 (read from L2 while the forward passes run)
+      if (sg > 0) load_table(d.prop + (sg == 1 ? 2 * N : 0));
+    }
     float2 org[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) org[j] = v[j];
@@ -273,7 +297,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
     if constexpr (HALF) {
       // every thread is past step it - 1's couplings, which read the buffer
       // of slice it - 1: fetch slice it + 1 into it
-      if (lead && it + 1 < steps) fetch(n + 1, (it + 1) & 1);
+      if (lead && sg == 0 && it + 1 < steps) fetch(n + 1, (it + 1) & 1);
     } else {
       if (lead) fetch(n, 0);
     }
@@ -319,7 +343,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
     dft<16, true, EX>(v);
     // send psi_p to the peer (asynchronous remote stores completing on the
     // peer's barrier of this parity); arm our own barrier for the peer's.
-    const int half = it & 1;
+    const int half = ex & 1;
     // (per warp: thread t receives the slots of the peer's thread t)
     if (lane == 0) mbar_expect_tx(&xbar[half * C::WARPS + warp], 32u * 16u * 8u);
     const uint32_t xo = xpeer + uint32_t(half * N) * 8u;
@@ -331,20 +355,41 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
       st_async_v4(xo + uint32_t(xpair(pp, t, T)) * 8u, v[2 * pp], v[2 * pp + 1], xbo);
     // (after one expired wait a thread stops waiting, so a fault costs one
     // bounded wait, not one per step; the host reports BPM_ERR_TIMEOUT)
-    if (!timed_out && !mbar_wait_cluster(&xbar[half * C::WARPS + warp], uint32_t((it >> 1) & 1)))
+    if (!timed_out && !mbar_wait_cluster(&xbar[half * C::WARPS + warp], uint32_t((ex >> 1) & 1)))
       timed_out = true;
 
     const float2* xi = xb + half * N;
     if constexpr (HALF) {
+      // (separable: the couplings read the column phasors of buffer 0 and
+      // the row heads of steps it and it + 1)
+      const float2* phc = ph + (sep ? 0 : (it & 1) * N);
+      const SepHead shc = sep ? sep_head(srow0 + (it & 1)) : SepHead{};
+      if (STAGES > 1 && sg < STAGES - 1) {
+        // Forest-Ruth, after the first two propagations: the inner
+        // couplings ((1 - t)/2) on this step's slice (awaited before this
+        // step: at the previous step's couplings or the launch's first)
+        auto couple_inner = [&](auto S) {
+          constexpr bool SEP = decltype(S)::value;
+          const float2 bs = slice_b<SEP>(bbi, shc, band);
+#pragma unroll
+          for (int pp = 0; pp < 8; ++pp) {
+            const float4 q2 = *reinterpret_cast<const float4*>(xi + xpair(pp, t, T));
+            const int c0 = t + 2 * pp * T, c1 = t + (2 * pp + 1) * T;
+            v[2 * pp] = couple_cell(v[2 * pp], make_float2(q2.x, q2.y),
+                                    slice_at<SEP>(phc, shc, c0, c0), band, am1i, bs);
+            v[2 * pp + 1] = couple_cell(v[2 * pp + 1], make_float2(q2.z, q2.w),
+                                        slice_at<SEP>(phc, shc, c1, c1), band, am1i, bs);
+          }
+        };
+        if (sep) couple_inner(BoolC<true>{});
+        else couple_inner(BoolC<false>{});
+        return;
+      }
       const bool next = it + 1 < steps;
       if (next && !timed_out &&
           !mbar_wait(bar + ((it + 1) & 1), uint32_t(((it + 1) >> 1) & 1)))
         timed_out = true;
-      // (separable: both couplings read the column phasors of buffer 0 and
-      // the row heads of steps it and it + 1)
-      const float2* phc = ph + (sep ? 0 : (it & 1) * N);
       const float2* phn = ph + (sep ? 0 : ((it + 1) & 1) * N);
-      const SepHead shc = sep ? sep_head(srow0 + (it & 1)) : SepHead{};
       const SepHead shn = (sep && next) ? sep_head(srow0 + ((it + 1) & 1)) : SepHead{};
       const float2 g = rec ? recph[(n + 1) & 1] : make_float2(1.f, 0.f);
       const int slot = rec ? (n + 1) / d.record_every - 1 : 0;
@@ -419,7 +464,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
         const float2 g = recph[(n + 1) & 1];
         double s = 0.0;
         float2* r0 = d.records ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
-  #pragma unroll
+#pragma unroll
         for (int j = 0; j < 16; ++j) {
           const float2 p = v[j];
           s = pow_acc(s, p);
@@ -427,13 +472,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
         }
         if (d.powers) {
           double ds = s;
-  #pragma unroll
+#pragma unroll
           for (int off = 16; off > 0; off >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, off);
           if (lane == 0) red[warp] = ds;
           if (lead) pending_slot = slot;
         }
       }
     }
+    };
+    if constexpr (STAGES == 1) {
+      stage(0);
+    } else {
+#pragma unroll 1
+      for (int sg = 0; sg < STAGES; ++sg) stage(sg);
+    }   // (the Forest-Ruth step ends on the t dz table, which its next step
+        // starts with)
   }
 
   __syncthreads();

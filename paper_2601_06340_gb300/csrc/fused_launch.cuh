@@ -138,20 +138,21 @@ int clusters_resident(K kernel, int cluster, int threads, int smem) {
   return n > 0 ? n : 1;
 }
 
-// 2-CTA cluster kernel (one row per cluster, one band per CTA).
-template <int LOGN, bool EX, bool HALF = false>
+// 2-CTA cluster kernel (one row per cluster, one band per CTA); SCH the
+// operator splitting.
+template <int LOGN, bool EX, int SCH = kSchFirst>
 int fused3_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const float4* d_tw,
                        int* d_status, cudaStream_t st) {
-  using C = F3Cfg<LOGN, HALF ? 2 : 1>;
+  using C = F3Cfg<LOGN, SCH != kSchFirst ? 2 : 1>;
   static std::atomic<bool> configured{false};
   if (!configured.load(std::memory_order_acquire)) {
-    cudaError_t e = cudaFuncSetAttribute(fused3_march_kernel<LOGN, EX, HALF>,
+    cudaError_t e = cudaFuncSetAttribute(fused3_march_kernel<LOGN, EX, SCH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused3)");
     configured.store(true, std::memory_order_release);
   }
-  fused3_march_kernel<LOGN, EX, HALF><<<2 * n_rows, C::T, C::SMEM, st>>>(d_rows, n_rows, steps,
-                                                                        d_tw, d_status);
+  fused3_march_kernel<LOGN, EX, SCH><<<2 * n_rows, C::T, C::SMEM, st>>>(d_rows, n_rows, steps,
+                                                                       d_tw, d_status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "fused3 march launch");
   return BPM_OK;
@@ -242,14 +243,29 @@ int fused4_launch_impl(const RowDescF32* d_rows, int n_rows, int steps, const fl
 #define BPM_INSTANTIATE_FUSED3H(L)                                                \
   namespace bpm {                                                                 \
   int fused3h_rows_resident_##L() {                                               \
-    return clusters_resident(fused3_march_kernel<L, true, true>, 2, F3Cfg<L, 2>::T, \
-                             F3Cfg<L, 2>::SMEM);                                  \
+    return clusters_resident(fused3_march_kernel<L, true, kSchVerlet>, 2,         \
+                             F3Cfg<L, 2>::T, F3Cfg<L, 2>::SMEM);                  \
   }                                                                               \
   int fused3h_launch_##L(const RowDescF32* r, int n, int s, const float4* tw,    \
                          int* status, cudaStream_t st) {                          \
     return fused_exact_constants()                                                \
-               ? fused3_launch_impl<L, true, true>(r, n, s, tw, status, st)       \
-               : fused3_launch_impl<L, false, true>(r, n, s, tw, status, st);     \
+               ? fused3_launch_impl<L, true, kSchVerlet>(r, n, s, tw, status, st) \
+               : fused3_launch_impl<L, false, kSchVerlet>(r, n, s, tw, status, st); \
+  }                                                                               \
+  }
+
+// fourth-order (Forest-Ruth) form of the 2-CTA cluster kernel
+#define BPM_INSTANTIATE_FUSED3F(L)                                                \
+  namespace bpm {                                                                 \
+  int fused3f_rows_resident_##L() {                                               \
+    return clusters_resident(fused3_march_kernel<L, true, kSchForestRuth>, 2,     \
+                             F3Cfg<L, 2>::T, F3Cfg<L, 2>::SMEM);                  \
+  }                                                                               \
+  int fused3f_launch_##L(const RowDescF32* r, int n, int s, const float4* tw,    \
+                         int* status, cudaStream_t st) {                          \
+    return fused_exact_constants()                                                \
+               ? fused3_launch_impl<L, true, kSchForestRuth>(r, n, s, tw, status, st) \
+               : fused3_launch_impl<L, false, kSchForestRuth>(r, n, s, tw, status, st); \
   }                                                                               \
   }
 

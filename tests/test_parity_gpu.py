@@ -265,6 +265,8 @@ def _capture_case(name):
         return inputs.serving_request(rng, 1024, 300), binding.BPM_SPLIT_VERLET
     if name == "Verlet N=4096":
         return inputs.serving_request(rng, 4096, 300), binding.BPM_SPLIT_VERLET
+    if name == "Forest-Ruth N=1024":
+        return inputs.serving_request(rng, 1024, 200), binding.BPM_SPLIT_FOREST_RUTH
     if name == "Forest-Ruth N=4096":
         return inputs.serving_request(rng, 4096, 200), binding.BPM_SPLIT_FOREST_RUTH
     if name == "Forest-Ruth N=8192":
@@ -275,7 +277,8 @@ def _capture_case(name):
 
 
 @pytest.mark.parametrize("name", ["cluster N=1024", "split N=4096", "rotated batch 160x4096",
-                                  "Verlet N=1024", "Verlet N=4096", "Forest-Ruth N=4096",
+                                  "Verlet N=1024", "Verlet N=4096", "Forest-Ruth N=1024",
+                                  "Forest-Ruth N=4096",
                                   "Forest-Ruth N=8192", "3D 256x256", "3D 256x256 Verlet"])
 def test_device_api_graph_capture_replays(bpm_lib, monkeypatch, name):
     """A device-API march captured into a CUDA graph (its per-call uploads go

@@ -29,6 +29,8 @@ CASES = [
     (1024, "cta", FIRST),
     (1024, "cluster", FIRST),
     (1024, "cluster", VERLET),
+    (1024, "cluster", FR),
+    (1024, "cta", FR),
     (4096, None, FIRST),
     (4096, "split16", FIRST),
     (4096, None, VERLET),
@@ -47,8 +49,8 @@ def _workload(nx):
 @pytest.fixture(scope="module")
 def refs():
     method = {FIRST: "first_order", VERLET: "verlet", FR: "forest_ruth"}
-    return {(nx, split): submit_ref(_workload(nx), method=method[split])
-            for nx, _, split in CASES}
+    keys = sorted({(nx, split) for nx, _, split in CASES})
+    return {k: submit_ref(_workload(k[0]), method=method[k[1]]) for k in keys}
 
 
 @pytest.mark.parametrize("nx,layout,split", CASES)

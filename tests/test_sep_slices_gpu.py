@@ -73,9 +73,10 @@ CASES = [
     (64, 300, None, FR, None),
     (1024, 300, "cta", FIRST, -1),       # band per thread, one CTA per row
     (1024, 300, "cta", VERLET, 3),
-    (1024, 300, None, FR, 6),
+    (1024, 300, "cta", FR, 6),
     (1024, 300, "cluster", FIRST, -1),   # 2-CTA cluster
     (1024, 300, "cluster", VERLET, 4),
+    (1024, 300, None, FR, 10),
     (4096, 400, None, FIRST, 2),         # half-band split, 8 points per thread
     (4096, 400, "split16", FIRST, 8),    # half-band split, 16 points per thread
     (4096, 400, None, VERLET, 5),        # the 8-point split's Verlet form

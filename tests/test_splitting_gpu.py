@@ -135,8 +135,9 @@ def test_small_n_splitting_fp32_matches_oracle(bpm_lib, nx, method):
 @pytest.mark.parametrize("name", ["n256", "laue_perfect", "bragg_bent", "asym_dislocation",
                                   "pulse"])
 def test_forest_ruth_fp32_matches_oracle(bpm_lib, name):
-    """The fused kernels' fourth-order step (the band-per-thread kernel, and
-    the N = 4096 half-band split for a single row; coupling t/2,
+    """The fused kernels' fourth-order step (the band-per-thread kernel, the
+    2-CTA cluster for single rows with 512 <= N <= 2048, and the N = 4096
+    half-band split for a single row; coupling t/2,
     then propagate t dz / couple (1-t)/2, propagate (1-2t) dz / couple
     (1-t)/2, propagate t dz / couple t/2, all on the slice of the step)
     against the oracle's Forest-Ruth march: fields, records and powers, rows
@@ -155,8 +156,10 @@ def test_forest_ruth_fp32_matches_oracle(bpm_lib, name):
     with binding.Plan(wl, FP32, splitting=binding.BPM_SPLIT_FOREST_RUTH) as plan:
         out = plan.propagate()
         shape = binding.bpm_launch_shape(plan.handle)
-    # a single N = 4096 row marches on the half-band split (layout 9)
-    assert shape[0] == (9 if wl.nx == 4096 and wl.batch == 1 else 6), shape
+    # a single N = 4096 row marches on the half-band split (layout 9), other
+    # single rows from N = 512 on the 2-CTA cluster (layout 10)
+    want = 6 if wl.batch > 1 or wl.nx < 512 else 9 if wl.nx == 4096 else 10
+    assert shape[0] == want, shape
     if wl.batch > 1:
         assert shape[1] > 0, shape       # rotated
     errs = band_errors(out.psi[rows], ref.psi, out.records[rows], ref.records)
