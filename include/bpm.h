@@ -165,8 +165,10 @@ int bpm_set_strain(bpm_plan_t plan, int32_t kind, const double* ux_um,
  * takes it at nx = 8192 too); 3D plans take the first-order step
  * and Verlet (the row kernel, which holds both bands of a line, applies the
  * half-step couplings); other combinations return BPM_ERR_INVALID.
- * bpm_submit takes FP32 plans set to Verlet (one CTA per row as well), not
- * Forest-Ruth.
+ * bpm_submit takes FP32 plans set to Verlet or Forest-Ruth: their rows
+ * march in their own launch groups, one CTA per row for nx <= 4096 and one
+ * split-band cluster per row for nx = 8192 (and 16384, Verlet); Forest-Ruth
+ * plans of nx = 16384 are refused there (BPM_ERR_INVALID).
  * BPM_ERR_BUSY while tickets are pending. */
 enum bpm_splitting {
   BPM_SPLIT_FIRST_ORDER = 0,

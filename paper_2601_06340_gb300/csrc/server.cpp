@@ -407,13 +407,20 @@ int launch_batch(Server& s, Bucket& b) {
     const bool cluster = layout < 0 && 2 * int(b.members.size()) <= s.sm_count;
     limit = size_t(std::max(1, layout == kLayoutSplit4 ? fused_split4_capacity()
                                                        : fused_launch_capacity(logn, cluster)));
-    // second-order (Verlet) rows march one CTA per row on the kernel's
-    // half-step form; a batch holding any stays within its residency
-    for (auto& r : b.members)
-      if (r->plan->split == BPM_SPLIT_VERLET)
-        limit = std::min(limit, size_t(std::max(1, fused_half_capacity(logn))));
+    // rows of the splitting forms march on their own kernels (N <= 4096: one
+    // CTA per row, on the half-step or the fourth-order form; N = 8192,
+    // 16384: the split-band cluster forms); a batch holding any stays
+    // within the one-CTA forms' residency
+    if (logn < kSplitLogN)
+      for (auto& r : b.members) {
+        if (r->plan->split == BPM_SPLIT_VERLET)
+          limit = std::min(limit, size_t(std::max(1, fused_half_capacity(logn))));
+        if (r->plan->split == BPM_SPLIT_FOREST_RUTH)
+          limit = std::min(limit, size_t(std::max(1, fused_fr_capacity(logn))));
+      }
   }
-  // FP32 rows by (step count, splitting): key 2 * steps + (Verlet ? 1 : 0)
+  // FP32 rows by (step count, splitting): key 3 * steps + bpm_split (0 first
+  // order, 1 Verlet, 2 Forest-Ruth)
   std::map<int, std::vector<RowDescF32>> groups;
   std::vector<RowDescF32> rows;
   cudaMemsetAsync(bt.d_status, 0, sizeof(int), b.st);
@@ -439,7 +446,7 @@ int launch_batch(Server& s, Bucket& b) {
     fused_rows(p, static_cast<float2*>(r->d_state), static_cast<float2*>(r->d_rec), r->d_pow,
                n0, n0 + steps, &rows);
     for (auto& d : rows) d.n_phase0 = 0;
-    auto& g = groups[2 * steps + (p->split == BPM_SPLIT_VERLET ? 1 : 0)];
+    auto& g = groups[3 * steps + p->split];
     g.insert(g.end(), rows.begin(), rows.end());
   }
   b.rr = nm ? (b.rr + bt.items.size()) % nm : 0;
@@ -479,10 +486,14 @@ int launch_batch(Server& s, Bucket& b) {
         bt.err = fail(BPM_ERR_CUDA, "injected launch failure");
         break;
       }
-      const bool verlet = (kv.first & 1) != 0;
-      bt.err = launch_fused_layout(logn, b.d_rows + off, int(kv.second.size()), kv.first >> 1,
-                                   s.d_tw[logn], bt.d_status, b.st,
-                                   verlet ? kLayoutCtaHalf : layout);
+      const int split = kv.first % 3;
+      const int lay = split == BPM_SPLIT_VERLET
+                          ? (logn >= kSplitLogN ? kLayoutSplit4Half : kLayoutCtaHalf)
+                      : split == BPM_SPLIT_FOREST_RUTH
+                          ? (logn >= kSplitLogN ? kLayoutSplit4FR : kLayoutCtaFR)
+                          : layout;
+      bt.err = launch_fused_layout(logn, b.d_rows + off, int(kv.second.size()), kv.first / 3,
+                                   s.d_tw[logn], bt.d_status, b.st, lay);
       off += kv.second.size();
     }
   }
@@ -678,9 +689,10 @@ int bpm_submit(bpm_plan_t plan, const double* psi_in, double* psi_out, void* rec
     return fail(BPM_ERR_INVALID, "plan, psi_in, psi_out and out must be non-NULL");
   *out = 0;
   if (plan->ny > 1) return fail(BPM_ERR_INVALID, "the server takes 2D plans only");
-  if (plan->precision == BPM_FP32_FUSED && plan->split != BPM_SPLIT_FIRST_ORDER &&
-      plan->split != BPM_SPLIT_VERLET)
-    return fail(BPM_ERR_INVALID, "the server marches FP32 plans first order or Verlet");
+  // (Forest-Ruth at nx = 16384 marches stage by stage: not in a shared launch)
+  if (plan->precision == BPM_FP32_FUSED && plan->split == BPM_SPLIT_FOREST_RUTH &&
+      plan->logn > kSplitLogN)
+    return fail(BPM_ERR_INVALID, "the server marches FP32 Forest-Ruth plans up to nx = 8192");
   Server& s = srv();
   auto r = std::make_shared<Request>();
   r->plan = plan;

@@ -96,12 +96,16 @@ def test_injected_launch_failure_fails_only_that_size(bpm_lib):
 
 
 def test_verlet_requests_share_the_server_with_first_order_ones(bpm_lib, monkeypatch):
-    # FP32 plans set to Verlet march on the one-CTA half-step kernel in their
-    # own launch group; each result equals the same plan marched alone (on
-    # the same kernel for Verlet rows: the solo march is forced to one CTA)
+    # FP32 plans set to Verlet or Forest-Ruth march in their own launch
+    # groups (N <= 4096 one CTA per row on the half-step or fourth-order
+    # kernel, N = 8192 and 16384 on the split-band forms); each result
+    # equals the same plan marched alone (on the same kernel: the solo march
+    # is forced to one CTA, which the split-band sizes do not have)
     binding.bpm_server_configure(0.6, 64, 128, 1000)
     V, F = binding.BPM_SPLIT_VERLET, binding.BPM_SPLIT_FIRST_ORDER
-    specs = [(512, V), (512, F), (1024, V), (4096, V), (4096, F), (2048, F)]
+    R = binding.BPM_SPLIT_FOREST_RUTH
+    specs = [(512, V), (512, F), (1024, V), (4096, V), (4096, F), (2048, F), (1024, R),
+             (4096, R), (8192, V), (8192, R), (16384, V), (8192, F)]
     rng = np.random.default_rng(21)
     wls = [inputs.serving_request(rng, nx, 300) for nx, _ in specs]
     plans = [binding.Plan(wl, FP32, splitting=sp) for wl, (_, sp) in zip(wls, specs)]
@@ -114,8 +118,9 @@ def test_verlet_requests_share_the_server_with_first_order_ones(bpm_lib, monkeyp
         for p, wl, o, (_, sp) in zip(plans, wls, outs, specs):
             alone = p.propagate(records=False, powers=False).psi
             errs = band_errors(o, alone)
-            # the same kernel and steps: Verlet rows agree to rounding
-            assert max(errs) <= (1e-6 if sp == V else TOL_FP32), (sp, errs)
+            # the same kernel and steps: Verlet and Forest-Ruth rows agree to
+            # rounding
+            assert max(errs) <= (TOL_FP32 if sp == F else 1e-6), (sp, errs)
     finally:
         for p in plans:
             p.close()
@@ -185,6 +190,17 @@ def test_queue_overflow_oversized_request_and_busy_plan(bpm_lib):
         binding.bpm_server_configure(0.6, 256, 256, 100000)
         for p in plans:
             p.close()
+
+
+def test_staged_forest_ruth_refused_by_the_server(bpm_lib):
+    """A Forest-Ruth plan of N = 16384 marches stage by stage, which does not
+    fit a shared launch: bpm_submit refuses it up front."""
+    wl = inputs.serving_request(np.random.default_rng(9), 16384, 50)
+    with binding.Plan(wl, FP32, splitting=binding.BPM_SPLIT_FOREST_RUTH) as plan:
+        out = np.empty_like(wl.psi0)
+        with pytest.raises(binding.BpmError) as e:
+            binding.bpm_submit(plan.handle, wl.psi0, out)
+        assert e.value.code == binding.BPM_ERR_INVALID
 
 
 def test_poll_timeout_and_collection(bpm_lib):
