@@ -12,9 +12,10 @@
 //     with asynchronous 16-byte remote stores that complete on the peer's mbarrier
 //     (armed with the expected byte count), and reads the partner band from
 //     its own buffer once its barrier completes -- no cluster-wide barrier
-//     per step.  The buffer alternates between two halves by step parity;
-//     a half is rewritten only after the sender has received the receiver's
-//     next-step values, which the receiver sends after consuming the half;
+//     per step.  The buffer alternates between two halves by exchange
+//     parity (the step's, or for Forest-Ruth that of 3 step + stage); a half
+//     is rewritten only after the sender has received the receiver's next
+//     values, which the receiver sends after consuming the half;
 //   * each CTA fetches the strain/mask slice of the step into its own shared
 //     memory with a bulk asynchronous copy on an mbarrier (bounded wait).
 #pragma once

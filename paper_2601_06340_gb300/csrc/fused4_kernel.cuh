@@ -41,12 +41,13 @@ namespace bpm {
 // marches past the FP32 tolerance.)  Both exchanges of the step (F within
 // the band, psi_p across the bands) are asynchronous remote stores that
 // complete on the receiver's mbarrier (see fused3_kernel.cuh), double
-// buffered by step parity; no cluster-wide barrier runs inside the march.
+// buffered by exchange parity (the step's, or for Forest-Ruth that of
+// 3 step + stage); no cluster-wide barrier runs inside the march.
 // Thread t sends and receives the slots of thread t, so each warp has its
 // own barrier per exchange and parity and waits only for the same warp of
 // the sender.
-// Buffer reuse: a half is rewritten two steps later, by a sender that has
-// by then received values the receiver computed from that half.
+// Buffer reuse: a half is rewritten two exchanges later, by a sender that
+// has by then received values the receiver computed from that half.
 // PHB: strain-slice buffers (2 for the second-order step, N = 4096 only)
 template <int LM, int PHB = 1>
 struct F4ECfg {
