@@ -309,8 +309,12 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
   // waits and raises s_abort; at the next step's first barrier (or after the
   // last step) the lead waits once more (again bounded) for its last slice
   // copy, so none is in flight when the CTA exits, and the CTA returns.
+  const bool rec_on = active && d.record_every > 0 &&
+                      (d.records != nullptr || d.powers != nullptr);
+  RecSteps rsteps(d.record_every, d.n_begin);
   for (int it = 0; it < steps; ++it) {
     const int n = d.n_begin + it;
+    const RecSteps::Step rs = rsteps.next();
     // the step's slice (separable: the column phasors and the row head)
     const float2* ph = ph0 + ((HALF && !sep) ? (it & 1) * N : 0);
     const float4* sr = sep ? srow0 + (HALF ? (it & 1) : 0) : nullptr;
@@ -322,8 +326,7 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
       }
       f2_couple<T>(v, ph, sr, t, band, d.am1h, d.bh);
     }
-    const bool rec = active && d.record_every > 0 && ((n + 1) % d.record_every) == 0 &&
-                     (d.records != nullptr || d.powers != nullptr);
+    const bool rec = rec_on && rs.at;
     if (lead && rec) {
       double ang = fmod(double(n + 1 - d.n_phase0) * d.gphase, 6.283185307179586);
       double sa, ca;
@@ -427,7 +430,7 @@ __global__ void __launch_bounds__(F2Cfg<LOGN>::THREADS, F2Cfg<LOGN>::THREADS >= 
     // ---- record ------------------------------------------------------------
     const bool want_pw = rec && d.powers != nullptr;
     if (rec) {
-      const int slot = (n + 1) / d.record_every - 1;
+      const int slot = rs.slot;
       const float2 g = recph[(n + 1) & 1];
       double s = 0.0;
       float2* r0 = d.records ? d.records + size_t(slot) * 2 * N + band * N : nullptr;

@@ -268,10 +268,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
     else first_half(BoolC<false>{});
   }
 
+  const bool rec_on = d.record_every > 0 && (d.records != nullptr || d.powers != nullptr);
+  RecSteps rsteps(d.record_every, d.n_begin);
   for (int it = 0; it < steps; ++it) {
     const int n = d.n_begin + it;
-    const bool rec = d.record_every > 0 && ((n + 1) % d.record_every) == 0 &&
-                     (d.records != nullptr || d.powers != nullptr);
+    const RecSteps::Step rs = rsteps.next();
+    const bool rec = rec_on && rs.at;
     if (lead && rec) {
       double ang = fmod(double(n + 1 - d.n_phase0) * d.gphase, 6.283185307179586);
       double sa, ca;
@@ -393,7 +395,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
       const float2* phn = ph + (sep ? 0 : ((it + 1) & 1) * N);
       const SepHead shn = (sep && next) ? sep_head(srow0 + ((it + 1) & 1)) : SepHead{};
       const float2 g = rec ? recph[(n + 1) & 1] : make_float2(1.f, 0.f);
-      const int slot = rec ? (n + 1) / d.record_every - 1 : 0;
+      const int slot = rec ? rs.slot : 0;
       float2* r0 = (rec && d.records) ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
       double s = 0.0;
       // Three couplings per point, unrolled over the thread's 16 points,
@@ -461,7 +463,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(F3Cfg<LOGN>::T, 1)
       else couple_all(BoolC<false>{});
 
       if (rec) {
-        const int slot = (n + 1) / d.record_every - 1;
+        const int slot = rs.slot;
         const float2 g = recph[(n + 1) & 1];
         double s = 0.0;
         float2* r0 = d.records ? d.records + size_t(slot) * 2 * N + band * N : nullptr;

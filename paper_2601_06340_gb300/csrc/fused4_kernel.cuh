@@ -288,12 +288,14 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
     else first_half(BoolC<false>{});
   }
 
+  const bool rec_on = d.record_every > 0 && (d.records != nullptr || d.powers != nullptr);
+  RecSteps rsteps(d.record_every, d.n_begin);
   for (int it = 0; it < steps; ++it) {
     const int n = d.n_begin + it;
-    const bool rec = d.record_every > 0 && ((n + 1) % d.record_every) == 0 &&
-                     (d.records != nullptr || d.powers != nullptr);
+    const RecSteps::Step rs = rsteps.next();
+    const bool rec = rec_on && rs.at;
     // the previous step was a record: its band-power part rides on this step's G
-    const bool part_due = pow_on && it > 0 && (n % d.record_every) == 0;
+    const bool part_due = pow_on && rs.prev;
     if (lead && rec) {
       double ang = fmod(double(n + 1 - d.n_phase0) * d.gphase, 6.283185307179586);
       double sa, ca;
@@ -368,7 +370,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
     // last-pass positions are its own in both directions)
     if (!timed_out && !mbar_wait_cluster(&gbar[half * C::WARPS + warp], xpar)) timed_out = true;
     if (lead && part_due && sg == 0 && h == 0)
-      d.powers[2 * (n / d.record_every - 1) + band] = (my_part + ppeer[half]) * d.dx_um;
+      d.powers[2 * rs.pslot + band] = (my_part + ppeer[half]) * d.dx_um;
     {
       const float2* gi = gx + half * M;
 #pragma unroll
@@ -454,7 +456,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
         const SepHead shn =
             (sep && next) ? sep_head(srow0 + (HALF_G ? 1 : ((it + 1) & 1))) : SepHead{};
         const float2 g = rec ? recph[(n + 1) & 1] : make_float2(1.f, 0.f);
-        const int slot = rec ? (n + 1) / d.record_every - 1 : 0;
+        const int slot = rec ? rs.slot : 0;
         float2* r0 = (rec && d.records) ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
         double s = 0.0;
         // a loop over shared memory (three couplings per point unrolled over
@@ -527,7 +529,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(F4ECfg<LM>::T, 1)
       else couple_all(BoolC<false>{});
 
       if (rec) {
-        const int slot = (n + 1) / d.record_every - 1;
+        const int slot = rs.slot;
         const float2 g = recph[(n + 1) & 1];
         double s = 0.0;
         float2* r0 = d.records ? d.records + size_t(slot) * 2 * N + band * N : nullptr;

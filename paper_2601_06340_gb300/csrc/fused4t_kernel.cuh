@@ -297,12 +297,14 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
     else first_half(BoolC<false>{});
   }
 
+  const bool rec_on = d.record_every > 0 && (d.records != nullptr || d.powers != nullptr);
+  RecSteps rsteps(d.record_every, d.n_begin);
   for (int it = 0; it < steps; ++it) {
     const int n = d.n_begin + it;
     const int half = it & 1;
-    const bool rec = d.record_every > 0 && ((n + 1) % d.record_every) == 0 &&
-                     (d.records != nullptr || d.powers != nullptr);
-    const bool part_due = pow_on && it > 0 && (n % d.record_every) == 0;
+    const RecSteps::Step rs = rsteps.next();
+    const bool rec = rec_on && rs.at;
+    const bool part_due = pow_on && rs.prev;
     if (lead && rec) {
       double ang = fmod(double(n + 1 - d.n_phase0) * d.gphase, 6.283185307179586);
       double sa, ca;
@@ -352,7 +354,7 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
     if (lead && part_due && h > 0) st_async_f64(pp_to, my_part, gbar_to[3 - h]);
     if (!timed_out && !mbar_wait_cluster(&gbar[warp], uint32_t(it & 1))) timed_out = true;
     if (lead && part_due && h == 0)
-      d.powers[2 * (n / d.record_every - 1) + band] =
+      d.powers[2 * rs.pslot + band] =
           (((my_part + ppeer[0]) + ppeer[1]) + ppeer[2]) * d.dx_um;
     {
       // E of frequency j from tensor memory, the next frequency's load in
@@ -441,7 +443,7 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
       const SepHead shc = sep ? sep_head(srow0) : SepHead{};
       const SepHead shn = (sep && next) ? sep_head(srow0 + 1) : SepHead{};
       const float2 g = rec ? recph[(n + 1) & 1] : make_float2(1.f, 0.f);
-      const int slot = rec ? (n + 1) / d.record_every - 1 : 0;
+      const int slot = rec ? rs.slot : 0;
       float2* r0 = (rec && d.records) ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
       double s = 0.0;
       // a loop over shared memory, as in fused4_kernel.cuh
@@ -512,7 +514,7 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
     else couple_all(BoolC<false>{});
 
     if (rec) {
-      const int slot = (n + 1) / d.record_every - 1;
+      const int slot = rs.slot;
       const float2 g = recph[(n + 1) & 1];
       double s = 0.0;
       float2* r0 = d.records ? d.records + size_t(slot) * 2 * N + band * N : nullptr;
