@@ -432,6 +432,18 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
       for (int pp = 0; pp < 8; ++pp)
         st_async_v4(co + uint32_t(xpair(pp, t, T)) * 8u, v[2 * pp], v[2 * pp + 1], cbo);
     }
+    // first order: the step's slice, and from its row head the interval mask
+    // and the coupling coefficient, while the psi_p stores are in flight
+    [[maybe_unused]] uint32_t msk1 = 0u;
+    [[maybe_unused]] float2 bs1 = bb;
+    if constexpr (!HALF) {
+      if (!timed_out && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
+      if (sep) {
+        const SepHead sh = sep_head(srow0);
+        msk1 = sep_mask<2, 8, 16>(sh, t, h);
+        bs1 = slice_b<true>(bb, sh, band);
+      }
+    }
     if (!timed_out && !mbar_wait_cluster(&cbar[half * C::WARPS + warp], uint32_t((it >> 1) & 1)))
       timed_out = true;
     if constexpr (HALF) {
@@ -493,13 +505,11 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(F4TCfg::T, 1)
         if (lane == 0) red[warp] = ds;   // summed by the lead after the next barrier
       }
     } else {
-    if (!timed_out && !mbar_wait(bar, uint32_t(it & 1))) timed_out = true;
     const float2* ci = cb + half * M;
-    const SepHead sh = sep ? sep_head(srow0) : SepHead{};
     auto couple_all = [&](auto S) {
       constexpr bool SEP = decltype(S)::value;
-      const float2 bs = slice_b<SEP>(bb, sh, band);
-      const uint32_t msk = SEP ? sep_mask<2, 8, 16>(sh, t, h) : 0u;
+      const float2 bs = SEP ? bs1 : bb;
+      const uint32_t msk = SEP ? msk1 : 0u;
 #pragma unroll
       for (int pp = 0; pp < 8; ++pp) {
         const float4 q2 = *reinterpret_cast<const float4*>(ci + xpair(pp, t, T));
